@@ -1,0 +1,379 @@
+"""Seeded synthetic inputs for the DDG two-level Schwarz PCG solver.
+
+This module builds the *problems* the solver is run on: a sparse SPD matrix
+``A`` (CSR, FP64), a non-overlapping node partition, the generating vectors
+``F`` (monomials in the nodal coordinates) and right-hand sides.  It contains
+none of the method's arithmetic (no coarse space, no Schwarz sweep, no CG):
+both the CPU oracle and the CUDA library consume what it produces, and
+neither shares any other code with the other.
+
+Problem families (structured grids, natural lexicographic order, x fastest):
+
+* 2D Poisson, 5-point FD, homogeneous Dirichlet, integer stencil [4, -1]
+  (the paper's scaling is unstated; relative residuals are scale invariant).
+* 3D Poisson, 7-point FD, homogeneous Dirichlet, integer stencil [6, -1]
+  (paper Sec. 7, problem A uses a 7-point stencil; the boundary conditions
+  here are all-Dirichlet).
+* 2D biharmonic, 13-point FD, clamped (Dirichlet + Neumann) boundary
+  (paper Sec. 7, problem F): interior stencil = square of the 5-point
+  Laplacian [20, -8, 2, 1]; u = 0 on the boundary nodes and the Neumann
+  condition by the ghost reflection u(-2) = u(0), which adds 1 to the
+  diagonal per adjacent boundary edge.
+* 3D variable-coefficient diffusion -div(kappa grad u), cell-centred FD,
+  harmonic-mean face coefficients, Dirichlet faces at half-cell distance
+  (coefficient 2*kappa), operator scaled by h^2.
+* Gaussian random field g with squared-exponential covariance
+  sigma^2 exp(-r^2 / (2 l^2)), sampled exactly through the separable
+  (Kronecker) factorisation, kappa = exp(g).
+
+Generators ``F`` (paper Sec. 4: "a small set of input vectors that span a
+low-degree polynomial space", built from nodal coordinates): all monomials
+of total degree <= p, ordered by total degree, then by descending exponent
+of x, then y (1, x, y, z, x^2, xy, xz, y^2, yz, z^2, ...).  Vector-valued
+problems take the monomials once per component.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import scipy.sparse as sp
+
+__all__ = [
+    "Problem", "poisson5_2d", "poisson7_3d", "biharmonic13_2d",
+    "varcoef7_3d", "gaussian_random_field", "box_partition", "monomials",
+    "fd_node_coords", "cell_centre_coords", "uniform_rhs", "normal_rhs",
+    "make_poisson2d", "make_poisson3d", "make_biharmonic2d",
+    "make_varcoef3d", "csr_arrays", "monomial_exponents",
+]
+
+# stencil kinds understood by the library's matrix-free SpMV (the CSR is
+# always supplied; the kind only enables a faster SpMV for the same matrix)
+STENCIL_NONE = 0
+STENCIL_5PT_2D = 1
+STENCIL_7PT_3D = 2
+STENCIL_13PT_2D = 3
+STENCIL_VAR7_3D = 4
+
+
+@dataclasses.dataclass
+class Problem:
+    """One SPD system plus everything the DDG preconditioner needs."""
+    name: str
+    A: sp.csr_matrix            # n x n, FP64, symmetric positive definite
+    shape: tuple                # grid shape (nx, ny[, nz]) of nodes/cells
+    part: np.ndarray            # int32[n], node -> non-overlapping subdomain
+    box: tuple                  # subdomain box size per axis (box partitions)
+    F: np.ndarray               # float64[n, k] generating vectors
+    f: np.ndarray               # float64[n] or [n, m] right-hand side(s)
+    overlap: int                # overlap layers Delta
+    overlap_mode: str           # "box" (L-inf growth) or "graph" (graph of A)
+    p: int                      # polynomial degree of F
+    stencil_kind: int = STENCIL_NONE
+    face_coef: Optional[np.ndarray] = None   # VAR7: float64[3, nz, ny, nx+1..]
+    kappa: Optional[np.ndarray] = None       # VAR7: cell coefficients
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def nsub(self) -> int:
+        return int(self.part.max()) + 1
+
+
+# --------------------------------------------------------------------------
+# grids and coordinates
+# --------------------------------------------------------------------------
+def _grid_index(shape):
+    """Per-axis integer coordinates of every node, x fastest."""
+    n = int(np.prod(shape))
+    idx = np.arange(n, dtype=np.int64)
+    out = []
+    stride = 1
+    for s in shape:
+        out.append((idx // stride) % s)
+        stride *= s
+    return out
+
+
+def fd_node_coords(shape):
+    """Interior FD nodes of the unit box: x_i = (i + 1) / (N + 1)."""
+    ax = _grid_index(shape)
+    return np.stack([(a + 1.0) / (s + 1.0) for a, s in zip(ax, shape)], axis=1)
+
+
+def cell_centre_coords(shape):
+    """Cell centres of a uniform grid on the unit box: x_i = (i + 1/2) / N."""
+    ax = _grid_index(shape)
+    return np.stack([(a + 0.5) / s for a, s in zip(ax, shape)], axis=1)
+
+
+def _stencil_csr(shape, offsets, weights, diag_extra=None):
+    """Assemble a constant stencil with homogeneous Dirichlet elimination.
+
+    ``offsets`` are integer tuples per axis; entries whose neighbour lies
+    outside the grid are dropped (the boundary value is zero).
+    """
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    ax = _grid_index(shape)
+    strides = np.cumprod((1,) + shape[:-1])
+    rows, cols, vals = [], [], []
+    idx = np.arange(n, dtype=np.int64)
+    for off, w in zip(offsets, weights):
+        ok = np.ones(n, dtype=bool)
+        shift = 0
+        for d, o in enumerate(off):
+            if o:
+                c = ax[d] + o
+                ok &= (c >= 0) & (c < shape[d])
+                shift += o * int(strides[d])
+        r = idx[ok]
+        rows.append(r)
+        cols.append(r + shift)
+        vals.append(np.full(r.size, float(w)))
+    if diag_extra is not None:
+        rows.append(idx)
+        cols.append(idx)
+        vals.append(diag_extra.astype(np.float64))
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    A.eliminate_zeros()
+    return A
+
+
+def poisson5_2d(nx, ny=None):
+    """5-point Laplacian [4, -1] on an nx x ny interior grid, Dirichlet."""
+    ny = nx if ny is None else ny
+    offs = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1)]
+    return _stencil_csr((nx, ny), offs, [4, -1, -1, -1, -1])
+
+
+def poisson7_3d(nx, ny=None, nz=None):
+    """7-point Laplacian [6, -1] on an nx x ny x nz interior grid, Dirichlet."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    offs = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    return _stencil_csr((nx, ny, nz), offs, [6, -1, -1, -1, -1, -1, -1])
+
+
+def biharmonic13_2d(nx, ny=None):
+    """13-point h^4 * biharmonic, clamped boundary (Sec. 7, problem F).
+
+    Interior weights: centre 20, face neighbours -8, diagonal neighbours 2,
+    distance-two axial neighbours 1.  u = 0 on the boundary ring; the
+    Neumann condition reflects the ghost two steps out onto the first
+    interior node (u(-2) = u(0)), adding 1 to the diagonal per adjacent edge.
+    """
+    ny = nx if ny is None else ny
+    offs = [(0, 0),
+            (-1, 0), (1, 0), (0, -1), (0, 1),
+            (-1, -1), (1, -1), (-1, 1), (1, 1),
+            (-2, 0), (2, 0), (0, -2), (0, 2)]
+    w = [20, -8, -8, -8, -8, 2, 2, 2, 2, 1, 1, 1, 1]
+    i, j = _grid_index((nx, ny))
+    extra = ((i == 0).astype(int) + (i == nx - 1) + (j == 0) + (j == ny - 1))
+    return _stencil_csr((nx, ny), offs, w, diag_extra=extra)
+
+
+def varcoef7_3d(kappa):
+    """Cell-centred FD of -div(kappa grad u) on the unit cube, scaled by h^2.
+
+    ``kappa`` has shape (nz, ny, nx) (x fastest when raveled).  Interior
+    face coefficient: harmonic mean 2 ka kb / (ka + kb); Dirichlet boundary
+    face at half-cell distance: 2 kappa_cell.  Returns (A, face) where
+    ``face`` = (cx[nz,ny,nx+1], cy[nz,ny+1,nx], cz[nz+1,ny,nx]) are the face
+    coefficients including boundary faces.
+    """
+    kap = np.asarray(kappa, dtype=np.float64)
+    nz, ny, nx = kap.shape
+    n = kap.size
+
+    def faces(axis):
+        k = np.moveaxis(kap, axis, 0)
+        m = k.shape[0]
+        c = np.empty((m + 1,) + k.shape[1:])
+        c[1:-1] = 2.0 * k[:-1] * k[1:] / (k[:-1] + k[1:])
+        c[0] = 2.0 * k[0]
+        c[-1] = 2.0 * k[-1]
+        return np.moveaxis(c, 0, axis)
+
+    cz, cy, cx = faces(0), faces(1), faces(2)
+    idx = np.arange(n, dtype=np.int64).reshape(nz, ny, nx)
+    diag = (cx[:, :, :-1] + cx[:, :, 1:] + cy[:, :-1, :] + cy[:, 1:, :]
+            + cz[:-1, :, :] + cz[1:, :, :])
+    rows = [idx.ravel()]
+    cols = [idx.ravel()]
+    vals = [diag.ravel()]
+    # interior faces couple the two cells with -c
+    for a, b, c in ((idx[:, :, :-1], idx[:, :, 1:], cx[:, :, 1:-1]),
+                    (idx[:, :-1, :], idx[:, 1:, :], cy[:, 1:-1, :]),
+                    (idx[:-1, :, :], idx[1:, :, :], cz[1:-1, :, :])):
+        rows += [a.ravel(), b.ravel()]
+        cols += [b.ravel(), a.ravel()]
+        vals += [-c.ravel(), -c.ravel()]
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A, (cx, cy, cz)
+
+
+def gaussian_random_field(shape, length, sigma, seed, coords="cell"):
+    """Exact sample of a squared-exponential Gaussian random field.
+
+    Covariance sigma^2 exp(-|x - y|^2 / (2 length^2)) on the grid points of
+    ``shape`` = (nx, ny, nz) (cell centres by default).  The kernel is a
+    product over axes, so g = sigma (S_z (x) S_y (x) S_x) xi with S the
+    symmetric square root of each 1D correlation matrix (eigenvalues below
+    zero from rounding are clipped to zero) and xi ~ N(0, 1) i.i.d. from
+    numpy's PCG64 generator seeded with ``seed``.  Returns an array of shape
+    (nz, ny, nx).
+    """
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    roots = []
+    for m in (nx, ny, nz):
+        x = (np.arange(m) + 0.5) / m if coords == "cell" else (np.arange(m) + 1.0) / (m + 1.0)
+        K = np.exp(-(x[:, None] - x[None, :]) ** 2 / (2.0 * length ** 2))
+        w, V = np.linalg.eigh(K)
+        w = np.clip(w, 0.0, None)
+        roots.append((V * np.sqrt(w)) @ V.T)
+    xi = rng.standard_normal((nz, ny, nx))
+    Sx, Sy, Sz = roots
+    g = np.einsum("ai,kji->kja", Sx, xi)
+    g = np.einsum("bj,kja->kba", Sy, g)
+    g = np.einsum("ck,kba->cba", Sz, g)
+    return sigma * g
+
+
+# --------------------------------------------------------------------------
+# partitions, generators, right-hand sides
+# --------------------------------------------------------------------------
+def box_partition(shape, box):
+    """Node -> subdomain id for a regular box partition (x-fastest boxes).
+
+    A trailing partial box along an axis (shape not divisible by box) is a
+    box of its own.
+    """
+    ax = _grid_index(shape)
+    nb = [(s + b - 1) // b for s, b in zip(shape, box)]
+    sid = np.zeros(ax[0].shape, dtype=np.int64)
+    stride = 1
+    for a, b, m in zip(ax, box, nb):
+        sid += (a // b) * stride
+        stride *= m
+    return sid.astype(np.int32)
+
+
+def monomial_exponents(d, p):
+    """Exponent tuples of all monomials of total degree <= p in d variables,
+    ordered by total degree, then descending exponent lexicographically."""
+    out = []
+    for deg in range(p + 1):
+        cur = []
+
+        def rec(prefix, left, dims):
+            if dims == 1:
+                cur.append(tuple(prefix + [left]))
+                return
+            for e in range(left, -1, -1):
+                rec(prefix + [e], left - e, dims - 1)
+        rec([], deg, d)
+        out += cur
+    return out
+
+
+def monomials(coords, p, components=1):
+    """Generating vectors: monomials of degree <= p in the nodal coordinates.
+
+    For ``components`` > 1 (vector problems, dofs interleaved per node) the
+    scalar monomials are placed once per component.
+    """
+    coords = np.asarray(coords, dtype=np.float64)
+    nn, d = coords.shape
+    ex = monomial_exponents(d, p)
+    S = np.empty((nn, len(ex)))
+    for c, e in enumerate(ex):
+        v = np.ones(nn)
+        for a in range(d):
+            if e[a]:
+                v = v * coords[:, a] ** e[a]
+        S[:, c] = v
+    if components == 1:
+        return S
+    F = np.zeros((nn * components, len(ex) * components))
+    for comp in range(components):
+        F[comp::components, comp * len(ex):(comp + 1) * len(ex)] = S
+    return F
+
+
+def uniform_rhs(n, seed, m=None):
+    """f ~ U(-1, 1) i.i.d. (PCG64 seeded)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=n if m is None else (n, m))
+
+
+def normal_rhs(n, seed, m=None):
+    """f ~ N(0, 1) i.i.d. (PCG64 seeded)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n if m is None else (n, m))
+
+
+def csr_arrays(A):
+    """(rowptr int64, col int32, val float64) of a scipy CSR matrix."""
+    A = A.tocsr()
+    return (np.ascontiguousarray(A.indptr, dtype=np.int64),
+            np.ascontiguousarray(A.indices, dtype=np.int32),
+            np.ascontiguousarray(A.data, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# ready-made workloads
+# --------------------------------------------------------------------------
+def make_poisson2d(N=64, box=16, overlap=2, p=2, seed=0, m=None, mode="box"):
+    """2D Poisson 5-point on N x N, box partition, U(-1,1) right-hand side."""
+    shape = (N, N)
+    A = poisson5_2d(N)
+    return Problem(name=f"poisson2d_{N}", A=A, shape=shape,
+                   part=box_partition(shape, (box, box)), box=(box, box),
+                   F=monomials(fd_node_coords(shape), p), f=uniform_rhs(A.shape[0], seed, m),
+                   overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_5PT_2D)
+
+
+def make_poisson3d(N=128, box=8, overlap=1, p=2, seed=1, m=None, mode="box"):
+    """3D Poisson 7-point on N^3, box partition, U(-1,1) right-hand side."""
+    shape = (N, N, N)
+    A = poisson7_3d(N)
+    return Problem(name=f"poisson3d_{N}", A=A, shape=shape,
+                   part=box_partition(shape, (box,) * 3), box=(box,) * 3,
+                   F=monomials(fd_node_coords(shape), p), f=uniform_rhs(A.shape[0], seed, m),
+                   overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_7PT_3D)
+
+
+def make_biharmonic2d(N=256, box=16, overlap=2, p=3, seed=100, m=None, mode="box"):
+    """2D clamped biharmonic 13-point on N x N, box partition."""
+    shape = (N, N)
+    A = biharmonic13_2d(N)
+    return Problem(name=f"biharmonic2d_{N}", A=A, shape=shape,
+                   part=box_partition(shape, (box, box)), box=(box, box),
+                   F=monomials(fd_node_coords(shape), p), f=uniform_rhs(A.shape[0], seed, m),
+                   overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_13PT_2D)
+
+
+def make_varcoef3d(N=96, box=8, overlap=1, p=2, field_seed=2, rhs_seed=3, m=64,
+                   length=0.1, sigma=1.0, mode="box"):
+    """3D cell-centred -div(exp(g) grad u) with g a GRF; N(0,1) right-hand sides."""
+    shape = (N, N, N)
+    g = gaussian_random_field(shape, length, sigma, field_seed)
+    kappa = np.exp(g)
+    A, face = varcoef7_3d(kappa)
+    return Problem(name=f"varcoef3d_{N}", A=A, shape=shape,
+                   part=box_partition(shape, (box,) * 3), box=(box,) * 3,
+                   F=monomials(cell_centre_coords(shape), p), f=normal_rhs(A.shape[0], rhs_seed, m),
+                   overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_VAR7_3D,
+                   face_coef=face, kappa=kappa)
