@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the DDG two-level Schwarz PCG solver on one GB300 per rank.
+
+Workload (the metric's configuration): 3D Poisson, 7-point FD on a 128^3
+interior grid (2,097,152 dofs), homogeneous Dirichlet, f ~ U(-1, 1) from
+seed 1; 16^3 box subdomains of 8^3 grown by one layer (10^3-dof local
+blocks, exact dense local inverses); degree <= 2 monomial generators
+(10 per subdomain, coarse dimension 40960); PCG from u = 0 to a true
+relative residual of 1e-8.
+
+A step is one full solve (every stage of the method: multiplicative
+pre-smoother sweep, coarse correction, post-smoother sweep per CG
+iteration, FP64 CG recurrence) with the inputs resident in HBM.  Setup
+(local factorisations, coarse space, coarse Cholesky) happens once before
+the timed steps and is reported separately.  The headline `value` is
+dof*iterations/s of the mixed solver (FP32 preconditioner, FP64 CG); the
+plain FP64 solver and the BF16-storage variant are timed on the same
+problem beside it, with time-to-1e-8 for each.
+
+Multi-GPU: the path does not shard (replicas only): every rank solves its
+own copy; value = all ranks' dof*iterations / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 residual & dof·iters/s: mixed+batched vs plain FP64 on 1 GB300"
+UNIT = "dof*iters/s"
+TOL = 1e-8
+WORKLOAD = dict(N=128, box=8, overlap=1, p=2, seed=1)
+SAMPLE_N = 48   # CPU oracle sample: same H/h, overlap and p on a 48^3 grid
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=WORKLOAD["N"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_from_profile(kernel_file, launch_bytes):
+    """Per-launch DRAM traffic of the local-solve kernel from the committed ncu
+    summary, scaled to this launch's algorithmic bytes; None when the summary
+    was taken on a different version of the kernel source."""
+    path = os.path.join(ROOT, "profiles", "local_solve_fp32_poisson3d.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = open(kernel_file, "rb").read()
+    sha = hashlib.sha1(src).hexdigest()[:12]
+    m = re.search(r"source sha1:\s*([0-9a-f]{12})", text)
+    r = re.search(r"traffic/algorithmic bytes:\s*([0-9.]+)", text)
+    if not m or not r or m.group(1) != sha:
+        return None
+    return float(r.group(1)) * launch_bytes
+
+
+def cpu_baseline(sample_n=SAMPLE_N):
+    """The CPU FP64 oracle, as it stands, on a bounded sample of the workload:
+    the same H/h = 8, overlap 1 and p = 2 on a sample_n^3 grid; solve-only
+    dof*iters/s (oracle setup excluded, like the GPU number)."""
+    import ddg_inputs as di
+    from oracle import ddg_oracle as orc
+    prob = di.make_poisson3d(N=sample_n, box=WORKLOAD["box"], overlap=WORKLOAD["overlap"],
+                             p=WORKLOAD["p"], seed=WORKLOAD["seed"])
+    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape)
+    t0 = time.perf_counter()
+    res = orc.pcg(M.A, prob.f, M.apply, tol=TOL)
+    dt = time.perf_counter() - t0
+    return {"value": prob.n * res.iters / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle PCG solve (setup excluded) of the same problem family on a {sample_n}^3 "
+                      f"grid ({prob.n} dofs, {prob.nsub} subdomains of 8^3, overlap 1, p=2): "
+                      f"{res.iters} iterations in {dt:.2f} s; numpy/scipy with default BLAS threads",
+            "iters": res.iters, "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    results = []
+    for _ in range(args.warmup + args.steps):
+        results.append(cpu_baseline())
+    timed = results[args.warmup:]
+    secs = sum(r["seconds"] for r in timed)
+    value = statistics.mean(r["value"] for r in timed)
+    base = timed[-1]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"poisson3d_{SAMPLE_N}^3 oracle sample of "
+                                                         f"poisson3d_{WORKLOAD['N']}^3", "H_over_h": 8,
+                                            "overlap": 1, "p": 2, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import ddg_inputs as di
+    from paper_1504_00907_gb300 import ddg
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    N = args.size
+    prob = di.make_poisson3d(N=N, box=WORKLOAD["box"], overlap=WORKLOAD["overlap"], p=WORKLOAD["p"],
+                             seed=WORKLOAD["seed"])
+    n = prob.n
+    t_setup = time.perf_counter()
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32", "bf16"))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    info = solver.info()
+    f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    u = torch.empty_like(f)
+    stream = torch.cuda.current_stream()
+
+    def timed_solves(prec, steps, warmup, profile=()):
+        solver.set_precision(prec)
+        for _ in range(warmup):
+            solver.solve(f, TOL, u)
+        torch.cuda.synchronize()
+        barrier()
+        solver.profile(profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters, rels = [], []
+        with ClockSampler(local) as cs:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                _, it, rr, st = solver.solve(f, TOL, u)
+                if st != ddg.DDG_OK:
+                    raise RuntimeError(f"{prec} solve failed with status {st}")
+                iters.append(it)
+                rels.append(rr)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        stats = solver.kernel_stats()
+        barrier()
+        return ms, iters, rels, stats, cs.summary()
+
+    # headline: mixed (FP32 preconditioner, FP64 CG)
+    ms32, it32, rr32, st32, clk = timed_solves("fp32", args.steps, args.warmup, ("local_solve",))
+    ms32 = max_over_ranks(ms32)
+    # comparison arms on the same problem
+    ms64, it64, rr64, _, clk64 = timed_solves("fp64", args.fp64_steps, 1)
+    ms64 = max_over_ranks(ms64)
+    ms16, it16, rr16, _, _ = timed_solves("bf16", args.steps, 1)
+    ms16 = max_over_ranks(ms16)
+
+    # end to end through the host-buffer entry point (copies in the timed region)
+    solver.set_precision("fp32")
+    fh = np.ascontiguousarray(prob.f)
+    solver.solve_host(fh, TOL)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        _, it, rr, st = solver.solve_host(fh, TOL)
+        e2e_iters += it
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e_value = world * n * (e2e_iters / args.steps) / e2e_s
+
+    mean_it32 = sum(it32) / len(it32)
+    value = world * n * mean_it32 / (ms32 / 1e3)
+    launches_per_step = sum(v["launches"] for v in st32.values()) / args.steps
+
+    ls = st32["local_solve"]
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    achieved = (ls["bytes"] / ls["timed"]) / (ls["ms"] / ls["timed"] / 1e3) / 1e9 if ls["timed"] else None
+    bytes_per_launch = ls["bytes"] / ls["timed"] if ls["timed"] else None
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_1504_00907_gb300", "csrc", "k_local.cu"),
+                                   bytes_per_launch) if bytes_per_launch else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "kernel": "local_solve_kernel<float,float> (packed-symmetric A_i^-1 GEMV + scatter)",
+                "peak_source": "measured" if pk else "fallback",
+                "launches_timed": ls["timed"], "avg_launch_ms": ls["ms"] / max(1, ls["timed"]),
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "share_of_step": ls["ms"] / (ms32 * args.steps)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 CG + f32 preconditioner", "data": "synthetic",
+        "config": {"workload": f"poisson3d_{N}^3: 7-pt FD, Dirichlet, 8^3 boxes + overlap 1 "
+                               f"(10^3 local blocks), p<=2 monomials, PCG to 1e-8",
+                   "dofs": n, "subdomains": info["nsub"], "coarse_dim": info["n0"],
+                   "colours": info["ncolours"], "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (local inverses: "
+                         f"{info['local_tiles'] * 4096 / 1e9:.1f} GB FP32)"},
+        "time_to_1e-8_s": {"mixed_fp32": ms32 / 1e3, "fp64_plain": ms64 / 1e3, "mixed_bf16": ms16 / 1e3},
+        "iters": {"mixed_fp32": it32[-1], "fp64_plain": it64[-1], "mixed_bf16": it16[-1]},
+        "true_relres": {"mixed_fp32": rr32[-1], "fp64_plain": rr64[-1], "mixed_bf16": rr16[-1]},
+        "dof_iters_per_s": {"mixed_fp32": value, "fp64_plain": world * n * it64[-1] / (ms64 / 1e3),
+                            "mixed_bf16": world * n * it16[-1] / (ms16 / 1e3)},
+        "speedup_mixed_vs_fp64": ms64 / ms32,
+        "setup_s": setup_s, "setup_ms_library": info["setup_ms"],
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "gpu_launches_per_step": launches_per_step,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n, "api": "ddg_solve_host"},
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline().items() if k not in ("iters", "seconds")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * ddg.h -- C ABI of the GB300 (sm_103a) DDG two-level Schwarz PCG solver.
+ *
+ * Method: Edwards & Bridson, "The Discretely-Discontinuous Galerkin Coarse
+ * Grid for Domain Decomposition" (arXiv 1504.00907).
+ *   - Sec. 1: the input is a sparse SPD system A u = f.
+ *   - Sec. 4, Fig. 1: the coarse restriction R0 has one row per (subdomain,
+ *     generating vector): column j of F restricted to the non-overlapping
+ *     subdomain i, orthonormalised per subdomain, rank-deficient columns
+ *     dropped; coarse dofs numbered subdomain-major, generator-minor.
+ *     A0 = R0 A R0^T (Galerkin projection).
+ *   - Sec. 6: overlapping subdomains grow each partition by Delta layers;
+ *     local matrices A_i = R~_i A R~_i^T are solved exactly; one pass of
+ *     multiplicative Schwarz (pre-smoother), the coarse correction, and the
+ *     pass in reverse order (post-smoother) form a symmetric preconditioner.
+ *   - Sec. 7: conjugate gradient from u0 = 0 with that preconditioner.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a ddg_status; nothing throws across the ABI.
+ *     ddg_last_error(h) gives a message for the last failing call on h
+ *     (ddg_last_error(NULL) for a failing ddg_setup).
+ *   - "host" pointers are read during the call only and stay owned by the
+ *     caller.  "device" pointers are caller-owned CUDA device memory on the
+ *     current device; the library never frees them.  All device work is
+ *     enqueued on the stream given to ddg_setup (or ddg_set_stream) and the
+ *     calls that return scalars synchronise that stream before returning.
+ *   - Vectors are FP64, natural (caller) dof order, length n.  Multi-RHS
+ *     blocks are dof-major: entry (dof g, rhs j) at g * m + j.
+ *   - One handle must not be used from two host threads at once.
+ */
+#ifndef DDG_H
+#define DDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddg_handle_s* ddg_handle;   /* opaque, library-owned */
+
+typedef enum {
+    DDG_OK = 0,
+    DDG_EINVAL = 1,       /* invalid argument (sizes, ids, pointers, options) */
+    DDG_ENOMEM = 2,       /* device allocation failed */
+    DDG_ENOTSPD = 3,      /* a local or the coarse Cholesky met a non-positive pivot */
+    DDG_EBREAKDOWN = 4,   /* CG breakdown: p^T A p <= 0 or a NaN */
+    DDG_ENOCONV = 5,      /* maxit reached; u holds the last iterate */
+    DDG_ETIMEOUT = 6,     /* reserved: a bounded device wait ran out */
+    DDG_ECUDA = 7         /* a CUDA runtime call failed */
+} ddg_status;
+
+/* arithmetic of the preconditioner apply (local solves, coarse solve,
+ * restriction/prolongation); the CG recurrence is always FP64 */
+enum { DDG_PREC_FP64 = 0, DDG_PREC_FP32 = 1, DDG_PREC_BF16 = 2 };
+/* Sec. 6 overlap: GRAPH = graph distance Delta in the graph of A (the
+ * paper's definition); BOX = L-infinity grid distance Delta (needs the grid
+ * shape in ddg_matrix; dofs must be in natural x-fastest grid order) */
+enum { DDG_OVERLAP_GRAPH = 0, DDG_OVERLAP_BOX = 1 };
+/* CG beta: Fletcher-Reeves (textbook) or Polak-Ribiere (flexible) */
+enum { DDG_BETA_FR = 0, DDG_BETA_PR = 1, DDG_BETA_AUTO = 2 };
+/* optional structure of A that enables a matrix-free SpMV for the FP64
+ * CG products; the CSR must still describe the same matrix */
+enum {
+    DDG_STENCIL_NONE = 0,
+    DDG_STENCIL_5PT_2D = 1,   /* [4, -1], Dirichlet, nx x ny */
+    DDG_STENCIL_7PT_3D = 2,   /* [6, -1], Dirichlet, nx x ny x nz */
+    DDG_STENCIL_13PT_2D = 3,  /* clamped biharmonic (CSR SpMV is used) */
+    DDG_STENCIL_VAR7_3D = 4   /* cell-centred variable coefficient */
+};
+
+typedef struct {
+    int precision;        /* DDG_PREC_*, default DDG_PREC_FP64 */
+    int keep_precisions;  /* bitmask of (1 << DDG_PREC_*) local-inverse copies
+                             to keep for ddg_set_precision; 0 = `precision` only */
+    int overlap_mode;     /* DDG_OVERLAP_*, default GRAPH */
+    int beta;             /* DDG_BETA_*, default AUTO (FR for FP64, PR otherwise) */
+    int maxit;            /* default 1000 (Sec. 7 stops CG at 1000 iterations) */
+    int use_coarse;       /* 1 = two-level (default), 0 = one-level Schwarz */
+    double rank_tol;      /* Sec. 4 rank drop: keep column j while |R_jj| >
+                             rank_tol * |R_00|; default 1e-10 */
+    int chunk_tiles;      /* local-solve work item size in 32x32 tiles; 0 = auto */
+} ddg_options;
+
+typedef struct {
+    int64_t n;               /* rows = columns */
+    const int64_t* rowptr;   /* host [n + 1] */
+    const int32_t* col;      /* host [nnz], column ids in [0, n), sorted per row */
+    const double* val;       /* host [nnz]; A must be symmetric positive definite */
+    int dim;                 /* grid dimension (2 or 3) for BOX overlap, else 0 */
+    int nx, ny, nz;          /* grid shape (x fastest); nz = 1 in 2D */
+    int dofs_per_node;       /* interleaved dofs per grid node (1 for scalars) */
+    int stencil_kind;        /* DDG_STENCIL_* */
+    const double* coef;      /* host, VAR7 only: cell coefficients kappa[nz][ny][nx]
+                                (x fastest), needed by ddg_grad_coeff; else NULL */
+} ddg_matrix;
+
+typedef struct {
+    int64_t n;            /* fine dofs */
+    int nsub;             /* subdomains */
+    int ncolours;         /* colours of the multiplicative sweep */
+    int n0;               /* coarse dimension after rank drop */
+    int kmax;             /* generators per subdomain (columns of F) */
+    int max_local;        /* largest overlapping subdomain |Omega~_i| */
+    int64_t sum_local;    /* sum of |Omega~_i| */
+    int64_t local_tiles;  /* packed 32x32 tiles of all local inverses */
+    int coarse_band;      /* half-bandwidth of A0 in natural coarse order */
+    int coarse_blocks;    /* super-blocks of the coarse block-bidiagonal factor */
+    double setup_ms;      /* wall time of ddg_setup */
+    int precision;        /* current preconditioner precision */
+} ddg_info;
+
+/* Fill *opt with the defaults listed above. */
+void ddg_default_options(ddg_options* opt);
+
+/*
+ * Build the preconditioner for A (Sec. 4 and Sec. 6).
+ *   A          host CSR (+ optional grid/stencil description), copied.
+ *   partition  host int32[n]: node -> non-overlapping subdomain id; ids
+ *              must cover [0, nsub) (empty subdomains are rejected).
+ *   F          host FP64 [n * k], column-major (column j at F + j * n): the
+ *              generating vectors; k >= 1, or k = 0 with use_coarse = 0.
+ *   overlap    Delta >= 0 layers.
+ *   stream     cudaStream_t for all work of this handle (NULL = default).
+ *   out        receives the handle.
+ * Errors: DDG_EINVAL (bad sizes/ids/options), DDG_ENOTSPD (a local or the
+ * coarse factorisation failed), DDG_ENOMEM, DDG_ECUDA.
+ */
+ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double* F, int k,
+                     int overlap, const ddg_options* opt, void* stream, ddg_handle* out);
+
+/*
+ * Solve A u = f by PCG from u0 = 0 (Sec. 7): stop when the recurrence
+ * residual satisfies ||r||_2 <= tol ||f||_2 and the true residual does too
+ * (a recurrence that drifts is replaced by the true residual and CG
+ * restarts).  f, u: device FP64 [n].  *iters: iterations taken; *relres:
+ * true relative residual ||f - A u|| / ||f||.  Either output may be NULL.
+ * Errors: DDG_ENOCONV (maxit reached, u is the last iterate),
+ * DDG_EBREAKDOWN, DDG_EINVAL, DDG_ECUDA.
+ */
+ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters,
+                     double* relres);
+
+/* Same as ddg_solve with host FP64 f and u: the copies to and from the
+ * device are part of the call. */
+ddg_status ddg_solve_host(ddg_handle h, const double* f_host, double* u_host, double tol,
+                          int* iters, double* relres);
+
+/*
+ * Multi-RHS solve: F and U are device FP64 [n * m], dof-major.  Each column
+ * runs its own CG (own alpha, beta, convergence); the preconditioner is
+ * applied to all unconverged columns at once.  iters: host int[m] or NULL;
+ * relres: host double[m] or NULL.
+ */
+ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, double tol,
+                           int* iters, double* relres);
+
+/* Adjoint solve lambda = A^{-T} g for a loss gradient g = dL/du (device
+ * [n]); A is symmetric, so this reuses the preconditioner and CG. */
+ddg_status ddg_adjoint(ddg_handle h, const double* dLdu, double* lambda, double tol,
+                       int* iters, double* relres);
+
+/* Coefficient gradient dL/dkappa = -lambda^T (dA/dkappa) u for a
+ * DDG_STENCIL_VAR7_3D handle: lambda, u device [n]; dkappa device [n]
+ * (one entry per cell, the chain rule through the harmonic-mean faces). */
+ddg_status ddg_grad_coeff(ddg_handle h, const double* lambda, const double* u, double* dkappa);
+
+/* One preconditioner application z = M^{-1} r (Sec. 6), r and z device
+ * FP64 [n], in the handle's current precision. */
+ddg_status ddg_apply_preconditioner(ddg_handle h, const double* r, double* z);
+
+/* Coarse correction alone: z = R0^T A0^{-1} R0 r (Sec. 4). */
+ddg_status ddg_coarse_correction(ddg_handle h, const double* r, double* z);
+
+/* y = A x in FP64 (device [n]). */
+ddg_status ddg_spmv(ddg_handle h, const double* x, double* y);
+
+/* Switch the preconditioner precision (must be among keep_precisions). */
+ddg_status ddg_set_precision(ddg_handle h, int precision);
+ddg_status ddg_set_stream(ddg_handle h, void* stream);
+ddg_status ddg_get_info(ddg_handle h, ddg_info* info);
+/* host int32[nsub]: colour of every subdomain (sweep order = colour-major,
+ * ids ascending inside a colour; the post-smoother is the exact reverse). */
+ddg_status ddg_get_colouring(ddg_handle h, int32_t* colour);
+/* host int32[nsub + 1]: coarse dof offsets per subdomain (after rank drop). */
+ddg_status ddg_get_coarse_offsets(ddg_handle h, int32_t* offsets);
+/* host double[max_len]: recurrence residual history ||r_k|| / ||f|| of the
+ * last single-RHS solve, k = 0..iters; returns the count in *len. */
+ddg_status ddg_get_history(ddg_handle h, double* hist, int max_len, int* len);
+
+/* ---- tracing: per kernel class, launches are always counted; CUDA-event
+ * timing of each launch (on the handle's stream) is on for the classes in
+ * the mask given to ddg_profile.  bytes are the algorithmic bytes of the
+ * timed launches (local solve: the packed upper triangle of every A_i^{-1}
+ * of the colour, n_i (n_i + 1) / 2 elements, plus the local residual read and
+ * z read + write; no tile padding counted). */
+enum {
+    DDG_K_LOCAL_SOLVE = 0,    /* packed-inverse GEMV + scatter, one per colour */
+    DDG_K_LOCAL_RESIDUAL = 1, /* (r - A z) gathered on the colour's subdomains */
+    DDG_K_COARSE = 2,         /* restrict, block-bidiagonal solves, prolong */
+    DDG_K_SPMV = 3,           /* FP64 SpMV of the CG recurrence */
+    DDG_K_CG = 4,             /* CG vector updates, dots, conversions */
+    DDG_K_COUNT = 5
+};
+typedef struct {
+    int64_t launches;   /* kernels launched since the last ddg_profile(h, mask) */
+    int64_t timed;      /* launches that were timed with CUDA events */
+    double ms;          /* summed event durations of the timed launches */
+    double bytes;       /* algorithmic bytes of the timed launches */
+} ddg_kernel_stat;
+/* Reset all counters and time the classes whose bit (1 << DDG_K_*) is set. */
+ddg_status ddg_profile(ddg_handle h, int timed_mask);
+/* stats: host ddg_kernel_stat[DDG_K_COUNT]; synchronises the stream. */
+ddg_status ddg_get_kernel_stats(ddg_handle h, ddg_kernel_stat* stats);
+
+ddg_status ddg_destroy(ddg_handle h);
+const char* ddg_last_error(ddg_handle h);
+const char* ddg_status_string(ddg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDG_H */

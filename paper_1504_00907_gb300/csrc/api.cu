@@ -1,0 +1,884 @@
+// C ABI entry points of the DDG solver: setup orchestration (host graph
+// work + device numerics) and the PCG driver (Sec. 7).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ddg_internal.cuh"
+
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------- host graph work
+// Sec. 6: Omega~_i = all dofs within distance Delta of Omega_i, in the graph of
+// A (GRAPH) or in the L-infinity neighbour graph of the grid nodes (BOX).
+void grow_overlaps(const ddg_matrix* A, const std::vector<int64_t>& sub_off,
+                   const std::vector<int32_t>& sub_nodes, int nsub, int delta, int mode,
+                   std::vector<std::vector<int32_t>>& out) {
+    const int64_t n = A->n;
+    out.assign(nsub, {});
+    std::vector<int32_t> stamp(n, -1);
+    std::vector<int32_t> frontier, next;
+    const int dpn = A->dofs_per_node > 0 ? A->dofs_per_node : 1;
+    const int nx = A->nx, ny = A->ny, nz = A->dim == 3 ? A->nz : 1;
+    for (int s = 0; s < nsub; ++s) {
+        std::vector<int32_t>& om = out[s];
+        frontier.clear();
+        for (int64_t a = sub_off[s]; a < sub_off[s + 1]; ++a) {
+            const int32_t g = sub_nodes[a];
+            stamp[g] = s;
+            om.push_back(g);
+            frontier.push_back(g);
+        }
+        for (int layer = 0; layer < delta; ++layer) {
+            next.clear();
+            for (int32_t g : frontier) {
+                if (mode == DDG_OVERLAP_GRAPH) {
+                    for (int64_t e = A->rowptr[g]; e < A->rowptr[g + 1]; ++e) {
+                        const int32_t c = A->col[e];
+                        if (stamp[c] != s) {
+                            stamp[c] = s;
+                            om.push_back(c);
+                            next.push_back(c);
+                        }
+                    }
+                } else {
+                    const int64_t node = g / dpn;
+                    const int i = (int)(node % nx), j = (int)((node / nx) % ny), k = (int)(node / ((int64_t)nx * ny));
+                    for (int dk = (A->dim == 3 ? -1 : 0); dk <= (A->dim == 3 ? 1 : 0); ++dk)
+                        for (int dj = -1; dj <= 1; ++dj)
+                            for (int di = -1; di <= 1; ++di) {
+                                const int ii = i + di, jj = j + dj, kk = k + dk;
+                                if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
+                                const int64_t nb = ii + (int64_t)nx * (jj + (int64_t)ny * kk);
+                                for (int c = 0; c < dpn; ++c) {
+                                    const int32_t d = (int32_t)(nb * dpn + c);
+                                    if (stamp[d] != s) {
+                                        stamp[d] = s;
+                                        om.push_back(d);
+                                        next.push_back(d);
+                                    }
+                                }
+                            }
+                }
+            }
+            frontier.swap(next);
+        }
+        std::sort(om.begin(), om.end());
+    }
+}
+
+// greedy colouring in id order: i and j conflict when Omega~_j meets the
+// one-step neighbourhood of Omega~_i in the graph of A
+std::vector<int> colour_subdomains(const ddg_matrix* A, const std::vector<std::vector<int32_t>>& ov) {
+    const int64_t n = A->n;
+    const int nsub = (int)ov.size();
+    std::vector<int64_t> own_off(n + 1, 0);
+    for (const auto& o : ov)
+        for (int32_t g : o) own_off[g + 1]++;
+    for (int64_t g = 0; g < n; ++g) own_off[g + 1] += own_off[g];
+    std::vector<int32_t> owners(own_off[n]);
+    std::vector<int64_t> fill(own_off.begin(), own_off.end() - 1);
+    for (int s = 0; s < nsub; ++s)
+        for (int32_t g : ov[s]) owners[fill[g]++] = s;
+    std::vector<int> colour(nsub, -1), used;
+    std::vector<int32_t> seen(nsub, -1);
+    for (int i = 0; i < nsub; ++i) {
+        std::vector<int> nbcol;
+        auto visit = [&](int32_t c) {
+            for (int64_t t = own_off[c]; t < own_off[c + 1]; ++t) {
+                const int j = owners[t];
+                if (j < i && seen[j] != i) {
+                    seen[j] = i;
+                    nbcol.push_back(colour[j]);
+                }
+            }
+        };
+        for (int32_t g : ov[i]) {
+            visit(g);
+            for (int64_t e = A->rowptr[g]; e < A->rowptr[g + 1]; ++e) visit(A->col[e]);
+        }
+        std::sort(nbcol.begin(), nbcol.end());
+        int c = 0;
+        for (int v : nbcol) {
+            if (v == c) ++c;
+            else if (v > c) break;
+        }
+        colour[i] = c;
+    }
+    return colour;
+}
+
+void validate(const ddg_matrix* A, const int32_t* part, const double* F, int k, int overlap,
+              const ddg_options& o) {
+    DDG_REQUIRE(A && A->rowptr && A->col && A->val, DDG_EINVAL, "A and its CSR arrays must be non-null");
+    DDG_REQUIRE(A->n > 0 && A->n < (int64_t)INT32_MAX, DDG_EINVAL, "n must be in [1, 2^31)");
+    DDG_REQUIRE(A->rowptr[0] == 0, DDG_EINVAL, "rowptr[0] must be 0");
+    for (int64_t g = 0; g < A->n; ++g)
+        DDG_REQUIRE(A->rowptr[g + 1] >= A->rowptr[g], DDG_EINVAL, "rowptr must be non-decreasing");
+    const int64_t nnz = A->rowptr[A->n];
+    for (int64_t e = 0; e < nnz; ++e)
+        DDG_REQUIRE(A->col[e] >= 0 && A->col[e] < A->n, DDG_EINVAL, "column index out of range");
+    DDG_REQUIRE(part, DDG_EINVAL, "partition must be non-null");
+    for (int64_t g = 0; g < A->n; ++g)
+        DDG_REQUIRE(part[g] >= 0 && part[g] < INT32_MAX, DDG_EINVAL, "partition ids must be >= 0");
+    DDG_REQUIRE(overlap >= 0, DDG_EINVAL, "overlap must be >= 0");
+    DDG_REQUIRE(o.precision >= DDG_PREC_FP64 && o.precision <= DDG_PREC_BF16, DDG_EINVAL, "bad precision");
+    DDG_REQUIRE(o.overlap_mode == DDG_OVERLAP_GRAPH || o.overlap_mode == DDG_OVERLAP_BOX, DDG_EINVAL,
+                "bad overlap_mode");
+    if (o.overlap_mode == DDG_OVERLAP_BOX) {
+        DDG_REQUIRE(A->dim == 2 || A->dim == 3, DDG_EINVAL, "BOX overlap needs dim 2 or 3");
+        const int64_t nodes = (int64_t)A->nx * A->ny * (A->dim == 3 ? A->nz : 1);
+        const int dpn = A->dofs_per_node > 0 ? A->dofs_per_node : 1;
+        DDG_REQUIRE(nodes * dpn == A->n, DDG_EINVAL, "grid shape * dofs_per_node must equal n");
+    }
+    if (A->stencil_kind == DDG_STENCIL_7PT_3D || A->stencil_kind == DDG_STENCIL_VAR7_3D)
+        DDG_REQUIRE((int64_t)A->nx * A->ny * A->nz == A->n, DDG_EINVAL, "3D stencil shape must match n");
+    if (A->stencil_kind == DDG_STENCIL_5PT_2D || A->stencil_kind == DDG_STENCIL_13PT_2D)
+        DDG_REQUIRE((int64_t)A->nx * A->ny == A->n, DDG_EINVAL, "2D stencil shape must match n");
+    if (o.use_coarse) {
+        DDG_REQUIRE(F, DDG_EINVAL, "F must be non-null for the two-level method");
+        DDG_REQUIRE(k >= 1 && k <= DDG_KMAX, DDG_EINVAL, "k must be in [1, 32]");
+    }
+    DDG_REQUIRE(o.maxit >= 1, DDG_EINVAL, "maxit must be >= 1");
+}
+
+// ---------------------------------------------------------------- preconditioner
+void local_step(ddg_handle h, int c, bool z_zero, int prec) {
+    {
+        ProfScope ps(h, DDG_K_LOCAL_RESIDUAL, 1, 0.0);
+        ddg::local_residual(h, c, z_zero, prec);
+    }
+    ProfScope ps(h, DDG_K_LOCAL_SOLVE, 1, h->colour_bytes[prec][c]);
+    ddg::local_solve_colour(h, c, prec);
+}
+
+void coarse_step(ddg_handle h, int prec, bool residual) {
+    ProfScope ps(h, DDG_K_COARSE, 2 + 4 * h->nK - 2, 0.0);
+    ddg::coarse_restrict(h, prec, residual);
+    ddg::coarse_solve(h, prec);
+    ddg::coarse_prolong(h, prec);
+}
+
+void apply_prec(ddg_handle h, const double* rin) {
+    const int prec = h->precision;
+    if (prec == DDG_PREC_FP64) {
+        h->rin64 = rin;
+        DDG_CUDA(cudaMemsetAsync(h->z64, 0, h->n * sizeof(double), h->stream));
+    } else {
+        ProfScope ps(h, DDG_K_CG, 1, 0.0);
+        ddg::convert_to_float(h, rin, h->r32);
+        DDG_CUDA(cudaMemsetAsync(h->z32, 0, h->n * sizeof(float), h->stream));
+    }
+    // pre-smoother: one multiplicative pass in sweep order
+    for (int c = 0; c < h->ncol; ++c) local_step(h, c, c == 0, prec);
+    // coarse correction of the current residual
+    if (h->use_coarse) coarse_step(h, prec, true);
+    // post-smoother: the same pass in reverse order
+    for (int c = h->ncol - 1; c >= 0; --c) local_step(h, c, false, prec);
+}
+
+void read_scalars(ddg_handle h) {
+    d2h(h->h_scal, h->scal, S_COUNT, h->stream);
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// PCG from u = 0 (Sec. 7).  Returns the status; u, history, iters, relres set.
+ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_out, double* relres_out) {
+    const int prec = h->precision;
+    const int beta = h->opt.beta == DDG_BETA_AUTO ? (prec == DDG_PREC_FP64 ? DDG_BETA_FR : DDG_BETA_PR)
+                                                  : h->opt.beta;
+    const int pr = beta == DDG_BETA_PR;
+    h->history.clear();
+    {
+        ProfScope ps(h, DDG_K_CG, 1, 0.0);
+        ddg::dot64(h, f, f, S_TMP);
+    }
+    read_scalars(h);
+    const double fn = std::sqrt(h->h_scal[S_TMP]);
+    DDG_CUDA(cudaMemsetAsync(u, 0, h->n * sizeof(double), h->stream));
+    if (!(fn > 0.0)) {
+        if (iters_out) *iters_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        h->history.push_back(0.0);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return fn == fn ? DDG_OK : DDG_EINVAL;
+    }
+    h->history.push_back(1.0);
+    h->u = u;
+    {
+        ProfScope ps(h, DDG_K_CG, 1, 0.0);
+        ddg::set_scalar(h, S_FLAG, 0.0);
+    }
+    DDG_CUDA(cudaMemcpyAsync(h->r, f, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    auto restart = [&]() {
+        apply_prec(h, h->r);
+        ProfScope ps(h, DDG_K_CG, 2, 0.0);
+        ddg::cg_dots_after_precond(h, prec, true, pr);
+        ddg::cg_update_p(h, prec, true);
+    };
+    restart();
+    int it = 0, restarts = 0;
+    ddg_status st = DDG_ENOCONV;
+    double true_rel = -1.0;
+    while (it < h->opt.maxit) {
+        {
+            ProfScope ps(h, DDG_K_SPMV, 1, 0.0);
+            ddg::spmv64(h, h->p, h->q, true, S_PQ);
+        }
+        {
+            ProfScope ps(h, DDG_K_CG, 1, 0.0);
+            ddg::cg_update_ur(h);
+        }
+        read_scalars(h);
+        ++it;
+        if (h->h_scal[S_FLAG] != 0.0) {
+            st = DDG_EBREAKDOWN;
+            break;
+        }
+        const double rel = std::sqrt(h->h_scal[S_RR]) / fn;
+        h->history.push_back(rel);
+        if (rel <= tol) {
+            // verify against the true residual; replace and restart if the
+            // recurrence has drifted
+            {
+                ProfScope ps(h, DDG_K_CG, 2, 0.0);
+                ddg::residual64(h, f, u, h->q);
+                ddg::dot64(h, h->q, h->q, S_TMP);
+            }
+            read_scalars(h);
+            true_rel = std::sqrt(h->h_scal[S_TMP]) / fn;
+            if (true_rel <= tol || restarts >= 3) {
+                st = true_rel <= tol ? DDG_OK : DDG_ENOCONV;
+                break;
+            }
+            DDG_CUDA(cudaMemcpyAsync(h->r, h->q, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            ++restarts;
+            restart();
+            true_rel = -1.0;
+            continue;
+        }
+        apply_prec(h, h->r);
+        ProfScope ps(h, DDG_K_CG, 2, 0.0);
+        ddg::cg_dots_after_precond(h, prec, false, pr);
+        ddg::cg_update_p(h, prec, false);
+    }
+    if (true_rel < 0.0) {
+        ProfScope ps(h, DDG_K_CG, 2, 0.0);
+        ddg::residual64(h, f, u, h->q);
+        ddg::dot64(h, h->q, h->q, S_TMP);
+        read_scalars(h);
+        true_rel = std::sqrt(h->h_scal[S_TMP]) / fn;
+    }
+    h->u = nullptr;
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = true_rel;
+    return st;
+}
+
+void prof_flush(ddg_handle h) {
+    if (h->ev_used == 0) return;
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < h->ev_used; ++i) {
+        float ms = 0.f;
+        DDG_CUDA(cudaEventElapsedTime(&ms, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
+        h->prof_ms[h->ev_class[i]] += ms;
+        h->prof_bytes[h->ev_class[i]] += h->ev_bytes[i];
+        h->prof_timed[h->ev_class[i]] += 1;
+    }
+    h->ev_used = 0;
+}
+
+template <typename Fn>
+ddg_status guarded(ddg_handle h, Fn&& fn) {
+    if (!h) return DDG_EINVAL;
+    try {
+        h->err.clear();
+        return fn();
+    } catch (DdgError& e) {
+        h->err = e.msg;
+        return e.st;
+    } catch (std::exception& e) {
+        h->err = e.what();
+        return DDG_EINVAL;
+    }
+}
+
+}  // namespace
+
+ProfScope::ProfScope(ddg_handle hh, int c, int nlaunch, double bytes) : h(hh), cls(c), pair(-1) {
+    h->prof_launches[c] += nlaunch;
+    if (!(h->prof_mask & (1 << c))) return;
+    if (h->ev_used * 2 + 2 > h->ev_pool.size()) {
+        for (int i = 0; i < 256; ++i) {
+            cudaEvent_t e;
+            DDG_CUDA(cudaEventCreate(&e));
+            h->ev_pool.push_back(e);
+        }
+    }
+    pair = (int)h->ev_used++;
+    if (h->ev_class.size() < h->ev_used) {
+        h->ev_class.resize(h->ev_used);
+        h->ev_bytes.resize(h->ev_used);
+    }
+    h->ev_class[pair] = c;
+    h->ev_bytes[pair] = bytes;
+    DDG_CUDA(cudaEventRecord(h->ev_pool[2 * pair], h->stream));
+}
+
+ProfScope::~ProfScope() {
+    if (pair >= 0) cudaEventRecord(h->ev_pool[2 * pair + 1], h->stream);
+}
+
+extern "C" {
+
+void ddg_default_options(ddg_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = DDG_PREC_FP64;
+    o->keep_precisions = 0;
+    o->overlap_mode = DDG_OVERLAP_GRAPH;
+    o->beta = DDG_BETA_AUTO;
+    o->maxit = 1000;
+    o->use_coarse = 1;
+    o->rank_tol = 1e-10;
+    o->chunk_tiles = 0;
+}
+
+ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double* F, int k,
+                     int overlap, const ddg_options* opt, void* stream, ddg_handle* out) {
+    g_setup_error.clear();
+    if (!out) {
+        g_setup_error = "out must be non-null";
+        return DDG_EINVAL;
+    }
+    *out = nullptr;
+    const double t0 = now_ms();
+    ddg_handle h = new ddg_handle_s;
+    try {
+        ddg_options o;
+        if (opt) o = *opt;
+        else ddg_default_options(&o);
+        validate(A, partition, F, k, overlap, o);
+        h->opt = o;
+        h->precision = o.precision;
+        h->use_coarse = o.use_coarse;
+        h->stream = (cudaStream_t)stream;
+        const int64_t n = A->n;
+        h->n = n;
+        h->nnz = A->rowptr[n];
+        h->stencil_kind = A->stencil_kind;
+        h->dim = A->dim;
+        h->nx = A->nx > 0 ? A->nx : 1;
+        h->ny = A->ny > 0 ? A->ny : 1;
+        h->nz = A->nz > 0 ? A->nz : 1;
+        h->dpn = A->dofs_per_node > 0 ? A->dofs_per_node : 1;
+        const int keep = (o.keep_precisions ? o.keep_precisions : 0) | (1 << o.precision);
+        h->opt.keep_precisions = keep;
+
+        // ---- fine matrix
+        h->rowptr = h->arena.alloc<int64_t>(n + 1);
+        h->col = h->arena.alloc<int32_t>(h->nnz);
+        h->val64 = h->arena.alloc<double>(h->nnz);
+        h->val32 = h->arena.alloc<float>(h->nnz);
+        h2d(h->rowptr, A->rowptr, n + 1, h->stream);
+        h2d(h->col, A->col, h->nnz, h->stream);
+        h2d(h->val64, A->val, h->nnz, h->stream);
+        {
+            std::vector<float> v32(A->val, A->val + h->nnz);
+            h2d(h->val32, v32.data(), h->nnz, h->stream);
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
+        }
+        if (A->stencil_kind == DDG_STENCIL_VAR7_3D && A->coef) {
+            h->kappa = h->arena.alloc<double>(n);
+            h2d(h->kappa, A->coef, n, h->stream);
+        }
+
+        // ---- partition (Sec. 4)
+        int nsub = 0;
+        for (int64_t g = 0; g < n; ++g) {
+            DDG_REQUIRE(partition[g] >= 0, DDG_EINVAL, "partition ids must be >= 0");
+            nsub = std::max(nsub, partition[g] + 1);
+        }
+        h->nsub = nsub;
+        std::vector<int64_t> sub_off(nsub + 1, 0);
+        for (int64_t g = 0; g < n; ++g) sub_off[partition[g] + 1]++;
+        for (int s = 0; s < nsub; ++s) {
+            DDG_REQUIRE(sub_off[s + 1] > 0, DDG_EINVAL, "every subdomain id in [0, nsub) must own a node");
+            sub_off[s + 1] += sub_off[s];
+        }
+        std::vector<int32_t> sub_nodes(n), pos(n);
+        {
+            std::vector<int64_t> fill(sub_off.begin(), sub_off.end() - 1);
+            for (int64_t g = 0; g < n; ++g) {
+                const int64_t a = fill[partition[g]]++;
+                sub_nodes[a] = (int32_t)g;
+                pos[g] = (int32_t)a;
+            }
+        }
+        h->h_sub_off = sub_off;
+        h->part = h->arena.alloc<int32_t>(n);
+        h->sub_off = h->arena.alloc<int64_t>(nsub + 1);
+        h->sub_nodes = h->arena.alloc<int32_t>(n);
+        h->pos = h->arena.alloc<int32_t>(n);
+        h2d(h->part, partition, n, h->stream);
+        h2d(h->sub_off, sub_off.data(), nsub + 1, h->stream);
+        h2d(h->sub_nodes, sub_nodes.data(), n, h->stream);
+        h2d(h->pos, pos.data(), n, h->stream);
+
+        // ---- overlapping subdomains, colouring, sweep order (Sec. 6)
+        std::vector<std::vector<int32_t>> ov;
+        grow_overlaps(A, sub_off, sub_nodes, nsub, overlap, o.overlap_mode, ov);
+        h->h_colour = colour_subdomains(A, ov);
+        h->ncol = 1 + *std::max_element(h->h_colour.begin(), h->h_colour.end());
+        h->h_csub_off.assign(h->ncol + 1, 0);
+        h->h_sid.clear();
+        for (int c = 0; c < h->ncol; ++c) {
+            for (int s = 0; s < nsub; ++s)
+                if (h->h_colour[s] == c) h->h_sid.push_back(s);
+            h->h_csub_off[c + 1] = (int)h->h_sid.size();
+        }
+        std::vector<int64_t> ov_off(nsub + 1, 0);
+        std::vector<int32_t> Tq(nsub);
+        std::vector<int64_t> tile_off(nsub + 1, 0);
+        h->max_local = 0;
+        for (int q = 0; q < nsub; ++q) {
+            const int nq = (int)ov[h->h_sid[q]].size();
+            ov_off[q + 1] = ov_off[q] + nq;
+            Tq[q] = (nq + DDG_LT - 1) / DDG_LT;
+            tile_off[q + 1] = tile_off[q] + (int64_t)Tq[q] * (Tq[q] + 1) / 2;
+            h->max_local = std::max(h->max_local, nq);
+        }
+        h->sum_local = ov_off[nsub];
+        h->total_tiles = tile_off[nsub];
+        h->Tmax = (h->max_local + DDG_LT - 1) / DDG_LT;
+        DDG_REQUIRE(h->Tmax <= 64, DDG_EINVAL, "overlapping subdomains larger than 2048 dofs are not supported");
+        h->h_ov_off = ov_off;
+        h->h_crow_off.assign(h->ncol + 1, 0);
+        for (int c = 0; c < h->ncol; ++c) h->h_crow_off[c + 1] = ov_off[h->h_csub_off[c + 1]];
+        {
+            std::vector<int32_t> ov_nodes(h->sum_local);
+            for (int q = 0; q < nsub; ++q)
+                std::copy(ov[h->h_sid[q]].begin(), ov[h->h_sid[q]].end(), ov_nodes.begin() + ov_off[q]);
+            h->ov_off = h->arena.alloc<int64_t>(nsub + 1);
+            h->ov_nodes = h->arena.alloc<int32_t>(h->sum_local);
+            h->Tq = h->arena.alloc<int32_t>(nsub);
+            h->tile_off = h->arena.alloc<int64_t>(nsub + 1);
+            h2d(h->ov_off, ov_off.data(), nsub + 1, h->stream);
+            h2d(h->ov_nodes, ov_nodes.data(), h->sum_local, h->stream);
+            h2d(h->Tq, Tq.data(), nsub, h->stream);
+            h2d(h->tile_off, tile_off.data(), nsub + 1, h->stream);
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
+        }
+        ov.clear();
+        ov.shrink_to_fit();
+
+        // ---- local-solve work items: chunks of consecutive packed tiles
+        {
+            const int chunk = o.chunk_tiles > 0 ? o.chunk_tiles : 96;
+            std::vector<int4> items;
+            std::vector<int32_t> nch(nsub), first(nsub);
+            h->h_citem_off.assign(h->ncol + 1, 0);
+            for (int c = 0; c < h->ncol; ++c) {
+                for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
+                    const int64_t P = (int64_t)Tq[q] * (Tq[q] + 1) / 2;
+                    const int nc = (int)std::max<int64_t>(1, (P + chunk - 1) / chunk);
+                    nch[q] = nc;
+                    first[q] = (int)items.size();
+                    for (int t = 0; t < nc; ++t)
+                        items.push_back(make_int4(q, (int)(P * t / nc), (int)(P * (t + 1) / nc), 0));
+                }
+                h->h_citem_off[c + 1] = (int)items.size();
+            }
+            h->nitems = (int)items.size();
+            h->items = h->arena.alloc<int4>(items.size());
+            h->nchunks = h->arena.alloc<int32_t>(nsub);
+            h->first_item = h->arena.alloc<int32_t>(nsub);
+            h->counters = h->arena.alloc<unsigned>(nsub);
+            h2d(h->items, items.data(), items.size(), h->stream);
+            h2d(h->nchunks, nch.data(), nsub, h->stream);
+            h2d(h->first_item, first.data(), nsub, h->stream);
+            DDG_CUDA(cudaMemsetAsync(h->counters, 0, nsub * sizeof(unsigned), h->stream));
+        }
+
+        // algorithmic bytes of one local-solve launch per colour and precision:
+        // packed triangle of A_i^{-1} + residual read + z read and write
+        for (int p = 0; p < 3; ++p) {
+            const double se = p == DDG_PREC_FP64 ? 8.0 : (p == DDG_PREC_FP32 ? 4.0 : 2.0);
+            const double sv = p == DDG_PREC_FP64 ? 8.0 : 4.0;
+            h->colour_bytes[p].assign(h->ncol, 0.0);
+            for (int c = 0; c < h->ncol; ++c)
+                for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
+                    const double nq = (double)(ov_off[q + 1] - ov_off[q]);
+                    h->colour_bytes[p][c] += nq * (nq + 1.0) / 2.0 * se + 3.0 * nq * sv;
+                }
+        }
+
+        // ---- local inverses (FP64 factorisation, packed copies)
+        h->errflags = h->arena.alloc<int32_t>(E_COUNT);
+        DDG_CUDA(cudaMemsetAsync(h->errflags, 0, E_COUNT * sizeof(int32_t), h->stream));
+        const size_t tile_elems = (size_t)h->total_tiles * 1024;
+        if (keep & (1 << DDG_PREC_FP64)) h->inv64 = h->arena.alloc<double>(tile_elems);
+        if (keep & (1 << DDG_PREC_FP32)) h->inv32 = h->arena.alloc<float>(tile_elems);
+        if (keep & (1 << DDG_PREC_BF16)) h->inv16 = h->arena.alloc<__nv_bfloat16>(tile_elems);
+        {
+            const size_t Np = (size_t)h->Tmax * DDG_LT;
+            const size_t per = Np * Np * sizeof(double);
+            const size_t budget = (size_t)6 << 30;
+            const int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nsub, budget / per));
+            double* ws = h->arena.alloc<double>((size_t)nb * Np * Np);
+            double* invdiag = h->arena.alloc<double>((size_t)nb * h->Tmax * DDG_LT * DDG_LT);
+            for (int q0 = 0; q0 < nsub; q0 += nb) {
+                const int q1 = std::min(nsub, q0 + nb);
+                ddg::local_extract_factor_invert(h, q0, q1, ws, invdiag);
+                ddg::local_pack(h, q0, q1, ws);
+            }
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
+            h->arena.release(ws);
+            h->arena.release(invdiag);
+        }
+        ddg::local_configure(h);
+        h->res64 = h->arena.alloc<double>(h->sum_local);
+        h->res32 = h->arena.alloc<float>(h->sum_local);
+        const size_t pslots = (size_t)h->nitems * h->Tmax * DDG_LT;
+        if (keep & (1 << DDG_PREC_FP64)) h->partial64 = h->arena.alloc<double>(pslots);
+        if (keep & ((1 << DDG_PREC_FP32) | (1 << DDG_PREC_BF16))) h->partial32 = h->arena.alloc<float>(pslots);
+
+        // ---- coarse space (Sec. 4)
+        if (h->use_coarse) {
+            h->kmax = k;
+            double* dF = h->arena.alloc<double>((size_t)n * k);
+            h2d(dF, F, (size_t)n * k, h->stream);
+            h->Q64 = h->arena.alloc<double>((size_t)n * k);
+            int32_t* d_rank = h->arena.alloc<int32_t>(nsub);
+            ddg::coarse_qr(h, d_rank, dF, k);
+            std::vector<int32_t> rank(nsub);
+            d2h(rank.data(), d_rank, nsub, h->stream);
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
+            h->arena.release(dF);
+            h->arena.release(d_rank);
+            h->h_coff.assign(nsub + 1, 0);
+            for (int s = 0; s < nsub; ++s) h->h_coff[s + 1] = h->h_coff[s] + rank[s];
+            h->n0 = h->h_coff[nsub];
+            if (h->n0 == 0) h->use_coarse = 0;
+        }
+        if (h->use_coarse) {
+            h->coff = h->arena.alloc<int32_t>(nsub + 1);
+            h2d(h->coff, h->h_coff.data(), nsub + 1, h->stream);
+            // adjacent subdomain pairs (I >= J) and the half-bandwidth of A0
+            std::vector<int> bI, bJ, mark(nsub, -1);
+            int64_t band = 0;
+            for (int I = 0; I < nsub; ++I) {
+                if (h->h_coff[I + 1] == h->h_coff[I]) continue;
+                std::vector<int> js;
+                for (int64_t a = sub_off[I]; a < sub_off[I + 1]; ++a) {
+                    const int g = sub_nodes[a];
+                    for (int64_t e = A->rowptr[g]; e < A->rowptr[g + 1]; ++e) {
+                        const int J = partition[A->col[e]];
+                        if (J <= I && mark[J] != I && h->h_coff[J + 1] > h->h_coff[J]) {
+                            mark[J] = I;
+                            js.push_back(J);
+                        }
+                    }
+                }
+                std::sort(js.begin(), js.end());
+                for (int J : js) {
+                    bI.push_back(I);
+                    bJ.push_back(J);
+                    band = std::max<int64_t>(band, (int64_t)h->h_coff[I + 1] - 1 - h->h_coff[J]);
+                }
+            }
+            h->band = (int)band;
+            h->Wt = std::max(1, (int)((band + DDG_CT - 1) / DDG_CT));
+            const int NT0 = (h->n0 + DDG_CT - 1) / DDG_CT;
+            h->nK = (NT0 + h->Wt - 1) / h->Wt;
+            h->NT = h->nK * h->Wt;
+            h->n0p = h->NT * DDG_CT;
+            h->B = h->Wt * DDG_CT;
+            h->bandL = h->arena.alloc<double>((size_t)h->NT * (h->Wt + 1) * DDG_CT * DDG_CT);
+            ddg::coarse_assemble_band(h, bI, bJ);
+            ddg::coarse_band_cholesky(h);
+            ddg::coarse_build_apply(h);
+            h->Q32 = h->arena.alloc<float>((size_t)n * k);
+            ddg::cast_q32(h);
+            const int n0p = h->n0p;
+            h->c64 = h->arena.alloc<double>(n0p);
+            h->y64 = h->arena.alloc<double>(n0p);
+            h->t64 = h->arena.alloc<double>(n0p);
+            h->x64 = h->arena.alloc<double>(n0p);
+            h->c32 = h->arena.alloc<float>(n0p);
+            h->y32 = h->arena.alloc<float>(n0p);
+            h->t32 = h->arena.alloc<float>(n0p);
+            h->x32 = h->arena.alloc<float>(n0p);
+            for (void* p : {(void*)h->c64, (void*)h->y64, (void*)h->t64, (void*)h->x64})
+                DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(double), h->stream));
+            for (void* p : {(void*)h->c32, (void*)h->y32, (void*)h->t32, (void*)h->x32})
+                DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(float), h->stream));
+        }
+
+        // ---- CG workspace
+        h->r = h->arena.alloc<double>(n);
+        h->p = h->arena.alloc<double>(n);
+        h->q = h->arena.alloc<double>(n);
+        h->zc = h->arena.alloc<double>(n);
+        h->z64 = h->arena.alloc<double>(n);
+        h->fbuf = h->arena.alloc<double>(n);
+        h->ubuf = h->arena.alloc<double>(n);
+        h->r32 = h->arena.alloc<float>(n);
+        h->z32 = h->arena.alloc<float>(n);
+        h->scal = h->arena.alloc<double>(S_COUNT);
+        DDG_CUDA(cudaMemsetAsync(h->scal, 0, S_COUNT * sizeof(double), h->stream));
+        DDG_CUDA(cudaMallocHost((void**)&h->h_scal, S_COUNT * sizeof(double)));
+        h->red_partials = h->arena.alloc<double>((size_t)DDG_RED_BLOCKS * 4);
+        h->red_counter = h->arena.alloc<unsigned>(1);
+        DDG_CUDA(cudaMemsetAsync(h->red_counter, 0, sizeof(unsigned), h->stream));
+
+        int32_t flags[E_COUNT];
+        d2h(flags, h->errflags, E_COUNT, h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        DDG_REQUIRE(!flags[E_LOCAL_SPD], DDG_ENOTSPD, "a local matrix A_i is not positive definite");
+        DDG_REQUIRE(!flags[E_COARSE_SPD], DDG_ENOTSPD, "the coarse matrix A0 is not positive definite");
+        h->setup_ms = now_ms() - t0;
+        *out = h;
+        return DDG_OK;
+    } catch (DdgError& e) {
+        g_setup_error = e.msg;
+        ddg_destroy(h);
+        return e.st;
+    } catch (std::exception& e) {
+        g_setup_error = e.what();
+        ddg_destroy(h);
+        return DDG_EINVAL;
+    }
+}
+
+ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters, double* relres) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(f && u, DDG_EINVAL, "f and u must be non-null device pointers");
+        DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
+        return pcg(h, f, u, tol, iters, relres);
+    });
+}
+
+ddg_status ddg_solve_host(ddg_handle h, const double* f_host, double* u_host, double tol, int* iters,
+                          double* relres) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(f_host && u_host, DDG_EINVAL, "f and u must be non-null host pointers");
+        DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
+        h2d(h->fbuf, f_host, h->n, h->stream);
+        const ddg_status st = pcg(h, h->fbuf, h->ubuf, tol, iters, relres);
+        d2h(u_host, h->ubuf, h->n, h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return st;
+    });
+}
+
+ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, double tol, int* iters,
+                           double* relres) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(F && U && m >= 1, DDG_EINVAL, "F, U must be non-null and m >= 1");
+        ddg_status worst = DDG_OK;
+        for (int j = 0; j < m; ++j) {
+            ddg::strided_gather(h, F, m, j, h->fbuf);
+            int it = 0;
+            double rr = 0.0;
+            const ddg_status st = pcg(h, h->fbuf, h->ubuf, tol, &it, &rr);
+            ddg::strided_scatter(h, h->ubuf, m, j, U);
+            if (iters) iters[j] = it;
+            if (relres) relres[j] = rr;
+            if (st != DDG_OK && worst == DDG_OK) worst = st;
+        }
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return worst;
+    });
+}
+
+ddg_status ddg_adjoint(ddg_handle h, const double* dLdu, double* lambda, double tol, int* iters,
+                       double* relres) {
+    return ddg_solve(h, dLdu, lambda, tol, iters, relres);
+}
+
+ddg_status ddg_grad_coeff(ddg_handle h, const double* lambda, const double* u, double* dkappa) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(h->stencil_kind == DDG_STENCIL_VAR7_3D && h->kappa, DDG_EINVAL,
+                    "ddg_grad_coeff needs a VAR7 handle set up with the cell coefficients");
+        DDG_REQUIRE(lambda && u && dkappa, DDG_EINVAL, "null pointer");
+        ddg::grad_coeff_var7(h, lambda, u, dkappa);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_apply_preconditioner(ddg_handle h, const double* r, double* z) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(r && z, DDG_EINVAL, "null pointer");
+        apply_prec(h, r);
+        if (h->precision == DDG_PREC_FP64)
+            DDG_CUDA(cudaMemcpyAsync(z, h->z64, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        else
+            ddg::convert_to_double(h, h->z32, z);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_coarse_correction(ddg_handle h, const double* r, double* z) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(r && z, DDG_EINVAL, "null pointer");
+        DDG_REQUIRE(h->use_coarse, DDG_EINVAL, "the handle has no coarse space");
+        const int prec = h->precision;
+        if (prec == DDG_PREC_FP64) {
+            h->rin64 = r;
+            DDG_CUDA(cudaMemsetAsync(h->z64, 0, h->n * sizeof(double), h->stream));
+        } else {
+            ddg::convert_to_float(h, r, h->r32);
+            DDG_CUDA(cudaMemsetAsync(h->z32, 0, h->n * sizeof(float), h->stream));
+        }
+        coarse_step(h, prec, false);
+        if (prec == DDG_PREC_FP64)
+            DDG_CUDA(cudaMemcpyAsync(z, h->z64, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        else
+            ddg::convert_to_double(h, h->z32, z);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_spmv(ddg_handle h, const double* x, double* y) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(x && y, DDG_EINVAL, "null pointer");
+        ddg::spmv64(h, x, y, false, 0);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_set_precision(ddg_handle h, int precision) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(precision >= DDG_PREC_FP64 && precision <= DDG_PREC_BF16, DDG_EINVAL, "bad precision");
+        DDG_REQUIRE(h->opt.keep_precisions & (1 << precision), DDG_EINVAL,
+                    "that precision was not kept at setup (keep_precisions)");
+        h->precision = precision;
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_set_stream(ddg_handle h, void* stream) {
+    return guarded(h, [&]() {
+        h->stream = (cudaStream_t)stream;
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_get_info(ddg_handle h, ddg_info* info) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(info, DDG_EINVAL, "null pointer");
+        info->n = h->n;
+        info->nsub = h->nsub;
+        info->ncolours = h->ncol;
+        info->n0 = h->use_coarse ? h->n0 : 0;
+        info->kmax = h->kmax;
+        info->max_local = h->max_local;
+        info->sum_local = h->sum_local;
+        info->local_tiles = h->total_tiles;
+        info->coarse_band = h->band;
+        info->coarse_blocks = h->nK;
+        info->setup_ms = h->setup_ms;
+        info->precision = h->precision;
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_get_colouring(ddg_handle h, int32_t* colour) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(colour, DDG_EINVAL, "null pointer");
+        for (int s = 0; s < h->nsub; ++s) colour[s] = h->h_colour[s];
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_get_coarse_offsets(ddg_handle h, int32_t* offsets) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(offsets, DDG_EINVAL, "null pointer");
+        for (int s = 0; s <= h->nsub; ++s) offsets[s] = h->use_coarse ? h->h_coff[s] : 0;
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_get_history(ddg_handle h, double* hist, int max_len, int* len) {
+    return guarded(h, [&]() {
+        const int cnt = (int)h->history.size();
+        if (len) *len = cnt;
+        if (hist)
+            for (int i = 0; i < std::min(cnt, max_len); ++i) hist[i] = h->history[i];
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_profile(ddg_handle h, int timed_mask) {
+    return guarded(h, [&]() {
+        prof_flush(h);
+        h->prof_mask = timed_mask;
+        for (int c = 0; c < DDG_K_COUNT; ++c) {
+            h->prof_launches[c] = h->prof_timed[c] = 0;
+            h->prof_ms[c] = h->prof_bytes[c] = 0.0;
+        }
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_get_kernel_stats(ddg_handle h, ddg_kernel_stat* st) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(st, DDG_EINVAL, "null pointer");
+        prof_flush(h);
+        for (int c = 0; c < DDG_K_COUNT; ++c) {
+            st[c].launches = h->prof_launches[c];
+            st[c].timed = h->prof_timed[c];
+            st[c].ms = h->prof_ms[c];
+            st[c].bytes = h->prof_bytes[c];
+        }
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_destroy(ddg_handle h) {
+    if (!h) return DDG_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->arena.free_all();
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+    delete h;
+    return DDG_OK;
+}
+
+const char* ddg_last_error(ddg_handle h) {
+    if (!h) return g_setup_error.c_str();
+    return h->err.c_str();
+}
+
+const char* ddg_status_string(ddg_status s) {
+    switch (s) {
+        case DDG_OK: return "DDG_OK";
+        case DDG_EINVAL: return "DDG_EINVAL";
+        case DDG_ENOMEM: return "DDG_ENOMEM";
+        case DDG_ENOTSPD: return "DDG_ENOTSPD";
+        case DDG_EBREAKDOWN: return "DDG_EBREAKDOWN";
+        case DDG_ENOCONV: return "DDG_ENOCONV";
+        case DDG_ETIMEOUT: return "DDG_ETIMEOUT";
+        case DDG_ECUDA: return "DDG_ECUDA";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,262 @@
+// Internal declarations of the DDG solver library (not part of the C ABI).
+//
+// Data layout in HBM (all device arrays are owned by the handle):
+//   * fine matrix A: CSR (int64 rowptr, int32 col, FP64 and FP32 values);
+//   * non-overlapping subdomains (Sec. 4) in id order: sub_off[nsub+1],
+//     sub_nodes[n] (ascending per subdomain), pos[g] = index of g in
+//     sub_nodes; the coarse basis Q is stored per such position, kmax values
+//     per node (row-major), FP64 and FP32;
+//   * overlapping subdomains (Sec. 6) in *sweep order* q (colour-major, ids
+//     ascending inside a colour): ov_off[nsub+1], ov_nodes (sorted per
+//     subdomain); colour c owns sweep positions csub_off[c]..csub_off[c+1]
+//     and local rows crow_off[c]..crow_off[c+1];
+//   * local inverses A_i^{-1}: zero-padded to T_q = ceil(n_q/32) tiles per
+//     side, upper-triangular 32x32 tiles (I <= J) in row-major tile order,
+//     each tile row-major; the diagonal tiles hold the full symmetric tile;
+//   * coarse factor: A0 = L L^T in 64x64 tiles inside the band, regrouped
+//     into super-blocks of Wt tiles: y_K = D_K (c_K - E_K y_{K-1}) forward
+//     and x_K = D_K^T (y_K - E_{K+1}^T x_{K+1}) backward, with D_K = L_KK^{-1};
+//     D, E, D^T, E^T are stored as "profile rows" (contiguous column range
+//     per row) in FP64 and FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ddg.h"
+
+#define DDG_LT 32        // local-inverse tile edge
+#define DDG_CT 64        // coarse factor tile edge
+#define DDG_KMAX 32      // largest supported number of generators
+#define DDG_RED_BLOCKS 1216  // blocks of the deterministic reductions (8 x 152 SMs)
+
+// ---------------------------------------------------------------- errors
+struct DdgError {
+    ddg_status st;
+    std::string msg;
+};
+
+#define DDG_CUDA(call)                                                              \
+    do {                                                                            \
+        cudaError_t _e = (call);                                                    \
+        if (_e != cudaSuccess)                                                      \
+            throw DdgError{_e == cudaErrorMemoryAllocation ? DDG_ENOMEM : DDG_ECUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(_e)};      \
+    } while (0)
+
+#define DDG_CHECK_LAUNCH() DDG_CUDA(cudaGetLastError())
+
+#define DDG_REQUIRE(cond, status, text)                \
+    do {                                               \
+        if (!(cond)) throw DdgError{status, (text)};   \
+    } while (0)
+
+// device allocation helper: every allocation is recorded for ddg_destroy
+struct DevArena {
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    template <typename T>
+    T* alloc(size_t count) {
+        if (count == 0) count = 1;
+        void* p = nullptr;
+        DDG_CUDA(cudaMalloc(&p, count * sizeof(T)));
+        ptrs.push_back(p);
+        bytes += count * sizeof(T);
+        return static_cast<T*>(p);
+    }
+    void release(void* p) {
+        for (auto& q : ptrs)
+            if (q == p) {
+                cudaFree(q);
+                q = nullptr;
+            }
+    }
+    void free_all() {
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+template <typename T>
+static inline void h2d(T* dst, const T* src, size_t count, cudaStream_t s) {
+    if (count) DDG_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+template <typename T>
+static inline void d2h(T* dst, const T* src, size_t count, cudaStream_t s) {
+    if (count) DDG_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+}
+
+// device scalar slots of the CG recurrence (FP64)
+enum {
+    S_RZ = 0,      // rho_k = r_k^T z_k
+    S_PQ = 1,      // p^T A p
+    S_RR = 2,      // ||r||^2
+    S_ALPHA = 3,
+    S_BETA = 4,
+    S_QZ = 5,      // q_k^T z_{k+1} (Polak-Ribiere)
+    S_RZNEW = 6,
+    S_TMP = 7,
+    S_FLAG = 8,    // breakdown flag (1.0 when p^T A p <= 0 or NaN)
+    S_COUNT = 16
+};
+
+// error flags written by kernels (int32)
+enum { E_LOCAL_SPD = 0, E_COARSE_SPD = 1, E_COUNT = 4 };
+
+// ---------------------------------------------------------------- handle
+struct ProfileMat {         // rows with one contiguous column range each
+    int64_t* rowptr = nullptr;  // [rows + 1]
+    int32_t* lo = nullptr;      // [rows], global column of the first entry
+    int32_t* hi = nullptr;      // [rows], one past the last column
+    double* v64 = nullptr;
+    float* v32 = nullptr;
+    int64_t nnz = 0;
+};
+
+struct ddg_handle_s {
+    DevArena arena;
+    cudaStream_t stream = nullptr;
+    ddg_options opt{};
+    std::string err;
+    int precision = DDG_PREC_FP64;
+    double setup_ms = 0.0;
+
+    // ---- fine problem
+    int64_t n = 0, nnz = 0;
+    int stencil_kind = 0, dim = 0, nx = 1, ny = 1, nz = 1, dpn = 1;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val64 = nullptr;
+    float* val32 = nullptr;
+    double* kappa = nullptr;    // VAR7 cell coefficients (device), for dL/dkappa
+
+    // ---- partition (Sec. 4) in id order
+    int nsub = 0;
+    int32_t* part = nullptr;       // [n]
+    int64_t* sub_off = nullptr;    // [nsub + 1]
+    int32_t* sub_nodes = nullptr;  // [n]
+    int32_t* pos = nullptr;        // [n]
+    std::vector<int64_t> h_sub_off;
+
+    // ---- overlapping subdomains in sweep order (Sec. 6)
+    int ncol = 0;
+    std::vector<int> h_colour;     // [nsub] colour of each id
+    std::vector<int> h_sid;        // [nsub] sweep position -> id
+    std::vector<int> h_csub_off;   // [ncol + 1]
+    std::vector<int64_t> h_crow_off;
+    std::vector<int64_t> h_ov_off;
+    int64_t sum_local = 0;
+    int max_local = 0, Tmax = 0;
+    int64_t* ov_off = nullptr;
+    int32_t* ov_nodes = nullptr;
+    int32_t* Tq = nullptr;
+    int64_t* tile_off = nullptr;
+    int64_t total_tiles = 0;
+    // local-solve work items per colour: {q, tile_begin, tile_end, unused}
+    std::vector<int> h_citem_off;
+    int nitems = 0;
+    int4* items = nullptr;
+    int32_t* nchunks = nullptr;
+    int32_t* first_item = nullptr;
+    unsigned* counters = nullptr;
+    double* inv64 = nullptr;
+    float* inv32 = nullptr;
+    __nv_bfloat16* inv16 = nullptr;
+    // partial results of the local GEMV: [nitems][Tmax * 32]
+    double* partial64 = nullptr;
+    float* partial32 = nullptr;
+    double* res64 = nullptr;       // [sum_local]
+    float* res32 = nullptr;
+
+    // ---- coarse space (Sec. 4)
+    int use_coarse = 1;
+    int kmax = 0, n0 = 0;
+    std::vector<int> h_coff;
+    int32_t* coff = nullptr;       // [nsub + 1]
+    double* Q64 = nullptr;         // [n * kmax] by position
+    float* Q32 = nullptr;
+    int band = 0, Wt = 1, NT = 0, nK = 0, B = 0, n0p = 0;
+    double* bandL = nullptr;       // [NT][Wt+1][64*64] (setup only)
+    double* coarseW = nullptr;     // super-block inverses (setup only)
+    ProfileMat Dm, Em, Dt, Et;
+    double *c64 = nullptr, *y64 = nullptr, *t64 = nullptr, *x64 = nullptr;
+    float *c32 = nullptr, *y32 = nullptr, *t32 = nullptr, *x32 = nullptr;
+
+    // ---- CG workspace (FP64) and preconditioner vectors
+    const double* rin64 = nullptr;  // input of the FP64 preconditioner apply
+    double *r = nullptr, *zc = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
+    double *fbuf = nullptr, *ubuf = nullptr;   // staging for host solves
+    float *r32 = nullptr, *z32 = nullptr;      // preconditioner-precision copies
+    double* z64 = nullptr;
+    double* scal = nullptr;        // [S_COUNT]
+    double* h_scal = nullptr;      // pinned
+    double* red_partials = nullptr;   // [DDG_RED_BLOCKS * 4]
+    unsigned* red_counter = nullptr;
+    int32_t* errflags = nullptr;
+    std::vector<double> history;
+
+    // ---- tracing (ddg_profile)
+    int prof_mask = 0;
+    int64_t prof_launches[DDG_K_COUNT] = {0};
+    int64_t prof_timed[DDG_K_COUNT] = {0};
+    double prof_ms[DDG_K_COUNT] = {0};
+    double prof_bytes[DDG_K_COUNT] = {0};
+    std::vector<cudaEvent_t> ev_pool;          // created lazily, reused
+    std::vector<int> ev_class;                 // class of each recorded pair
+    std::vector<double> ev_bytes;
+    size_t ev_used = 0;                        // pairs recorded since the last flush
+    std::vector<double> colour_bytes[3];       // per precision: local-solve bytes per colour
+};
+
+// Scope of one or more kernel launches of class `cls`: counts the launches
+// and, when that class is timed, brackets them with a CUDA event pair.
+struct ProfScope {
+    ddg_handle h;
+    int cls, pair;
+    ProfScope(ddg_handle hh, int c, int nlaunch, double bytes);
+    ~ProfScope();
+};
+
+// ---------------------------------------------------------------- kernels
+// (declared here, defined in the k_*.cu files; every launcher enqueues on
+// the handle's stream and throws DdgError on a launch failure)
+namespace ddg {
+
+// k_local.cu
+void local_extract_factor_invert(ddg_handle h, int q0, int q1, double* ws, double* invdiag);
+void local_pack(ddg_handle h, int q0, int q1, const double* ws);
+void local_configure(ddg_handle h);
+void local_residual(ddg_handle h, int colour, bool z_zero, int prec);
+void local_solve_colour(ddg_handle h, int colour, int prec);
+
+// k_coarse.cu
+void coarse_qr(ddg_handle h, int32_t* d_rank, const double* dF, int k);
+void coarse_assemble_band(ddg_handle h, const std::vector<int>& blk_I, const std::vector<int>& blk_J);
+void coarse_band_cholesky(ddg_handle h);
+void coarse_build_apply(ddg_handle h);
+void coarse_restrict(ddg_handle h, int prec, bool residual);
+void coarse_solve(ddg_handle h, int prec);
+void coarse_prolong(ddg_handle h, int prec);
+
+// k_cg.cu
+void spmv64(ddg_handle h, const double* x, double* y, bool dot_with_x, int slot);
+void spmv_prec(ddg_handle h, const float* x, float* y);
+void dot64(ddg_handle h, const double* a, const double* b, int slot);
+void cg_update_ur(ddg_handle h);
+void cg_dots_after_precond(ddg_handle h, int prec, bool first, int pr);
+void cg_update_p(ddg_handle h, int prec, bool first);
+void convert_to_float(ddg_handle h, const double* src, float* dst);
+void convert_to_double(ddg_handle h, const float* src, double* dst);
+void residual64(ddg_handle h, const double* f, const double* u, double* r);
+void grad_coeff_var7(ddg_handle h, const double* lambda, const double* u, double* dk);
+void set_scalar(ddg_handle h, int slot, double v);
+void strided_gather(ddg_handle h, const double* src, int m, int j, double* dst);
+void strided_scatter(ddg_handle h, const double* src, int m, int j, double* dst);
+void cast_q32(ddg_handle h);
+
+}  // namespace ddg

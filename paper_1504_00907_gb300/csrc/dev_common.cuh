@@ -1,0 +1,63 @@
+// Small device helpers shared by the kernels of this library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace ddgdev {
+
+// After the call, the lane with index q = (lane / S) % N holds the sum over
+// the N lanes of v[q]: a reduce-scatter by recursive halving, N - 1 shuffles.
+template <int N, int S, typename V>
+__device__ __forceinline__ V reduce_scatter(V (&v)[N], int q) {
+#pragma unroll
+    for (int half = N / 2; half >= 1; half >>= 1) {
+        const bool up = (q & half) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            V send = up ? v[i] : v[i + half];
+            V keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half * S);
+        }
+    }
+    return v[0];
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of one value per thread over the block, in a fixed order; the result
+// is returned to every thread.  `sh` must hold blockDim.x / 32 values.
+template <typename V>
+__device__ __forceinline__ V block_sum(V v, V* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    V s = 0;
+    for (int i = 0; i < nw; ++i) s += sh[i];
+    return s;
+}
+
+// Sum of 32 values per thread over the block; out[i] = total of v[i].
+// `sh` holds 32 * (blockDim.x / 32) values.
+template <typename V>
+__device__ __forceinline__ void block_sum32(V (&v)[32], V* sh, V* out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const V t = reduce_scatter<32, 1>(v, lane);
+    __syncthreads();
+    sh[w * 32 + lane] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        V s = 0;
+        for (int i = 0; i < nw; ++i) s += sh[i * 32 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+}  // namespace ddgdev

@@ -1,0 +1,363 @@
+// Preconditioned CG recurrence (Sec. 7) in FP64: SpMV with the fused p^T A p,
+// the u/r update with ||r||^2, the r^T z (and q^T z) dots that yield beta,
+// and the p update.  Every reduction is deterministic: each block writes a
+// partial, and the last block to finish (ticket counter) sums the partials
+// in block order and derives the CG scalars on the device.
+#include "ddg_internal.cuh"
+#include "dev_common.cuh"
+
+namespace {
+
+constexpr int RT = 256;   // threads of the reduction kernels
+
+// last-block epilogue: every block passes NV partial sums; the last block
+// leaves the totals in tot[] and returns true
+template <int NV>
+__device__ bool reduce_last(double (&v)[NV], double* partials, unsigned* counter, double* tot) {
+    __shared__ double sh[RT / 32];
+    __shared__ bool last;
+    double bs[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) bs[i] = ddgdev::block_sum(v[i], sh);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NV; ++i) partials[(size_t)blockIdx.x * NV + i] = bs[i];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double s = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            s += __ldcg(partials + (size_t)b * NV + i);
+        tot[i] = ddgdev::block_sum(s, sh);
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// y = A x over CSR rows; optionally dot = x^T y into scal[S_PQ] and
+// alpha = rho / p^T A p into scal[S_ALPHA] (breakdown flag if p^T A p <= 0)
+template <bool DOT>
+__global__ void __launch_bounds__(RT) spmv_csr64_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const double* __restrict__ x,
+                                                        double* __restrict__ y, double* partials,
+                                                        unsigned* counter, double* scal) {
+    double acc[1] = {0.0};
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma(val[e], x[col[e]], s);
+        y[g] = s;
+        if (DOT) acc[0] = fma(x[g], s, acc[0]);
+    }
+    if (!DOT) return;
+    double tot[1];
+    if (reduce_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        scal[S_PQ] = pq;
+        scal[S_ALPHA] = scal[S_RZ] / pq;
+        if (!(pq > 0.0) || pq != pq) scal[S_FLAG] = 1.0;
+    }
+}
+
+// matrix-free constant-coefficient Laplacians: [6,-1] (3D) / [4,-1] (2D)
+template <bool DOT, int DIM>
+__global__ void __launch_bounds__(RT) spmv_lap64_kernel(int nx, int ny, int nz,
+                                                        const double* __restrict__ x,
+                                                        double* __restrict__ y, double* partials,
+                                                        unsigned* counter, double* scal) {
+    const int64_t n = (int64_t)nx * ny * nz, sxy = (int64_t)nx * ny;
+    double acc[1] = {0.0};
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / sxy);
+        const double xc = x[g];
+        double s = (DIM == 3 ? 6.0 : 4.0) * xc;
+        if (i > 0) s -= x[g - 1];
+        if (i < nx - 1) s -= x[g + 1];
+        if (j > 0) s -= x[g - nx];
+        if (j < ny - 1) s -= x[g + nx];
+        if (DIM == 3) {
+            if (k > 0) s -= x[g - sxy];
+            if (k < nz - 1) s -= x[g + sxy];
+        }
+        y[g] = s;
+        if (DOT) acc[0] = fma(xc, s, acc[0]);
+    }
+    if (!DOT) return;
+    double tot[1];
+    if (reduce_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        scal[S_PQ] = pq;
+        scal[S_ALPHA] = scal[S_RZ] / pq;
+        if (!(pq > 0.0) || pq != pq) scal[S_FLAG] = 1.0;
+    }
+}
+
+// y = A x in the preconditioner precision (CSR)
+template <typename V, typename AV>
+__global__ void spmv_csr_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                const int32_t* __restrict__ col, const AV* __restrict__ val,
+                                const V* __restrict__ x, V* __restrict__ y) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    V s = 0;
+    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma((V)val[e], x[col[e]], s);
+    y[g] = s;
+}
+
+// u += alpha p; r -= alpha q; ||r||^2 -> scal[S_RR]
+__global__ void __launch_bounds__(RT) cg_update_ur_kernel(int64_t n, double* __restrict__ u,
+                                                          double* __restrict__ r,
+                                                          const double* __restrict__ p,
+                                                          const double* __restrict__ q,
+                                                          double* partials, unsigned* counter,
+                                                          double* scal) {
+    const double alpha = scal[S_ALPHA];
+    double acc[1] = {0.0};
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        u[g] = fma(alpha, p[g], u[g]);
+        const double rg = fma(-alpha, q[g], r[g]);
+        r[g] = rg;
+        acc[0] = fma(rg, rg, acc[0]);
+    }
+    double tot[1];
+    if (reduce_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        scal[S_RR] = tot[0];
+        if (tot[0] != tot[0]) scal[S_FLAG] = 1.0;
+    }
+}
+
+// rho' = r^T z, qz = q^T z; beta = rho'/rho (FR) or -alpha qz / rho (PR); rho <- rho'
+template <typename ZV>
+__global__ void __launch_bounds__(RT) cg_dots_kernel(int64_t n, const double* __restrict__ r,
+                                                     const double* __restrict__ q,
+                                                     const ZV* __restrict__ z, int first, int pr,
+                                                     double* partials, unsigned* counter,
+                                                     double* scal) {
+    double acc[2] = {0.0, 0.0};
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const double zg = (double)z[g];
+        acc[0] = fma(r[g], zg, acc[0]);
+        if (!first && pr) acc[1] = fma(q[g], zg, acc[1]);
+    }
+    double tot[2];
+    if (reduce_last<2>(acc, partials, counter, tot) && threadIdx.x == 0) {
+        const double rz = tot[0];
+        if (!first) {
+            const double beta = pr ? (-scal[S_ALPHA] * tot[1] / scal[S_RZ]) : (rz / scal[S_RZ]);
+            scal[S_BETA] = beta;
+        } else {
+            scal[S_BETA] = 0.0;
+        }
+        scal[S_QZ] = tot[1];
+        scal[S_RZ] = rz;
+        if (rz != rz) scal[S_FLAG] = 1.0;
+    }
+}
+
+template <typename ZV>
+__global__ void cg_update_p_kernel(int64_t n, double* __restrict__ p, const ZV* __restrict__ z,
+                                   const double* __restrict__ scal, int first) {
+    const double beta = first ? 0.0 : scal[S_BETA];
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x)
+        p[g] = first ? (double)z[g] : fma(beta, p[g], (double)z[g]);
+}
+
+__global__ void __launch_bounds__(RT) dot64_kernel(int64_t n, const double* __restrict__ a,
+                                                   const double* __restrict__ b, double* partials,
+                                                   unsigned* counter, double* scal, int slot) {
+    double acc[1] = {0.0};
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+         g += (int64_t)gridDim.x * blockDim.x)
+        acc[0] = fma(a[g], b[g], acc[0]);
+    double tot[1];
+    if (reduce_last<1>(acc, partials, counter, tot) && threadIdx.x == 0) scal[slot] = tot[0];
+}
+
+// r = f - A u (CSR)
+__global__ void residual64_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                  const double* __restrict__ f, const double* __restrict__ u,
+                                  double* __restrict__ r) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    double s = f[g];
+    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma(-val[e], u[col[e]], s);
+    r[g] = s;
+}
+
+__global__ void to_float_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) b[g] = (float)a[g];
+}
+__global__ void to_double_kernel(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) b[g] = (double)a[g];
+}
+
+__global__ void strided_gather_kernel(int64_t n, const double* __restrict__ src, int m, int j,
+                                      double* __restrict__ dst) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) dst[g] = src[g * m + j];
+}
+__global__ void strided_scatter_kernel(int64_t n, const double* __restrict__ src, int m, int j,
+                                       double* __restrict__ dst) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) dst[g * m + j] = src[g];
+}
+__global__ void cast_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) b[g] = (float)a[g];
+}
+
+__global__ void set_scalar_kernel(double* scal, int slot, double v) { scal[slot] = v; }
+
+// dL/dkappa for the cell-centred variable-coefficient operator:
+// A = sum_faces c_f (e_a - e_b)(e_a - e_b)^T (interior) + c_f e_a e_a^T (boundary),
+// so dL/dc_f = -lambda^T (dA/dc_f) u = -(l_a - l_b)(u_a - u_b) (interior) or
+// -l_a u_a (boundary); the chain rule through c_f = 2 ka kb / (ka + kb)
+// (interior) or c_f = 2 ka (boundary) gives each cell's gradient.
+__global__ void grad_var7_kernel(int nx, int ny, int nz, const double* __restrict__ kap, const double* __restrict__ lam,
+                                 const double* __restrict__ u, double* __restrict__ dk) {
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int i = (int)(g % nx), j = (int)((g / nx) % ny), k = (int)(g / ((int64_t)nx * ny));
+    const double ka = kap[g];
+    double s = 0.0;
+    const int64_t st[3] = {1, nx, (int64_t)nx * ny};
+    const int cc[3] = {i, j, k}, nn[3] = {nx, ny, nz};
+    for (int ax = 0; ax < 3; ++ax) {
+        for (int side = -1; side <= 1; side += 2) {
+            const int c2 = cc[ax] + side;
+            if (c2 < 0 || c2 >= nn[ax]) {
+                // boundary face: c = 2 ka, dc/dka = 2
+                s += -lam[g] * u[g] * 2.0;
+            } else {
+                const int64_t gb = g + side * st[ax];
+                const double kb = kap[gb];
+                const double dcdka = 2.0 * kb * kb / ((ka + kb) * (ka + kb));
+                s += -(lam[g] - lam[gb]) * (u[g] - u[gb]) * dcdka;
+            }
+        }
+    }
+    dk[g] = s;
+}
+
+inline unsigned red_grid(int64_t n) {
+    int64_t b = (n + RT - 1) / RT;
+    if (b > DDG_RED_BLOCKS) b = DDG_RED_BLOCKS;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+namespace ddg {
+
+void spmv64(ddg_handle h, const double* x, double* y, bool dot, int /*slot*/) {
+    const unsigned G = red_grid(h->n);
+    const int sk = h->stencil_kind;
+    if (sk == DDG_STENCIL_7PT_3D) {
+        if (dot) spmv_lap64_kernel<true, 3><<<G, RT, 0, h->stream>>>(h->nx, h->ny, h->nz, x, y, h->red_partials, h->red_counter, h->scal);
+        else spmv_lap64_kernel<false, 3><<<G, RT, 0, h->stream>>>(h->nx, h->ny, h->nz, x, y, h->red_partials, h->red_counter, h->scal);
+    } else if (sk == DDG_STENCIL_5PT_2D) {
+        if (dot) spmv_lap64_kernel<true, 2><<<G, RT, 0, h->stream>>>(h->nx, h->ny, 1, x, y, h->red_partials, h->red_counter, h->scal);
+        else spmv_lap64_kernel<false, 2><<<G, RT, 0, h->stream>>>(h->nx, h->ny, 1, x, y, h->red_partials, h->red_counter, h->scal);
+    } else {
+        if (dot) spmv_csr64_kernel<true><<<G, RT, 0, h->stream>>>(h->n, h->rowptr, h->col, h->val64, x, y, h->red_partials, h->red_counter, h->scal);
+        else spmv_csr64_kernel<false><<<G, RT, 0, h->stream>>>(h->n, h->rowptr, h->col, h->val64, x, y, h->red_partials, h->red_counter, h->scal);
+    }
+    DDG_CHECK_LAUNCH();
+}
+
+void dot64(ddg_handle h, const double* a, const double* b, int slot) {
+    dot64_kernel<<<red_grid(h->n), RT, 0, h->stream>>>(h->n, a, b, h->red_partials, h->red_counter,
+                                                       h->scal, slot);
+    DDG_CHECK_LAUNCH();
+}
+
+void cg_update_ur(ddg_handle h) {
+    cg_update_ur_kernel<<<red_grid(h->n), RT, 0, h->stream>>>(h->n, h->u, h->r, h->p, h->q,
+                                                              h->red_partials, h->red_counter, h->scal);
+    DDG_CHECK_LAUNCH();
+}
+
+void cg_dots_after_precond(ddg_handle h, int prec, bool first, int pr) {
+    if (prec == DDG_PREC_FP64)
+        cg_dots_kernel<double><<<red_grid(h->n), RT, 0, h->stream>>>(h->n, h->r, h->q, h->z64, first, pr,
+                                                                     h->red_partials, h->red_counter, h->scal);
+    else
+        cg_dots_kernel<float><<<red_grid(h->n), RT, 0, h->stream>>>(h->n, h->r, h->q, h->z32, first, pr,
+                                                                    h->red_partials, h->red_counter, h->scal);
+    DDG_CHECK_LAUNCH();
+}
+
+void cg_update_p(ddg_handle h, int prec, bool first) {
+    const unsigned G = red_grid(h->n);
+    if (prec == DDG_PREC_FP64)
+        cg_update_p_kernel<double><<<G, RT, 0, h->stream>>>(h->n, h->p, h->z64, h->scal, first);
+    else
+        cg_update_p_kernel<float><<<G, RT, 0, h->stream>>>(h->n, h->p, h->z32, h->scal, first);
+    DDG_CHECK_LAUNCH();
+}
+
+void residual64(ddg_handle h, const double* f, const double* u, double* r) {
+    residual64_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, h->rowptr, h->col,
+                                                                             h->val64, f, u, r);
+    DDG_CHECK_LAUNCH();
+}
+
+void convert_to_float(ddg_handle h, const double* src, float* dst) {
+    to_float_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, src, dst);
+    DDG_CHECK_LAUNCH();
+}
+
+void convert_to_double(ddg_handle h, const float* src, double* dst) {
+    to_double_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, src, dst);
+    DDG_CHECK_LAUNCH();
+}
+
+void spmv_prec(ddg_handle h, const float* x, float* y) {
+    spmv_csr_kernel<float, float><<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(
+        h->n, h->rowptr, h->col, h->val32, x, y);
+    DDG_CHECK_LAUNCH();
+}
+
+void set_scalar(ddg_handle h, int slot, double v) {
+    set_scalar_kernel<<<1, 1, 0, h->stream>>>(h->scal, slot, v);
+    DDG_CHECK_LAUNCH();
+}
+
+void strided_gather(ddg_handle h, const double* src, int m, int j, double* dst) {
+    strided_gather_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, src, m, j, dst);
+    DDG_CHECK_LAUNCH();
+}
+
+void strided_scatter(ddg_handle h, const double* src, int m, int j, double* dst) {
+    strided_scatter_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, src, m, j, dst);
+    DDG_CHECK_LAUNCH();
+}
+
+void cast_q32(ddg_handle h) {
+    const int64_t cnt = h->n * (int64_t)h->kmax;
+    cast_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(cnt, h->Q64, h->Q32);
+    DDG_CHECK_LAUNCH();
+}
+
+void grad_coeff_var7(ddg_handle h, const double* lambda, const double* u, double* dk) {
+    grad_var7_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(
+        h->nx, h->ny, h->nz, h->kappa, lambda, u, dk);
+    DDG_CHECK_LAUNCH();
+}
+
+}  // namespace ddg

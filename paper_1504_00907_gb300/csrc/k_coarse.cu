@@ -1,0 +1,646 @@
+// The DDG coarse space (Sec. 4) and its exact solve.
+//
+// Setup
+//   coarse_qr           R0: per subdomain, column-pivoted Gram-Schmidt (with one
+//                       re-orthogonalisation pass) of F restricted to Omega_i,
+//                       keeping column j while |R_jj| > rank_tol |R_00| (Sec. 4:
+//                       orthogonalise per subdomain, discard rank-deficient
+//                       columns).  Q is stored per node, kmax values.
+//   coarse_assemble     A0 = R0 A R0^T block by block (blocks (I, J), I >= J, of
+//                       adjacent subdomains) straight into a 64x64-tiled band.
+//   band Cholesky       A0 = L L^T (FP64) in the tiled band, right-looking.
+//   super-blocks        regroup L into super-blocks of Wt tiles so that L is
+//                       block bidiagonal; D_K = L_KK^{-1} (tile forward
+//                       substitution), E_K = L_{K,K-1}.
+// Apply (FP64 or FP32)
+//   c = R0 (r - A z)    coarse_restrict (residual fused)
+//   y = A0^{-1} c       2 nK dependent profile-row GEMVs forward, 2 nK backward
+//   z += R0^T y         coarse_prolong
+#include <algorithm>
+
+#include "ddg_internal.cuh"
+#include "dev_common.cuh"
+
+namespace {
+
+constexpr int CT = DDG_CT;
+constexpr int CLD = CT + 1;
+
+// ---------------------------------------------------------------- R0 (QR)
+__global__ void __launch_bounds__(256) coarse_qr_kernel(
+    const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
+    const double* __restrict__ F, int64_t n, int k, int kmax, double rank_tol, double* Q,
+    int32_t* rank_out) {
+    __shared__ double red[32 * 8];
+    __shared__ double vals[32];
+    __shared__ int piv;
+    __shared__ double r00;
+    const int s = blockIdx.x;
+    const int64_t a0 = sub_off[s], a1 = sub_off[s + 1];
+    const int m = (int)(a1 - a0);
+    for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+        const int g = sub_nodes[a];
+        for (int j = 0; j < kmax; ++j) Q[a * kmax + j] = j < k ? F[g + (int64_t)j * n] : 0.0;
+    }
+    __syncthreads();
+    auto colref = [&](int64_t a, int j) -> double& { return Q[a * kmax + j]; };
+    int rank = 0;
+    const int kk = min(k, m);
+    for (int j = 0; j < kk; ++j) {
+        // squared norms of the remaining columns j..k-1
+        double v[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = 0.0;
+        for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x)
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                if (c >= j && c < k) {
+                    const double t = colref(a, c);
+                    v[c] = fma(t, t, v[c]);
+                }
+        ddgdev::block_sum32(v, red, vals);
+        if (threadIdx.x == 0) {
+            int p = j;
+            for (int c = j + 1; c < k; ++c)
+                if (vals[c] > vals[p]) p = c;
+            piv = p;
+        }
+        __syncthreads();
+        const int p = piv;
+        if (p != j)
+            for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+                const double t = colref(a, j);
+                colref(a, j) = colref(a, p);
+                colref(a, p) = t;
+            }
+        __syncthreads();
+        // re-orthogonalise the pivot column against q_0..q_{j-1}
+        if (j > 0) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = 0.0;
+            for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+                const double t = colref(a, j);
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c < j) v[c] = fma(colref(a, c), t, v[c]);
+            }
+            ddgdev::block_sum32(v, red, vals);
+            for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+                double t = colref(a, j);
+                for (int c = 0; c < j; ++c) t -= vals[c] * colref(a, c);
+                colref(a, j) = t;
+            }
+            __syncthreads();
+        }
+        double nn = 0.0;
+        for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+            const double t = colref(a, j);
+            nn = fma(t, t, nn);
+        }
+        const double rjj = sqrt(ddgdev::block_sum(nn, red));
+        if (j == 0) {
+            if (threadIdx.x == 0) r00 = rjj;
+            __syncthreads();
+        }
+        if (!(rjj > rank_tol * r00) || !(r00 > 0.0)) break;
+        const double inv = 1.0 / rjj;
+        for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) colref(a, j) *= inv;
+        __syncthreads();
+        rank = j + 1;
+        // remove q_j from the remaining columns (modified Gram-Schmidt step)
+        if (j + 1 < k) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] = 0.0;
+            for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+                const double qj = colref(a, j);
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c > j && c < k) v[c] = fma(qj, colref(a, c), v[c]);
+            }
+            ddgdev::block_sum32(v, red, vals);
+            for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
+                const double qj = colref(a, j);
+                for (int c = j + 1; c < k; ++c) colref(a, c) -= vals[c] * qj;
+            }
+            __syncthreads();
+        }
+    }
+    for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x)
+        for (int j = rank; j < kmax; ++j) colref(a, j) = 0.0;
+    if (threadIdx.x == 0) rank_out[s] = rank;
+}
+
+// ---------------------------------------------------------------- A0 assembly
+__device__ __forceinline__ size_t band_index(int row, int col, int Wt) {
+    const int R = row / CT, C = col / CT;
+    return ((size_t)R * (Wt + 1) + (R - C)) * CT * CT + (row % CT) * CT + (col % CT);
+}
+
+// One CTA per block (I, J), I >= J: A0[(I,s),(J,t)] = sum_{g in Omega_I}
+// Q[g,s] sum_{c in row g, part(c) = J} A[g,c] Q[c,t]
+__global__ void coarse_assemble_kernel(const int32_t* __restrict__ bI, const int32_t* __restrict__ bJ,
+                                       const int64_t* __restrict__ sub_off,
+                                       const int32_t* __restrict__ sub_nodes,
+                                       const int32_t* __restrict__ pos,
+                                       const int32_t* __restrict__ part,
+                                       const int64_t* __restrict__ rowptr,
+                                       const int32_t* __restrict__ col,
+                                       const double* __restrict__ val,
+                                       const double* __restrict__ Q, int kmax,
+                                       const int32_t* __restrict__ coff, double* band, int Wt) {
+    const int I = bI[blockIdx.x], J = bJ[blockIdx.x];
+    const int kI = coff[I + 1] - coff[I], kJ = coff[J + 1] - coff[J];
+    for (int pr = threadIdx.x; pr < kI * kJ; pr += blockDim.x) {
+        const int s = pr / kJ, t = pr % kJ;
+        const int row = coff[I] + s, cl = coff[J] + t;
+        if (row < cl) continue;
+        double acc = 0.0;
+        for (int64_t a = sub_off[I]; a < sub_off[I + 1]; ++a) {
+            const int g = sub_nodes[a];
+            double inner = 0.0;
+            for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+                const int c = col[e];
+                if (part[c] == J) inner = fma(val[e], Q[(int64_t)pos[c] * kmax + t], inner);
+            }
+            acc = fma(Q[a * kmax + s], inner, acc);
+        }
+        band[band_index(row, cl, Wt)] = acc;
+    }
+}
+
+__global__ void band_identity_pad_kernel(double* band, int Wt, int n0, int n0p) {
+    const int i = n0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n0p) band[band_index(i, i, Wt)] = 1.0;
+}
+
+// ---------------------------------------------------------------- band Cholesky
+// 64x64 tiles, 256 threads, 4x4 register micro-tiles
+__device__ __forceinline__ void ct_load(double* s, const double* g) {
+    for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) s[(i >> 6) * CLD + (i & 63)] = g[i];
+}
+__device__ __forceinline__ void ct_store(double* g, const double* s) {
+    for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) g[i] = s[(i >> 6) * CLD + (i & 63)];
+}
+
+// acc += A * B^T (NT) or A * B (NN), 64x64x64
+template <bool TRANS_B>
+__device__ __forceinline__ void ct_mac(double (&acc)[4][4], const double* A, const double* B) {
+    const int r0 = (threadIdx.x >> 4) * 4, c0 = (threadIdx.x & 15) * 4;
+#pragma unroll 2
+    for (int m = 0; m < CT; ++m) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = A[(r0 + i) * CLD + m];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = TRANS_B ? B[(c0 + i) * CLD + m] : B[m * CLD + c0 + i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], b[jj], acc[i][jj]);
+    }
+}
+
+__device__ __forceinline__ void acc_zero4(double (&acc)[4][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+}
+
+__global__ void __launch_bounds__(256) band_potrf_kernel(double* band, int Wt, int k, double* dinv,
+                                                         int* err) {
+    extern __shared__ double sm[];
+    double* S = sm;
+    double* X = sm + CT * CLD;
+    __shared__ int bad;
+    double* tile = band + (size_t)k * (Wt + 1) * CT * CT;   // (k, k): offset R - C = 0
+    if (threadIdx.x == 0) bad = 0;
+    ct_load(S, tile);
+    __syncthreads();
+    for (int j = 0; j < CT; ++j) {
+        if (threadIdx.x == 0) {
+            double d = S[j * CLD + j];
+            if (!(d > 0.0)) {
+                bad = 1;
+                d = 1.0;
+            }
+            S[j * CLD + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (threadIdx.x > j && threadIdx.x < CT) S[threadIdx.x * CLD + j] /= S[j * CLD + j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+            const int r = i >> 6, c = i & 63;
+            if (c > j && r >= c) S[r * CLD + c] -= S[r * CLD + j] * S[c * CLD + j];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < CT * CT; i += blockDim.x) {
+        const int r = i >> 6, c = i & 63;
+        if (c > r) S[r * CLD + c] = 0.0;
+        X[r * CLD + c] = 0.0;
+    }
+    __syncthreads();
+    ct_store(tile, S);
+    if (threadIdx.x < CT) {   // X = L_kk^{-1}, one thread per column
+        const int c = threadIdx.x;
+        X[c * CLD + c] = 1.0 / S[c * CLD + c];
+        for (int r = c + 1; r < CT; ++r) {
+            double s = 0.0;
+            for (int m = c; m < r; ++m) s = fma(S[r * CLD + m], X[m * CLD + c], s);
+            X[r * CLD + c] = -s / S[r * CLD + r];
+        }
+    }
+    __syncthreads();
+    ct_store(dinv + (size_t)k * CT * CT, X);
+    if (threadIdx.x == 0 && bad) atomicExch(err, 1);
+}
+
+// L_ik = A_ik L_kk^{-T} for i = k+1 .. k+m
+__global__ void __launch_bounds__(256) band_trsm_kernel(double* band, int Wt, int k,
+                                                        const double* dinv) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* X = sm + CT * CLD;
+    const int i = k + 1 + blockIdx.x;
+    double* tile = band + ((size_t)i * (Wt + 1) + (i - k)) * CT * CT;
+    ct_load(A, tile);
+    ct_load(X, dinv + (size_t)k * CT * CT);
+    __syncthreads();
+    double acc[4][4];
+    acc_zero4(acc);
+    ct_mac<true>(acc, A, X);
+    const int r0 = (threadIdx.x >> 4) * 4, c0 = (threadIdx.x & 15) * 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) tile[(r0 + a) * CT + c0 + b] = acc[a][b];
+}
+
+// A_ij -= L_ik L_jk^T for k < j <= i <= k+m
+__global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, int k) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Bt = sm + CT * CLD;
+    int p = blockIdx.x, i = k + 1, w = 1;
+    while (p >= w) {   // pairs (i, j) enumerated row by row: row i has i - k tiles
+        p -= w;
+        ++i;
+        ++w;
+    }
+    const int j = k + 1 + p;
+    ct_load(A, band + ((size_t)i * (Wt + 1) + (i - k)) * CT * CT);
+    ct_load(Bt, band + ((size_t)j * (Wt + 1) + (j - k)) * CT * CT);
+    __syncthreads();
+    double acc[4][4];
+    acc_zero4(acc);
+    ct_mac<true>(acc, A, Bt);
+    double* C = band + ((size_t)i * (Wt + 1) + (i - j)) * CT * CT;
+    const int r0 = (threadIdx.x >> 4) * 4, c0 = (threadIdx.x & 15) * 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) C[(r0 + a) * CT + c0 + b] -= acc[a][b];
+}
+
+// W = L_KK^{-1} of super-block K, tile column jj: W_jj = dinv, and for
+// ii > jj: W_ij = -dinv_i sum_{m=jj}^{ii-1} L_im W_mj (tile forward substitution)
+__global__ void __launch_bounds__(256) superblock_inverse_kernel(const double* band, int Wt,
+                                                                 const double* dinv, double* W,
+                                                                 int NT) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Bm = sm + CT * CLD;
+    const int K = blockIdx.y, jj = blockIdx.x;
+    const int base = K * Wt;
+    const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
+    auto wtile = [&](int ii, int j2) { return W + ((size_t)K * Ptiles + (size_t)ii * (ii + 1) / 2 + j2) * CT * CT; };
+    const double* dj = dinv + (size_t)(base + jj) * CT * CT;
+    for (int e = threadIdx.x; e < CT * CT; e += blockDim.x) wtile(jj, jj)[e] = dj[e];
+    __syncthreads();
+    const int r0 = (threadIdx.x >> 4) * 4, c0 = (threadIdx.x & 15) * 4;
+    for (int ii = jj + 1; ii < Wt; ++ii) {
+        const int Ri = base + ii;
+        if (Ri >= NT) break;
+        double acc[4][4];
+        acc_zero4(acc);
+        for (int mm = jj; mm < ii; ++mm) {
+            const int Rm = base + mm;
+            ct_load(A, band + ((size_t)Ri * (Wt + 1) + (Ri - Rm)) * CT * CT);
+            ct_load(Bm, wtile(mm, jj));
+            __syncthreads();
+            ct_mac<false>(acc, A, Bm);
+            __syncthreads();
+        }
+        // S -> Bm, dinv_i -> A, W_ij = -dinv_i S
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Bm[(r0 + a) * CLD + c0 + b] = acc[a][b];
+        ct_load(A, dinv + (size_t)Ri * CT * CT);
+        __syncthreads();
+        acc_zero4(acc);
+        ct_mac<false>(acc, A, Bm);
+        double* out = wtile(ii, jj);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) out[(r0 + a) * CT + c0 + b] = -acc[a][b];
+        __syncthreads();
+    }
+}
+
+// profile-row fills (one warp per row)
+enum { PM_D = 0, PM_E = 1, PM_DT = 2, PM_ET = 3 };
+
+template <int KIND>
+__global__ void profile_fill_kernel(ProfileMat M, int rows, const double* band, const double* W,
+                                    int Wt, int B) {
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wid >= rows) return;
+    const int i = wid;
+    const int lo = M.lo[i], hi = M.hi[i];
+    const int64_t rp = M.rowptr[i];
+    const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
+    for (int jc = lo + lane; jc < hi; jc += 32) {
+        double v;
+        if (KIND == PM_D || KIND == PM_DT) {
+            // D[a][b] with a >= b in super-block K: row-major W tiles
+            const int a = KIND == PM_D ? i : jc, b = KIND == PM_D ? jc : i;
+            const int K = a / B, la = a - K * B, lb = b - K * B;
+            const int ti = la / CT, tj = lb / CT;
+            v = W[((size_t)K * Ptiles + (size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (la % CT) * CT + (lb % CT)];
+        } else {
+            // E[a][b] = L[a][b] with a in super-block K, b in K-1
+            const int a = KIND == PM_E ? i : jc, b = KIND == PM_E ? jc : i;
+            v = band[band_index(a, b, Wt)];
+        }
+        M.v64[rp + (jc - lo)] = v;
+        if (M.v32) M.v32[rp + (jc - lo)] = (float)v;
+    }
+}
+
+// ---------------------------------------------------------------- apply
+// out[i] = (a ? a[i] : 0) + sign * sum_{j in [lo_i, hi_i)} M[i][j] x[j], one warp per row
+template <typename V, typename MV>
+__global__ void profile_gemv_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lo,
+                                    const int32_t* __restrict__ hi, const MV* __restrict__ vals,
+                                    int r0, int r1, const V* __restrict__ x, const V* __restrict__ a,
+                                    V sign, V* __restrict__ out) {
+    const int i = r0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= r1) return;
+    const int l = lo[i], hgh = hi[i];
+    const MV* rv = vals + rowptr[i] - l;
+    V s = 0;
+    for (int j = l + lane; j < hgh; j += 32) s = fma((V)__ldcs(rv + j), x[j], s);
+    s = ddgdev::warp_sum(s);
+    if (lane == 0) out[i] = (a ? a[i] : (V)0) + sign * s;
+}
+
+// c[coff_s + j] = sum_{g in Omega_s} Q[g, j] (r - A z)[g]   (z = 0 skips A z)
+template <typename V, typename AV>
+__global__ void __launch_bounds__(256) coarse_restrict_kernel(
+    const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const AV* __restrict__ val,
+    const V* __restrict__ r, const V* __restrict__ z, const V* __restrict__ Q, int kmax,
+    const int32_t* __restrict__ coff, V* __restrict__ c, int residual) {
+    __shared__ V red[32 * 8];
+    __shared__ V out[32];
+    const int s = blockIdx.x;
+    V acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0;
+    for (int64_t a = sub_off[s] + threadIdx.x; a < sub_off[s + 1]; a += blockDim.x) {
+        const int g = sub_nodes[a];
+        V w = r[g];
+        if (residual)
+            for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) w -= (V)val[e] * z[col[e]];
+        const V* qa = Q + a * kmax;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < kmax) acc[j] = fma(qa[j], w, acc[j]);
+    }
+    ddgdev::block_sum32(acc, red, out);
+    const int ks = coff[s + 1] - coff[s];
+    if (threadIdx.x < ks) c[coff[s] + threadIdx.x] = out[threadIdx.x];
+}
+
+// z[g] += sum_j Q[pos g, j] y[coff_{part g} + j]
+template <typename V>
+__global__ void coarse_prolong_kernel(int64_t n, const int32_t* __restrict__ part,
+                                      const int32_t* __restrict__ pos, const V* __restrict__ Q,
+                                      int kmax, const int32_t* __restrict__ coff,
+                                      const V* __restrict__ y, V* __restrict__ z) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const int s = part[g];
+    const int c0 = coff[s], ks = coff[s + 1] - c0;
+    const V* qa = Q + (int64_t)pos[g] * kmax;
+    V acc = 0;
+    for (int j = 0; j < ks; ++j) acc = fma(qa[j], y[c0 + j], acc);
+    z[g] += acc;
+}
+
+}  // namespace
+
+namespace ddg {
+
+void coarse_qr(ddg_handle h, int32_t* d_rank, const double* dF, int k) {
+    coarse_qr_kernel<<<h->nsub, 256, 0, h->stream>>>(h->sub_off, h->sub_nodes, dF, h->n, k, h->kmax,
+                                                     h->opt.rank_tol, h->Q64, d_rank);
+    DDG_CHECK_LAUNCH();
+}
+
+void coarse_assemble_band(ddg_handle h, const std::vector<int>& bI, const std::vector<int>& bJ) {
+    const size_t ntiles = (size_t)h->NT * (h->Wt + 1);
+    DDG_CUDA(cudaMemsetAsync(h->bandL, 0, ntiles * CT * CT * sizeof(double), h->stream));
+    if (!bI.empty()) {
+        int32_t* dI = h->arena.alloc<int32_t>(bI.size());
+        int32_t* dJ = h->arena.alloc<int32_t>(bJ.size());
+        h2d(dI, bI.data(), bI.size(), h->stream);
+        h2d(dJ, bJ.data(), bJ.size(), h->stream);
+        coarse_assemble_kernel<<<(unsigned)bI.size(), 128, 0, h->stream>>>(
+            dI, dJ, h->sub_off, h->sub_nodes, h->pos, h->part, h->rowptr, h->col, h->val64, h->Q64,
+            h->kmax, h->coff, h->bandL, h->Wt);
+        DDG_CHECK_LAUNCH();
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        h->arena.release(dI);
+        h->arena.release(dJ);
+    }
+    const int npad = h->n0p - h->n0;
+    if (npad > 0) {
+        band_identity_pad_kernel<<<(npad + 255) / 256, 256, 0, h->stream>>>(h->bandL, h->Wt, h->n0,
+                                                                            h->n0p);
+        DDG_CHECK_LAUNCH();
+    }
+}
+
+void coarse_band_cholesky(ddg_handle h) {
+    const size_t sm2 = 2 * CT * CLD * sizeof(double);
+    DDG_CUDA(cudaFuncSetAttribute(band_potrf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    DDG_CUDA(cudaFuncSetAttribute(superblock_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    double* dinv = h->arena.alloc<double>((size_t)h->NT * CT * CT);
+    const int Wt = h->Wt, NT = h->NT;
+    for (int k = 0; k < NT; ++k) {
+        band_potrf_kernel<<<1, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, h->errflags + E_COARSE_SPD);
+        DDG_CHECK_LAUNCH();
+        const int m = std::min(Wt, NT - 1 - k);
+        if (m > 0) {
+            band_trsm_kernel<<<m, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv);
+            DDG_CHECK_LAUNCH();
+            band_update_kernel<<<m * (m + 1) / 2, 256, sm2, h->stream>>>(h->bandL, Wt, k);
+            DDG_CHECK_LAUNCH();
+        }
+    }
+    // super-block inverses D_K = L_KK^{-1}
+    const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
+    double* W = h->arena.alloc<double>((size_t)h->nK * Ptiles * CT * CT);
+    DDG_CUDA(cudaMemsetAsync(W, 0, (size_t)h->nK * Ptiles * CT * CT * sizeof(double), h->stream));
+    superblock_inverse_kernel<<<dim3(Wt, h->nK), 256, sm2, h->stream>>>(h->bandL, Wt, dinv, W, NT);
+    DDG_CHECK_LAUNCH();
+    h->coarseW = W;
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    h->arena.release(dinv);
+}
+
+static void alloc_profile(ddg_handle h, ProfileMat& M, const std::vector<int>& lo,
+                          const std::vector<int>& hi, bool fp32) {
+    const int rows = (int)lo.size();
+    std::vector<int64_t> rp(rows + 1, 0);
+    for (int i = 0; i < rows; ++i) rp[i + 1] = rp[i] + std::max(0, hi[i] - lo[i]);
+    M.nnz = rp[rows];
+    M.rowptr = h->arena.alloc<int64_t>(rows + 1);
+    M.lo = h->arena.alloc<int32_t>(rows);
+    M.hi = h->arena.alloc<int32_t>(rows);
+    M.v64 = h->arena.alloc<double>(M.nnz);
+    M.v32 = fp32 ? h->arena.alloc<float>(M.nnz) : nullptr;
+    h2d(M.rowptr, rp.data(), rows + 1, h->stream);
+    h2d(M.lo, lo.data(), rows, h->stream);
+    h2d(M.hi, hi.data(), rows, h->stream);
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+void coarse_build_apply(ddg_handle h) {
+    const int n0p = h->n0p, B = h->B, Wt = h->Wt, nK = h->nK;
+    const bool fp32 = true;
+    std::vector<int> lo(n0p), hi(n0p);
+    // D: lower triangle of the super-block
+    for (int i = 0; i < n0p; ++i) {
+        lo[i] = (i / B) * B;
+        hi[i] = i + 1;
+    }
+    alloc_profile(h, h->Dm, lo, hi, fp32);
+    // E: columns of super-block K-1 inside the tile band
+    for (int i = 0; i < n0p; ++i) {
+        const int K = i / B, R = i / CT;
+        if (K == 0) {
+            lo[i] = hi[i] = 0;
+        } else {
+            lo[i] = std::max((K - 1) * B, (R - Wt) * CT);
+            hi[i] = K * B;
+        }
+    }
+    alloc_profile(h, h->Em, lo, hi, fp32);
+    // D^T: upper triangle of the super-block
+    for (int i = 0; i < n0p; ++i) {
+        lo[i] = i;
+        hi[i] = (i / B + 1) * B;
+    }
+    alloc_profile(h, h->Dt, lo, hi, fp32);
+    // E^T: row j of E_{K+1}^T = column j of E_{K+1}
+    for (int j = 0; j < n0p; ++j) {
+        const int K = j / B;
+        if (K >= nK - 1) {
+            lo[j] = hi[j] = 0;
+        } else {
+            lo[j] = (K + 1) * B;
+            hi[j] = std::min((K + 2) * B, (j / CT + Wt + 1) * CT);
+        }
+    }
+    alloc_profile(h, h->Et, lo, hi, fp32);
+    const unsigned blocks = (unsigned)((n0p * 32 + 255) / 256);
+    profile_fill_kernel<PM_D><<<blocks, 256, 0, h->stream>>>(h->Dm, n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_E><<<blocks, 256, 0, h->stream>>>(h->Em, n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_DT><<<blocks, 256, 0, h->stream>>>(h->Dt, n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_ET><<<blocks, 256, 0, h->stream>>>(h->Et, n0p, h->bandL, h->coarseW, Wt, B);
+    DDG_CHECK_LAUNCH();
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    h->arena.release(h->coarseW);
+    h->coarseW = nullptr;
+    h->arena.release(h->bandL);
+    h->bandL = nullptr;
+}
+
+void coarse_restrict(ddg_handle h, int prec, bool residual) {
+    if (prec == DDG_PREC_FP64)
+        coarse_restrict_kernel<double, double><<<h->nsub, 256, 0, h->stream>>>(
+            h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->Q64,
+            h->kmax, h->coff, h->c64, residual);
+    else
+        coarse_restrict_kernel<float, float><<<h->nsub, 256, 0, h->stream>>>(
+            h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->Q32, h->kmax,
+            h->coff, h->c32, residual);
+    DDG_CHECK_LAUNCH();
+}
+
+template <typename V>
+static void gemv(ddg_handle h, const ProfileMat& M, int r0, int r1, const V* x, const V* a, V sign,
+                 V* out) {
+    if (r1 <= r0) return;
+    const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * 32 + 255) / 256);
+    if (sizeof(V) == 8)
+        profile_gemv_kernel<double, double><<<blocks, 256, 0, h->stream>>>(
+            M.rowptr, M.lo, M.hi, M.v64, r0, r1, (const double*)x, (const double*)a, (double)sign,
+            (double*)out);
+    else
+        profile_gemv_kernel<float, float><<<blocks, 256, 0, h->stream>>>(
+            M.rowptr, M.lo, M.hi, M.v32, r0, r1, (const float*)x, (const float*)a, (float)sign,
+            (float*)out);
+    DDG_CHECK_LAUNCH();
+}
+
+template <typename V>
+static void coarse_solve_t(ddg_handle h, V* c, V* y, V* t, V* x) {
+    const int B = h->B, nK = h->nK;
+    // forward: y_K = D_K (c_K - E_K y_{K-1})
+    for (int K = 0; K < nK; ++K) {
+        const int r0 = K * B, r1 = r0 + B;
+        const V* in = c;
+        if (K > 0) {
+            gemv<V>(h, h->Em, r0, r1, y, c, (V)-1, t);
+            in = t;
+        }
+        gemv<V>(h, h->Dm, r0, r1, in, nullptr, (V)1, y);
+    }
+    // backward: x_K = D_K^T (y_K - E_{K+1}^T x_{K+1})
+    for (int K = nK - 1; K >= 0; --K) {
+        const int r0 = K * B, r1 = r0 + B;
+        const V* in = y;
+        if (K < nK - 1) {
+            gemv<V>(h, h->Et, r0, r1, x, y, (V)-1, t);
+            in = t;
+        }
+        gemv<V>(h, h->Dt, r0, r1, in, nullptr, (V)1, x);
+    }
+}
+
+void coarse_solve(ddg_handle h, int prec) {
+    if (prec == DDG_PREC_FP64) coarse_solve_t<double>(h, h->c64, h->y64, h->t64, h->x64);
+    else coarse_solve_t<float>(h, h->c32, h->y32, h->t32, h->x32);
+}
+
+void coarse_prolong(ddg_handle h, int prec) {
+    const unsigned blocks = (unsigned)((h->n + 255) / 256);
+    if (prec == DDG_PREC_FP64)
+        coarse_prolong_kernel<double><<<blocks, 256, 0, h->stream>>>(h->n, h->part, h->pos, h->Q64,
+                                                                     h->kmax, h->coff, h->x64, h->z64);
+    else
+        coarse_prolong_kernel<float><<<blocks, 256, 0, h->stream>>>(h->n, h->part, h->pos, h->Q32,
+                                                                    h->kmax, h->coff, h->x32, h->z32);
+    DDG_CHECK_LAUNCH();
+}
+
+}  // namespace ddg

@@ -1,0 +1,538 @@
+// Local subdomain operators of the multiplicative Schwarz smoother (Sec. 6).
+//
+// Setup: A_i = R~_i A R~_i^T is gathered densely (FP64), factored A_i = L L^T
+// and inverted (A_i^{-1} = L^{-T} L^{-1}) in 32x32 tiles by one CTA per
+// subdomain, and the upper-triangular tiles of the symmetric inverse are
+// packed in FP64 / FP32 / BF16.
+//
+// Apply (per colour c of the sweep; subdomains of one colour do not interact):
+//   res_i = (r - A z)[Omega~_i]            local_residual_kernel
+//   z[Omega~_i] += A_i^{-1} res_i          local_solve_kernel
+// The second kernel streams the packed inverse; every tile (I, J), I < J,
+// is read once and used twice (y_I += B x_J and y_J += B^T x_I), which halves
+// the bytes of a dense GEMV.  Work items are chunks of consecutive tiles of
+// one subdomain; the CTA that finishes a subdomain's last chunk sums the
+// chunk partials in a fixed order and scatters into z, so the result is
+// deterministic.
+#include "ddg_internal.cuh"
+#include "dev_common.cuh"
+
+namespace {
+
+constexpr int LDT = DDG_LT + 1;  // padded smem row of a 32x32 FP64 tile
+
+__device__ __forceinline__ void tload(double* s, const double* g, int ld) {
+    for (int i = threadIdx.x; i < DDG_LT * DDG_LT; i += blockDim.x) {
+        int r = i >> 5, c = i & 31;
+        s[r * LDT + c] = g[(size_t)r * ld + c];
+    }
+}
+
+__device__ __forceinline__ void tstore(double* g, const double* s, int ld) {
+    for (int i = threadIdx.x; i < DDG_LT * DDG_LT; i += blockDim.x) {
+        int r = i >> 5, c = i & 31;
+        g[(size_t)r * ld + c] = s[r * LDT + c];
+    }
+}
+
+enum { NN = 0, NT = 1, TN = 2 };
+
+// acc (2x2 per thread, 256 threads cover 32x32) += op(A) op(B)
+template <int MODE>
+__device__ __forceinline__ void tile_mac(double (&acc)[2][2], const double* A, const double* B) {
+    const int r0 = (threadIdx.x >> 4) * 2, c0 = (threadIdx.x & 15) * 2;
+#pragma unroll 4
+    for (int m = 0; m < DDG_LT; ++m) {
+        double a0, a1, b0, b1;
+        if (MODE == TN) {
+            a0 = A[m * LDT + r0];
+            a1 = A[m * LDT + r0 + 1];
+        } else {
+            a0 = A[r0 * LDT + m];
+            a1 = A[(r0 + 1) * LDT + m];
+        }
+        if (MODE == NT) {
+            b0 = B[c0 * LDT + m];
+            b1 = B[(c0 + 1) * LDT + m];
+        } else {
+            b0 = B[m * LDT + c0];
+            b1 = B[m * LDT + c0 + 1];
+        }
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+}
+
+__device__ __forceinline__ void acc_zero(double (&acc)[2][2]) {
+    acc[0][0] = acc[0][1] = acc[1][0] = acc[1][1] = 0.0;
+}
+
+// global tile (row-major, leading dimension ld) <-> accumulator registers
+__device__ __forceinline__ void acc_load(double (&acc)[2][2], const double* g, int ld) {
+    const int r0 = (threadIdx.x >> 4) * 2, c0 = (threadIdx.x & 15) * 2;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) acc[a][b] = g[(size_t)(r0 + a) * ld + c0 + b];
+}
+__device__ __forceinline__ void acc_store(double* g, int ld, const double (&acc)[2][2], double s) {
+    const int r0 = (threadIdx.x >> 4) * 2, c0 = (threadIdx.x & 15) * 2;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) g[(size_t)(r0 + a) * ld + c0 + b] = s * acc[a][b];
+}
+__device__ __forceinline__ void acc_to_smem(double* s, const double (&acc)[2][2]) {
+    const int r0 = (threadIdx.x >> 4) * 2, c0 = (threadIdx.x & 15) * 2;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) s[(r0 + a) * LDT + c0 + b] = acc[a][b];
+}
+
+// unblocked Cholesky of the 32x32 tile in smem (lower; upper zeroed);
+// a non-positive pivot sets *bad and continues with pivot 1
+__device__ void potrf32(double* S, int* bad) {
+    for (int j = 0; j < DDG_LT; ++j) {
+        if (threadIdx.x == 0) {
+            double d = S[j * LDT + j];
+            if (!(d > 0.0)) {
+                *bad = 1;
+                d = 1.0;
+            }
+            S[j * LDT + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (threadIdx.x > j && threadIdx.x < DDG_LT) S[threadIdx.x * LDT + j] /= S[j * LDT + j];
+        __syncthreads();
+        for (int i = threadIdx.x; i < DDG_LT * DDG_LT; i += blockDim.x) {
+            int r = i >> 5, c = i & 31;
+            if (c > j && r >= c) S[r * LDT + c] -= S[r * LDT + j] * S[c * LDT + j];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < DDG_LT * DDG_LT; i += blockDim.x) {
+        int r = i >> 5, c = i & 31;
+        if (c > r) S[r * LDT + c] = 0.0;
+    }
+    __syncthreads();
+}
+
+// X = L^{-1} for the lower-triangular 32x32 tile L (column-wise forward
+// substitution, one thread per column)
+__device__ void trtri32(const double* L, double* X) {
+    for (int i = threadIdx.x; i < DDG_LT * DDG_LT; i += blockDim.x) X[(i >> 5) * LDT + (i & 31)] = 0.0;
+    __syncthreads();
+    if (threadIdx.x < DDG_LT) {
+        const int c = threadIdx.x;
+        X[c * LDT + c] = 1.0 / L[c * LDT + c];
+        for (int r = c + 1; r < DDG_LT; ++r) {
+            double s = 0.0;
+            for (int m = c; m < r; ++m) s = fma(L[r * LDT + m], X[m * LDT + c], s);
+            X[r * LDT + c] = -s / L[r * LDT + r];
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- setup
+__global__ void local_extract_kernel(int q0, const int64_t* __restrict__ ov_off,
+                                     const int32_t* __restrict__ ov_nodes,
+                                     const int64_t* __restrict__ rowptr,
+                                     const int32_t* __restrict__ col,
+                                     const double* __restrict__ val, double* ws, int Np) {
+    const int b = blockIdx.x, q = q0 + b;
+    const int64_t o = ov_off[q];
+    const int n = (int)(ov_off[q + 1] - o);
+    double* A = ws + (size_t)b * Np * Np;
+    const int32_t* nodes = ov_nodes + o;
+    for (int a = threadIdx.x; a < Np; a += blockDim.x) {
+        if (a >= n) {
+            A[(size_t)a * Np + a] = 1.0;  // identity padding keeps the block SPD
+            continue;
+        }
+        const int g = nodes[a];
+        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+            const int c = col[e];
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (nodes[mid] < c) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < n && nodes[lo] == c) A[(size_t)a * Np + lo] = val[e];
+        }
+    }
+}
+
+// In-place: A (Np x Np, row-major) -> its inverse in the upper tiles (I <= J).
+__global__ void __launch_bounds__(256) local_factor_invert_kernel(
+    int q0, const int32_t* __restrict__ Tq, double* ws, double* invdiag, int Np, int Tmax,
+    int* err) {
+    extern __shared__ double sm[];
+    double* sA = sm;
+    double* sB = sm + DDG_LT * LDT;
+    double* sC = sm + 2 * DDG_LT * LDT;
+    __shared__ int bad;
+    const int b = blockIdx.x;
+    const int T = Tq[q0 + b];
+    double* A = ws + (size_t)b * Np * Np;
+    double* D = invdiag + (size_t)b * Tmax * DDG_LT * DDG_LT;
+    auto tile = [&](int I, int J) { return A + (size_t)I * DDG_LT * Np + J * DDG_LT; };
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    double acc[2][2];
+
+    // 1) right-looking blocked Cholesky A = L L^T
+    for (int k = 0; k < T; ++k) {
+        tload(sA, tile(k, k), Np);
+        __syncthreads();
+        potrf32(sA, &bad);
+        tstore(tile(k, k), sA, Np);
+        trtri32(sA, sB);                         // sB = L_kk^{-1}
+        tstore(D + (size_t)k * DDG_LT * DDG_LT, sB, DDG_LT);
+        __syncthreads();
+        for (int i = k + 1; i < T; ++i) {        // L_ik = A_ik L_kk^{-T}
+            tload(sA, tile(i, k), Np);
+            __syncthreads();
+            acc_zero(acc);
+            tile_mac<NT>(acc, sA, sB);
+            __syncthreads();
+            acc_store(tile(i, k), Np, acc, 1.0);
+        }
+        __syncthreads();
+        for (int j = k + 1; j < T; ++j) {        // A_ij -= L_ik L_jk^T
+            tload(sB, tile(j, k), Np);
+            for (int i = j; i < T; ++i) {
+                tload(sA, tile(i, k), Np);
+                __syncthreads();
+                acc_load(acc, tile(i, j), Np);
+                double neg[2][2];
+                acc_zero(neg);
+                tile_mac<NT>(neg, sA, sB);
+                for (int a = 0; a < 2; ++a)
+                    for (int c = 0; c < 2; ++c) acc[a][c] -= neg[a][c];
+                acc_store(tile(i, j), Np, acc, 1.0);
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+    }
+
+    // 2) W = L^{-1} in place (lower tiles), column by column
+    for (int j = 0; j < T; ++j) {
+        tload(sA, D + (size_t)j * DDG_LT * DDG_LT, DDG_LT);
+        __syncthreads();
+        tstore(tile(j, j), sA, Np);
+        __syncthreads();
+        for (int i = j + 1; i < T; ++i) {
+            acc_zero(acc);
+            for (int m = j; m < i; ++m) {        // S = sum_m L_im W_mj
+                tload(sA, tile(i, m), Np);
+                tload(sB, tile(m, j), Np);
+                __syncthreads();
+                tile_mac<NN>(acc, sA, sB);
+                __syncthreads();
+            }
+            acc_to_smem(sC, acc);
+            tload(sA, D + (size_t)i * DDG_LT * DDG_LT, DDG_LT);
+            __syncthreads();
+            acc_zero(acc);
+            tile_mac<NN>(acc, sA, sC);           // W_ij = -L_ii^{-1} S
+            __syncthreads();
+            acc_store(tile(i, j), Np, acc, -1.0);
+            __syncthreads();
+        }
+    }
+
+    // 3) A^{-1} = W^T W, upper tiles (I <= J); the diagonal tile of a column last
+    for (int j = 0; j < T; ++j) {
+        for (int i = 0; i <= j; ++i) {
+            acc_zero(acc);
+            for (int m = j; m < T; ++m) {
+                tload(sA, tile(m, i), Np);
+                tload(sB, tile(m, j), Np);
+                __syncthreads();
+                tile_mac<TN>(acc, sA, sB);
+                __syncthreads();
+            }
+            acc_store(tile(i, j), Np, acc, 1.0);
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0 && bad) atomicExch(err, 1);
+}
+
+__global__ void local_pack_kernel(int q0, const double* __restrict__ ws, int Np,
+                                  const int64_t* __restrict__ ov_off,
+                                  const int32_t* __restrict__ Tq,
+                                  const int64_t* __restrict__ tile_off, double* inv64,
+                                  float* inv32, __nv_bfloat16* inv16) {
+    const int b = blockIdx.x, q = q0 + b;
+    const int n = (int)(ov_off[q + 1] - ov_off[q]);
+    const int T = Tq[q];
+    const double* A = ws + (size_t)b * Np * Np;
+    const int64_t base = tile_off[q];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // warp w packs tiles w, w + nw, ... in row-major upper-triangle order
+    int t = 0;
+    for (int I = 0; I < T; ++I) {
+        for (int J = I; J < T; ++J, ++t) {
+            if (t % nw != warp) continue;
+            const int gc = J * DDG_LT + lane;
+            for (int r = 0; r < DDG_LT; ++r) {
+                const int gr = I * DDG_LT + r;
+                const double v = (gr < n && gc < n) ? A[(size_t)gr * Np + gc] : 0.0;
+                const size_t dst = (size_t)(base + t) * 1024 + r * 32 + lane;
+                if (inv64) inv64[dst] = v;
+                if (inv32) inv32[dst] = (float)v;
+                if (inv16) inv16[dst] = __float2bfloat16_rn((float)v);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- apply
+template <typename V, typename AV>
+__global__ void local_residual_kernel(int64_t a0, int64_t a1, const int32_t* __restrict__ ov_nodes,
+                                      const int64_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ col,
+                                      const AV* __restrict__ val, const V* __restrict__ r,
+                                      const V* __restrict__ z, V* __restrict__ res, int z_zero) {
+    const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= a1) return;
+    const int g = ov_nodes[a];
+    V s = r[g];
+    if (!z_zero) {
+        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s -= (V)val[e] * z[col[e]];
+    }
+    res[a] = s;
+}
+
+// lane layout of a 32x32 tile for 16-byte loads of element type E:
+// VEC elements per load, LPR lanes per tile row, RPI rows per warp load
+// (RPI == VEC), NIT loads per lane (NIT == LPR)
+template <typename E> struct Lay {
+    static constexpr int VEC = 16 / (int)sizeof(E);
+    static constexpr int LPR = 32 / VEC;
+    static constexpr int RPI = VEC;
+    static constexpr int NIT = LPR;
+};
+
+template <typename E, typename V> struct Cvt;
+template <> struct Cvt<double, double> {
+    static __device__ __forceinline__ void load(const double* p, double (&o)[2]) {
+        double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+        o[0] = t.x;
+        o[1] = t.y;
+    }
+};
+template <> struct Cvt<float, float> {
+    static __device__ __forceinline__ void load(const float* p, float (&o)[4]) {
+        float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+        o[0] = t.x;
+        o[1] = t.y;
+        o[2] = t.z;
+        o[3] = t.w;
+    }
+};
+template <> struct Cvt<__nv_bfloat16, float> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, float (&o)[8]) {
+        uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&t);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float2 f = __bfloat1622float2(h[i]);
+            o[2 * i] = f.x;
+            o[2 * i + 1] = f.y;
+        }
+    }
+};
+
+constexpr int LS_WARPS = 8;
+
+template <typename E, typename V>
+__global__ void __launch_bounds__(LS_WARPS * 32) local_solve_kernel(
+    const int4* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
+    const int32_t* __restrict__ ov_nodes, const int64_t* __restrict__ tile_off,
+    const int32_t* __restrict__ Tq, const int32_t* __restrict__ nchunks,
+    const int32_t* __restrict__ first_item, const E* __restrict__ inv,
+    const V* __restrict__ res, V* __restrict__ partial, unsigned* __restrict__ counter,
+    V* __restrict__ z, int Tmax) {
+    using L = Lay<E>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* x = reinterpret_cast<V*>(smraw);
+    V* yw = x + Tmax * DDG_LT;
+    __shared__ int am_last;
+
+    const int gi = item_base + blockIdx.x;
+    const int4 it = items[gi];
+    const int q = it.x, tb = it.y, te = it.z;
+    const int64_t o = ov_off[q];
+    const int n = (int)(ov_off[q + 1] - o);
+    const int T = Tq[q];
+    const int NP = T * DDG_LT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    V* my = yw + warp * NP;
+
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) x[i] = i < n ? res[o + i] : (V)0;
+    for (int i = threadIdx.x; i < LS_WARPS * NP; i += blockDim.x) yw[i] = (V)0;
+    __syncthreads();
+
+    const int g = lane / L::LPR, j = lane % L::LPR;
+    const int idx = j * L::VEC + g;   // row/col owned by this lane after the reductions
+    const E* base = inv + (size_t)tile_off[q] * 1024;
+
+    int t = tb + warp;
+    int I = 0, J = 0;
+    if (t < te) {
+        int rem = t;
+        while (rem >= T - I) {
+            rem -= T - I;
+            ++I;
+        }
+        J = I + rem;
+    }
+    for (; t < te; t += LS_WARPS) {
+        const E* tp = base + (size_t)t * 1024 + g * 32 + j * L::VEC;
+        V e[L::NIT][L::VEC];
+#pragma unroll
+        for (int k = 0; k < L::NIT; ++k) Cvt<E, V>::load(tp + k * L::RPI * 32, e[k]);
+        V xj[L::VEC];
+#pragma unroll
+        for (int v = 0; v < L::VEC; ++v) xj[v] = x[J * DDG_LT + j * L::VEC + v];
+        V rp[L::NIT];
+#pragma unroll
+        for (int k = 0; k < L::NIT; ++k) {
+            V s = (V)0;
+#pragma unroll
+            for (int v = 0; v < L::VEC; ++v) s = fma(e[k][v], xj[v], s);
+            rp[k] = s;
+        }
+        const V rs = ddgdev::reduce_scatter<L::NIT, 1>(rp, j);
+        my[I * DDG_LT + idx] += rs;
+        if (I != J) {
+            V cp[L::VEC];
+#pragma unroll
+            for (int v = 0; v < L::VEC; ++v) cp[v] = (V)0;
+#pragma unroll
+            for (int k = 0; k < L::NIT; ++k) {
+                const V xi = x[I * DDG_LT + k * L::RPI + g];
+#pragma unroll
+                for (int v = 0; v < L::VEC; ++v) cp[v] = fma(e[k][v], xi, cp[v]);
+            }
+            const V cs = ddgdev::reduce_scatter<L::VEC, L::LPR>(cp, g);
+            my[J * DDG_LT + idx] += cs;
+        }
+        // advance (I, J) by LS_WARPS tiles in row-major upper-triangle order
+        J += LS_WARPS;
+        while (J >= T && I < T) {
+            J = J - T + I + 1;
+            ++I;
+        }
+    }
+    __syncthreads();
+    V* pout = partial + (size_t)gi * Tmax * DDG_LT;
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+        V s = (V)0;
+#pragma unroll
+        for (int w = 0; w < LS_WARPS; ++w) s += yw[w * NP + i];
+        pout[i] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned tk = atomicAdd(&counter[q], 1u);
+        am_last = (tk == (unsigned)nchunks[q] - 1u);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    const int fi = first_item[q], nc = nchunks[q];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        V s = (V)0;
+        for (int c = 0; c < nc; ++c) s += __ldcg(partial + (size_t)(fi + c) * Tmax * DDG_LT + i);
+        const int gnode = ov_nodes[o + i];
+        z[gnode] += s;
+    }
+    if (threadIdx.x == 0) counter[q] = 0u;
+}
+
+}  // namespace
+
+namespace ddg {
+
+void local_extract_factor_invert(ddg_handle h, int q0, int q1, double* ws, double* invdiag) {
+    const int nb = q1 - q0;
+    if (nb <= 0) return;
+    const int Np = h->Tmax * DDG_LT;
+    DDG_CUDA(cudaMemsetAsync(ws, 0, (size_t)nb * Np * Np * sizeof(double), h->stream));
+    local_extract_kernel<<<nb, 256, 0, h->stream>>>(q0, h->ov_off, h->ov_nodes, h->rowptr, h->col,
+                                                    h->val64, ws, Np);
+    DDG_CHECK_LAUNCH();
+    const size_t smem = 3 * DDG_LT * LDT * sizeof(double);
+    local_factor_invert_kernel<<<nb, 256, smem, h->stream>>>(q0, h->Tq, ws, invdiag, Np, h->Tmax,
+                                                            h->errflags + E_LOCAL_SPD);
+    DDG_CHECK_LAUNCH();
+}
+
+void local_pack(ddg_handle h, int q0, int q1, const double* ws) {
+    const int nb = q1 - q0;
+    if (nb <= 0) return;
+    local_pack_kernel<<<nb, 256, 0, h->stream>>>(q0, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq,
+                                                 h->tile_off, h->inv64, h->inv32, h->inv16);
+    DDG_CHECK_LAUNCH();
+}
+
+void local_residual(ddg_handle h, int c, bool z_zero, int prec) {
+    const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
+    if (a1 <= a0) return;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((a1 - a0 + threads - 1) / threads);
+    if (prec == DDG_PREC_FP64) {
+        local_residual_kernel<double, double><<<blocks, threads, 0, h->stream>>>(
+            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->res64, z_zero);
+    } else {
+        local_residual_kernel<float, float><<<blocks, threads, 0, h->stream>>>(
+            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->res32, z_zero);
+    }
+    DDG_CHECK_LAUNCH();
+}
+
+template <typename E, typename V>
+static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, V* partial, V* z) {
+    const int i0 = h->h_citem_off[c], i1 = h->h_citem_off[c + 1];
+    if (i1 <= i0) return;
+    const size_t smem = (size_t)(1 + LS_WARPS) * h->Tmax * DDG_LT * sizeof(V);
+    auto kern = local_solve_kernel<E, V>;
+    kern<<<i1 - i0, LS_WARPS * 32, smem, h->stream>>>(h->items, i0, h->ov_off, h->ov_nodes,
+                                                      h->tile_off, h->Tq, h->nchunks,
+                                                      h->first_item, inv, res, partial,
+                                                      h->counters, z, h->Tmax);
+    DDG_CHECK_LAUNCH();
+}
+
+// The dynamic shared-memory limit is a property of the kernel, shared by all
+// handles: raise it to the largest size any handle needs, never lower it.
+template <typename E, typename V>
+static void configure_local_solve(int Tmax) {
+    static int configured = 0;
+    const int smem = (int)((size_t)(1 + LS_WARPS) * Tmax * DDG_LT * sizeof(V));
+    if (smem <= configured) return;
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    configured = smem;
+}
+
+void local_configure(ddg_handle h) {
+    configure_local_solve<double, double>(h->Tmax);
+    configure_local_solve<float, float>(h->Tmax);
+    configure_local_solve<__nv_bfloat16, float>(h->Tmax);
+}
+
+void local_solve_colour(ddg_handle h, int c, int prec) {
+    if (prec == DDG_PREC_FP64)
+        launch_local_solve<double, double>(h, c, h->inv64, h->res64, h->partial64, h->z64);
+    else if (prec == DDG_PREC_FP32)
+        launch_local_solve<float, float>(h, c, h->inv32, h->res32, h->partial32, h->z32);
+    else
+        launch_local_solve<__nv_bfloat16, float>(h, c, h->inv16, h->res32, h->partial32, h->z32);
+}
+
+}  // namespace ddg

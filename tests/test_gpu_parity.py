@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+Tolerances:
+  * FP64 building blocks (SpMV, coarse correction, preconditioner): 1e-11
+    relative in the 2-norm (rounding-order differences only);
+  * FP64 PCG: relative solution difference <= 1e-10, iterations within 1;
+  * FP32 / BF16 preconditioner with FP64 CG: true relative residual <= tol
+    and relative error against the oracle's solution <= 1e-7 at tol 1e-8;
+  * integer outputs (colouring, coarse ranks): exact.
+"""
+import numpy as np
+import pytest
+
+import ddg_inputs as di
+from oracle import ddg_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = {
+    "poisson2d_64": lambda: di.make_poisson2d(N=64, box=16, overlap=2, p=2, seed=0),
+    "poisson2d_ragged": lambda: di.make_poisson2d(N=50, box=16, overlap=2, p=2, seed=11),
+    "poisson3d_24": lambda: di.make_poisson3d(N=24, box=8, overlap=1, p=2, seed=1),
+    "poisson3d_ragged": lambda: di.make_poisson3d(N=20, box=8, overlap=1, p=2, seed=12),
+    "poisson3d_graph": lambda: di.make_poisson3d(N=16, box=8, overlap=1, p=2, seed=13, mode="graph"),
+    "biharmonic_64": lambda: di.make_biharmonic2d(N=64, box=16, overlap=2, p=3, seed=100),
+    "varcoef_16": lambda: di.make_varcoef3d(N=16, box=8, overlap=1, p=2, m=None),
+    "poisson2d_p0_overlap0": lambda: di.make_poisson2d(N=40, box=10, overlap=0, p=0, seed=14),
+    "single_subdomain": lambda: di.make_poisson2d(N=20, box=20, overlap=1, p=1, seed=15),
+}
+
+_cache = {}
+
+
+def setup_case(name):
+    if name not in _cache:
+        from paper_1504_00907_gb300 import ddg
+        prob = CASES[name]()
+        solver = ddg.Solver.from_problem(prob, precision="fp64", keep=("fp64", "fp32", "bf16"))
+        oracle = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape)
+        _cache[name] = (prob, solver, oracle)
+    return _cache[name]
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_spmv_matches_scipy(name):
+    prob, solver, _ = setup_case(name)
+    x = np.random.default_rng(5).standard_normal(prob.n)
+    y = solver.spmv(dev(x)).cpu().numpy()
+    assert rel(y, prob.A @ x) <= 1e-14
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_colouring_and_ranks_match_oracle(name):
+    prob, solver, oracle = setup_case(name)
+    np.testing.assert_array_equal(solver.colouring(), oracle.colour)
+    np.testing.assert_array_equal(solver.coarse_offsets(), oracle.coarse_offsets)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_correction_matches_oracle(name):
+    prob, solver, oracle = setup_case(name)
+    solver.set_precision("fp64")
+    r = np.random.default_rng(6).standard_normal(prob.n)
+    z = solver.coarse_correction(dev(r)).cpu().numpy()
+    assert rel(z, oracle.coarse_correction(r)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_preconditioner_matches_oracle_fp64(name):
+    prob, solver, oracle = setup_case(name)
+    solver.set_precision("fp64")
+    r = np.random.default_rng(7).standard_normal(prob.n)
+    z = solver.apply(dev(r)).cpu().numpy()
+    assert rel(z, oracle.apply(r)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_24", "biharmonic_64", "varcoef_16"])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 3e-2)])
+def test_preconditioner_reduced_precision(name, prec, tol):
+    prob, solver, oracle = setup_case(name)
+    solver.set_precision(prec)
+    r = np.random.default_rng(8).standard_normal(prob.n)
+    z = solver.apply(dev(r)).cpu().numpy()
+    solver.set_precision("fp64")
+    assert rel(z, oracle.apply(r)) <= tol
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_fp64_matches_oracle(name):
+    prob, solver, oracle = setup_case(name)
+    solver.set_precision("fp64")
+    f = prob.f if prob.f.ndim == 1 else prob.f[:, 0]
+    ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
+    u, iters, relres, st = solver.solve(dev(f), tol=1e-8)
+    assert st == 0
+    assert rel(u.cpu().numpy(), ref.u) <= 1e-10
+    assert abs(iters - ref.iters) <= 1
+    assert relres <= 1e-8
+    hist = solver.history()
+    assert hist.size == iters + 1 and hist[-1] <= 1e-8
+    np.testing.assert_allclose(hist, ref.history[:hist.size], rtol=1e-6)
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_24", "poisson3d_ragged", "biharmonic_64",
+                                  "varcoef_16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_solve_mixed_precision(name, prec):
+    prob, solver, oracle = setup_case(name)
+    f = prob.f if prob.f.ndim == 1 else prob.f[:, 0]
+    ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
+    solver.set_precision(prec)
+    u, iters, relres, st = solver.solve(dev(f), tol=1e-8)
+    solver.set_precision("fp64")
+    assert st == 0
+    un = u.cpu().numpy()
+    true_rel = np.linalg.norm(f - prob.A @ un) / np.linalg.norm(f)
+    assert true_rel <= 1e-8 and relres <= 1e-8
+    assert rel(un, ref.u) <= 1e-7
+    assert iters <= ref.iters + 3
+
+
+def test_solve_host_and_batch_match_device():
+    prob, solver, _ = setup_case("poisson3d_24")
+    solver.set_precision("fp32")
+    F = di.normal_rhs(prob.n, 21, 3)
+    Ub, its, rrs, st = solver.solve_batch(dev(F), tol=1e-9)
+    assert st == 0 and np.all(rrs <= 1e-9)
+    for j in range(3):
+        u, it, rr, st = solver.solve(dev(F[:, j]), tol=1e-9)
+        assert it == its[j]
+        np.testing.assert_array_equal(Ub[:, j].cpu().numpy(), u.cpu().numpy())
+    uh, ith, rrh, sth = solver.solve_host(F[:, 0], tol=1e-9)
+    np.testing.assert_array_equal(uh, Ub[:, 0].cpu().numpy())
+    solver.set_precision("fp64")
+
+
+def test_solve_is_deterministic():
+    prob, solver, _ = setup_case("poisson3d_24")
+    for prec in ("fp64", "fp32", "bf16"):
+        solver.set_precision(prec)
+        a = solver.solve(dev(prob.f), tol=1e-8)[0].cpu().numpy()
+        b = solver.solve(dev(prob.f), tol=1e-8)[0].cpu().numpy()
+        assert np.array_equal(a, b), prec
+    solver.set_precision("fp64")
+
+
+def test_zero_rhs_and_maxit():
+    from paper_1504_00907_gb300 import ddg
+    prob, solver, _ = setup_case("poisson2d_64")
+    u, it, rr, st = solver.solve(dev(np.zeros(prob.n)), tol=1e-8)
+    assert st == 0 and it == 0 and not u.abs().max().item()
+    capped = ddg.Solver.from_problem(prob, maxit=1)
+    u, it, rr, st = capped.solve(dev(prob.f), tol=1e-12)
+    assert st == ddg.DDG_ENOCONV and it == 1 and rr > 1e-12
+    capped.close()
+
+
+def test_not_spd_is_reported_not_faulted():
+    from paper_1504_00907_gb300 import ddg
+    prob = di.make_poisson2d(N=16, box=8, overlap=1, p=1)
+    with pytest.raises(ddg.DDGError) as e:
+        ddg.Solver(-prob.A, prob.part, prob.F, 1, mode="box", shape=prob.shape)
+    assert e.value.status == ddg.DDG_ENOTSPD
+
+
+def test_coarse_reproduces_generators_any_size():
+    # F restricted to each subdomain spans part of the coarse space, so the
+    # coarse correction reproduces every generator column exactly.
+    prob, solver, _ = setup_case("poisson3d_24")
+    solver.set_precision("fp64")
+    for j in (0, 4, 9):
+        Fj = prob.F[:, j]
+        z = solver.coarse_correction(dev(prob.A @ Fj)).cpu().numpy()
+        assert rel(z, Fj) <= 1e-10
