@@ -45,12 +45,14 @@ SAMPLE_N = 48   # CPU oracle sample: same H/h, overlap and p on a 48^3 grid
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=WORKLOAD["N"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--keep", default="fp64,fp32,bf16",
+                    help="local-inverse precisions kept at setup (profiling runs keep fewer)")
     return ap.parse_args()
 
 
@@ -75,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -212,7 +214,8 @@ def main():
                              seed=WORKLOAD["seed"])
     n = prob.n
     t_setup = time.perf_counter()
-    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32", "bf16"))
+    keep = tuple(args.keep.split(","))
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=keep)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     info = solver.info()
@@ -249,10 +252,27 @@ def main():
     ms32, it32, rr32, st32, clk = timed_solves("fp32", args.steps, args.warmup, ("local_solve",))
     ms32 = max_over_ranks(ms32)
     # comparison arms on the same problem
-    ms64, it64, rr64, _, clk64 = timed_solves("fp64", args.fp64_steps, 1)
-    ms64 = max_over_ranks(ms64)
-    ms16, it16, rr16, _, _ = timed_solves("bf16", args.steps, 1)
-    ms16 = max_over_ranks(ms16)
+    ms64 = ms16 = float("nan")
+    it64 = it16 = rr64 = rr16 = [None]
+    if "fp64" in keep:
+        ms64, it64, rr64, _, clk64 = timed_solves("fp64", args.fp64_steps, 1)
+        ms64 = max_over_ranks(ms64)
+    if "bf16" in keep:
+        ms16, it16, rr16, _, _ = timed_solves("bf16", args.steps, 1)
+        ms16 = max_over_ranks(ms16)
+
+    # per-class breakdown of one extra mixed solve with every class event-timed
+    solver.set_precision("fp32")
+    solver.profile(ddg.KERNEL_CLASSES)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.solve(f, TOL, u)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof_total = e0.elapsed_time(e1)
+    breakdown = {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in solver.kernel_stats().items()}
+    breakdown["untimed_gaps_ms"] = prof_total - sum(v["ms"] for v in breakdown.values())
+    breakdown["solve_ms_with_events"] = prof_total
 
     # end to end through the host-buffer entry point (copies in the timed region)
     solver.set_precision("fp32")
@@ -299,8 +319,9 @@ def main():
         "time_to_1e-8_s": {"mixed_fp32": ms32 / 1e3, "fp64_plain": ms64 / 1e3, "mixed_bf16": ms16 / 1e3},
         "iters": {"mixed_fp32": it32[-1], "fp64_plain": it64[-1], "mixed_bf16": it16[-1]},
         "true_relres": {"mixed_fp32": rr32[-1], "fp64_plain": rr64[-1], "mixed_bf16": rr16[-1]},
-        "dof_iters_per_s": {"mixed_fp32": value, "fp64_plain": world * n * it64[-1] / (ms64 / 1e3),
-                            "mixed_bf16": world * n * it16[-1] / (ms16 / 1e3)},
+        "dof_iters_per_s": {"mixed_fp32": value,
+                            "fp64_plain": world * n * it64[-1] / (ms64 / 1e3) if it64[-1] else None,
+                            "mixed_bf16": world * n * it16[-1] / (ms16 / 1e3) if it16[-1] else None},
         "speedup_mixed_vs_fp64": ms64 / ms32,
         "setup_s": setup_s, "setup_ms_library": info["setup_ms"],
         "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -308,6 +329,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n, "api": "ddg_solve_host"},
         "roofline": roofline,
+        "breakdown_one_mixed_solve": breakdown,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

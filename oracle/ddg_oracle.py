@@ -390,11 +390,6 @@ def lanczos_extremes(alphas, betas):
     return float(w[0]), float(w[-1])
 
 
-def cg_iteration_bound(kappa, tol):
-    """Classical CG bound: iterations <= ceil(sqrt(kappa)/2 * ln(2/tol))."""
-    return int(np.ceil(0.5 * np.sqrt(kappa) * np.log(2.0 / tol)))
-
-
 def solve(A, part, F, f, overlap, mode="graph", shape=None, tol=1e-8, maxit=1000, beta="FR"):
     """Setup plus PCG in one call; returns (PCGResult, DDGOracle)."""
     M = DDGOracle(A, part, F, overlap, mode, shape)

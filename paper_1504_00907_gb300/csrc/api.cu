@@ -535,8 +535,13 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         {
             const size_t Np = (size_t)h->Tmax * DDG_LT;
             const size_t per = Np * Np * sizeof(double);
-            const size_t budget = (size_t)6 << 30;
-            const int nb = (int)std::max<size_t>(1, std::min<size_t>((size_t)nsub, budget / per));
+            // chunks of whole waves (a multiple of the SM count), about 3 GB of workspace
+            int dev = 0, sms = 1;
+            DDG_CUDA(cudaGetDevice(&dev));
+            DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            const size_t budget = (size_t)3 << 30;
+            size_t waves = std::max<size_t>(1, budget / (per * (size_t)sms));
+            const int nb = (int)std::min<size_t>((size_t)nsub, waves * (size_t)sms);
             double* ws = h->arena.alloc<double>((size_t)nb * Np * Np);
             double* invdiag = h->arena.alloc<double>((size_t)nb * h->Tmax * DDG_LT * DDG_LT);
             for (int q0 = 0; q0 < nsub; q0 += nb) {
