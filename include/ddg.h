@@ -18,7 +18,8 @@
  * Conventions for every entry point:
  *   - Every call returns a ddg_status; nothing throws across the ABI.
  *     ddg_last_error(h) gives a message for the last failing call on h
- *     (ddg_last_error(NULL) for a failing ddg_setup).
+ *     (ddg_last_error(NULL) for a failing ddg_setup or a failing call that
+ *     takes no handle).
  *   - "host" pointers are read during the call only and stay owned by the
  *     caller.  "device" pointers are caller-owned CUDA device memory on the
  *     current device; the library never frees them.  All device work is
@@ -212,6 +213,30 @@ typedef struct {
 ddg_status ddg_profile(ddg_handle h, int timed_mask);
 /* stats: host ddg_kernel_stat[DDG_K_COUNT]; synchronises the stream. */
 ddg_status ddg_get_kernel_stats(ddg_handle h, ddg_kernel_stat* stats);
+
+/* ---- no-allocation entry point (the paper has no counterpart) ----
+ * y = A x and xAx = x^T A x for a caller-owned FP64 CSR matrix, without a
+ * handle and without allocating device memory: for callers that cannot call
+ * cudaMalloc (a host framework's caching allocator owns the device memory, a
+ * fixed memory budget set at start-up, a caller inside another library's
+ * critical section).  Same arithmetic as the library's CSR SpMV with the
+ * fused dot of the CG recurrence (deterministic block-order reduction).
+ *   n       rows, 0 <= n <= DDG_NOALLOC_MAX_ROWS, else DDG_EINVAL
+ *   rowptr, col, val, x   device inputs (int64 [n+1], int32 [nnz], FP64 [nnz], FP64 [n])
+ *   y       device output FP64 [n];  xAx  device output, one FP64
+ *   stream  cudaStream_t (NULL = default stream)
+ * Scratch: one file-scope static device array (32 KB of block partial sums
+ * plus a ticket counter) that every GPU loading the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (which may load the module): make that first call before any
+ * stream capture.  All calls share the array, so calls whose kernels
+ * overlap on the GPU (different streams, different threads) race; each call
+ * clears the ticket it needs at zero on its stream.  Errors: DDG_EINVAL (size
+ * or null pointer), DDG_ECUDA; the message is in ddg_last_error(NULL). */
+#define DDG_NOALLOC_MAX_ROWS 1048576
+ddg_status ddg_spmv_dot_noalloc(int64_t n, const int64_t* rowptr, const int32_t* col,
+                                const double* val, const double* x, double* y, double* xAx,
+                                void* stream);
 
 ddg_status ddg_destroy(ddg_handle h);
 const char* ddg_last_error(ddg_handle h);

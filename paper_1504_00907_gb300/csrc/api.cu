@@ -317,6 +317,11 @@ ddg_status guarded(ddg_handle h, Fn&& fn) {
 
 }  // namespace
 
+namespace ddg {
+// message for ddg_last_error(NULL) from calls that have no handle
+void set_handleless_error(const char* msg) { g_setup_error = msg ? msg : ""; }
+}  // namespace ddg
+
 ProfScope::ProfScope(ddg_handle hh, int c, int nlaunch, double bytes) : h(hh), cls(c), pair(-1) {
     h->prof_launches[c] += nlaunch;
     if (!(h->prof_mask & (1 << c))) return;

@@ -259,4 +259,7 @@ void strided_gather(ddg_handle h, const double* src, int m, int j, double* dst);
 void strided_scatter(ddg_handle h, const double* src, int m, int j, double* dst);
 void cast_q32(ddg_handle h);
 
+// api.cu: error message of a handle-less call, read by ddg_last_error(NULL)
+void set_handleless_error(const char* msg);
+
 }  // namespace ddg

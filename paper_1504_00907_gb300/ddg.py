@@ -85,6 +85,7 @@ _SIGS = {
     "ddg_get_history": (_I, [_P, _P, _I, _PI]),
     "ddg_profile": (_I, [_P, _I]),
     "ddg_get_kernel_stats": (_I, [_P, _P]),
+    "ddg_spmv_dot_noalloc": (_I, [ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P]),
     "ddg_destroy": (_I, [_P]),
     "ddg_last_error": (ctypes.c_char_p, [_P]),
     "ddg_status_string": (ctypes.c_char_p, [_I]),
