@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -189,6 +190,51 @@ void apply_prec(ddg_handle h, const double* rin) {
     for (int c = h->ncol - 1; c >= 0; --c) local_step(h, c, false, prec);
 }
 
+// The preconditioner of the PCG loop always reads h->r, so its launch
+// sequence is fixed per precision: capture it once into a CUDA graph (on a
+// private non-blocking stream: the caller's stream may be the legacy default
+// stream, which cannot be captured) and replay it on the caller's stream.
+// Per-kernel event timing (ddg_profile) needs the individual launches, so it
+// bypasses the graph.
+void apply_in_pcg(ddg_handle h) {
+    const int p = h->precision;
+    if (!h->use_graphs || h->prof_mask != 0) {
+        apply_prec(h, h->r);
+        return;
+    }
+    if (!h->apply_exec[p]) {
+        if (!h->cap_stream) DDG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        int64_t saved_counts[DDG_K_COUNT];
+        for (int c = 0; c < DDG_K_COUNT; ++c) saved_counts[c] = h->prof_launches[c];
+        cudaStream_t saved = h->stream;
+        // order the capture after earlier work of the handle
+        DDG_CUDA(cudaStreamSynchronize(saved));
+        h->stream = h->cap_stream;
+        DDG_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        try {
+            apply_prec(h, h->r);
+        } catch (...) {
+            cudaStreamEndCapture(h->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            h->stream = saved;
+            throw;
+        }
+        const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        h->stream = saved;
+        DDG_CUDA(e);
+        const cudaError_t ei = cudaGraphInstantiate(&h->apply_exec[p], g, 0);
+        cudaGraphDestroy(g);
+        DDG_CUDA(ei);
+        for (int c = 0; c < DDG_K_COUNT; ++c) {
+            h->apply_launches[p][c] = h->prof_launches[c] - saved_counts[c];
+            h->prof_launches[c] = saved_counts[c];
+        }
+    }
+    DDG_CUDA(cudaGraphLaunch(h->apply_exec[p], h->stream));
+    for (int c = 0; c < DDG_K_COUNT; ++c) h->prof_launches[c] += h->apply_launches[p][c];
+}
+
 void read_scalars(ddg_handle h) {
     d2h(h->h_scal, h->scal, S_COUNT, h->stream);
     DDG_CUDA(cudaStreamSynchronize(h->stream));
@@ -223,7 +269,7 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
     }
     DDG_CUDA(cudaMemcpyAsync(h->r, f, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     auto restart = [&]() {
-        apply_prec(h, h->r);
+        apply_in_pcg(h);
         ProfScope ps(h, DDG_K_CG, 2, 0.0);
         ddg::cg_dots_after_precond(h, prec, true, pr);
         ddg::cg_update_p(h, prec, true);
@@ -269,7 +315,7 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
             true_rel = -1.0;
             continue;
         }
-        apply_prec(h, h->r);
+        apply_in_pcg(h);
         ProfScope ps(h, DDG_K_CG, 2, 0.0);
         ddg::cg_dots_after_precond(h, prec, false, pr);
         ddg::cg_update_p(h, prec, false);
@@ -378,6 +424,7 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         validate(A, partition, F, k, overlap, o);
         h->opt = o;
         h->precision = o.precision;
+        if (const char* ev = std::getenv("DDG_NO_GRAPHS")) h->use_graphs = ev[0] == '0';
         h->use_coarse = o.use_coarse;
         h->stream = (cudaStream_t)stream;
         const int64_t n = A->n;
@@ -866,6 +913,9 @@ ddg_status ddg_destroy(ddg_handle h) {
     if (!h) return DDG_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : h->apply_exec)
+        if (g) cudaGraphExecDestroy(g);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->arena.free_all();
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete h;

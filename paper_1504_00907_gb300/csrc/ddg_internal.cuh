@@ -200,6 +200,12 @@ struct ddg_handle_s {
     int32_t* errflags = nullptr;
     std::vector<double> history;
 
+    // ---- CUDA graphs of the preconditioner apply inside PCG (one per precision)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t apply_exec[3] = {nullptr, nullptr, nullptr};
+    int64_t apply_launches[3][DDG_K_COUNT] = {};
+    bool use_graphs = true;
+
     // ---- tracing (ddg_profile)
     int prof_mask = 0;
     int64_t prof_launches[DDG_K_COUNT] = {0};

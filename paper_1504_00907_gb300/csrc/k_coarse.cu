@@ -354,26 +354,30 @@ __global__ void __launch_bounds__(256) superblock_inverse_kernel(const double* b
 enum { PM_D = 0, PM_E = 1, PM_DT = 2, PM_ET = 3 };
 
 template <int KIND>
-__global__ void profile_fill_kernel(ProfileMat M, int rows, const double* band, const double* W,
-                                    int Wt, int B) {
+__global__ void profile_fill_kernel(ProfileMat M, const int32_t* __restrict__ vlo,
+                                    const int32_t* __restrict__ vhi, int rows, const double* band,
+                                    const double* W, int Wt, int B) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (wid >= rows) return;
     const int i = wid;
-    const int lo = M.lo[i], hi = M.hi[i];
+    const int lo = M.lo[i], hi = M.hi[i];          // stored range (multiples of 4)
+    const int tlo = vlo[i], thi = vhi[i];          // true nonzero range
     const int64_t rp = M.rowptr[i];
     const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
     for (int jc = lo + lane; jc < hi; jc += 32) {
-        double v;
-        if (KIND == PM_D || KIND == PM_DT) {
-            // D[a][b] with a >= b in super-block K: row-major W tiles
-            const int a = KIND == PM_D ? i : jc, b = KIND == PM_D ? jc : i;
-            const int K = a / B, la = a - K * B, lb = b - K * B;
-            const int ti = la / CT, tj = lb / CT;
-            v = W[((size_t)K * Ptiles + (size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (la % CT) * CT + (lb % CT)];
-        } else {
-            // E[a][b] = L[a][b] with a in super-block K, b in K-1
-            const int a = KIND == PM_E ? i : jc, b = KIND == PM_E ? jc : i;
-            v = band[band_index(a, b, Wt)];
+        double v = 0.0;
+        if (jc >= tlo && jc < thi) {
+            if (KIND == PM_D || KIND == PM_DT) {
+                // D[a][b] with a >= b in super-block K: row-major W tiles
+                const int a = KIND == PM_D ? i : jc, b = KIND == PM_D ? jc : i;
+                const int K = a / B, la = a - K * B, lb = b - K * B;
+                const int ti = la / CT, tj = lb / CT;
+                v = W[((size_t)K * Ptiles + (size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (la % CT) * CT + (lb % CT)];
+            } else {
+                // E[a][b] = L[a][b] with a in super-block K, b in K-1
+                const int a = KIND == PM_E ? i : jc, b = KIND == PM_E ? jc : i;
+                v = band[band_index(a, b, Wt)];
+            }
         }
         M.v64[rp + (jc - lo)] = v;
         if (M.v32) M.v32[rp + (jc - lo)] = (float)v;
@@ -381,30 +385,62 @@ __global__ void profile_fill_kernel(ProfileMat M, int rows, const double* band, 
 }
 
 // ---------------------------------------------------------------- apply
-// out[i] = (a ? a[i] : 0) + sign * sum_{j in [lo_i, hi_i)} M[i][j] x[j], one warp per row
+// out[i] = (a ? a[i] : 0) + sign * sum_{j in [lo_i, hi_i)} M[i][j] x[j], one warp
+// per row.  Rows are stored on 4-aligned column ranges (zero padded), so each
+// lane streams 16-byte chunks of the row and of x.
+template <typename V> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ float dot(const float* m, const float* x) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(m));
+        const float4 b = *reinterpret_cast<const float4*>(x);
+        return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+    }
+};
+template <> struct Vec4<double> {
+    static __device__ __forceinline__ double dot(const double* m, const double* x) {
+        const double2 a0 = __ldcs(reinterpret_cast<const double2*>(m));
+        const double2 a1 = __ldcs(reinterpret_cast<const double2*>(m + 2));
+        const double2 b0 = *reinterpret_cast<const double2*>(x);
+        const double2 b1 = *reinterpret_cast<const double2*>(x + 2);
+        return a0.x * b0.x + a0.y * b0.y + a1.x * b1.x + a1.y * b1.y;
+    }
+};
+
+constexpr int GEMV_TPR = 128;   // threads per row: a whole row's loads in flight
+
 template <typename V, typename MV>
-__global__ void profile_gemv_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lo,
-                                    const int32_t* __restrict__ hi, const MV* __restrict__ vals,
-                                    int r0, int r1, const V* __restrict__ x, const V* __restrict__ a,
-                                    V sign, V* __restrict__ out) {
-    const int i = r0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= r1) return;
-    const int l = lo[i], hgh = hi[i];
-    const MV* rv = vals + rowptr[i] - l;
+__global__ void __launch_bounds__(GEMV_TPR) profile_gemv_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+    const MV* __restrict__ vals, int r0, const V* __restrict__ x, const V* __restrict__ a, V sign,
+    V* __restrict__ out) {
+    __shared__ V sh[GEMV_TPR / 32];
+    const int i = r0 + blockIdx.x;
+    const int l = lo[i];
+    const int nch = (hi[i] - l) >> 2;
+    const MV* rv = vals + rowptr[i];
+    const V* xv = x + l;
     V s = 0;
-    for (int j = l + lane; j < hgh; j += 32) s = fma((V)__ldcs(rv + j), x[j], s);
+#pragma unroll 4
+    for (int c = threadIdx.x; c < nch; c += GEMV_TPR) s += Vec4<V>::dot(rv + 4 * c, xv + 4 * c);
     s = ddgdev::warp_sum(s);
-    if (lane == 0) out[i] = (a ? a[i] : (V)0) + sign * s;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        V t = 0;
+#pragma unroll
+        for (int w = 0; w < GEMV_TPR / 32; ++w) t += sh[w];
+        out[i] = (a ? a[i] : (V)0) + sign * t;
+    }
 }
 
-// c[coff_s + j] = sum_{g in Omega_s} Q[g, j] (r - A z)[g]   (z = 0 skips A z)
-template <typename V, typename AV>
+// c[coff_s + j] = sum_{g in Omega_s} Q[g, j] (r - A z)[g]   (z = 0 skips A z);
+// the residual is matrix-free for the constant-coefficient Laplacians
+template <int SK, typename V, typename AV>
 __global__ void __launch_bounds__(256) coarse_restrict_kernel(
     const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const AV* __restrict__ val,
     const V* __restrict__ r, const V* __restrict__ z, const V* __restrict__ Q, int kmax,
-    const int32_t* __restrict__ coff, V* __restrict__ c, int residual) {
+    const int32_t* __restrict__ coff, V* __restrict__ c, int residual, int nx, int ny, int nz) {
     __shared__ V red[32 * 8];
     __shared__ V out[32];
     const int s = blockIdx.x;
@@ -414,8 +450,24 @@ __global__ void __launch_bounds__(256) coarse_restrict_kernel(
     for (int64_t a = sub_off[s] + threadIdx.x; a < sub_off[s + 1]; a += blockDim.x) {
         const int g = sub_nodes[a];
         V w = r[g];
-        if (residual)
-            for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) w -= (V)val[e] * z[col[e]];
+        if (residual) {
+            if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+                const int i = g % nx, jj = (g / nx) % ny;
+                V az = (SK == DDG_STENCIL_7PT_3D ? (V)6 : (V)4) * z[g];
+                if (i > 0) az -= z[g - 1];
+                if (i < nx - 1) az -= z[g + 1];
+                if (jj > 0) az -= z[g - nx];
+                if (jj < ny - 1) az -= z[g + nx];
+                if (SK == DDG_STENCIL_7PT_3D) {
+                    const int k = g / (nx * ny);
+                    if (k > 0) az -= z[g - nx * ny];
+                    if (k < nz - 1) az -= z[g + nx * ny];
+                }
+                w -= az;
+            } else {
+                for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) w -= (V)val[e] * z[col[e]];
+            }
+        }
         const V* qa = Q + a * kmax;
 #pragma unroll
         for (int j = 0; j < 32; ++j)
@@ -506,20 +558,35 @@ void coarse_band_cholesky(ddg_handle h) {
     h->arena.release(dinv);
 }
 
+// Rows are stored on [lo & ~3, (hi + 3) & ~3) so that every row starts on a
+// 16-byte boundary; returns the true ranges (device) for the fill kernel.
 static void alloc_profile(ddg_handle h, ProfileMat& M, const std::vector<int>& lo,
-                          const std::vector<int>& hi, bool fp32) {
+                          const std::vector<int>& hi, bool fp32, int32_t** vlo, int32_t** vhi) {
     const int rows = (int)lo.size();
+    std::vector<int> lo4(rows), hi4(rows);
     std::vector<int64_t> rp(rows + 1, 0);
-    for (int i = 0; i < rows; ++i) rp[i + 1] = rp[i] + std::max(0, hi[i] - lo[i]);
+    for (int i = 0; i < rows; ++i) {
+        if (hi[i] > lo[i]) {
+            lo4[i] = lo[i] & ~3;
+            hi4[i] = (hi[i] + 3) & ~3;
+        } else {
+            lo4[i] = hi4[i] = 0;
+        }
+        rp[i + 1] = rp[i] + (hi4[i] - lo4[i]);
+    }
     M.nnz = rp[rows];
     M.rowptr = h->arena.alloc<int64_t>(rows + 1);
     M.lo = h->arena.alloc<int32_t>(rows);
     M.hi = h->arena.alloc<int32_t>(rows);
     M.v64 = h->arena.alloc<double>(M.nnz);
     M.v32 = fp32 ? h->arena.alloc<float>(M.nnz) : nullptr;
+    *vlo = h->arena.alloc<int32_t>(rows);
+    *vhi = h->arena.alloc<int32_t>(rows);
     h2d(M.rowptr, rp.data(), rows + 1, h->stream);
-    h2d(M.lo, lo.data(), rows, h->stream);
-    h2d(M.hi, hi.data(), rows, h->stream);
+    h2d(M.lo, lo4.data(), rows, h->stream);
+    h2d(M.hi, hi4.data(), rows, h->stream);
+    h2d(*vlo, lo.data(), rows, h->stream);
+    h2d(*vhi, hi.data(), rows, h->stream);
     DDG_CUDA(cudaStreamSynchronize(h->stream));
 }
 
@@ -527,12 +594,13 @@ void coarse_build_apply(ddg_handle h) {
     const int n0p = h->n0p, B = h->B, Wt = h->Wt, nK = h->nK;
     const bool fp32 = true;
     std::vector<int> lo(n0p), hi(n0p);
+    int32_t *vlo[4], *vhi[4];
     // D: lower triangle of the super-block
     for (int i = 0; i < n0p; ++i) {
         lo[i] = (i / B) * B;
         hi[i] = i + 1;
     }
-    alloc_profile(h, h->Dm, lo, hi, fp32);
+    alloc_profile(h, h->Dm, lo, hi, fp32, &vlo[0], &vhi[0]);
     // E: columns of super-block K-1 inside the tile band
     for (int i = 0; i < n0p; ++i) {
         const int K = i / B, R = i / CT;
@@ -543,13 +611,13 @@ void coarse_build_apply(ddg_handle h) {
             hi[i] = K * B;
         }
     }
-    alloc_profile(h, h->Em, lo, hi, fp32);
+    alloc_profile(h, h->Em, lo, hi, fp32, &vlo[1], &vhi[1]);
     // D^T: upper triangle of the super-block
     for (int i = 0; i < n0p; ++i) {
         lo[i] = i;
         hi[i] = (i / B + 1) * B;
     }
-    alloc_profile(h, h->Dt, lo, hi, fp32);
+    alloc_profile(h, h->Dt, lo, hi, fp32, &vlo[2], &vhi[2]);
     // E^T: row j of E_{K+1}^T = column j of E_{K+1}
     for (int j = 0; j < n0p; ++j) {
         const int K = j / B;
@@ -560,44 +628,55 @@ void coarse_build_apply(ddg_handle h) {
             hi[j] = std::min((K + 2) * B, (j / CT + Wt + 1) * CT);
         }
     }
-    alloc_profile(h, h->Et, lo, hi, fp32);
+    alloc_profile(h, h->Et, lo, hi, fp32, &vlo[3], &vhi[3]);
     const unsigned blocks = (unsigned)((n0p * 32 + 255) / 256);
-    profile_fill_kernel<PM_D><<<blocks, 256, 0, h->stream>>>(h->Dm, n0p, h->bandL, h->coarseW, Wt, B);
-    profile_fill_kernel<PM_E><<<blocks, 256, 0, h->stream>>>(h->Em, n0p, h->bandL, h->coarseW, Wt, B);
-    profile_fill_kernel<PM_DT><<<blocks, 256, 0, h->stream>>>(h->Dt, n0p, h->bandL, h->coarseW, Wt, B);
-    profile_fill_kernel<PM_ET><<<blocks, 256, 0, h->stream>>>(h->Et, n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_D><<<blocks, 256, 0, h->stream>>>(h->Dm, vlo[0], vhi[0], n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_E><<<blocks, 256, 0, h->stream>>>(h->Em, vlo[1], vhi[1], n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_DT><<<blocks, 256, 0, h->stream>>>(h->Dt, vlo[2], vhi[2], n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_ET><<<blocks, 256, 0, h->stream>>>(h->Et, vlo[3], vhi[3], n0p, h->bandL, h->coarseW, Wt, B);
     DDG_CHECK_LAUNCH();
     DDG_CUDA(cudaStreamSynchronize(h->stream));
+    for (int t = 0; t < 4; ++t) {
+        h->arena.release(vlo[t]);
+        h->arena.release(vhi[t]);
+    }
     h->arena.release(h->coarseW);
     h->coarseW = nullptr;
     h->arena.release(h->bandL);
     h->bandL = nullptr;
 }
 
-void coarse_restrict(ddg_handle h, int prec, bool residual) {
+template <int SK>
+static void launch_restrict(ddg_handle h, int prec, bool residual) {
     if (prec == DDG_PREC_FP64)
-        coarse_restrict_kernel<double, double><<<h->nsub, 256, 0, h->stream>>>(
+        coarse_restrict_kernel<SK, double, double><<<h->nsub, 256, 0, h->stream>>>(
             h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->Q64,
-            h->kmax, h->coff, h->c64, residual);
+            h->kmax, h->coff, h->c64, residual, h->nx, h->ny, h->nz);
     else
-        coarse_restrict_kernel<float, float><<<h->nsub, 256, 0, h->stream>>>(
+        coarse_restrict_kernel<SK, float, float><<<h->nsub, 256, 0, h->stream>>>(
             h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->Q32, h->kmax,
-            h->coff, h->c32, residual);
+            h->coff, h->c32, residual, h->nx, h->ny, h->nz);
     DDG_CHECK_LAUNCH();
+}
+
+void coarse_restrict(ddg_handle h, int prec, bool residual) {
+    if (h->stencil_kind == DDG_STENCIL_7PT_3D) launch_restrict<DDG_STENCIL_7PT_3D>(h, prec, residual);
+    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) launch_restrict<DDG_STENCIL_5PT_2D>(h, prec, residual);
+    else launch_restrict<DDG_STENCIL_NONE>(h, prec, residual);
 }
 
 template <typename V>
 static void gemv(ddg_handle h, const ProfileMat& M, int r0, int r1, const V* x, const V* a, V sign,
                  V* out) {
     if (r1 <= r0) return;
-    const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * 32 + 255) / 256);
+    const unsigned blocks = (unsigned)(r1 - r0);
     if (sizeof(V) == 8)
-        profile_gemv_kernel<double, double><<<blocks, 256, 0, h->stream>>>(
-            M.rowptr, M.lo, M.hi, M.v64, r0, r1, (const double*)x, (const double*)a, (double)sign,
+        profile_gemv_kernel<double, double><<<blocks, GEMV_TPR, 0, h->stream>>>(
+            M.rowptr, M.lo, M.hi, M.v64, r0, (const double*)x, (const double*)a, (double)sign,
             (double*)out);
     else
-        profile_gemv_kernel<float, float><<<blocks, 256, 0, h->stream>>>(
-            M.rowptr, M.lo, M.hi, M.v32, r0, r1, (const float*)x, (const float*)a, (float)sign,
+        profile_gemv_kernel<float, float><<<blocks, GEMV_TPR, 0, h->stream>>>(
+            M.rowptr, M.lo, M.hi, M.v32, r0, (const float*)x, (const float*)a, (float)sign,
             (float*)out);
     DDG_CHECK_LAUNCH();
 }

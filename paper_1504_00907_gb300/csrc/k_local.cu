@@ -289,20 +289,44 @@ __global__ void local_pack_kernel(int q0, const double* __restrict__ ws, int Np,
 }
 
 // ---------------------------------------------------------------- apply
-template <typename V, typename AV>
+// (r - A z)[g] for grid dof g: CSR rows in general, matrix-free for the
+// constant-coefficient Laplacians ([6,-1] 3D, [4,-1] 2D, Dirichlet)
+template <int SK, typename V, typename AV>
+__device__ __forceinline__ V residual_at(int g, const int64_t* __restrict__ rowptr,
+                                         const int32_t* __restrict__ col, const AV* __restrict__ val,
+                                         const V* __restrict__ r, const V* __restrict__ z, int nx,
+                                         int ny, int nz) {
+    V s = r[g];
+    if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+        const int i = g % nx, j = (g / nx) % ny;
+        V az = (SK == DDG_STENCIL_7PT_3D ? (V)6 : (V)4) * z[g];
+        if (i > 0) az -= z[g - 1];
+        if (i < nx - 1) az -= z[g + 1];
+        if (j > 0) az -= z[g - nx];
+        if (j < ny - 1) az -= z[g + nx];
+        if (SK == DDG_STENCIL_7PT_3D) {
+            const int k = g / (nx * ny);
+            if (k > 0) az -= z[g - nx * ny];
+            if (k < nz - 1) az -= z[g + nx * ny];
+        }
+        s -= az;
+    } else {
+        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s -= (V)val[e] * z[col[e]];
+    }
+    return s;
+}
+
+template <int SK, typename V, typename AV>
 __global__ void local_residual_kernel(int64_t a0, int64_t a1, const int32_t* __restrict__ ov_nodes,
                                       const int64_t* __restrict__ rowptr,
                                       const int32_t* __restrict__ col,
                                       const AV* __restrict__ val, const V* __restrict__ r,
-                                      const V* __restrict__ z, V* __restrict__ res, int z_zero) {
+                                      const V* __restrict__ z, V* __restrict__ res, int z_zero,
+                                      int nx, int ny, int nz) {
     const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= a1) return;
     const int g = ov_nodes[a];
-    V s = r[g];
-    if (!z_zero) {
-        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s -= (V)val[e] * z[col[e]];
-    }
-    res[a] = s;
+    res[a] = z_zero ? r[g] : residual_at<SK>(g, rowptr, col, val, r, z, nx, ny, nz);
 }
 
 // lane layout of a 32x32 tile for 16-byte loads of element type E:
@@ -480,19 +504,27 @@ void local_pack(ddg_handle h, int q0, int q1, const double* ws) {
     DDG_CHECK_LAUNCH();
 }
 
+template <int SK>
+static void launch_residual(ddg_handle h, int64_t a0, int64_t a1, bool z_zero, int prec) {
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((a1 - a0 + threads - 1) / threads);
+    if (prec == DDG_PREC_FP64)
+        local_residual_kernel<SK, double, double><<<blocks, threads, 0, h->stream>>>(
+            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->res64, z_zero,
+            h->nx, h->ny, h->nz);
+    else
+        local_residual_kernel<SK, float, float><<<blocks, threads, 0, h->stream>>>(
+            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->res32, z_zero,
+            h->nx, h->ny, h->nz);
+    DDG_CHECK_LAUNCH();
+}
+
 void local_residual(ddg_handle h, int c, bool z_zero, int prec) {
     const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
     if (a1 <= a0) return;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)((a1 - a0 + threads - 1) / threads);
-    if (prec == DDG_PREC_FP64) {
-        local_residual_kernel<double, double><<<blocks, threads, 0, h->stream>>>(
-            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->res64, z_zero);
-    } else {
-        local_residual_kernel<float, float><<<blocks, threads, 0, h->stream>>>(
-            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->res32, z_zero);
-    }
-    DDG_CHECK_LAUNCH();
+    if (h->stencil_kind == DDG_STENCIL_7PT_3D) launch_residual<DDG_STENCIL_7PT_3D>(h, a0, a1, z_zero, prec);
+    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) launch_residual<DDG_STENCIL_5PT_2D>(h, a0, a1, z_zero, prec);
+    else launch_residual<DDG_STENCIL_NONE>(h, a0, a1, z_zero, prec);
 }
 
 template <typename E, typename V>
