@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--size", type=int, default=WORKLOAD["N"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-size", type=int, default=96,
+                    help="grid of the multi-RHS arm (0 skips it)")
+    ap.add_argument("--batched-m", type=int, default=64)
     ap.add_argument("--keep", default="fp64,fp32,bf16",
                     help="local-inverse precisions kept at setup (profiling runs keep fewer)")
     return ap.parse_args()
@@ -174,6 +177,50 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
+
+
+def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
+    """Many right-hand sides in one batched solve: 3D variable-coefficient
+    diffusion (cell-centred, kappa = exp(GRF, length 0.1, sigma 1)), 12^3 boxes
+    of 8^3 + overlap 1, p <= 2, m right-hand sides ~ N(0, 1), FP32
+    preconditioner with per-column FP64 CG; compared with the same columns
+    solved one at a time."""
+    N, m = args.batched_size, args.batched_m
+    prob = di.make_varcoef3d(N=N, box=8, overlap=1, p=2, m=m)
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32", "bf16"))
+    F = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    out = {"workload": f"varcoef3d_{N}^3, {m} right-hand sides", "dofs": prob.n, "m": m}
+    for prec in ("fp32", "bf16"):
+        solver.set_precision(prec)
+        solver.solve_batch(F, TOL)            # warm-up (allocates the batch workspace)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U, its, rrs, st = solver.solve_batch(F, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        out[prec] = {"ms": ms, "status": int(st), "iters_mean": float(its.mean()),
+                     "iters_max": int(its.max()), "max_true_relres": float(rrs.max()),
+                     "dof_iters_per_s": world * prob.n * float(its.sum()) / (ms / 1e3)}
+    # the first few columns one at a time, same precision
+    solver.set_precision("fp32")
+    k1 = min(4, m)
+    cols = [F[:, j].contiguous() for j in range(k1)]
+    solver.solve(cols[0], TOL)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tot_it = 0
+    for c in cols:
+        tot_it += solver.solve(c, TOL)[1]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    out["single_rhs_fp32"] = {"ms_per_rhs": ms1 / k1, "dof_iters_per_s": prob.n * tot_it / (ms1 / 1e3)}
+    solver.close()
+    return out
 
 
 def main():
@@ -312,6 +359,10 @@ def main():
                 "region": "second timed region of the same solves with an event pair per "
                           "local-solve launch (graph replay off there)"}
 
+    batched = None
+    if args.batched_size > 0:
+        batched = batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
@@ -336,6 +387,7 @@ def main():
                 "d2h_bytes_per_step": 8 * n, "api": "ddg_solve_host"},
         "roofline": roofline,
         "breakdown_one_mixed_solve": breakdown,
+        "batched": batched,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

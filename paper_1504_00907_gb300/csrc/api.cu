@@ -346,6 +346,140 @@ void prof_flush(ddg_handle h) {
     h->ev_used = 0;
 }
 
+// Batched PCG on an n x m block (m <= DDG_MCHUNK), FP32/BF16 preconditioner:
+// every column runs its own CG (alpha, beta, convergence, restarts); the
+// preconditioner is applied to all columns at once.
+ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol, int* iters,
+                     double* relres) {
+    ddg::multi_ensure(h, m);
+    MultiWork& w = h->mw;
+    const int64_t n = h->n;
+    const int beta = h->opt.beta == DDG_BETA_AUTO ? DDG_BETA_PR : h->opt.beta;
+    const int pr = beta == DDG_BETA_PR;
+    std::vector<double> sc(S_COUNT * DDG_MCHUNK);
+    auto read_sc = [&]() {
+        d2h(sc.data(), w.scal, sc.size(), h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+    };
+    auto at = [&](int slot, int c) { return sc[slot * DDG_MCHUNK + c]; };
+    DDG_CUDA(cudaMemsetAsync(w.scal, 0, S_COUNT * DDG_MCHUNK * sizeof(double), h->stream));
+    ddg::multi_resnorm(h, m, F, nullptr, nullptr, S_TMP);
+    read_sc();
+    std::vector<double> fn(m);
+    std::vector<int> active(DDG_MCHUNK, 0), restart(DDG_MCHUNK, 0), nrest(m, 0), done_it(m, -1);
+    std::vector<double> done_rel(m, -1.0);
+    std::vector<ddg_status> st(m, DDG_OK);
+    for (int j = 0; j < m; ++j) {
+        fn[j] = std::sqrt(at(S_TMP, j));
+        active[j] = fn[j] > 0.0;
+        restart[j] = 1;
+        if (!active[j]) {
+            done_it[j] = 0;
+            done_rel[j] = 0.0;
+        }
+    }
+    DDG_CUDA(cudaMemsetAsync(U, 0, n * m * sizeof(double), h->stream));
+    DDG_CUDA(cudaMemsetAsync(w.P, 0, n * m * sizeof(double), h->stream));
+    DDG_CUDA(cudaMemcpyAsync(w.R, F, n * m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    auto upload = [&]() {
+        h2d(w.active, active.data(), DDG_MCHUNK, h->stream);
+        h2d(w.restart, restart.data(), DDG_MCHUNK, h->stream);
+    };
+    upload();
+    auto precond_and_p = [&]() {
+        {
+            ProfScope ps(h, DDG_K_LOCAL_SOLVE, 1, 0.0);
+            ddg::multi_apply(h, m);
+        }
+        ProfScope ps(h, DDG_K_CG, 2, 0.0);
+        ddg::multi_dots(h, m, pr);
+        ddg::multi_update_p(h, m);
+    };
+    precond_and_p();
+    std::fill(restart.begin(), restart.end(), 0);
+    upload();
+    int it = 0;
+    auto any_active = [&]() {
+        for (int j = 0; j < m; ++j)
+            if (active[j]) return true;
+        return false;
+    };
+    while (any_active() && it < h->opt.maxit) {
+        {
+            ProfScope ps(h, DDG_K_SPMV, 1, 0.0);
+            ddg::multi_spmv_pq(h, m);
+        }
+        {
+            ProfScope ps(h, DDG_K_CG, 1, 0.0);
+            ddg::multi_update_ur(h, m, U);
+        }
+        read_sc();
+        ++it;
+        bool candidates = false;
+        for (int j = 0; j < m; ++j) {
+            if (!active[j]) continue;
+            if (at(S_FLAG, j) != 0.0) {
+                st[j] = DDG_EBREAKDOWN;
+                active[j] = 0;
+                done_it[j] = it;
+                continue;
+            }
+            if (std::sqrt(at(S_RR, j)) / fn[j] <= tol) candidates = true;
+        }
+        bool any_restart = false;
+        if (candidates) {
+            ProfScope ps(h, DDG_K_CG, 1, 0.0);
+            ddg::multi_resnorm(h, m, F, U, w.T, S_TMP);
+            read_sc();
+            for (int j = 0; j < m; ++j) {
+                if (!active[j] || std::sqrt(at(S_RR, j)) / fn[j] > tol) continue;
+                const double trel = std::sqrt(at(S_TMP, j)) / fn[j];
+                if (trel <= tol || nrest[j] >= 3) {
+                    active[j] = 0;
+                    done_it[j] = it;
+                    done_rel[j] = trel;
+                    st[j] = trel <= tol ? DDG_OK : DDG_ENOCONV;
+                } else {
+                    restart[j] = 1;
+                    ++nrest[j];
+                    any_restart = true;
+                }
+            }
+            upload();
+            if (any_restart) ddg::multi_replace_cols(h, m, w.T, w.R, w.restart);
+        }
+        if (!any_active()) break;
+        precond_and_p();
+        if (any_restart) {
+            std::fill(restart.begin(), restart.end(), 0);
+            upload();
+        }
+    }
+    // columns still running hit maxit: report their true residual
+    bool unfinished = false;
+    for (int j = 0; j < m; ++j)
+        if (done_rel[j] < 0.0) unfinished = true;
+    if (unfinished) {
+        ddg::multi_resnorm(h, m, F, U, nullptr, S_TMP);
+        read_sc();
+        for (int j = 0; j < m; ++j)
+            if (done_rel[j] < 0.0) {
+                done_rel[j] = std::sqrt(at(S_TMP, j)) / fn[j];
+                if (done_it[j] < 0) {
+                    done_it[j] = it;
+                    st[j] = DDG_ENOCONV;
+                }
+            }
+    }
+    ddg_status worst = DDG_OK;
+    for (int j = 0; j < m; ++j) {
+        if (iters) iters[j] = done_it[j];
+        if (relres) relres[j] = done_rel[j];
+        if (st[j] != DDG_OK && worst == DDG_OK) worst = st[j];
+    }
+    return worst;
+}
+
 template <typename Fn>
 ddg_status guarded(ddg_handle h, Fn&& fn) {
     if (!h) return DDG_EINVAL;
@@ -745,16 +879,33 @@ ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, doub
                            double* relres) {
     return guarded(h, [&]() {
         DDG_REQUIRE(F && U && m >= 1, DDG_EINVAL, "F, U must be non-null and m >= 1");
+        DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
         ddg_status worst = DDG_OK;
-        for (int j = 0; j < m; ++j) {
-            ddg::strided_gather(h, F, m, j, h->fbuf);
-            int it = 0;
-            double rr = 0.0;
-            const ddg_status st = pcg(h, h->fbuf, h->ubuf, tol, &it, &rr);
-            ddg::strided_scatter(h, h->ubuf, m, j, U);
-            if (iters) iters[j] = it;
-            if (relres) relres[j] = rr;
-            if (st != DDG_OK && worst == DDG_OK) worst = st;
+        if (h->precision == DDG_PREC_FP64) {
+            // the FP64 preconditioner runs one column at a time
+            for (int j = 0; j < m; ++j) {
+                ddg::strided_gather(h, F, m, j, h->fbuf);
+                int it = 0;
+                double rr = 0.0;
+                const ddg_status st = pcg(h, h->fbuf, h->ubuf, tol, &it, &rr);
+                ddg::strided_scatter(h, h->ubuf, m, j, U);
+                if (iters) iters[j] = it;
+                if (relres) relres[j] = rr;
+                if (st != DDG_OK && worst == DDG_OK) worst = st;
+            }
+        } else if (m <= DDG_MCHUNK) {
+            worst = pcg_batch(h, F, U, m, tol, iters, relres);
+        } else {
+            // groups of DDG_MCHUNK columns through staging blocks
+            ddg::multi_ensure(h, DDG_MCHUNK);
+            for (int j0 = 0; j0 < m; j0 += DDG_MCHUNK) {
+                const int mg = std::min(DDG_MCHUNK, m - j0);
+                ddg::copy_cols(h, F, m, j0, h->mw.Fb, mg, 0, mg);
+                const ddg_status st = pcg_batch(h, h->mw.Fb, h->mw.Ub, mg, tol, iters ? iters + j0 : nullptr,
+                                                relres ? relres + j0 : nullptr);
+                ddg::copy_cols(h, h->mw.Ub, mg, 0, U, m, j0, mg);
+                if (st != DDG_OK && worst == DDG_OK) worst = st;
+            }
         }
         DDG_CUDA(cudaStreamSynchronize(h->stream));
         return worst;

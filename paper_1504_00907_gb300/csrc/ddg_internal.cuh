@@ -33,6 +33,7 @@
 #define DDG_CT 64        // coarse factor tile edge
 #define DDG_KMAX 32      // largest supported number of generators
 #define DDG_RED_BLOCKS 1216  // blocks of the deterministic reductions (8 x 152 SMs)
+#define DDG_MCHUNK 64        // right-hand sides per batched PCG group
 
 // ---------------------------------------------------------------- errors
 struct DdgError {
@@ -118,6 +119,21 @@ struct ProfileMat {         // rows with one contiguous column range each
     int64_t nnz = 0;
 };
 
+// workspace of the batched (multi-RHS) PCG, grown on first use
+struct MultiWork {
+    int m_alloc = 0;
+    double *R = nullptr, *P = nullptr, *Q = nullptr, *T = nullptr;   // n x m FP64
+    double *Fb = nullptr, *Ub = nullptr;                              // column-group staging
+    float *r32 = nullptr, *z32 = nullptr, *res32 = nullptr;
+    float *c32 = nullptr, *y32 = nullptr, *t32 = nullptr, *x32 = nullptr;
+    double* scal = nullptr;       // [S_COUNT][DDG_MCHUNK]
+    double* partials = nullptr;   // [DDG_RED_BLOCKS][2][DDG_MCHUNK]
+    int* active = nullptr;        // [DDG_MCHUNK]
+    int* restart = nullptr;       // [DDG_MCHUNK]
+    int2* items = nullptr;        // (sweep position, tile row) per colour
+    std::vector<int> h_citem_off;
+};
+
 struct ddg_handle_s {
     DevArena arena;
     cudaStream_t stream = nullptr;
@@ -200,6 +216,8 @@ struct ddg_handle_s {
     int32_t* errflags = nullptr;
     std::vector<double> history;
 
+    MultiWork mw;
+
     // ---- CUDA graphs of the preconditioner apply inside PCG (one per precision)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t apply_exec[3] = {nullptr, nullptr, nullptr};
@@ -264,6 +282,17 @@ void set_scalar(ddg_handle h, int slot, double v);
 void strided_gather(ddg_handle h, const double* src, int m, int j, double* dst);
 void strided_scatter(ddg_handle h, const double* src, int m, int j, double* dst);
 void cast_q32(ddg_handle h);
+
+// k_multi.cu (batched PCG on n x m blocks, m <= DDG_MCHUNK)
+void multi_ensure(ddg_handle h, int m);
+void multi_apply(ddg_handle h, int m);
+void multi_spmv_pq(ddg_handle h, int m);
+void multi_update_ur(ddg_handle h, int m, double* U);
+void multi_dots(ddg_handle h, int m, int pr);
+void multi_update_p(ddg_handle h, int m);
+void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double* out, int slot);
+void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace);
+void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int md, int k0, int cnt);
 
 // api.cu: error message of a handle-less call, read by ddg_last_error(NULL)
 void set_handleless_error(const char* msg);

@@ -1,0 +1,558 @@
+// Many right-hand sides at once (m <= DDG_MCHUNK per group): the same PCG and
+// the same preconditioner (Sec. 6, Sec. 7) on an n x m block stored dof-major
+// (entry (g, j) at g * m + j), with per-column CG scalars, convergence masks
+// and restarts.  Every stage is a multi-column version of the single-RHS
+// kernel: the preconditioner reads each local inverse once per colour phase
+// for all m columns, which is what makes batching pay.
+#include "ddg_internal.cuh"
+#include "dev_common.cuh"
+
+namespace {
+
+constexpr int MT = 256;
+
+// threads of the column-mapped kernels: a multiple of m, at most 256
+inline int col_block(int m) { return (MT / m) * m; }
+
+// A z at dof g, column c of an n x m block (matrix-free for the Laplacians)
+template <int SK, typename V, typename AV>
+__device__ __forceinline__ V apply_row(int g, int c, int m, const int64_t* __restrict__ rowptr,
+                                       const int32_t* __restrict__ col, const AV* __restrict__ val,
+                                       const V* __restrict__ z, int nx, int ny, int nz) {
+    if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+        const int i = g % nx, j = (g / nx) % ny;
+        V az = (SK == DDG_STENCIL_7PT_3D ? (V)6 : (V)4) * z[(int64_t)g * m + c];
+        if (i > 0) az -= z[(int64_t)(g - 1) * m + c];
+        if (i < nx - 1) az -= z[(int64_t)(g + 1) * m + c];
+        if (j > 0) az -= z[(int64_t)(g - nx) * m + c];
+        if (j < ny - 1) az -= z[(int64_t)(g + nx) * m + c];
+        if (SK == DDG_STENCIL_7PT_3D) {
+            const int k = g / (nx * ny);
+            if (k > 0) az -= z[(int64_t)(g - nx * ny) * m + c];
+            if (k < nz - 1) az -= z[(int64_t)(g + nx * ny) * m + c];
+        }
+        return az;
+    }
+    V s = 0;
+    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma((V)val[e], z[(int64_t)col[e] * m + c], s);
+    return s;
+}
+
+// per-column deterministic reduction: thread t owns column t % m; block
+// partials summed in block order by the last block.  Returns true in the
+// last block, with tot[c] valid for threads t < m (column t).
+template <int NV>
+__device__ bool reduce_cols(double (&v)[NV], int m, double* partials, unsigned* counter,
+                            double (&tot)[NV]) {
+    __shared__ double sh[MT];
+    __shared__ bool last;
+    const int rpb = blockDim.x / m;
+    double bs[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        __syncthreads();
+        sh[threadIdx.x] = v[q];
+        __syncthreads();
+        bs[q] = 0.0;
+        if ((int)threadIdx.x < m)
+            for (int r = 0; r < rpb; ++r) bs[q] += sh[r * m + threadIdx.x];
+    }
+    if ((int)threadIdx.x < m)
+        for (int q = 0; q < NV; ++q) partials[((size_t)blockIdx.x * NV + q) * m + threadIdx.x] = bs[q];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if ((int)threadIdx.x < m)
+        for (int q = 0; q < NV; ++q) {
+            double s = 0.0;
+            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + ((size_t)b * NV + q) * m + threadIdx.x);
+            tot[q] = s;
+        }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+// scalars: sc[slot * DDG_MCHUNK + column]
+__device__ __forceinline__ double& S(double* sc, int slot, int c) { return sc[slot * DDG_MCHUNK + c]; }
+
+template <int SK>
+__global__ void __launch_bounds__(MT) spmv_multi_kernel(int64_t n, int m, const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ col,
+                                                        const double* __restrict__ val,
+                                                        const double* __restrict__ P, double* __restrict__ Q,
+                                                        int nx, int ny, int nz, double* partials,
+                                                        unsigned* counter, double* sc,
+                                                        const int* __restrict__ active) {
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m, rl = threadIdx.x / m;
+    double acc[1] = {0.0};
+    if ((int)threadIdx.x < rpb * m)
+        for (int64_t g = (int64_t)blockIdx.x * rpb + rl; g < n; g += (int64_t)gridDim.x * rpb) {
+            const double q = apply_row<SK, double, double>((int)g, c, m, rowptr, col, val, P, nx, ny, nz);
+            Q[g * m + c] = q;
+            acc[0] = fma(P[g * m + c], q, acc[0]);
+        }
+    double tot[1];
+    if (reduce_cols<1>(acc, m, partials, counter, tot) && (int)threadIdx.x < m) {
+        const double pq = tot[0];
+        S(sc, S_PQ, c) = pq;
+        if (active[c]) {
+            S(sc, S_ALPHA, c) = S(sc, S_RZ, c) / pq;
+            if (!(pq > 0.0) || pq != pq) S(sc, S_FLAG, c) = 1.0;
+        } else {
+            S(sc, S_ALPHA, c) = 0.0;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MT) update_ur_multi_kernel(int64_t n, int m, double* __restrict__ U,
+                                                             double* __restrict__ R,
+                                                             const double* __restrict__ P,
+                                                             const double* __restrict__ Q,
+                                                             double* partials, unsigned* counter,
+                                                             double* sc) {
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m, rl = threadIdx.x / m;
+    const double alpha = S(sc, S_ALPHA, c);
+    double acc[1] = {0.0};
+    if ((int)threadIdx.x < rpb * m)
+        for (int64_t g = (int64_t)blockIdx.x * rpb + rl; g < n; g += (int64_t)gridDim.x * rpb) {
+            const int64_t e = g * m + c;
+            U[e] = fma(alpha, P[e], U[e]);
+            const double r = fma(-alpha, Q[e], R[e]);
+            R[e] = r;
+            acc[0] = fma(r, r, acc[0]);
+        }
+    double tot[1];
+    if (reduce_cols<1>(acc, m, partials, counter, tot) && (int)threadIdx.x < m) {
+        S(sc, S_RR, c) = tot[0];
+        if (tot[0] != tot[0]) S(sc, S_FLAG, c) = 1.0;
+    }
+}
+
+// rho' = r^T z, qz = q^T z per column; beta = FR / PR, or 0 for a column
+// that restarts; rho <- rho' for active columns
+template <typename ZV>
+__global__ void __launch_bounds__(MT) dots_multi_kernel(int64_t n, int m, const double* __restrict__ R,
+                                                        const double* __restrict__ Q,
+                                                        const ZV* __restrict__ Z, int pr,
+                                                        double* partials, unsigned* counter, double* sc,
+                                                        const int* __restrict__ active,
+                                                        const int* __restrict__ restart) {
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m, rl = threadIdx.x / m;
+    double acc[2] = {0.0, 0.0};
+    if ((int)threadIdx.x < rpb * m)
+        for (int64_t g = (int64_t)blockIdx.x * rpb + rl; g < n; g += (int64_t)gridDim.x * rpb) {
+            const int64_t e = g * m + c;
+            const double z = (double)Z[e];
+            acc[0] = fma(R[e], z, acc[0]);
+            acc[1] = fma(Q[e], z, acc[1]);
+        }
+    double tot[2];
+    if (reduce_cols<2>(acc, m, partials, counter, tot) && (int)threadIdx.x < m) {
+        if (!active[c]) {
+            S(sc, S_BETA, c) = 0.0;
+        } else {
+            const double rz = tot[0];
+            double beta = 0.0;
+            if (!restart[c]) beta = pr ? (-S(sc, S_ALPHA, c) * tot[1] / S(sc, S_RZ, c)) : (rz / S(sc, S_RZ, c));
+            S(sc, S_BETA, c) = beta;
+            S(sc, S_RZ, c) = rz;
+            if (rz != rz) S(sc, S_FLAG, c) = 1.0;
+        }
+    }
+}
+
+template <typename ZV>
+__global__ void update_p_multi_kernel(int64_t n, int m, double* __restrict__ P, const ZV* __restrict__ Z,
+                                      const double* __restrict__ sc, const int* __restrict__ active) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    const int c = (int)(e % m);
+    if (!active[c]) return;
+    P[e] = fma(sc[S_BETA * DDG_MCHUNK + c], P[e], (double)Z[e]);
+}
+
+// per-column ||a - A b||^2 (true residual) or ||a||^2 (b = null), into slot
+template <int SK>
+__global__ void __launch_bounds__(MT) resnorm_multi_kernel(int64_t n, int m, const int64_t* __restrict__ rowptr,
+                                                           const int32_t* __restrict__ col,
+                                                           const double* __restrict__ val,
+                                                           const double* __restrict__ A_, const double* __restrict__ B_,
+                                                           double* __restrict__ out, int nx, int ny, int nz,
+                                                           double* partials, unsigned* counter, double* sc,
+                                                           int slot) {
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m, rl = threadIdx.x / m;
+    double acc[1] = {0.0};
+    if ((int)threadIdx.x < rpb * m)
+        for (int64_t g = (int64_t)blockIdx.x * rpb + rl; g < n; g += (int64_t)gridDim.x * rpb) {
+            double r = A_[g * m + c];
+            if (B_) r -= apply_row<SK, double, double>((int)g, c, m, rowptr, col, val, B_, nx, ny, nz);
+            if (out) out[g * m + c] = r;
+            acc[0] = fma(r, r, acc[0]);
+        }
+    double tot[1];
+    if (reduce_cols<1>(acc, m, partials, counter, tot) && (int)threadIdx.x < m) S(sc, slot, c) = tot[0];
+}
+
+// copy the columns with replace[c] != 0 from src into dst (restart with the true residual)
+__global__ void replace_cols_kernel(int64_t n, int m, const double* __restrict__ src, double* __restrict__ dst,
+                                    const int* __restrict__ replace) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    if (replace[e % m]) dst[e] = src[e];
+}
+
+// dst[g, k0 + t] = src[g, j0 + t] for t < cnt (column blocks of dof-major arrays)
+__global__ void copy_cols_kernel(int64_t n, const double* __restrict__ src, int ms, int j0,
+                                 double* __restrict__ dst, int md, int k0, int cnt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * cnt) return;
+    const int64_t g = e / cnt;
+    const int t = (int)(e % cnt);
+    dst[g * md + k0 + t] = src[g * ms + j0 + t];
+}
+
+__global__ void to_float_n_kernel(int64_t cnt, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < cnt) b[g] = (float)a[g];
+}
+
+// ---------------------------------------------------------------- preconditioner
+template <int SK>
+__global__ void local_residual_multi_kernel(int64_t a0, int64_t a1, int m, const int32_t* __restrict__ ov_nodes,
+                                            const int64_t* __restrict__ rowptr,
+                                            const int32_t* __restrict__ col, const float* __restrict__ val,
+                                            const float* __restrict__ r, const float* __restrict__ z,
+                                            float* __restrict__ res, int z_zero, int nx, int ny, int nz) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (a1 - a0) * m) return;
+    const int64_t a = a0 + e / m;
+    const int c = (int)(e % m);
+    const int g = ov_nodes[a];
+    float s = r[(int64_t)g * m + c];
+    if (!z_zero) s -= apply_row<SK, float, float>(g, c, m, rowptr, col, val, z, nx, ny, nz);
+    res[a * m + c] = s;
+}
+
+// Y_I = sum_J A_IJ X_J for one 32-row tile row I of one subdomain, all m
+// columns; A_IJ is the stored tile (I, J) for J >= I and the transpose of
+// (J, I) below the diagonal.  z[rows of I] += Y_I.
+template <typename E>
+__global__ void __launch_bounds__(MT) local_solve_multi_kernel(
+    const int2* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
+    const int32_t* __restrict__ ov_nodes, const int64_t* __restrict__ tile_off,
+    const int32_t* __restrict__ Tq, const E* __restrict__ inv, const float* __restrict__ res,
+    float* __restrict__ z, int m) {
+    __shared__ float sB[DDG_LT][DDG_LT + 1];
+    __shared__ float sX[DDG_LT][DDG_MCHUNK];
+    const int2 it = items[item_base + blockIdx.x];
+    const int q = it.x, I = it.y;
+    const int64_t o = ov_off[q];
+    const int n = (int)(ov_off[q + 1] - o);
+    const int T = Tq[q];
+    const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
+    float acc[DDG_MCHUNK / 8];
+#pragma unroll
+    for (int u = 0; u < DDG_MCHUNK / 8; ++u) acc[u] = 0.f;
+    const E* base = inv + (size_t)tile_off[q] * 1024;
+    for (int J = 0; J < T; ++J) {
+        const bool upper = J >= I;
+        const int a = upper ? I : J, b = upper ? J : I;
+        const E* tp = base + ((size_t)a * T - (size_t)a * (a - 1) / 2 + (b - a)) * 1024;
+        for (int e = threadIdx.x; e < 1024; e += MT) {
+            const int rr = e >> 5, kk = e & 31;
+            const float v = (float)tp[e];
+            if (upper) sB[rr][kk] = v;
+            else sB[kk][rr] = v;
+        }
+        for (int e = threadIdx.x; e < DDG_LT * m; e += MT) {
+            const int k = e / m, c = e % m;
+            const int row = J * DDG_LT + k;
+            sX[k][c] = row < n ? res[(o + row) * m + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < DDG_LT; ++k) {
+            const float bv = sB[r][k];
+#pragma unroll
+            for (int u = 0; u < DDG_MCHUNK / 8; ++u)
+                if (cg + 8 * u < m) acc[u] = fma(bv, sX[k][cg + 8 * u], acc[u]);
+        }
+        __syncthreads();
+    }
+    const int row = I * DDG_LT + r;
+    if (row < n) {
+        const int g = ov_nodes[o + row];
+#pragma unroll
+        for (int u = 0; u < DDG_MCHUNK / 8; ++u)
+            if (cg + 8 * u < m) z[(int64_t)g * m + cg + 8 * u] += acc[u];
+    }
+}
+
+// c[(coff_s + jj) m + col] = sum_{g in Omega_s} Q[g, jj] (r - A z)[g, col]
+template <int SK>
+__global__ void __launch_bounds__(MT) coarse_restrict_multi_kernel(
+    const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
+    const float* __restrict__ r, const float* __restrict__ z, const float* __restrict__ Q, int kmax,
+    const int32_t* __restrict__ coff, float* __restrict__ cvec, int m, int nx, int ny, int nz) {
+    extern __shared__ float shm[];   // [groups][kmax][m]
+    const int s = blockIdx.x;
+    const int groups = blockDim.x / m;
+    const int c = threadIdx.x % m, gq = threadIdx.x / m;
+    float acc[DDG_KMAX];
+#pragma unroll
+    for (int jj = 0; jj < DDG_KMAX; ++jj) acc[jj] = 0.f;
+    if (gq < groups)
+        for (int64_t a = sub_off[s] + gq; a < sub_off[s + 1]; a += groups) {
+            const int g = sub_nodes[a];
+            const float w = r[(int64_t)g * m + c] - apply_row<SK, float, float>(g, c, m, rowptr, col, val, z, nx, ny, nz);
+            const float* qa = Q + a * kmax;
+#pragma unroll
+            for (int jj = 0; jj < DDG_KMAX; ++jj)
+                if (jj < kmax) acc[jj] = fma(qa[jj], w, acc[jj]);
+        }
+    if (gq < groups)
+        for (int jj = 0; jj < kmax; ++jj) shm[(gq * kmax + jj) * m + c] = acc[jj];
+    __syncthreads();
+    const int ks = coff[s + 1] - coff[s];
+    for (int e = threadIdx.x; e < ks * m; e += blockDim.x) {
+        const int jj = e / m, cc = e % m;
+        float t = 0.f;
+        for (int g2 = 0; g2 < groups; ++g2) t += shm[(g2 * kmax + jj) * m + cc];
+        cvec[(int64_t)(coff[s] + jj) * m + cc] = t;
+    }
+}
+
+// out[i, c] = (a ? a[i, c] : 0) + sign sum_j M[i][j] x[j, c]; one block per row
+__global__ void __launch_bounds__(MT) profile_gemm_kernel(const int64_t* __restrict__ rowptr,
+                                                          const int32_t* __restrict__ lo,
+                                                          const int32_t* __restrict__ hi,
+                                                          const float* __restrict__ vals, int r0,
+                                                          const float* __restrict__ x,
+                                                          const float* __restrict__ a, float sign,
+                                                          float* __restrict__ out, int m) {
+    __shared__ float sh[MT];
+    const int i = r0 + blockIdx.x;
+    const int splits = blockDim.x / m;
+    const int c = threadIdx.x % m, sp = threadIdx.x / m;
+    const int l = lo[i], h = hi[i];
+    const float* rv = vals + rowptr[i] - l;
+    float s = 0.f;
+    if (sp < splits)
+        for (int j = l + sp; j < h; j += splits) s = fma(rv[j], x[(int64_t)j * m + c], s);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    if ((int)threadIdx.x < m) {
+        float t = 0.f;
+        for (int q = 0; q < splits; ++q) t += sh[q * m + threadIdx.x];
+        const int64_t e = (int64_t)i * m + threadIdx.x;
+        out[e] = (a ? a[e] : 0.f) + sign * t;
+    }
+}
+
+__global__ void coarse_prolong_multi_kernel(int64_t n, int m, const int32_t* __restrict__ part,
+                                            const int32_t* __restrict__ pos, const float* __restrict__ Q,
+                                            int kmax, const int32_t* __restrict__ coff,
+                                            const float* __restrict__ y, float* __restrict__ z) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    const int64_t g = e / m;
+    const int c = (int)(e % m);
+    const int s = part[g];
+    const int c0 = coff[s], ks = coff[s + 1] - c0;
+    const float* qa = Q + (int64_t)pos[g] * kmax;
+    float acc = 0.f;
+    for (int jj = 0; jj < ks; ++jj) acc = fma(qa[jj], y[(int64_t)(c0 + jj) * m + c], acc);
+    z[e] += acc;
+}
+
+inline unsigned grid_for(int64_t n, int m) {
+    const int rpb = MT / m;
+    int64_t b = (n + rpb - 1) / rpb;
+    if (b > DDG_RED_BLOCKS) b = DDG_RED_BLOCKS;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+namespace ddg {
+
+void multi_ensure(ddg_handle h, int m) {
+    MultiWork& w = h->mw;
+    if (w.m_alloc >= m) return;
+    for (void* p : {(void*)w.R, (void*)w.P, (void*)w.Q, (void*)w.T, (void*)w.Fb, (void*)w.Ub,
+                    (void*)w.r32, (void*)w.z32,
+                    (void*)w.res32, (void*)w.c32, (void*)w.y32, (void*)w.t32, (void*)w.x32,
+                    (void*)w.scal, (void*)w.partials, (void*)w.active, (void*)w.restart,
+                    (void*)w.items})
+        if (p) h->arena.release(p);
+    const int64_t n = h->n;
+    w.R = h->arena.alloc<double>(n * m);
+    w.P = h->arena.alloc<double>(n * m);
+    w.Q = h->arena.alloc<double>(n * m);
+    w.T = h->arena.alloc<double>(n * m);
+    w.Fb = h->arena.alloc<double>(n * m);
+    w.Ub = h->arena.alloc<double>(n * m);
+    w.r32 = h->arena.alloc<float>(n * m);
+    w.z32 = h->arena.alloc<float>(n * m);
+    w.res32 = h->arena.alloc<float>(h->sum_local * m);
+    const int64_t n0p = h->use_coarse ? h->n0p : 1;
+    w.c32 = h->arena.alloc<float>(n0p * m);
+    w.y32 = h->arena.alloc<float>(n0p * m);
+    w.t32 = h->arena.alloc<float>(n0p * m);
+    w.x32 = h->arena.alloc<float>(n0p * m);
+    for (float* p : {w.c32, w.y32, w.t32, w.x32})
+        DDG_CUDA(cudaMemsetAsync(p, 0, n0p * m * sizeof(float), h->stream));
+    w.scal = h->arena.alloc<double>(S_COUNT * DDG_MCHUNK);
+    w.partials = h->arena.alloc<double>((size_t)DDG_RED_BLOCKS * 2 * DDG_MCHUNK);
+    w.active = h->arena.alloc<int>(DDG_MCHUNK);
+    w.restart = h->arena.alloc<int>(DDG_MCHUNK);
+    // work items of the multi-RHS local solve: one per (subdomain, tile row)
+    std::vector<int2> it;
+    w.h_citem_off.assign(h->ncol + 1, 0);
+    std::vector<int> Tq(h->nsub);
+    for (int q = 0; q < h->nsub; ++q) {
+        const int nq = (int)(h->h_ov_off[q + 1] - h->h_ov_off[q]);
+        Tq[q] = (nq + DDG_LT - 1) / DDG_LT;
+    }
+    for (int c = 0; c < h->ncol; ++c) {
+        for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q)
+            for (int I = 0; I < Tq[q]; ++I) it.push_back(make_int2(q, I));
+        w.h_citem_off[c + 1] = (int)it.size();
+    }
+    w.items = h->arena.alloc<int2>(it.size());
+    h2d(w.items, it.data(), it.size(), h->stream);
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    w.m_alloc = m;
+}
+
+template <int SK>
+static void multi_apply_t(ddg_handle h, int m) {
+    MultiWork& w = h->mw;
+    const int64_t n = h->n;
+    const int prec = h->precision;
+    to_float_n_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, h->stream>>>(n * m, w.R, w.r32);
+    DDG_CUDA(cudaMemsetAsync(w.z32, 0, n * m * sizeof(float), h->stream));
+    auto local = [&](int c, bool zz) {
+        const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
+        if (a1 > a0) {
+            local_residual_multi_kernel<SK><<<(unsigned)(((a1 - a0) * m + 255) / 256), 256, 0, h->stream>>>(
+                a0, a1, m, h->ov_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, w.res32, zz, h->nx,
+                h->ny, h->nz);
+        }
+        const int i0 = w.h_citem_off[c], i1 = w.h_citem_off[c + 1];
+        if (i1 > i0) {
+            if (prec == DDG_PREC_BF16 && h->inv16)
+                local_solve_multi_kernel<__nv_bfloat16><<<i1 - i0, MT, 0, h->stream>>>(
+                    w.items, i0, h->ov_off, h->ov_nodes, h->tile_off, h->Tq, h->inv16, w.res32, w.z32, m);
+            else
+                local_solve_multi_kernel<float><<<i1 - i0, MT, 0, h->stream>>>(
+                    w.items, i0, h->ov_off, h->ov_nodes, h->tile_off, h->Tq, h->inv32, w.res32, w.z32, m);
+        }
+        DDG_CHECK_LAUNCH();
+    };
+    for (int c = 0; c < h->ncol; ++c) local(c, c == 0);
+    if (h->use_coarse) {
+        const int bd = col_block(m);
+        const size_t smem = (size_t)(bd / m) * h->kmax * m * sizeof(float);
+        coarse_restrict_multi_kernel<SK><<<h->nsub, bd, smem, h->stream>>>(
+            h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff,
+            w.c32, m, h->nx, h->ny, h->nz);
+        const int B = h->B, nK = h->nK;
+        auto gemm = [&](const ProfileMat& M, int r0, const float* x, const float* a, float sign, float* out) {
+            profile_gemm_kernel<<<B, bd, 0, h->stream>>>(M.rowptr, M.lo, M.hi, M.v32, r0, x, a, sign, out, m);
+        };
+        for (int K = 0; K < nK; ++K) {
+            const float* in = w.c32;
+            if (K > 0) {
+                gemm(h->Em, K * B, w.y32, w.c32, -1.f, w.t32);
+                in = w.t32;
+            }
+            gemm(h->Dm, K * B, in, nullptr, 1.f, w.y32);
+        }
+        for (int K = nK - 1; K >= 0; --K) {
+            const float* in = w.y32;
+            if (K < nK - 1) {
+                gemm(h->Et, K * B, w.x32, w.y32, -1.f, w.t32);
+                in = w.t32;
+            }
+            gemm(h->Dt, K * B, in, nullptr, 1.f, w.x32);
+        }
+        coarse_prolong_multi_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, h->stream>>>(
+            n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);
+        DDG_CHECK_LAUNCH();
+    }
+    for (int c = h->ncol - 1; c >= 0; --c) local(c, false);
+}
+
+void multi_apply(ddg_handle h, int m) {
+    if (h->stencil_kind == DDG_STENCIL_7PT_3D) multi_apply_t<DDG_STENCIL_7PT_3D>(h, m);
+    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) multi_apply_t<DDG_STENCIL_5PT_2D>(h, m);
+    else multi_apply_t<DDG_STENCIL_NONE>(h, m);
+}
+
+void multi_spmv_pq(ddg_handle h, int m) {
+    MultiWork& w = h->mw;
+    const unsigned G = grid_for(h->n, m);
+    const int bd = col_block(m);
+    const int sk = h->stencil_kind;
+    if (sk == DDG_STENCIL_7PT_3D)
+        spmv_multi_kernel<DDG_STENCIL_7PT_3D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, w.P, w.Q, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, w.active);
+    else if (sk == DDG_STENCIL_5PT_2D)
+        spmv_multi_kernel<DDG_STENCIL_5PT_2D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, w.P, w.Q, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, w.active);
+    else
+        spmv_multi_kernel<DDG_STENCIL_NONE><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, w.P, w.Q, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, w.active);
+    DDG_CHECK_LAUNCH();
+}
+
+void multi_update_ur(ddg_handle h, int m, double* U) {
+    MultiWork& w = h->mw;
+    update_ur_multi_kernel<<<grid_for(h->n, m), col_block(m), 0, h->stream>>>(h->n, m, U, w.R, w.P, w.Q, w.partials, h->red_counter, w.scal);
+    DDG_CHECK_LAUNCH();
+}
+
+void multi_dots(ddg_handle h, int m, int pr) {
+    MultiWork& w = h->mw;
+    dots_multi_kernel<float><<<grid_for(h->n, m), col_block(m), 0, h->stream>>>(h->n, m, w.R, w.Q, w.z32, pr, w.partials, h->red_counter, w.scal, w.active, w.restart);
+    DDG_CHECK_LAUNCH();
+}
+
+void multi_update_p(ddg_handle h, int m) {
+    MultiWork& w = h->mw;
+    update_p_multi_kernel<float><<<(unsigned)((h->n * m + 255) / 256), 256, 0, h->stream>>>(h->n, m, w.P, w.z32, w.scal, w.active);
+    DDG_CHECK_LAUNCH();
+}
+
+// slot <- per-column ||a - A b||^2 (b may be null); out (may be null) <- a - A b
+void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double* out, int slot) {
+    MultiWork& w = h->mw;
+    const unsigned G = grid_for(h->n, m);
+    const int bd = col_block(m);
+    const int sk = h->stencil_kind;
+    if (sk == DDG_STENCIL_7PT_3D)
+        resnorm_multi_kernel<DDG_STENCIL_7PT_3D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, slot);
+    else if (sk == DDG_STENCIL_5PT_2D)
+        resnorm_multi_kernel<DDG_STENCIL_5PT_2D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, slot);
+    else
+        resnorm_multi_kernel<DDG_STENCIL_NONE><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, slot);
+    DDG_CHECK_LAUNCH();
+}
+
+void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int md, int k0, int cnt) {
+    copy_cols_kernel<<<(unsigned)((h->n * cnt + 255) / 256), 256, 0, h->stream>>>(h->n, src, ms, j0, dst, md, k0, cnt);
+    DDG_CHECK_LAUNCH();
+}
+
+void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace) {
+    replace_cols_kernel<<<(unsigned)((h->n * m + 255) / 256), 256, 0, h->stream>>>(h->n, m, src, dst, replace);
+    DDG_CHECK_LAUNCH();
+}
+
+}  // namespace ddg
