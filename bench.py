@@ -187,10 +187,12 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
     solved one at a time."""
     N, m = args.batched_size, args.batched_m
     prob = di.make_varcoef3d(N=N, box=8, overlap=1, p=2, m=m)
-    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32", "bf16"))
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32", "bf16"), tensor_cores=True)
     F = torch.tensor(prob.f, dtype=torch.float64, device=dev)
-    out = {"workload": f"varcoef3d_{N}^3, {m} right-hand sides", "dofs": prob.n, "m": m}
-    for prec in ("fp32", "bf16"):
+    out = {"workload": f"varcoef3d_{N}^3, {m} right-hand sides", "dofs": prob.n, "m": m,
+           "arms": {"fp32": "FP32 SIMT local solves on packed FP32 inverses",
+                    "bf16_tc": "tcgen05 BF16 local solves (FP32 accumulate) on BF16 inverse slabs"}}
+    for prec, key in (("fp32", "fp32"), ("bf16", "bf16_tc")):
         solver.set_precision(prec)
         solver.solve_batch(F, TOL)            # warm-up (allocates the batch workspace)
         torch.cuda.synchronize()
@@ -201,7 +203,7 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
         e1.record(stream)
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1))
-        out[prec] = {"ms": ms, "status": int(st), "iters_mean": float(its.mean()),
+        out[key] = {"ms": ms, "status": int(st), "iters_mean": float(its.mean()),
                      "iters_max": int(its.max()), "max_true_relres": float(rrs.max()),
                      "dof_iters_per_s": world * prob.n * float(its.sum()) / (ms / 1e3)}
     # the first few columns one at a time, same precision

@@ -47,7 +47,7 @@ typedef enum {
     DDG_ENOTSPD = 3,      /* a local or the coarse Cholesky met a non-positive pivot */
     DDG_EBREAKDOWN = 4,   /* CG breakdown: p^T A p <= 0 or a NaN */
     DDG_ENOCONV = 5,      /* maxit reached; u holds the last iterate */
-    DDG_ETIMEOUT = 6,     /* reserved: a bounded device wait ran out */
+    DDG_ETIMEOUT = 6,     /* a bounded device wait ran out (the result is not valid) */
     DDG_ECUDA = 7         /* a CUDA runtime call failed */
 } ddg_status;
 
@@ -81,6 +81,10 @@ typedef struct {
     double rank_tol;      /* Sec. 4 rank drop: keep column j while |R_jj| >
                              rank_tol * |R_00|; default 1e-10 */
     int chunk_tiles;      /* local-solve work item size in 32x32 tiles; 0 = auto */
+    int tensor_cores;     /* 1: also keep BF16 128x32 slabs of every A_i^{-1}; then
+                             ddg_solve_batch in DDG_PREC_BF16 runs its local solves on
+                             the tcgen05 tensor cores (BF16 x BF16, FP32 accumulate);
+                             default 0 */
 } ddg_options;
 
 typedef struct {

@@ -472,6 +472,16 @@ ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol
             }
     }
     ddg_status worst = DDG_OK;
+    {
+        int32_t flags[E_COUNT];
+        d2h(flags, h->errflags, E_COUNT, h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        if (flags[E_TIMEOUT]) {
+            DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
+            h->err = "a bounded wait of the tensor-core local solve ran out";
+            worst = DDG_ETIMEOUT;
+        }
+    }
     for (int j = 0; j < m; ++j) {
         if (iters) iters[j] = done_it[j];
         if (relres) relres[j] = done_rel[j];
@@ -711,6 +721,40 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
                 }
         }
 
+        // ---- tensor-core slabs and residual layout for the batched solve
+        if (o.tensor_cores) {
+            std::vector<int64_t> soff(nsub + 1, 0), xo(nsub + 1, 0);
+            std::vector<int32_t> ovs(h->sum_local);
+            std::vector<int2> tit;
+            h->tc.h_citem_off.assign(h->ncol + 1, 0);
+            for (int c = 0; c < h->ncol; ++c) {
+                for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
+                    const int nq = (int)(ov_off[q + 1] - ov_off[q]);
+                    const int Mb = (nq + 127) / 128;
+                    for (int b = 0; b < Mb; ++b) tit.push_back(make_int2(q, b));
+                }
+                h->tc.h_citem_off[c + 1] = (int)tit.size();
+            }
+            for (int q = 0; q < nsub; ++q) {
+                const int nq = (int)(ov_off[q + 1] - ov_off[q]);
+                soff[q + 1] = soff[q] + (int64_t)((nq + 127) / 128) * Tq[q];
+                xo[q + 1] = xo[q] + Tq[q];
+                for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) ovs[a] = q;
+            }
+            h->tc.slab_off = h->arena.alloc<int64_t>(nsub + 1);
+            h->tc.xoff = h->arena.alloc<int64_t>(nsub + 1);
+            h->tc.ov_sub = h->arena.alloc<int32_t>(h->sum_local);
+            h->tc.items = h->arena.alloc<int2>(tit.size());
+            h2d(h->tc.slab_off, soff.data(), nsub + 1, h->stream);
+            h2d(h->tc.xoff, xo.data(), nsub + 1, h->stream);
+            h2d(h->tc.ov_sub, ovs.data(), h->sum_local, h->stream);
+            h2d(h->tc.items, tit.data(), tit.size(), h->stream);
+            h->tc.A = h->arena.alloc<__nv_bfloat16>((size_t)soff[nsub] * 128 * 32);
+            h->tc.x_elems = xo[nsub] * (int64_t)DDG_MCHUNK * 32;
+            h->tc.X = h->arena.alloc<__nv_bfloat16>(h->tc.x_elems);
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
+        }
+
         // ---- local inverses (FP64 factorisation, packed copies)
         h->errflags = h->arena.alloc<int32_t>(E_COUNT);
         DDG_CUDA(cudaMemsetAsync(h->errflags, 0, E_COUNT * sizeof(int32_t), h->stream));
@@ -734,6 +778,7 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
                 const int q1 = std::min(nsub, q0 + nb);
                 ddg::local_extract_factor_invert(h, q0, q1, ws, invdiag);
                 ddg::local_pack(h, q0, q1, ws);
+                ddg::tc_pack(h, q0, q1, ws);
             }
             DDG_CUDA(cudaStreamSynchronize(h->stream));
             h->arena.release(ws);

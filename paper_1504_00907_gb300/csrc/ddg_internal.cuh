@@ -107,7 +107,7 @@ enum {
 };
 
 // error flags written by kernels (int32)
-enum { E_LOCAL_SPD = 0, E_COARSE_SPD = 1, E_COUNT = 4 };
+enum { E_LOCAL_SPD = 0, E_COARSE_SPD = 1, E_TIMEOUT = 2, E_COUNT = 4 };
 
 // ---------------------------------------------------------------- handle
 struct ProfileMat {         // rows with one contiguous column range each
@@ -132,6 +132,19 @@ struct MultiWork {
     int* restart = nullptr;       // [DDG_MCHUNK]
     int2* items = nullptr;        // (sweep position, tile row) per colour
     std::vector<int> h_citem_off;
+};
+
+// tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}
+struct TcData {
+    __nv_bfloat16* A = nullptr;    // 128 x 32 slabs, core-matrix order
+    __nv_bfloat16* X = nullptr;    // residual slabs N x 32 per subdomain
+    int64_t* slab_off = nullptr;   // [nsub + 1] in A slabs
+    int64_t* xoff = nullptr;       // [nsub + 1] in X slabs
+    int32_t* ov_sub = nullptr;     // [sum_local] sweep position of each local row
+    int2* items = nullptr;         // (sweep position, 128-row block) per colour
+    std::vector<int> h_citem_off;
+    int64_t x_elems = 0;
+    int last_m = -1;
 };
 
 struct ddg_handle_s {
@@ -217,6 +230,7 @@ struct ddg_handle_s {
     std::vector<double> history;
 
     MultiWork mw;
+    TcData tc;
 
     // ---- CUDA graphs of the preconditioner apply inside PCG (one per precision)
     cudaStream_t cap_stream = nullptr;
@@ -293,6 +307,12 @@ void multi_update_p(ddg_handle h, int m);
 void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double* out, int slot);
 void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace);
 void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int md, int k0, int cnt);
+
+// k_tc.cu (tcgen05 local solves of the batched path)
+int tc_n_for(int m);
+void tc_pack(ddg_handle h, int q0, int q1, const double* ws);
+void tc_residual(ddg_handle h, int colour, bool z_zero, int m);
+void tc_local_solve(ddg_handle h, int colour, int m);
 
 // api.cu: error message of a handle-less call, read by ddg_last_error(NULL)
 void set_handleless_error(const char* msg);

@@ -440,7 +440,18 @@ static void multi_apply_t(ddg_handle h, int m) {
     const int prec = h->precision;
     to_float_n_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, h->stream>>>(n * m, w.R, w.r32);
     DDG_CUDA(cudaMemsetAsync(w.z32, 0, n * m * sizeof(float), h->stream));
+    const bool tc = prec == DDG_PREC_BF16 && h->tc.A != nullptr;
+    if (tc && h->tc.last_m != m) {
+        // padding rows/columns of the BF16 residual slabs must read as zero
+        DDG_CUDA(cudaMemsetAsync(h->tc.X, 0, h->tc.x_elems * sizeof(__nv_bfloat16), h->stream));
+        h->tc.last_m = m;
+    }
     auto local = [&](int c, bool zz) {
+        if (tc) {
+            tc_residual(h, c, zz, m);
+            tc_local_solve(h, c, m);
+            return;
+        }
         const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
         if (a1 > a0) {
             local_residual_multi_kernel<SK><<<(unsigned)(((a1 - a0) * m + 255) / 256), 256, 0, h->stream>>>(

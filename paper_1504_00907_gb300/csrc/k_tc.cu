@@ -1,0 +1,321 @@
+// Multi-RHS local solves on the 5th-generation tensor cores (tcgen05).
+//
+// For the batched solve the local step z[Omega~_i] += A_i^{-1} R~_i (r - A z)
+// (Sec. 6) is a dense GEMM Y_i = A_i^{-1} X_i with X_i = n_i x m.  A_i^{-1} is
+// kept in BF16 as 128 x 32 slabs (K-major, SWIZZLE_NONE core-matrix order:
+// core matrix (8 rows x 16 bytes) (mc, kc) at byte (mc * 4 + kc) * 128); the
+// local residual is written straight into BF16 X^T slabs (N x 32, same core
+// order).  One CTA computes one 128-row block of Y_i:
+//   thread 0      producer: cp.async.bulk of the A slab and the X slab of each
+//                 K step into a STAGES-deep shared-memory ring (mbarrier
+//                 transaction counts);
+//   thread 32     issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32, M = 128,
+//                 N = m rounded up to 16, K = 16, two per slab) into a TMEM
+//                 accumulator and commits each stage back to the producer;
+//   warps 0-3     read their 32 TMEM lanes (tcgen05.ld 32x32b) and add the
+//                 rows into z.
+// Every wait is bounded: a wait that runs out sets the error flag, the kernel
+// drains its own copies (bounded), frees its TMEM and returns.
+#include "ddg_internal.cuh"
+
+namespace {
+
+constexpr int TC_M = 128;            // rows of Y per CTA (MMA M)
+constexpr int TC_K = 32;             // K per slab (two K = 16 MMAs)
+constexpr int TC_STAGES = 6;
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_POLLS = 1u << 22;   // bounded mbarrier polls
+constexpr int A_SLAB = TC_M * TC_K;       // elements per A slab
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO (K-direction stride between
+// core matrices), SBO (M/N-direction stride), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok = 0;
+    for (uint32_t i = 0; i < TC_POLLS; ++i) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(sa(bar)), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// core-matrix offset of element (row, k) in a rows x 32 K-major slab
+__device__ __forceinline__ int core_off(int row, int k) {
+    return ((row >> 3) * 4 + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+template <int N>
+__global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
+    const int2* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
+    const int32_t* __restrict__ ov_nodes, const int32_t* __restrict__ Tq,
+    const int64_t* __restrict__ slab_off, const int64_t* __restrict__ xoff,
+    const __nv_bfloat16* __restrict__ Aslab, const __nv_bfloat16* __restrict__ Xslab,
+    float* __restrict__ z, int m, int* err) {
+    constexpr int X_SLAB = N * TC_K;
+    constexpr uint32_t A_BYTES = A_SLAB * 2, X_BYTES = X_SLAB * 2, STAGE = A_BYTES + X_BYTES;
+    constexpr uint32_t TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE);
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* done = empty + TC_STAGES;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int failed;
+
+    const int2 it = items[item_base + blockIdx.x];
+    const int q = it.x, blk = it.y;
+    const int T = Tq[q];
+    const int64_t o = ov_off[q];
+    const int n = (int)(ov_off[q + 1] - o);
+    const __nv_bfloat16* Ab = Aslab + (slab_off[q] + (int64_t)blk * T) * A_SLAB;
+    const __nv_bfloat16* Xb = Xslab + xoff[q] * X_SLAB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        failed = 0;
+        for (int s = 0; s < TC_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(sa(done)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(sa(tslot)), "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    int issued = 0;   // stages handed to the copy engine (producer only)
+    if (threadIdx.x == 0) {
+        for (int J = 0; J < T; ++J) {
+            const int s = J % TC_STAGES;
+            if (J >= TC_STAGES && !mbar_wait(&empty[s], ((J / TC_STAGES) - 1) & 1)) {
+                failed = 1;
+                break;
+            }
+            unsigned char* st = smem + s * STAGE;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(sa(&full[s])), "r"(STAGE) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(sa(st)), "l"(Ab + (int64_t)J * A_SLAB), "r"(A_BYTES), "r"(sa(&full[s])) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(sa(st + A_BYTES)), "l"(Xb + (int64_t)J * X_SLAB), "r"(X_BYTES), "r"(sa(&full[s])) : "memory");
+            issued = J + 1;
+        }
+    } else if (threadIdx.x == 32) {
+        // kind::f16: D F32 (bit 4), A BF16 (bit 7), B BF16 (bit 10), K-major A and B,
+        // N >> 3 at bit 17, M >> 4 at bit 24
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                               ((uint32_t)(TC_M >> 4) << 24);
+        bool ok = true;
+        for (int J = 0; J < T; ++J) {
+            const int s = J % TC_STAGES;
+            if (!mbar_wait(&full[s], (J / TC_STAGES) & 1)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = sa(smem + s * STAGE), b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint64_t ad = sdesc(a0 + kk * 256, 128, 512);
+                const uint64_t bd = sdesc(b0 + kk * 256, 128, 512);
+                const uint32_t acc = (J > 0 || kk > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(sa(&empty[s])) : "memory");
+        }
+        if (!ok) failed = 1;
+        // arrives on `done` once every MMA issued above has completed
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(sa(done)) : "memory");
+    }
+    // epilogue: TMEM lanes [32 w, 32 w + 32) hold rows blk * 128 + 32 w + lane
+    const bool have = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!have) failed = 1;
+    __syncthreads();
+    if (!failed) {
+        const int row = blk * TC_M + warp * 32 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        const int g = row < n ? ov_nodes[o + row] : 0;
+#pragma unroll
+        for (int cb = 0; cb < N / 16; ++cb) {
+            float v[16];
+            tmem_ld16(taddr + cb * 16, v);
+            if (row < n) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = cb * 16 + i;
+                    if (c < m) z[(int64_t)g * m + c] += v[i];
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        // drain the copies this CTA still has in flight before its shared
+        // memory goes away (bounded)
+        for (int J = (issued > TC_STAGES ? issued - TC_STAGES : 0); J < issued; ++J)
+            mbar_wait(&full[J % TC_STAGES], (J / TC_STAGES) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS));
+    }
+}
+
+// A_i^{-1} (FP64 workspace after local_factor_invert: inverse in the upper
+// 32x32 tiles) -> BF16 128 x 32 slabs in core-matrix order
+__global__ void tc_pack_kernel(int q0, const double* __restrict__ ws, int Np,
+                               const int64_t* __restrict__ ov_off, const int32_t* __restrict__ Tq,
+                               const int64_t* __restrict__ slab_off, __nv_bfloat16* __restrict__ out) {
+    const int b = blockIdx.x, q = q0 + b;
+    const int n = (int)(ov_off[q + 1] - ov_off[q]);
+    const int T = Tq[q];
+    const int Mb = (n + TC_M - 1) / TC_M;
+    const double* A = ws + (size_t)b * Np * Np;
+    __nv_bfloat16* dst = out + slab_off[q] * A_SLAB;
+    const int64_t total = (int64_t)Mb * T * A_SLAB;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int64_t slab = e / A_SLAB;
+        const int w = (int)(e % A_SLAB);
+        const int blk = (int)(slab / T), J = (int)(slab % T);
+        // invert core_off: w = ((mc * 4 + kc) * 64) + (r % 8) * 8 + (k % 8)
+        const int core = w >> 6, within = w & 63;
+        const int mc = core >> 2, kc = core & 3;
+        const int row = blk * TC_M + mc * 8 + (within >> 3);
+        const int col = J * TC_K + kc * 8 + (within & 7);
+        double v = 0.0;
+        if (row < n && col < n)
+            v = (row / DDG_LT <= col / DDG_LT) ? A[(size_t)row * Np + col] : A[(size_t)col * Np + row];
+        dst[e] = __float2bfloat16_rn((float)v);
+    }
+}
+
+// (r - A z) at the colour's rows, all m columns, written as BF16 X^T slabs
+template <int SK>
+__global__ void tc_residual_kernel(int64_t a0, int64_t a1, int m, int N, const int32_t* __restrict__ ov_nodes,
+                                   const int32_t* __restrict__ ov_sub, const int64_t* __restrict__ ov_off,
+                                   const int64_t* __restrict__ xoff, const int64_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ col, const float* __restrict__ val,
+                                   const float* __restrict__ r, const float* __restrict__ z,
+                                   __nv_bfloat16* __restrict__ X, int z_zero, int nx, int ny, int nz) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (a1 - a0) * m) return;
+    const int64_t a = a0 + e / m;
+    const int c = (int)(e % m);
+    const int g = ov_nodes[a];
+    float s = r[(int64_t)g * m + c];
+    if (!z_zero) {
+        if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+            const int i = g % nx, j = (g / nx) % ny;
+            float az = (SK == DDG_STENCIL_7PT_3D ? 6.f : 4.f) * z[(int64_t)g * m + c];
+            if (i > 0) az -= z[(int64_t)(g - 1) * m + c];
+            if (i < nx - 1) az -= z[(int64_t)(g + 1) * m + c];
+            if (j > 0) az -= z[(int64_t)(g - nx) * m + c];
+            if (j < ny - 1) az -= z[(int64_t)(g + nx) * m + c];
+            if (SK == DDG_STENCIL_7PT_3D) {
+                const int k = g / (nx * ny);
+                if (k > 0) az -= z[(int64_t)(g - nx * ny) * m + c];
+                if (k < nz - 1) az -= z[(int64_t)(g + nx * ny) * m + c];
+            }
+            s -= az;
+        } else {
+            for (int64_t p = rowptr[g]; p < rowptr[g + 1]; ++p) s -= val[p] * z[(int64_t)col[p] * m + c];
+        }
+    }
+    const int q = ov_sub[a];
+    const int la = (int)(a - ov_off[q]);
+    const int J = la / TC_K, k = la % TC_K;
+    X[(xoff[q] + J) * (int64_t)(N * TC_K) + core_off(c, k)] = __float2bfloat16_rn(s);
+}
+
+template <int N>
+void configure_tc() {
+    static bool done = false;
+    if (done) return;
+    const int smem = TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    done = true;
+}
+
+template <int N>
+void launch_tc(ddg_handle h, int i0, int i1, int m) {
+    configure_tc<N>();
+    const int smem = TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+    local_solve_tc_kernel<N><<<i1 - i0, TC_THREADS, smem, h->stream>>>(
+        h->tc.items, i0, h->ov_off, h->ov_nodes, h->Tq, h->tc.slab_off, h->tc.xoff, h->tc.A, h->tc.X,
+        h->mw.z32, m, h->errflags + E_TIMEOUT);
+    DDG_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+namespace ddg {
+
+int tc_n_for(int m) { return ((m + 15) / 16) * 16; }
+
+void tc_pack(ddg_handle h, int q0, int q1, const double* ws) {
+    const int nb = q1 - q0;
+    if (nb <= 0 || !h->tc.A) return;
+    tc_pack_kernel<<<nb, 256, 0, h->stream>>>(q0, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq, h->tc.slab_off, h->tc.A);
+    DDG_CHECK_LAUNCH();
+}
+
+void tc_residual(ddg_handle h, int c, bool z_zero, int m) {
+    const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
+    if (a1 <= a0) return;
+    const int N = tc_n_for(m);
+    const unsigned blocks = (unsigned)(((a1 - a0) * m + 255) / 256);
+    MultiWork& w = h->mw;
+#define TC_RES(SK)                                                                                          \
+    tc_residual_kernel<SK><<<blocks, 256, 0, h->stream>>>(a0, a1, m, N, h->ov_nodes, h->tc.ov_sub,        \
+                                                          h->ov_off, h->tc.xoff, h->rowptr, h->col,         \
+                                                          h->val32, w.r32, w.z32, h->tc.X, z_zero, h->nx,   \
+                                                          h->ny, h->nz)
+    if (h->stencil_kind == DDG_STENCIL_7PT_3D) TC_RES(DDG_STENCIL_7PT_3D);
+    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) TC_RES(DDG_STENCIL_5PT_2D);
+    else TC_RES(DDG_STENCIL_NONE);
+#undef TC_RES
+    DDG_CHECK_LAUNCH();
+}
+
+void tc_local_solve(ddg_handle h, int c, int m) {
+    const int i0 = h->tc.h_citem_off[c], i1 = h->tc.h_citem_off[c + 1];
+    if (i1 <= i0) return;
+    switch (tc_n_for(m)) {
+        case 16: launch_tc<16>(h, i0, i1, m); break;
+        case 32: launch_tc<32>(h, i0, i1, m); break;
+        case 48: launch_tc<48>(h, i0, i1, m); break;
+        default: launch_tc<64>(h, i0, i1, m); break;
+    }
+}
+
+}  // namespace ddg

@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("keep_precisions", ctypes.c_int),
                 ("overlap_mode", ctypes.c_int), ("beta", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("use_coarse", ctypes.c_int), ("rank_tol", ctypes.c_double),
-                ("chunk_tiles", ctypes.c_int)]
+                ("chunk_tiles", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -150,7 +150,8 @@ class Solver:
 
     def __init__(self, A, part, F, overlap, *, mode="graph", shape=None, stencil_kind=0,
                  coef=None, dofs_per_node=1, precision="fp64", keep=None, beta="auto",
-                 maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, stream=None):
+                 maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
+                 stream=None):
         import torch
         lib = load()
         if not torch.cuda.is_available():
@@ -188,6 +189,7 @@ class Solver:
         o.use_coarse = 1 if use_coarse else 0
         o.rank_tol = rank_tol
         o.chunk_tiles = chunk_tiles
+        o.tensor_cores = 1 if tensor_cores else 0
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream

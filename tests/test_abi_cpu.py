@@ -35,8 +35,8 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "ddg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu\\n", sizeof(ddg_options), offsetof(ddg_options, rank_tol),
-         offsetof(ddg_options, chunk_tiles), sizeof(ddg_matrix));
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(ddg_options), offsetof(ddg_options, rank_tol),
+         offsetof(ddg_options, chunk_tiles), offsetof(ddg_options, tensor_cores), sizeof(ddg_matrix));
   printf("%zu %zu %zu\\n", offsetof(ddg_matrix, coef), sizeof(ddg_info), offsetof(ddg_info, setup_ms));
   return 0;
 }
@@ -46,7 +46,7 @@ int main(void) {
     out = subprocess.check_output([str(exe)]).decode().split()
     got = [int(x) for x in out]
     exp = [ctypes.sizeof(ddg.Options), ddg.Options.rank_tol.offset, ddg.Options.chunk_tiles.offset,
-           ctypes.sizeof(ddg.Matrix), ddg.Matrix.coef.offset, ctypes.sizeof(ddg.Info),
+           ddg.Options.tensor_cores.offset, ctypes.sizeof(ddg.Matrix), ddg.Matrix.coef.offset, ctypes.sizeof(ddg.Info),
            ddg.Info.setup_ms.offset]
     assert got == exp
 

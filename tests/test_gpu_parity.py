@@ -168,6 +168,32 @@ def test_batched_solve_matches_oracle_per_column(name, m, prec):
             assert its[j] <= ref.iters + 3, (j, its[j], ref.iters)
 
 
+_tc_cache = {}
+
+
+@pytest.mark.parametrize("name,m", [("varcoef_16", 64), ("varcoef_16", 5), ("poisson3d_ragged", 33),
+                                    ("poisson2d_64", 16), ("poisson3d_graph", 48)])
+def test_batched_tensor_core_solve_matches_oracle(name, m):
+    # tcgen05 BF16 local solves (residual and A_i^{-1} rounded to BF16, FP32
+    # accumulation) inside the FP32 preconditioner, FP64 CG per column
+    from paper_1504_00907_gb300 import ddg
+    prob, _, oracle = setup_case(name)
+    if name not in _tc_cache:
+        _tc_cache[name] = ddg.Solver.from_problem(prob, precision="bf16", keep=("bf16",),
+                                                  tensor_cores=True)
+    solver = _tc_cache[name]
+    F = di.normal_rhs(prob.n, 90 + m, m)
+    U, its, rrs, st = solver.solve_batch(dev(F), tol=1e-8)
+    assert st == 0 and np.all(rrs <= 1e-8)
+    Un = U.cpu().numpy()
+    for j in sorted({0, m // 2, m - 1}):
+        f = F[:, j]
+        assert np.linalg.norm(f - prob.A @ Un[:, j]) / np.linalg.norm(f) <= 1e-8
+        ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
+        assert rel(Un[:, j], ref.u) <= 1e-7, j
+        assert its[j] <= ref.iters + 3, (j, its[j], ref.iters)
+
+
 def test_batched_zero_column_and_single_solve_agree():
     prob, solver, _ = setup_case("poisson3d_24")
     solver.set_precision("fp32")
