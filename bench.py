@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--batched-size", type=int, default=96,
                     help="grid of the multi-RHS arm (0 skips it)")
     ap.add_argument("--batched-m", type=int, default=64)
+    ap.add_argument("--uneven", type=int, default=1, help="run the uneven 24-problem arm (0 skips it)")
     ap.add_argument("--keep", default="fp64,fp32,bf16",
                     help="local-inverse precisions kept at setup (profiling runs keep fewer)")
     return ap.parse_args()
@@ -206,6 +207,26 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
         out[key] = {"ms": ms, "status": int(st), "iters_mean": float(its.mean()),
                      "iters_max": int(its.max()), "max_true_relres": float(rrs.max()),
                      "dof_iters_per_s": world * prob.n * float(its.sum()) / (ms / 1e3)}
+    # breakdown of one tensor-core batched solve, every kernel class event-timed
+    solver.set_precision("bf16")
+    solver.profile(ddg.KERNEL_CLASSES)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.solve_batch(F, TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = solver.kernel_stats()
+    out["breakdown_bf16_tc"] = {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in st.items()}
+    out["breakdown_bf16_tc"]["total_ms_with_events"] = e0.elapsed_time(e1)
+    ls = st["local_solve"]
+    if ls["timed"]:
+        pk = peaks()
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        ach = ls["bytes"] / (ls["ms"] / 1e3) / 1e9
+        out["roofline_tc_local_solve"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                          "frac": ach / peak, "launches": ls["timed"],
+                                          "avg_launch_ms": ls["ms"] / ls["timed"],
+                                          "algorithmic_bytes_per_launch": ls["bytes"] / ls["timed"]}
     # the first few columns one at a time, same precision
     solver.set_precision("fp32")
     k1 = min(4, m)
@@ -223,6 +244,57 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
     out["single_rhs_fp32"] = {"ms_per_rhs": ms1 / k1, "dof_iters_per_s": prob.n * tot_it / (ms1 / 1e3)}
     solver.close()
     return out
+
+
+def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
+    """24 independent problems of uneven sizes: 16 3D Poisson (n in
+    {32,48,64,80}^3, 4 each, 8^3 boxes + overlap 1, p <= 2) and 8 clamped 2D
+    biharmonic (256^2 x3, 512^2 x3, 1024^2 x2, 16^2 boxes + overlap 2, p <= 3),
+    f ~ U(-1, 1) from seed 100 + index, FP32 preconditioner, FP64 CG, tol 1e-8;
+    one after another on one stream, then concurrently (ddg_solve_many, one
+    stream per problem)."""
+    probs = []
+    for i, N in enumerate([32, 48, 64, 80] * 4):
+        probs.append(di.make_poisson3d(N=N, box=8, overlap=1, p=2, seed=100 + i))
+    for i, N in enumerate([256, 256, 256, 512, 512, 512, 1024, 1024]):
+        probs.append(di.make_biharmonic2d(N=N, box=16, overlap=2, p=3, seed=116 + i))
+    streams = [torch.cuda.Stream(device=dev) for _ in probs]
+    t0 = time.perf_counter()
+    solvers = [ddg.Solver.from_problem(p, precision="fp32", keep=("fp32",), stream=s.cuda_stream)
+               for p, s in zip(probs, streams)]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    rhs = [torch.tensor(p.f, dtype=torch.float64, device=dev) for p in probs]
+    dofs = sum(p.n for p in probs)
+    # warm-up (graph capture per solver)
+    outs, its, rrs, st = ddg.solve_many(solvers, rhs, TOL)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    tot_seq = 0
+    seq_status = []
+    for s, f in zip(solvers, rhs):
+        _, it, rr, st1 = s.solve(f, TOL)
+        tot_seq += it
+        seq_status.append(int(st1))
+    torch.cuda.synchronize()
+    seq_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    t0 = time.perf_counter()
+    outs, its, rrs, st = ddg.solve_many(solvers, rhs, TOL)
+    torch.cuda.synchronize()
+    conc_s = max_over_ranks(time.perf_counter() - t0)
+    work = sum(p.n * int(i) for p, i in zip(probs, its))
+    res = {"workload": "16 x 3D Poisson (32..80)^3 + 8 x 2D biharmonic 256^2..1024^2",
+           "problems": len(probs), "dofs_total": dofs, "setup_s": setup_s,
+           "status": int(st), "iters": [int(i) for i in its], "max_true_relres": float(rrs.max()),
+           "sequential_s": seq_s, "concurrent_s": conc_s,
+           "dof_iters_per_s_concurrent": world * work / conc_s,
+           "dof_iters_per_s_sequential": world * work / seq_s,
+           "speedup_concurrent": seq_s / conc_s, "sequential_status": seq_status}
+    for s in solvers:
+        s.close()
+    return res
 
 
 def main():
@@ -365,6 +437,10 @@ def main():
     if args.batched_size > 0:
         batched = batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
 
+    uneven = None
+    if args.uneven:
+        uneven = uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
@@ -390,6 +466,7 @@ def main():
         "roofline": roofline,
         "breakdown_one_mixed_solve": breakdown,
         "batched": batched,
+        "uneven_batch": uneven,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -160,6 +160,18 @@ ddg_status ddg_solve_host(ddg_handle h, const double* f_host, double* u_host, do
 ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, double tol,
                            int* iters, double* relres);
 
+/*
+ * Many independent problems of uneven sizes at once: problem p (handle
+ * hs[p], which must be distinct handles, each with its own stream for the
+ * problems to overlap on the GPU) solves F[p] (device FP64 [n_p * m[p]],
+ * dof-major) into U[p], as ddg_solve_batch would (m[p] = 1: ddg_solve).
+ * The problems run concurrently from one host thread each.  iters / relres:
+ * host arrays of sum(m) entries (problem-major) or NULL.  Returns the first
+ * non-OK status of any problem (its message: ddg_last_error(hs[p])).
+ */
+ddg_status ddg_solve_many(ddg_handle* hs, int nprob, const double* const* F, double* const* U,
+                          const int* m, double tol, int* iters, double* relres);
+
 /* Adjoint solve lambda = A^{-T} g for a loss gradient g = dL/du (device
  * [n]); A is symmetric, so this reuses the preconditioner and CG. */
 ddg_status ddg_adjoint(ddg_handle h, const double* dLdu, double* lambda, double tol,

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -387,10 +388,7 @@ ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol
     };
     upload();
     auto precond_and_p = [&]() {
-        {
-            ProfScope ps(h, DDG_K_LOCAL_SOLVE, 1, 0.0);
-            ddg::multi_apply(h, m);
-        }
+        ddg::multi_apply(h, m);
         ProfScope ps(h, DDG_K_CG, 2, 0.0);
         ddg::multi_dots(h, m, pr);
         ddg::multi_update_p(h, m);
@@ -574,6 +572,8 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         const int64_t n = A->n;
         h->n = n;
         h->nnz = A->rowptr[n];
+        for (int64_t g = 0; g < n; ++g)
+            h->max_row_nnz = std::max<int>(h->max_row_nnz, (int)(A->rowptr[g + 1] - A->rowptr[g]));
         h->stencil_kind = A->stencil_kind;
         h->dim = A->dim;
         h->nx = A->nx > 0 ? A->nx : 1;
@@ -741,6 +741,15 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
                 xo[q + 1] = xo[q] + Tq[q];
                 for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) ovs[a] = q;
             }
+            std::vector<int2> tsl;
+            h->tc.h_cslab_off.assign(h->ncol + 1, 0);
+            for (int c = 0; c < h->ncol; ++c) {
+                for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q)
+                    for (int J = 0; J < Tq[q]; ++J) tsl.push_back(make_int2(q, J));
+                h->tc.h_cslab_off[c + 1] = (int)tsl.size();
+            }
+            h->tc.slabs = h->arena.alloc<int2>(tsl.size());
+            h2d(h->tc.slabs, tsl.data(), tsl.size(), h->stream);
             h->tc.slab_off = h->arena.alloc<int64_t>(nsub + 1);
             h->tc.xoff = h->arena.alloc<int64_t>(nsub + 1);
             h->tc.ov_sub = h->arena.alloc<int32_t>(h->sum_local);
@@ -955,6 +964,32 @@ ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, doub
         DDG_CUDA(cudaStreamSynchronize(h->stream));
         return worst;
     });
+}
+
+ddg_status ddg_solve_many(ddg_handle* hs, int nprob, const double* const* F, double* const* U,
+                          const int* m, double tol, int* iters, double* relres) {
+    if (!hs || !F || !U || !m || nprob < 1) return DDG_EINVAL;
+    for (int p = 0; p < nprob; ++p) {
+        if (!hs[p] || !F[p] || !U[p] || m[p] < 1) return DDG_EINVAL;
+        for (int q = 0; q < p; ++q)
+            if (hs[q] == hs[p]) return DDG_EINVAL;   // a handle serves one thread
+    }
+    std::vector<int64_t> off(nprob + 1, 0);
+    for (int p = 0; p < nprob; ++p) off[p + 1] = off[p] + m[p];
+    std::vector<ddg_status> st(nprob, DDG_OK);
+    std::vector<std::thread> th;
+    th.reserve(nprob);
+    for (int p = 0; p < nprob; ++p)
+        th.emplace_back([&, p]() {
+            int* it = iters ? iters + off[p] : nullptr;
+            double* rr = relres ? relres + off[p] : nullptr;
+            if (m[p] == 1) st[p] = ddg_solve(hs[p], F[p], U[p], tol, it, rr);
+            else st[p] = ddg_solve_batch(hs[p], F[p], U[p], m[p], tol, it, rr);
+        });
+    for (auto& t : th) t.join();
+    for (int p = 0; p < nprob; ++p)
+        if (st[p] != DDG_OK) return st[p];
+    return DDG_OK;
 }
 
 ddg_status ddg_adjoint(ddg_handle h, const double* dLdu, double* lambda, double tol, int* iters,

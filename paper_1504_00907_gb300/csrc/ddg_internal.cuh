@@ -92,6 +92,17 @@ static inline void d2h(T* dst, const T* src, size_t count, cudaStream_t s) {
     if (count) DDG_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
 }
 
+// kernel flavour of the A z products: the matrix-free Laplacians, or the CSR
+// path with rows unrolled when they are short (see dev_common.cuh)
+#define DDG_DISPATCH_SK(h, CALL)                                                  \
+    do {                                                                          \
+        if ((h)->stencil_kind == DDG_STENCIL_7PT_3D) { CALL(DDG_STENCIL_7PT_3D); } \
+        else if ((h)->stencil_kind == DDG_STENCIL_5PT_2D) { CALL(DDG_STENCIL_5PT_2D); } \
+        else if ((h)->max_row_nnz <= 8) { CALL(100); }                             \
+        else if ((h)->max_row_nnz <= 16) { CALL(101); }                            \
+        else { CALL(DDG_STENCIL_NONE); }                                           \
+    } while (0)
+
 // device scalar slots of the CG recurrence (FP64)
 enum {
     S_RZ = 0,      // rho_k = r_k^T z_k
@@ -132,6 +143,8 @@ struct MultiWork {
     int* restart = nullptr;       // [DDG_MCHUNK]
     int2* items = nullptr;        // (sweep position, tile row) per colour
     std::vector<int> h_citem_off;
+    float* gpart = nullptr;       // split partials of the coarse GEMMs
+    unsigned* gtick = nullptr;    // one ticket per 32-row tile
 };
 
 // tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}
@@ -143,6 +156,8 @@ struct TcData {
     int32_t* ov_sub = nullptr;     // [sum_local] sweep position of each local row
     int2* items = nullptr;         // (sweep position, 128-row block) per colour
     std::vector<int> h_citem_off;
+    int2* slabs = nullptr;         // (sweep position, 32-row K slab) per colour
+    std::vector<int> h_cslab_off;
     int64_t x_elems = 0;
     int last_m = -1;
 };
@@ -157,6 +172,7 @@ struct ddg_handle_s {
 
     // ---- fine problem
     int64_t n = 0, nnz = 0;
+    int max_row_nnz = 0;        // longest CSR row (selects the unrolled row kernels)
     int stencil_kind = 0, dim = 0, nx = 1, ny = 1, nz = 1, dpn = 1;
     int64_t* rowptr = nullptr;
     int32_t* col = nullptr;

@@ -60,4 +60,31 @@ __device__ __forceinline__ void block_sum32(V (&v)[32], V* sh, V* out) {
     __syncthreads();
 }
 
+// Pseudo stencil kinds of the CSR path: rows of at most 8 / 16 entries are
+// applied fully unrolled so that all column and value loads of a row, then
+// all x loads, are in flight together (same summation order as the loop).
+constexpr int SK_CSR8 = 100;
+constexpr int SK_CSR16 = 101;
+
+template <int NMAX, typename V, typename AV>
+__device__ __forceinline__ V csr_row_dot_unrolled(int g, const int64_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const AV* __restrict__ val, const V* __restrict__ x,
+                                                  int stride, int c) {
+    const int64_t e0 = rowptr[g];
+    const int cnt = (int)(rowptr[g + 1] - e0);
+    int cl[NMAX];
+    V vl[NMAX];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        cl[i] = i < cnt ? col[e0 + i] : 0;
+        vl[i] = i < cnt ? (V)val[e0 + i] : (V)0;
+    }
+    V s = 0;
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i)
+        if (i < cnt) s = fma(vl[i], x[(int64_t)cl[i] * stride + c], s);
+    return s;
+}
+
 }  // namespace ddgdev

@@ -464,6 +464,10 @@ __global__ void __launch_bounds__(256) coarse_restrict_kernel(
                     if (k < nz - 1) az -= z[g + nx * ny];
                 }
                 w -= az;
+            } else if (SK == ddgdev::SK_CSR8) {
+                w -= ddgdev::csr_row_dot_unrolled<8>(g, rowptr, col, val, z, 1, 0);
+            } else if (SK == ddgdev::SK_CSR16) {
+                w -= ddgdev::csr_row_dot_unrolled<16>(g, rowptr, col, val, z, 1, 0);
             } else {
                 for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) w -= (V)val[e] * z[col[e]];
             }
@@ -660,9 +664,9 @@ static void launch_restrict(ddg_handle h, int prec, bool residual) {
 }
 
 void coarse_restrict(ddg_handle h, int prec, bool residual) {
-    if (h->stencil_kind == DDG_STENCIL_7PT_3D) launch_restrict<DDG_STENCIL_7PT_3D>(h, prec, residual);
-    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) launch_restrict<DDG_STENCIL_5PT_2D>(h, prec, residual);
-    else launch_restrict<DDG_STENCIL_NONE>(h, prec, residual);
+#define CR_CALL(SK) launch_restrict<SK>(h, prec, residual)
+    DDG_DISPATCH_SK(h, CR_CALL);
+#undef CR_CALL
 }
 
 template <typename V>

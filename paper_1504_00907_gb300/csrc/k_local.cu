@@ -310,6 +310,10 @@ __device__ __forceinline__ V residual_at(int g, const int64_t* __restrict__ rowp
             if (k < nz - 1) az -= z[g + nx * ny];
         }
         s -= az;
+    } else if (SK == ddgdev::SK_CSR8) {
+        s -= ddgdev::csr_row_dot_unrolled<8>(g, rowptr, col, val, z, 1, 0);
+    } else if (SK == ddgdev::SK_CSR16) {
+        s -= ddgdev::csr_row_dot_unrolled<16>(g, rowptr, col, val, z, 1, 0);
     } else {
         for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s -= (V)val[e] * z[col[e]];
     }
@@ -522,9 +526,9 @@ static void launch_residual(ddg_handle h, int64_t a0, int64_t a1, bool z_zero, i
 void local_residual(ddg_handle h, int c, bool z_zero, int prec) {
     const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
     if (a1 <= a0) return;
-    if (h->stencil_kind == DDG_STENCIL_7PT_3D) launch_residual<DDG_STENCIL_7PT_3D>(h, a0, a1, z_zero, prec);
-    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) launch_residual<DDG_STENCIL_5PT_2D>(h, a0, a1, z_zero, prec);
-    else launch_residual<DDG_STENCIL_NONE>(h, a0, a1, z_zero, prec);
+#define LR_CALL(SK) launch_residual<SK>(h, a0, a1, z_zero, prec)
+    DDG_DISPATCH_SK(h, LR_CALL);
+#undef LR_CALL
 }
 
 template <typename E, typename V>

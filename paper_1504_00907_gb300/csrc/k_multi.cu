@@ -33,6 +33,8 @@ __device__ __forceinline__ V apply_row(int g, int c, int m, const int64_t* __res
         }
         return az;
     }
+    if (SK == ddgdev::SK_CSR8) return ddgdev::csr_row_dot_unrolled<8>(g, rowptr, col, val, z, m, c);
+    if (SK == ddgdev::SK_CSR16) return ddgdev::csr_row_dot_unrolled<16>(g, rowptr, col, val, z, m, c);
     V s = 0;
     for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma((V)val[e], z[(int64_t)col[e] * m + c], s);
     return s;
@@ -65,12 +67,30 @@ __device__ bool reduce_cols(double (&v)[NV], int m, double* partials, unsigned* 
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if ((int)threadIdx.x < m)
-        for (int q = 0; q < NV; ++q) {
+    // the rpb thread groups of a column sum interleaved blocks with four
+    // independent accumulators, then the groups combine in group order
+    const int gq = threadIdx.x / m, cc = threadIdx.x % m;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        unsigned b = gq;
+        const unsigned step = (unsigned)rpb;
+        for (; b + 3 * step < gridDim.x; b += 4 * step) {
+            s0 += __ldcg(partials + ((size_t)b * NV + q) * m + cc);
+            s1 += __ldcg(partials + ((size_t)(b + step) * NV + q) * m + cc);
+            s2 += __ldcg(partials + ((size_t)(b + 2 * step) * NV + q) * m + cc);
+            s3 += __ldcg(partials + ((size_t)(b + 3 * step) * NV + q) * m + cc);
+        }
+        for (; b < gridDim.x; b += step) s0 += __ldcg(partials + ((size_t)b * NV + q) * m + cc);
+        __syncthreads();
+        sh[threadIdx.x] = (s0 + s1) + (s2 + s3);
+        __syncthreads();
+        if ((int)threadIdx.x < m) {
             double s = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(partials + ((size_t)b * NV + q) * m + threadIdx.x);
+            for (int r = 0; r < rpb; ++r) s += sh[r * m + threadIdx.x];
             tot[q] = s;
         }
+    }
     if (threadIdx.x == 0) *counter = 0u;
     return true;
 }
@@ -167,13 +187,16 @@ __global__ void __launch_bounds__(MT) dots_multi_kernel(int64_t n, int m, const 
     }
 }
 
+// element kernels over n x m blocks: block = rpb rows x m columns, so the
+// column is threadIdx.x % m and no per-element 64-bit division is needed
 template <typename ZV>
 __global__ void update_p_multi_kernel(int64_t n, int m, double* __restrict__ P, const ZV* __restrict__ Z,
                                       const double* __restrict__ sc, const int* __restrict__ active) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * m) return;
-    const int c = (int)(e % m);
-    if (!active[c]) return;
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m;
+    const int64_t g = (int64_t)blockIdx.x * rpb + threadIdx.x / m;
+    if (g >= n || !active[c]) return;
+    const int64_t e = g * m + c;
     P[e] = fma(sc[S_BETA * DDG_MCHUNK + c], P[e], (double)Z[e]);
 }
 
@@ -203,9 +226,11 @@ __global__ void __launch_bounds__(MT) resnorm_multi_kernel(int64_t n, int m, con
 // copy the columns with replace[c] != 0 from src into dst (restart with the true residual)
 __global__ void replace_cols_kernel(int64_t n, int m, const double* __restrict__ src, double* __restrict__ dst,
                                     const int* __restrict__ replace) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * m) return;
-    if (replace[e % m]) dst[e] = src[e];
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m;
+    const int64_t g = (int64_t)blockIdx.x * rpb + threadIdx.x / m;
+    if (g >= n || !replace[c]) return;
+    dst[g * m + c] = src[g * m + c];
 }
 
 // dst[g, k0 + t] = src[g, j0 + t] for t < cnt (column blocks of dof-major arrays)
@@ -230,10 +255,10 @@ __global__ void local_residual_multi_kernel(int64_t a0, int64_t a1, int m, const
                                             const int32_t* __restrict__ col, const float* __restrict__ val,
                                             const float* __restrict__ r, const float* __restrict__ z,
                                             float* __restrict__ res, int z_zero, int nx, int ny, int nz) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (a1 - a0) * m) return;
-    const int64_t a = a0 + e / m;
-    const int c = (int)(e % m);
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m;
+    const int64_t a = a0 + (int64_t)blockIdx.x * rpb + threadIdx.x / m;
+    if (a >= a1) return;
     const int g = ov_nodes[a];
     float s = r[(int64_t)g * m + c];
     if (!z_zero) s -= apply_row<SK, float, float>(g, c, m, rowptr, col, val, z, nx, ny, nz);
@@ -295,8 +320,9 @@ __global__ void __launch_bounds__(MT) local_solve_multi_kernel(
     }
 }
 
-// c[(coff_s + jj) m + col] = sum_{g in Omega_s} Q[g, jj] (r - A z)[g, col]
-template <int SK>
+// c[(coff_s + jj) m + col] = sum_{g in Omega_s} Q[g, jj] (r - A z)[g, col];
+// each thread keeps four nodes in flight (independent load chains)
+template <int SK, int KM>
 __global__ void __launch_bounds__(MT) coarse_restrict_multi_kernel(
     const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
@@ -306,20 +332,37 @@ __global__ void __launch_bounds__(MT) coarse_restrict_multi_kernel(
     const int s = blockIdx.x;
     const int groups = blockDim.x / m;
     const int c = threadIdx.x % m, gq = threadIdx.x / m;
-    float acc[DDG_KMAX];
+    float acc[KM];
 #pragma unroll
-    for (int jj = 0; jj < DDG_KMAX; ++jj) acc[jj] = 0.f;
-    if (gq < groups)
-        for (int64_t a = sub_off[s] + gq; a < sub_off[s + 1]; a += groups) {
-            const int g = sub_nodes[a];
-            const float w = r[(int64_t)g * m + c] - apply_row<SK, float, float>(g, c, m, rowptr, col, val, z, nx, ny, nz);
-            const float* qa = Q + a * kmax;
+    for (int jj = 0; jj < KM; ++jj) acc[jj] = 0.f;
+    const int64_t b0 = sub_off[s], b1 = sub_off[s + 1];
+    int64_t a = b0 + gq;
+    for (; a + 3 * groups < b1; a += 4 * groups) {
+        float w[4];
 #pragma unroll
-            for (int jj = 0; jj < DDG_KMAX; ++jj)
-                if (jj < kmax) acc[jj] = fma(qa[jj], w, acc[jj]);
+        for (int u = 0; u < 4; ++u) {
+            const int g = sub_nodes[a + u * groups];
+            w[u] = r[(int64_t)g * m + c] - apply_row<SK, float, float>(g, c, m, rowptr, col, val, z, nx, ny, nz);
         }
-    if (gq < groups)
-        for (int jj = 0; jj < kmax; ++jj) shm[(gq * kmax + jj) * m + c] = acc[jj];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float* qa = Q + (a + u * groups) * kmax;
+#pragma unroll
+            for (int jj = 0; jj < KM; ++jj)
+                if (jj < kmax) acc[jj] = fma(qa[jj], w[u], acc[jj]);
+        }
+    }
+    for (; a < b1; a += groups) {
+        const int g = sub_nodes[a];
+        const float w = r[(int64_t)g * m + c] - apply_row<SK, float, float>(g, c, m, rowptr, col, val, z, nx, ny, nz);
+        const float* qa = Q + a * kmax;
+#pragma unroll
+        for (int jj = 0; jj < KM; ++jj)
+            if (jj < kmax) acc[jj] = fma(qa[jj], w, acc[jj]);
+    }
+#pragma unroll
+    for (int jj = 0; jj < KM; ++jj)
+        if (jj < kmax) shm[(gq * kmax + jj) * m + c] = acc[jj];
     __syncthreads();
     const int ks = coff[s + 1] - coff[s];
     for (int e = threadIdx.x; e < ks * m; e += blockDim.x) {
@@ -330,53 +373,111 @@ __global__ void __launch_bounds__(MT) coarse_restrict_multi_kernel(
     }
 }
 
-// out[i, c] = (a ? a[i, c] : 0) + sign sum_j M[i][j] x[j, c]; one block per row
-__global__ void __launch_bounds__(MT) profile_gemm_kernel(const int64_t* __restrict__ rowptr,
-                                                          const int32_t* __restrict__ lo,
-                                                          const int32_t* __restrict__ hi,
-                                                          const float* __restrict__ vals, int r0,
-                                                          const float* __restrict__ x,
-                                                          const float* __restrict__ a, float sign,
-                                                          float* __restrict__ out, int m) {
-    __shared__ float sh[MT];
-    const int i = r0 + blockIdx.x;
-    const int splits = blockDim.x / m;
-    const int c = threadIdx.x % m, sp = threadIdx.x / m;
-    const int l = lo[i], h = hi[i];
-    const float* rv = vals + rowptr[i] - l;
-    float s = 0.f;
-    if (sp < splits)
-        for (int j = l + sp; j < h; j += splits) s = fma(rv[j], x[(int64_t)j * m + c], s);
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    if ((int)threadIdx.x < m) {
-        float t = 0.f;
-        for (int q = 0; q < splits; ++q) t += sh[q * m + threadIdx.x];
-        const int64_t e = (int64_t)i * m + threadIdx.x;
-        out[e] = (a ? a[e] : 0.f) + sign * t;
+// out[i, c] = (a ? a[i, c] : 0) + sign sum_j M[i][j] x[j, c] for the rows of
+// one super-block.  CTA (row tile of 32, column split of CG_KS): stages 32x32
+// pieces of M (zero outside each row's profile) and 32 x m pieces of x in
+// shared memory, 8 outputs per thread; partial sums go to scratch and the
+// last CTA of a row tile (ticket) adds the splits in split order.
+constexpr int CG_ROWS = 32, CG_KS = 128;
+
+__global__ void __launch_bounds__(MT) coarse_gemm_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+    const float* __restrict__ vals, int r0, int nrows, int cbase, int nsplit,
+    const float* __restrict__ x, const float* __restrict__ a, float sign, float* __restrict__ out, int m,
+    float* __restrict__ partial, unsigned* __restrict__ tickets) {
+    __shared__ float sM[CG_ROWS][33];
+    __shared__ float sX[32][DDG_MCHUNK];
+    __shared__ int rlo[CG_ROWS], rhi[CG_ROWS];
+    __shared__ int64_t rptr[CG_ROWS];
+    __shared__ bool last;
+    const int rt = blockIdx.x, sp = blockIdx.y;
+    const int row0 = r0 + rt * CG_ROWS;
+    const int t = threadIdx.x, r = t >> 3, cg = t & 7;
+    if (t < CG_ROWS) {
+        const int i = row0 + t;
+        rlo[t] = lo[i];
+        rhi[t] = hi[i];
+        rptr[t] = rowptr[i];
     }
+    __syncthreads();
+    const int c_lo = cbase + sp * CG_KS, c_hi = c_lo + CG_KS;
+    int ulo = c_hi, uhi = c_lo;
+    for (int q = 0; q < CG_ROWS; ++q)
+        if (rhi[q] > rlo[q]) {
+            ulo = min(ulo, max(rlo[q], c_lo));
+            uhi = max(uhi, min(rhi[q], c_hi));
+        }
+    float acc[DDG_MCHUNK / 8];
+#pragma unroll
+    for (int u = 0; u < DDG_MCHUNK / 8; ++u) acc[u] = 0.f;
+    for (int jc = c_lo + ((ulo - c_lo) & ~31); jc < uhi; jc += 32) {
+        for (int e = t; e < CG_ROWS * 32; e += MT) {
+            const int rr = e >> 5, jj = e & 31, j = jc + jj;
+            sM[rr][jj] = (j >= rlo[rr] && j < rhi[rr]) ? vals[rptr[rr] + (j - rlo[rr])] : 0.f;
+        }
+        for (int e = t; e < 32 * m; e += MT) {
+            const int jj = e / m, c = e % m;
+            sX[jj][c] = x[(int64_t)(jc + jj) * m + c];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int jj = 0; jj < 32; ++jj) {
+            const float mv = sM[r][jj];
+#pragma unroll
+            for (int u = 0; u < DDG_MCHUNK / 8; ++u)
+                if (cg + 8 * u < m) acc[u] = fma(mv, sX[jj][cg + 8 * u], acc[u]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < DDG_MCHUNK / 8; ++u)
+        if (cg + 8 * u < m) partial[((size_t)sp * nrows + rt * CG_ROWS + r) * m + cg + 8 * u] = acc[u];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) last = (atomicAdd(&tickets[rt], 1u) == (unsigned)nsplit - 1u);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int e = t; e < CG_ROWS * m; e += MT) {
+        const int rr = e / m, c = e % m;
+        const float* pp = partial + ((size_t)rt * CG_ROWS + rr) * m + c;
+        const size_t st = (size_t)nrows * m;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int q2 = 0;
+        for (; q2 + 3 < nsplit; q2 += 4) {
+            s0 += __ldcg(pp + (size_t)q2 * st);
+            s1 += __ldcg(pp + (size_t)(q2 + 1) * st);
+            s2 += __ldcg(pp + (size_t)(q2 + 2) * st);
+            s3 += __ldcg(pp + (size_t)(q2 + 3) * st);
+        }
+        for (; q2 < nsplit; ++q2) s0 += __ldcg(pp + (size_t)q2 * st);
+        const float s = (s0 + s1) + (s2 + s3);
+        const int64_t o = (int64_t)(row0 + rr) * m + c;
+        out[o] = (a ? a[o] : 0.f) + sign * s;
+    }
+    if (t == 0) tickets[rt] = 0u;
 }
 
 __global__ void coarse_prolong_multi_kernel(int64_t n, int m, const int32_t* __restrict__ part,
                                             const int32_t* __restrict__ pos, const float* __restrict__ Q,
                                             int kmax, const int32_t* __restrict__ coff,
                                             const float* __restrict__ y, float* __restrict__ z) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n * m) return;
-    const int64_t g = e / m;
-    const int c = (int)(e % m);
+    const int rpb = blockDim.x / m;
+    const int c = threadIdx.x % m;
+    const int64_t g = (int64_t)blockIdx.x * rpb + threadIdx.x / m;
+    if (g >= n) return;
     const int s = part[g];
     const int c0 = coff[s], ks = coff[s + 1] - c0;
     const float* qa = Q + (int64_t)pos[g] * kmax;
     float acc = 0.f;
     for (int jj = 0; jj < ks; ++jj) acc = fma(qa[jj], y[(int64_t)(c0 + jj) * m + c], acc);
-    z[e] += acc;
+    z[g * m + c] += acc;
 }
 
 inline unsigned grid_for(int64_t n, int m) {
     const int rpb = MT / m;
     int64_t b = (n + rpb - 1) / rpb;
-    if (b > DDG_RED_BLOCKS) b = DDG_RED_BLOCKS;
+    if (b > 4 * 152) b = 4 * 152;     // few partials: the final sum stays short
     return (unsigned)(b < 1 ? 1 : b);
 }
 
@@ -391,7 +492,7 @@ void multi_ensure(ddg_handle h, int m) {
                     (void*)w.r32, (void*)w.z32,
                     (void*)w.res32, (void*)w.c32, (void*)w.y32, (void*)w.t32, (void*)w.x32,
                     (void*)w.scal, (void*)w.partials, (void*)w.active, (void*)w.restart,
-                    (void*)w.items})
+                    (void*)w.items, (void*)w.gpart, (void*)w.gtick})
         if (p) h->arena.release(p);
     const int64_t n = h->n;
     w.R = h->arena.alloc<double>(n * m);
@@ -410,6 +511,12 @@ void multi_ensure(ddg_handle h, int m) {
     w.x32 = h->arena.alloc<float>(n0p * m);
     for (float* p : {w.c32, w.y32, w.t32, w.x32})
         DDG_CUDA(cudaMemsetAsync(p, 0, n0p * m * sizeof(float), h->stream));
+    if (h->use_coarse) {
+        const int nsplit = (h->B + CG_KS - 1) / CG_KS;
+        w.gpart = h->arena.alloc<float>((size_t)nsplit * h->B * m);
+        w.gtick = h->arena.alloc<unsigned>(h->B / CG_ROWS);
+        DDG_CUDA(cudaMemsetAsync(w.gtick, 0, (h->B / CG_ROWS) * sizeof(unsigned), h->stream));
+    }
     w.scal = h->arena.alloc<double>(S_COUNT * DDG_MCHUNK);
     w.partials = h->arena.alloc<double>((size_t)DDG_RED_BLOCKS * 2 * DDG_MCHUNK);
     w.active = h->arena.alloc<int>(DDG_MCHUNK);
@@ -433,6 +540,17 @@ void multi_ensure(ddg_handle h, int m) {
     w.m_alloc = m;
 }
 
+// algorithmic bytes of one tensor-core local-solve launch: the BF16 inverse
+// (n_i^2 * 2) plus the BF16 residual read and the FP32 z read + write
+static double tc_bytes(ddg_handle h, int c, int m) {
+    double b = 0.0;
+    for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
+        const double nq = (double)(h->h_ov_off[q + 1] - h->h_ov_off[q]);
+        b += nq * nq * 2.0 + nq * m * (2.0 + 8.0);
+    }
+    return b;
+}
+
 template <int SK>
 static void multi_apply_t(ddg_handle h, int m) {
     MultiWork& w = h->mw;
@@ -448,13 +566,19 @@ static void multi_apply_t(ddg_handle h, int m) {
     }
     auto local = [&](int c, bool zz) {
         if (tc) {
-            tc_residual(h, c, zz, m);
+            {
+                ProfScope ps(h, DDG_K_LOCAL_RESIDUAL, 1, 0.0);
+                tc_residual(h, c, zz, m);
+            }
+            ProfScope ps(h, DDG_K_LOCAL_SOLVE, 1, tc_bytes(h, c, m));
             tc_local_solve(h, c, m);
             return;
         }
         const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
+        ProfScope ps(h, DDG_K_LOCAL_SOLVE, 2, 0.0);
         if (a1 > a0) {
-            local_residual_multi_kernel<SK><<<(unsigned)(((a1 - a0) * m + 255) / 256), 256, 0, h->stream>>>(
+            const int bd = col_block(m), rpb = bd / m;
+            local_residual_multi_kernel<SK><<<(unsigned)((a1 - a0 + rpb - 1) / rpb), bd, 0, h->stream>>>(
                 a0, a1, m, h->ov_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, w.res32, zz, h->nx,
                 h->ny, h->nz);
         }
@@ -471,32 +595,42 @@ static void multi_apply_t(ddg_handle h, int m) {
     };
     for (int c = 0; c < h->ncol; ++c) local(c, c == 0);
     if (h->use_coarse) {
+        ProfScope ps(h, DDG_K_COARSE, 2 + 4 * h->nK - 2, 0.0);
         const int bd = col_block(m);
         const size_t smem = (size_t)(bd / m) * h->kmax * m * sizeof(float);
-        coarse_restrict_multi_kernel<SK><<<h->nsub, bd, smem, h->stream>>>(
-            h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff,
-            w.c32, m, h->nx, h->ny, h->nz);
+#define RESTRICT_MULTI(KM)                                                                              \
+    coarse_restrict_multi_kernel<SK, KM><<<h->nsub, bd, smem, h->stream>>>(                             \
+        h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff, \
+        w.c32, m, h->nx, h->ny, h->nz)
+        if (h->kmax <= 8) RESTRICT_MULTI(8);
+        else if (h->kmax <= 16) RESTRICT_MULTI(16);
+        else RESTRICT_MULTI(32);
+#undef RESTRICT_MULTI
         const int B = h->B, nK = h->nK;
-        auto gemm = [&](const ProfileMat& M, int r0, const float* x, const float* a, float sign, float* out) {
-            profile_gemm_kernel<<<B, bd, 0, h->stream>>>(M.rowptr, M.lo, M.hi, M.v32, r0, x, a, sign, out, m);
+        const int nsplit = (B + CG_KS - 1) / CG_KS;
+        const dim3 grid(B / CG_ROWS, nsplit);
+        auto gemm = [&](const ProfileMat& M, int r0, int cbase, const float* x, const float* a, float sign,
+                        float* out) {
+            coarse_gemm_kernel<<<grid, MT, 0, h->stream>>>(M.rowptr, M.lo, M.hi, M.v32, r0, B, cbase, nsplit,
+                                                           x, a, sign, out, m, w.gpart, w.gtick);
         };
         for (int K = 0; K < nK; ++K) {
             const float* in = w.c32;
             if (K > 0) {
-                gemm(h->Em, K * B, w.y32, w.c32, -1.f, w.t32);
+                gemm(h->Em, K * B, (K - 1) * B, w.y32, w.c32, -1.f, w.t32);
                 in = w.t32;
             }
-            gemm(h->Dm, K * B, in, nullptr, 1.f, w.y32);
+            gemm(h->Dm, K * B, K * B, in, nullptr, 1.f, w.y32);
         }
         for (int K = nK - 1; K >= 0; --K) {
             const float* in = w.y32;
             if (K < nK - 1) {
-                gemm(h->Et, K * B, w.x32, w.y32, -1.f, w.t32);
+                gemm(h->Et, K * B, (K + 1) * B, w.x32, w.y32, -1.f, w.t32);
                 in = w.t32;
             }
-            gemm(h->Dt, K * B, in, nullptr, 1.f, w.x32);
+            gemm(h->Dt, K * B, K * B, in, nullptr, 1.f, w.x32);
         }
-        coarse_prolong_multi_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, h->stream>>>(
+        coarse_prolong_multi_kernel<<<(unsigned)((n + bd / m - 1) / (bd / m)), bd, 0, h->stream>>>(
             n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);
         DDG_CHECK_LAUNCH();
     }
@@ -504,22 +638,20 @@ static void multi_apply_t(ddg_handle h, int m) {
 }
 
 void multi_apply(ddg_handle h, int m) {
-    if (h->stencil_kind == DDG_STENCIL_7PT_3D) multi_apply_t<DDG_STENCIL_7PT_3D>(h, m);
-    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) multi_apply_t<DDG_STENCIL_5PT_2D>(h, m);
-    else multi_apply_t<DDG_STENCIL_NONE>(h, m);
+#define MA_CALL(SK) multi_apply_t<SK>(h, m)
+    DDG_DISPATCH_SK(h, MA_CALL);
+#undef MA_CALL
 }
 
 void multi_spmv_pq(ddg_handle h, int m) {
     MultiWork& w = h->mw;
     const unsigned G = grid_for(h->n, m);
     const int bd = col_block(m);
-    const int sk = h->stencil_kind;
-    if (sk == DDG_STENCIL_7PT_3D)
-        spmv_multi_kernel<DDG_STENCIL_7PT_3D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, w.P, w.Q, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, w.active);
-    else if (sk == DDG_STENCIL_5PT_2D)
-        spmv_multi_kernel<DDG_STENCIL_5PT_2D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, w.P, w.Q, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, w.active);
-    else
-        spmv_multi_kernel<DDG_STENCIL_NONE><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, w.P, w.Q, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, w.active);
+#define MS_CALL(SK)                                                                                       \
+    spmv_multi_kernel<SK><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, w.P, w.Q, h->nx, \
+                                                   h->ny, h->nz, w.partials, h->red_counter, w.scal, w.active)
+    DDG_DISPATCH_SK(h, MS_CALL);
+#undef MS_CALL
     DDG_CHECK_LAUNCH();
 }
 
@@ -537,7 +669,8 @@ void multi_dots(ddg_handle h, int m, int pr) {
 
 void multi_update_p(ddg_handle h, int m) {
     MultiWork& w = h->mw;
-    update_p_multi_kernel<float><<<(unsigned)((h->n * m + 255) / 256), 256, 0, h->stream>>>(h->n, m, w.P, w.z32, w.scal, w.active);
+    const int bd = col_block(m), rpb = bd / m;
+    update_p_multi_kernel<float><<<(unsigned)((h->n + rpb - 1) / rpb), bd, 0, h->stream>>>(h->n, m, w.P, w.z32, w.scal, w.active);
     DDG_CHECK_LAUNCH();
 }
 
@@ -546,13 +679,11 @@ void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double
     MultiWork& w = h->mw;
     const unsigned G = grid_for(h->n, m);
     const int bd = col_block(m);
-    const int sk = h->stencil_kind;
-    if (sk == DDG_STENCIL_7PT_3D)
-        resnorm_multi_kernel<DDG_STENCIL_7PT_3D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, slot);
-    else if (sk == DDG_STENCIL_5PT_2D)
-        resnorm_multi_kernel<DDG_STENCIL_5PT_2D><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, slot);
-    else
-        resnorm_multi_kernel<DDG_STENCIL_NONE><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, h->ny, h->nz, w.partials, h->red_counter, w.scal, slot);
+#define MR_CALL(SK)                                                                                        \
+    resnorm_multi_kernel<SK><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, \
+                                                      h->ny, h->nz, w.partials, h->red_counter, w.scal, slot)
+    DDG_DISPATCH_SK(h, MR_CALL);
+#undef MR_CALL
     DDG_CHECK_LAUNCH();
 }
 
@@ -562,7 +693,8 @@ void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int
 }
 
 void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace) {
-    replace_cols_kernel<<<(unsigned)((h->n * m + 255) / 256), 256, 0, h->stream>>>(h->n, m, src, dst, replace);
+    const int bd = col_block(m), rpb = bd / m;
+    replace_cols_kernel<<<(unsigned)((h->n + rpb - 1) / rpb), bd, 0, h->stream>>>(h->n, m, src, dst, replace);
     DDG_CHECK_LAUNCH();
 }
 

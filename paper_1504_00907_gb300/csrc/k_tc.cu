@@ -17,6 +17,7 @@
 // Every wait is bounded: a wait that runs out sets the error flag, the kernel
 // drains its own copies (bounded), frees its TMEM and returns.
 #include "ddg_internal.cuh"
+#include "dev_common.cuh"
 
 namespace {
 
@@ -155,26 +156,35 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      :: "r"(sa(done)) : "memory");
     }
+    // the other lanes of the producer and MMA warps park here instead of
+    // polling `done` beside their role thread
+    __syncwarp();
     // epilogue: TMEM lanes [32 w, 32 w + 32) hold rows blk * 128 + 32 w + lane
     const bool have = mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!have) failed = 1;
     __syncthreads();
     if (!failed) {
-        const int row = blk * TC_M + warp * 32 + lane;
+        // TMEM -> shared tile [128][N + 1] (the stage ring is free: every
+        // copy has been consumed by an MMA that completed before `done`)
+        float* tile = reinterpret_cast<float*>(smem);
+        constexpr int LDS = N + 1;
+        const int rl = warp * 32 + lane;
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-        const int g = row < n ? ov_nodes[o + row] : 0;
 #pragma unroll
         for (int cb = 0; cb < N / 16; ++cb) {
             float v[16];
             tmem_ld16(taddr + cb * 16, v);
-            if (row < n) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int c = cb * 16 + i;
-                    if (c < m) z[(int64_t)g * m + c] += v[i];
-                }
-            }
+            for (int i = 0; i < 16; ++i) tile[rl * LDS + cb * 16 + i] = v[i];
+        }
+        __syncthreads();
+        // each warp updates its 32 rows of z, lanes along the columns
+        for (int rr = warp * 32; rr < warp * 32 + 32; ++rr) {
+            const int row = blk * TC_M + rr;
+            if (row >= n) break;
+            const int g = ov_nodes[o + row];
+            for (int c = lane; c < m; c += 32) z[(int64_t)g * m + c] += tile[rr * LDS + c];
         }
     } else if (threadIdx.x == 0) {
         atomicExch(err, 1);
@@ -219,42 +229,95 @@ __global__ void tc_pack_kernel(int q0, const double* __restrict__ ws, int Np,
     }
 }
 
-// (r - A z) at the colour's rows, all m columns, written as BF16 X^T slabs
+// (r - A z) at the colour's rows, all m columns, written as BF16 X^T slabs:
+// one CTA per (subdomain, 32-row slab); the residual is computed with
+// coalesced reads (consecutive threads = consecutive columns), staged in
+// shared memory and written out in core-matrix order with 16-byte stores.
 template <int SK>
-__global__ void tc_residual_kernel(int64_t a0, int64_t a1, int m, int N, const int32_t* __restrict__ ov_nodes,
-                                   const int32_t* __restrict__ ov_sub, const int64_t* __restrict__ ov_off,
-                                   const int64_t* __restrict__ xoff, const int64_t* __restrict__ rowptr,
-                                   const int32_t* __restrict__ col, const float* __restrict__ val,
-                                   const float* __restrict__ r, const float* __restrict__ z,
-                                   __nv_bfloat16* __restrict__ X, int z_zero, int nx, int ny, int nz) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (a1 - a0) * m) return;
-    const int64_t a = a0 + e / m;
-    const int c = (int)(e % m);
-    const int g = ov_nodes[a];
-    float s = r[(int64_t)g * m + c];
-    if (!z_zero) {
-        if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
-            const int i = g % nx, j = (g / nx) % ny;
-            float az = (SK == DDG_STENCIL_7PT_3D ? 6.f : 4.f) * z[(int64_t)g * m + c];
-            if (i > 0) az -= z[(int64_t)(g - 1) * m + c];
-            if (i < nx - 1) az -= z[(int64_t)(g + 1) * m + c];
-            if (j > 0) az -= z[(int64_t)(g - nx) * m + c];
-            if (j < ny - 1) az -= z[(int64_t)(g + nx) * m + c];
-            if (SK == DDG_STENCIL_7PT_3D) {
-                const int k = g / (nx * ny);
-                if (k > 0) az -= z[(int64_t)(g - nx * ny) * m + c];
-                if (k < nz - 1) az -= z[(int64_t)(g + nx * ny) * m + c];
+__global__ void __launch_bounds__(256) tc_residual_kernel(
+    const int2* __restrict__ slabs, int slab_base, int m, int N, const int32_t* __restrict__ ov_nodes,
+    const int64_t* __restrict__ ov_off, const int64_t* __restrict__ xoff,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
+    const float* __restrict__ r, const float* __restrict__ z, __nv_bfloat16* __restrict__ X, int z_zero,
+    int nx, int ny, int nz) {
+    __shared__ __nv_bfloat16 sx[TC_K][DDG_MCHUNK + 8];
+    // row metadata of the slab, shared by all m columns: node, and for the
+    // CSR path up to 16 (column, value) pairs per row
+    __shared__ int sg[TC_K], scnt[TC_K];
+    __shared__ int scol[TC_K][16];
+    __shared__ float sval[TC_K][16];
+    const int2 sl = slabs[slab_base + blockIdx.x];
+    const int q = sl.x, J = sl.y;
+    const int64_t o = ov_off[q];
+    const int n = (int)(ov_off[q + 1] - o);
+    constexpr bool csr = SK == ddgdev::SK_CSR8 || SK == ddgdev::SK_CSR16;
+    if (threadIdx.x < TC_K) {
+        const int la = J * TC_K + threadIdx.x;
+        const int g = la < n ? ov_nodes[o + la] : -1;
+        sg[threadIdx.x] = g;
+        if (csr) {
+            int cnt = 0;
+            if (g >= 0) {
+                const int64_t e0 = rowptr[g];
+                cnt = (int)(rowptr[g + 1] - e0);
+                for (int i = 0; i < cnt; ++i) {
+                    scol[threadIdx.x][i] = col[e0 + i];
+                    sval[threadIdx.x][i] = val[e0 + i];
+                }
             }
-            s -= az;
-        } else {
-            for (int64_t p = rowptr[g]; p < rowptr[g + 1]; ++p) s -= val[p] * z[(int64_t)col[p] * m + c];
+            scnt[threadIdx.x] = cnt;
         }
     }
-    const int q = ov_sub[a];
-    const int la = (int)(a - ov_off[q]);
-    const int J = la / TC_K, k = la % TC_K;
-    X[(xoff[q] + J) * (int64_t)(N * TC_K) + core_off(c, k)] = __float2bfloat16_rn(s);
+    __syncthreads();
+#pragma unroll 4
+    for (int e = threadIdx.x; e < TC_K * N; e += blockDim.x) {
+        const int kr = e / N, c = e % N;
+        const int g = sg[kr];
+        float s = 0.f;
+        if (g >= 0 && c < m) {
+            s = r[(int64_t)g * m + c];
+            if (!z_zero) {
+                if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+                    const int i = g % nx, j = (g / nx) % ny;
+                    float az = (SK == DDG_STENCIL_7PT_3D ? 6.f : 4.f) * z[(int64_t)g * m + c];
+                    if (i > 0) az -= z[(int64_t)(g - 1) * m + c];
+                    if (i < nx - 1) az -= z[(int64_t)(g + 1) * m + c];
+                    if (j > 0) az -= z[(int64_t)(g - nx) * m + c];
+                    if (j < ny - 1) az -= z[(int64_t)(g + nx) * m + c];
+                    if (SK == DDG_STENCIL_7PT_3D) {
+                        const int k = g / (nx * ny);
+                        if (k > 0) az -= z[(int64_t)(g - nx * ny) * m + c];
+                        if (k < nz - 1) az -= z[(int64_t)(g + nx * ny) * m + c];
+                    }
+                    s -= az;
+                } else if (csr) {
+                    constexpr int NMAX = SK == ddgdev::SK_CSR8 ? 8 : 16;
+                    const int cnt = scnt[kr];
+                    float acc = 0.f;
+#pragma unroll
+                    for (int i2 = 0; i2 < NMAX; ++i2)
+                        if (i2 < cnt) acc = fma(sval[kr][i2], z[(int64_t)scol[kr][i2] * m + c], acc);
+                    s -= acc;
+                } else {
+                    for (int64_t p = rowptr[g]; p < rowptr[g + 1]; ++p) s -= val[p] * z[(int64_t)col[p] * m + c];
+                }
+            }
+        }
+        sx[kr][c] = __float2bfloat16_rn(s);
+    }
+    __syncthreads();
+    // core-matrix rows: (n, kc) holds k = kc*8 .. kc*8+7 of column n, 16 bytes
+    uint4* dst = reinterpret_cast<uint4*>(X + (xoff[q] + J) * (int64_t)(N * TC_K));
+    for (int e = threadIdx.x; e < N * 4; e += blockDim.x) {
+        const int core_row = e;                   // ((nc * 4 + kc) * 8 + n % 8)
+        const int cm = core_row >> 3, nr = core_row & 7;
+        const int nc = cm >> 2, kc = cm & 3;
+        const int nn = nc * 8 + nr;
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v[t] = sx[kc * 8 + t][nn];
+        dst[e] = *reinterpret_cast<const uint4*>(v);
+    }
 }
 
 template <int N>
@@ -290,19 +353,15 @@ void tc_pack(ddg_handle h, int q0, int q1, const double* ws) {
 }
 
 void tc_residual(ddg_handle h, int c, bool z_zero, int m) {
-    const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
-    if (a1 <= a0) return;
+    const int s0 = h->tc.h_cslab_off[c], s1 = h->tc.h_cslab_off[c + 1];
+    if (s1 <= s0) return;
     const int N = tc_n_for(m);
-    const unsigned blocks = (unsigned)(((a1 - a0) * m + 255) / 256);
     MultiWork& w = h->mw;
-#define TC_RES(SK)                                                                                          \
-    tc_residual_kernel<SK><<<blocks, 256, 0, h->stream>>>(a0, a1, m, N, h->ov_nodes, h->tc.ov_sub,        \
-                                                          h->ov_off, h->tc.xoff, h->rowptr, h->col,         \
-                                                          h->val32, w.r32, w.z32, h->tc.X, z_zero, h->nx,   \
-                                                          h->ny, h->nz)
-    if (h->stencil_kind == DDG_STENCIL_7PT_3D) TC_RES(DDG_STENCIL_7PT_3D);
-    else if (h->stencil_kind == DDG_STENCIL_5PT_2D) TC_RES(DDG_STENCIL_5PT_2D);
-    else TC_RES(DDG_STENCIL_NONE);
+#define TC_RES(SK)                                                                                       \
+    tc_residual_kernel<SK><<<s1 - s0, 256, 0, h->stream>>>(h->tc.slabs, s0, m, N, h->ov_nodes, h->ov_off, \
+                                                           h->tc.xoff, h->rowptr, h->col, h->val32, w.r32, \
+                                                           w.z32, h->tc.X, z_zero, h->nx, h->ny, h->nz)
+    DDG_DISPATCH_SK(h, TC_RES);
 #undef TC_RES
     DDG_CHECK_LAUNCH();
 }

@@ -72,6 +72,7 @@ _SIGS = {
     "ddg_solve": (_I, [_P, _P, _P, _D, _PI, _PD]),
     "ddg_solve_host": (_I, [_P, _P, _P, _D, _PI, _PD]),
     "ddg_solve_batch": (_I, [_P, _P, _P, _I, _D, _P, _P]),
+    "ddg_solve_many": (_I, [_P, _I, _P, _P, _P, _D, _P, _P]),
     "ddg_adjoint": (_I, [_P, _P, _P, _D, _PI, _PD]),
     "ddg_grad_coeff": (_I, [_P, _P, _P, _P]),
     "ddg_apply_preconditioner": (_I, [_P, _P, _P]),
@@ -333,6 +334,43 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def solve_many(solvers, rhs, tol=1e-8):
+    """Solve independent problems of uneven sizes concurrently.
+
+    ``solvers``: distinct Solver objects (give each its own CUDA stream so the
+    problems overlap); ``rhs``: one CUDA float64 tensor per problem, [n] or
+    [n, m].  Returns (solutions, iterations per column, true relative
+    residual per column, status).
+    """
+    import torch
+    lib = load()
+    nprob = len(solvers)
+    hs = (ctypes.c_void_p * nprob)(*[s.h for s in solvers])
+    outs, fptr, uptr, ms = [], [], [], []
+    for s, f in zip(solvers, rhs):
+        if f.dim() == 1:
+            _dev(f, s.n, "f")
+            ms.append(1)
+        else:
+            _dev(f, None, "F")
+            ms.append(f.shape[1])
+        u = torch.empty_like(f)
+        outs.append(u)
+        fptr.append(f.data_ptr())
+        uptr.append(u.data_ptr())
+    tot = sum(ms)
+    its = np.zeros(tot, dtype=np.int32)
+    rr = np.zeros(tot, dtype=np.float64)
+    F = (ctypes.c_void_p * nprob)(*fptr)
+    U = (ctypes.c_void_p * nprob)(*uptr)
+    M = (ctypes.c_int * nprob)(*ms)
+    st = lib.ddg_solve_many(hs, nprob, F, U, M, tol, its.ctypes.data_as(ctypes.c_void_p),
+                            rr.ctypes.data_as(ctypes.c_void_p))
+    if st not in (DDG_OK, DDG_ENOCONV):
+        raise DDGError(st, "ddg_solve_many failed")
+    return outs, its, rr, st
 
 
 def solve_autograd(solver, kappa, f, tol=1e-10):

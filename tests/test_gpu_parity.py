@@ -211,6 +211,37 @@ def test_batched_zero_column_and_single_solve_agree():
     solver.set_precision("fp64")
 
 
+def test_solve_many_uneven_problems_concurrently():
+    # uneven multi-problem batch: different PDEs, sizes, precisions and RHS
+    # counts, each on its own stream, solved concurrently
+    from paper_1504_00907_gb300 import ddg
+    probs = [di.make_poisson3d(N=16, box=8, overlap=1, p=2, seed=101),
+             di.make_poisson3d(N=24, box=8, overlap=1, p=2, seed=102),
+             di.make_biharmonic2d(N=48, box=16, overlap=2, p=3, seed=103),
+             di.make_poisson2d(N=40, box=10, overlap=1, p=2, seed=104)]
+    streams = [torch.cuda.Stream() for _ in probs]
+    precs = ["fp32", "fp32", "fp64", "bf16"]
+    solvers = [ddg.Solver.from_problem(p, precision=pr, keep=(pr,), stream=s.cuda_stream)
+               for p, pr, s in zip(probs, precs, streams)]
+    rhs = [dev(probs[0].f), dev(di.normal_rhs(probs[1].n, 7, 3)), dev(probs[2].f), dev(probs[3].f)]
+    torch.cuda.synchronize()
+    outs, its, rrs, st = ddg.solve_many(solvers, rhs, tol=1e-8)
+    torch.cuda.synchronize()
+    assert st == 0 and np.all(rrs <= 1e-8)
+    k = 0
+    for p, f, u in zip(probs, rhs, outs):
+        F = f.cpu().numpy().reshape(p.n, -1)
+        Un = u.cpu().numpy().reshape(p.n, -1)
+        M = orc.DDGOracle(p.A, p.part, p.F, p.overlap, p.overlap_mode, p.shape)
+        for j in range(F.shape[1]):
+            ref = orc.pcg(M.A, F[:, j], M.apply, tol=1e-8)
+            assert rel(Un[:, j], ref.u) <= 1e-7
+            assert its[k] <= ref.iters + 3
+            k += 1
+    for s in solvers:
+        s.close()
+
+
 def test_solve_is_deterministic():
     prob, solver, _ = setup_case("poisson3d_24")
     for prec in ("fp64", "fp32", "bf16"):
