@@ -329,6 +329,16 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
         true_rel = std::sqrt(h->h_scal[S_TMP]) / fn;
     }
     h->u = nullptr;
+    {
+        int32_t tflag = 0;
+        d2h(&tflag, h->errflags + E_TIMEOUT, 1, h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        if (tflag) {
+            DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
+            h->err = "a bounded grid barrier of the coarse solve ran out";
+            st = DDG_ETIMEOUT;
+        }
+    }
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = true_rel;
     return st;
@@ -858,6 +868,9 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             h->Q32 = h->arena.alloc<float>((size_t)n * k);
             ddg::cast_q32(h);
             const int n0p = h->n0p;
+            h->cgbar = reinterpret_cast<ddgdev::GridBar*>(h->arena.alloc<unsigned>(2));
+            DDG_CUDA(cudaMemsetAsync(h->cgbar, 0, 2 * sizeof(unsigned), h->stream));
+            if (const char* ev = std::getenv("DDG_PERSISTENT_COARSE")) h->persistent_coarse = ev[0] == '1';
             h->c64 = h->arena.alloc<double>(n0p);
             h->y64 = h->arena.alloc<double>(n0p);
             h->t64 = h->arena.alloc<double>(n0p);

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "ddg.h"
+#include "dev_common.cuh"
 
 #define DDG_LT 32        // local-inverse tile edge
 #define DDG_CT 64        // coarse factor tile edge
@@ -230,6 +231,12 @@ struct ddg_handle_s {
     double* coarseW = nullptr;     // super-block inverses (setup only)
     ProfileMat Dm, Em, Dt, Et;
     double *c64 = nullptr, *y64 = nullptr, *t64 = nullptr, *x64 = nullptr;
+    // one cooperative launch per single-RHS coarse solve instead of 4 nK graph-
+    // replayed GEMV launches; off by default: on GB300 its 62 grid barriers
+    // cost more than the launch boundaries (3.75 vs 3.03 ms per solve on the
+    // 128^3 Poisson problem); DDG_PERSISTENT_COARSE=1 selects it
+    bool persistent_coarse = false;
+    ddgdev::GridBar* cgbar = nullptr;  // its grid barrier
     float *c32 = nullptr, *y32 = nullptr, *t32 = nullptr, *x32 = nullptr;
 
     // ---- CG workspace (FP64) and preconditioner vectors

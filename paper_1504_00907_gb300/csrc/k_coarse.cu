@@ -433,6 +433,59 @@ __global__ void __launch_bounds__(GEMV_TPR) profile_gemv_kernel(
     }
 }
 
+// The whole single-RHS coarse recurrence in one cooperative launch: in every
+// step each warp takes rows of the step's profile matrix (16-byte loads of
+// the aligned rows) and writes out[i] = a[i] + sign * (M x)[i]; a bounded grid
+// barrier separates the steps.
+template <typename V>
+__global__ void __launch_bounds__(512) coarse_gemv_persistent_kernel(
+    ProfileMat Dm, ProfileMat Em, ProfileMat Dt, ProfileMat Et, int B, int nK, const V* __restrict__ c,
+    V* y, V* t, V* x, ddgdev::GridBar* gb, int* err) {
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    auto vals = [](const ProfileMat& M) -> const V* {
+        return sizeof(V) == 8 ? reinterpret_cast<const V*>(M.v64) : reinterpret_cast<const V*>(M.v32);
+    };
+    auto step = [&](const ProfileMat& M, int r0, const V* xin, const V* a, V sign, V* out) -> bool {
+        const V* mv = vals(M);
+        for (int i = r0 + wid; i < r0 + B; i += nw) {
+            const int l = M.lo[i];
+            const int nch = (M.hi[i] - l) >> 2;
+            const V* rv = mv + M.rowptr[i];
+            const V* xv = xin + l;
+            V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            int ch = lane;
+            for (; ch + 96 < nch; ch += 128) {
+                s0 += Vec4<V>::dot(rv + 4 * ch, xv + 4 * ch);
+                s1 += Vec4<V>::dot(rv + 4 * (ch + 32), xv + 4 * (ch + 32));
+                s2 += Vec4<V>::dot(rv + 4 * (ch + 64), xv + 4 * (ch + 64));
+                s3 += Vec4<V>::dot(rv + 4 * (ch + 96), xv + 4 * (ch + 96));
+            }
+            for (; ch < nch; ch += 32) s0 += Vec4<V>::dot(rv + 4 * ch, xv + 4 * ch);
+            const V s = ddgdev::warp_sum((s0 + s1) + (s2 + s3));
+            if (lane == 0) out[i] = (a ? a[i] : (V)0) + sign * s;
+        }
+        return ddgdev::grid_barrier(gb, gridDim.x, err);
+    };
+    for (int K = 0; K < nK; ++K) {
+        const V* in = c;
+        if (K > 0) {
+            if (!step(Em, K * B, y, c, (V)-1, t)) return;
+            in = t;
+        }
+        if (!step(Dm, K * B, in, nullptr, (V)1, y)) return;
+    }
+    for (int K = nK - 1; K >= 0; --K) {
+        const V* in = y;
+        if (K < nK - 1) {
+            if (!step(Et, K * B, x, y, (V)-1, t)) return;
+            in = t;
+        }
+        if (!step(Dt, K * B, in, nullptr, (V)1, x)) return;
+    }
+}
+
 // c[coff_s + j] = sum_{g in Omega_s} Q[g, j] (r - A z)[g]   (z = 0 skips A z);
 // the residual is matrix-free for the constant-coefficient Laplacians
 template <int SK, typename V, typename AV>
@@ -710,7 +763,28 @@ static void coarse_solve_t(ddg_handle h, V* c, V* y, V* t, V* x) {
     }
 }
 
+// one cooperative launch of the persistent recurrence (one CTA per SM)
+template <typename V>
+static void coarse_solve_persistent(ddg_handle h, V* c, V* y, V* t, V* x) {
+    int dev = 0, sms = 0;
+    DDG_CUDA(cudaGetDevice(&dev));
+    DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    ProfileMat Dm = h->Dm, Em = h->Em, Dt = h->Dt, Et = h->Et;
+    int B = h->B, nK = h->nK;
+    const V* cv = c;
+    ddgdev::GridBar* gb = h->cgbar;
+    int* err = h->errflags + E_TIMEOUT;
+    void* args[] = {&Dm, &Em, &Dt, &Et, &B, &nK, &cv, &y, &t, &x, &gb, &err};
+    DDG_CUDA(cudaLaunchCooperativeKernel((const void*)coarse_gemv_persistent_kernel<V>, dim3(sms), dim3(512), args, 0,
+                                         h->stream));
+}
+
 void coarse_solve(ddg_handle h, int prec) {
+    if (h->persistent_coarse) {
+        if (prec == DDG_PREC_FP64) coarse_solve_persistent<double>(h, h->c64, h->y64, h->t64, h->x64);
+        else coarse_solve_persistent<float>(h, h->c32, h->y32, h->t32, h->x32);
+        return;
+    }
     if (prec == DDG_PREC_FP64) coarse_solve_t<double>(h, h->c64, h->y64, h->t64, h->x64);
     else coarse_solve_t<float>(h, h->c32, h->y32, h->t32, h->x32);
 }

@@ -5,6 +5,8 @@
 // kernel: the preconditioner reads each local inverse once per colour phase
 // for all m columns, which is what makes batching pay.
 #include "ddg_internal.cuh"
+#include <algorithm>
+
 #include "dev_common.cuh"
 
 namespace {
@@ -458,6 +460,125 @@ __global__ void __launch_bounds__(MT) coarse_gemm_kernel(
     if (t == 0) tickets[rt] = 0u;
 }
 
+// ---------------------------------------------------------------- persistent coarse solve
+// The whole block-bidiagonal coarse solve for m columns in one cooperative
+// launch: every GEMM of the recurrence is split into (32-row tile, 128-column
+// split) items spread over the co-resident CTAs, a grid barrier separates the
+// partial products from their reduction (done by all threads), and another
+// separates the reduction from the next GEMM.  Barrier waits are bounded: a
+// wait that runs out sets the error flag and the kernel returns.
+struct CoarseStep {            // one GEMM of the recurrence
+    const int64_t* rowptr;
+    const int32_t* lo;
+    const int32_t* hi;
+    const float* vals;
+    int r0, cbase;
+    const float* x;
+    const float* a;
+    float sign;
+    float* out;
+};
+
+// partial products of one (row tile, split) item of a step
+__device__ void coarse_item(const CoarseStep& S, int B, int rt, int sp, int m, float* __restrict__ part,
+                            float (*sM)[33], float (*sX)[DDG_MCHUNK], int* rlo, int* rhi, int64_t* rptr) {
+    const int row0 = S.r0 + rt * CG_ROWS;
+    const int t = threadIdx.x, r = t >> 3, cg = t & 7;
+    __syncthreads();
+    if (t < CG_ROWS) {
+        rlo[t] = S.lo[row0 + t];
+        rhi[t] = S.hi[row0 + t];
+        rptr[t] = S.rowptr[row0 + t];
+    }
+    __syncthreads();
+    const int c_lo = S.cbase + sp * CG_KS, c_hi = c_lo + CG_KS;
+    int ulo = c_hi, uhi = c_lo;
+    for (int q = 0; q < CG_ROWS; ++q)
+        if (rhi[q] > rlo[q]) {
+            ulo = min(ulo, max(rlo[q], c_lo));
+            uhi = max(uhi, min(rhi[q], c_hi));
+        }
+    float acc[DDG_MCHUNK / 8];
+#pragma unroll
+    for (int u = 0; u < DDG_MCHUNK / 8; ++u) acc[u] = 0.f;
+    for (int jc = c_lo + ((ulo - c_lo) & ~31); jc < uhi; jc += 32) {
+        for (int e = t; e < CG_ROWS * 32; e += MT) {
+            const int rr = e >> 5, jj = e & 31, j = jc + jj;
+            sM[rr][jj] = (j >= rlo[rr] && j < rhi[rr]) ? S.vals[rptr[rr] + (j - rlo[rr])] : 0.f;
+        }
+        for (int e = t; e < 32 * m; e += MT) {
+            const int jj = e / m, c = e % m;
+            sX[jj][c] = S.x[(int64_t)(jc + jj) * m + c];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int jj = 0; jj < 32; ++jj) {
+            const float mv = sM[r][jj];
+#pragma unroll
+            for (int u = 0; u < DDG_MCHUNK / 8; ++u)
+                if (cg + 8 * u < m) acc[u] = fma(mv, sX[jj][cg + 8 * u], acc[u]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < DDG_MCHUNK / 8; ++u)
+        if (cg + 8 * u < m) part[((size_t)sp * B + rt * CG_ROWS + r) * m + cg + 8 * u] = acc[u];
+}
+
+__global__ void __launch_bounds__(MT) coarse_solve_persistent_kernel(
+    ProfileMat Dm, ProfileMat Em, ProfileMat Dt, ProfileMat Et, int B, int nK, int m,
+    const float* __restrict__ c, float* y, float* t, float* x, float* part, ddgdev::GridBar* gb, int* err) {
+    __shared__ float sM[CG_ROWS][33];
+    __shared__ float sX[32][DDG_MCHUNK];
+    __shared__ int rlo[CG_ROWS], rhi[CG_ROWS];
+    __shared__ int64_t rptr[CG_ROWS];
+    const int nsplit = (B + CG_KS - 1) / CG_KS;
+    const int ntiles = B / CG_ROWS;
+    const int nitems = ntiles * nsplit;
+    const unsigned G = gridDim.x;
+    auto run = [&](const CoarseStep& S) -> bool {
+        for (int it = blockIdx.x; it < nitems; it += G)
+            coarse_item(S, B, it / nsplit, it % nsplit, m, part, sM, sX, rlo, rhi, rptr);
+        if (!ddgdev::grid_barrier(gb, G, err)) return false;
+        // out[rows of the step] = a + sign * sum of the split partials
+        const int64_t tot = (int64_t)B * m;
+        for (int64_t e = (int64_t)blockIdx.x * MT + threadIdx.x; e < tot; e += (int64_t)G * MT) {
+            const float* pp = part + e;
+            const size_t st = (size_t)B * m;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int q = 0;
+            for (; q + 3 < nsplit; q += 4) {
+                s0 += __ldcg(pp + (size_t)q * st);
+                s1 += __ldcg(pp + (size_t)(q + 1) * st);
+                s2 += __ldcg(pp + (size_t)(q + 2) * st);
+                s3 += __ldcg(pp + (size_t)(q + 3) * st);
+            }
+            for (; q < nsplit; ++q) s0 += __ldcg(pp + (size_t)q * st);
+            const int64_t o = (int64_t)S.r0 * m + e;
+            S.out[o] = (S.a ? S.a[o] : 0.f) + S.sign * ((s0 + s1) + (s2 + s3));
+        }
+        return ddgdev::grid_barrier(gb, G, err);
+    };
+    // forward: y_K = D_K (c_K - E_K y_{K-1})
+    for (int K = 0; K < nK; ++K) {
+        const float* in = c;
+        if (K > 0) {
+            if (!run(CoarseStep{Em.rowptr, Em.lo, Em.hi, Em.v32, K * B, (K - 1) * B, y, c, -1.f, t})) return;
+            in = t;
+        }
+        if (!run(CoarseStep{Dm.rowptr, Dm.lo, Dm.hi, Dm.v32, K * B, K * B, in, nullptr, 1.f, y})) return;
+    }
+    // backward: x_K = D_K^T (y_K - E_{K+1}^T x_{K+1})
+    for (int K = nK - 1; K >= 0; --K) {
+        const float* in = y;
+        if (K < nK - 1) {
+            if (!run(CoarseStep{Et.rowptr, Et.lo, Et.hi, Et.v32, K * B, (K + 1) * B, x, y, -1.f, t})) return;
+            in = t;
+        }
+        if (!run(CoarseStep{Dt.rowptr, Dt.lo, Dt.hi, Dt.v32, K * B, K * B, in, nullptr, 1.f, x})) return;
+    }
+}
+
 __global__ void coarse_prolong_multi_kernel(int64_t n, int m, const int32_t* __restrict__ part,
                                             const int32_t* __restrict__ pos, const float* __restrict__ Q,
                                             int kmax, const int32_t* __restrict__ coff,
@@ -514,8 +635,8 @@ void multi_ensure(ddg_handle h, int m) {
     if (h->use_coarse) {
         const int nsplit = (h->B + CG_KS - 1) / CG_KS;
         w.gpart = h->arena.alloc<float>((size_t)nsplit * h->B * m);
-        w.gtick = h->arena.alloc<unsigned>(h->B / CG_ROWS);
-        DDG_CUDA(cudaMemsetAsync(w.gtick, 0, (h->B / CG_ROWS) * sizeof(unsigned), h->stream));
+        w.gtick = h->arena.alloc<unsigned>(std::max(2, h->B / CG_ROWS));
+        DDG_CUDA(cudaMemsetAsync(w.gtick, 0, std::max(2, h->B / CG_ROWS) * sizeof(unsigned), h->stream));
     }
     w.scal = h->arena.alloc<double>(S_COUNT * DDG_MCHUNK);
     w.partials = h->arena.alloc<double>((size_t)DDG_RED_BLOCKS * 2 * DDG_MCHUNK);
@@ -607,28 +728,25 @@ static void multi_apply_t(ddg_handle h, int m) {
         else RESTRICT_MULTI(32);
 #undef RESTRICT_MULTI
         const int B = h->B, nK = h->nK;
-        const int nsplit = (B + CG_KS - 1) / CG_KS;
-        const dim3 grid(B / CG_ROWS, nsplit);
-        auto gemm = [&](const ProfileMat& M, int r0, int cbase, const float* x, const float* a, float sign,
-                        float* out) {
-            coarse_gemm_kernel<<<grid, MT, 0, h->stream>>>(M.rowptr, M.lo, M.hi, M.v32, r0, B, cbase, nsplit,
-                                                           x, a, sign, out, m, w.gpart, w.gtick);
-        };
-        for (int K = 0; K < nK; ++K) {
-            const float* in = w.c32;
-            if (K > 0) {
-                gemm(h->Em, K * B, (K - 1) * B, w.y32, w.c32, -1.f, w.t32);
-                in = w.t32;
+        {
+            // one cooperative launch for the whole recurrence
+            static int max_blocks = 0;
+            if (!max_blocks) {
+                int per_sm = 0, dev = 0, sms = 0;
+                DDG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_solve_persistent_kernel, MT, 0));
+                DDG_CUDA(cudaGetDevice(&dev));
+                DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                max_blocks = std::max(1, std::min(per_sm, 4)) * sms;
             }
-            gemm(h->Dm, K * B, K * B, in, nullptr, 1.f, w.y32);
-        }
-        for (int K = nK - 1; K >= 0; --K) {
-            const float* in = w.y32;
-            if (K < nK - 1) {
-                gemm(h->Et, K * B, (K + 1) * B, w.x32, w.y32, -1.f, w.t32);
-                in = w.t32;
-            }
-            gemm(h->Dt, K * B, K * B, in, nullptr, 1.f, w.x32);
+            ProfileMat Dm = h->Dm, Em = h->Em, Dt = h->Dt, Et = h->Et;
+            int Bv = B, nKv = nK, mv = m;
+            const float* cv = w.c32;
+            float *yv = w.y32, *tv = w.t32, *xv = w.x32, *pv = w.gpart;
+            ddgdev::GridBar* gbv = reinterpret_cast<ddgdev::GridBar*>(w.gtick);
+            int* ev = h->errflags + E_TIMEOUT;
+            void* args[] = {&Dm, &Em, &Dt, &Et, &Bv, &nKv, &mv, &cv, &yv, &tv, &xv, &pv, &gbv, &ev};
+            DDG_CUDA(cudaLaunchCooperativeKernel((const void*)coarse_solve_persistent_kernel, dim3(max_blocks),
+                                                 dim3(MT), args, 0, h->stream));
         }
         coarse_prolong_multi_kernel<<<(unsigned)((n + bd / m - 1) / (bd / m)), bd, 0, h->stream>>>(
             n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);

@@ -178,13 +178,28 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
 #pragma unroll
             for (int i = 0; i < 16; ++i) tile[rl * LDS + cb * 16 + i] = v[i];
         }
+        int* grow = reinterpret_cast<int*>(tile + TC_M * LDS);
+        grow[rl] = (blk * TC_M + rl < n) ? ov_nodes[o + blk * TC_M + rl] : -1;
         __syncthreads();
-        // each warp updates its 32 rows of z, lanes along the columns
-        for (int rr = warp * 32; rr < warp * 32 + 32; ++rr) {
-            const int row = blk * TC_M + rr;
-            if (row >= n) break;
-            const int g = ov_nodes[o + row];
-            for (int c = lane; c < m; c += 32) z[(int64_t)g * m + c] += tile[rr * LDS + c];
+        // z[rows of the block] += tile: consecutive threads take consecutive
+        // columns of a row (coalesced), and each thread first loads the 8
+        // distinct z entries it updates, then writes them back
+        for (int e0 = threadIdx.x; e0 < TC_M * N; e0 += TC_THREADS * 8) {
+            float zv[8];
+            int64_t ad[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                const int rr = e / N, c = e % N;
+                const int g = e < TC_M * N ? grow[rr] : -1;
+                ad[u] = (g >= 0 && c < m) ? (int64_t)g * m + c : -1;
+                zv[u] = ad[u] >= 0 ? z[ad[u]] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * TC_THREADS;
+                if (ad[u] >= 0) z[ad[u]] = zv[u] + tile[(e / N) * LDS + e % N];
+            }
         }
     } else if (threadIdx.x == 0) {
         atomicExch(err, 1);
