@@ -375,90 +375,8 @@ __global__ void __launch_bounds__(MT) coarse_restrict_multi_kernel(
     }
 }
 
-// out[i, c] = (a ? a[i, c] : 0) + sign sum_j M[i][j] x[j, c] for the rows of
-// one super-block.  CTA (row tile of 32, column split of CG_KS): stages 32x32
-// pieces of M (zero outside each row's profile) and 32 x m pieces of x in
-// shared memory, 8 outputs per thread; partial sums go to scratch and the
-// last CTA of a row tile (ticket) adds the splits in split order.
+// Coarse GEMMs of the batched path: (32-row tile, CG_KS-column split) items
 constexpr int CG_ROWS = 32, CG_KS = 128;
-
-__global__ void __launch_bounds__(MT) coarse_gemm_kernel(
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-    const float* __restrict__ vals, int r0, int nrows, int cbase, int nsplit,
-    const float* __restrict__ x, const float* __restrict__ a, float sign, float* __restrict__ out, int m,
-    float* __restrict__ partial, unsigned* __restrict__ tickets) {
-    __shared__ float sM[CG_ROWS][33];
-    __shared__ float sX[32][DDG_MCHUNK];
-    __shared__ int rlo[CG_ROWS], rhi[CG_ROWS];
-    __shared__ int64_t rptr[CG_ROWS];
-    __shared__ bool last;
-    const int rt = blockIdx.x, sp = blockIdx.y;
-    const int row0 = r0 + rt * CG_ROWS;
-    const int t = threadIdx.x, r = t >> 3, cg = t & 7;
-    if (t < CG_ROWS) {
-        const int i = row0 + t;
-        rlo[t] = lo[i];
-        rhi[t] = hi[i];
-        rptr[t] = rowptr[i];
-    }
-    __syncthreads();
-    const int c_lo = cbase + sp * CG_KS, c_hi = c_lo + CG_KS;
-    int ulo = c_hi, uhi = c_lo;
-    for (int q = 0; q < CG_ROWS; ++q)
-        if (rhi[q] > rlo[q]) {
-            ulo = min(ulo, max(rlo[q], c_lo));
-            uhi = max(uhi, min(rhi[q], c_hi));
-        }
-    float acc[DDG_MCHUNK / 8];
-#pragma unroll
-    for (int u = 0; u < DDG_MCHUNK / 8; ++u) acc[u] = 0.f;
-    for (int jc = c_lo + ((ulo - c_lo) & ~31); jc < uhi; jc += 32) {
-        for (int e = t; e < CG_ROWS * 32; e += MT) {
-            const int rr = e >> 5, jj = e & 31, j = jc + jj;
-            sM[rr][jj] = (j >= rlo[rr] && j < rhi[rr]) ? vals[rptr[rr] + (j - rlo[rr])] : 0.f;
-        }
-        for (int e = t; e < 32 * m; e += MT) {
-            const int jj = e / m, c = e % m;
-            sX[jj][c] = x[(int64_t)(jc + jj) * m + c];
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int jj = 0; jj < 32; ++jj) {
-            const float mv = sM[r][jj];
-#pragma unroll
-            for (int u = 0; u < DDG_MCHUNK / 8; ++u)
-                if (cg + 8 * u < m) acc[u] = fma(mv, sX[jj][cg + 8 * u], acc[u]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < DDG_MCHUNK / 8; ++u)
-        if (cg + 8 * u < m) partial[((size_t)sp * nrows + rt * CG_ROWS + r) * m + cg + 8 * u] = acc[u];
-    __threadfence();
-    __syncthreads();
-    if (t == 0) last = (atomicAdd(&tickets[rt], 1u) == (unsigned)nsplit - 1u);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    for (int e = t; e < CG_ROWS * m; e += MT) {
-        const int rr = e / m, c = e % m;
-        const float* pp = partial + ((size_t)rt * CG_ROWS + rr) * m + c;
-        const size_t st = (size_t)nrows * m;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int q2 = 0;
-        for (; q2 + 3 < nsplit; q2 += 4) {
-            s0 += __ldcg(pp + (size_t)q2 * st);
-            s1 += __ldcg(pp + (size_t)(q2 + 1) * st);
-            s2 += __ldcg(pp + (size_t)(q2 + 2) * st);
-            s3 += __ldcg(pp + (size_t)(q2 + 3) * st);
-        }
-        for (; q2 < nsplit; ++q2) s0 += __ldcg(pp + (size_t)q2 * st);
-        const float s = (s0 + s1) + (s2 + s3);
-        const int64_t o = (int64_t)(row0 + rr) * m + c;
-        out[o] = (a ? a[o] : 0.f) + sign * s;
-    }
-    if (t == 0) tickets[rt] = 0u;
-}
 
 // ---------------------------------------------------------------- persistent coarse solve
 // The whole block-bidiagonal coarse solve for m columns in one cooperative

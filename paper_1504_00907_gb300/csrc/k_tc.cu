@@ -61,11 +61,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// core-matrix offset of element (row, k) in a rows x 32 K-major slab
-__device__ __forceinline__ int core_off(int row, int k) {
-    return ((row >> 3) * 4 + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
-}
-
 template <int N>
 __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
     const int2* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
