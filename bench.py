@@ -145,7 +145,7 @@ def cpu_baseline(sample_n=SAMPLE_N):
     from oracle import ddg_oracle as orc
     prob = di.make_poisson3d(N=sample_n, box=WORKLOAD["box"], overlap=WORKLOAD["overlap"],
                              p=WORKLOAD["p"], seed=WORKLOAD["seed"])
-    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape)
+    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape, dpn=prob.dofs_per_node)
     t0 = time.perf_counter()
     res = orc.pcg(M.A, prob.f, M.apply, tol=TOL)
     dt = time.perf_counter() - t0

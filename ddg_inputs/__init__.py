@@ -22,6 +22,10 @@ Problem families (structured grids, natural lexicographic order, x fastest):
 * 3D variable-coefficient diffusion -div(kappa grad u), cell-centred FD,
   harmonic-mean face coefficients, Dirichlet faces at half-cell distance
   (coefficient 2*kappa), operator scaled by h^2.
+* 3D linear elasticity, trilinear (Q1) hexahedral finite elements on ne^3
+  elements of the unit cube, Lame lambda constant and shear modulus mu per
+  element, 2x2x2 Gauss quadrature, the x = 0 face clamped; 3 interleaved
+  displacement dofs per node (analogue of the paper's vector problem E).
 * Gaussian random field g with squared-exponential covariance
   sigma^2 exp(-r^2 / (2 l^2)), sampled exactly through the separable
   (Kronecker) factorisation, kappa = exp(g).
@@ -45,7 +49,8 @@ __all__ = [
     "varcoef7_3d", "gaussian_random_field", "box_partition", "monomials",
     "fd_node_coords", "cell_centre_coords", "uniform_rhs", "normal_rhs",
     "make_poisson2d", "make_poisson3d", "make_biharmonic2d",
-    "make_varcoef3d", "csr_arrays", "monomial_exponents",
+    "make_varcoef3d", "csr_arrays", "monomial_exponents", "q1_reference_stiffness",
+    "elasticity_q1_3d", "make_elasticity3d",
 ]
 
 # stencil kinds understood by the library's matrix-free SpMV (the CSR is
@@ -55,6 +60,7 @@ STENCIL_5PT_2D = 1
 STENCIL_7PT_3D = 2
 STENCIL_13PT_2D = 3
 STENCIL_VAR7_3D = 4
+STENCIL_Q1_ELASTIC = 5
 
 
 @dataclasses.dataclass
@@ -72,7 +78,9 @@ class Problem:
     p: int                      # polynomial degree of F
     stencil_kind: int = STENCIL_NONE
     face_coef: Optional[np.ndarray] = None   # VAR7: float64[3, nz, ny, nx+1..]
-    kappa: Optional[np.ndarray] = None       # VAR7: cell coefficients
+    kappa: Optional[np.ndarray] = None       # VAR7: cell coefficients; Q1: mu per element
+    dofs_per_node: int = 1
+    target: Optional[np.ndarray] = None      # Q1 workload: u_t of the loss
 
     @property
     def n(self) -> int:
@@ -223,6 +231,74 @@ def varcoef7_3d(kappa):
     return A, (cx, cy, cz)
 
 
+def q1_reference_stiffness():
+    """Element matrices of trilinear (Q1) linear elasticity on the unit cube.
+
+    Local dof 3 a + i = component i of node a = (a & 1, (a >> 1) & 1, a >> 2).
+    With N_a the trilinear shape functions and 2x2x2 Gauss quadrature (exact
+    here): K_lam[ai, bj] = int d_i N_a d_j N_b and
+    K_mu[ai, bj] = int (delta_ij grad N_a . grad N_b + d_j N_a d_i N_b), so
+    that the element stiffness of lam, mu on a cube of side h is
+    h (lam K_lam + mu K_mu) (bilinear form int lam div u div v + 2 mu eps:eps).
+    """
+    g = 0.5 + np.array([-0.5, 0.5]) / np.sqrt(3.0)
+    Kl = np.zeros((24, 24))
+    Km = np.zeros((24, 24))
+    for x in g:
+        for y in g:
+            for z in g:
+                xi = (x, y, z)
+                grad = np.zeros((8, 3))
+                for a in range(8):
+                    bits = (a & 1, (a >> 1) & 1, (a >> 2) & 1)
+                    f = [xi[d] if bits[d] else 1.0 - xi[d] for d in range(3)]
+                    df = [1.0 if bits[d] else -1.0 for d in range(3)]
+                    grad[a] = [df[0] * f[1] * f[2], f[0] * df[1] * f[2], f[0] * f[1] * df[2]]
+                w = 1.0 / 8.0
+                for a in range(8):
+                    for b in range(8):
+                        gg = grad[a] @ grad[b]
+                        for i in range(3):
+                            for j in range(3):
+                                Kl[3 * a + i, 3 * b + j] += w * grad[a, i] * grad[b, j]
+                                Km[3 * a + i, 3 * b + j] += w * ((i == j) * gg + grad[a, j] * grad[b, i])
+    return Kl, Km
+
+
+def elasticity_q1_3d(mu, lam=1.0):
+    """Q1 hexahedral linear elasticity on ne^3 elements of the unit cube.
+
+    ``mu`` has shape (ne, ne, ne) (x fastest when raveled), one shear modulus
+    per element; ``lam`` is constant.  The nodes of the x = 0 face are clamped
+    (their dofs eliminated); the remaining nodes (i = 1..ne, j, k = 0..ne) are
+    numbered x fastest with 3 interleaved displacement dofs each.  Returns
+    (A, node_shape) with node_shape = (ne, ne + 1, ne + 1).
+    """
+    mu = np.asarray(mu, dtype=np.float64)
+    ne = mu.shape[0]
+    h = 1.0 / ne
+    Kl, Km = q1_reference_stiffness()
+    Kl = Kl * h
+    Km = Km * h
+    E = np.arange(ne ** 3, dtype=np.int64)
+    ei, ej, ek = E % ne, (E // ne) % ne, E // (ne * ne)
+    dofs = np.empty((ne ** 3, 24), dtype=np.int64)
+    for a in range(8):
+        I, J, K = ei + (a & 1), ej + ((a >> 1) & 1), ek + (a >> 2)
+        base = np.where(I >= 1, 3 * ((I - 1) + ne * (J + (ne + 1) * K)), -1)
+        for i in range(3):
+            dofs[:, 3 * a + i] = np.where(base >= 0, base + i, -1)
+    n = 3 * ne * (ne + 1) ** 2
+    rows = np.repeat(dofs, 24, axis=1).ravel()
+    cols = np.tile(dofs, (1, 24)).ravel()
+    vals = (lam * Kl[None, :, :] + mu.ravel()[:, None, None] * Km[None, :, :]).ravel()
+    keep = (rows >= 0) & (cols >= 0)
+    A = sp.csr_matrix((vals[keep], (rows[keep], cols[keep])), shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A, (ne, ne + 1, ne + 1)
+
+
 def gaussian_random_field(shape, length, sigma, seed, coords="cell"):
     """Exact sample of a squared-exponential Gaussian random field.
 
@@ -363,6 +439,36 @@ def make_biharmonic2d(N=256, box=16, overlap=2, p=3, seed=100, m=None, mode="box
                    part=box_partition(shape, (box, box)), box=(box, box),
                    F=monomials(fd_node_coords(shape), p), f=uniform_rhs(A.shape[0], seed, m),
                    overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_13PT_2D)
+
+
+def make_elasticity3d(ne=64, box=8, overlap=1, p=2, lam=1.0, length=0.15, sigma=1.0,
+                      field_seed=4, body_seed=5, target_seed=6, mode="box"):
+    """Q1 elasticity on ne^3 elements, mu = exp(GRF) per element, clamped x = 0,
+    body force ~ N(0, 1) per dof, target displacement u_t ~ N(0, 1); node
+    partition by boxes of ``box`` node layers (node index // box, the last
+    box absorbing the end layer); generators: monomials of degree <= p in the
+    node coordinates, once per displacement component."""
+    g = gaussian_random_field((ne, ne, ne), length, sigma, field_seed)
+    mu = np.exp(g)
+    A, nshape = elasticity_q1_3d(mu, lam)
+    nx, ny, nz = nshape
+    nn = nx * ny * nz
+    node = np.arange(nn)
+    I = node % nx + 1
+    J = (node // nx) % ny
+    K = node // (nx * ny)
+    nb = ne // box
+    sid = (np.minimum(I // box, nb - 1) + nb * (np.minimum(J // box, nb - 1)
+           + nb * np.minimum(K // box, nb - 1)))
+    part = np.repeat(sid, 3).astype(np.int32)
+    h = 1.0 / ne
+    coords = np.stack([I * h, J * h, K * h], axis=1)
+    F = monomials(coords, p, components=3)
+    n = A.shape[0]
+    return Problem(name=f"elasticity3d_{ne}", A=A, shape=nshape, part=part, box=(box,) * 3, F=F,
+                   f=normal_rhs(n, body_seed), overlap=overlap, overlap_mode=mode, p=p,
+                   stencil_kind=STENCIL_Q1_ELASTIC, kappa=mu, dofs_per_node=3,
+                   target=normal_rhs(n, target_seed))
 
 
 def make_varcoef3d(N=96, box=8, overlap=1, p=2, field_seed=2, rhs_seed=3, m=64,

@@ -67,7 +67,11 @@ enum {
     DDG_STENCIL_5PT_2D = 1,   /* [4, -1], Dirichlet, nx x ny */
     DDG_STENCIL_7PT_3D = 2,   /* [6, -1], Dirichlet, nx x ny x nz */
     DDG_STENCIL_13PT_2D = 3,  /* clamped biharmonic (CSR SpMV is used) */
-    DDG_STENCIL_VAR7_3D = 4   /* cell-centred variable coefficient */
+    DDG_STENCIL_VAR7_3D = 4,  /* cell-centred variable coefficient */
+    DDG_STENCIL_Q1_ELASTIC = 5 /* trilinear hexahedral linear elasticity on ne^3 elements
+                                  of the unit cube, nodes of the x = 0 face clamped:
+                                  nx, ny, nz = ne, ne + 1, ne + 1 unclamped nodes,
+                                  dofs_per_node = 3 (CSR SpMV is used) */
 };
 
 typedef struct {
@@ -96,8 +100,9 @@ typedef struct {
     int nx, ny, nz;          /* grid shape (x fastest); nz = 1 in 2D */
     int dofs_per_node;       /* interleaved dofs per grid node (1 for scalars) */
     int stencil_kind;        /* DDG_STENCIL_* */
-    const double* coef;      /* host, VAR7 only: cell coefficients kappa[nz][ny][nx]
-                                (x fastest), needed by ddg_grad_coeff; else NULL */
+    const double* coef;      /* host, needed by ddg_grad_coeff: VAR7: cell coefficients
+                                kappa[nz][ny][nx]; Q1_ELASTIC: shear modulus per element
+                                mu[ne][ne][ne] (x fastest); else NULL */
 } ddg_matrix;
 
 typedef struct {
@@ -177,10 +182,12 @@ ddg_status ddg_solve_many(ddg_handle* hs, int nprob, const double* const* F, dou
 ddg_status ddg_adjoint(ddg_handle h, const double* dLdu, double* lambda, double tol,
                        int* iters, double* relres);
 
-/* Coefficient gradient dL/dkappa = -lambda^T (dA/dkappa) u for a
- * DDG_STENCIL_VAR7_3D handle: lambda, u device [n]; dkappa device [n]
- * (one entry per cell, the chain rule through the harmonic-mean faces). */
-ddg_status ddg_grad_coeff(ddg_handle h, const double* lambda, const double* u, double* dkappa);
+/* Coefficient gradient dL/dc = -lambda^T (dA/dc) u (lambda = A^{-1} dL/du,
+ * u = A^{-1} f) for the coefficient array c given at setup: VAR7 handles:
+ * c = kappa per cell, dcoef device [n] (chain rule through the harmonic-mean
+ * faces); Q1_ELASTIC handles: c = mu per element, dcoef device [ne^3]
+ * (dL/dmu_e = -lambda_e^T K^mu_e u_e).  lambda, u: device [n]. */
+ddg_status ddg_grad_coeff(ddg_handle h, const double* lambda, const double* u, double* dcoef);
 
 /* One preconditioner application z = M^{-1} r (Sec. 6), r and z device
  * FP64 [n], in the handle's current precision. */

@@ -83,12 +83,13 @@ def neighbour_graph_box(shape, reach=1):
     return sp.csr_matrix((np.ones(r.size), (r, np.concatenate(cols))), shape=(n, n))
 
 
-def grow_overlap(A, part, delta, mode="graph", shape=None):
+def grow_overlap(A, part, delta, mode="graph", shape=None, dpn=1):
     """Overlapping subdomains: Omega~_i = nodes within distance Delta of Omega_i.
 
     Sec. 6: "expanding the partition to include nodes within graph distance
-    Delta in the graph defined by A".  Returns a list of sorted int64 index
-    arrays, one per subdomain.
+    Delta in the graph defined by A".  In box mode the distance is measured
+    between grid nodes, and all ``dpn`` interleaved dofs of a node move
+    together.  Returns a list of sorted int64 index arrays, one per subdomain.
     """
     n = A.shape[0]
     nsub = int(part.max()) + 1
@@ -96,7 +97,7 @@ def grow_overlap(A, part, delta, mode="graph", shape=None):
     if mode == "graph":
         G = _pattern(A) + sp.identity(n, format="csr")
     elif mode == "box":
-        G = neighbour_graph_box(shape, 1)
+        G = sp.kron(neighbour_graph_box(shape, 1), np.ones((dpn, dpn)), format="csr")
     else:
         raise ValueError(mode)
     G = _pattern(G)
@@ -216,13 +217,13 @@ class DDGOracle:
     """Setup and application of the DDG two-level Schwarz preconditioner."""
 
     def __init__(self, A, part, F, overlap, mode="graph", shape=None, rank_tol=RANK_TOL,
-                 coarse=True):
+                 coarse=True, dpn=1):
         self.A = sp.csr_matrix(A, dtype=np.float64)
         self.n = self.A.shape[0]
         self.part = np.asarray(part, dtype=np.int64)
         self.nsub = int(self.part.max()) + 1
         # Sec. 6: overlapping subdomains and the processing order
-        self.omega = grow_overlap(self.A, self.part, overlap, mode, shape)
+        self.omega = grow_overlap(self.A, self.part, overlap, mode, shape, dpn)
         self.colour = colour_subdomains(self.A, self.omega)
         self.order = sweep_order(self.colour)
         # Sec. 6: local matrices A_i = R~_i A R~_i^T, solved exactly (Cholesky)

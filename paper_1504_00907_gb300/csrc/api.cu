@@ -122,6 +122,42 @@ std::vector<int> colour_subdomains(const ddg_matrix* A, const std::vector<std::v
     return colour;
 }
 
+// dK_e / dmu_e of trilinear hexahedral elasticity on a cube of side h: the
+// shear part of the bilinear form int lam div u div v + 2 mu eps(u):eps(v),
+// i.e. h * int_[0,1]^3 (delta_ij grad N_a . grad N_b + d_j N_a d_i N_b),
+// integrated exactly by 2x2x2 Gauss points; local dof 3 a + i, node
+// a = (a & 1, (a >> 1) & 1, a >> 2)
+std::vector<double> q1_dk_dmu(double h) {
+    std::vector<double> K(576, 0.0);
+    const double gp[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
+    for (double x : gp)
+        for (double y : gp)
+            for (double z : gp) {
+                const double xi[3] = {x, y, z};
+                double grad[8][3];
+                for (int a = 0; a < 8; ++a) {
+                    const int bits[3] = {a & 1, (a >> 1) & 1, a >> 2};
+                    double f[3], df[3];
+                    for (int d = 0; d < 3; ++d) {
+                        f[d] = bits[d] ? xi[d] : 1.0 - xi[d];
+                        df[d] = bits[d] ? 1.0 : -1.0;
+                    }
+                    grad[a][0] = df[0] * f[1] * f[2];
+                    grad[a][1] = f[0] * df[1] * f[2];
+                    grad[a][2] = f[0] * f[1] * df[2];
+                }
+                for (int a = 0; a < 8; ++a)
+                    for (int b = 0; b < 8; ++b) {
+                        const double gg = grad[a][0] * grad[b][0] + grad[a][1] * grad[b][1] + grad[a][2] * grad[b][2];
+                        for (int i = 0; i < 3; ++i)
+                            for (int j = 0; j < 3; ++j)
+                                K[(3 * a + i) * 24 + 3 * b + j] +=
+                                    0.125 * h * ((i == j ? gg : 0.0) + grad[a][j] * grad[b][i]);
+                    }
+            }
+    return K;
+}
+
 void validate(const ddg_matrix* A, const int32_t* part, const double* F, int k, int overlap,
               const ddg_options& o) {
     DDG_REQUIRE(A && A->rowptr && A->col && A->val, DDG_EINVAL, "A and its CSR arrays must be non-null");
@@ -607,8 +643,24 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             DDG_CUDA(cudaStreamSynchronize(h->stream));
         }
         if (A->stencil_kind == DDG_STENCIL_VAR7_3D && A->coef) {
+            h->ncoef = n;
             h->kappa = h->arena.alloc<double>(n);
             h2d(h->kappa, A->coef, n, h->stream);
+        }
+        if (A->stencil_kind == DDG_STENCIL_Q1_ELASTIC) {
+            const int ne = A->nx;
+            DDG_REQUIRE(ne >= 1 && A->ny == ne + 1 && A->nz == ne + 1 && A->dofs_per_node == 3 &&
+                            (int64_t)3 * ne * (ne + 1) * (ne + 1) == n,
+                        DDG_EINVAL, "Q1 elasticity needs nx = ne, ny = nz = ne + 1, 3 dofs per node");
+            const std::vector<double> K = q1_dk_dmu(1.0 / ne);
+            h->kmu = h->arena.alloc<double>(576);
+            h2d(h->kmu, K.data(), 576, h->stream);
+            if (A->coef) {
+                h->ncoef = (int64_t)ne * ne * ne;
+                h->kappa = h->arena.alloc<double>(h->ncoef);
+                h2d(h->kappa, A->coef, h->ncoef, h->stream);
+            }
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
         }
 
         // ---- partition (Sec. 4)
@@ -669,7 +721,7 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         h->sum_local = ov_off[nsub];
         h->total_tiles = tile_off[nsub];
         h->Tmax = (h->max_local + DDG_LT - 1) / DDG_LT;
-        DDG_REQUIRE(h->Tmax <= 64, DDG_EINVAL, "overlapping subdomains larger than 2048 dofs are not supported");
+        DDG_REQUIRE(h->Tmax <= 96, DDG_EINVAL, "overlapping subdomains larger than 3072 dofs are not supported");
         h->h_ov_off = ov_off;
         h->h_crow_off.assign(h->ncol + 1, 0);
         for (int c = 0; c < h->ncol; ++c) h->h_crow_off[c + 1] = ov_off[h->h_csub_off[c + 1]];
@@ -1010,12 +1062,16 @@ ddg_status ddg_adjoint(ddg_handle h, const double* dLdu, double* lambda, double 
     return ddg_solve(h, dLdu, lambda, tol, iters, relres);
 }
 
-ddg_status ddg_grad_coeff(ddg_handle h, const double* lambda, const double* u, double* dkappa) {
+ddg_status ddg_grad_coeff(ddg_handle h, const double* lambda, const double* u, double* dcoef) {
     return guarded(h, [&]() {
-        DDG_REQUIRE(h->stencil_kind == DDG_STENCIL_VAR7_3D && h->kappa, DDG_EINVAL,
-                    "ddg_grad_coeff needs a VAR7 handle set up with the cell coefficients");
-        DDG_REQUIRE(lambda && u && dkappa, DDG_EINVAL, "null pointer");
-        ddg::grad_coeff_var7(h, lambda, u, dkappa);
+        DDG_REQUIRE(lambda && u && dcoef, DDG_EINVAL, "null pointer");
+        if (h->stencil_kind == DDG_STENCIL_Q1_ELASTIC && h->kmu) {
+            ddg::grad_coeff_q1(h, lambda, u, dcoef);
+        } else {
+            DDG_REQUIRE(h->stencil_kind == DDG_STENCIL_VAR7_3D && h->kappa, DDG_EINVAL,
+                        "ddg_grad_coeff needs a VAR7 or Q1 handle set up with its coefficients");
+            ddg::grad_coeff_var7(h, lambda, u, dcoef);
+        }
         DDG_CUDA(cudaStreamSynchronize(h->stream));
         return DDG_OK;
     });

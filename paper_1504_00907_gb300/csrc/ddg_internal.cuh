@@ -179,7 +179,9 @@ struct ddg_handle_s {
     int32_t* col = nullptr;
     double* val64 = nullptr;
     float* val32 = nullptr;
-    double* kappa = nullptr;    // VAR7 cell coefficients (device), for dL/dkappa
+    double* kappa = nullptr;    // VAR7 cell coefficients / Q1 shear moduli (device)
+    double* kmu = nullptr;      // Q1: 24 x 24 element matrix dK_e / dmu_e (device)
+    int64_t ncoef = 0;
 
     // ---- partition (Sec. 4) in id order
     int nsub = 0;
@@ -315,6 +317,7 @@ void convert_to_float(ddg_handle h, const double* src, float* dst);
 void convert_to_double(ddg_handle h, const float* src, double* dst);
 void residual64(ddg_handle h, const double* f, const double* u, double* r);
 void grad_coeff_var7(ddg_handle h, const double* lambda, const double* u, double* dk);
+void grad_coeff_q1(ddg_handle h, const double* lambda, const double* u, double* dk);
 void set_scalar(ddg_handle h, int slot, double v);
 void strided_gather(ddg_handle h, const double* src, int m, int j, double* dst);
 void strided_scatter(ddg_handle h, const double* src, int m, int j, double* dst);

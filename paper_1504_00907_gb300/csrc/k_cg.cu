@@ -253,6 +253,35 @@ __global__ void grad_var7_kernel(int nx, int ny, int nz, const double* __restric
     dk[g] = s;
 }
 
+// dL/dmu_e = -lambda_e^T K^mu u_e for Q1 elasticity: gather the 24 dofs of
+// element e (clamped x = 0 nodes contribute zero) and contract with the
+// element matrix dK_e / dmu_e
+__global__ void grad_q1_kernel(int ne, const double* __restrict__ kmu, const double* __restrict__ lam,
+                               const double* __restrict__ u, double* __restrict__ dmu) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)ne * ne * ne) return;
+    const int ei = (int)(e % ne), ej = (int)((e / ne) % ne), ek = (int)(e / ((int64_t)ne * ne));
+    double lv[24], uv[24];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int I = ei + (a & 1), J = ej + ((a >> 1) & 1), K = ek + (a >> 2);
+        const int64_t base = I >= 1 ? 3 * ((int64_t)(I - 1) + (int64_t)ne * (J + (int64_t)(ne + 1) * K)) : -1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            lv[3 * a + i] = base >= 0 ? lam[base + i] : 0.0;
+            uv[3 * a + i] = base >= 0 ? u[base + i] : 0.0;
+        }
+    }
+    double s = 0.0;
+    for (int a = 0; a < 24; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < 24; ++b) t = fma(__ldg(kmu + a * 24 + b), uv[b], t);
+        s = fma(lv[a], t, s);
+    }
+    dmu[e] = -s;
+}
+
 inline unsigned red_grid(int64_t n) {
     int64_t b = (n + RT - 1) / RT;
     if (b > DDG_RED_BLOCKS) b = DDG_RED_BLOCKS;
@@ -351,6 +380,13 @@ void strided_scatter(ddg_handle h, const double* src, int m, int j, double* dst)
 void cast_q32(ddg_handle h) {
     const int64_t cnt = h->n * (int64_t)h->kmax;
     cast_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, h->stream>>>(cnt, h->Q64, h->Q32);
+    DDG_CHECK_LAUNCH();
+}
+
+void grad_coeff_q1(ddg_handle h, const double* lambda, const double* u, double* dk) {
+    const int ne = h->nx;
+    const int64_t ncell = (int64_t)ne * ne * ne;
+    grad_q1_kernel<<<(unsigned)((ncell + 255) / 256), 256, 0, h->stream>>>(ne, h->kmu, lambda, u, dk);
     DDG_CHECK_LAUNCH();
 }
 

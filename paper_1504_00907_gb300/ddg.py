@@ -207,6 +207,7 @@ class Solver:
         kw.setdefault("mode", prob.overlap_mode)
         kw.setdefault("shape", prob.shape)
         kw.setdefault("stencil_kind", prob.stencil_kind)
+        kw.setdefault("dofs_per_node", getattr(prob, "dofs_per_node", 1))
         if prob.kappa is not None:
             kw.setdefault("coef", prob.kappa)
         return cls(prob.A, prob.part, prob.F, prob.overlap, **kw)
@@ -259,9 +260,12 @@ class Solver:
         return lam, it.value, rr.value
 
     def grad_coeff(self, lam, u):
+        """dL/dc for the coefficient array c given at setup (kappa per cell
+        for VAR7, mu per element for Q1 elasticity)."""
         import torch
-        dk = torch.empty_like(u)
-        _check(load().ddg_grad_coeff(self.h, _dev(lam, self.n), _dev(u, self.n), _dev(dk, self.n)), self.h)
+        ncoef = self._coef.size if self._coef is not None else u.numel()
+        dk = torch.empty(ncoef, dtype=torch.float64, device=u.device)
+        _check(load().ddg_grad_coeff(self.h, _dev(lam, self.n), _dev(u, self.n), _dev(dk, ncoef)), self.h)
         return dk
 
     # ---- building blocks (parity tests)

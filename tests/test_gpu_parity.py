@@ -28,6 +28,7 @@ CASES = {
     "varcoef_16": lambda: di.make_varcoef3d(N=16, box=8, overlap=1, p=2, m=None),
     "poisson2d_p0_overlap0": lambda: di.make_poisson2d(N=40, box=10, overlap=0, p=0, seed=14),
     "single_subdomain": lambda: di.make_poisson2d(N=20, box=20, overlap=1, p=1, seed=15),
+    "elasticity_q1_6": lambda: di.make_elasticity3d(ne=6, box=3, overlap=1, p=2),
 }
 
 _cache = {}
@@ -38,7 +39,7 @@ def setup_case(name):
         from paper_1504_00907_gb300 import ddg
         prob = CASES[name]()
         solver = ddg.Solver.from_problem(prob, precision="fp64", keep=("fp64", "fp32", "bf16"))
-        oracle = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape)
+        oracle = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape, dpn=prob.dofs_per_node)
         _cache[name] = (prob, solver, oracle)
     return _cache[name]
 
@@ -232,7 +233,7 @@ def test_solve_many_uneven_problems_concurrently():
     for p, f, u in zip(probs, rhs, outs):
         F = f.cpu().numpy().reshape(p.n, -1)
         Un = u.cpu().numpy().reshape(p.n, -1)
-        M = orc.DDGOracle(p.A, p.part, p.F, p.overlap, p.overlap_mode, p.shape)
+        M = orc.DDGOracle(p.A, p.part, p.F, p.overlap, p.overlap_mode, p.shape, dpn=p.dofs_per_node)
         for j in range(F.shape[1]):
             ref = orc.pcg(M.A, F[:, j], M.apply, tol=1e-8)
             assert rel(Un[:, j], ref.u) <= 1e-7

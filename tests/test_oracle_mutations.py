@@ -14,7 +14,7 @@ from oracle import ddg_oracle as orc
 
 def _setup():
     prob = di.make_poisson2d(N=14, box=5, overlap=1, p=1)
-    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape)
+    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape, dpn=prob.dofs_per_node)
     return prob, M
 
 

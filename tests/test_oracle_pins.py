@@ -339,3 +339,29 @@ def test_table1_plausibility_poisson3d():
     paper = [gold["cg_iterations"][f"P{p}"] for p in range(4)]
     assert all(a <= b + 2 for a, b in zip(its, paper)), (its, paper)
     assert all(b <= a for a, b in zip(its, its[1:])), its
+
+
+def test_q1_elasticity_patch_test_and_rigid_modes():
+    # element matrices annihilate rigid motions; the assembled operator with
+    # constant coefficients maps any linear displacement field (constant
+    # strain, an exact FE solution of the homogeneous equations) to zero at
+    # the interior nodes -- the FEM patch test
+    Kl, Km = di.q1_reference_stiffness()
+    pts = np.array([[a & 1, (a >> 1) & 1, a >> 2] for a in range(8)], float)
+    for fn in (lambda p: [1, 0, 0], lambda p: [0, 0, 1], lambda p: [-p[1], p[0], 0],
+               lambda p: [p[2], 0, -p[0]]):
+        v = np.concatenate([fn(p) for p in pts])
+        assert np.abs(Kl @ v).max() < 1e-14 and np.abs(Km @ v).max() < 1e-14
+    ne = 5
+    A, (nx, ny, nz) = di.elasticity_q1_3d(np.full((ne, ne, ne), 1.3), lam=0.7)
+    node = np.arange(nx * ny * nz)
+    I, J, K = node % nx + 1, (node // nx) % ny, node // (nx * ny)
+    x, y, z = I / ne, J / ne, K / ne
+    u = np.stack([0.3 * x + 0.2 * y - 0.1 * z, -0.4 * x + 0.5 * z, 0.25 * y + 0.6 * z], axis=1).ravel()
+    r = (A @ u).reshape(-1, 3)
+    # interior: every neighbouring node carries the linear field (nodes at
+    # I = 1 touch the clamped, eliminated x = 0 layer)
+    interior = (I > 1) & (I < ne) & (J > 0) & (J < ne) & (K > 0) & (K < ne)
+    assert np.abs(r[interior]).max() < 1e-13
+    assert np.abs(r[~interior]).max() > 1e-3          # boundary rows carry tractions
+    assert np.linalg.eigvalsh(A.toarray()).min() > 0  # clamped: SPD
