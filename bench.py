@@ -55,6 +55,9 @@ def parse():
                     help="grid of the multi-RHS arm (0 skips it)")
     ap.add_argument("--batched-m", type=int, default=64)
     ap.add_argument("--uneven", type=int, default=1, help="run the uneven 24-problem arm (0 skips it)")
+    ap.add_argument("--elasticity-size", type=int, default=64,
+                    help="elements per side of the Q1 elasticity arm (0 skips it)")
+    ap.add_argument("--elasticity-steps", type=int, default=3)
     ap.add_argument("--keep", default="fp64,fp32,bf16",
                     help="local-inverse precisions kept at setup (profiling runs keep fewer)")
     return ap.parse_args()
@@ -297,6 +300,117 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
     return res
 
 
+def elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
+    """Differentiation workload: 3D linear elasticity, trilinear (Q1) hexahedra
+    on ne^3 elements (x = 0 face clamped, 3 dofs per node), lambda = 1,
+    mu = exp(GRF, length 0.15, sigma 1) per element, body force ~ N(0, 1);
+    8^3-node boxes + overlap 1, p <= 2 monomials per displacement component
+    (30 per subdomain), FP32 preconditioner, FP64 CG, tol 1e-8.  One
+    differentiation step = forward solve + adjoint solve + dL/dmu for
+    L = 0.5 ||u - u_t||^2; the forward solve is also run in plain FP64."""
+    ne = args.elasticity_size
+    t0 = time.perf_counter()
+    prob = di.make_elasticity3d(ne=ne, box=8, overlap=1, p=2)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = solver.info()
+    b = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    ut = torch.tensor(prob.target, dtype=torch.float64, device=dev)
+    mu = torch.tensor(prob.kappa, dtype=torch.float64, device=dev).reshape(-1)
+    n = prob.n
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step():
+        u, it, rr, st = solver.solve(b, TOL)
+        g = (u - ut).contiguous()
+        lam, ita, rra = solver.adjoint(g, TOL)
+        dmu = solver.grad_coeff(lam, u)
+        return u, lam, dmu, (it, rr, st), (ita, rra)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    steps = max(1, args.elasticity_steps)
+    e0, e1 = ev()
+    e0.record(stream)
+    fw, ad = [], []
+    for _ in range(steps):
+        u, lam, dmu, f_inf, a_inf = step()
+        fw.append(f_inf)
+        ad.append(a_inf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / steps)
+    loss = 0.5 * float(((u - ut) ** 2).sum())
+    dlogmu = mu * dmu
+    # the three parts of one step, separately
+    e0, e1 = ev()
+    e2, e3 = ev()
+    e0.record(stream)
+    u, it_f, rr_f, st_f = solver.solve(b, TOL)
+    e1.record(stream)
+    lam, it_a, rr_a = solver.adjoint((u - ut).contiguous(), TOL)
+    e2.record(stream)
+    solver.grad_coeff(lam, u)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    parts = {"forward_ms": e0.elapsed_time(e1), "adjoint_ms": e1.elapsed_time(e2),
+             "grad_coeff_ms": e2.elapsed_time(e3)}
+    # plain FP64 forward solve
+    solver.set_precision("fp64")
+    solver.solve(b, TOL)
+    torch.cuda.synchronize()
+    e0, e1 = ev()
+    e0.record(stream)
+    _, it64, rr64, st64 = solver.solve(b, TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(e0.elapsed_time(e1))
+    # local-solve roofline on the ~3000-dof blocks of this workload
+    solver.set_precision("fp32")
+    solver.profile(ddg.KERNEL_CLASSES)
+    e0, e1 = ev()
+    e0.record(stream)
+    solver.solve(b, TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ks = solver.kernel_stats()
+    solver.profile(())
+    breakdown = {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in ks.items()}
+    breakdown["solve_ms_with_events"] = e0.elapsed_time(e1)
+    out = {"workload": f"elasticity_q1_{ne}^3 elements: clamped x=0, lambda=1, mu=exp(GRF 0.15), "
+                       "8^3-node boxes + overlap 1, 30 generators, tol 1e-8",
+           "dofs": n, "subdomains": info["nsub"], "coarse_dim": info["n0"],
+           "colours": info["ncolours"], "max_local_dofs": info["max_local"],
+           "generate_s_host": gen_s, "setup_s": setup_s, "setup_ms_library": info["setup_ms"],
+           "step_ms": ms_step, "steps": steps, "parts_ms": parts,
+           "forward": {"iters": int(fw[-1][0]), "true_relres": float(fw[-1][1]), "status": int(fw[-1][2])},
+           "adjoint": {"iters": int(ad[-1][0]), "true_relres": float(ad[-1][1])},
+           "fp64_plain_forward": {"ms": ms64, "iters": int(it64), "true_relres": float(rr64),
+                                  "status": int(st64)},
+           "speedup_mixed_vs_fp64_forward": ms64 / parts["forward_ms"],
+           "dof_iters_per_s_step": world * n * (fw[-1][0] + ad[-1][0]) / (ms_step / 1e3),
+           "loss": loss, "dL_dlogmu_norm": float(dlogmu.norm()),
+           "breakdown_one_mixed_forward": breakdown}
+    ls = ks.get("local_solve")
+    if ls and ls["timed"]:
+        pk = peaks()
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        ach = ls["bytes"] / (ls["ms"] / 1e3) / 1e9
+        out["roofline_local_solve"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                       "frac": ach / peak, "launches": ls["timed"],
+                                       "avg_launch_ms": ls["ms"] / ls["timed"],
+                                       "algorithmic_bytes_per_launch": ls["bytes"] / ls["timed"]}
+    solver.close()
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -441,6 +555,10 @@ def main():
     if args.uneven:
         uneven = uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world)
 
+    elasticity = None
+    if args.elasticity_size > 0:
+        elasticity = elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
@@ -467,6 +585,7 @@ def main():
         "breakdown_one_mixed_solve": breakdown,
         "batched": batched,
         "uneven_batch": uneven,
+        "elasticity_differentiation": elasticity,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
