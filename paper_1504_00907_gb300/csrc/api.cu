@@ -768,6 +768,13 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             h2d(h->nchunks, nch.data(), nsub, h->stream);
             h2d(h->first_item, first.data(), nsub, h->stream);
             DDG_CUDA(cudaMemsetAsync(h->counters, 0, nsub * sizeof(unsigned), h->stream));
+            std::vector<int32_t> ovs(h->sum_local);
+            for (int q = 0; q < nsub; ++q)
+                for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) ovs[a] = q;
+            h->ov_sub = h->arena.alloc<int32_t>(h->sum_local);
+            h2d(h->ov_sub, ovs.data(), h->sum_local, h->stream);
+            h->split_gather = *std::max_element(nch.begin(), nch.end()) > DDG_GATHER_SPLIT_CHUNKS;
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
         }
 
         // algorithmic bytes of one local-solve launch per colour and precision:
@@ -786,7 +793,6 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         // ---- tensor-core slabs and residual layout for the batched solve
         if (o.tensor_cores) {
             std::vector<int64_t> soff(nsub + 1, 0), xo(nsub + 1, 0);
-            std::vector<int32_t> ovs(h->sum_local);
             std::vector<int2> tit;
             h->tc.h_citem_off.assign(h->ncol + 1, 0);
             for (int c = 0; c < h->ncol; ++c) {
@@ -801,7 +807,6 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
                 const int nq = (int)(ov_off[q + 1] - ov_off[q]);
                 soff[q + 1] = soff[q] + (int64_t)((nq + 127) / 128) * Tq[q];
                 xo[q + 1] = xo[q] + Tq[q];
-                for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) ovs[a] = q;
             }
             std::vector<int2> tsl;
             h->tc.h_cslab_off.assign(h->ncol + 1, 0);
@@ -814,11 +819,9 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             h2d(h->tc.slabs, tsl.data(), tsl.size(), h->stream);
             h->tc.slab_off = h->arena.alloc<int64_t>(nsub + 1);
             h->tc.xoff = h->arena.alloc<int64_t>(nsub + 1);
-            h->tc.ov_sub = h->arena.alloc<int32_t>(h->sum_local);
             h->tc.items = h->arena.alloc<int2>(tit.size());
             h2d(h->tc.slab_off, soff.data(), nsub + 1, h->stream);
             h2d(h->tc.xoff, xo.data(), nsub + 1, h->stream);
-            h2d(h->tc.ov_sub, ovs.data(), h->sum_local, h->stream);
             h2d(h->tc.items, tit.data(), tit.size(), h->stream);
             h->tc.A = h->arena.alloc<__nv_bfloat16>((size_t)soff[nsub] * 128 * 32);
             h->tc.x_elems = xo[nsub] * (int64_t)DDG_MCHUNK * 32;

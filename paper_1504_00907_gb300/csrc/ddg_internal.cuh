@@ -34,6 +34,7 @@
 #define DDG_CT 64        // coarse factor tile edge
 #define DDG_KMAX 32      // largest supported number of generators
 #define DDG_RED_BLOCKS 1216  // blocks of the deterministic reductions (8 x 152 SMs)
+#define DDG_GATHER_SPLIT_CHUNKS 8  // chunks per subdomain above which the gather is a kernel of its own
 #define DDG_MCHUNK 64        // right-hand sides per batched PCG group
 
 // ---------------------------------------------------------------- errors
@@ -154,7 +155,6 @@ struct TcData {
     __nv_bfloat16* X = nullptr;    // residual slabs N x 32 per subdomain
     int64_t* slab_off = nullptr;   // [nsub + 1] in A slabs
     int64_t* xoff = nullptr;       // [nsub + 1] in X slabs
-    int32_t* ov_sub = nullptr;     // [sum_local] sweep position of each local row
     int2* items = nullptr;         // (sweep position, 128-row block) per colour
     std::vector<int> h_citem_off;
     int2* slabs = nullptr;         // (sweep position, 32-row K slab) per colour
@@ -212,6 +212,10 @@ struct ddg_handle_s {
     int32_t* nchunks = nullptr;
     int32_t* first_item = nullptr;
     unsigned* counters = nullptr;
+    int32_t* ov_sub = nullptr;      // [sum_local] sweep position of each local row
+    // subdomains cut into many chunks sum their chunk partials in a separate
+    // row-parallel kernel instead of in the CTA that finishes last
+    bool split_gather = false;
     double* inv64 = nullptr;
     float* inv32 = nullptr;
     __nv_bfloat16* inv16 = nullptr;

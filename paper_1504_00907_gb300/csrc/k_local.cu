@@ -13,7 +13,9 @@
 // the bytes of a dense GEMV.  Work items are chunks of consecutive tiles of
 // one subdomain; the CTA that finishes a subdomain's last chunk sums the
 // chunk partials in a fixed order and scatters into z, so the result is
-// deterministic.
+// deterministic.  Large subdomains (many chunks) leave that sum to a
+// row-parallel gather kernel with the same order, which keeps one CTA's
+// serial sum off the end of the launch.
 #include "ddg_internal.cuh"
 #include "dev_common.cuh"
 
@@ -375,7 +377,7 @@ template <> struct Cvt<__nv_bfloat16, float> {
 
 constexpr int LS_WARPS = 8;
 
-template <typename E, typename V>
+template <typename E, typename V, bool SPLIT>
 __global__ void __launch_bounds__(LS_WARPS * 32) local_solve_kernel(
     const int4* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
     const int32_t* __restrict__ ov_nodes, const int64_t* __restrict__ tile_off,
@@ -463,6 +465,7 @@ __global__ void __launch_bounds__(LS_WARPS * 32) local_solve_kernel(
         for (int w = 0; w < LS_WARPS; ++w) s += yw[w * NP + i];
         pout[i] = s;
     }
+    if (SPLIT) return;  // local_gather_kernel sums the chunks
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -480,6 +483,36 @@ __global__ void __launch_bounds__(LS_WARPS * 32) local_solve_kernel(
         z[gnode] += s;
     }
     if (threadIdx.x == 0) counter[q] = 0u;
+}
+
+// z[Omega~_i] += sum over the chunks of subdomain i of their partials, one
+// thread per local row of the colour; the chunks are summed in the same
+// fixed order as in the last-CTA path, so both give the same bits.
+template <typename V>
+__global__ void local_gather_kernel(int64_t a0, int64_t a1, const int32_t* __restrict__ ov_sub,
+                                    const int64_t* __restrict__ ov_off,
+                                    const int32_t* __restrict__ ov_nodes,
+                                    const int32_t* __restrict__ nchunks,
+                                    const int32_t* __restrict__ first_item,
+                                    const V* __restrict__ partial, int Tmax, V* __restrict__ z) {
+    const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= a1) return;
+    const int q = ov_sub[a];
+    const int i = (int)(a - ov_off[q]);
+    const int nc = nchunks[q];
+    const size_t stride = (size_t)Tmax * DDG_LT;
+    const V* p = partial + (size_t)first_item[q] * stride + i;
+    V s = (V)0;
+    int c = 0;
+    for (; c + 8 <= nc; c += 8) {
+        V v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __ldcg(p + (size_t)(c + k) * stride);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += v[k];
+    }
+    for (; c < nc; ++c) s += __ldcg(p + (size_t)c * stride);
+    z[ov_nodes[a]] += s;
 }
 
 }  // namespace
@@ -536,12 +569,20 @@ static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, 
     const int i0 = h->h_citem_off[c], i1 = h->h_citem_off[c + 1];
     if (i1 <= i0) return;
     const size_t smem = (size_t)(1 + LS_WARPS) * h->Tmax * DDG_LT * sizeof(V);
-    auto kern = local_solve_kernel<E, V>;
+    auto kern = h->split_gather ? local_solve_kernel<E, V, true> : local_solve_kernel<E, V, false>;
     kern<<<i1 - i0, LS_WARPS * 32, smem, h->stream>>>(h->items, i0, h->ov_off, h->ov_nodes,
                                                       h->tile_off, h->Tq, h->nchunks,
                                                       h->first_item, inv, res, partial,
                                                       h->counters, z, h->Tmax);
     DDG_CHECK_LAUNCH();
+    if (h->split_gather) {
+        const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
+        const unsigned blocks = (unsigned)((a1 - a0 + 255) / 256);
+        local_gather_kernel<V><<<blocks, 256, 0, h->stream>>>(a0, a1, h->ov_sub, h->ov_off,
+                                                              h->ov_nodes, h->nchunks,
+                                                              h->first_item, partial, h->Tmax, z);
+        DDG_CHECK_LAUNCH();
+    }
 }
 
 // The dynamic shared-memory limit is a property of the kernel, shared by all
@@ -551,7 +592,9 @@ static void configure_local_solve(int Tmax) {
     static int configured = 0;
     const int smem = (int)((size_t)(1 + LS_WARPS) * Tmax * DDG_LT * sizeof(V));
     if (smem <= configured) return;
-    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V>,
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured = smem;
 }

@@ -281,3 +281,25 @@ def test_coarse_reproduces_generators_any_size():
         Fj = prob.F[:, j]
         z = solver.coarse_correction(dev(prob.A @ Fj)).cpu().numpy()
         assert rel(z, Fj) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["poisson3d_24", "elasticity_q1_6"])
+def test_many_chunk_gather_matches_oracle(name):
+    # four packed tiles per chunk cut every subdomain into more than eight
+    # chunks, so their partials are summed by the row-parallel gather kernel
+    from paper_1504_00907_gb300 import ddg
+    prob, _, oracle = setup_case(name)
+    s = ddg.Solver.from_problem(prob, precision="fp64", keep=("fp64", "fp32"), chunk_tiles=4)
+    r = np.random.default_rng(9).standard_normal(prob.n)
+    assert rel(s.apply(dev(r)).cpu().numpy(), oracle.apply(r)) <= 1e-11
+    s.set_precision("fp32")
+    assert rel(s.apply(dev(r)).cpu().numpy(), oracle.apply(r)) <= 1e-5
+    ref = orc.pcg(oracle.A, prob.f, oracle.apply, tol=1e-8)
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-7)):
+        s.set_precision(prec)
+        u, it, rr, st = s.solve(dev(prob.f), tol=1e-8)
+        u2 = s.solve(dev(prob.f), tol=1e-8)[0]
+        assert st == 0 and abs(it - ref.iters) <= 1
+        assert rel(u.cpu().numpy(), ref.u) <= tol
+        assert torch.equal(u, u2)
+    s.close()
