@@ -742,7 +742,8 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         ov.clear();
         ov.shrink_to_fit();
 
-        // ---- local-solve work items: chunks of consecutive packed tiles
+        // ---- local-solve work items: bands of whole tile rows of the packed
+        // upper triangle, about `chunk` tiles and at most DDG_BAND_ROWS rows each
         {
             const int chunk = o.chunk_tiles > 0 ? o.chunk_tiles : 96;
             std::vector<int4> items;
@@ -750,12 +751,22 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             h->h_citem_off.assign(h->ncol + 1, 0);
             for (int c = 0; c < h->ncol; ++c) {
                 for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
-                    const int64_t P = (int64_t)Tq[q] * (Tq[q] + 1) / 2;
-                    const int nc = (int)std::max<int64_t>(1, (P + chunk - 1) / chunk);
-                    nch[q] = nc;
+                    const int T = Tq[q];
                     first[q] = (int)items.size();
-                    for (int t = 0; t < nc; ++t)
-                        items.push_back(make_int4(q, (int)(P * t / nc), (int)(P * (t + 1) / nc), 0));
+                    int I = 0;
+                    while (I < T) {
+                        const int I0 = I;
+                        int cnt = 0;
+                        while (I < T && I - I0 < DDG_BAND_ROWS) {
+                            const int len = T - I;
+                            // a further row only if it brings the band closer to `chunk` tiles
+                            if (cnt > 0 && cnt + len - chunk > chunk - cnt) break;
+                            cnt += len;
+                            ++I;
+                        }
+                        items.push_back(make_int4(q, I0, I, 0));
+                    }
+                    nch[q] = (int)items.size() - first[q];
                 }
                 h->h_citem_off[c + 1] = (int)items.size();
             }
@@ -768,11 +779,19 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             h2d(h->nchunks, nch.data(), nsub, h->stream);
             h2d(h->first_item, first.data(), nsub, h->stream);
             DDG_CUDA(cudaMemsetAsync(h->counters, 0, nsub * sizeof(unsigned), h->stream));
-            std::vector<int32_t> ovs(h->sum_local);
+            std::vector<int32_t> ovs(h->sum_local), rnc(h->sum_local);
             for (int q = 0; q < nsub; ++q)
-                for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) ovs[a] = q;
+                for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) {
+                    ovs[a] = q;
+                    const int row_tile = (int)((a - ov_off[q]) / DDG_LT);
+                    int c = 0;
+                    while (c < nch[q] && items[first[q] + c].y <= row_tile) ++c;
+                    rnc[a] = c;
+                }
             h->ov_sub = h->arena.alloc<int32_t>(h->sum_local);
+            h->row_nchunks = h->arena.alloc<int32_t>(h->sum_local);
             h2d(h->ov_sub, ovs.data(), h->sum_local, h->stream);
+            h2d(h->row_nchunks, rnc.data(), h->sum_local, h->stream);
             h->split_gather = *std::max_element(nch.begin(), nch.end()) > DDG_GATHER_SPLIT_CHUNKS;
             DDG_CUDA(cudaStreamSynchronize(h->stream));
         }

@@ -34,6 +34,7 @@
 #define DDG_CT 64        // coarse factor tile edge
 #define DDG_KMAX 32      // largest supported number of generators
 #define DDG_RED_BLOCKS 1216  // blocks of the deterministic reductions (8 x 152 SMs)
+#define DDG_BAND_ROWS 16     // tile rows per local-solve work item at most
 #define DDG_GATHER_SPLIT_CHUNKS 8  // chunks per subdomain above which the gather is a kernel of its own
 #define DDG_MCHUNK 64        // right-hand sides per batched PCG group
 
@@ -213,6 +214,7 @@ struct ddg_handle_s {
     int32_t* first_item = nullptr;
     unsigned* counters = nullptr;
     int32_t* ov_sub = nullptr;      // [sum_local] sweep position of each local row
+    int32_t* row_nchunks = nullptr; // [sum_local] chunks whose band starts at or above the row
     // subdomains cut into many chunks sum their chunk partials in a separate
     // row-parallel kernel instead of in the CTA that finishes last
     bool split_gather = false;

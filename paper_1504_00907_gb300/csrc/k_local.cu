@@ -377,92 +377,101 @@ template <> struct Cvt<__nv_bfloat16, float> {
 
 constexpr int LS_WARPS = 8;
 
+// x and yT (Tmax * 32 each) and the per-warp row slices yR
+template <typename V>
+constexpr size_t local_solve_smem(int Tmax) {
+    return (2 * (size_t)Tmax * DDG_LT + (size_t)LS_WARPS * DDG_BAND_ROWS * DDG_LT) * sizeof(V);
+}
+
+// One work item = a band of whole tile rows [I0, I1) of one subdomain's
+// packed upper triangle.  Tile (I, J) belongs to warp J mod LS_WARPS, so the
+// transposed products B^T x_I land in y[J] entries that only one warp
+// writes (one shared accumulator yT, no atomics); each warp keeps the row
+// products B x_J of the current row in a register and stores them once per
+// row in its slice of yR (at most DDG_BAND_ROWS rows per band).  The chunk
+// result yT + sum_w yR[w] is formed in a fixed order, so it is deterministic.
 template <typename E, typename V, bool SPLIT>
-__global__ void __launch_bounds__(LS_WARPS * 32) local_solve_kernel(
+__global__ void __launch_bounds__(LS_WARPS * 32, sizeof(V) == 4 ? 4 : 2) local_solve_kernel(
     const int4* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
     const int32_t* __restrict__ ov_nodes, const int64_t* __restrict__ tile_off,
     const int32_t* __restrict__ Tq, const int32_t* __restrict__ nchunks,
-    const int32_t* __restrict__ first_item, const E* __restrict__ inv,
-    const V* __restrict__ res, V* __restrict__ partial, unsigned* __restrict__ counter,
-    V* __restrict__ z, int Tmax) {
+    const int32_t* __restrict__ first_item, const int32_t* __restrict__ row_nchunks,
+    const E* __restrict__ inv, const V* __restrict__ res, V* __restrict__ partial,
+    unsigned* __restrict__ counter, V* __restrict__ z, int Tmax) {
     using L = Lay<E>;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* x = reinterpret_cast<V*>(smraw);
-    V* yw = x + Tmax * DDG_LT;
+    V* yT = x + Tmax * DDG_LT;
+    V* yR = yT + Tmax * DDG_LT;   // [LS_WARPS][DDG_BAND_ROWS][32]
     __shared__ int am_last;
 
     const int gi = item_base + blockIdx.x;
     const int4 it = items[gi];
-    const int q = it.x, tb = it.y, te = it.z;
+    const int q = it.x, I0 = it.y, I1 = it.z;
     const int64_t o = ov_off[q];
     const int n = (int)(ov_off[q + 1] - o);
     const int T = Tq[q];
     const int NP = T * DDG_LT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    V* my = yw + warp * NP;
 
-    for (int i = threadIdx.x; i < NP; i += blockDim.x) x[i] = i < n ? res[o + i] : (V)0;
-    for (int i = threadIdx.x; i < LS_WARPS * NP; i += blockDim.x) yw[i] = (V)0;
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+        x[i] = i < n ? res[o + i] : (V)0;
+        yT[i] = (V)0;
+    }
     __syncthreads();
 
     const int g = lane / L::LPR, j = lane % L::LPR;
     const int idx = j * L::VEC + g;   // row/col owned by this lane after the reductions
-    const E* base = inv + (size_t)tile_off[q] * 1024;
+    const E* base = inv + (size_t)tile_off[q] * 1024 + g * 32 + j * L::VEC;
+    V* myR = yR + warp * (DDG_BAND_ROWS * DDG_LT);
 
-    int t = tb + warp;
-    int I = 0, J = 0;
-    if (t < te) {
-        int rem = t;
-        while (rem >= T - I) {
-            rem -= T - I;
-            ++I;
-        }
-        J = I + rem;
-    }
-    for (; t < te; t += LS_WARPS) {
-        const E* tp = base + (size_t)t * 1024 + g * 32 + j * L::VEC;
-        V e[L::NIT][L::VEC];
+    for (int I = I0; I < I1; ++I) {
+        // packed index of tile (I, I): rows 0..I-1 hold T, T-1, ..., T-I+1 tiles
+        const size_t rowstart = (size_t)I * T - (size_t)I * (I - 1) / 2;
+        V racc = (V)0;
+        for (int J = I + ((warp - I) % LS_WARPS + LS_WARPS) % LS_WARPS; J < T; J += LS_WARPS) {
+            const E* tp = base + (rowstart + (J - I)) * 1024;
+            V e[L::NIT][L::VEC];
 #pragma unroll
-        for (int k = 0; k < L::NIT; ++k) Cvt<E, V>::load(tp + k * L::RPI * 32, e[k]);
-        V xj[L::VEC];
+            for (int k = 0; k < L::NIT; ++k) Cvt<E, V>::load(tp + k * L::RPI * 32, e[k]);
+            V xj[L::VEC];
 #pragma unroll
-        for (int v = 0; v < L::VEC; ++v) xj[v] = x[J * DDG_LT + j * L::VEC + v];
-        V rp[L::NIT];
-#pragma unroll
-        for (int k = 0; k < L::NIT; ++k) {
-            V s = (V)0;
-#pragma unroll
-            for (int v = 0; v < L::VEC; ++v) s = fma(e[k][v], xj[v], s);
-            rp[k] = s;
-        }
-        const V rs = ddgdev::reduce_scatter<L::NIT, 1>(rp, j);
-        my[I * DDG_LT + idx] += rs;
-        if (I != J) {
-            V cp[L::VEC];
-#pragma unroll
-            for (int v = 0; v < L::VEC; ++v) cp[v] = (V)0;
+            for (int v = 0; v < L::VEC; ++v) xj[v] = x[J * DDG_LT + j * L::VEC + v];
+            V rp[L::NIT];
 #pragma unroll
             for (int k = 0; k < L::NIT; ++k) {
-                const V xi = x[I * DDG_LT + k * L::RPI + g];
+                V s = (V)0;
 #pragma unroll
-                for (int v = 0; v < L::VEC; ++v) cp[v] = fma(e[k][v], xi, cp[v]);
+                for (int v = 0; v < L::VEC; ++v) s = fma(e[k][v], xj[v], s);
+                rp[k] = s;
             }
-            const V cs = ddgdev::reduce_scatter<L::VEC, L::LPR>(cp, g);
-            my[J * DDG_LT + idx] += cs;
+            racc += ddgdev::reduce_scatter<L::NIT, 1>(rp, j);
+            if (I != J) {
+                V cp[L::VEC];
+#pragma unroll
+                for (int v = 0; v < L::VEC; ++v) cp[v] = (V)0;
+#pragma unroll
+                for (int k = 0; k < L::NIT; ++k) {
+                    const V xi = x[I * DDG_LT + k * L::RPI + g];
+#pragma unroll
+                    for (int v = 0; v < L::VEC; ++v) cp[v] = fma(e[k][v], xi, cp[v]);
+                }
+                yT[J * DDG_LT + idx] += ddgdev::reduce_scatter<L::VEC, L::LPR>(cp, g);
+            }
         }
-        // advance (I, J) by LS_WARPS tiles in row-major upper-triangle order
-        J += LS_WARPS;
-        while (J >= T && I < T) {
-            J = J - T + I + 1;
-            ++I;
-        }
+        myR[(I - I0) * DDG_LT + idx] = racc;
     }
     __syncthreads();
+    // rows above the band get nothing from it: only rows >= 32 I0 are stored,
+    // and the chunk sums stop at the last band that starts at or above a row
     V* pout = partial + (size_t)gi * Tmax * DDG_LT;
-    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
-        V s = (V)0;
+    for (int i = I0 * DDG_LT + threadIdx.x; i < NP; i += blockDim.x) {
+        V s = yT[i];
+        const int I = i >> 5;
+        if (I >= I0 && I < I1) {
 #pragma unroll
-        for (int w = 0; w < LS_WARPS; ++w) s += yw[w * NP + i];
+            for (int w = 0; w < LS_WARPS; ++w) s += yR[(w * DDG_BAND_ROWS + I - I0) * DDG_LT + (i & 31)];
+        }
         pout[i] = s;
     }
     if (SPLIT) return;  // local_gather_kernel sums the chunks
@@ -475,10 +484,11 @@ __global__ void __launch_bounds__(LS_WARPS * 32) local_solve_kernel(
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    const int fi = first_item[q], nc = nchunks[q];
+    const int fi = first_item[q];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         V s = (V)0;
-        for (int c = 0; c < nc; ++c) s += __ldcg(partial + (size_t)(fi + c) * Tmax * DDG_LT + i);
+        const int nci = row_nchunks[o + i];
+        for (int c = 0; c < nci; ++c) s += __ldcg(partial + (size_t)(fi + c) * Tmax * DDG_LT + i);
         const int gnode = ov_nodes[o + i];
         z[gnode] += s;
     }
@@ -494,14 +504,16 @@ __global__ void local_gather_kernel(int64_t a0, int64_t a1, const int32_t* __res
                                     const int32_t* __restrict__ ov_nodes,
                                     const int32_t* __restrict__ nchunks,
                                     const int32_t* __restrict__ first_item,
+                                    const int32_t* __restrict__ row_nchunks,
                                     const V* __restrict__ partial, int Tmax, V* __restrict__ z) {
     const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= a1) return;
     const int q = ov_sub[a];
     const int i = (int)(a - ov_off[q]);
-    const int nc = nchunks[q];
+    const int fi = first_item[q];
+    const int nc = row_nchunks[a];
     const size_t stride = (size_t)Tmax * DDG_LT;
-    const V* p = partial + (size_t)first_item[q] * stride + i;
+    const V* p = partial + (size_t)fi * stride + i;
     V s = (V)0;
     int c = 0;
     for (; c + 8 <= nc; c += 8) {
@@ -568,19 +580,20 @@ template <typename E, typename V>
 static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, V* partial, V* z) {
     const int i0 = h->h_citem_off[c], i1 = h->h_citem_off[c + 1];
     if (i1 <= i0) return;
-    const size_t smem = (size_t)(1 + LS_WARPS) * h->Tmax * DDG_LT * sizeof(V);
+    const size_t smem = local_solve_smem<V>(h->Tmax);
     auto kern = h->split_gather ? local_solve_kernel<E, V, true> : local_solve_kernel<E, V, false>;
     kern<<<i1 - i0, LS_WARPS * 32, smem, h->stream>>>(h->items, i0, h->ov_off, h->ov_nodes,
                                                       h->tile_off, h->Tq, h->nchunks,
-                                                      h->first_item, inv, res, partial,
-                                                      h->counters, z, h->Tmax);
+                                                      h->first_item, h->row_nchunks, inv, res,
+                                                      partial, h->counters, z, h->Tmax);
     DDG_CHECK_LAUNCH();
     if (h->split_gather) {
         const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
         const unsigned blocks = (unsigned)((a1 - a0 + 255) / 256);
         local_gather_kernel<V><<<blocks, 256, 0, h->stream>>>(a0, a1, h->ov_sub, h->ov_off,
                                                               h->ov_nodes, h->nchunks,
-                                                              h->first_item, partial, h->Tmax, z);
+                                                              h->first_item, h->row_nchunks,
+                                                              partial, h->Tmax, z);
         DDG_CHECK_LAUNCH();
     }
 }
@@ -590,7 +603,7 @@ static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, 
 template <typename E, typename V>
 static void configure_local_solve(int Tmax) {
     static int configured = 0;
-    const int smem = (int)((size_t)(1 + LS_WARPS) * Tmax * DDG_LT * sizeof(V));
+    const int smem = (int)local_solve_smem<V>(Tmax);
     if (smem <= configured) return;
     DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
