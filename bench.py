@@ -539,7 +539,7 @@ def main():
                                    bytes_per_launch) if bytes_per_launch else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": "local_solve_kernel<float,float> (packed-symmetric A_i^-1 GEMV + scatter)",
+                "kernel": "local_solve_kernel<float,float,false> (row-band packed-symmetric A_i^-1 GEMV, fused chunk sum and scatter)",
                 "peak_source": "measured" if pk else "fallback",
                 "launches_timed": ls["timed"], "avg_launch_ms": ls["ms"] / max(1, ls["timed"]),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
