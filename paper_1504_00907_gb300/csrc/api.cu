@@ -613,6 +613,7 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         h->opt = o;
         h->precision = o.precision;
         if (const char* ev = std::getenv("DDG_NO_GRAPHS")) h->use_graphs = ev[0] == '0';
+        if (const char* ev = std::getenv("DDG_PDL")) h->use_pdl = ev[0] != '0';
         h->use_coarse = o.use_coarse;
         h->stream = (cudaStream_t)stream;
         const int64_t n = A->n;

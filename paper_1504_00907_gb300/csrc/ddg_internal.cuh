@@ -218,6 +218,9 @@ struct ddg_handle_s {
     // subdomains cut into many chunks sum their chunk partials in a separate
     // row-parallel kernel instead of in the CTA that finishes last
     bool split_gather = false;
+    // dependent launches of chained kernels may start before their predecessor
+    // ends (programmatic dependent launch); DDG_PDL=0 turns it off
+    bool use_pdl = true;
     double* inv64 = nullptr;
     float* inv32 = nullptr;
     __nv_bfloat16* inv16 = nullptr;

@@ -390,38 +390,64 @@ __global__ void profile_fill_kernel(ProfileMat M, const int32_t* __restrict__ vl
 // lane streams 16-byte chunks of the row and of x.
 template <typename V> struct Vec4;
 template <> struct Vec4<float> {
-    static __device__ __forceinline__ float dot(const float* m, const float* x) {
-        const float4 a = __ldcs(reinterpret_cast<const float4*>(m));
+    using M = float4;
+    static __device__ __forceinline__ M load(const float* m) {
+        return __ldcs(reinterpret_cast<const float4*>(m));
+    }
+    static __device__ __forceinline__ float dot(const M& a, const float* x) {
         const float4 b = *reinterpret_cast<const float4*>(x);
         return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
     }
+    static __device__ __forceinline__ float dot(const float* m, const float* x) { return dot(load(m), x); }
 };
 template <> struct Vec4<double> {
-    static __device__ __forceinline__ double dot(const double* m, const double* x) {
-        const double2 a0 = __ldcs(reinterpret_cast<const double2*>(m));
-        const double2 a1 = __ldcs(reinterpret_cast<const double2*>(m + 2));
+    struct M {
+        double2 a0, a1;
+    };
+    static __device__ __forceinline__ M load(const double* m) {
+        return {__ldcs(reinterpret_cast<const double2*>(m)), __ldcs(reinterpret_cast<const double2*>(m + 2))};
+    }
+    static __device__ __forceinline__ double dot(const M& a, const double* x) {
         const double2 b0 = *reinterpret_cast<const double2*>(x);
         const double2 b1 = *reinterpret_cast<const double2*>(x + 2);
-        return a0.x * b0.x + a0.y * b0.y + a1.x * b1.x + a1.y * b1.y;
+        return a.a0.x * b0.x + a.a0.y * b0.y + a.a1.x * b1.x + a.a1.y * b1.y;
     }
+    static __device__ __forceinline__ double dot(const double* m, const double* x) { return dot(load(m), x); }
 };
 
 constexpr int GEMV_TPR = 128;   // threads per row: a whole row's loads in flight
+constexpr int GEMV_PF = 8;      // 16-byte chunks per thread loaded before the dependency wait
 
+// Launched as a programmatic dependent of the previous step: the matrix row
+// does not depend on that step, so it is read first; griddepcontrol.wait
+// then orders the reads of x and a after the previous kernel's writes.
+// Without the launch attribute both griddepcontrol instructions are no-ops.
 template <typename V, typename MV>
 __global__ void __launch_bounds__(GEMV_TPR) profile_gemv_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-    const MV* __restrict__ vals, int r0, const V* __restrict__ x, const V* __restrict__ a, V sign,
-    V* __restrict__ out) {
+    const MV* __restrict__ vals, int r0, const V* x, const V* a, V sign, V* out) {
     __shared__ V sh[GEMV_TPR / 32];
     const int i = r0 + blockIdx.x;
     const int l = lo[i];
     const int nch = (hi[i] - l) >> 2;
     const MV* rv = vals + rowptr[i];
+    typename Vec4<V>::M m[GEMV_PF];
+#pragma unroll
+    for (int k = 0; k < GEMV_PF; ++k) {
+        const int c = threadIdx.x + k * GEMV_TPR;
+        if (c < nch) m[k] = Vec4<V>::load(rv + 4 * c);
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const V* xv = x + l;
     V s = 0;
-#pragma unroll 4
-    for (int c = threadIdx.x; c < nch; c += GEMV_TPR) s += Vec4<V>::dot(rv + 4 * c, xv + 4 * c);
+#pragma unroll
+    for (int k = 0; k < GEMV_PF; ++k) {
+        const int c = threadIdx.x + k * GEMV_TPR;
+        if (c < nch) s += Vec4<V>::dot(m[k], xv + 4 * c);
+    }
+    for (int c = threadIdx.x + GEMV_PF * GEMV_TPR; c < nch; c += GEMV_TPR)
+        s += Vec4<V>::dot(Vec4<V>::load(rv + 4 * c), xv + 4 * c);
     s = ddgdev::warp_sum(s);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
@@ -726,16 +752,23 @@ template <typename V>
 static void gemv(ddg_handle h, const ProfileMat& M, int r0, int r1, const V* x, const V* a, V sign,
                  V* out) {
     if (r1 <= r0) return;
-    const unsigned blocks = (unsigned)(r1 - r0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(r1 - r0));
+    cfg.blockDim = dim3(GEMV_TPR);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = h->use_pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (sizeof(V) == 8)
-        profile_gemv_kernel<double, double><<<blocks, GEMV_TPR, 0, h->stream>>>(
-            M.rowptr, M.lo, M.hi, M.v64, r0, (const double*)x, (const double*)a, (double)sign,
-            (double*)out);
+        DDG_CUDA(cudaLaunchKernelEx(&cfg, profile_gemv_kernel<double, double>, (const int64_t*)M.rowptr,
+                                    (const int32_t*)M.lo, (const int32_t*)M.hi, (const double*)M.v64, r0,
+                                    (const double*)x, (const double*)a, (double)sign, (double*)out));
     else
-        profile_gemv_kernel<float, float><<<blocks, GEMV_TPR, 0, h->stream>>>(
-            M.rowptr, M.lo, M.hi, M.v32, r0, (const float*)x, (const float*)a, (float)sign,
-            (float*)out);
-    DDG_CHECK_LAUNCH();
+        DDG_CUDA(cudaLaunchKernelEx(&cfg, profile_gemv_kernel<float, float>, (const int64_t*)M.rowptr,
+                                    (const int32_t*)M.lo, (const int32_t*)M.hi, (const float*)M.v32, r0,
+                                    (const float*)x, (const float*)a, (float)sign, (float*)out));
 }
 
 template <typename V>
