@@ -621,6 +621,7 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         h->nnz = A->rowptr[n];
         for (int64_t g = 0; g < n; ++g)
             h->max_row_nnz = std::max<int>(h->max_row_nnz, (int)(A->rowptr[g + 1] - A->rowptr[g]));
+        h->wide_rows = h->nnz >= 32 * n;
         h->stencil_kind = A->stencil_kind;
         h->dim = A->dim;
         h->nx = A->nx > 0 ? A->nx : 1;

@@ -103,6 +103,7 @@ static inline void d2h(T* dst, const T* src, size_t count, cudaStream_t s) {
         else if ((h)->stencil_kind == DDG_STENCIL_5PT_2D) { CALL(DDG_STENCIL_5PT_2D); } \
         else if ((h)->max_row_nnz <= 8) { CALL(100); }                             \
         else if ((h)->max_row_nnz <= 16) { CALL(101); }                            \
+        else if ((h)->wide_rows) { CALL(102); }                                    \
         else { CALL(DDG_STENCIL_NONE); }                                           \
     } while (0)
 
@@ -175,6 +176,7 @@ struct ddg_handle_s {
     // ---- fine problem
     int64_t n = 0, nnz = 0;
     int max_row_nnz = 0;        // longest CSR row (selects the unrolled row kernels)
+    bool wide_rows = false;     // rows average >= 32 entries: a lane group per row
     int stencil_kind = 0, dim = 0, nx = 1, ny = 1, nz = 1, dpn = 1;
     int64_t* rowptr = nullptr;
     int32_t* col = nullptr;
@@ -317,7 +319,6 @@ void coarse_prolong(ddg_handle h, int prec);
 
 // k_cg.cu
 void spmv64(ddg_handle h, const double* x, double* y, bool dot_with_x, int slot);
-void spmv_prec(ddg_handle h, const float* x, float* y);
 void dot64(ddg_handle h, const double* a, const double* b, int slot);
 void cg_update_ur(ddg_handle h);
 void cg_dots_after_precond(ddg_handle h, int prec, bool first, int pr);

@@ -87,6 +87,29 @@ __device__ __forceinline__ V csr_row_dot_unrolled(int g, const int64_t* __restri
     return s;
 }
 
+// Long CSR rows (Q1 elasticity: 81 entries) go to groups of CSRW_G lanes:
+// lane l of a group takes entries l, l + G, ... of its row (coalesced column
+// and value loads) and the group sums by a fixed butterfly, after which every
+// lane of the group holds the row's dot product.  All lanes of the warp must
+// call it; `live` masks the loads of groups past the last row.
+constexpr int SK_CSRW = 102;
+constexpr int CSRW_G = 16;
+
+template <int G, typename V, typename AV>
+__device__ __forceinline__ V csr_row_dot_group(int g, bool live, const int64_t* __restrict__ rowptr,
+                                               const int32_t* __restrict__ col,
+                                               const AV* __restrict__ val, const V* __restrict__ x) {
+    V s = 0;
+    if (live) {
+        const int sub = threadIdx.x & (G - 1);
+        const int64_t e1 = rowptr[g + 1];
+        for (int64_t e = rowptr[g] + sub; e < e1; e += G) s = fma((V)val[e], x[col[e]], s);
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 struct GridBar {
     unsigned count;
     unsigned gen;

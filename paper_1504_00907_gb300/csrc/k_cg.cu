@@ -40,7 +40,8 @@ __device__ bool reduce_last(double (&v)[NV], double* partials, unsigned* counter
 
 // y = A x over CSR rows; optionally dot = x^T y into scal[S_PQ] and
 // alpha = rho / p^T A p into scal[S_ALPHA] (breakdown flag if p^T A p <= 0)
-template <bool DOT>
+// G = 1: a thread per row; G > 1: a group of G lanes per row (long rows)
+template <bool DOT, int G>
 __global__ void __launch_bounds__(RT) spmv_csr64_kernel(int64_t n, const int64_t* __restrict__ rowptr,
                                                         const int32_t* __restrict__ col,
                                                         const double* __restrict__ val,
@@ -48,12 +49,26 @@ __global__ void __launch_bounds__(RT) spmv_csr64_kernel(int64_t n, const int64_t
                                                         double* __restrict__ y, double* partials,
                                                         unsigned* counter, double* scal) {
     double acc[1] = {0.0};
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma(val[e], x[col[e]], s);
-        y[g] = s;
-        if (DOT) acc[0] = fma(x[g], s, acc[0]);
+    if (G == 1) {
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
+             g += (int64_t)gridDim.x * blockDim.x) {
+            double s = 0.0;
+            for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma(val[e], x[col[e]], s);
+            y[g] = s;
+            if (DOT) acc[0] = fma(x[g], s, acc[0]);
+        }
+    } else {
+        // the trip count depends on the block only, so all lanes reach the shuffles
+        constexpr int RPB = RT / G;
+        for (int64_t base = (int64_t)blockIdx.x * RPB; base < n; base += (int64_t)gridDim.x * RPB) {
+            const int64_t g = base + threadIdx.x / G;
+            const bool live = g < n;
+            const double s = ddgdev::csr_row_dot_group<G>((int)(live ? g : 0), live, rowptr, col, val, x);
+            if (live && (threadIdx.x & (G - 1)) == 0) {
+                y[g] = s;
+                if (DOT) acc[0] = fma(x[g], s, acc[0]);
+            }
+        }
     }
     if (!DOT) return;
     double tot[1];
@@ -97,18 +112,6 @@ __global__ void __launch_bounds__(RT) spmv_lap64_kernel(int nx, int ny, int nz,
         scal[S_ALPHA] = scal[S_RZ] / pq;
         if (!(pq > 0.0) || pq != pq) scal[S_FLAG] = 1.0;
     }
-}
-
-// y = A x in the preconditioner precision (CSR)
-template <typename V, typename AV>
-__global__ void spmv_csr_kernel(int64_t n, const int64_t* __restrict__ rowptr,
-                                const int32_t* __restrict__ col, const AV* __restrict__ val,
-                                const V* __restrict__ x, V* __restrict__ y) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
-    V s = 0;
-    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma((V)val[e], x[col[e]], s);
-    y[g] = s;
 }
 
 // u += alpha p; r -= alpha q; ||r||^2 -> scal[S_RR]
@@ -303,8 +306,9 @@ void spmv64(ddg_handle h, const double* x, double* y, bool dot, int /*slot*/) {
         if (dot) spmv_lap64_kernel<true, 2><<<G, RT, 0, h->stream>>>(h->nx, h->ny, 1, x, y, h->red_partials, h->red_counter, h->scal);
         else spmv_lap64_kernel<false, 2><<<G, RT, 0, h->stream>>>(h->nx, h->ny, 1, x, y, h->red_partials, h->red_counter, h->scal);
     } else {
-        if (dot) spmv_csr64_kernel<true><<<G, RT, 0, h->stream>>>(h->n, h->rowptr, h->col, h->val64, x, y, h->red_partials, h->red_counter, h->scal);
-        else spmv_csr64_kernel<false><<<G, RT, 0, h->stream>>>(h->n, h->rowptr, h->col, h->val64, x, y, h->red_partials, h->red_counter, h->scal);
+        auto kern = h->wide_rows ? (dot ? spmv_csr64_kernel<true, ddgdev::CSRW_G> : spmv_csr64_kernel<false, ddgdev::CSRW_G>)
+                                 : (dot ? spmv_csr64_kernel<true, 1> : spmv_csr64_kernel<false, 1>);
+        kern<<<G, RT, 0, h->stream>>>(h->n, h->rowptr, h->col, h->val64, x, y, h->red_partials, h->red_counter, h->scal);
     }
     DDG_CHECK_LAUNCH();
 }
@@ -353,12 +357,6 @@ void convert_to_float(ddg_handle h, const double* src, float* dst) {
 
 void convert_to_double(ddg_handle h, const float* src, double* dst) {
     to_double_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, src, dst);
-    DDG_CHECK_LAUNCH();
-}
-
-void spmv_prec(ddg_handle h, const float* x, float* y) {
-    spmv_csr_kernel<float, float><<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(
-        h->n, h->rowptr, h->col, h->val32, x, y);
     DDG_CHECK_LAUNCH();
 }
 

@@ -526,35 +526,56 @@ __global__ void __launch_bounds__(256) coarse_restrict_kernel(
     V acc[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) acc[j] = 0;
-    for (int64_t a = sub_off[s] + threadIdx.x; a < sub_off[s + 1]; a += blockDim.x) {
-        const int g = sub_nodes[a];
-        V w = r[g];
-        if (residual) {
-            if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
-                const int i = g % nx, jj = (g / nx) % ny;
-                V az = (SK == DDG_STENCIL_7PT_3D ? (V)6 : (V)4) * z[g];
-                if (i > 0) az -= z[g - 1];
-                if (i < nx - 1) az -= z[g + 1];
-                if (jj > 0) az -= z[g - nx];
-                if (jj < ny - 1) az -= z[g + nx];
-                if (SK == DDG_STENCIL_7PT_3D) {
-                    const int k = g / (nx * ny);
-                    if (k > 0) az -= z[g - nx * ny];
-                    if (k < nz - 1) az -= z[g + nx * ny];
-                }
-                w -= az;
-            } else if (SK == ddgdev::SK_CSR8) {
-                w -= ddgdev::csr_row_dot_unrolled<8>(g, rowptr, col, val, z, 1, 0);
-            } else if (SK == ddgdev::SK_CSR16) {
-                w -= ddgdev::csr_row_dot_unrolled<16>(g, rowptr, col, val, z, 1, 0);
-            } else {
-                for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) w -= (V)val[e] * z[col[e]];
+    if constexpr (SK == ddgdev::SK_CSRW) {
+        // a group of CSRW_G lanes per row computes its residual; the group's
+        // first lane adds the row's Q contributions
+        constexpr int G = ddgdev::CSRW_G;
+        const int64_t a_end = sub_off[s + 1];
+        for (int64_t base = sub_off[s]; base < a_end; base += blockDim.x / G) {
+            const int64_t a = base + threadIdx.x / G;
+            const bool live = a < a_end;
+            const int g = live ? sub_nodes[a] : 0;
+            V az = 0;
+            if (residual) az = ddgdev::csr_row_dot_group<G>(g, live, rowptr, col, val, z);
+            if (live && (threadIdx.x & (G - 1)) == 0) {
+                const V w = r[g] - az;
+                const V* qa = Q + a * kmax;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < kmax) acc[j] = fma(qa[j], w, acc[j]);
             }
         }
-        const V* qa = Q + a * kmax;
+    } else {
+        for (int64_t a = sub_off[s] + threadIdx.x; a < sub_off[s + 1]; a += blockDim.x) {
+            const int g = sub_nodes[a];
+            V w = r[g];
+            if (residual) {
+                if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+                    const int i = g % nx, jj = (g / nx) % ny;
+                    V az = (SK == DDG_STENCIL_7PT_3D ? (V)6 : (V)4) * z[g];
+                    if (i > 0) az -= z[g - 1];
+                    if (i < nx - 1) az -= z[g + 1];
+                    if (jj > 0) az -= z[g - nx];
+                    if (jj < ny - 1) az -= z[g + nx];
+                    if (SK == DDG_STENCIL_7PT_3D) {
+                        const int k = g / (nx * ny);
+                        if (k > 0) az -= z[g - nx * ny];
+                        if (k < nz - 1) az -= z[g + nx * ny];
+                    }
+                    w -= az;
+                } else if (SK == ddgdev::SK_CSR8) {
+                    w -= ddgdev::csr_row_dot_unrolled<8>(g, rowptr, col, val, z, 1, 0);
+                } else if (SK == ddgdev::SK_CSR16) {
+                    w -= ddgdev::csr_row_dot_unrolled<16>(g, rowptr, col, val, z, 1, 0);
+                } else {
+                    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) w -= (V)val[e] * z[col[e]];
+                }
+            }
+            const V* qa = Q + a * kmax;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j < kmax) acc[j] = fma(qa[j], w, acc[j]);
+            for (int j = 0; j < 32; ++j)
+                if (j < kmax) acc[j] = fma(qa[j], w, acc[j]);
+        }
     }
     ddgdev::block_sum32(acc, red, out);
     const int ks = coff[s + 1] - coff[s];

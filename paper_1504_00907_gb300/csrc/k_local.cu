@@ -329,10 +329,21 @@ __global__ void local_residual_kernel(int64_t a0, int64_t a1, const int32_t* __r
                                       const AV* __restrict__ val, const V* __restrict__ r,
                                       const V* __restrict__ z, V* __restrict__ res, int z_zero,
                                       int nx, int ny, int nz) {
-    const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= a1) return;
-    const int g = ov_nodes[a];
-    res[a] = z_zero ? r[g] : residual_at<SK>(g, rowptr, col, val, r, z, nx, ny, nz);
+    if constexpr (SK == ddgdev::SK_CSRW) {
+        // a group of CSRW_G lanes per local row; the whole warp reaches the shuffles
+        constexpr int G = ddgdev::CSRW_G;
+        const int64_t a = a0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+        const bool live = a < a1;
+        const int g = live ? ov_nodes[a] : 0;
+        V s = 0;
+        if (!z_zero) s = ddgdev::csr_row_dot_group<G>(g, live, rowptr, col, val, z);
+        if (live && (threadIdx.x & (G - 1)) == 0) res[a] = r[g] - s;
+    } else {
+        const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (a >= a1) return;
+        const int g = ov_nodes[a];
+        res[a] = z_zero ? r[g] : residual_at<SK>(g, rowptr, col, val, r, z, nx, ny, nz);
+    }
 }
 
 // lane layout of a 32x32 tile for 16-byte loads of element type E:
@@ -556,7 +567,8 @@ void local_pack(ddg_handle h, int q0, int q1, const double* ws) {
 template <int SK>
 static void launch_residual(ddg_handle h, int64_t a0, int64_t a1, bool z_zero, int prec) {
     const int threads = 256;
-    const unsigned blocks = (unsigned)((a1 - a0 + threads - 1) / threads);
+    const int64_t lanes = (a1 - a0) * (SK == ddgdev::SK_CSRW ? ddgdev::CSRW_G : 1);
+    const unsigned blocks = (unsigned)((lanes + threads - 1) / threads);
     if (prec == DDG_PREC_FP64)
         local_residual_kernel<SK, double, double><<<blocks, threads, 0, h->stream>>>(
             a0, a1, h->ov_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->res64, z_zero,
