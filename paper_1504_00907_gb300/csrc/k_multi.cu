@@ -42,6 +42,54 @@ __device__ __forceinline__ V apply_row(int g, int c, int m, const int64_t* __res
     return s;
 }
 
+// A z at dof g for the 4 columns c4..c4+3 (m % 4 == 0: one 16-byte word of
+// each z row); the row's CSR entries are shared by the 4 columns
+template <int SK>
+__device__ __forceinline__ float4 apply_row4(int g, int c4, int m, const int64_t* __restrict__ rowptr,
+                                             const int32_t* __restrict__ col, const float* __restrict__ val,
+                                             const float* __restrict__ z, int nx, int ny, int nz) {
+    auto ld = [&](int gg) { return *reinterpret_cast<const float4*>(z + (int64_t)gg * m + c4); };
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto fma4 = [&](float a, const float4& b) {
+        s.x = fma(a, b.x, s.x);
+        s.y = fma(a, b.y, s.y);
+        s.z = fma(a, b.z, s.z);
+        s.w = fma(a, b.w, s.w);
+    };
+    if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+        const int i = g % nx, j = (g / nx) % ny;
+        fma4(SK == DDG_STENCIL_7PT_3D ? 6.f : 4.f, ld(g));
+        if (i > 0) fma4(-1.f, ld(g - 1));
+        if (i < nx - 1) fma4(-1.f, ld(g + 1));
+        if (j > 0) fma4(-1.f, ld(g - nx));
+        if (j < ny - 1) fma4(-1.f, ld(g + nx));
+        if (SK == DDG_STENCIL_7PT_3D) {
+            const int k = g / (nx * ny);
+            if (k > 0) fma4(-1.f, ld(g - nx * ny));
+            if (k < nz - 1) fma4(-1.f, ld(g + nx * ny));
+        }
+        return s;
+    }
+    if (SK == ddgdev::SK_CSR8 || SK == ddgdev::SK_CSR16) {
+        constexpr int NMAX = SK == ddgdev::SK_CSR8 ? 8 : 16;
+        const int64_t e0 = rowptr[g];
+        const int cnt = (int)(rowptr[g + 1] - e0);
+        int cl[NMAX];
+        float vl[NMAX];
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i) {
+            cl[i] = i < cnt ? col[e0 + i] : 0;
+            vl[i] = i < cnt ? val[e0 + i] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < NMAX; ++i)
+            if (i < cnt) fma4(vl[i], ld(cl[i]));
+        return s;
+    }
+    for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) fma4(val[e], ld(col[e]));
+    return s;
+}
+
 // per-column deterministic reduction: thread t owns column t % m; block
 // partials summed in block order by the last block.  Returns true in the
 // last block, with tot[c] valid for threads t < m (column t).
@@ -378,13 +426,104 @@ __global__ void __launch_bounds__(MT) coarse_restrict_multi_kernel(
 // Coarse GEMMs of the batched path: (32-row tile, CG_KS-column split) items
 constexpr int CG_ROWS = 32, CG_KS = 128;
 
-// ---------------------------------------------------------------- persistent coarse solve
-// The whole block-bidiagonal coarse solve for m columns in one cooperative
-// launch: every GEMM of the recurrence is split into (32-row tile, 128-column
-// split) items spread over the co-resident CTAs, a grid barrier separates the
-// partial products from their reduction (done by all threads), and another
-// separates the reduction from the next GEMM.  Barrier waits are bounded: a
-// wait that runs out sets the error flag and the kernel returns.
+// c = R0 (r - A z) for m % 4 == 0 and kmax <= KM <= 16: a CTA of RT4 threads
+// per subdomain, m/4 threads per row each owning 4 columns; the row slots'
+// float4 accumulators are added into shared memory one slot after another
+// (fixed order)
+constexpr int RT4 = 128;
+template <int SK, int KM>
+__global__ void __launch_bounds__(RT4) coarse_restrict_multi4_kernel(
+    const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
+    const float* __restrict__ r, const float* __restrict__ z, const float* __restrict__ Q, int kmax,
+    const int32_t* __restrict__ coff, float* __restrict__ cvec, int m, int nx, int ny, int nz) {
+    extern __shared__ __align__(16) float shr[];   // [kmax][m]
+    const int s = blockIdx.x;
+    const int q4 = m >> 2, rp = RT4 / q4;
+    const int cq = threadIdx.x % q4, gq = threadIdx.x / q4;
+    const bool lane_on = gq < rp;
+    float4 acc[KM];
+#pragma unroll
+    for (int jj = 0; jj < KM; ++jj) acc[jj] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t b0 = sub_off[s], b1 = sub_off[s + 1];
+    if (lane_on) {
+        for (int64_t a = b0 + gq; a < b1; a += rp) {
+            const int g = sub_nodes[a];
+            const float4 rv = *reinterpret_cast<const float4*>(r + (int64_t)g * m + 4 * cq);
+            const float4 az = apply_row4<SK>(g, 4 * cq, m, rowptr, col, val, z, nx, ny, nz);
+            const float4 w = make_float4(rv.x - az.x, rv.y - az.y, rv.z - az.z, rv.w - az.w);
+            const float* qa = Q + a * kmax;
+#pragma unroll
+            for (int jj = 0; jj < KM; ++jj)
+                if (jj < kmax) {
+                    const float qv = qa[jj];
+                    acc[jj].x = fma(qv, w.x, acc[jj].x);
+                    acc[jj].y = fma(qv, w.y, acc[jj].y);
+                    acc[jj].z = fma(qv, w.z, acc[jj].z);
+                    acc[jj].w = fma(qv, w.w, acc[jj].w);
+                }
+        }
+    }
+    for (int e = threadIdx.x; e < kmax * m; e += RT4) shr[e] = 0.f;
+    for (int slot = 0; slot < rp; ++slot) {
+        __syncthreads();
+        if (gq == slot) {
+#pragma unroll
+            for (int jj = 0; jj < KM; ++jj)
+                if (jj < kmax) {
+                    float4* d = reinterpret_cast<float4*>(shr + jj * m + 4 * cq);
+                    float4 v = *d;
+                    v.x += acc[jj].x;
+                    v.y += acc[jj].y;
+                    v.z += acc[jj].z;
+                    v.w += acc[jj].w;
+                    *d = v;
+                }
+        }
+    }
+    __syncthreads();
+    const int ks = coff[s + 1] - coff[s];
+    for (int e = threadIdx.x; e < ks * m; e += RT4) cvec[(int64_t)coff[s] * m + e] = shr[e];
+}
+
+// z[g, c4..c4+3] += sum_j Q[pos g, j] y[coff_{part g} + j, c4..c4+3]  (m % 4 == 0)
+__global__ void coarse_prolong_multi4_kernel(int64_t n, int m, const int32_t* __restrict__ part,
+                                             const int32_t* __restrict__ pos, const float* __restrict__ Q,
+                                             int kmax, const int32_t* __restrict__ coff,
+                                             const float* __restrict__ y, float* __restrict__ z) {
+    const int q4 = m >> 2;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * q4) return;
+    const int64_t g = e / q4;
+    const int c4 = 4 * (int)(e - g * q4);
+    const int sb = part[g];
+    const int c0 = coff[sb], ks = coff[sb + 1] - c0;
+    const float* qa = Q + (int64_t)pos[g] * kmax;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int jj = 0; jj < ks; ++jj) {
+        const float qv = qa[jj];
+        const float4 yv = *reinterpret_cast<const float4*>(y + (int64_t)(c0 + jj) * m + c4);
+        acc.x = fma(qv, yv.x, acc.x);
+        acc.y = fma(qv, yv.y, acc.y);
+        acc.z = fma(qv, yv.z, acc.z);
+        acc.w = fma(qv, yv.w, acc.w);
+    }
+    float4* zp = reinterpret_cast<float4*>(z + g * m + c4);
+    float4 zv = *zp;
+    zv.x += acc.x;
+    zv.y += acc.y;
+    zv.z += acc.z;
+    zv.w += acc.w;
+    *zp = zv;
+}
+
+// ---------------------------------------------------------------- batched coarse solve
+// Each GEMM of the block-bidiagonal recurrence, out[r0 + i] = a + sign * M x
+// for m columns, is one launch of (32-row tile, 128-column split) CTAs; the
+// CTA that finishes a row tile last sums its splits' partial products in a
+// fixed order.  Steps are chained by programmatic dependent launch: a CTA
+// stages its block of M (which no earlier step writes) in shared memory, and
+// only then waits for the previous step before it reads x and a.
 struct CoarseStep {            // one GEMM of the recurrence
     const int64_t* rowptr;
     const int32_t* lo;
@@ -397,104 +536,183 @@ struct CoarseStep {            // one GEMM of the recurrence
     float* out;
 };
 
-// partial products of one (row tile, split) item of a step
-__device__ void coarse_item(const CoarseStep& S, int B, int rt, int sp, int m, float* __restrict__ part,
-                            float (*sM)[33], float (*sX)[DDG_MCHUNK], int* rlo, int* rhi, int64_t* rptr) {
+constexpr int CG_LOADS = 16;   // split partials loaded together by the reducing CTA
+constexpr int CG_T = 128;      // threads of a step CTA: a 4-row x 4-column block each
+constexpr int CG_B = 8;        // loads in flight per thread while staging
+constexpr int CG_MT = CG_ROWS + 4;   // row stride of the transposed M block (16-byte rows)
+
+// x rows of the split are staged with a row stride mp = m rounded up to 4
+// (zero columns past m) so that every thread reads its 4 columns as one
+// 16-byte word; M is staged transposed so that its 4 rows are one word too.
+__global__ void __launch_bounds__(CG_T) coarse_step_multi_kernel(CoarseStep S, int B, int m, int nsplit,
+                                                                 float* __restrict__ part,
+                                                                 unsigned* __restrict__ tickets) {
+    extern __shared__ __align__(16) float smx[];      // [CG_KS][mp]
+    __shared__ __align__(16) float sMt[CG_KS][CG_MT];
+    __shared__ int rlo[CG_ROWS], rhi[CG_ROWS];
+    __shared__ int64_t rptr[CG_ROWS];
+    __shared__ int span[2];
+    __shared__ int am_last;
+    const int rt = blockIdx.x / nsplit, sp = blockIdx.x % nsplit;
     const int row0 = S.r0 + rt * CG_ROWS;
-    const int t = threadIdx.x, r = t >> 3, cg = t & 7;
-    __syncthreads();
+    const int t = threadIdx.x;
+    const int ty = t >> 4, tx = t & 15;   // rows 4ty..4ty+3, columns 4tx..4tx+3
+    const int mp = (m + 3) & ~3;
     if (t < CG_ROWS) {
         rlo[t] = S.lo[row0 + t];
         rhi[t] = S.hi[row0 + t];
         rptr[t] = S.rowptr[row0 + t];
     }
     __syncthreads();
-    const int c_lo = S.cbase + sp * CG_KS, c_hi = c_lo + CG_KS;
-    int ulo = c_hi, uhi = c_lo;
-    for (int q = 0; q < CG_ROWS; ++q)
-        if (rhi[q] > rlo[q]) {
-            ulo = min(ulo, max(rlo[q], c_lo));
-            uhi = max(uhi, min(rhi[q], c_hi));
-        }
-    float acc[DDG_MCHUNK / 8];
-#pragma unroll
-    for (int u = 0; u < DDG_MCHUNK / 8; ++u) acc[u] = 0.f;
-    for (int jc = c_lo + ((ulo - c_lo) & ~31); jc < uhi; jc += 32) {
-        for (int e = t; e < CG_ROWS * 32; e += MT) {
-            const int rr = e >> 5, jj = e & 31, j = jc + jj;
-            sM[rr][jj] = (j >= rlo[rr] && j < rhi[rr]) ? S.vals[rptr[rr] + (j - rlo[rr])] : 0.f;
-        }
-        for (int e = t; e < 32 * m; e += MT) {
-            const int jj = e / m, c = e % m;
-            sX[jj][c] = S.x[(int64_t)(jc + jj) * m + c];
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int jj = 0; jj < 32; ++jj) {
-            const float mv = sM[r][jj];
-#pragma unroll
-            for (int u = 0; u < DDG_MCHUNK / 8; ++u)
-                if (cg + 8 * u < m) acc[u] = fma(mv, sX[jj][cg + 8 * u], acc[u]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < DDG_MCHUNK / 8; ++u)
-        if (cg + 8 * u < m) part[((size_t)sp * B + rt * CG_ROWS + r) * m + cg + 8 * u] = acc[u];
-}
-
-__global__ void __launch_bounds__(MT) coarse_solve_persistent_kernel(
-    ProfileMat Dm, ProfileMat Em, ProfileMat Dt, ProfileMat Et, int B, int nK, int m,
-    const float* __restrict__ c, float* y, float* t, float* x, float* part, ddgdev::GridBar* gb, int* err) {
-    __shared__ float sM[CG_ROWS][33];
-    __shared__ float sX[32][DDG_MCHUNK];
-    __shared__ int rlo[CG_ROWS], rhi[CG_ROWS];
-    __shared__ int64_t rptr[CG_ROWS];
-    const int nsplit = (B + CG_KS - 1) / CG_KS;
-    const int ntiles = B / CG_ROWS;
-    const int nitems = ntiles * nsplit;
-    const unsigned G = gridDim.x;
-    auto run = [&](const CoarseStep& S) -> bool {
-        for (int it = blockIdx.x; it < nitems; it += G)
-            coarse_item(S, B, it / nsplit, it % nsplit, m, part, sM, sX, rlo, rhi, rptr);
-        if (!ddgdev::grid_barrier(gb, G, err)) return false;
-        // out[rows of the step] = a + sign * sum of the split partials
-        const int64_t tot = (int64_t)B * m;
-        for (int64_t e = (int64_t)blockIdx.x * MT + threadIdx.x; e < tot; e += (int64_t)G * MT) {
-            const float* pp = part + e;
-            const size_t st = (size_t)B * m;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int q = 0;
-            for (; q + 3 < nsplit; q += 4) {
-                s0 += __ldcg(pp + (size_t)q * st);
-                s1 += __ldcg(pp + (size_t)(q + 1) * st);
-                s2 += __ldcg(pp + (size_t)(q + 2) * st);
-                s3 += __ldcg(pp + (size_t)(q + 3) * st);
+    if (t == 0) {
+        int ulo = INT32_MAX, uhi = INT32_MIN;
+        for (int q = 0; q < CG_ROWS; ++q)
+            if (rhi[q] > rlo[q]) {
+                ulo = min(ulo, rlo[q]);
+                uhi = max(uhi, rhi[q]);
             }
-            for (; q < nsplit; ++q) s0 += __ldcg(pp + (size_t)q * st);
-            const int64_t o = (int64_t)S.r0 * m + e;
-            S.out[o] = (S.a ? S.a[o] : 0.f) + S.sign * ((s0 + s1) + (s2 + s3));
-        }
-        return ddgdev::grid_barrier(gb, G, err);
-    };
-    // forward: y_K = D_K (c_K - E_K y_{K-1})
-    for (int K = 0; K < nK; ++K) {
-        const float* in = c;
-        if (K > 0) {
-            if (!run(CoarseStep{Em.rowptr, Em.lo, Em.hi, Em.v32, K * B, (K - 1) * B, y, c, -1.f, t})) return;
-            in = t;
-        }
-        if (!run(CoarseStep{Dm.rowptr, Dm.lo, Dm.hi, Dm.v32, K * B, K * B, in, nullptr, 1.f, y})) return;
+        span[0] = ulo;
+        span[1] = uhi;
     }
-    // backward: x_K = D_K^T (y_K - E_{K+1}^T x_{K+1})
-    for (int K = nK - 1; K >= 0; --K) {
-        const float* in = y;
-        if (K < nK - 1) {
-            if (!run(CoarseStep{Et.rowptr, Et.lo, Et.hi, Et.v32, K * B, (K + 1) * B, x, y, -1.f, t})) return;
-            in = t;
+    __syncthreads();
+    // the columns of this split that some row of the tile reaches
+    const int c_lo = S.cbase + sp * CG_KS;
+    const int ulo = max(span[0], c_lo), uhi = min(span[1], c_lo + CG_KS);
+    const bool work = uhi > ulo;
+    const int jb = ulo - c_lo, je = uhi - c_lo;   // local column range [jb, je)
+    // staging loops issue CG_B loads before their first shared-memory store,
+    // so a thread waits about one memory latency per CG_B elements
+    if (work) {
+        for (int e0 = t; e0 < CG_ROWS * CG_KS; e0 += CG_B * CG_T) {
+            float v[CG_B];
+#pragma unroll
+            for (int i = 0; i < CG_B; ++i) {
+                const int e = e0 + i * CG_T, rr = e / CG_KS, jj = e % CG_KS, j = c_lo + jj;
+                v[i] = (e < CG_ROWS * CG_KS && jj >= jb && jj < je && j >= rlo[rr] && j < rhi[rr])
+                           ? S.vals[rptr[rr] + (j - rlo[rr])] : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < CG_B; ++i) {
+                const int e = e0 + i * CG_T, rr = e / CG_KS, jj = e % CG_KS;
+                if (e < CG_ROWS * CG_KS && jj >= jb && jj < je) sMt[jj][rr] = v[i];
+            }
         }
-        if (!run(CoarseStep{Dt.rowptr, Dt.lo, Dt.hi, Dt.v32, K * B, K * B, in, nullptr, 1.f, x})) return;
     }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (work) {
+        if (mp == m) {
+            // whole rows: (je - jb) * m contiguous floats, 16-byte words
+            const float4* src = reinterpret_cast<const float4*>(S.x + (int64_t)(c_lo + jb) * m);
+            float4* dst = reinterpret_cast<float4*>(smx + jb * m);
+            const int n4 = (je - jb) * (m >> 2);
+            for (int e0 = t; e0 < n4; e0 += CG_B * CG_T) {
+                float4 v[CG_B];
+#pragma unroll
+                for (int i = 0; i < CG_B; ++i)
+                    if (e0 + i * CG_T < n4) v[i] = src[e0 + i * CG_T];
+#pragma unroll
+                for (int i = 0; i < CG_B; ++i)
+                    if (e0 + i * CG_T < n4) dst[e0 + i * CG_T] = v[i];
+            }
+        } else {
+            const int ne = (je - jb) * mp;
+            for (int e0 = t; e0 < ne; e0 += CG_B * CG_T) {
+                float v[CG_B];
+#pragma unroll
+                for (int i = 0; i < CG_B; ++i) {
+                    const int e = e0 + i * CG_T, jj = jb + e / mp, c = e % mp;
+                    v[i] = (e < ne && c < m) ? S.x[(int64_t)(c_lo + jj) * m + c] : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < CG_B; ++i) {
+                    const int e = e0 + i * CG_T;
+                    if (e < ne) smx[jb * mp + e] = v[i];
+                }
+            }
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+        if (4 * tx < mp) {
+#pragma unroll 4
+            for (int jj = jb; jj < je; ++jj) {
+                const float4 mv = *reinterpret_cast<const float4*>(&sMt[jj][4 * ty]);
+                const float4 xv = *reinterpret_cast<const float4*>(&smx[jj * mp + 4 * tx]);
+                const float mr[4] = {mv.x, mv.y, mv.z, mv.w};
+                const float xc[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc[i][k] = fma(mr[i], xc[k], acc[i][k]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = 4 * tx + k;
+                if (c < m) part[((size_t)sp * B + rt * CG_ROWS + 4 * ty + i) * m + c] = acc[i][k];
+            }
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) am_last = atomicAdd(&tickets[rt], 1u) == (unsigned)nsplit - 1u;
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    // splits that reach no column of the tile wrote nothing and add nothing;
+    // the others are loaded together and summed in split order
+    const int sp0 = span[1] > span[0] ? max((span[0] - S.cbase) / CG_KS, 0) : 0;
+    const int sp1 = span[1] > span[0] ? min((span[1] - 1 - S.cbase) / CG_KS, nsplit - 1) : -1;
+    if (mp == m) {
+        // 16-byte words: 4 outputs per load
+        const int n4 = CG_ROWS * (m >> 2);
+        const float4* p4 = reinterpret_cast<const float4*>(part + (size_t)rt * CG_ROWS * m);
+        const size_t st4 = (size_t)B * m / 4;
+        for (int e = t; e < n4; e += CG_T) {
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q0 = sp0; q0 <= sp1; q0 += CG_LOADS) {
+                float4 v[CG_LOADS];
+#pragma unroll
+                for (int i = 0; i < CG_LOADS; ++i)
+                    if (q0 + i <= sp1) v[i] = __ldcg(p4 + (size_t)(q0 + i) * st4 + e);
+#pragma unroll
+                for (int i = 0; i < CG_LOADS; ++i)
+                    if (q0 + i <= sp1) {
+                        s.x += v[i].x;
+                        s.y += v[i].y;
+                        s.z += v[i].z;
+                        s.w += v[i].w;
+                    }
+            }
+            const int64_t o = (int64_t)row0 * m + 4 * e;
+            float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (S.a) a4 = *reinterpret_cast<const float4*>(S.a + o);
+            *reinterpret_cast<float4*>(S.out + o) =
+                make_float4(a4.x + S.sign * s.x, a4.y + S.sign * s.y, a4.z + S.sign * s.z, a4.w + S.sign * s.w);
+        }
+        if (t == 0) tickets[rt] = 0u;
+        return;
+    }
+    for (int e = t; e < CG_ROWS * m; e += CG_T) {
+        float s = 0.f;
+        for (int q0 = sp0; q0 <= sp1; q0 += CG_LOADS) {
+            float v[CG_LOADS];
+#pragma unroll
+            for (int i = 0; i < CG_LOADS; ++i)
+                v[i] = q0 + i <= sp1 ? __ldcg(part + ((size_t)(q0 + i) * B + rt * CG_ROWS) * m + e) : 0.f;
+#pragma unroll
+            for (int i = 0; i < CG_LOADS; ++i)
+                if (q0 + i <= sp1) s += v[i];
+        }
+        const int64_t o = (int64_t)row0 * m + e;
+        S.out[o] = (S.a ? S.a[o] : 0.f) + S.sign * s;
+    }
+    if (t == 0) tickets[rt] = 0u;
 }
 
 __global__ void coarse_prolong_multi_kernel(int64_t n, int m, const int32_t* __restrict__ part,
@@ -553,8 +771,9 @@ void multi_ensure(ddg_handle h, int m) {
     if (h->use_coarse) {
         const int nsplit = (h->B + CG_KS - 1) / CG_KS;
         w.gpart = h->arena.alloc<float>((size_t)nsplit * h->B * m);
-        w.gtick = h->arena.alloc<unsigned>(std::max(2, h->B / CG_ROWS));
-        DDG_CUDA(cudaMemsetAsync(w.gtick, 0, std::max(2, h->B / CG_ROWS) * sizeof(unsigned), h->stream));
+        // one ticket per 32-row tile of a step; reset by the CTA that uses it last
+        w.gtick = h->arena.alloc<unsigned>(h->B / CG_ROWS);
+        DDG_CUDA(cudaMemsetAsync(w.gtick, 0, (h->B / CG_ROWS) * sizeof(unsigned), h->stream));
     }
     w.scal = h->arena.alloc<double>(S_COUNT * DDG_MCHUNK);
     w.partials = h->arena.alloc<double>((size_t)DDG_RED_BLOCKS * 2 * DDG_MCHUNK);
@@ -641,33 +860,65 @@ static void multi_apply_t(ddg_handle h, int m) {
     coarse_restrict_multi_kernel<SK, KM><<<h->nsub, bd, smem, h->stream>>>(                             \
         h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff, \
         w.c32, m, h->nx, h->ny, h->nz)
-        if (h->kmax <= 8) RESTRICT_MULTI(8);
+#define RESTRICT_MULTI4(KM)                                                                              \
+    coarse_restrict_multi4_kernel<SK, KM><<<h->nsub, RT4, (size_t)h->kmax * m * sizeof(float), h->stream>>>( \
+        h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff,  \
+        w.c32, m, h->nx, h->ny, h->nz)
+        const bool vec4 = m % 4 == 0;
+        if (vec4 && h->kmax <= 8) RESTRICT_MULTI4(8);
+        else if (vec4 && h->kmax <= 16) RESTRICT_MULTI4(16);
+        else if (h->kmax <= 8) RESTRICT_MULTI(8);
         else if (h->kmax <= 16) RESTRICT_MULTI(16);
         else RESTRICT_MULTI(32);
 #undef RESTRICT_MULTI
+#undef RESTRICT_MULTI4
         const int B = h->B, nK = h->nK;
-        {
-            // one cooperative launch for the whole recurrence
-            static int max_blocks = 0;
-            if (!max_blocks) {
-                int per_sm = 0, dev = 0, sms = 0;
-                DDG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_solve_persistent_kernel, MT, 0));
-                DDG_CUDA(cudaGetDevice(&dev));
-                DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-                max_blocks = std::max(1, std::min(per_sm, 4)) * sms;
+        const int nsplit = (B + CG_KS - 1) / CG_KS;
+        auto step = [&](const ProfileMat& M, int r0, int cbase, const float* x, const float* a, float sign,
+                        float* out) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)((B / CG_ROWS) * nsplit));
+            cfg.blockDim = dim3(CG_T);
+            cfg.dynamicSmemBytes = (size_t)CG_KS * ((m + 3) & ~3) * sizeof(float);
+            cfg.stream = h->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = h->use_pdl ? 1 : 0;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            static bool configured = false;
+            if (!configured) {
+                DDG_CUDA(cudaFuncSetAttribute(coarse_step_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(CG_KS * DDG_MCHUNK * sizeof(float))));
+                configured = true;
             }
-            ProfileMat Dm = h->Dm, Em = h->Em, Dt = h->Dt, Et = h->Et;
-            int Bv = B, nKv = nK, mv = m;
-            const float* cv = w.c32;
-            float *yv = w.y32, *tv = w.t32, *xv = w.x32, *pv = w.gpart;
-            ddgdev::GridBar* gbv = reinterpret_cast<ddgdev::GridBar*>(w.gtick);
-            int* ev = h->errflags + E_TIMEOUT;
-            void* args[] = {&Dm, &Em, &Dt, &Et, &Bv, &nKv, &mv, &cv, &yv, &tv, &xv, &pv, &gbv, &ev};
-            DDG_CUDA(cudaLaunchCooperativeKernel((const void*)coarse_solve_persistent_kernel, dim3(max_blocks),
-                                                 dim3(MT), args, 0, h->stream));
+            const CoarseStep S{M.rowptr, M.lo, M.hi, M.v32, r0, cbase, x, a, sign, out};
+            DDG_CUDA(cudaLaunchKernelEx(&cfg, coarse_step_multi_kernel, S, B, m, nsplit, w.gpart, w.gtick));
+        };
+        // forward: y_K = D_K (c_K - E_K y_{K-1})
+        for (int K = 0; K < nK; ++K) {
+            const float* in = w.c32;
+            if (K > 0) {
+                step(h->Em, K * B, (K - 1) * B, w.y32, w.c32, -1.f, w.t32);
+                in = w.t32;
+            }
+            step(h->Dm, K * B, K * B, in, nullptr, 1.f, w.y32);
         }
-        coarse_prolong_multi_kernel<<<(unsigned)((n + bd / m - 1) / (bd / m)), bd, 0, h->stream>>>(
-            n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);
+        // backward: x_K = D_K^T (y_K - E_{K+1}^T x_{K+1})
+        for (int K = nK - 1; K >= 0; --K) {
+            const float* in = w.y32;
+            if (K < nK - 1) {
+                step(h->Et, K * B, (K + 1) * B, w.x32, w.y32, -1.f, w.t32);
+                in = w.t32;
+            }
+            step(h->Dt, K * B, K * B, in, nullptr, 1.f, w.x32);
+        }
+        if (vec4)
+            coarse_prolong_multi4_kernel<<<(unsigned)((n * (m / 4) + 255) / 256), 256, 0, h->stream>>>(
+                n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);
+        else
+            coarse_prolong_multi_kernel<<<(unsigned)((n + bd / m - 1) / (bd / m)), bd, 0, h->stream>>>(
+                n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);
         DDG_CHECK_LAUNCH();
     }
     for (int c = h->ncol - 1; c >= 0; --c) local(c, false);

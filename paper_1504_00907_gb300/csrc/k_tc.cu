@@ -261,24 +261,29 @@ __global__ void __launch_bounds__(256) tc_residual_kernel(
     const int64_t o = ov_off[q];
     const int n = (int)(ov_off[q + 1] - o);
     constexpr bool csr = SK == ddgdev::SK_CSR8 || SK == ddgdev::SK_CSR16;
+    __shared__ int64_t se0[TC_K];
     if (threadIdx.x < TC_K) {
         const int la = J * TC_K + threadIdx.x;
         const int g = la < n ? ov_nodes[o + la] : -1;
         sg[threadIdx.x] = g;
         if (csr) {
-            int cnt = 0;
-            if (g >= 0) {
-                const int64_t e0 = rowptr[g];
-                cnt = (int)(rowptr[g + 1] - e0);
-                for (int i = 0; i < cnt; ++i) {
-                    scol[threadIdx.x][i] = col[e0 + i];
-                    sval[threadIdx.x][i] = val[e0 + i];
-                }
-            }
-            scnt[threadIdx.x] = cnt;
+            const int64_t e0 = g >= 0 ? rowptr[g] : 0;
+            se0[threadIdx.x] = e0;
+            scnt[threadIdx.x] = g >= 0 ? (int)(rowptr[g + 1] - e0) : 0;
         }
     }
     __syncthreads();
+    if (csr) {
+        // every (row, entry) pair of the slab by its own thread: one round of loads
+        for (int e = threadIdx.x; e < TC_K * 16; e += blockDim.x) {
+            const int kr = e >> 4, i = e & 15;
+            if (i < scnt[kr]) {
+                scol[kr][i] = col[se0[kr] + i];
+                sval[kr][i] = val[se0[kr] + i];
+            }
+        }
+        __syncthreads();
+    }
 #pragma unroll 4
     for (int e = threadIdx.x; e < TC_K * N; e += blockDim.x) {
         const int kr = e / N, c = e % N;
