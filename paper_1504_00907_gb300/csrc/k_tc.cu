@@ -284,41 +284,90 @@ __global__ void __launch_bounds__(256) tc_residual_kernel(
         }
         __syncthreads();
     }
-#pragma unroll 4
-    for (int e = threadIdx.x; e < TC_K * N; e += blockDim.x) {
-        const int kr = e / N, c = e % N;
-        const int g = sg[kr];
-        float s = 0.f;
-        if (g >= 0 && c < m) {
-            s = r[(int64_t)g * m + c];
-            if (!z_zero) {
-                if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
-                    const int i = g % nx, j = (g / nx) % ny;
-                    float az = (SK == DDG_STENCIL_7PT_3D ? 6.f : 4.f) * z[(int64_t)g * m + c];
-                    if (i > 0) az -= z[(int64_t)(g - 1) * m + c];
-                    if (i < nx - 1) az -= z[(int64_t)(g + 1) * m + c];
-                    if (j > 0) az -= z[(int64_t)(g - nx) * m + c];
-                    if (j < ny - 1) az -= z[(int64_t)(g + nx) * m + c];
-                    if (SK == DDG_STENCIL_7PT_3D) {
-                        const int k = g / (nx * ny);
-                        if (k > 0) az -= z[(int64_t)(g - nx * ny) * m + c];
-                        if (k < nz - 1) az -= z[(int64_t)(g + nx * ny) * m + c];
-                    }
-                    s -= az;
-                } else if (csr) {
-                    constexpr int NMAX = SK == ddgdev::SK_CSR8 ? 8 : 16;
-                    const int cnt = scnt[kr];
-                    float acc = 0.f;
+    if ((m & 3) == 0) {
+        // 4 adjacent columns per thread (16-byte z words); the row's stencil
+        // or CSR entries and index arithmetic are shared by the 4 columns
+        const int nq = N >> 2, cq = threadIdx.x % nq;
+        const int c4 = 4 * cq;
+        auto ld = [&](const float* v, int gg) { return *reinterpret_cast<const float4*>(v + (int64_t)gg * m + c4); };
+        for (int kr = threadIdx.x / nq; kr < TC_K; kr += blockDim.x / nq) {
+            const int g = sg[kr];
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g >= 0 && c4 < m) {
+                s = ld(r, g);
+                if (!z_zero) {
+                    float4 az = make_float4(0.f, 0.f, 0.f, 0.f);
+                    auto fma4 = [&](float a, const float4& b) {
+                        az.x = fma(a, b.x, az.x);
+                        az.y = fma(a, b.y, az.y);
+                        az.z = fma(a, b.z, az.z);
+                        az.w = fma(a, b.w, az.w);
+                    };
+                    if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+                        const int i = g % nx, j = (g / nx) % ny;
+                        fma4(SK == DDG_STENCIL_7PT_3D ? 6.f : 4.f, ld(z, g));
+                        if (i > 0) fma4(-1.f, ld(z, g - 1));
+                        if (i < nx - 1) fma4(-1.f, ld(z, g + 1));
+                        if (j > 0) fma4(-1.f, ld(z, g - nx));
+                        if (j < ny - 1) fma4(-1.f, ld(z, g + nx));
+                        if (SK == DDG_STENCIL_7PT_3D) {
+                            const int k = g / (nx * ny);
+                            if (k > 0) fma4(-1.f, ld(z, g - nx * ny));
+                            if (k < nz - 1) fma4(-1.f, ld(z, g + nx * ny));
+                        }
+                    } else if (csr) {
+                        constexpr int NMAX = SK == ddgdev::SK_CSR8 ? 8 : 16;
+                        const int cnt = scnt[kr];
 #pragma unroll
-                    for (int i2 = 0; i2 < NMAX; ++i2)
-                        if (i2 < cnt) acc = fma(sval[kr][i2], z[(int64_t)scol[kr][i2] * m + c], acc);
-                    s -= acc;
-                } else {
-                    for (int64_t p = rowptr[g]; p < rowptr[g + 1]; ++p) s -= val[p] * z[(int64_t)col[p] * m + c];
+                        for (int i2 = 0; i2 < NMAX; ++i2)
+                            if (i2 < cnt) fma4(sval[kr][i2], ld(z, scol[kr][i2]));
+                    } else {
+                        for (int64_t p = rowptr[g]; p < rowptr[g + 1]; ++p) fma4(val[p], ld(z, col[p]));
+                    }
+                    s = make_float4(s.x - az.x, s.y - az.y, s.z - az.z, s.w - az.w);
                 }
             }
+            __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(&sx[kr][c4]);
+            d[0] = __floats2bfloat162_rn(s.x, s.y);
+            d[1] = __floats2bfloat162_rn(s.z, s.w);
         }
-        sx[kr][c] = __float2bfloat16_rn(s);
+    } else {
+    #pragma unroll 4
+        for (int e = threadIdx.x; e < TC_K * N; e += blockDim.x) {
+            const int kr = e / N, c = e % N;
+            const int g = sg[kr];
+            float s = 0.f;
+            if (g >= 0 && c < m) {
+                s = r[(int64_t)g * m + c];
+                if (!z_zero) {
+                    if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
+                        const int i = g % nx, j = (g / nx) % ny;
+                        float az = (SK == DDG_STENCIL_7PT_3D ? 6.f : 4.f) * z[(int64_t)g * m + c];
+                        if (i > 0) az -= z[(int64_t)(g - 1) * m + c];
+                        if (i < nx - 1) az -= z[(int64_t)(g + 1) * m + c];
+                        if (j > 0) az -= z[(int64_t)(g - nx) * m + c];
+                        if (j < ny - 1) az -= z[(int64_t)(g + nx) * m + c];
+                        if (SK == DDG_STENCIL_7PT_3D) {
+                            const int k = g / (nx * ny);
+                            if (k > 0) az -= z[(int64_t)(g - nx * ny) * m + c];
+                            if (k < nz - 1) az -= z[(int64_t)(g + nx * ny) * m + c];
+                        }
+                        s -= az;
+                    } else if (csr) {
+                        constexpr int NMAX = SK == ddgdev::SK_CSR8 ? 8 : 16;
+                        const int cnt = scnt[kr];
+                        float acc = 0.f;
+    #pragma unroll
+                        for (int i2 = 0; i2 < NMAX; ++i2)
+                            if (i2 < cnt) acc = fma(sval[kr][i2], z[(int64_t)scol[kr][i2] * m + c], acc);
+                        s -= acc;
+                    } else {
+                        for (int64_t p = rowptr[g]; p < rowptr[g + 1]; ++p) s -= val[p] * z[(int64_t)col[p] * m + c];
+                    }
+                }
+            }
+            sx[kr][c] = __float2bfloat16_rn(s);
+        }
     }
     __syncthreads();
     // core-matrix rows: (n, kc) holds k = kc*8 .. kc*8+7 of column n, 16 bytes
