@@ -16,6 +16,9 @@ constexpr int MT = 256;
 // threads of the column-mapped kernels: a multiple of m, at most 256
 inline int col_block(int m) { return (MT / m) * m; }
 
+// rows per round of the grid-stride reduction kernels (loads issued together)
+constexpr int UNR = 4;
+
 // A z at dof g, column c of an n x m block (matrix-free for the Laplacians)
 template <int SK, typename V, typename AV>
 __device__ __forceinline__ V apply_row(int g, int c, int m, const int64_t* __restrict__ rowptr,
@@ -188,14 +191,36 @@ __global__ void __launch_bounds__(MT) update_ur_multi_kernel(int64_t n, int m, d
     const int c = threadIdx.x % m, rl = threadIdx.x / m;
     const double alpha = S(sc, S_ALPHA, c);
     double acc[1] = {0.0};
-    if ((int)threadIdx.x < rpb * m)
-        for (int64_t g = (int64_t)blockIdx.x * rpb + rl; g < n; g += (int64_t)gridDim.x * rpb) {
-            const int64_t e = g * m + c;
-            U[e] = fma(alpha, P[e], U[e]);
-            const double r = fma(-alpha, Q[e], R[e]);
-            R[e] = r;
-            acc[0] = fma(r, r, acc[0]);
+    if ((int)threadIdx.x < rpb * m) {
+        // UNR rows per round: all loads of the round before its arithmetic,
+        // the norm still accumulated row after row
+        const int64_t stride = (int64_t)gridDim.x * rpb;
+        for (int64_t g0 = (int64_t)blockIdx.x * rpb + rl; g0 < n; g0 += UNR * stride) {
+            double pv[UNR], qv[UNR], rv[UNR], uv[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int64_t g = g0 + k * stride;
+                if (g < n) {
+                    const int64_t e = g * m + c;
+                    pv[k] = P[e];
+                    qv[k] = Q[e];
+                    rv[k] = R[e];
+                    uv[k] = U[e];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int64_t g = g0 + k * stride;
+                if (g < n) {
+                    const int64_t e = g * m + c;
+                    U[e] = fma(alpha, pv[k], uv[k]);
+                    const double r = fma(-alpha, qv[k], rv[k]);
+                    R[e] = r;
+                    acc[0] = fma(r, r, acc[0]);
+                }
+            }
         }
+    }
     double tot[1];
     if (reduce_cols<1>(acc, m, partials, counter, tot) && (int)threadIdx.x < m) {
         S(sc, S_RR, c) = tot[0];
@@ -215,13 +240,28 @@ __global__ void __launch_bounds__(MT) dots_multi_kernel(int64_t n, int m, const 
     const int rpb = blockDim.x / m;
     const int c = threadIdx.x % m, rl = threadIdx.x / m;
     double acc[2] = {0.0, 0.0};
-    if ((int)threadIdx.x < rpb * m)
-        for (int64_t g = (int64_t)blockIdx.x * rpb + rl; g < n; g += (int64_t)gridDim.x * rpb) {
-            const int64_t e = g * m + c;
-            const double z = (double)Z[e];
-            acc[0] = fma(R[e], z, acc[0]);
-            acc[1] = fma(Q[e], z, acc[1]);
+    if ((int)threadIdx.x < rpb * m) {
+        const int64_t stride = (int64_t)gridDim.x * rpb;
+        for (int64_t g0 = (int64_t)blockIdx.x * rpb + rl; g0 < n; g0 += UNR * stride) {
+            double rv[UNR], qv[UNR], zv[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                const int64_t g = g0 + k * stride;
+                if (g < n) {
+                    const int64_t e = g * m + c;
+                    zv[k] = (double)Z[e];
+                    rv[k] = R[e];
+                    qv[k] = Q[e];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k)
+                if (g0 + k * stride < n) {
+                    acc[0] = fma(rv[k], zv[k], acc[0]);
+                    acc[1] = fma(qv[k], zv[k], acc[1]);
+                }
         }
+    }
     double tot[2];
     if (reduce_cols<2>(acc, m, partials, counter, tot) && (int)threadIdx.x < m) {
         if (!active[c]) {
