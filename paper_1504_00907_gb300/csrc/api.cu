@@ -203,7 +203,7 @@ void local_step(ddg_handle h, int c, bool z_zero, int prec) {
 }
 
 void coarse_step(ddg_handle h, int prec, bool residual) {
-    ProfScope ps(h, DDG_K_COARSE, 2 + 4 * h->nK - 2, 0.0);
+    ProfScope ps(h, DDG_K_COARSE, 2 + 2 * h->nK, 0.0);
     ddg::coarse_restrict(h, prec, residual);
     ddg::coarse_solve(h, prec);
     ddg::coarse_prolong(h, prec);
@@ -944,20 +944,15 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             h->Q32 = h->arena.alloc<float>((size_t)n * k);
             ddg::cast_q32(h);
             const int n0p = h->n0p;
-            h->cgbar = reinterpret_cast<ddgdev::GridBar*>(h->arena.alloc<unsigned>(2));
-            DDG_CUDA(cudaMemsetAsync(h->cgbar, 0, 2 * sizeof(unsigned), h->stream));
-            if (const char* ev = std::getenv("DDG_PERSISTENT_COARSE")) h->persistent_coarse = ev[0] == '1';
             h->c64 = h->arena.alloc<double>(n0p);
             h->y64 = h->arena.alloc<double>(n0p);
-            h->t64 = h->arena.alloc<double>(n0p);
             h->x64 = h->arena.alloc<double>(n0p);
             h->c32 = h->arena.alloc<float>(n0p);
             h->y32 = h->arena.alloc<float>(n0p);
-            h->t32 = h->arena.alloc<float>(n0p);
             h->x32 = h->arena.alloc<float>(n0p);
-            for (void* p : {(void*)h->c64, (void*)h->y64, (void*)h->t64, (void*)h->x64})
+            for (void* p : {(void*)h->c64, (void*)h->y64, (void*)h->x64})
                 DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(double), h->stream));
-            for (void* p : {(void*)h->c32, (void*)h->y32, (void*)h->t32, (void*)h->x32})
+            for (void* p : {(void*)h->c32, (void*)h->y32, (void*)h->x32})
                 DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(float), h->stream));
         }
 

@@ -140,7 +140,7 @@ struct MultiWork {
     double *R = nullptr, *P = nullptr, *Q = nullptr, *T = nullptr;   // n x m FP64
     double *Fb = nullptr, *Ub = nullptr;                              // column-group staging
     float *r32 = nullptr, *z32 = nullptr, *res32 = nullptr;
-    float *c32 = nullptr, *y32 = nullptr, *t32 = nullptr, *x32 = nullptr;
+    float *c32 = nullptr, *y32 = nullptr, *x32 = nullptr;
     double* scal = nullptr;       // [S_COUNT][DDG_MCHUNK]
     double* partials = nullptr;   // [DDG_RED_BLOCKS][2][DDG_MCHUNK]
     int* active = nullptr;        // [DDG_MCHUNK]
@@ -242,15 +242,11 @@ struct ddg_handle_s {
     int band = 0, Wt = 1, NT = 0, nK = 0, B = 0, n0p = 0;
     double* bandL = nullptr;       // [NT][Wt+1][64*64] (setup only)
     double* coarseW = nullptr;     // super-block inverses (setup only)
-    ProfileMat Dm, Em, Dt, Et;
-    double *c64 = nullptr, *y64 = nullptr, *t64 = nullptr, *x64 = nullptr;
-    // one cooperative launch per single-RHS coarse solve instead of 4 nK graph-
-    // replayed GEMV launches; off by default: on GB300 its 62 grid barriers
-    // cost more than the launch boundaries (3.75 vs 3.03 ms per solve on the
-    // 128^3 Poisson problem); DDG_PERSISTENT_COARSE=1 selects it
-    bool persistent_coarse = false;
-    ddgdev::GridBar* cgbar = nullptr;  // its grid barrier
-    float *c32 = nullptr, *y32 = nullptr, *t32 = nullptr, *x32 = nullptr;
+    // block-bidiagonal factor: D_K = L_KK^{-1} (Dm) and its transpose (Dt);
+    // coupling blocks F_K = D_K L_{K,K-1} (Fm) and G_K = D_K^T L_{K+1,K}^T (Gm)
+    ProfileMat Dm, Dt, Fm, Gm;
+    double *c64 = nullptr, *y64 = nullptr, *x64 = nullptr;
+    float *c32 = nullptr, *y32 = nullptr, *x32 = nullptr;
 
     // ---- CG workspace (FP64) and preconditioner vectors
     const double* rin64 = nullptr;  // input of the FP64 preconditioner apply

@@ -110,48 +110,4 @@ __device__ __forceinline__ V csr_row_dot_group(int g, bool live, const int64_t* 
     return s;
 }
 
-struct GridBar {
-    unsigned count;
-    unsigned gen;
-};
-
-// Grid-wide barrier of a cooperative (co-resident) launch: one arrival
-// counter and a generation word.  The wait is bounded: when it runs out the
-// error flag is set and false is returned, so the caller can leave.
-constexpr unsigned GB_POLLS = 1u << 26;
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned nblocks, int* err) {
-    __shared__ int ok_sh;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = ld_acquire_gpu(&gb->gen);
-        unsigned old;
-        // release: this block's writes are visible before its arrival counts
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
-        if (old == nblocks - 1u) {
-            gb->count = 0u;
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(&gb->gen) : "memory");
-        } else {
-            unsigned polls = 0;
-            while (ld_acquire_gpu(&gb->gen) == g) {
-                if (++polls > GB_POLLS) {
-                    ok = 0;
-                    atomicExch(err, 1);
-                    break;
-                }
-            }
-        }
-        ok_sh = ok;
-    }
-    __syncthreads();
-    return ok_sh != 0;
-}
-
 }  // namespace ddgdev

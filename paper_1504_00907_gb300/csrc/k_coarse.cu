@@ -350,13 +350,61 @@ __global__ void __launch_bounds__(256) superblock_inverse_kernel(const double* b
     }
 }
 
+// Coupling blocks of the block-bidiagonal recurrence, 64x64 FP64 tiles:
+//   F_K = D_K E_K      (K >= 1;  E_K = L_{K,K-1})
+//   G_K = D_K^T E_{K+1}^T = (E_{K+1} D_K)^T   (K <= nK - 2)
+// so that y_K = D_K c_K - F_K y_{K-1} and x_K = D_K^T y_K - G_K x_{K+1}.
+// In tile terms E_K(m, J) is band tile (K Wt + m, Wt + m - J), nonzero for
+// J >= m, and D_K(I, m) = W(K, I, m) for m <= I.  grid (Wt * Wt, nK, 2).
+__global__ void __launch_bounds__(256) coupling_product_kernel(const double* band, const double* W, int Wt,
+                                                               int nK, double* Ft, double* Gt) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Bm = sm + CT * CLD;
+    const int K = blockIdx.y, I = blockIdx.x / Wt, J = blockIdx.x % Wt;
+    const bool is_f = blockIdx.z == 0;
+    if (is_f ? K == 0 : K >= nK - 1) return;
+    const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
+    auto wtile = [&](int ii, int j2) { return W + ((size_t)K * Ptiles + (size_t)ii * (ii + 1) / 2 + j2) * CT * CT; };
+    auto btile = [&](int R, int d) { return band + ((size_t)R * (Wt + 1) + d) * CT * CT; };
+    double acc[4][4];
+    acc_zero4(acc);
+    if (is_f) {
+        for (int m = 0; m <= min(I, J); ++m) {
+            ct_load(A, wtile(I, m));
+            ct_load(Bm, btile(K * Wt + m, Wt + m - J));
+            __syncthreads();
+            ct_mac<false>(acc, A, Bm);
+            __syncthreads();
+        }
+    } else {
+        // acc = H(J, I) = sum_m E_{K+1}(J, m) W(K, m, I)
+        for (int m = max(I, J); m < Wt; ++m) {
+            ct_load(A, btile((K + 1) * Wt + J, Wt + J - m));
+            ct_load(Bm, wtile(m, I));
+            __syncthreads();
+            ct_mac<false>(acc, A, Bm);
+            __syncthreads();
+        }
+    }
+    const int r0 = (threadIdx.x >> 4) * 4, c0 = (threadIdx.x & 15) * 4;
+    double* out = (is_f ? Ft : Gt) + (((size_t)K * Wt + I) * Wt + J) * CT * CT;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            if (is_f) out[(r0 + a) * CT + c0 + b] = acc[a][b];
+            else out[(c0 + b) * CT + r0 + a] = acc[a][b];   // G tile = H tile transposed
+        }
+}
+
 // profile-row fills (one warp per row)
-enum { PM_D = 0, PM_E = 1, PM_DT = 2, PM_ET = 3 };
+enum { PM_D = 0, PM_DT = 1, PM_F = 2, PM_G = 3 };
 
 template <int KIND>
 __global__ void profile_fill_kernel(ProfileMat M, const int32_t* __restrict__ vlo,
-                                    const int32_t* __restrict__ vhi, int rows, const double* band,
-                                    const double* W, int Wt, int B) {
+                                    const int32_t* __restrict__ vhi, int rows, const double* W,
+                                    const double* Tc, int Wt, int B) {
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (wid >= rows) return;
     const int i = wid;
@@ -374,9 +422,10 @@ __global__ void profile_fill_kernel(ProfileMat M, const int32_t* __restrict__ vl
                 const int ti = la / CT, tj = lb / CT;
                 v = W[((size_t)K * Ptiles + (size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (la % CT) * CT + (lb % CT)];
             } else {
-                // E[a][b] = L[a][b] with a in super-block K, b in K-1
-                const int a = KIND == PM_E ? i : jc, b = KIND == PM_E ? jc : i;
-                v = band[band_index(a, b, Wt)];
+                // F_K (columns in super-block K-1) or G_K (columns in K+1) tiles
+                const int K = i / B, li = i - K * B;
+                const int lj = jc - (KIND == PM_F ? K - 1 : K + 1) * B;
+                v = Tc[(((size_t)K * Wt + li / CT) * Wt + lj / CT) * CT * CT + (li % CT) * CT + (lj % CT)];
             }
         }
         M.v64[rp + (jc - lo)] = v;
@@ -456,59 +505,6 @@ __global__ void __launch_bounds__(GEMV_TPR) profile_gemv_kernel(
 #pragma unroll
         for (int w = 0; w < GEMV_TPR / 32; ++w) t += sh[w];
         out[i] = (a ? a[i] : (V)0) + sign * t;
-    }
-}
-
-// The whole single-RHS coarse recurrence in one cooperative launch: in every
-// step each warp takes rows of the step's profile matrix (16-byte loads of
-// the aligned rows) and writes out[i] = a[i] + sign * (M x)[i]; a bounded grid
-// barrier separates the steps.
-template <typename V>
-__global__ void __launch_bounds__(512) coarse_gemv_persistent_kernel(
-    ProfileMat Dm, ProfileMat Em, ProfileMat Dt, ProfileMat Et, int B, int nK, const V* __restrict__ c,
-    V* y, V* t, V* x, ddgdev::GridBar* gb, int* err) {
-    const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    auto vals = [](const ProfileMat& M) -> const V* {
-        return sizeof(V) == 8 ? reinterpret_cast<const V*>(M.v64) : reinterpret_cast<const V*>(M.v32);
-    };
-    auto step = [&](const ProfileMat& M, int r0, const V* xin, const V* a, V sign, V* out) -> bool {
-        const V* mv = vals(M);
-        for (int i = r0 + wid; i < r0 + B; i += nw) {
-            const int l = M.lo[i];
-            const int nch = (M.hi[i] - l) >> 2;
-            const V* rv = mv + M.rowptr[i];
-            const V* xv = xin + l;
-            V s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-            int ch = lane;
-            for (; ch + 96 < nch; ch += 128) {
-                s0 += Vec4<V>::dot(rv + 4 * ch, xv + 4 * ch);
-                s1 += Vec4<V>::dot(rv + 4 * (ch + 32), xv + 4 * (ch + 32));
-                s2 += Vec4<V>::dot(rv + 4 * (ch + 64), xv + 4 * (ch + 64));
-                s3 += Vec4<V>::dot(rv + 4 * (ch + 96), xv + 4 * (ch + 96));
-            }
-            for (; ch < nch; ch += 32) s0 += Vec4<V>::dot(rv + 4 * ch, xv + 4 * ch);
-            const V s = ddgdev::warp_sum((s0 + s1) + (s2 + s3));
-            if (lane == 0) out[i] = (a ? a[i] : (V)0) + sign * s;
-        }
-        return ddgdev::grid_barrier(gb, gridDim.x, err);
-    };
-    for (int K = 0; K < nK; ++K) {
-        const V* in = c;
-        if (K > 0) {
-            if (!step(Em, K * B, y, c, (V)-1, t)) return;
-            in = t;
-        }
-        if (!step(Dm, K * B, in, nullptr, (V)1, y)) return;
-    }
-    for (int K = nK - 1; K >= 0; --K) {
-        const V* in = y;
-        if (K < nK - 1) {
-            if (!step(Et, K * B, x, y, (V)-1, t)) return;
-            in = t;
-        }
-        if (!step(Dt, K * B, in, nullptr, (V)1, x)) return;
     }
 }
 
@@ -697,6 +693,16 @@ static void alloc_profile(ddg_handle h, ProfileMat& M, const std::vector<int>& l
 void coarse_build_apply(ddg_handle h) {
     const int n0p = h->n0p, B = h->B, Wt = h->Wt, nK = h->nK;
     const bool fp32 = true;
+    // coupling blocks F_K, G_K (FP64 tiles, released after the fill)
+    const size_t ntile = (size_t)nK * Wt * Wt * CT * CT;
+    double* Ft = h->arena.alloc<double>(ntile);
+    double* Gt = h->arena.alloc<double>(ntile);
+    if (nK > 1) {
+        const size_t sm2 = 2 * CT * CLD * sizeof(double);
+        DDG_CUDA(cudaFuncSetAttribute(coupling_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+        coupling_product_kernel<<<dim3(Wt * Wt, nK, 2), 256, sm2, h->stream>>>(h->bandL, h->coarseW, Wt, nK, Ft, Gt);
+        DDG_CHECK_LAUNCH();
+    }
     std::vector<int> lo(n0p), hi(n0p);
     int32_t *vlo[4], *vhi[4];
     // D: lower triangle of the super-block
@@ -705,45 +711,39 @@ void coarse_build_apply(ddg_handle h) {
         hi[i] = i + 1;
     }
     alloc_profile(h, h->Dm, lo, hi, fp32, &vlo[0], &vhi[0]);
-    // E: columns of super-block K-1 inside the tile band
-    for (int i = 0; i < n0p; ++i) {
-        const int K = i / B, R = i / CT;
-        if (K == 0) {
-            lo[i] = hi[i] = 0;
-        } else {
-            lo[i] = std::max((K - 1) * B, (R - Wt) * CT);
-            hi[i] = K * B;
-        }
-    }
-    alloc_profile(h, h->Em, lo, hi, fp32, &vlo[1], &vhi[1]);
     // D^T: upper triangle of the super-block
     for (int i = 0; i < n0p; ++i) {
         lo[i] = i;
         hi[i] = (i / B + 1) * B;
     }
-    alloc_profile(h, h->Dt, lo, hi, fp32, &vlo[2], &vhi[2]);
-    // E^T: row j of E_{K+1}^T = column j of E_{K+1}
-    for (int j = 0; j < n0p; ++j) {
-        const int K = j / B;
-        if (K >= nK - 1) {
-            lo[j] = hi[j] = 0;
-        } else {
-            lo[j] = (K + 1) * B;
-            hi[j] = std::min((K + 2) * B, (j / CT + Wt + 1) * CT);
-        }
+    alloc_profile(h, h->Dt, lo, hi, fp32, &vlo[1], &vhi[1]);
+    // F_K: rows of super-block K >= 1, all columns of K - 1
+    for (int i = 0; i < n0p; ++i) {
+        const int K = i / B;
+        lo[i] = K == 0 ? 0 : (K - 1) * B;
+        hi[i] = K == 0 ? 0 : K * B;
     }
-    alloc_profile(h, h->Et, lo, hi, fp32, &vlo[3], &vhi[3]);
+    alloc_profile(h, h->Fm, lo, hi, fp32, &vlo[2], &vhi[2]);
+    // G_K: rows of super-block K <= nK - 2, all columns of K + 1
+    for (int i = 0; i < n0p; ++i) {
+        const int K = i / B;
+        lo[i] = K >= nK - 1 ? 0 : (K + 1) * B;
+        hi[i] = K >= nK - 1 ? 0 : (K + 2) * B;
+    }
+    alloc_profile(h, h->Gm, lo, hi, fp32, &vlo[3], &vhi[3]);
     const unsigned blocks = (unsigned)((n0p * 32 + 255) / 256);
-    profile_fill_kernel<PM_D><<<blocks, 256, 0, h->stream>>>(h->Dm, vlo[0], vhi[0], n0p, h->bandL, h->coarseW, Wt, B);
-    profile_fill_kernel<PM_E><<<blocks, 256, 0, h->stream>>>(h->Em, vlo[1], vhi[1], n0p, h->bandL, h->coarseW, Wt, B);
-    profile_fill_kernel<PM_DT><<<blocks, 256, 0, h->stream>>>(h->Dt, vlo[2], vhi[2], n0p, h->bandL, h->coarseW, Wt, B);
-    profile_fill_kernel<PM_ET><<<blocks, 256, 0, h->stream>>>(h->Et, vlo[3], vhi[3], n0p, h->bandL, h->coarseW, Wt, B);
+    profile_fill_kernel<PM_D><<<blocks, 256, 0, h->stream>>>(h->Dm, vlo[0], vhi[0], n0p, h->coarseW, nullptr, Wt, B);
+    profile_fill_kernel<PM_DT><<<blocks, 256, 0, h->stream>>>(h->Dt, vlo[1], vhi[1], n0p, h->coarseW, nullptr, Wt, B);
+    profile_fill_kernel<PM_F><<<blocks, 256, 0, h->stream>>>(h->Fm, vlo[2], vhi[2], n0p, nullptr, Ft, Wt, B);
+    profile_fill_kernel<PM_G><<<blocks, 256, 0, h->stream>>>(h->Gm, vlo[3], vhi[3], n0p, nullptr, Gt, Wt, B);
     DDG_CHECK_LAUNCH();
     DDG_CUDA(cudaStreamSynchronize(h->stream));
     for (int t = 0; t < 4; ++t) {
         h->arena.release(vlo[t]);
         h->arena.release(vhi[t]);
     }
+    h->arena.release(Ft);
+    h->arena.release(Gt);
     h->arena.release(h->coarseW);
     h->coarseW = nullptr;
     h->arena.release(h->bandL);
@@ -792,55 +792,22 @@ static void gemv(ddg_handle h, const ProfileMat& M, int r0, int r1, const V* x, 
                                     (const float*)x, (const float*)a, (float)sign, (float*)out));
 }
 
+// y = L^{-1} c and x = L^{-T} y on the block-bidiagonal factor:
+//   y = D c (all super-blocks at once), then y_K -= F_K y_{K-1} for K = 1, 2, ...
+//   x = D^T y, then x_K -= G_K x_{K+1} for K = nK-2, ..., 0
+// 2 nK launches, of which 2 (nK - 1) form the dependent chain
 template <typename V>
-static void coarse_solve_t(ddg_handle h, V* c, V* y, V* t, V* x) {
-    const int B = h->B, nK = h->nK;
-    // forward: y_K = D_K (c_K - E_K y_{K-1})
-    for (int K = 0; K < nK; ++K) {
-        const int r0 = K * B, r1 = r0 + B;
-        const V* in = c;
-        if (K > 0) {
-            gemv<V>(h, h->Em, r0, r1, y, c, (V)-1, t);
-            in = t;
-        }
-        gemv<V>(h, h->Dm, r0, r1, in, nullptr, (V)1, y);
-    }
-    // backward: x_K = D_K^T (y_K - E_{K+1}^T x_{K+1})
-    for (int K = nK - 1; K >= 0; --K) {
-        const int r0 = K * B, r1 = r0 + B;
-        const V* in = y;
-        if (K < nK - 1) {
-            gemv<V>(h, h->Et, r0, r1, x, y, (V)-1, t);
-            in = t;
-        }
-        gemv<V>(h, h->Dt, r0, r1, in, nullptr, (V)1, x);
-    }
-}
-
-// one cooperative launch of the persistent recurrence (one CTA per SM)
-template <typename V>
-static void coarse_solve_persistent(ddg_handle h, V* c, V* y, V* t, V* x) {
-    int dev = 0, sms = 0;
-    DDG_CUDA(cudaGetDevice(&dev));
-    DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ProfileMat Dm = h->Dm, Em = h->Em, Dt = h->Dt, Et = h->Et;
-    int B = h->B, nK = h->nK;
-    const V* cv = c;
-    ddgdev::GridBar* gb = h->cgbar;
-    int* err = h->errflags + E_TIMEOUT;
-    void* args[] = {&Dm, &Em, &Dt, &Et, &B, &nK, &cv, &y, &t, &x, &gb, &err};
-    DDG_CUDA(cudaLaunchCooperativeKernel((const void*)coarse_gemv_persistent_kernel<V>, dim3(sms), dim3(512), args, 0,
-                                         h->stream));
+static void coarse_solve_t(ddg_handle h, V* c, V* y, V* x) {
+    const int B = h->B, nK = h->nK, n0p = h->n0p;
+    gemv<V>(h, h->Dm, 0, n0p, c, nullptr, (V)1, y);
+    for (int K = 1; K < nK; ++K) gemv<V>(h, h->Fm, K * B, (K + 1) * B, y, y, (V)-1, y);
+    gemv<V>(h, h->Dt, 0, n0p, y, nullptr, (V)1, x);
+    for (int K = nK - 2; K >= 0; --K) gemv<V>(h, h->Gm, K * B, (K + 1) * B, x, x, (V)-1, x);
 }
 
 void coarse_solve(ddg_handle h, int prec) {
-    if (h->persistent_coarse) {
-        if (prec == DDG_PREC_FP64) coarse_solve_persistent<double>(h, h->c64, h->y64, h->t64, h->x64);
-        else coarse_solve_persistent<float>(h, h->c32, h->y32, h->t32, h->x32);
-        return;
-    }
-    if (prec == DDG_PREC_FP64) coarse_solve_t<double>(h, h->c64, h->y64, h->t64, h->x64);
-    else coarse_solve_t<float>(h, h->c32, h->y32, h->t32, h->x32);
+    if (prec == DDG_PREC_FP64) coarse_solve_t<double>(h, h->c64, h->y64, h->x64);
+    else coarse_solve_t<float>(h, h->c32, h->y32, h->x32);
 }
 
 void coarse_prolong(ddg_handle h, int prec) {

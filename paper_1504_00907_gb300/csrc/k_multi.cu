@@ -564,7 +564,7 @@ __global__ void coarse_prolong_multi4_kernel(int64_t n, int m, const int32_t* __
 // fixed order.  Steps are chained by programmatic dependent launch: a CTA
 // stages its block of M (which no earlier step writes) in shared memory, and
 // only then waits for the previous step before it reads x and a.
-struct CoarseStep {            // one GEMM of the recurrence
+struct CoarseStep {            // one GEMM of the recurrence (cbase < 0: block-diagonal)
     const int64_t* rowptr;
     const int32_t* lo;
     const int32_t* hi;
@@ -594,6 +594,7 @@ __global__ void __launch_bounds__(CG_T) coarse_step_multi_kernel(CoarseStep S, i
     __shared__ int span[2];
     __shared__ int am_last;
     const int rt = blockIdx.x / nsplit, sp = blockIdx.x % nsplit;
+    const int R = (gridDim.x / nsplit) * CG_ROWS;   // rows of the launch: split stride of part
     const int row0 = S.r0 + rt * CG_ROWS;
     const int t = threadIdx.x;
     const int ty = t >> 4, tx = t & 15;   // rows 4ty..4ty+3, columns 4tx..4tx+3
@@ -616,7 +617,8 @@ __global__ void __launch_bounds__(CG_T) coarse_step_multi_kernel(CoarseStep S, i
     }
     __syncthreads();
     // the columns of this split that some row of the tile reaches
-    const int c_lo = S.cbase + sp * CG_KS;
+    const int cb = S.cbase >= 0 ? S.cbase : (row0 / B) * B;   // block-diagonal: own super-block
+    const int c_lo = cb + sp * CG_KS;
     const int ulo = max(span[0], c_lo), uhi = min(span[1], c_lo + CG_KS);
     const bool work = uhi > ulo;
     const int jb = ulo - c_lo, je = uhi - c_lo;   // local column range [jb, je)
@@ -695,7 +697,7 @@ __global__ void __launch_bounds__(CG_T) coarse_step_multi_kernel(CoarseStep S, i
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int c = 4 * tx + k;
-                if (c < m) part[((size_t)sp * B + rt * CG_ROWS + 4 * ty + i) * m + c] = acc[i][k];
+                if (c < m) part[((size_t)sp * R + rt * CG_ROWS + 4 * ty + i) * m + c] = acc[i][k];
             }
     }
     __threadfence();
@@ -706,13 +708,13 @@ __global__ void __launch_bounds__(CG_T) coarse_step_multi_kernel(CoarseStep S, i
     __threadfence();
     // splits that reach no column of the tile wrote nothing and add nothing;
     // the others are loaded together and summed in split order
-    const int sp0 = span[1] > span[0] ? max((span[0] - S.cbase) / CG_KS, 0) : 0;
-    const int sp1 = span[1] > span[0] ? min((span[1] - 1 - S.cbase) / CG_KS, nsplit - 1) : -1;
+    const int sp0 = span[1] > span[0] ? max((span[0] - cb) / CG_KS, 0) : 0;
+    const int sp1 = span[1] > span[0] ? min((span[1] - 1 - cb) / CG_KS, nsplit - 1) : -1;
     if (mp == m) {
         // 16-byte words: 4 outputs per load
         const int n4 = CG_ROWS * (m >> 2);
         const float4* p4 = reinterpret_cast<const float4*>(part + (size_t)rt * CG_ROWS * m);
-        const size_t st4 = (size_t)B * m / 4;
+        const size_t st4 = (size_t)R * m / 4;
         for (int e = t; e < n4; e += CG_T) {
             float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int q0 = sp0; q0 <= sp1; q0 += CG_LOADS) {
@@ -744,7 +746,7 @@ __global__ void __launch_bounds__(CG_T) coarse_step_multi_kernel(CoarseStep S, i
             float v[CG_LOADS];
 #pragma unroll
             for (int i = 0; i < CG_LOADS; ++i)
-                v[i] = q0 + i <= sp1 ? __ldcg(part + ((size_t)(q0 + i) * B + rt * CG_ROWS) * m + e) : 0.f;
+                v[i] = q0 + i <= sp1 ? __ldcg(part + ((size_t)(q0 + i) * R + rt * CG_ROWS) * m + e) : 0.f;
 #pragma unroll
             for (int i = 0; i < CG_LOADS; ++i)
                 if (q0 + i <= sp1) s += v[i];
@@ -787,7 +789,7 @@ void multi_ensure(ddg_handle h, int m) {
     if (w.m_alloc >= m) return;
     for (void* p : {(void*)w.R, (void*)w.P, (void*)w.Q, (void*)w.T, (void*)w.Fb, (void*)w.Ub,
                     (void*)w.r32, (void*)w.z32,
-                    (void*)w.res32, (void*)w.c32, (void*)w.y32, (void*)w.t32, (void*)w.x32,
+                    (void*)w.res32, (void*)w.c32, (void*)w.y32, (void*)w.x32,
                     (void*)w.scal, (void*)w.partials, (void*)w.active, (void*)w.restart,
                     (void*)w.items, (void*)w.gpart, (void*)w.gtick})
         if (p) h->arena.release(p);
@@ -804,16 +806,16 @@ void multi_ensure(ddg_handle h, int m) {
     const int64_t n0p = h->use_coarse ? h->n0p : 1;
     w.c32 = h->arena.alloc<float>(n0p * m);
     w.y32 = h->arena.alloc<float>(n0p * m);
-    w.t32 = h->arena.alloc<float>(n0p * m);
     w.x32 = h->arena.alloc<float>(n0p * m);
-    for (float* p : {w.c32, w.y32, w.t32, w.x32})
+    for (float* p : {w.c32, w.y32, w.x32})
         DDG_CUDA(cudaMemsetAsync(p, 0, n0p * m * sizeof(float), h->stream));
     if (h->use_coarse) {
         const int nsplit = (h->B + CG_KS - 1) / CG_KS;
-        w.gpart = h->arena.alloc<float>((size_t)nsplit * h->B * m);
+        // a step covers at most all n0p rows (the block-diagonal D launches)
+        w.gpart = h->arena.alloc<float>((size_t)nsplit * h->n0p * m);
         // one ticket per 32-row tile of a step; reset by the CTA that uses it last
-        w.gtick = h->arena.alloc<unsigned>(h->B / CG_ROWS);
-        DDG_CUDA(cudaMemsetAsync(w.gtick, 0, (h->B / CG_ROWS) * sizeof(unsigned), h->stream));
+        w.gtick = h->arena.alloc<unsigned>(h->n0p / CG_ROWS);
+        DDG_CUDA(cudaMemsetAsync(w.gtick, 0, (h->n0p / CG_ROWS) * sizeof(unsigned), h->stream));
     }
     w.scal = h->arena.alloc<double>(S_COUNT * DDG_MCHUNK);
     w.partials = h->arena.alloc<double>((size_t)DDG_RED_BLOCKS * 2 * DDG_MCHUNK);
@@ -893,7 +895,7 @@ static void multi_apply_t(ddg_handle h, int m) {
     };
     for (int c = 0; c < h->ncol; ++c) local(c, c == 0);
     if (h->use_coarse) {
-        ProfScope ps(h, DDG_K_COARSE, 2 + 4 * h->nK - 2, 0.0);
+        ProfScope ps(h, DDG_K_COARSE, 2 + 2 * h->nK, 0.0);
         const int bd = col_block(m);
         const size_t smem = (size_t)(bd / m) * h->kmax * m * sizeof(float);
 #define RESTRICT_MULTI(KM)                                                                              \
@@ -914,10 +916,11 @@ static void multi_apply_t(ddg_handle h, int m) {
 #undef RESTRICT_MULTI4
         const int B = h->B, nK = h->nK;
         const int nsplit = (B + CG_KS - 1) / CG_KS;
-        auto step = [&](const ProfileMat& M, int r0, int cbase, const float* x, const float* a, float sign,
-                        float* out) {
+        // rows [r0, r0 + rows); cbase < 0: each row's own super-block
+        auto step = [&](const ProfileMat& M, int r0, int rows, int cbase, const float* x, const float* a,
+                        float sign, float* out) {
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)((B / CG_ROWS) * nsplit));
+            cfg.gridDim = dim3((unsigned)((rows / CG_ROWS) * nsplit));
             cfg.blockDim = dim3(CG_T);
             cfg.dynamicSmemBytes = (size_t)CG_KS * ((m + 3) & ~3) * sizeof(float);
             cfg.stream = h->stream;
@@ -935,24 +938,12 @@ static void multi_apply_t(ddg_handle h, int m) {
             const CoarseStep S{M.rowptr, M.lo, M.hi, M.v32, r0, cbase, x, a, sign, out};
             DDG_CUDA(cudaLaunchKernelEx(&cfg, coarse_step_multi_kernel, S, B, m, nsplit, w.gpart, w.gtick));
         };
-        // forward: y_K = D_K (c_K - E_K y_{K-1})
-        for (int K = 0; K < nK; ++K) {
-            const float* in = w.c32;
-            if (K > 0) {
-                step(h->Em, K * B, (K - 1) * B, w.y32, w.c32, -1.f, w.t32);
-                in = w.t32;
-            }
-            step(h->Dm, K * B, K * B, in, nullptr, 1.f, w.y32);
-        }
-        // backward: x_K = D_K^T (y_K - E_{K+1}^T x_{K+1})
-        for (int K = nK - 1; K >= 0; --K) {
-            const float* in = w.y32;
-            if (K < nK - 1) {
-                step(h->Et, K * B, (K + 1) * B, w.x32, w.y32, -1.f, w.t32);
-                in = w.t32;
-            }
-            step(h->Dt, K * B, K * B, in, nullptr, 1.f, w.x32);
-        }
+        // y = D c (all super-blocks), y_K -= F_K y_{K-1}; x = D^T y, x_K -= G_K x_{K+1}
+        const int n0p = h->n0p;
+        step(h->Dm, 0, n0p, -1, w.c32, nullptr, 1.f, w.y32);
+        for (int K = 1; K < nK; ++K) step(h->Fm, K * B, B, (K - 1) * B, w.y32, w.y32, -1.f, w.y32);
+        step(h->Dt, 0, n0p, -1, w.y32, nullptr, 1.f, w.x32);
+        for (int K = nK - 2; K >= 0; --K) step(h->Gm, K * B, B, (K + 1) * B, w.x32, w.x32, -1.f, w.x32);
         if (vec4)
             coarse_prolong_multi4_kernel<<<(unsigned)((n * (m / 4) + 255) / 256), 256, 0, h->stream>>>(
                 n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);
