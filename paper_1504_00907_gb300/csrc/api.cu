@@ -365,16 +365,7 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
         true_rel = std::sqrt(h->h_scal[S_TMP]) / fn;
     }
     h->u = nullptr;
-    {
-        int32_t tflag = 0;
-        d2h(&tflag, h->errflags + E_TIMEOUT, 1, h->stream);
-        DDG_CUDA(cudaStreamSynchronize(h->stream));
-        if (tflag) {
-            DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
-            h->err = "a bounded grid barrier of the coarse solve ran out";
-            st = DDG_ETIMEOUT;
-        }
-    }
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = true_rel;
     return st;
