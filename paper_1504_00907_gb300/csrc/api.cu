@@ -419,6 +419,7 @@ ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol
     DDG_CUDA(cudaMemsetAsync(U, 0, n * m * sizeof(double), h->stream));
     DDG_CUDA(cudaMemsetAsync(w.P, 0, n * m * sizeof(double), h->stream));
     DDG_CUDA(cudaMemcpyAsync(w.R, F, n * m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    w.r32_current = false;
     auto upload = [&]() {
         h2d(w.active, active.data(), DDG_MCHUNK, h->stream);
         h2d(w.restart, restart.data(), DDG_MCHUNK, h->stream);

@@ -136,6 +136,7 @@ struct ProfileMat {         // rows with one contiguous column range each
 
 // workspace of the batched (multi-RHS) PCG, grown on first use
 struct MultiWork {
+    bool r32_current = false;   // r32 holds (float)R (written by update_ur)
     int m_alloc = 0;
     double *R = nullptr, *P = nullptr, *Q = nullptr, *T = nullptr;   // n x m FP64
     double *Fb = nullptr, *Ub = nullptr;                              // column-group staging

@@ -181,10 +181,12 @@ __global__ void __launch_bounds__(MT) spmv_multi_kernel(int64_t n, int m, const 
     }
 }
 
+// also writes R32 = (float)R, the preconditioner's input
 __global__ void __launch_bounds__(MT) update_ur_multi_kernel(int64_t n, int m, double* __restrict__ U,
                                                              double* __restrict__ R,
                                                              const double* __restrict__ P,
                                                              const double* __restrict__ Q,
+                                                             float* __restrict__ R32,
                                                              double* partials, unsigned* counter,
                                                              double* sc) {
     const int rpb = blockDim.x / m;
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__(MT) update_ur_multi_kernel(int64_t n, int m, d
                     U[e] = fma(alpha, pv[k], uv[k]);
                     const double r = fma(-alpha, qv[k], rv[k]);
                     R[e] = r;
+                    R32[e] = (float)r;
                     acc[0] = fma(r, r, acc[0]);
                 }
             }
@@ -856,7 +859,8 @@ static void multi_apply_t(ddg_handle h, int m) {
     MultiWork& w = h->mw;
     const int64_t n = h->n;
     const int prec = h->precision;
-    to_float_n_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, h->stream>>>(n * m, w.R, w.r32);
+    if (!w.r32_current)
+        to_float_n_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, h->stream>>>(n * m, w.R, w.r32);
     DDG_CUDA(cudaMemsetAsync(w.z32, 0, n * m * sizeof(float), h->stream));
     const bool tc = prec == DDG_PREC_BF16 && h->tc.A != nullptr;
     if (tc && h->tc.last_m != m) {
@@ -975,8 +979,9 @@ void multi_spmv_pq(ddg_handle h, int m) {
 
 void multi_update_ur(ddg_handle h, int m, double* U) {
     MultiWork& w = h->mw;
-    update_ur_multi_kernel<<<grid_for(h->n, m), col_block(m), 0, h->stream>>>(h->n, m, U, w.R, w.P, w.Q, w.partials, h->red_counter, w.scal);
+    update_ur_multi_kernel<<<grid_for(h->n, m), col_block(m), 0, h->stream>>>(h->n, m, U, w.R, w.P, w.Q, w.r32, w.partials, h->red_counter, w.scal);
     DDG_CHECK_LAUNCH();
+    w.r32_current = true;
 }
 
 void multi_dots(ddg_handle h, int m, int pr) {
@@ -1011,6 +1016,7 @@ void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int
 }
 
 void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace) {
+    h->mw.r32_current = false;
     const int bd = col_block(m), rpb = bd / m;
     replace_cols_kernel<<<(unsigned)((h->n + rpb - 1) / rpb), bd, 0, h->stream>>>(h->n, m, src, dst, replace);
     DDG_CHECK_LAUNCH();

@@ -141,6 +141,13 @@ def _dev(t, n=None, name="vector"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def torch_empty_like_host(t):
+    """An output buffer like the host tensor ``t`` (page-locked if ``t`` is)."""
+    import torch
+    out = torch.empty_like(t)
+    return out.pin_memory() if t.is_pinned() else out
+
+
 def _host(a, dtype):
     a = np.ascontiguousarray(a, dtype=dtype)
     return a, a.ctypes.data_as(ctypes.c_void_p)
@@ -225,12 +232,24 @@ class Solver:
             _check(st, self.h)
         return u, it.value, rr.value, st
 
-    def solve_host(self, f, tol=1e-8):
-        f, pf = _host(f, np.float64)
-        u = np.empty_like(f)
+    def solve_host(self, f, tol=1e-8, u=None):
+        """Solve from and into host memory (the copies happen inside the call).
+        ``f`` is a numpy array or a CPU float64 torch tensor; page-locked
+        tensors (``pin_memory()``) let the copies run at link speed.  ``u``
+        is an optional output of the same kind."""
+        if hasattr(f, "data_ptr"):
+            if f.device.type != "cpu" or not f.is_contiguous() or f.numel() != self.n:
+                raise ValueError(f"f must be a contiguous CPU tensor of {self.n} entries")
+            if u is None:
+                u = torch_empty_like_host(f)
+            pf, pu = ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr())
+        else:
+            f, pf = _host(f, np.float64)
+            if u is None:
+                u = np.empty_like(f)
+            pu = u.ctypes.data_as(ctypes.c_void_p)
         it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
-        st = load().ddg_solve_host(self.h, pf, u.ctypes.data_as(ctypes.c_void_p), tol,
-                                   ctypes.byref(it), ctypes.byref(rr))
+        st = load().ddg_solve_host(self.h, pf, pu, tol, ctypes.byref(it), ctypes.byref(rr))
         if st not in (DDG_OK, DDG_ENOCONV):
             _check(st, self.h)
         return u, it.value, rr.value, st

@@ -209,6 +209,12 @@ def test_batched_zero_column_and_single_solve_agree():
     uh, ith, rrh, sth = solver.solve_host(F[:, 0], tol=1e-9)
     u0, it0, _, _ = solver.solve(dev(F[:, 0]), tol=1e-9)
     np.testing.assert_array_equal(uh, u0.cpu().numpy())
+    # page-locked torch buffers: same call, same bits
+    fp = torch.tensor(np.ascontiguousarray(F[:, 0])).pin_memory()
+    up = torch.empty_like(fp).pin_memory()
+    u2, it2, _, st2 = solver.solve_host(fp, tol=1e-9, u=up)
+    assert u2 is up and st2 == 0 and it2 == it0
+    np.testing.assert_array_equal(up.numpy(), uh)
     solver.set_precision("fp64")
 
 
