@@ -113,7 +113,7 @@ typedef struct {
     int kmax;             /* generators per subdomain (columns of F) */
     int max_local;        /* largest overlapping subdomain |Omega~_i| */
     int64_t sum_local;    /* sum of |Omega~_i| */
-    int64_t local_tiles;  /* packed 32x32 tiles of all local inverses */
+    int64_t local_tiles;  /* size of all packed local inverses in 32x32-tile units (1024 values) */
     int coarse_band;      /* half-bandwidth of A0 in natural coarse order */
     int coarse_blocks;    /* super-blocks of the coarse block-bidiagonal factor */
     double setup_ms;      /* wall time of ddg_setup */

@@ -709,11 +709,11 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
             const int nq = (int)ov[h->h_sid[q]].size();
             ov_off[q + 1] = ov_off[q] + nq;
             Tq[q] = (nq + DDG_LT - 1) / DDG_LT;
-            tile_off[q + 1] = tile_off[q] + (int64_t)Tq[q] * (Tq[q] + 1) / 2;
+            tile_off[q + 1] = tile_off[q] + (int64_t)ddgdev::packed_elems(Tq[q], ddgdev::packed_narrow_width(nq, Tq[q]));
             h->max_local = std::max(h->max_local, nq);
         }
         h->sum_local = ov_off[nsub];
-        h->total_tiles = tile_off[nsub];
+        h->inv_elems = tile_off[nsub];
         h->Tmax = (h->max_local + DDG_LT - 1) / DDG_LT;
         DDG_REQUIRE(h->Tmax <= 96, DDG_EINVAL, "overlapping subdomains larger than 3072 dofs are not supported");
         h->h_ov_off = ov_off;
@@ -845,7 +845,7 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         // ---- local inverses (FP64 factorisation, packed copies)
         h->errflags = h->arena.alloc<int32_t>(E_COUNT);
         DDG_CUDA(cudaMemsetAsync(h->errflags, 0, E_COUNT * sizeof(int32_t), h->stream));
-        const size_t tile_elems = (size_t)h->total_tiles * 1024;
+        const size_t tile_elems = (size_t)h->inv_elems;
         if (keep & (1 << DDG_PREC_FP64)) h->inv64 = h->arena.alloc<double>(tile_elems);
         if (keep & (1 << DDG_PREC_FP32)) h->inv32 = h->arena.alloc<float>(tile_elems);
         if (keep & (1 << DDG_PREC_BF16)) h->inv16 = h->arena.alloc<__nv_bfloat16>(tile_elems);
@@ -1159,7 +1159,7 @@ ddg_status ddg_get_info(ddg_handle h, ddg_info* info) {
         info->kmax = h->kmax;
         info->max_local = h->max_local;
         info->sum_local = h->sum_local;
-        info->local_tiles = h->total_tiles;
+        info->local_tiles = (h->inv_elems + 1023) / 1024;
         info->coarse_band = h->band;
         info->coarse_blocks = h->nK;
         info->setup_ms = h->setup_ms;

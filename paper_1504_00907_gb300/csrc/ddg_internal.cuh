@@ -207,8 +207,8 @@ struct ddg_handle_s {
     int64_t* ov_off = nullptr;
     int32_t* ov_nodes = nullptr;
     int32_t* Tq = nullptr;
-    int64_t* tile_off = nullptr;
-    int64_t total_tiles = 0;
+    int64_t* tile_off = nullptr;   // [nsub + 1] element offset of each packed inverse
+    int64_t inv_elems = 0;         // elements of all packed inverses
     // local-solve work items per colour: {q, tile_begin, tile_end, unused}
     std::vector<int> h_citem_off;
     int nitems = 0;

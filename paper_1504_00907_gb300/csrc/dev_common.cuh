@@ -87,6 +87,22 @@ __device__ __forceinline__ V csr_row_dot_unrolled(int g, const int64_t* __restri
     return s;
 }
 
+// Packed upper tile triangle of one local inverse with T tile rows of 32:
+// band row I holds tiles J = I .. T-1; tiles J < T-1 are 32 x 32, the last
+// tile column (J = T-1) is stored narrow, 32 x wp with wp = the valid width
+// n - 32 (T - 1) rounded up to 8 (16-byte rows for 8-, 4- and 2-byte
+// elements).  Row stride inside a tile: 32, or wp for the last column.
+__host__ __device__ __forceinline__ int packed_narrow_width(int n, int T) {
+    return ((n - 32 * (T - 1)) + 7) & ~7;
+}
+__host__ __device__ __forceinline__ size_t packed_tile_start(int I, int J, int T, int wp) {
+    const size_t rowstart = (size_t)1024 * ((size_t)I * (T - 1) - (size_t)I * (I - 1) / 2) + (size_t)32 * wp * I;
+    return rowstart + (size_t)(J - I) * 1024;
+}
+__host__ __device__ __forceinline__ size_t packed_elems(int T, int wp) {
+    return (size_t)1024 * T * (T - 1) / 2 + (size_t)32 * wp * T;
+}
+
 // Long CSR rows (Q1 elasticity: 81 entries) go to groups of CSRW_G lanes:
 // lane l of a group takes entries l, l + G, ... of its row (coalesced column
 // and value loads) and the group sums by a fixed butterfly, after which every

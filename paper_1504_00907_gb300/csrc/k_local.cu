@@ -271,17 +271,21 @@ __global__ void local_pack_kernel(int q0, const double* __restrict__ ws, int Np,
     const int T = Tq[q];
     const double* A = ws + (size_t)b * Np * Np;
     const int64_t base = tile_off[q];
+    const int wp = ddgdev::packed_narrow_width(n, T);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     // warp w packs tiles w, w + nw, ... in row-major upper-triangle order
     int t = 0;
     for (int I = 0; I < T; ++I) {
         for (int J = I; J < T; ++J, ++t) {
             if (t % nw != warp) continue;
+            const int ld = J == T - 1 ? wp : DDG_LT;   // stored columns of the tile
+            if (lane >= ld) continue;
             const int gc = J * DDG_LT + lane;
+            const size_t t0 = (size_t)base + ddgdev::packed_tile_start(I, J, T, wp);
             for (int r = 0; r < DDG_LT; ++r) {
                 const int gr = I * DDG_LT + r;
                 const double v = (gr < n && gc < n) ? A[(size_t)gr * Np + gc] : 0.0;
-                const size_t dst = (size_t)(base + t) * 1024 + r * 32 + lane;
+                const size_t dst = t0 + (size_t)r * ld + lane;
                 if (inv64) inv64[dst] = v;
                 if (inv32) inv32[dst] = (float)v;
                 if (inv16) inv16[dst] = __float2bfloat16_rn((float)v);
@@ -433,18 +437,19 @@ __global__ void __launch_bounds__(LS_WARPS * 32, sizeof(V) == 4 ? 4 : 2) local_s
 
     const int g = lane / L::LPR, j = lane % L::LPR;
     const int idx = j * L::VEC + g;   // row/col owned by this lane after the reductions
-    const E* base = inv + (size_t)tile_off[q] * 1024 + g * 32 + j * L::VEC;
+    const E* sub = inv + tile_off[q];
+    const int wp = ddgdev::packed_narrow_width(n, T);
+    const int lane_32 = g * DDG_LT + j * L::VEC, lane_w = g * wp + j * L::VEC;
+    const int kstride_w = L::RPI * wp;
+    const bool lane_in_w = j * L::VEC < wp;
     V* myR = yR + warp * (DDG_BAND_ROWS * DDG_LT);
 
     for (int I = I0; I < I1; ++I) {
-        // packed index of tile (I, I): rows 0..I-1 hold T, T-1, ..., T-I+1 tiles
-        const size_t rowstart = (size_t)I * T - (size_t)I * (I - 1) / 2;
+        // element offset of tile (I, I) in the packed triangle
+        const size_t rowstart = ddgdev::packed_tile_start(I, I, T, wp);
         V racc = (V)0;
-        for (int J = I + ((warp - I) % LS_WARPS + LS_WARPS) % LS_WARPS; J < T; J += LS_WARPS) {
-            const E* tp = base + (rowstart + (J - I)) * 1024;
-            V e[L::NIT][L::VEC];
-#pragma unroll
-            for (int k = 0; k < L::NIT; ++k) Cvt<E, V>::load(tp + k * L::RPI * 32, e[k]);
+        // one tile's products: row part into racc, transposed part into yT[J]
+        auto tile = [&](int J, const V (&e)[L::NIT][L::VEC]) {
             V xj[L::VEC];
 #pragma unroll
             for (int v = 0; v < L::VEC; ++v) xj[v] = x[J * DDG_LT + j * L::VEC + v];
@@ -468,6 +473,42 @@ __global__ void __launch_bounds__(LS_WARPS * 32, sizeof(V) == 4 ? 4 : 2) local_s
                     for (int v = 0; v < L::VEC; ++v) cp[v] = fma(e[k][v], xi, cp[v]);
                 }
                 yT[J * DDG_LT + idx] += ddgdev::reduce_scatter<L::VEC, L::LPR>(cp, g);
+            }
+        };
+        // tiles J < T-1 are 32 wide, the last tile column wp wide (lanes past
+        // wp read zeros).  4- and 8-byte tiles: one loop selecting precomputed
+        // offsets and strides; 2-byte tiles (instruction-bound): the full
+        // tiles in a loop of their own and the narrow one after it.
+        auto load_tile = [&](int J, bool last, V (&e)[L::NIT][L::VEC]) {
+            const E* tp = sub + rowstart + (size_t)(J - I) * 1024 + (last ? lane_w : lane_32);
+            const int ks = last ? kstride_w : L::RPI * DDG_LT;
+            if (!last || lane_in_w) {
+#pragma unroll
+                for (int k = 0; k < L::NIT; ++k) Cvt<E, V>::load(tp + k * ks, e[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < L::NIT; ++k)
+#pragma unroll
+                    for (int v = 0; v < L::VEC; ++v) e[k][v] = (V)0;
+            }
+        };
+        int J = I + ((warp - I) % LS_WARPS + LS_WARPS) % LS_WARPS;
+        if constexpr (sizeof(E) == 2) {
+            for (; J < T - 1; J += LS_WARPS) {
+                V e[L::NIT][L::VEC];
+                load_tile(J, false, e);
+                tile(J, e);
+            }
+            if (J == T - 1) {
+                V e[L::NIT][L::VEC];
+                load_tile(J, true, e);
+                tile(J, e);
+            }
+        } else {
+            for (; J < T; J += LS_WARPS) {
+                V e[L::NIT][L::VEC];
+                load_tile(J, J == T - 1, e);
+                tile(J, e);
             }
         }
         myR[(I - I0) * DDG_LT + idx] = racc;

@@ -378,14 +378,16 @@ __global__ void __launch_bounds__(MT) local_solve_multi_kernel(
     float acc[DDG_MCHUNK / 8];
 #pragma unroll
     for (int u = 0; u < DDG_MCHUNK / 8; ++u) acc[u] = 0.f;
-    const E* base = inv + (size_t)tile_off[q] * 1024;
+    const E* sub = inv + tile_off[q];
+    const int wp = ddgdev::packed_narrow_width(n, T);
     for (int J = 0; J < T; ++J) {
         const bool upper = J >= I;
         const int a = upper ? I : J, b = upper ? J : I;
-        const E* tp = base + ((size_t)a * T - (size_t)a * (a - 1) / 2 + (b - a)) * 1024;
+        const E* tp = sub + ddgdev::packed_tile_start(a, b, T, wp);
+        const int ld = b == T - 1 ? wp : DDG_LT;   // stored columns of tile (a, b)
         for (int e = threadIdx.x; e < 1024; e += MT) {
             const int rr = e >> 5, kk = e & 31;
-            const float v = (float)tp[e];
+            const float v = kk < ld ? (float)tp[rr * ld + kk] : 0.f;
             if (upper) sB[rr][kk] = v;
             else sB[kk][rr] = v;
         }
