@@ -103,13 +103,14 @@ __host__ __device__ __forceinline__ size_t packed_elems(int T, int wp) {
     return (size_t)1024 * T * (T - 1) / 2 + (size_t)32 * wp * T;
 }
 
-// Long CSR rows (Q1 elasticity: 81 entries) go to groups of CSRW_G lanes:
+// Long CSR rows (Q1 elasticity: 81 entries) go to groups of CSRW_G lanes
+// (4 measured best for 81-entry rows against 8, 16 and 32):
 // lane l of a group takes entries l, l + G, ... of its row (coalesced column
 // and value loads) and the group sums by a fixed butterfly, after which every
 // lane of the group holds the row's dot product.  All lanes of the warp must
 // call it; `live` masks the loads of groups past the last row.
 constexpr int SK_CSRW = 102;
-constexpr int CSRW_G = 16;
+constexpr int CSRW_G = 4;
 
 template <int G, typename V, typename AV>
 __device__ __forceinline__ V csr_row_dot_group(int g, bool live, const int64_t* __restrict__ rowptr,
