@@ -464,7 +464,7 @@ template <> struct Vec4<double> {
     static __device__ __forceinline__ double dot(const double* m, const double* x) { return dot(load(m), x); }
 };
 
-constexpr int GEMV_TPR = 128;   // threads per row: a whole row's loads in flight
+constexpr int GEMV_TPR = 64;    // threads per row (measured against 32, 128 and 256)
 constexpr int GEMV_PF = 8;      // 16-byte chunks per thread loaded before the dependency wait
 
 // Launched as a programmatic dependent of the previous step: the matrix row
