@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ddg.h"
@@ -94,6 +95,14 @@ template <typename T>
 static inline void d2h(T* dst, const T* src, size_t count, cudaStream_t s) {
     if (count) DDG_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
 }
+
+// Launch a kernel that may start before its predecessor in the stream ends
+// (programmatic dependent launch, when h->use_pdl): the kernel itself
+// executes griddepcontrol.wait before it reads anything the predecessor
+// writes.  Kernels after a memset or a copy keep the ordinary dependency.
+template <typename... KArgs, typename... Args>
+static inline void launch_pdl(ddg_handle h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              Args&&... args);
 
 // kernel flavour of the A z products: the matrix-free Laplacians, or the CSR
 // path with rows unrolled when they are short (see dev_common.cuh)
@@ -351,3 +360,19 @@ void tc_local_solve(ddg_handle h, int colour, int m);
 void set_handleless_error(const char* msg);
 
 }  // namespace ddg
+
+template <typename... KArgs, typename... Args>
+static inline void launch_pdl(ddg_handle h, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = h->use_pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    DDG_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}

@@ -300,9 +300,8 @@ __global__ void local_pack_kernel(int q0, const double* __restrict__ ws, int Np,
 template <int SK, typename V, typename AV>
 __device__ __forceinline__ V residual_at(int g, const int64_t* __restrict__ rowptr,
                                          const int32_t* __restrict__ col, const AV* __restrict__ val,
-                                         const V* __restrict__ r, const V* __restrict__ z, int nx,
-                                         int ny, int nz) {
-    V s = r[g];
+                                         V rg, const V* __restrict__ z, int nx, int ny, int nz) {
+    V s = rg;
     if (SK == DDG_STENCIL_7PT_3D || SK == DDG_STENCIL_5PT_2D) {
         const int i = g % nx, j = (g / nx) % ny;
         V az = (SK == DDG_STENCIL_7PT_3D ? (V)6 : (V)4) * z[g];
@@ -333,20 +332,28 @@ __global__ void local_residual_kernel(int64_t a0, int64_t a1, const int32_t* __r
                                       const AV* __restrict__ val, const V* __restrict__ r,
                                       const V* __restrict__ z, V* __restrict__ res, int z_zero,
                                       int nx, int ny, int nz) {
+    // launched as a programmatic dependent: the row's node and r (fixed during
+    // the sweep) are read before griddepcontrol.wait, z after it
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if constexpr (SK == ddgdev::SK_CSRW) {
         // a group of CSRW_G lanes per local row; the whole warp reaches the shuffles
         constexpr int G = ddgdev::CSRW_G;
         const int64_t a = a0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
         const bool live = a < a1;
         const int g = live ? ov_nodes[a] : 0;
+        const V rg = live ? r[g] : (V)0;
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         V s = 0;
         if (!z_zero) s = ddgdev::csr_row_dot_group<G>(g, live, rowptr, col, val, z);
-        if (live && (threadIdx.x & (G - 1)) == 0) res[a] = r[g] - s;
+        if (live && (threadIdx.x & (G - 1)) == 0) res[a] = rg - s;
     } else {
         const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (a >= a1) return;
-        const int g = ov_nodes[a];
-        res[a] = z_zero ? r[g] : residual_at<SK>(g, rowptr, col, val, r, z, nx, ny, nz);
+        const bool live = a < a1;
+        const int g = live ? ov_nodes[a] : 0;
+        const V rg = live ? r[g] : (V)0;
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        if (!live) return;
+        res[a] = z_zero ? rg : residual_at<SK>(g, rowptr, col, val, rg, z, nx, ny, nz);
     }
 }
 
@@ -429,6 +436,10 @@ __global__ void __launch_bounds__(LS_WARPS * 32, sizeof(V) == 4 ? 4 : 2) local_s
     const int NP = T * DDG_LT;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+    // launched as a programmatic dependent: the item and its metadata are
+    // fixed; res, z and the tickets are read after griddepcontrol.wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = threadIdx.x; i < NP; i += blockDim.x) {
         x[i] = i < n ? res[o + i] : (V)0;
         yT[i] = (V)0;
@@ -558,6 +569,8 @@ __global__ void local_gather_kernel(int64_t a0, int64_t a1, const int32_t* __res
                                     const int32_t* __restrict__ first_item,
                                     const int32_t* __restrict__ row_nchunks,
                                     const V* __restrict__ partial, int Tmax, V* __restrict__ z) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t a = a0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= a1) return;
     const int q = ov_sub[a];
@@ -610,15 +623,17 @@ static void launch_residual(ddg_handle h, int64_t a0, int64_t a1, bool z_zero, i
     const int threads = 256;
     const int64_t lanes = (a1 - a0) * (SK == ddgdev::SK_CSRW ? ddgdev::CSRW_G : 1);
     const unsigned blocks = (unsigned)((lanes + threads - 1) / threads);
+    const int zz = z_zero ? 1 : 0;
     if (prec == DDG_PREC_FP64)
-        local_residual_kernel<SK, double, double><<<blocks, threads, 0, h->stream>>>(
-            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->res64, z_zero,
-            h->nx, h->ny, h->nz);
+        launch_pdl(h, local_residual_kernel<SK, double, double>, dim3(blocks), dim3(threads), 0, a0, a1,
+                   (const int32_t*)h->ov_nodes, (const int64_t*)h->rowptr, (const int32_t*)h->col,
+                   (const double*)h->val64, (const double*)h->rin64, (const double*)h->z64, h->res64, zz,
+                   h->nx, h->ny, h->nz);
     else
-        local_residual_kernel<SK, float, float><<<blocks, threads, 0, h->stream>>>(
-            a0, a1, h->ov_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->res32, z_zero,
-            h->nx, h->ny, h->nz);
-    DDG_CHECK_LAUNCH();
+        launch_pdl(h, local_residual_kernel<SK, float, float>, dim3(blocks), dim3(threads), 0, a0, a1,
+                   (const int32_t*)h->ov_nodes, (const int64_t*)h->rowptr, (const int32_t*)h->col,
+                   (const float*)h->val32, (const float*)h->r32, (const float*)h->z32, h->res32, zz, h->nx,
+                   h->ny, h->nz);
 }
 
 void local_residual(ddg_handle h, int c, bool z_zero, int prec) {
@@ -635,19 +650,17 @@ static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, 
     if (i1 <= i0) return;
     const size_t smem = local_solve_smem<V>(h->Tmax);
     auto kern = h->split_gather ? local_solve_kernel<E, V, true> : local_solve_kernel<E, V, false>;
-    kern<<<i1 - i0, LS_WARPS * 32, smem, h->stream>>>(h->items, i0, h->ov_off, h->ov_nodes,
-                                                      h->tile_off, h->Tq, h->nchunks,
-                                                      h->first_item, h->row_nchunks, inv, res,
-                                                      partial, h->counters, z, h->Tmax);
-    DDG_CHECK_LAUNCH();
+    launch_pdl(h, kern, dim3(i1 - i0), dim3(LS_WARPS * 32), smem, (const int4*)h->items, i0,
+               (const int64_t*)h->ov_off, (const int32_t*)h->ov_nodes, (const int64_t*)h->tile_off,
+               (const int32_t*)h->Tq, (const int32_t*)h->nchunks, (const int32_t*)h->first_item,
+               (const int32_t*)h->row_nchunks, inv, res, partial, h->counters, z, h->Tmax);
     if (h->split_gather) {
         const int64_t a0 = h->h_crow_off[c], a1 = h->h_crow_off[c + 1];
         const unsigned blocks = (unsigned)((a1 - a0 + 255) / 256);
-        local_gather_kernel<V><<<blocks, 256, 0, h->stream>>>(a0, a1, h->ov_sub, h->ov_off,
-                                                              h->ov_nodes, h->nchunks,
-                                                              h->first_item, h->row_nchunks,
-                                                              partial, h->Tmax, z);
-        DDG_CHECK_LAUNCH();
+        launch_pdl(h, local_gather_kernel<V>, dim3(blocks), dim3(256), 0, a0, a1, (const int32_t*)h->ov_sub,
+                   (const int64_t*)h->ov_off, (const int32_t*)h->ov_nodes, (const int32_t*)h->nchunks,
+                   (const int32_t*)h->first_item, (const int32_t*)h->row_nchunks, (const V*)partial,
+                   h->Tmax, z);
     }
 }
 
