@@ -23,7 +23,7 @@ namespace {
 
 constexpr int TC_M = 128;            // rows of Y per CTA (MMA M)
 constexpr int TC_K = 32;             // K per slab (two K = 16 MMAs)
-constexpr int TC_STAGES = 6;
+constexpr int TC_STAGES = 4;           // ring depth (measured against 3, 5, 6 and 8)
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_POLLS = 1u << 22;   // bounded mbarrier polls
 constexpr int A_SLAB = TC_M * TC_K;       // elements per A slab
