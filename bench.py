@@ -412,6 +412,34 @@ def elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, w
     return out
 
 
+class Replicas:
+    """Independent replicas, one per rank: the solver does not shard, so every
+    rank solves its own copy of the workload.  Timed regions are bracketed by
+    a barrier, the slowest rank's time counts, and the whole-job throughput is
+    all ranks' units over that time."""
+
+    def __init__(self, dist=None, device=None):
+        self.dist = dist
+        self.device = device
+        self.rank = dist.get_rank() if dist is not None else 0
+        self.world = dist.get_world_size() if dist is not None else 1
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x):
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return t.item()
+
+    def throughput(self, units_per_rank, seconds):
+        return self.world * units_per_rank / seconds
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
@@ -434,16 +462,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return t.item()
+    replicas = Replicas(dist, dev)
+    barrier, max_over_ranks = replicas.barrier, replicas.max
 
     N = args.size
     prob = di.make_poisson3d(N=N, box=WORKLOAD["box"], overlap=WORKLOAD["overlap"], p=WORKLOAD["p"],
@@ -528,10 +548,10 @@ def main():
         _, it, rr, st = solver.solve_host(fh, TOL, uh)
         e2e_iters += it
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
-    e2e_value = world * n * (e2e_iters / args.steps) / e2e_s
+    e2e_value = replicas.throughput(n * (e2e_iters / args.steps), e2e_s)
 
     mean_it32 = sum(it32) / len(it32)
-    value = world * n * mean_it32 / (ms32 / 1e3)
+    value = replicas.throughput(n * mean_it32, ms32 / 1e3)
     launches_per_step = sum(v["launches"] for v in st32.values()) / args.steps
 
     ls = st32e["local_solve"]
