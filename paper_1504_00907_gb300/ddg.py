@@ -397,11 +397,13 @@ def solve_many(solvers, rhs, tol=1e-8):
 
 
 def solve_autograd(solver, kappa, f, tol=1e-10):
-    """u = A(kappa)^{-1} f with gradients for kappa and f (VAR7 handles).
+    """u = A(c)^{-1} f with gradients for the coefficient array c and for f.
 
-    The forward solve and the adjoint solve both run through the library;
-    the backward returns dL/df = lambda and dL/dkappa = -lambda^T (dA/dkappa) u
-    (ddg_grad_coeff).  ``solver`` must have been set up for this ``kappa``.
+    ``solver`` must have been set up with coefficients ``c`` (the cell
+    conductivities kappa of a variable-coefficient handle, or the element
+    shear moduli mu of a Q1-elasticity handle).  The forward solve and the
+    adjoint solve both run through the library; the backward returns
+    dL/df = lambda and dL/dc = -lambda^T (dA/dc) u (``ddg_grad_coeff``).
     """
     import torch
 
