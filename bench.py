@@ -122,6 +122,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def code_hash(path):
+    """First 12 hex digits of the sha1 of a source file without its comments
+    and with whitespace runs collapsed: edits to comments keep the hash, any
+    change to the code changes it."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", " ", src).strip()
+    return hashlib.sha1(src.encode()).hexdigest()[:12]
+
+
 def traffic_from_profile(kernel_file, launch_bytes):
     """Per-launch DRAM traffic of the local-solve kernel from the committed ncu
     summary, scaled to this launch's algorithmic bytes; None when the summary
@@ -131,8 +142,7 @@ def traffic_from_profile(kernel_file, launch_bytes):
         text = open(path).read()
     except OSError:
         return None
-    src = open(kernel_file, "rb").read()
-    sha = hashlib.sha1(src).hexdigest()[:12]
+    sha = code_hash(kernel_file)
     m = re.search(r"source sha1:\s*([0-9a-f]{12})", text)
     r = re.search(r"traffic/algorithmic bytes:\s*([0-9.]+)", text)
     if not m or not r or m.group(1) != sha:

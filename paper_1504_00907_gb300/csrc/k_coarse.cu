@@ -11,10 +11,12 @@
 //   band Cholesky       A0 = L L^T (FP64) in the tiled band, right-looking.
 //   super-blocks        regroup L into super-blocks of Wt tiles so that L is
 //                       block bidiagonal; D_K = L_KK^{-1} (tile forward
-//                       substitution), E_K = L_{K,K-1}.
+//                       substitution) and the coupling blocks
+//                       F_K = D_K L_{K,K-1}, G_K = D_K^T L_{K+1,K}^T.
 // Apply (FP64 or FP32)
 //   c = R0 (r - A z)    coarse_restrict (residual fused)
-//   y = A0^{-1} c       2 nK dependent profile-row GEMVs forward, 2 nK backward
+//   y = A0^{-1} c       y = D c, y_K -= F_K y_{K-1}; x = D^T y, x_K -= G_K x_{K+1}:
+//                       profile-row GEMVs, 2 (nK - 1) of them chained
 //   z += R0^T y         coarse_prolong
 #include <algorithm>
 

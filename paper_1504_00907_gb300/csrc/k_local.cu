@@ -3,17 +3,17 @@
 // Setup: A_i = R~_i A R~_i^T is gathered densely (FP64), factored A_i = L L^T
 // and inverted (A_i^{-1} = L^{-T} L^{-1}) in 32x32 tiles by one CTA per
 // subdomain, and the upper-triangular tiles of the symmetric inverse are
-// packed in FP64 / FP32 / BF16.
+// packed in FP64 / FP32 / BF16 (the last tile column at its valid width).
 //
 // Apply (per colour c of the sweep; subdomains of one colour do not interact):
 //   res_i = (r - A z)[Omega~_i]            local_residual_kernel
 //   z[Omega~_i] += A_i^{-1} res_i          local_solve_kernel
 // The second kernel streams the packed inverse; every tile (I, J), I < J,
 // is read once and used twice (y_I += B x_J and y_J += B^T x_I), which halves
-// the bytes of a dense GEMV.  Work items are chunks of consecutive tiles of
-// one subdomain; the CTA that finishes a subdomain's last chunk sums the
-// chunk partials in a fixed order and scatters into z, so the result is
-// deterministic.  Large subdomains (many chunks) leave that sum to a
+// the bytes of a dense GEMV.  Work items are bands of whole tile rows of one
+// subdomain; the CTA that finishes a subdomain's last band sums the band
+// partials in a fixed order and scatters into z, so the result is
+// deterministic.  Large subdomains (many bands) leave that sum to a
 // row-parallel gather kernel with the same order, which keeps one CTA's
 // serial sum off the end of the launch.
 #include "ddg_internal.cuh"

@@ -9,10 +9,10 @@
 // the deterministic reduction -- in one file-scope static device array,
 // which every GPU that loads this library holds until the process exits.
 //
-// The arithmetic is the same as the library's FP64 CSR SpMV with the fused
-// p^T A p of the CG recurrence: y[g] = sum_e val[e] x[col[e]] in column order,
-// and the reduction sums one partial per block in block order, so the
-// result is deterministic.  The paper has no counterpart of this call.
+// The arithmetic is that of the library's thread-per-row FP64 CSR SpMV with
+// the fused p^T A p of the CG recurrence: y[g] = sum_e val[e] x[col[e]] in
+// column order, and the reduction sums one partial per block in block order,
+// so the result is deterministic.  The paper has no counterpart of this call.
 #include <mutex>
 
 #include "ddg_internal.cuh"
