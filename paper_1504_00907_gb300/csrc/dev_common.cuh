@@ -87,20 +87,34 @@ __device__ __forceinline__ V csr_row_dot_unrolled(int g, const int64_t* __restri
     return s;
 }
 
-// Packed upper tile triangle of one local inverse with T tile rows of 32:
-// band row I holds tiles J = I .. T-1; tiles J < T-1 are 32 x 32, the last
-// tile column (J = T-1) is stored narrow, 32 x wp with wp = the valid width
-// n - 32 (T - 1) rounded up to 8 (16-byte rows for 8-, 4- and 2-byte
-// elements).  Row stride inside a tile: 32, or wp for the last column.
+// Packed upper tile triangle of one local inverse with T tile rows of 32.
+// Band row I < T-1 holds, in this order: the diagonal tile (I, I) as an
+// upper trapezoid in 8-column blocks (row r keeps columns 8 floor(r/8) .. 31,
+// PACKED_DIAG = 640 values, the 8x8 diagonal blocks in full), the full 32x32
+// tiles J = I+1 .. T-2, and the last tile column J = T-1 stored 32 x wp with
+// wp = n - 32 (T - 1) rounded up to 8.  Band row T-1 holds only its narrow
+// diagonal tile, 32 x wp.  Every 8-column block of a row starts on a 16-byte
+// boundary for 2-, 4- and 8-byte elements.
+constexpr int PACKED_DIAG = 640;
+
 __host__ __device__ __forceinline__ int packed_narrow_width(int n, int T) {
     return ((n - 32 * (T - 1)) + 7) & ~7;
 }
+__host__ __device__ __forceinline__ size_t packed_row_start(int I, int T, int wp) {
+    return (size_t)I * (PACKED_DIAG + 32 * wp) + (size_t)1024 * ((size_t)I * (T - 2) - (size_t)I * (I - 1) / 2);
+}
+// first element of tile (I, J), J >= I
 __host__ __device__ __forceinline__ size_t packed_tile_start(int I, int J, int T, int wp) {
-    const size_t rowstart = (size_t)1024 * ((size_t)I * (T - 1) - (size_t)I * (I - 1) / 2) + (size_t)32 * wp * I;
-    return rowstart + (size_t)(J - I) * 1024;
+    const size_t rs = packed_row_start(I, T, wp);
+    return J == I ? rs : rs + PACKED_DIAG + (size_t)(J - I - 1) * 1024;
 }
 __host__ __device__ __forceinline__ size_t packed_elems(int T, int wp) {
-    return (size_t)1024 * T * (T - 1) / 2 + (size_t)32 * wp * T;
+    return packed_row_start(T - 1, T, wp) + (size_t)32 * wp;
+}
+// element (r, c), c >= 8 floor(r / 8), of a trapezoid diagonal tile
+__host__ __device__ __forceinline__ int packed_diag_offset(int r, int c) {
+    const int a = r >> 3, b = r & 7;
+    return 256 * a - 32 * a * (a - 1) + b * (32 - 8 * a) + (c - 8 * a);
 }
 
 // Long CSR rows (Q1 elasticity: 81 entries) go to groups of CSRW_G lanes

@@ -280,12 +280,14 @@ __global__ void local_pack_kernel(int q0, const double* __restrict__ ws, int Np,
             if (t % nw != warp) continue;
             const int ld = J == T - 1 ? wp : DDG_LT;   // stored columns of the tile
             if (lane >= ld) continue;
+            const bool trap = J == I && I < T - 1;      // upper trapezoid diagonal tile
             const int gc = J * DDG_LT + lane;
             const size_t t0 = (size_t)base + ddgdev::packed_tile_start(I, J, T, wp);
             for (int r = 0; r < DDG_LT; ++r) {
+                if (trap && lane < 8 * (r >> 3)) continue;
                 const int gr = I * DDG_LT + r;
                 const double v = (gr < n && gc < n) ? A[(size_t)gr * Np + gc] : 0.0;
-                const size_t dst = t0 + (size_t)r * ld + lane;
+                const size_t dst = t0 + (trap ? (size_t)ddgdev::packed_diag_offset(r, lane) : (size_t)r * ld + lane);
                 if (inv64) inv64[dst] = v;
                 if (inv32) inv32[dst] = (float)v;
                 if (inv16) inv16[dst] = __float2bfloat16_rn((float)v);
@@ -491,7 +493,10 @@ __global__ void __launch_bounds__(LS_WARPS * 32, sizeof(V) == 4 ? 4 : 2) local_s
         // offsets and strides; 2-byte tiles (instruction-bound): the full
         // tiles in a loop of their own and the narrow one after it.
         auto load_tile = [&](int J, bool last, V (&e)[L::NIT][L::VEC]) {
-            const E* tp = sub + rowstart + (size_t)(J - I) * 1024 + (last ? lane_w : lane_32);
+            // tiles right of the diagonal follow the trapezoid diagonal tile;
+            // J == I here only for the narrow diagonal tile of band row T-1
+            const size_t toff = J == I ? 0 : (size_t)ddgdev::PACKED_DIAG + (size_t)(J - I - 1) * 1024;
+            const E* tp = sub + rowstart + toff + (last ? lane_w : lane_32);
             const int ks = last ? kstride_w : L::RPI * DDG_LT;
             if (!last || lane_in_w) {
 #pragma unroll
@@ -504,6 +509,51 @@ __global__ void __launch_bounds__(LS_WARPS * 32, sizeof(V) == 4 ? 4 : 2) local_s
             }
         };
         int J = I + ((warp - I) % LS_WARPS + LS_WARPS) % LS_WARPS;
+        if (J == I && I < T - 1) {
+            // trapezoid diagonal tile: chunks left of the row's 8-column block
+            // are not stored (zero here); the row products use every stored
+            // chunk, the transposed products skip the 8x8 diagonal blocks,
+            // which are stored in full
+            const E* dp = sub + rowstart;
+            const int cb = (j * L::VEC) >> 3;
+            V e[L::NIT][L::VEC];
+            bool tr[L::NIT];
+#pragma unroll
+            for (int k = 0; k < L::NIT; ++k) {
+                const int rk = g + k * L::RPI, rb = rk >> 3;
+                tr[k] = cb > rb;
+                if (cb >= rb) {
+                    Cvt<E, V>::load(dp + ddgdev::packed_diag_offset(rk, j * L::VEC), e[k]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < L::VEC; ++v) e[k][v] = (V)0;
+                }
+            }
+            V xj[L::VEC];
+#pragma unroll
+            for (int v = 0; v < L::VEC; ++v) xj[v] = x[I * DDG_LT + j * L::VEC + v];
+            V rp[L::NIT];
+#pragma unroll
+            for (int k = 0; k < L::NIT; ++k) {
+                V s = (V)0;
+#pragma unroll
+                for (int v = 0; v < L::VEC; ++v) s = fma(e[k][v], xj[v], s);
+                rp[k] = s;
+            }
+            racc += ddgdev::reduce_scatter<L::NIT, 1>(rp, j);
+            V cp[L::VEC];
+#pragma unroll
+            for (int v = 0; v < L::VEC; ++v) cp[v] = (V)0;
+#pragma unroll
+            for (int k = 0; k < L::NIT; ++k) {
+                if (!tr[k]) continue;
+                const V xi = x[I * DDG_LT + k * L::RPI + g];
+#pragma unroll
+                for (int v = 0; v < L::VEC; ++v) cp[v] = fma(e[k][v], xi, cp[v]);
+            }
+            yT[I * DDG_LT + idx] += ddgdev::reduce_scatter<L::VEC, L::LPR>(cp, g);
+            J += LS_WARPS;
+        }
         if constexpr (sizeof(E) == 2) {
             for (; J < T - 1; J += LS_WARPS) {
                 V e[L::NIT][L::VEC];

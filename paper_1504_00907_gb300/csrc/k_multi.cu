@@ -385,9 +385,17 @@ __global__ void __launch_bounds__(MT) local_solve_multi_kernel(
         const int a = upper ? I : J, b = upper ? J : I;
         const E* tp = sub + ddgdev::packed_tile_start(a, b, T, wp);
         const int ld = b == T - 1 ? wp : DDG_LT;   // stored columns of tile (a, b)
+        const bool trap = a == b && a < T - 1;     // upper trapezoid diagonal tile
         for (int e = threadIdx.x; e < 1024; e += MT) {
             const int rr = e >> 5, kk = e & 31;
-            const float v = kk < ld ? (float)tp[rr * ld + kk] : 0.f;
+            float v;
+            if (trap) {
+                // (rr, kk) left of its row's 8-column block is the mirror (kk, rr)
+                v = kk >= 8 * (rr >> 3) ? (float)tp[ddgdev::packed_diag_offset(rr, kk)]
+                                        : (float)tp[ddgdev::packed_diag_offset(kk, rr)];
+            } else {
+                v = kk < ld ? (float)tp[rr * ld + kk] : 0.f;
+            }
             if (upper) sB[rr][kk] = v;
             else sB[kk][rr] = v;
         }
