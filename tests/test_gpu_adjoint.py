@@ -1,4 +1,4 @@
-"""Adjoint solve and coefficient gradient (spec pattern 3) on the GPU.
+"""Adjoint solve and coefficient gradient (the differentiation workload) on the GPU.
 
 Loss L(u) = 0.5 ||u - u_t||^2 with u = A(kappa)^{-1} f for the cell-centred
 variable-coefficient operator.  The GPU gradient (adjoint PCG through the
@@ -95,7 +95,7 @@ def test_autograd_function(precision):
 
 
 def test_q1_elasticity_mu_gradient_matches_central_differences():
-    # spec differentiation workload on a 6^3-element copy: loss
+    # the Q1 elasticity differentiation workload on a 6^3-element copy: loss
     # L = 0.5 ||u - u_t||^2, u = A(mu)^{-1} b; dL/dmu_e by the adjoint solve
     # and ddg_grad_coeff against central differences of dense solves
     from paper_1504_00907_gb300 import ddg
