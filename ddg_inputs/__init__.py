@@ -346,6 +346,18 @@ def box_partition(shape, box):
     return sid.astype(np.int32)
 
 
+def subdomain_groups(shape, box, group):
+    """Subdomain -> coarse-level subdomain for the three-level method.
+
+    The subdomains of ``box_partition(shape, box)`` form a grid of boxes (x
+    fastest); the coarse-level subdomains are boxes of ``group`` subdomains
+    per axis of that grid, numbered the same way.
+    """
+    nb = tuple((s + b - 1) // b for s, b in zip(shape, box))
+    g = group if isinstance(group, (tuple, list)) else (group,) * len(nb)
+    return box_partition(nb, tuple(g))
+
+
 def monomial_exponents(d, p):
     """Exponent tuples of all monomials of total degree <= p in d variables,
     ordered by total degree, then descending exponent lexicographically."""

@@ -35,6 +35,12 @@ notes):
   1000 iterations.
 * beta: Fletcher-Reeves (textbook CG) by default; Polak-Ribiere
   (flexible) on request.
+* Three-level V-cycle (Sec. 6): the exact coarse solve A0^{-1} is replaced
+  by one application of the two-level method to A0 with the coarsened
+  generators F0 = R0 F.  The coarse-level subdomains are given as groups of
+  fine subdomains (a coarse dof belongs to the group of its subdomain; groups
+  without coarse dofs are dropped and the ids compacted); their overlap is
+  the same Delta, grown in the graph of A0.
 """
 from __future__ import annotations
 
@@ -217,7 +223,7 @@ class DDGOracle:
     """Setup and application of the DDG two-level Schwarz preconditioner."""
 
     def __init__(self, A, part, F, overlap, mode="graph", shape=None, rank_tol=RANK_TOL,
-                 coarse=True, dpn=1):
+                 coarse=True, dpn=1, coarse_groups=None):
         self.A = sp.csr_matrix(A, dtype=np.float64)
         self.n = self.A.shape[0]
         self.part = np.asarray(part, dtype=np.int64)
@@ -240,7 +246,17 @@ class DDGOracle:
             self.R0, self.coarse_offsets = coarse_basis(np.asarray(F, dtype=np.float64),
                                                          self.part, rank_tol)
             self.A0 = galerkin_coarse(self.A, self.R0)
-            self.coarse = CoarseSolver(self.A0)
+            self.inner = None
+            if coarse_groups is not None and self.A0.shape[0] > 0:
+                # Sec. 6: the three-level method applies the two-level
+                # method to A0, with generators F0 = R0 F
+                sub_of_dof = np.repeat(np.arange(self.nsub), np.diff(self.coarse_offsets))
+                group = np.asarray(coarse_groups, dtype=np.int64)[sub_of_dof]
+                _, part0 = np.unique(group, return_inverse=True)
+                F0 = self.R0 @ np.asarray(F, dtype=np.float64)
+                self.inner = DDGOracle(self.A0, part0, F0, overlap, "graph", rank_tol=rank_tol)
+            else:
+                self.coarse = CoarseSolver(self.A0)
 
     # one subdomain step of Sec. 6: u <- u + R~_i^T A_i^{-1} R~_i (f - A u)
     def _subdomain_step(self, i, r, z):
@@ -249,8 +265,14 @@ class DDGOracle:
         z[idx] += sla.cho_solve(self.local[i], res)
 
     def coarse_correction(self, r):
-        """R0^T A0^{-1} R0 r (Sec. 4: coarse approximation R0^T u0, A0 u0 = R0 f)."""
-        return self.R0.T @ self.coarse.solve(self.R0 @ r)
+        """R0^T A0^{-1} R0 r (Sec. 4: coarse approximation R0^T u0, A0 u0 = R0 f).
+
+        In the three-level method A0^{-1} is replaced by one application of
+        the two-level preconditioner of A0 (Sec. 6).
+        """
+        c = self.R0 @ r
+        x = self.inner.apply(c) if self.inner is not None else self.coarse.solve(c)
+        return self.R0.T @ x
 
     def apply(self, r):
         """z = M^{-1} r: one two-level symmetric multiplicative step from z = 0.
