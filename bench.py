@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--elasticity-size", type=int, default=64,
                     help="elements per side of the Q1 elasticity arm (0 skips it)")
     ap.add_argument("--elasticity-steps", type=int, default=3)
+    ap.add_argument("--vcycle-group", type=int, default=4,
+                    help="three-level arm: subdomains per axis of a coarse-level subdomain (0 skips it)")
     ap.add_argument("--keep", default="fp64,fp32,bf16",
                     help="local-inverse precisions kept at setup (profiling runs keep fewer)")
     return ap.parse_args()
@@ -309,6 +311,57 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
     for s in solvers:
         s.close()
     return res
+
+
+def vcycle_arm(args, prob, two_level, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
+    """Three-level V-cycle (Sec. 6) on the headline problem: the exact coarse
+    solve is replaced by one two-level step on A0 with generators F0 = R0 F,
+    coarse-level subdomains of args.vcycle_group^3 subdomains, overlap 1 in
+    the graph of A0; FP32 preconditioner, FP64 CG to 1e-8."""
+    g = args.vcycle_group
+    groups = di.subdomain_groups(prob.shape, prob.box, g)
+    t0 = time.perf_counter()
+    s3 = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32",), coarse_groups=groups)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    u = torch.empty_like(f)
+    for _ in range(args.warmup):
+        s3.solve(f, TOL, u)
+    torch.cuda.synchronize()
+    barrier()
+    s3.profile(())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, rels, sts = [], [], []
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, it, rr, st = s3.solve(f, TOL, u)
+        iters.append(it)
+        rels.append(rr)
+        sts.append(int(st))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    launches = sum(v["launches"] for v in s3.kernel_stats().values()) / args.steps
+    s3.profile(ddg.KERNEL_CLASSES)
+    s3.solve(f, TOL, u)
+    torch.cuda.synchronize()
+    breakdown = {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in s3.kernel_stats().items()}
+    s3.profile(())
+    info = s3.info()
+    s3.close()
+    nb = [(a + b - 1) // b for a, b in zip(prob.shape, prob.box)]
+    ng = 1
+    for m in nb:
+        ng *= (m + g - 1) // g
+    return {"workload": f"{prob.name}: {g}^3 subdomains per coarse-level subdomain ({ng} of them), "
+                        "overlap 1 in the graph of A0, FP32 preconditioner, tol 1e-8",
+            "coarse_level_subdomains": ng, "coarse_dim": info["n0"], "setup_s": setup_s,
+            "status": max(sts), "iters": iters[-1], "true_relres": rels[-1], "ms": ms,
+            "dof_iters_per_s": world * prob.n * iters[-1] / (ms / 1e3),
+            "two_level": {"ms": two_level[0], "iters": two_level[1]},
+            "gpu_launches_per_step": launches,
+            "breakdown_one_solve": breakdown}
 
 
 def elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
@@ -589,6 +642,11 @@ def main():
     if args.uneven:
         uneven = uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world)
 
+    vcycle = None
+    if args.vcycle_group > 0:
+        vcycle = vcycle_arm(args, prob, (ms32, it32[-1]), ddg, di, torch, dev, stream, barrier,
+                            max_over_ranks, world)
+
     elasticity = None
     if args.elasticity_size > 0:
         elasticity = elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
@@ -621,6 +679,7 @@ def main():
         "batched": batched,
         "uneven_batch": uneven,
         "elasticity_differentiation": elasticity,
+        "three_level_vcycle": vcycle,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

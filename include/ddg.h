@@ -140,6 +140,29 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
                      int overlap, const ddg_options* opt, void* stream, ddg_handle* out);
 
 /*
+ * Three-level V-cycle (Sec. 6): as ddg_setup, but inside the preconditioner
+ * the exact coarse solve A0^{-1} is replaced by one application of the
+ * two-level method to A0, built from the coarsened generators F0 = R0 F on
+ * coarse-level subdomains that group the fine subdomains (no Cholesky factor
+ * of A0 is formed; the coarsest matrix A1 = R1 A0 R1^T is factorised).
+ *   coarse_partition  host int32[nsub]: fine subdomain -> coarse-level
+ *              subdomain id >= 0.  Groups without coarse dofs are dropped
+ *              and the rest numbered in ascending id order.
+ * The coarse level uses the same overlap Delta, grown by graph distance in
+ * the graph of A0, and the same precision, keep_precisions and rank_tol;
+ * tensor_cores applies to the fine level only.  Every solve entry point
+ * accepts the handle; ddg_solve_batch then solves its columns one at a time.
+ * Overlapping coarse-level subdomains are limited to 3072 coarse dofs, like
+ * fine ones.
+ * Errors: as ddg_setup; DDG_EINVAL also for coarse_partition == NULL or
+ * use_coarse == 0; a failure on the coarse level is reported with the
+ * prefix "coarse level of the V-cycle: " in ddg_last_error(NULL).
+ */
+ddg_status ddg_setup_vcycle(const ddg_matrix* A, const int32_t* partition,
+                            const int32_t* coarse_partition, const double* F, int k, int overlap,
+                            const ddg_options* opt, void* stream, ddg_handle* out);
+
+/*
  * Solve A u = f by PCG from u0 = 0 (Sec. 7): stop when the recurrence
  * residual satisfies ||r||_2 <= tol ||f||_2 and the true residual does too
  * (a recurrence that drifts is replaced by the true residual and CG

@@ -202,11 +202,45 @@ void local_step(ddg_handle h, int c, bool z_zero, int prec) {
     ddg::local_solve_colour(h, c, prec);
 }
 
+int64_t coarse_vcycle(ddg_handle h, int prec);
+
 void coarse_step(ddg_handle h, int prec, bool residual) {
-    ProfScope ps(h, DDG_K_COARSE, 2 + 2 * h->nK, 0.0);
+    ProfScope ps(h, DDG_K_COARSE, h->inner ? 2 : 2 + 2 * h->nK, 0.0);
     ddg::coarse_restrict(h, prec, residual);
-    ddg::coarse_solve(h, prec);
+    if (h->inner) h->prof_launches[DDG_K_COARSE] += coarse_vcycle(h, prec);
+    else ddg::coarse_solve(h, prec);
     ddg::coarse_prolong(h, prec);
+}
+
+// One symmetric two-level step from z = 0 on the input already in rin64
+// (FP64) or r32, z already zeroed (Sec. 6).
+void sweeps_and_coarse(ddg_handle h, int prec) {
+    // pre-smoother: one multiplicative pass in sweep order
+    for (int c = 0; c < h->ncol; ++c) local_step(h, c, c == 0, prec);
+    // coarse correction of the current residual
+    if (h->use_coarse) coarse_step(h, prec, true);
+    // post-smoother: the same pass in reverse order
+    for (int c = h->ncol - 1; c >= 0; --c) local_step(h, c, false, prec);
+}
+
+// Sec. 6, three-level V-cycle: x = B0 c, one application of the two-level
+// preconditioner of A0 to the restricted residual c, enqueued on this
+// handle's stream.  The inner handle reads c (c64 in place, c32 as its r32)
+// and leaves B0 c in x (its z64 / z32).  Returns the inner kernel launches.
+int64_t coarse_vcycle(ddg_handle h, int prec) {
+    ddg_handle in = h->inner;
+    int64_t before = 0, after = 0;
+    for (int c = 0; c < DDG_K_COUNT; ++c) before += in->prof_launches[c];
+    in->stream = h->stream;
+    if (prec == DDG_PREC_FP64) {
+        in->rin64 = h->c64;
+        DDG_CUDA(cudaMemsetAsync(in->z64, 0, in->n * sizeof(double), h->stream));
+    } else {
+        DDG_CUDA(cudaMemsetAsync(in->z32, 0, in->n * sizeof(float), h->stream));
+    }
+    sweeps_and_coarse(in, prec);
+    for (int c = 0; c < DDG_K_COUNT; ++c) after += in->prof_launches[c];
+    return after - before;
 }
 
 void apply_prec(ddg_handle h, const double* rin) {
@@ -219,12 +253,7 @@ void apply_prec(ddg_handle h, const double* rin) {
         ddg::convert_to_float(h, rin, h->r32);
         DDG_CUDA(cudaMemsetAsync(h->z32, 0, h->n * sizeof(float), h->stream));
     }
-    // pre-smoother: one multiplicative pass in sweep order
-    for (int c = 0; c < h->ncol; ++c) local_step(h, c, c == 0, prec);
-    // coarse correction of the current residual
-    if (h->use_coarse) coarse_step(h, prec, true);
-    // post-smoother: the same pass in reverse order
-    for (int c = h->ncol - 1; c >= 0; --c) local_step(h, c, false, prec);
+    sweeps_and_coarse(h, prec);
 }
 
 // The preconditioner of the PCG loop always reads h->r, so its launch
@@ -587,8 +616,17 @@ void ddg_default_options(ddg_options* o) {
     o->chunk_tiles = 0;
 }
 
-ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double* F, int k,
-                     int overlap, const ddg_options* opt, void* stream, ddg_handle* out) {
+}  // extern "C"
+
+namespace {
+void setup_vcycle(ddg_handle h, const double* F, int k, int overlap, const ddg_options& o,
+                  const int32_t* groups, const std::vector<int>& bI, const std::vector<int>& bJ,
+                  const std::vector<int64_t>& sub_off, const std::vector<int32_t>& sub_nodes);
+}  // namespace
+
+static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, const int32_t* groups,
+                             const double* F, int k, int overlap, const ddg_options* opt, void* stream,
+                             ddg_handle* out) {
     g_setup_error.clear();
     if (!out) {
         g_setup_error = "out must be non-null";
@@ -602,6 +640,12 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
         if (opt) o = *opt;
         else ddg_default_options(&o);
         validate(A, partition, F, k, overlap, o);
+        if (groups) {
+            int nsub_ids = 0;
+            for (int64_t g = 0; g < A->n; ++g) nsub_ids = std::max(nsub_ids, partition[g] + 1);
+            for (int s = 0; s < nsub_ids; ++s)
+                DDG_REQUIRE(groups[s] >= 0, DDG_EINVAL, "coarse_partition ids must be >= 0");
+        }
         h->opt = o;
         h->precision = o.precision;
         if (const char* ev = std::getenv("DDG_NO_GRAPHS")) h->use_graphs = ev[0] == '0';
@@ -923,29 +967,33 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
                 }
             }
             h->band = (int)band;
-            h->Wt = std::max(1, (int)((band + DDG_CT - 1) / DDG_CT));
-            const int NT0 = (h->n0 + DDG_CT - 1) / DDG_CT;
-            h->nK = (NT0 + h->Wt - 1) / h->Wt;
-            h->NT = h->nK * h->Wt;
-            h->n0p = h->NT * DDG_CT;
-            h->B = h->Wt * DDG_CT;
-            h->bandL = h->arena.alloc<double>((size_t)h->NT * (h->Wt + 1) * DDG_CT * DDG_CT);
-            ddg::coarse_assemble_band(h, bI, bJ);
-            ddg::coarse_band_cholesky(h);
-            ddg::coarse_build_apply(h);
+            if (groups) {
+                setup_vcycle(h, F, k, overlap, o, groups, bI, bJ, sub_off, sub_nodes);
+            } else {
+                h->Wt = std::max(1, (int)((band + DDG_CT - 1) / DDG_CT));
+                const int NT0 = (h->n0 + DDG_CT - 1) / DDG_CT;
+                h->nK = (NT0 + h->Wt - 1) / h->Wt;
+                h->NT = h->nK * h->Wt;
+                h->n0p = h->NT * DDG_CT;
+                h->B = h->Wt * DDG_CT;
+                h->bandL = h->arena.alloc<double>((size_t)h->NT * (h->Wt + 1) * DDG_CT * DDG_CT);
+                ddg::coarse_assemble_band(h, bI, bJ);
+                ddg::coarse_band_cholesky(h);
+                ddg::coarse_build_apply(h);
+                const int n0p = h->n0p;
+                h->c64 = h->arena.alloc<double>(n0p);
+                h->y64 = h->arena.alloc<double>(n0p);
+                h->x64 = h->arena.alloc<double>(n0p);
+                h->c32 = h->arena.alloc<float>(n0p);
+                h->y32 = h->arena.alloc<float>(n0p);
+                h->x32 = h->arena.alloc<float>(n0p);
+                for (void* p : {(void*)h->c64, (void*)h->y64, (void*)h->x64})
+                    DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(double), h->stream));
+                for (void* p : {(void*)h->c32, (void*)h->y32, (void*)h->x32})
+                    DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(float), h->stream));
+            }
             h->Q32 = h->arena.alloc<float>((size_t)n * k);
             ddg::cast_q32(h);
-            const int n0p = h->n0p;
-            h->c64 = h->arena.alloc<double>(n0p);
-            h->y64 = h->arena.alloc<double>(n0p);
-            h->x64 = h->arena.alloc<double>(n0p);
-            h->c32 = h->arena.alloc<float>(n0p);
-            h->y32 = h->arena.alloc<float>(n0p);
-            h->x32 = h->arena.alloc<float>(n0p);
-            for (void* p : {(void*)h->c64, (void*)h->y64, (void*)h->x64})
-                DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(double), h->stream));
-            for (void* p : {(void*)h->c32, (void*)h->y32, (void*)h->x32})
-                DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(float), h->stream));
         }
 
         // ---- CG workspace
@@ -984,6 +1032,134 @@ ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double
     }
 }
 
+namespace {
+// Sec. 6, three-level V-cycle: the two-level method applied again to A0, with
+// the coarsened generators F0 = R0 F, on coarse-level subdomains that group
+// the fine ones (coarse dof (I, s) belongs to group groups[I]; groups without
+// coarse dofs are dropped and the rest numbered in ascending id order).  The
+// coarse level's overlap is the same Delta, grown in the graph of A0.
+void setup_vcycle(ddg_handle h, const double* F, int k, int overlap, const ddg_options& o,
+                  const int32_t* groups, const std::vector<int>& bI, const std::vector<int>& bJ,
+                  const std::vector<int64_t>& sub_off, const std::vector<int32_t>& sub_nodes) {
+    const int nsub = h->nsub, kmax = h->kmax, n0 = h->n0;
+    const int64_t n = h->n;
+    const std::vector<int>& coff = h->h_coff;
+
+    // A0 in CSR, both triangles, columns ascending (diagonal blocks taken
+    // from their lower triangle, so that the matrix is exactly symmetric)
+    std::vector<double> blk;
+    ddg::coarse_assemble_blocks(h, bI, bJ, blk);
+    struct Nb {
+        int J;
+        size_t p;
+        bool tr;
+    };
+    std::vector<std::vector<Nb>> nb(nsub);
+    for (size_t p = 0; p < bI.size(); ++p) {
+        nb[bI[p]].push_back({bJ[p], p, false});
+        if (bI[p] != bJ[p]) nb[bJ[p]].push_back({bI[p], p, true});
+    }
+    for (auto& v : nb) std::sort(v.begin(), v.end(), [](const Nb& a, const Nb& b) { return a.J < b.J; });
+    const size_t per = (size_t)kmax * kmax;
+    std::vector<int64_t> rp(n0 + 1, 0);
+    std::vector<int32_t> cols;
+    std::vector<double> vals;
+    for (int I = 0; I < nsub; ++I)
+        for (int s = 0; s < coff[I + 1] - coff[I]; ++s) {
+            for (const Nb& e : nb[I]) {
+                const double* B = blk.data() + e.p * per;
+                for (int t = 0; t < coff[e.J + 1] - coff[e.J]; ++t) {
+                    double v;
+                    if (e.J == I) v = B[(size_t)std::max(s, t) * kmax + std::min(s, t)];
+                    else if (e.tr) v = B[(size_t)t * kmax + s];
+                    else v = B[(size_t)s * kmax + t];
+                    cols.push_back(coff[e.J] + t);
+                    vals.push_back(v);
+                }
+            }
+            rp[coff[I] + s + 1] = (int64_t)cols.size();
+        }
+    blk.clear();
+    blk.shrink_to_fit();
+
+    // F0 = R0 F: row (I, s) is q_{I,s}^T F on the non-overlapping subdomain I
+    std::vector<double> Q((size_t)n * kmax);
+    d2h(Q.data(), h->Q64, Q.size(), h->stream);
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<double> F0((size_t)n0 * k, 0.0);
+    for (int I = 0; I < nsub; ++I) {
+        const int kI = coff[I + 1] - coff[I];
+        for (int64_t a = sub_off[I]; a < sub_off[I + 1]; ++a) {
+            const int64_t g = sub_nodes[a];
+            for (int s = 0; s < kI; ++s) {
+                const double q = Q[(size_t)a * kmax + s];
+                double* row = F0.data() + coff[I] + s;
+                for (int j = 0; j < k; ++j) row[(size_t)j * n0] += q * F[(size_t)j * n + g];
+            }
+        }
+    }
+    Q.clear();
+    Q.shrink_to_fit();
+
+    // coarse dof -> coarse-level subdomain, ids compacted in ascending order
+    std::vector<int32_t> ids;
+    for (int I = 0; I < nsub; ++I)
+        if (coff[I + 1] > coff[I]) ids.push_back(groups[I]);
+    std::sort(ids.begin(), ids.end());
+    ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    std::vector<int32_t> part0(n0);
+    for (int I = 0; I < nsub; ++I) {
+        const int32_t gid = (int32_t)(std::lower_bound(ids.begin(), ids.end(), groups[I]) - ids.begin());
+        for (int s = coff[I]; s < coff[I + 1]; ++s) part0[s] = gid;
+    }
+
+    ddg_matrix A0{};
+    A0.n = n0;
+    A0.rowptr = rp.data();
+    A0.col = cols.data();
+    A0.val = vals.data();
+    A0.dofs_per_node = 1;
+    A0.stencil_kind = DDG_STENCIL_NONE;
+    ddg_options oi = o;
+    oi.overlap_mode = DDG_OVERLAP_GRAPH;
+    oi.tensor_cores = 0;
+    oi.keep_precisions = h->opt.keep_precisions;
+    ddg_handle in = nullptr;
+    const ddg_status st = setup_impl(&A0, part0.data(), nullptr, F0.data(), k, overlap, &oi, h->stream, &in);
+    if (st != DDG_OK) throw DdgError{st, "coarse level of the V-cycle: " + g_setup_error};
+    h->inner = in;
+    in->use_graphs = false;
+    h->n0p = n0;
+    h->nK = 0;
+    h->c64 = h->arena.alloc<double>(n0);
+    DDG_CUDA(cudaMemsetAsync(h->c64, 0, (size_t)n0 * sizeof(double), h->stream));
+    h->x64 = in->z64;
+    h->c32 = in->r32;
+    h->x32 = in->z32;
+}
+}  // namespace
+
+extern "C" {
+
+ddg_status ddg_setup(const ddg_matrix* A, const int32_t* partition, const double* F, int k,
+                     int overlap, const ddg_options* opt, void* stream, ddg_handle* out) {
+    return setup_impl(A, partition, nullptr, F, k, overlap, opt, stream, out);
+}
+
+ddg_status ddg_setup_vcycle(const ddg_matrix* A, const int32_t* partition, const int32_t* coarse_partition,
+                            const double* F, int k, int overlap, const ddg_options* opt, void* stream,
+                            ddg_handle* out) {
+    ddg_options o;
+    if (opt) o = *opt;
+    else ddg_default_options(&o);
+    if (!coarse_partition || !o.use_coarse) {
+        g_setup_error = "the V-cycle needs coarse_partition and use_coarse = 1";
+        if (out) *out = nullptr;
+        return DDG_EINVAL;
+    }
+    return setup_impl(A, partition, coarse_partition, F, k, overlap, &o, stream, out);
+}
+
 ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters, double* relres) {
     return guarded(h, [&]() {
         DDG_REQUIRE(f && u, DDG_EINVAL, "f and u must be non-null device pointers");
@@ -1011,8 +1187,8 @@ ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, doub
         DDG_REQUIRE(F && U && m >= 1, DDG_EINVAL, "F, U must be non-null and m >= 1");
         DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
         ddg_status worst = DDG_OK;
-        if (h->precision == DDG_PREC_FP64) {
-            // the FP64 preconditioner runs one column at a time
+        if (h->precision == DDG_PREC_FP64 || h->inner) {
+            // the FP64 and the V-cycle preconditioners run one column at a time
             for (int j = 0; j < m; ++j) {
                 ddg::strided_gather(h, F, m, j, h->fbuf);
                 int it = 0;
@@ -1145,6 +1321,7 @@ ddg_status ddg_set_precision(ddg_handle h, int precision) {
 ddg_status ddg_set_stream(ddg_handle h, void* stream) {
     return guarded(h, [&]() {
         h->stream = (cudaStream_t)stream;
+        if (h->inner) h->inner->stream = h->stream;
         return DDG_OK;
     });
 }
@@ -1223,6 +1400,7 @@ ddg_status ddg_get_kernel_stats(ddg_handle h, ddg_kernel_stat* st) {
 ddg_status ddg_destroy(ddg_handle h) {
     if (!h) return DDG_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->inner) ddg_destroy(h->inner);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (cudaGraphExec_t g : h->apply_exec)
         if (g) cudaGraphExecDestroy(g);

@@ -257,6 +257,10 @@ struct ddg_handle_s {
     ProfileMat Dm, Dt, Fm, Gm;
     double *c64 = nullptr, *y64 = nullptr, *x64 = nullptr;
     float *c32 = nullptr, *y32 = nullptr, *x32 = nullptr;
+    // three-level V-cycle (Sec. 6): the two-level preconditioner of A0 that
+    // replaces A0^{-1}.  Its input r32 and outputs z32, z64 are this handle's
+    // c32, x32 and x64 (owned by the inner handle); it reads c64 in place.
+    ddg_handle_s* inner = nullptr;
 
     // ---- CG workspace (FP64) and preconditioner vectors
     const double* rin64 = nullptr;  // input of the FP64 preconditioner apply
@@ -317,6 +321,9 @@ void local_solve_colour(ddg_handle h, int colour, int prec);
 // k_coarse.cu
 void coarse_qr(ddg_handle h, int32_t* d_rank, const double* dF, int k);
 void coarse_assemble_band(ddg_handle h, const std::vector<int>& blk_I, const std::vector<int>& blk_J);
+// the kmax x kmax blocks A0[(I,.),(J,.)] of the listed pairs, copied to the host
+void coarse_assemble_blocks(ddg_handle h, const std::vector<int>& blk_I, const std::vector<int>& blk_J,
+                            std::vector<double>& blocks);
 void coarse_band_cholesky(ddg_handle h);
 void coarse_build_apply(ddg_handle h);
 void coarse_restrict(ddg_handle h, int prec, bool residual);

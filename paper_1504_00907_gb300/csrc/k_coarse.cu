@@ -139,7 +139,9 @@ __device__ __forceinline__ size_t band_index(int row, int col, int Wt) {
 }
 
 // One CTA per block (I, J), I >= J: A0[(I,s),(J,t)] = sum_{g in Omega_I}
-// Q[g,s] sum_{c in row g, part(c) = J} A[g,c] Q[c,t]
+// Q[g,s] sum_{c in row g, part(c) = J} A[g,c] Q[c,t].  With blk set, the
+// whole kI x kJ block goes to blk[blockIdx.x][s][t] (row stride kmax)
+// instead of the band's lower triangle.
 __global__ void coarse_assemble_kernel(const int32_t* __restrict__ bI, const int32_t* __restrict__ bJ,
                                        const int64_t* __restrict__ sub_off,
                                        const int32_t* __restrict__ sub_nodes,
@@ -149,13 +151,14 @@ __global__ void coarse_assemble_kernel(const int32_t* __restrict__ bI, const int
                                        const int32_t* __restrict__ col,
                                        const double* __restrict__ val,
                                        const double* __restrict__ Q, int kmax,
-                                       const int32_t* __restrict__ coff, double* band, int Wt) {
+                                       const int32_t* __restrict__ coff, double* band, int Wt,
+                                       double* blk) {
     const int I = bI[blockIdx.x], J = bJ[blockIdx.x];
     const int kI = coff[I + 1] - coff[I], kJ = coff[J + 1] - coff[J];
     for (int pr = threadIdx.x; pr < kI * kJ; pr += blockDim.x) {
         const int s = pr / kJ, t = pr % kJ;
         const int row = coff[I] + s, cl = coff[J] + t;
-        if (row < cl) continue;
+        if (!blk && row < cl) continue;
         double acc = 0.0;
         for (int64_t a = sub_off[I]; a < sub_off[I + 1]; ++a) {
             const int g = sub_nodes[a];
@@ -166,7 +169,8 @@ __global__ void coarse_assemble_kernel(const int32_t* __restrict__ bI, const int
             }
             acc = fma(Q[a * kmax + s], inner, acc);
         }
-        band[band_index(row, cl, Wt)] = acc;
+        if (blk) blk[((size_t)blockIdx.x * kmax + s) * kmax + t] = acc;
+        else band[band_index(row, cl, Wt)] = acc;
     }
 }
 
@@ -616,7 +620,7 @@ void coarse_assemble_band(ddg_handle h, const std::vector<int>& bI, const std::v
         h2d(dJ, bJ.data(), bJ.size(), h->stream);
         coarse_assemble_kernel<<<(unsigned)bI.size(), 128, 0, h->stream>>>(
             dI, dJ, h->sub_off, h->sub_nodes, h->pos, h->part, h->rowptr, h->col, h->val64, h->Q64,
-            h->kmax, h->coff, h->bandL, h->Wt);
+            h->kmax, h->coff, h->bandL, h->Wt, nullptr);
         DDG_CHECK_LAUNCH();
         DDG_CUDA(cudaStreamSynchronize(h->stream));
         h->arena.release(dI);
@@ -628,6 +632,28 @@ void coarse_assemble_band(ddg_handle h, const std::vector<int>& bI, const std::v
                                                                             h->n0p);
         DDG_CHECK_LAUNCH();
     }
+}
+
+void coarse_assemble_blocks(ddg_handle h, const std::vector<int>& bI, const std::vector<int>& bJ,
+                            std::vector<double>& blocks) {
+    const size_t per = (size_t)h->kmax * h->kmax;
+    blocks.assign(bI.size() * per, 0.0);
+    if (bI.empty()) return;
+    int32_t* dI = h->arena.alloc<int32_t>(bI.size());
+    int32_t* dJ = h->arena.alloc<int32_t>(bJ.size());
+    double* dB = h->arena.alloc<double>(bI.size() * per);
+    DDG_CUDA(cudaMemsetAsync(dB, 0, bI.size() * per * sizeof(double), h->stream));
+    h2d(dI, bI.data(), bI.size(), h->stream);
+    h2d(dJ, bJ.data(), bJ.size(), h->stream);
+    coarse_assemble_kernel<<<(unsigned)bI.size(), 128, 0, h->stream>>>(
+        dI, dJ, h->sub_off, h->sub_nodes, h->pos, h->part, h->rowptr, h->col, h->val64, h->Q64, h->kmax,
+        h->coff, nullptr, 0, dB);
+    DDG_CHECK_LAUNCH();
+    d2h(blocks.data(), dB, blocks.size(), h->stream);
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    h->arena.release(dI);
+    h->arena.release(dJ);
+    h->arena.release(dB);
 }
 
 void coarse_band_cholesky(ddg_handle h) {

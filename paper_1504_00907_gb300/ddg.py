@@ -69,6 +69,8 @@ _PD = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "ddg_default_options": (None, [ctypes.POINTER(Options)]),
     "ddg_setup": (_I, [ctypes.POINTER(Matrix), _P, _P, _I, _I, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)]),
+    "ddg_setup_vcycle": (_I, [ctypes.POINTER(Matrix), _P, _P, _P, _I, _I, ctypes.POINTER(Options), _P,
+                              ctypes.POINTER(_P)]),
     "ddg_solve": (_I, [_P, _P, _P, _D, _PI, _PD]),
     "ddg_solve_host": (_I, [_P, _P, _P, _D, _PI, _PD]),
     "ddg_solve_batch": (_I, [_P, _P, _P, _I, _D, _P, _P]),
@@ -159,7 +161,7 @@ class Solver:
     def __init__(self, A, part, F, overlap, *, mode="graph", shape=None, stencil_kind=0,
                  coef=None, dofs_per_node=1, precision="fp64", keep=None, beta="auto",
                  maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
-                 stream=None):
+                 stream=None, coarse_groups=None):
         import torch
         lib = load()
         if not torch.cuda.is_available():
@@ -202,8 +204,15 @@ class Solver:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
         h = ctypes.c_void_p()
-        st = lib.ddg_setup(ctypes.byref(m), p_part, p_F, k, overlap, ctypes.byref(o),
-                           ctypes.c_void_p(stream), ctypes.byref(h))
+        if coarse_groups is None:
+            st = lib.ddg_setup(ctypes.byref(m), p_part, p_F, k, overlap, ctypes.byref(o),
+                               ctypes.c_void_p(stream), ctypes.byref(h))
+        else:
+            # three-level V-cycle: coarse_groups maps each subdomain to its
+            # coarse-level subdomain
+            groups, p_groups = _host(coarse_groups, np.int32)
+            st = lib.ddg_setup_vcycle(ctypes.byref(m), p_part, p_groups, p_F, k, overlap,
+                                      ctypes.byref(o), ctypes.c_void_p(stream), ctypes.byref(h))
         _check(st, None)
         self.h = h
         self.precision = precision

@@ -97,6 +97,31 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib, case):
     assert len(lib.ddg_last_error(None)) > 0
 
 
+@pytest.mark.parametrize("case", ["no_groups", "one_level", "neg_group"])
+def test_vcycle_setup_rejects_bad_arguments_before_touching_the_gpu(lib, case):
+    from paper_1504_00907_gb300 import ddg
+    import ddg_inputs as di
+    A = di.poisson5_2d(4)
+    rowptr, col, val = di.csr_arrays(A)
+    part = np.repeat(np.arange(4, dtype=np.int32), 4)
+    groups = np.array([0, 0, 1, 1], dtype=np.int32)
+    F = np.ones(16)
+    o = ddg.default_options()
+    if case == "one_level":
+        o.use_coarse = 0
+    if case == "neg_group":
+        groups[2] = -1
+    p_groups = None if case == "no_groups" else groups.ctypes.data_as(ctypes.c_void_p)
+    m = _matrix(rowptr, col, val)
+    h = ctypes.c_void_p()
+    st = lib.ddg_setup_vcycle(ctypes.byref(m), part.ctypes.data_as(ctypes.c_void_p), p_groups,
+                              F.ctypes.data_as(ctypes.c_void_p), 1, 1, ctypes.byref(o), None,
+                              ctypes.byref(h))
+    assert st == ddg.DDG_EINVAL
+    assert h.value is None
+    assert len(lib.ddg_last_error(None)) > 0
+
+
 def test_product_path_has_no_cpu_fallback():
     # the binding never imports the oracle and refuses to run without a GPU
     src = open(os.path.join(ROOT, "paper_1504_00907_gb300", "ddg.py")).read()

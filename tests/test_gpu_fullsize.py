@@ -16,6 +16,8 @@ property that holds at any size, evaluated independently of the CUDA path
 * Q1 elasticity on 64^3 elements: forward and adjoint solves reach 1e-8
   (scipy residuals); sampled entries of dL/dmu equal -lambda_e^T K^mu u_e
   recomputed on the CPU from the element matrices.
+* the three-level V-cycle on Poisson 128^3 (4^3 subdomains per
+  coarse-level subdomain) reaches 1e-8 (scipy residual).
 """
 import numpy as np
 import pytest
@@ -139,3 +141,17 @@ def test_elasticity64_forward_adjoint_and_sampled_gradient():
                 ue[3 * a:3 * a + 3] = uc[base:base + 3]
         ref = -le @ Km @ ue
         assert abs(dmu[e] - ref) <= 1e-10 * max(abs(ref), 1e-300) + 1e-14 * np.abs(dmu).max(), e
+
+
+def test_poisson128_vcycle_reaches_true_residual():
+    # three-level V-cycle with 4^3 subdomains per coarse-level subdomain
+    # (64 of them, about 1600 coarse dofs each with their overlap)
+    from paper_1504_00907_gb300 import ddg
+    prob = di.make_poisson3d(N=128, box=8, overlap=1, p=2, seed=1)
+    groups = di.subdomain_groups(prob.shape, prob.box, 4)
+    s = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32",), coarse_groups=groups)
+    u, it, rr, st = s.solve(dev(prob.f), tol=1e-8)
+    s.close()
+    assert st == ddg.DDG_OK and it <= 12
+    r = true_rel(prob.A, u.cpu().numpy(), prob.f)
+    assert r <= 1e-8 and abs(r - rr) <= 1e-3 * r
