@@ -343,6 +343,7 @@ def vcycle_arm(args, prob, two_level, ddg, di, torch, dev, stream, barrier, max_
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
     launches = sum(v["launches"] for v in s3.kernel_stats().values()) / args.steps
+    lmin, lmax, ibound = s3.condition_estimate(TOL)
     s3.profile(ddg.KERNEL_CLASSES)
     s3.solve(f, TOL, u)
     torch.cuda.synchronize()
@@ -360,6 +361,8 @@ def vcycle_arm(args, prob, two_level, ddg, di, torch, dev, stream, barrier, max_
             "status": max(sts), "iters": iters[-1], "true_relres": rels[-1], "ms": ms,
             "dof_iters_per_s": world * prob.n * iters[-1] / (ms / 1e3),
             "two_level": {"ms": two_level[0], "iters": two_level[1]},
+            "condition_estimate": {"lambda_min": lmin, "lambda_max": lmax, "kappa": lmax / lmin,
+                                   "cg_iteration_bound_1e-8": ibound},
             "gpu_launches_per_step": launches,
             "breakdown_one_solve": breakdown}
 
@@ -584,6 +587,14 @@ def main():
         ms16, it16, rr16, _, _ = timed_solves("bf16", args.steps, 1)
         ms16 = max_over_ranks(ms16)
 
+    # Sec. 7: condition estimate of M^{-1}A from the Lanczos tridiagonal of
+    # the last mixed solve, and the CG iteration bound it implies
+    solver.set_precision("fp32")
+    solver.solve(f, TOL, u)
+    lmin, lmax, ibound = solver.condition_estimate(TOL)
+    cond = {"lambda_min": lmin, "lambda_max": lmax, "kappa": lmax / lmin,
+            "cg_iteration_bound_1e-8": ibound, "source": "Lanczos tridiagonal of the last mixed solve"}
+
     # per-class breakdown of one extra mixed solve with every class event-timed
     solver.set_precision("fp32")
     solver.profile(ddg.KERNEL_CLASSES)
@@ -676,6 +687,7 @@ def main():
                 "host_memory": "page-locked"},
         "roofline": roofline,
         "breakdown_one_mixed_solve": breakdown,
+        "condition_estimate": cond,
         "batched": batched,
         "uneven_batch": uneven,
         "elasticity_differentiation": elasticity,

@@ -235,6 +235,25 @@ ddg_status ddg_get_coarse_offsets(ddg_handle h, int32_t* offsets);
  * last single-RHS solve, k = 0..iters; returns the count in *len. */
 ddg_status ddg_get_history(ddg_handle h, double* hist, int max_len, int* len);
 
+/* Sec. 7: the CG coefficients of the last single-vector solve on h
+ * (ddg_solve, ddg_solve_host, ddg_adjoint), from the last restart on:
+ * alpha_j for j < *len and beta_j for j < *len - 1 (beta_j forms
+ * p_{j+1} = z_{j+1} + beta_j p_j).  Host arrays of max_len entries; *len
+ * receives the number of alphas (both arrays may be NULL to query it). */
+ddg_status ddg_get_cg_coefficients(ddg_handle h, double* alpha, double* beta, int max_len, int* len);
+
+/* Sec. 7: condition estimate from m >= 1 CG steps (host only, no handle, no
+ * GPU).  The Lanczos tridiagonal of CG has diagonal 1/alpha_0 and
+ * 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal sqrt(beta_j)/alpha_j; its
+ * extreme eigenvalues (bisection on Sturm counts, to a relative 1e-14)
+ * estimate those of M^{-1} A.  iter_bound (may be NULL) receives the CG
+ * bound ln(2/tol) / ln((sqrt(k)+1)/(sqrt(k)-1)) for k = lambda_max/lambda_min
+ * (0 when k <= 1), the iterations that reduce the A-norm error by tol.
+ * Errors: DDG_EINVAL for m < 1, NULL arrays or outputs, tol outside (0, 1),
+ * or a non-positive alpha or negative beta. */
+ddg_status ddg_condition_estimate(const double* alpha, const double* beta, int m, double tol,
+                                  double* lambda_min, double* lambda_max, double* iter_bound);
+
 /* ---- tracing: per kernel class, launches are always counted; CUDA-event
  * timing of each launch (on the handle's stream) is on for the classes in
  * the mask given to ddg_profile.  bytes are the algorithmic bytes of the

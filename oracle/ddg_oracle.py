@@ -413,6 +413,16 @@ def lanczos_extremes(alphas, betas):
     return float(w[0]), float(w[-1])
 
 
+def cg_iteration_bound(kappa, tol):
+    """Sec. 7: iterations that CG needs for a tol reduction of the A-norm
+    error given the condition number kappa (the Chebyshev bound
+    2 ((sqrt k - 1)/(sqrt k + 1))^j <= tol solved for j)."""
+    if kappa <= 1.0:
+        return 0.0
+    sk = np.sqrt(kappa)
+    return float(np.log(2.0 / tol) / np.log((sk + 1.0) / (sk - 1.0)))
+
+
 def solve(A, part, F, f, overlap, mode="graph", shape=None, tol=1e-8, maxit=1000, beta="FR"):
     """Setup plus PCG in one call; returns (PCGResult, DDGOracle)."""
     M = DDGOracle(A, part, F, overlap, mode, shape)

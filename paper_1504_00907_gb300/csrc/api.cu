@@ -313,6 +313,8 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
                                                   : h->opt.beta;
     const int pr = beta == DDG_BETA_PR;
     h->history.clear();
+    h->cg_alpha.clear();
+    h->cg_beta.clear();
     {
         ProfScope ps(h, DDG_K_CG, 1, 0.0);
         ddg::dot64(h, f, f, S_TMP);
@@ -335,6 +337,8 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
     }
     DDG_CUDA(cudaMemcpyAsync(h->r, f, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     auto restart = [&]() {
+        h->cg_alpha.clear();
+        h->cg_beta.clear();
         apply_in_pcg(h);
         ProfScope ps(h, DDG_K_CG, 2, 0.0);
         ddg::cg_dots_after_precond(h, prec, true, pr);
@@ -359,6 +363,10 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
             st = DDG_EBREAKDOWN;
             break;
         }
+        // Sec. 7: the coefficients of the Lanczos tridiagonal; the beta read
+        // here formed the current p
+        if (!h->cg_alpha.empty()) h->cg_beta.push_back(h->h_scal[S_BETA]);
+        h->cg_alpha.push_back(h->h_scal[S_ALPHA]);
         const double rel = std::sqrt(h->h_scal[S_RR]) / fn;
         h->history.push_back(rel);
         if (rel <= tol) {
@@ -1369,6 +1377,78 @@ ddg_status ddg_get_history(ddg_handle h, double* hist, int max_len, int* len) {
             for (int i = 0; i < std::min(cnt, max_len); ++i) hist[i] = h->history[i];
         return DDG_OK;
     });
+}
+
+ddg_status ddg_get_cg_coefficients(ddg_handle h, double* alpha, double* beta, int max_len, int* len) {
+    return guarded(h, [&]() {
+        const int cnt = (int)h->cg_alpha.size();
+        if (len) *len = cnt;
+        for (int i = 0; i < std::min(cnt, max_len); ++i) {
+            if (alpha) alpha[i] = h->cg_alpha[i];
+            if (beta && i + 1 < cnt) beta[i] = h->cg_beta[i];
+        }
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_condition_estimate(const double* alpha, const double* beta, int m, double tol,
+                                  double* lambda_min, double* lambda_max, double* iter_bound) {
+    if (!alpha || (m > 1 && !beta) || m < 1 || !lambda_min || !lambda_max || !(tol > 0.0 && tol < 1.0)) {
+        ddg::set_handleless_error("alpha, beta, lambda_min, lambda_max must be non-null, m >= 1, 0 < tol < 1");
+        return DDG_EINVAL;
+    }
+    for (int j = 0; j < m; ++j)
+        if (!(alpha[j] > 0.0) || (j + 1 < m && !(beta[j] >= 0.0))) {
+            ddg::set_handleless_error("alpha must be > 0 and beta >= 0");
+            return DDG_EINVAL;
+        }
+    // T = tridiag(e, d, e): d_0 = 1/alpha_0, d_j = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+    // e_j = sqrt(beta_j)/alpha_j
+    std::vector<double> d(m), e2(m > 1 ? m - 1 : 1, 0.0);
+    for (int j = 0; j < m; ++j) d[j] = 1.0 / alpha[j] + (j > 0 ? beta[j - 1] / alpha[j - 1] : 0.0);
+    for (int j = 0; j + 1 < m; ++j) e2[j] = beta[j] / (alpha[j] * alpha[j]);
+    // Gershgorin interval
+    double lo = d[0], hi = d[0];
+    for (int j = 0; j < m; ++j) {
+        const double r = (j > 0 ? std::sqrt(e2[j - 1]) : 0.0) + (j + 1 < m ? std::sqrt(e2[j]) : 0.0);
+        lo = std::min(lo, d[j] - r);
+        hi = std::max(hi, d[j] + r);
+    }
+    // Sturm count: the number of eigenvalues of T below x (LDL^T pivots)
+    auto below = [&](double x) {
+        int cnt = 0;
+        double q = d[0] - x;
+        const double tiny = 1e-300;
+        for (int j = 0;; ++j) {
+            if (q == 0.0) q = -tiny;
+            if (q < 0.0) ++cnt;
+            if (j + 1 == m) break;
+            q = d[j + 1] - x - e2[j] / q;
+        }
+        return cnt;
+    };
+    // the k-th smallest eigenvalue (k = 1..m) by bisection
+    auto kth = [&](int k) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 400 && b - a > 1e-14 * std::max(std::fabs(a), std::fabs(b)); ++it) {
+            const double mid = 0.5 * (a + b);
+            if (below(mid) >= k) b = mid;
+            else a = mid;
+        }
+        return 0.5 * (a + b);
+    };
+    *lambda_min = kth(1);
+    *lambda_max = kth(m);
+    if (iter_bound) {
+        const double kappa = *lambda_max / *lambda_min;
+        if (!(kappa > 1.0)) {
+            *iter_bound = 0.0;
+        } else {
+            const double sk = std::sqrt(kappa);
+            *iter_bound = std::log(2.0 / tol) / std::log((sk + 1.0) / (sk - 1.0));
+        }
+    }
+    return DDG_OK;
 }
 
 ddg_status ddg_profile(ddg_handle h, int timed_mask) {

@@ -274,6 +274,7 @@ struct ddg_handle_s {
     unsigned* red_counter = nullptr;
     int32_t* errflags = nullptr;
     std::vector<double> history;
+    std::vector<double> cg_alpha, cg_beta;   // CG coefficients since the last restart
 
     MultiWork mw;
     TcData tc;

@@ -86,6 +86,8 @@ _SIGS = {
     "ddg_get_colouring": (_I, [_P, _P]),
     "ddg_get_coarse_offsets": (_I, [_P, _P]),
     "ddg_get_history": (_I, [_P, _P, _I, _PI]),
+    "ddg_get_cg_coefficients": (_I, [_P, _P, _P, _I, _PI]),
+    "ddg_condition_estimate": (_I, [_P, _P, _I, _D, _PD, _PD, _PD]),
     "ddg_profile": (_I, [_P, _I]),
     "ddg_get_kernel_stats": (_I, [_P, _P]),
     "ddg_spmv_dot_noalloc": (_I, [ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P]),
@@ -153,6 +155,17 @@ def torch_empty_like_host(t):
 def _host(a, dtype):
     a = np.ascontiguousarray(a, dtype=dtype)
     return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def condition_estimate(alpha, beta, tol=1e-8):
+    """Sec. 7: (lambda_min, lambda_max, iteration bound) from CG coefficients
+    (``ddg_condition_estimate``; host only, needs no GPU)."""
+    a, pa = _host(alpha, np.float64)
+    b, pb = _host(beta if len(beta) else np.zeros(1), np.float64)
+    lo, hi, it = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().ddg_condition_estimate(pa, pb, int(a.size), tol, ctypes.byref(lo), ctypes.byref(hi),
+                                         ctypes.byref(it)), None)
+    return lo.value, hi.value, it.value
 
 
 class Solver:
@@ -344,6 +357,23 @@ class Solver:
         buf = np.zeros(max(1, ln.value))
         load().ddg_get_history(self.h, buf.ctypes.data_as(ctypes.c_void_p), ln.value, ctypes.byref(ln))
         return buf[:ln.value]
+
+    def cg_coefficients(self):
+        """(alpha, beta) of the last single-vector solve (Sec. 7)."""
+        ln = ctypes.c_int(0)
+        _check(load().ddg_get_cg_coefficients(self.h, None, None, 0, ctypes.byref(ln)), self.h)
+        a = np.zeros(max(1, ln.value))
+        b = np.zeros(max(1, ln.value))
+        _check(load().ddg_get_cg_coefficients(self.h, a.ctypes.data_as(ctypes.c_void_p),
+                                              b.ctypes.data_as(ctypes.c_void_p), ln.value,
+                                              ctypes.byref(ln)), self.h)
+        return a[:ln.value], b[:max(0, ln.value - 1)]
+
+    def condition_estimate(self, tol=1e-8):
+        """(lambda_min, lambda_max, CG iteration bound for tol) of M^{-1}A
+        from the last solve's Lanczos tridiagonal (Sec. 7)."""
+        a, b = self.cg_coefficients()
+        return condition_estimate(a, b, tol)
 
     def profile(self, classes=()):
         """Reset the launch counters; time the named kernel classes with events."""

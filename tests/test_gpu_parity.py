@@ -309,3 +309,23 @@ def test_many_chunk_gather_matches_oracle(name):
         assert rel(u.cpu().numpy(), ref.u) <= tol
         assert torch.equal(u, u2)
     s.close()
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_24", "biharmonic_64"])
+def test_cg_coefficients_and_condition_estimate_match_oracle(name):
+    # Sec. 7: the library records alpha_j, beta_j of each solve; the Lanczos
+    # estimates of the extreme eigenvalues of M^{-1}A follow from them
+    prob, solver, oracle = setup_case(name)
+    solver.set_precision("fp64")
+    f = prob.f if prob.f.ndim == 1 else prob.f[:, 0]
+    ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
+    _, iters, _, st = solver.solve(dev(f), tol=1e-8)
+    a, b = solver.cg_coefficients()
+    assert st == 0 and a.size == iters and b.size == iters - 1
+    m = min(a.size, ref.alphas.size)
+    np.testing.assert_allclose(a[:m], ref.alphas[:m], rtol=1e-6)
+    np.testing.assert_allclose(b[:m - 1], ref.betas[:m - 1], rtol=1e-6)
+    lo, hi, bound = solver.condition_estimate(1e-8)
+    lo_o, hi_o = orc.lanczos_extremes(ref.alphas[:m], ref.betas[:m - 1])
+    assert abs(lo - lo_o) <= 1e-5 * hi_o and abs(hi - hi_o) <= 1e-5 * hi_o
+    assert 0 < lo <= hi <= 1.0 + 1e-10 and bound > 0
