@@ -495,3 +495,88 @@ def make_varcoef3d(N=96, box=8, overlap=1, p=2, field_seed=2, rhs_seed=3, m=64,
                    F=monomials(cell_centre_coords(shape), p), f=normal_rhs(A.shape[0], rhs_seed, m),
                    overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_VAR7_3D,
                    face_coef=face, kappa=kappa)
+
+
+def two_material_coefficient(coords):
+    """Sec. 7 problem C's coefficient on cell centres: D = S + 100 J with the
+    smooth S = exp(1 + sin(pi (x + y))) and the material indicator
+    J = H(0.25 + cos(pi x) cos(2 pi y)) (H the Heaviside step); returns (D, J).
+    On the unit cube the fields do not depend on z."""
+    x, y = coords[:, 0], coords[:, 1]
+    S = np.exp(1.0 + np.sin(np.pi * (x + y)))
+    J = (0.25 + np.cos(np.pi * x) * np.cos(2.0 * np.pi * y) > 0.0).astype(np.float64)
+    return S + 100.0 * J, J
+
+
+def material_aware_generators(F, J):
+    """Generators that are piecewise in the materials (Sec. 7, problem C):
+    every column of F once times the indicator of each material, [F(1-J), FJ]."""
+    J = np.asarray(J, dtype=np.float64)[:, None]
+    return np.hstack([F * (1.0 - J), F * J])
+
+
+def varcoef5_2d(kappa):
+    """Cell-centred FD of -div(kappa grad u) on the unit square, scaled by
+    h^2 (the 2D analogue of ``varcoef7_3d``): interior faces take the
+    harmonic mean of the two cells, Dirichlet boundary faces 2 kappa_cell.
+    ``kappa`` has shape (ny, nx), x fastest when raveled."""
+    kap = np.asarray(kappa, dtype=np.float64)
+    ny, nx = kap.shape
+    n = kap.size
+    cx = np.empty((ny, nx + 1))
+    cx[:, 1:-1] = 2.0 * kap[:, :-1] * kap[:, 1:] / (kap[:, :-1] + kap[:, 1:])
+    cx[:, 0], cx[:, -1] = 2.0 * kap[:, 0], 2.0 * kap[:, -1]
+    cy = np.empty((ny + 1, nx))
+    cy[1:-1] = 2.0 * kap[:-1] * kap[1:] / (kap[:-1] + kap[1:])
+    cy[0], cy[-1] = 2.0 * kap[0], 2.0 * kap[-1]
+    idx = np.arange(n, dtype=np.int64).reshape(ny, nx)
+    diag = cx[:, :-1] + cx[:, 1:] + cy[:-1, :] + cy[1:, :]
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [diag.ravel()]
+    for a, b, c in ((idx[:, :-1], idx[:, 1:], cx[:, 1:-1]), (idx[:-1, :], idx[1:, :], cy[1:-1, :])):
+        rows += [a.ravel(), b.ravel()]
+        cols += [b.ravel(), a.ravel()]
+        vals += [-c.ravel(), -c.ravel()]
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    A.sum_duplicates()
+    A.sort_indices()
+    return A
+
+
+def make_twomaterial2d(N=1024, box=16, overlap=0, p=3, material_aware=False, rhs_seed=8, m=None,
+                       mode="graph"):
+    """2D cell-centred -div(D grad u) with the two-material coefficient of
+    Sec. 7 problem C, D = S + 100 J, on an N x N grid (a structured stand-in
+    for the paper's annulus mesh); box partitions that do not follow the
+    material boundary; monomials of degree <= p, or their material-aware
+    split; N(0,1) right-hand side.  General CSR (no matrix-free stencil)."""
+    shape = (N, N)
+    coords = cell_centre_coords(shape)
+    D, J = two_material_coefficient(coords)
+    A = varcoef5_2d(D.reshape(N, N))
+    F = monomials(coords, p)
+    if material_aware:
+        F = material_aware_generators(F, J)
+    return Problem(name=f"twomaterial2d_{N}" + ("_aware" if material_aware else ""), A=A, shape=shape,
+                   part=box_partition(shape, (box, box)), box=(box, box), F=F,
+                   f=normal_rhs(A.shape[0], rhs_seed, m), overlap=overlap, overlap_mode=mode, p=p)
+
+
+def make_twomaterial3d(N=128, box=8, overlap=1, p=2, material_aware=False, rhs_seed=7, m=None,
+                       mode="box"):
+    """3D cell-centred -div(D grad u) with the two-material coefficient
+    D = S + 100 J of Sec. 7 problem C (extruded in z); box partitions that do
+    not follow the material boundary; monomial generators, or their
+    material-aware split (twice the columns); N(0,1) right-hand side."""
+    shape = (N, N, N)
+    coords = cell_centre_coords(shape)
+    D, J = two_material_coefficient(coords)
+    kappa = D.reshape(N, N, N)
+    A, face = varcoef7_3d(kappa)
+    F = monomials(coords, p)
+    if material_aware:
+        F = material_aware_generators(F, J)
+    return Problem(name=f"twomaterial3d_{N}" + ("_aware" if material_aware else ""), A=A, shape=shape,
+                   part=box_partition(shape, (box,) * 3), box=(box,) * 3, F=F,
+                   f=normal_rhs(A.shape[0], rhs_seed, m), overlap=overlap, overlap_mode=mode, p=p,
+                   stencil_kind=STENCIL_VAR7_3D, face_coef=face, kappa=kappa)
