@@ -29,7 +29,21 @@ CASES = {
     "poisson2d_p0_overlap0": lambda: di.make_poisson2d(N=40, box=10, overlap=0, p=0, seed=14),
     "single_subdomain": lambda: di.make_poisson2d(N=20, box=20, overlap=1, p=1, seed=15),
     "elasticity_q1_6": lambda: di.make_elasticity3d(ne=6, box=3, overlap=1, p=2),
+    # material-aware generators [F(1-J), FJ] (k = 20) on the two-material
+    # coefficient: general CSR in 2D without overlap, matrix-free VAR7 in 3D
+    "twomaterial2d_aware_64": lambda: di.make_twomaterial2d(N=64, box=8, overlap=0, p=3,
+                                                           material_aware=True),
+    "twomaterial3d_aware_16": lambda: di.make_twomaterial3d(N=16, box=4, overlap=1, p=2,
+                                                           material_aware=True),
 }
+
+# FP64 building blocks agree to 1e-11 unless a subdomain's generator block
+# is close to rank-deficient: the coarse basis vectors then carry about
+# u / (|R_jj| / |R_00|) of rounding from the two QR methods (pivoted
+# Gram-Schmidt on the GPU, Householder in the oracle).  In the 2D
+# material-aware case a subdomain keeps a column with |R_jj| / |R_00| =
+# 4.6e-7 (a few cells of one material), so u / 4.6e-7 = 2.4e-10.
+FP64_TOL = {"twomaterial2d_aware_64": 2.4e-10}
 
 _cache = {}
 
@@ -73,7 +87,7 @@ def test_coarse_correction_matches_oracle(name):
     solver.set_precision("fp64")
     r = np.random.default_rng(6).standard_normal(prob.n)
     z = solver.coarse_correction(dev(r)).cpu().numpy()
-    assert rel(z, oracle.coarse_correction(r)) <= 1e-11
+    assert rel(z, oracle.coarse_correction(r)) <= FP64_TOL.get(name, 1e-11)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -82,7 +96,7 @@ def test_preconditioner_matches_oracle_fp64(name):
     solver.set_precision("fp64")
     r = np.random.default_rng(7).standard_normal(prob.n)
     z = solver.apply(dev(r)).cpu().numpy()
-    assert rel(z, oracle.apply(r)) <= 1e-11
+    assert rel(z, oracle.apply(r)) <= FP64_TOL.get(name, 1e-11)
 
 
 @pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_24", "biharmonic_64", "varcoef_16"])
@@ -115,7 +129,7 @@ def test_solve_fp64_matches_oracle(name):
 
 
 MIXED = [(n, "fp32") for n in ("poisson2d_64", "poisson3d_24", "poisson3d_ragged", "biharmonic_64",
-                                 "varcoef_16")]
+                                 "varcoef_16", "twomaterial2d_aware_64", "twomaterial3d_aware_16")]
 MIXED += [(n, "bf16") for n in ("poisson2d_64", "poisson3d_24", "poisson3d_ragged", "varcoef_16")]
 
 
