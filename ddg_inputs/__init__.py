@@ -400,6 +400,58 @@ def monomials(coords, p, components=1):
     return F
 
 
+def local_monomials(coords, part, p):
+    """Monomials of degree <= p in coordinates centred and scaled per
+    subdomain: column j on the nodes of subdomain i is m_j((x - c_i) / s_i),
+    with c_i the centre and s_i the half-width of the subdomain's bounding box
+    (per axis; 1 where the box is flat).
+
+    The coarse space uses only each generator's restriction to each
+    subdomain (Sec. 4), and on one subdomain these columns span the same
+    polynomials as the global monomials, so the coarse space is the same; the
+    per-subdomain blocks are far better conditioned at high degree.
+    """
+    coords = np.asarray(coords, dtype=np.float64)
+    part = np.asarray(part, dtype=np.int64)
+    nsub = int(part.max()) + 1
+    d = coords.shape[1]
+    lo = np.full((nsub, d), np.inf)
+    hi = np.full((nsub, d), -np.inf)
+    np.minimum.at(lo, part, coords)
+    np.maximum.at(hi, part, coords)
+    centre = 0.5 * (lo + hi)
+    half = 0.5 * (hi - lo)
+    half[half == 0.0] = 1.0
+    return monomials((coords - centre[part]) / half[part], p)
+
+
+def aggregate_generators(shape, box, agg, p=1):
+    """Generators for aggregation on subdomains smaller than the smoothing
+    ones (the comparison of Fig. 3): each box x box subdomain is cut into
+    aggregates of agg x agg nodes (box % agg == 0), and column
+    (slot * nm + j) holds the j-th local monomial of degree <= p on the
+    aggregate at position ``slot`` inside every subdomain, zero elsewhere.
+    Restricted to a subdomain these columns span the piecewise polynomials
+    on its aggregates."""
+    if any(b % agg for b in box):
+        raise ValueError("aggregates must tile the subdomain boxes")
+    ax = _grid_index(shape)
+    apart = box_partition(shape, (agg,) * len(shape))
+    per = [b // agg for b in box]
+    slot = np.zeros(ax[0].shape, dtype=np.int64)
+    stride = 1
+    for a, b, q in zip(ax, box, per):
+        slot += ((a % b) // agg) * stride
+        stride *= q
+    L = local_monomials(fd_node_coords(shape), apart, p)
+    nm = L.shape[1]
+    F = np.zeros((L.shape[0], nm * stride))
+    for sl in range(stride):
+        rows = slot == sl
+        F[rows, sl * nm:(sl + 1) * nm] = L[rows]
+    return F
+
+
 def uniform_rhs(n, seed, m=None):
     """f ~ U(-1, 1) i.i.d. (PCG64 seeded)."""
     rng = np.random.default_rng(seed)
@@ -443,13 +495,18 @@ def make_poisson3d(N=128, box=8, overlap=1, p=2, seed=1, m=None, mode="box"):
                    overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_7PT_3D)
 
 
-def make_biharmonic2d(N=256, box=16, overlap=2, p=3, seed=100, m=None, mode="box"):
-    """2D clamped biharmonic 13-point on N x N, box partition."""
+def make_biharmonic2d(N=256, box=16, overlap=2, p=3, seed=100, m=None, mode="box", local=False):
+    """2D clamped biharmonic 13-point on N x N, box partition; ``local``
+    takes the generators centred and scaled per subdomain (same coarse
+    space, better conditioned at high p)."""
     shape = (N, N)
     A = biharmonic13_2d(N)
+    part = box_partition(shape, (box, box))
+    coords = fd_node_coords(shape)
+    F = local_monomials(coords, part, p) if local else monomials(coords, p)
     return Problem(name=f"biharmonic2d_{N}", A=A, shape=shape,
-                   part=box_partition(shape, (box, box)), box=(box, box),
-                   F=monomials(fd_node_coords(shape), p), f=uniform_rhs(A.shape[0], seed, m),
+                   part=part, box=(box, box),
+                   F=F, f=uniform_rhs(A.shape[0], seed, m),
                    overlap=overlap, overlap_mode=mode, p=p, stencil_kind=STENCIL_13PT_2D)
 
 

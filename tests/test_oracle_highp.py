@@ -1,0 +1,73 @@
+"""High-degree generators (Fig. 3), oracle pins on the CPU.
+
+* The local monomials map every subdomain's bounding box onto [-1, 1] per
+  axis, and they give the same coarse space as the global monomials (only
+  restrictions to subdomains enter R0, Sec. 4).
+* Fig. 3: on the clamped biharmonic with Delta = 2 the iteration count falls
+  quickly as p grows, and p = 1 aggregated on smaller subdomains needs more
+  iterations than a higher p with no more coarse variables.
+"""
+import numpy as np
+
+import ddg_inputs as di
+from oracle import ddg_oracle as orc
+
+
+def _oracle(prob, F=None):
+    return orc.DDGOracle(prob.A, prob.part, prob.F if F is None else F, prob.overlap,
+                         prob.overlap_mode, prob.shape)
+
+
+def test_local_monomials_map_each_box_onto_the_unit_square():
+    shape = (20, 12)
+    part = di.box_partition(shape, (8, 6))
+    coords = di.fd_node_coords(shape)
+    L = di.local_monomials(coords, part, 1)          # columns 1, x, y
+    for s in range(int(part.max()) + 1):
+        rows = part == s
+        np.testing.assert_array_equal(L[rows, 0], 1.0)
+        for c in (1, 2):
+            assert abs(L[rows, c].min() + 1.0) < 1e-14 and abs(L[rows, c].max() - 1.0) < 1e-14
+
+
+def test_local_and_global_monomials_give_the_same_coarse_space():
+    g = di.make_biharmonic2d(N=48, box=12, overlap=2, p=3)
+    l = di.make_biharmonic2d(N=48, box=12, overlap=2, p=3, local=True)
+    Mg, Ml = _oracle(g), _oracle(l)
+    np.testing.assert_array_equal(np.diff(Mg.coarse_offsets), np.diff(Ml.coarse_offsets))
+    r = np.random.default_rng(60).standard_normal(g.n)
+    zg, zl = Mg.coarse_correction(r), Ml.coarse_correction(r)
+    assert np.linalg.norm(zg - zl) <= 1e-8 * np.linalg.norm(zg)
+
+
+def test_aggregate_generators_tile_each_subdomain():
+    shape = (24, 24)
+    F = di.aggregate_generators(shape, (12, 12), 6, p=1)
+    assert F.shape == (576, 4 * 3)
+    part = di.box_partition(shape, (12, 12))
+    agg = di.box_partition(shape, (6, 6))
+    # every node has exactly one nonzero constant column: the one of its slot
+    const = F[:, 0::3]
+    np.testing.assert_array_equal(const.sum(axis=1), 1.0)
+    # two nodes share a constant column inside a subdomain iff same aggregate
+    for s in range(int(part.max()) + 1):
+        rows = np.flatnonzero(part == s)
+        same = np.argmax(const[rows], axis=1)
+        for a in np.unique(agg[rows]):
+            assert np.unique(same[agg[rows] == a]).size == 1
+
+
+def test_iterations_fall_with_p_and_beat_smaller_aggregates():
+    its = {}
+    for p in (1, 2, 3, 5):
+        prob = di.make_biharmonic2d(N=60, box=12, overlap=2, p=p, local=True)
+        res = orc.pcg(prob.A, prob.f, _oracle(prob).apply, tol=1e-8)
+        assert res.converged
+        its[p] = res.iters
+    assert its[1] > its[2] > its[3] >= its[5], its
+    assert its[1] >= 2 * its[3], its
+    # p = 1 on 6 x 6 aggregates: 12 coarse variables per subdomain (p = 3 has 10)
+    prob = di.make_biharmonic2d(N=60, box=12, overlap=2, p=1)
+    F = di.aggregate_generators(prob.shape, prob.box, 6, p=1)
+    res = orc.pcg(prob.A, prob.f, _oracle(prob, F).apply, tol=1e-8)
+    assert res.converged and res.iters > its[3], (res.iters, its)
