@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--elasticity-steps", type=int, default=3)
     ap.add_argument("--materials-size", type=int, default=1024,
                     help="material-aware generator arm: N of the N^2 two-material grid (0 skips it)")
+    ap.add_argument("--psweep-size", type=int, default=500,
+                    help="Fig. 3 arm: N of the N^2 biharmonic for the p sweep (0 skips it)")
     ap.add_argument("--vcycle-group", type=int, default=4,
                     help="three-level arm: subdomains per axis of a coarse-level subdomain (0 skips it)")
     ap.add_argument("--keep", default="fp64,fp32,bf16",
@@ -409,6 +411,58 @@ def materials_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, wo
     return out
 
 
+def fractional_iters(hist, tol):
+    """Where the log-linear interpolation of the residual history meets tol."""
+    import math
+    for k in range(1, len(hist)):
+        if hist[k] <= tol:
+            a, b = math.log(hist[k - 1]), math.log(hist[k])
+            return (k - 1) + (a - math.log(tol)) / (a - b)
+    return None
+
+
+def psweep_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
+    """Fig. 3: iterations against the degree p of the coarse basis on the
+    clamped biharmonic, N^2 nodes, H/h = 50 (subdomains of 50^2 nodes),
+    Delta = 2, monomials centred and scaled per subdomain, p = 1..10; then
+    p = 1 aggregated on 25^2 and 10^2 sub-boxes.  FP64 preconditioner (exact
+    local solves, as in the paper), FP64 CG to 1e-8, f ~ U(-1, 1)."""
+    N, box = args.psweep_size, 50
+    runs = [("p", p) for p in range(1, 11)] + [("agg", 25), ("agg", 10)]
+    out = []
+    for kind, v in runs:
+        prob = di.make_biharmonic2d(N=N, box=box, overlap=2, p=v if kind == "p" else 1, local=True)
+        F = prob.F if kind == "p" else di.aggregate_generators(prob.shape, prob.box, v, p=1)
+        t0 = time.perf_counter()
+        s = ddg.Solver(prob.A, prob.part, F, prob.overlap, mode=prob.overlap_mode, shape=prob.shape,
+                       precision="fp64", keep=("fp64",))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+        u = torch.empty_like(f)
+        s.solve(f, TOL, u)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it, rr, st = s.solve(f, TOL, u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        hist = s.history()
+        lmin, lmax, ibound = s.condition_estimate(TOL)
+        info = s.info()
+        s.close()
+        out.append({"basis": f"p={v}" if kind == "p" else f"p=1 on {v}^2 aggregates",
+                    "generators": int(F.shape[1]), "coarse_dim": info["n0"], "iters": it,
+                    "fractional_iters": fractional_iters(list(hist), TOL), "true_relres": rr,
+                    "status": int(st), "ms": ms, "setup_s": setup_s, "kappa_estimate": lmax / lmin,
+                    "n_over_n0": prob.n / info["n0"]})
+    return {"workload": f"biharmonic2d_{N}^2: 13-pt clamped, {box}^2 boxes (H/h = {box}), overlap 2, "
+                        "local monomials p = 1..10 and p = 1 on smaller aggregates, FP64, tol 1e-8",
+            "runs": out}
+
+
 def elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
     """Differentiation workload: 3D linear elasticity, trilinear (Q1) hexahedra
     on ne^3 elements (x = 0 face clamped, 3 dofs per node), lambda = 1,
@@ -700,6 +754,10 @@ def main():
         vcycle = vcycle_arm(args, prob, (ms32, it32[-1]), ddg, di, torch, dev, stream, barrier,
                             max_over_ranks, world)
 
+    psweep = None
+    if args.psweep_size > 0:
+        psweep = psweep_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
+
     materials = None
     if args.materials_size > 0:
         materials = materials_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
@@ -739,6 +797,7 @@ def main():
         "elasticity_differentiation": elasticity,
         "three_level_vcycle": vcycle,
         "material_aware_generators": materials,
+        "p_sweep_biharmonic": psweep,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

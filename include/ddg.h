@@ -129,7 +129,8 @@ void ddg_default_options(ddg_options* opt);
  *   partition  host int32[n]: node -> non-overlapping subdomain id; ids
  *              must cover [0, nsub) (empty subdomains are rejected).
  *   F          host FP64 [n * k], column-major (column j at F + j * n): the
- *              generating vectors; k >= 1, or k = 0 with use_coarse = 0.
+ *              generating vectors; 1 <= k <= 96, or k = 0 with use_coarse = 0.
+ *              With k > 32, ddg_solve_batch solves its columns one at a time.
  *   overlap    Delta >= 0 layers.
  *   stream     cudaStream_t for all work of this handle (NULL = default).
  *   out        receives the handle.
@@ -236,7 +237,8 @@ ddg_status ddg_get_coarse_offsets(ddg_handle h, int32_t* offsets);
 ddg_status ddg_get_history(ddg_handle h, double* hist, int max_len, int* len);
 
 /* Sec. 7: the CG coefficients of the last single-vector solve on h
- * (ddg_solve, ddg_solve_host, ddg_adjoint), from the last restart on:
+ * (ddg_solve, ddg_solve_host, ddg_adjoint), of its longest stretch without
+ * a true-residual restart (the whole solve when there was none):
  * alpha_j for j < *len and beta_j for j < *len - 1 (beta_j forms
  * p_{j+1} = z_{j+1} + beta_j p_j).  Host arrays of max_len entries; *len
  * receives the number of alphas (both arrays may be NULL to query it). */

@@ -187,7 +187,7 @@ void validate(const ddg_matrix* A, const int32_t* part, const double* F, int k, 
         DDG_REQUIRE((int64_t)A->nx * A->ny == A->n, DDG_EINVAL, "2D stencil shape must match n");
     if (o.use_coarse) {
         DDG_REQUIRE(F, DDG_EINVAL, "F must be non-null for the two-level method");
-        DDG_REQUIRE(k >= 1 && k <= DDG_KMAX, DDG_EINVAL, "k must be in [1, 32]");
+        DDG_REQUIRE(k >= 1 && k <= DDG_KMAX, DDG_EINVAL, "k must be in [1, 96]");
     }
     DDG_REQUIRE(o.maxit >= 1, DDG_EINVAL, "maxit must be >= 1");
 }
@@ -313,8 +313,16 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
                                                   : h->opt.beta;
     const int pr = beta == DDG_BETA_PR;
     h->history.clear();
-    h->cg_alpha.clear();
-    h->cg_beta.clear();
+    for (auto* v : {&h->cg_alpha, &h->cg_beta, &h->seg_alpha, &h->seg_beta}) v->clear();
+    // a true-residual restart starts a new Lanczos sequence: keep the longest
+    auto keep_segment = [&]() {
+        if (h->seg_alpha.size() > h->cg_alpha.size()) {
+            h->cg_alpha.swap(h->seg_alpha);
+            h->cg_beta.swap(h->seg_beta);
+        }
+        h->seg_alpha.clear();
+        h->seg_beta.clear();
+    };
     {
         ProfScope ps(h, DDG_K_CG, 1, 0.0);
         ddg::dot64(h, f, f, S_TMP);
@@ -337,8 +345,7 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
     }
     DDG_CUDA(cudaMemcpyAsync(h->r, f, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     auto restart = [&]() {
-        h->cg_alpha.clear();
-        h->cg_beta.clear();
+        keep_segment();
         apply_in_pcg(h);
         ProfScope ps(h, DDG_K_CG, 2, 0.0);
         ddg::cg_dots_after_precond(h, prec, true, pr);
@@ -365,8 +372,8 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
         }
         // Sec. 7: the coefficients of the Lanczos tridiagonal; the beta read
         // here formed the current p
-        if (!h->cg_alpha.empty()) h->cg_beta.push_back(h->h_scal[S_BETA]);
-        h->cg_alpha.push_back(h->h_scal[S_ALPHA]);
+        if (!h->seg_alpha.empty()) h->seg_beta.push_back(h->h_scal[S_BETA]);
+        h->seg_alpha.push_back(h->h_scal[S_ALPHA]);
         const double rel = std::sqrt(h->h_scal[S_RR]) / fn;
         h->history.push_back(rel);
         if (rel <= tol) {
@@ -401,6 +408,7 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
         read_scalars(h);
         true_rel = std::sqrt(h->h_scal[S_TMP]) / fn;
     }
+    keep_segment();
     h->u = nullptr;
     DDG_CUDA(cudaStreamSynchronize(h->stream));
     if (iters_out) *iters_out = it;
@@ -1195,8 +1203,9 @@ ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, doub
         DDG_REQUIRE(F && U && m >= 1, DDG_EINVAL, "F, U must be non-null and m >= 1");
         DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
         ddg_status worst = DDG_OK;
-        if (h->precision == DDG_PREC_FP64 || h->inner) {
-            // the FP64 and the V-cycle preconditioners run one column at a time
+        if (h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32) {
+            // the FP64 and the V-cycle preconditioners, and coarse spaces of
+            // more than 32 generators per subdomain, run one column at a time
             for (int j = 0; j < m; ++j) {
                 ddg::strided_gather(h, F, m, j, h->fbuf);
                 int it = 0;

@@ -33,7 +33,7 @@
 
 #define DDG_LT 32        // local-inverse tile edge
 #define DDG_CT 64        // coarse factor tile edge
-#define DDG_KMAX 32      // largest supported number of generators
+#define DDG_KMAX 96      // largest supported number of generators (a multiple of 32)
 #define DDG_RED_BLOCKS 1216  // blocks of the deterministic reductions (8 x 152 SMs)
 #define DDG_BAND_ROWS 16     // tile rows per local-solve work item at most
 #define DDG_GATHER_SPLIT_CHUNKS 8  // chunks per subdomain above which the gather is a kernel of its own
@@ -274,7 +274,9 @@ struct ddg_handle_s {
     unsigned* red_counter = nullptr;
     int32_t* errflags = nullptr;
     std::vector<double> history;
-    std::vector<double> cg_alpha, cg_beta;   // CG coefficients since the last restart
+    // CG coefficients of the longest restart segment of the last solve, and
+    // of the segment in progress
+    std::vector<double> cg_alpha, cg_beta, seg_alpha, seg_beta;
 
     MultiWork mw;
     TcData tc;

@@ -60,6 +60,17 @@ __device__ __forceinline__ void block_sum32(V (&v)[32], V* sh, V* out) {
     __syncthreads();
 }
 
+// block_sum32 on K (a multiple of 32) values per thread, 32 at a time.
+template <int K, typename V>
+__device__ __forceinline__ void block_sum_k(V (&v)[K], V* sh, V* out) {
+    if constexpr (K == 32) {
+        block_sum32(v, sh, out);
+    } else {
+#pragma unroll
+        for (int c = 0; c < K / 32; ++c) block_sum32(*reinterpret_cast<V(*)[32]>(v + 32 * c), sh, out + 32 * c);
+    }
+}
+
 // Pseudo stencil kinds of the CSR path: rows of at most 8 / 16 entries are
 // applied fully unrolled so that all column and value loads of a row, then
 // all x loads, are in flight together (same summation order as the loop).

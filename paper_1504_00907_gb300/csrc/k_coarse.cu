@@ -29,12 +29,14 @@ constexpr int CT = DDG_CT;
 constexpr int CLD = CT + 1;
 
 // ---------------------------------------------------------------- R0 (QR)
+// KC >= k: per-thread partial sums of KC columns (32, or 96 for k > 32)
+template <int KC>
 __global__ void __launch_bounds__(256) coarse_qr_kernel(
     const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
     const double* __restrict__ F, int64_t n, int k, int kmax, double rank_tol, double* Q,
     int32_t* rank_out) {
     __shared__ double red[32 * 8];
-    __shared__ double vals[32];
+    __shared__ double vals[KC];
     __shared__ int piv;
     __shared__ double r00;
     const int s = blockIdx.x;
@@ -50,17 +52,17 @@ __global__ void __launch_bounds__(256) coarse_qr_kernel(
     const int kk = min(k, m);
     for (int j = 0; j < kk; ++j) {
         // squared norms of the remaining columns j..k-1
-        double v[32];
+        double v[KC];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = 0.0;
+        for (int c = 0; c < KC; ++c) v[c] = 0.0;
         for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x)
 #pragma unroll
-            for (int c = 0; c < 32; ++c)
+            for (int c = 0; c < KC; ++c)
                 if (c >= j && c < k) {
                     const double t = colref(a, c);
                     v[c] = fma(t, t, v[c]);
                 }
-        ddgdev::block_sum32(v, red, vals);
+        ddgdev::block_sum_k<KC>(v, red, vals);
         if (threadIdx.x == 0) {
             int p = j;
             for (int c = j + 1; c < k; ++c)
@@ -79,14 +81,14 @@ __global__ void __launch_bounds__(256) coarse_qr_kernel(
         // re-orthogonalise the pivot column against q_0..q_{j-1}
         if (j > 0) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = 0.0;
+            for (int c = 0; c < KC; ++c) v[c] = 0.0;
             for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
                 const double t = colref(a, j);
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
+                for (int c = 0; c < KC; ++c)
                     if (c < j) v[c] = fma(colref(a, c), t, v[c]);
             }
-            ddgdev::block_sum32(v, red, vals);
+            ddgdev::block_sum_k<KC>(v, red, vals);
             for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
                 double t = colref(a, j);
                 for (int c = 0; c < j; ++c) t -= vals[c] * colref(a, c);
@@ -112,14 +114,14 @@ __global__ void __launch_bounds__(256) coarse_qr_kernel(
         // remove q_j from the remaining columns (modified Gram-Schmidt step)
         if (j + 1 < k) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] = 0.0;
+            for (int c = 0; c < KC; ++c) v[c] = 0.0;
             for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
                 const double qj = colref(a, j);
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
+                for (int c = 0; c < KC; ++c)
                     if (c > j && c < k) v[c] = fma(qj, colref(a, c), v[c]);
             }
-            ddgdev::block_sum32(v, red, vals);
+            ddgdev::block_sum_k<KC>(v, red, vals);
             for (int64_t a = a0 + threadIdx.x; a < a1; a += blockDim.x) {
                 const double qj = colref(a, j);
                 for (int c = j + 1; c < k; ++c) colref(a, c) -= vals[c] * qj;
@@ -516,18 +518,18 @@ __global__ void __launch_bounds__(GEMV_TPR) profile_gemv_kernel(
 
 // c[coff_s + j] = sum_{g in Omega_s} Q[g, j] (r - A z)[g]   (z = 0 skips A z);
 // the residual is matrix-free for the constant-coefficient Laplacians
-template <int SK, typename V, typename AV>
+template <int SK, int KC, typename V, typename AV>
 __global__ void __launch_bounds__(256) coarse_restrict_kernel(
     const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const AV* __restrict__ val,
     const V* __restrict__ r, const V* __restrict__ z, const V* __restrict__ Q, int kmax,
     const int32_t* __restrict__ coff, V* __restrict__ c, int residual, int nx, int ny, int nz) {
     __shared__ V red[32 * 8];
-    __shared__ V out[32];
+    __shared__ V out[KC];
     const int s = blockIdx.x;
-    V acc[32];
+    V acc[KC];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0;
+    for (int j = 0; j < KC; ++j) acc[j] = 0;
     if constexpr (SK == ddgdev::SK_CSRW) {
         // a group of CSRW_G lanes per row computes its residual; the group's
         // first lane adds the row's Q contributions
@@ -543,7 +545,7 @@ __global__ void __launch_bounds__(256) coarse_restrict_kernel(
                 const V w = r[g] - az;
                 const V* qa = Q + a * kmax;
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
+                for (int j = 0; j < KC; ++j)
                     if (j < kmax) acc[j] = fma(qa[j], w, acc[j]);
             }
         }
@@ -575,11 +577,11 @@ __global__ void __launch_bounds__(256) coarse_restrict_kernel(
             }
             const V* qa = Q + a * kmax;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < KC; ++j)
                 if (j < kmax) acc[j] = fma(qa[j], w, acc[j]);
         }
     }
-    ddgdev::block_sum32(acc, red, out);
+    ddgdev::block_sum_k<KC>(acc, red, out);
     const int ks = coff[s + 1] - coff[s];
     if (threadIdx.x < ks) c[coff[s] + threadIdx.x] = out[threadIdx.x];
 }
@@ -605,7 +607,8 @@ __global__ void coarse_prolong_kernel(int64_t n, const int32_t* __restrict__ par
 namespace ddg {
 
 void coarse_qr(ddg_handle h, int32_t* d_rank, const double* dF, int k) {
-    coarse_qr_kernel<<<h->nsub, 256, 0, h->stream>>>(h->sub_off, h->sub_nodes, dF, h->n, k, h->kmax,
+    auto qr = h->kmax <= 32 ? coarse_qr_kernel<32> : coarse_qr_kernel<DDG_KMAX>;
+    qr<<<h->nsub, 256, 0, h->stream>>>(h->sub_off, h->sub_nodes, dF, h->n, k, h->kmax,
                                                      h->opt.rank_tol, h->Q64, d_rank);
     DDG_CHECK_LAUNCH();
 }
@@ -778,17 +781,23 @@ void coarse_build_apply(ddg_handle h) {
     h->bandL = nullptr;
 }
 
-template <int SK>
-static void launch_restrict(ddg_handle h, int prec, bool residual) {
+template <int SK, int KC>
+static void launch_restrict_k(ddg_handle h, int prec, bool residual) {
     if (prec == DDG_PREC_FP64)
-        coarse_restrict_kernel<SK, double, double><<<h->nsub, 256, 0, h->stream>>>(
+        coarse_restrict_kernel<SK, KC, double, double><<<h->nsub, 256, 0, h->stream>>>(
             h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->Q64,
             h->kmax, h->coff, h->c64, residual, h->nx, h->ny, h->nz);
     else
-        coarse_restrict_kernel<SK, float, float><<<h->nsub, 256, 0, h->stream>>>(
+        coarse_restrict_kernel<SK, KC, float, float><<<h->nsub, 256, 0, h->stream>>>(
             h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->Q32, h->kmax,
             h->coff, h->c32, residual, h->nx, h->ny, h->nz);
     DDG_CHECK_LAUNCH();
+}
+
+template <int SK>
+static void launch_restrict(ddg_handle h, int prec, bool residual) {
+    if (h->kmax <= 32) launch_restrict_k<SK, 32>(h, prec, residual);
+    else launch_restrict_k<SK, DDG_KMAX>(h, prec, residual);
 }
 
 void coarse_restrict(ddg_handle h, int prec, bool residual) {

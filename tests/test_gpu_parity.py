@@ -35,6 +35,9 @@ CASES = {
                                                            material_aware=True),
     "twomaterial3d_aware_16": lambda: di.make_twomaterial3d(N=16, box=4, overlap=1, p=2,
                                                            material_aware=True),
+    # 66 generators per subdomain (p = 10, centred and scaled per subdomain):
+    # the wide (96-column) QR and restriction kernels
+    "biharmonic_p10_local": lambda: di.make_biharmonic2d(N=64, box=16, overlap=2, p=10, local=True),
 }
 
 # FP64 building blocks agree to 1e-11 unless a subdomain's generator block
@@ -43,7 +46,9 @@ CASES = {
 # Gram-Schmidt on the GPU, Householder in the oracle).  In the 2D
 # material-aware case a subdomain keeps a column with |R_jj| / |R_00| =
 # 4.6e-7 (a few cells of one material), so u / 4.6e-7 = 2.4e-10.
-FP64_TOL = {"twomaterial2d_aware_64": 2.4e-10}
+# The p = 10 biharmonic coarse matrix has cond(A0) = 5.1e5: a solve with it
+# carries about cond(A0) u sqrt(n0) = 5.7e-11 * 32 = 1.8e-9 of rounding.
+FP64_TOL = {"twomaterial2d_aware_64": 2.4e-10, "biharmonic_p10_local": 2e-9}
 
 _cache = {}
 
@@ -129,7 +134,8 @@ def test_solve_fp64_matches_oracle(name):
 
 
 MIXED = [(n, "fp32") for n in ("poisson2d_64", "poisson3d_24", "poisson3d_ragged", "biharmonic_64",
-                                 "varcoef_16", "twomaterial2d_aware_64", "twomaterial3d_aware_16")]
+                                 "varcoef_16", "twomaterial2d_aware_64", "twomaterial3d_aware_16",
+                                 "biharmonic_p10_local")]
 MIXED += [(n, "bf16") for n in ("poisson2d_64", "poisson3d_24", "poisson3d_ragged", "varcoef_16")]
 
 
@@ -164,7 +170,8 @@ def test_bf16_biharmonic_reports_non_convergence():
 @pytest.mark.parametrize("name,m,prec", [("poisson3d_24", 1, "fp32"), ("poisson3d_24", 3, "fp32"),
                                          ("varcoef_16", 64, "fp32"), ("varcoef_16", 70, "bf16"),
                                          ("poisson2d_ragged", 5, "fp32"), ("biharmonic_64", 4, "fp32"),
-                                         ("poisson3d_graph", 2, "fp64")])
+                                         ("poisson3d_graph", 2, "fp64"),
+                                         ("biharmonic_p10_local", 3, "fp32")])
 def test_batched_solve_matches_oracle_per_column(name, m, prec):
     prob, solver, oracle = setup_case(name)
     F = di.normal_rhs(prob.n, 40 + m, m)
