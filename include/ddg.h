@@ -89,6 +89,10 @@ typedef struct {
                              ddg_solve_batch in DDG_PREC_BF16 runs its local solves on
                              the tcgen05 tensor cores (BF16 x BF16, FP32 accumulate);
                              default 0 */
+    int dedup_local;      /* 1: subdomains whose local matrices A_i are equal entry for
+                             entry (rows and columns in ascending dof order) share one
+                             stored inverse (constant-coefficient problems: the
+                             interior subdomains); the results do not change; default 0 */
 } ddg_options;
 
 typedef struct {
@@ -118,6 +122,7 @@ typedef struct {
     int coarse_blocks;    /* super-blocks of the coarse block-bidiagonal factor */
     double setup_ms;      /* wall time of ddg_setup */
     int precision;        /* current preconditioner precision */
+    int local_inverses;   /* stored local inverses: nsub, fewer with dedup_local */
 } ddg_info;
 
 /* Fill *opt with the defaults listed above. */

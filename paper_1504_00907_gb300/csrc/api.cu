@@ -7,6 +7,7 @@
 #include <cstring>
 #include <numeric>
 #include <thread>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -79,6 +80,58 @@ void grow_overlaps(const ddg_matrix* A, const std::vector<int64_t>& sub_off,
         }
         std::sort(om.begin(), om.end());
     }
+}
+
+// Subdomains (in sweep position q) whose local matrices A[ov, ov] (rows and
+// columns in ascending dof order) are equal entry for entry: rep[q] is the
+// first such position, rep[q] == q for the ones that keep their own inverse.
+std::vector<int32_t> identical_locals(const ddg_matrix* A, const std::vector<std::vector<int32_t>>& ov,
+                                      const std::vector<int>& sid) {
+    const int nsub = (int)sid.size();
+    std::vector<int32_t> rep(nsub), loc(A->n, -1);
+    std::vector<int64_t> ki, kr;
+    std::vector<double> kv, kvr;
+    // canonical form: size, then per row the (local column, value) pairs in CSR order
+    auto key = [&](int q, std::vector<int64_t>& kidx, std::vector<double>& kval) {
+        const std::vector<int32_t>& idx = ov[sid[q]];
+        for (size_t r = 0; r < idx.size(); ++r) loc[idx[r]] = (int32_t)r;
+        kidx.assign(1, (int64_t)idx.size());
+        kval.clear();
+        for (size_t r = 0; r < idx.size(); ++r) {
+            for (int64_t e = A->rowptr[idx[r]]; e < A->rowptr[idx[r] + 1]; ++e) {
+                const int32_t c = loc[A->col[e]];
+                if (c < 0) continue;
+                kidx.push_back(((int64_t)r << 32) | (uint32_t)c);
+                kval.push_back(A->val[e]);
+            }
+            kidx.push_back(-1);
+        }
+        for (int32_t g : idx) loc[g] = -1;
+        uint64_t hsh = 1469598103934665603ull;   // FNV-1a over the bytes of the key
+        auto mix = [&](const void* p, size_t bytes) {
+            const unsigned char* b = static_cast<const unsigned char*>(p);
+            for (size_t i = 0; i < bytes; ++i) hsh = (hsh ^ b[i]) * 1099511628211ull;
+        };
+        mix(kidx.data(), kidx.size() * sizeof(int64_t));
+        mix(kval.data(), kval.size() * sizeof(double));
+        return hsh;
+    };
+    std::unordered_map<uint64_t, std::vector<int32_t>> seen;
+    for (int q = 0; q < nsub; ++q) {
+        const uint64_t hq = key(q, ki, kv);
+        rep[q] = q;
+        std::vector<int32_t>& cands = seen[hq];
+        for (int32_t r : cands) {
+            key(r, kr, kvr);
+            if (kr == ki && kvr.size() == kv.size() &&
+                std::memcmp(kvr.data(), kv.data(), kv.size() * sizeof(double)) == 0) {
+                rep[q] = r;
+                break;
+            }
+        }
+        if (rep[q] == q) cands.push_back(q);
+    }
+    return rep;
 }
 
 // greedy colouring in id order: i and j conflict when Omega~_j meets the
@@ -764,16 +817,31 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         std::vector<int64_t> ov_off(nsub + 1, 0);
         std::vector<int32_t> Tq(nsub);
         std::vector<int64_t> tile_off(nsub + 1, 0);
+        // subdomains with equal local matrices share the stored inverse of the
+        // first of them (opt.dedup_local); rep[q] == q keeps its own
+        std::vector<int32_t> rep(nsub);
+        if (o.dedup_local) rep = identical_locals(A, ov, h->h_sid);
+        else std::iota(rep.begin(), rep.end(), 0);
+        std::vector<int32_t> reps;
+        int64_t tile_cursor = 0;
         h->max_local = 0;
         for (int q = 0; q < nsub; ++q) {
             const int nq = (int)ov[h->h_sid[q]].size();
             ov_off[q + 1] = ov_off[q] + nq;
             Tq[q] = (nq + DDG_LT - 1) / DDG_LT;
-            tile_off[q + 1] = tile_off[q] + (int64_t)ddgdev::packed_elems(Tq[q], ddgdev::packed_narrow_width(nq, Tq[q]));
+            if (rep[q] == q) {
+                reps.push_back(q);
+                tile_off[q] = tile_cursor;
+                tile_cursor += (int64_t)ddgdev::packed_elems(Tq[q], ddgdev::packed_narrow_width(nq, Tq[q]));
+            } else {
+                tile_off[q] = tile_off[rep[q]];
+            }
             h->max_local = std::max(h->max_local, nq);
         }
+        tile_off[nsub] = tile_cursor;
+        h->nrep_local = (int)reps.size();
         h->sum_local = ov_off[nsub];
-        h->inv_elems = tile_off[nsub];
+        h->inv_elems = tile_cursor;
         h->Tmax = (h->max_local + DDG_LT - 1) / DDG_LT;
         DDG_REQUIRE(h->Tmax <= 96, DDG_EINVAL, "overlapping subdomains larger than 3072 dofs are not supported");
         h->h_ov_off = ov_off;
@@ -876,11 +944,18 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
                 }
                 h->tc.h_citem_off[c + 1] = (int)tit.size();
             }
+            int64_t slab_cursor = 0;
             for (int q = 0; q < nsub; ++q) {
                 const int nq = (int)(ov_off[q + 1] - ov_off[q]);
-                soff[q + 1] = soff[q] + (int64_t)((nq + 127) / 128) * Tq[q];
+                if (rep[q] == q) {
+                    soff[q] = slab_cursor;
+                    slab_cursor += (int64_t)((nq + 127) / 128) * Tq[q];
+                } else {
+                    soff[q] = soff[rep[q]];
+                }
                 xo[q + 1] = xo[q] + Tq[q];
             }
+            soff[nsub] = slab_cursor;
             std::vector<int2> tsl;
             h->tc.h_cslab_off.assign(h->ncol + 1, 0);
             for (int c = 0; c < h->ncol; ++c) {
@@ -918,18 +993,25 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
             DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
             const size_t budget = (size_t)3 << 30;
             size_t waves = std::max<size_t>(1, budget / (per * (size_t)sms));
-            const int nb = (int)std::min<size_t>((size_t)nsub, waves * (size_t)sms);
+            const int nrep = (int)reps.size();
+            const int nb = (int)std::min<size_t>((size_t)nrep, waves * (size_t)sms);
             double* ws = h->arena.alloc<double>((size_t)nb * Np * Np);
             double* invdiag = h->arena.alloc<double>((size_t)nb * h->Tmax * DDG_LT * DDG_LT);
-            for (int q0 = 0; q0 < nsub; q0 += nb) {
-                const int q1 = std::min(nsub, q0 + nb);
-                ddg::local_extract_factor_invert(h, q0, q1, ws, invdiag);
-                ddg::local_pack(h, q0, q1, ws);
-                ddg::tc_pack(h, q0, q1, ws);
+            int32_t* qlist = nullptr;
+            if (nrep < nsub) {
+                qlist = h->arena.alloc<int32_t>(nrep);
+                h2d(qlist, reps.data(), nrep, h->stream);
+            }
+            for (int q0 = 0; q0 < nrep; q0 += nb) {
+                const int q1 = std::min(nrep, q0 + nb);
+                ddg::local_extract_factor_invert(h, q0, q1, qlist, ws, invdiag);
+                ddg::local_pack(h, q0, q1, qlist, ws);
+                ddg::tc_pack(h, q0, q1, qlist, ws);
             }
             DDG_CUDA(cudaStreamSynchronize(h->stream));
             h->arena.release(ws);
             h->arena.release(invdiag);
+            if (qlist) h->arena.release(qlist);
         }
         ddg::local_configure(h);
         h->res64 = h->arena.alloc<double>(h->sum_local);
@@ -1358,6 +1440,7 @@ ddg_status ddg_get_info(ddg_handle h, ddg_info* info) {
         info->coarse_blocks = h->nK;
         info->setup_ms = h->setup_ms;
         info->precision = h->precision;
+        info->local_inverses = h->nrep_local;
         return DDG_OK;
     });
 }

@@ -273,6 +273,7 @@ struct ddg_handle_s {
     double* red_partials = nullptr;   // [DDG_RED_BLOCKS * 4]
     unsigned* red_counter = nullptr;
     int32_t* errflags = nullptr;
+    int nrep_local = 0;            // distinct stored local inverses (dedup_local)
     std::vector<double> history;
     // CG coefficients of the longest restart segment of the last solve, and
     // of the segment in progress
@@ -315,8 +316,10 @@ struct ProfScope {
 namespace ddg {
 
 // k_local.cu
-void local_extract_factor_invert(ddg_handle h, int q0, int q1, double* ws, double* invdiag);
-void local_pack(ddg_handle h, int q0, int q1, const double* ws);
+// setup of the subdomains q0..q1-1, or of qlist[q0..q1-1] when qlist (device) is set
+void local_extract_factor_invert(ddg_handle h, int q0, int q1, const int32_t* qlist, double* ws,
+                                 double* invdiag);
+void local_pack(ddg_handle h, int q0, int q1, const int32_t* qlist, const double* ws);
 void local_configure(ddg_handle h);
 void local_residual(ddg_handle h, int colour, bool z_zero, int prec);
 void local_solve_colour(ddg_handle h, int colour, int prec);
@@ -362,7 +365,7 @@ void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int
 
 // k_tc.cu (tcgen05 local solves of the batched path)
 int tc_n_for(int m);
-void tc_pack(ddg_handle h, int q0, int q1, const double* ws);
+void tc_pack(ddg_handle h, int q0, int q1, const int32_t* qlist, const double* ws);
 void tc_residual(ddg_handle h, int colour, bool z_zero, int m);
 void tc_local_solve(ddg_handle h, int colour, int m);
 

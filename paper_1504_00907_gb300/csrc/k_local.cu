@@ -134,12 +134,13 @@ __device__ void trtri32(const double* L, double* X) {
 }
 
 // ---------------------------------------------------------------- setup
-__global__ void local_extract_kernel(int q0, const int64_t* __restrict__ ov_off,
+__global__ void local_extract_kernel(int q0, const int32_t* __restrict__ qlist,
+                                     const int64_t* __restrict__ ov_off,
                                      const int32_t* __restrict__ ov_nodes,
                                      const int64_t* __restrict__ rowptr,
                                      const int32_t* __restrict__ col,
                                      const double* __restrict__ val, double* ws, int Np) {
-    const int b = blockIdx.x, q = q0 + b;
+    const int b = blockIdx.x, q = qlist ? qlist[q0 + b] : q0 + b;
     const int64_t o = ov_off[q];
     const int n = (int)(ov_off[q + 1] - o);
     double* A = ws + (size_t)b * Np * Np;
@@ -165,15 +166,15 @@ __global__ void local_extract_kernel(int q0, const int64_t* __restrict__ ov_off,
 
 // In-place: A (Np x Np, row-major) -> its inverse in the upper tiles (I <= J).
 __global__ void __launch_bounds__(256) local_factor_invert_kernel(
-    int q0, const int32_t* __restrict__ Tq, double* ws, double* invdiag, int Np, int Tmax,
-    int* err) {
+    int q0, const int32_t* __restrict__ qlist, const int32_t* __restrict__ Tq, double* ws,
+    double* invdiag, int Np, int Tmax, int* err) {
     extern __shared__ double sm[];
     double* sA = sm;
     double* sB = sm + DDG_LT * LDT;
     double* sC = sm + 2 * DDG_LT * LDT;
     __shared__ int bad;
     const int b = blockIdx.x;
-    const int T = Tq[q0 + b];
+    const int T = Tq[qlist ? qlist[q0 + b] : q0 + b];
     double* A = ws + (size_t)b * Np * Np;
     double* D = invdiag + (size_t)b * Tmax * DDG_LT * DDG_LT;
     auto tile = [&](int I, int J) { return A + (size_t)I * DDG_LT * Np + J * DDG_LT; };
@@ -261,12 +262,13 @@ __global__ void __launch_bounds__(256) local_factor_invert_kernel(
     if (threadIdx.x == 0 && bad) atomicExch(err, 1);
 }
 
-__global__ void local_pack_kernel(int q0, const double* __restrict__ ws, int Np,
+__global__ void local_pack_kernel(int q0, const int32_t* __restrict__ qlist, const double* __restrict__ ws,
+                                  int Np,
                                   const int64_t* __restrict__ ov_off,
                                   const int32_t* __restrict__ Tq,
                                   const int64_t* __restrict__ tile_off, double* inv64,
                                   float* inv32, __nv_bfloat16* inv16) {
-    const int b = blockIdx.x, q = q0 + b;
+    const int b = blockIdx.x, q = qlist ? qlist[q0 + b] : q0 + b;
     const int n = (int)(ov_off[q + 1] - ov_off[q]);
     const int T = Tq[q];
     const double* A = ws + (size_t)b * Np * Np;
@@ -646,24 +648,25 @@ __global__ void local_gather_kernel(int64_t a0, int64_t a1, const int32_t* __res
 
 namespace ddg {
 
-void local_extract_factor_invert(ddg_handle h, int q0, int q1, double* ws, double* invdiag) {
+void local_extract_factor_invert(ddg_handle h, int q0, int q1, const int32_t* qlist, double* ws,
+                                 double* invdiag) {
     const int nb = q1 - q0;
     if (nb <= 0) return;
     const int Np = h->Tmax * DDG_LT;
     DDG_CUDA(cudaMemsetAsync(ws, 0, (size_t)nb * Np * Np * sizeof(double), h->stream));
-    local_extract_kernel<<<nb, 256, 0, h->stream>>>(q0, h->ov_off, h->ov_nodes, h->rowptr, h->col,
+    local_extract_kernel<<<nb, 256, 0, h->stream>>>(q0, qlist, h->ov_off, h->ov_nodes, h->rowptr, h->col,
                                                     h->val64, ws, Np);
     DDG_CHECK_LAUNCH();
     const size_t smem = 3 * DDG_LT * LDT * sizeof(double);
-    local_factor_invert_kernel<<<nb, 256, smem, h->stream>>>(q0, h->Tq, ws, invdiag, Np, h->Tmax,
+    local_factor_invert_kernel<<<nb, 256, smem, h->stream>>>(q0, qlist, h->Tq, ws, invdiag, Np, h->Tmax,
                                                             h->errflags + E_LOCAL_SPD);
     DDG_CHECK_LAUNCH();
 }
 
-void local_pack(ddg_handle h, int q0, int q1, const double* ws) {
+void local_pack(ddg_handle h, int q0, int q1, const int32_t* qlist, const double* ws) {
     const int nb = q1 - q0;
     if (nb <= 0) return;
-    local_pack_kernel<<<nb, 256, 0, h->stream>>>(q0, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq,
+    local_pack_kernel<<<nb, 256, 0, h->stream>>>(q0, qlist, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq,
                                                  h->tile_off, h->inv64, h->inv32, h->inv16);
     DDG_CHECK_LAUNCH();
 }

@@ -213,10 +213,10 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
 
 // A_i^{-1} (FP64 workspace after local_factor_invert: inverse in the upper
 // 32x32 tiles) -> BF16 128 x 32 slabs in core-matrix order
-__global__ void tc_pack_kernel(int q0, const double* __restrict__ ws, int Np,
+__global__ void tc_pack_kernel(int q0, const int32_t* __restrict__ qlist, const double* __restrict__ ws, int Np,
                                const int64_t* __restrict__ ov_off, const int32_t* __restrict__ Tq,
                                const int64_t* __restrict__ slab_off, __nv_bfloat16* __restrict__ out) {
-    const int b = blockIdx.x, q = q0 + b;
+    const int b = blockIdx.x, q = qlist ? qlist[q0 + b] : q0 + b;
     const int n = (int)(ov_off[q + 1] - ov_off[q]);
     const int T = Tq[q];
     const int Mb = (n + TC_M - 1) / TC_M;
@@ -409,10 +409,11 @@ namespace ddg {
 
 int tc_n_for(int m) { return ((m + 15) / 16) * 16; }
 
-void tc_pack(ddg_handle h, int q0, int q1, const double* ws) {
+void tc_pack(ddg_handle h, int q0, int q1, const int32_t* qlist, const double* ws) {
     const int nb = q1 - q0;
     if (nb <= 0 || !h->tc.A) return;
-    tc_pack_kernel<<<nb, 256, 0, h->stream>>>(q0, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq, h->tc.slab_off, h->tc.A);
+    tc_pack_kernel<<<nb, 256, 0, h->stream>>>(q0, qlist, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq, h->tc.slab_off,
+                                              h->tc.A);
     DDG_CHECK_LAUNCH();
 }
 

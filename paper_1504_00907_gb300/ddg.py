@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("keep_precisions", ctypes.c_int),
                 ("overlap_mode", ctypes.c_int), ("beta", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("use_coarse", ctypes.c_int), ("rank_tol", ctypes.c_double),
-                ("chunk_tiles", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("chunk_tiles", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("dedup_local", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -49,7 +50,8 @@ class Info(ctypes.Structure):
                 ("n0", ctypes.c_int), ("kmax", ctypes.c_int), ("max_local", ctypes.c_int),
                 ("sum_local", ctypes.c_int64), ("local_tiles", ctypes.c_int64),
                 ("coarse_band", ctypes.c_int), ("coarse_blocks", ctypes.c_int),
-                ("setup_ms", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("setup_ms", ctypes.c_double), ("precision", ctypes.c_int),
+                ("local_inverses", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -174,7 +176,7 @@ class Solver:
     def __init__(self, A, part, F, overlap, *, mode="graph", shape=None, stencil_kind=0,
                  coef=None, dofs_per_node=1, precision="fp64", keep=None, beta="auto",
                  maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
-                 stream=None, coarse_groups=None):
+                 stream=None, coarse_groups=None, dedup_local=False):
         import torch
         lib = load()
         if not torch.cuda.is_available():
@@ -213,6 +215,7 @@ class Solver:
         o.rank_tol = rank_tol
         o.chunk_tiles = chunk_tiles
         o.tensor_cores = 1 if tensor_cores else 0
+        o.dedup_local = 1 if dedup_local else 0
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
