@@ -74,3 +74,26 @@ def test_library_estimate_rejects_bad_input(ddg):
         ddg.condition_estimate(np.array([1.0, -1.0]), np.array([0.5]), 1e-8)
     with pytest.raises(ddg.DDGError):
         ddg.condition_estimate(np.array([1.0]), np.array([]), 2.0)
+
+
+def test_planted_dropped_beta_term_fails_the_diagonal_pin():
+    # mistake: diagonal 1/alpha_j without beta_{j-1}/alpha_{j-1}
+    import scipy.linalg as sla
+    res = _plain_cg_on_diagonal(10)
+    a, b = np.asarray(res.alphas), np.asarray(res.betas)
+    d = 1.0 / a
+    e = np.sqrt(b) / a[:-1]
+    w = sla.eigh_tridiagonal(d, e, eigvals_only=True)
+    assert abs(w[0] - 1.0) > 1e-3 or abs(w[-1] - 10.0) > 1e-3
+
+
+def test_planted_swapped_offdiagonal_scale_fails_the_diagonal_pin():
+    # mistake: off-diagonal sqrt(beta_j) / alpha_{j+1} instead of / alpha_j
+    import scipy.linalg as sla
+    res = _plain_cg_on_diagonal(10)
+    a, b = np.asarray(res.alphas), np.asarray(res.betas)
+    d = 1.0 / a
+    d[1:] += b / a[:-1]
+    e = np.sqrt(b) / a[1:]
+    w = sla.eigh_tridiagonal(d, e, eigvals_only=True)
+    assert abs(w[0] - 1.0) > 1e-3 or abs(w[-1] - 10.0) > 1e-3
