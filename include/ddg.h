@@ -177,6 +177,18 @@ ddg_status ddg_setup_vcycle(const ddg_matrix* A, const int32_t* partition,
  * Errors: DDG_ENOCONV (maxit reached, u is the last iterate),
  * DDG_EBREAKDOWN, DDG_EINVAL, DDG_ECUDA.
  */
+/*
+ * Replace the generators of a built handle (Sec. 4): R0, A0 and its factor
+ * are rebuilt from F (host FP64 [n * k], column-major, 1 <= k <= 96); the
+ * overlapping subdomains, colouring and local inverses are kept, so a sweep
+ * over coarse spaces factorises the local blocks once.  The result equals a
+ * handle set up with F from the start.  Also turns the coarse level on for a
+ * handle built with use_coarse = 0.  Not for V-cycle handles (DDG_EINVAL).
+ * Errors: DDG_EINVAL, DDG_ENOTSPD, DDG_ENOMEM, DDG_ECUDA (the handle then has
+ * no usable coarse space and must be destroyed).
+ */
+ddg_status ddg_set_generators(ddg_handle h, const double* F, int k);
+
 ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters,
                      double* relres);
 

@@ -691,6 +691,105 @@ namespace {
 void setup_vcycle(ddg_handle h, const double* F, int k, int overlap, const ddg_options& o,
                   const int32_t* groups, const std::vector<int>& bI, const std::vector<int>& bJ,
                   const std::vector<int64_t>& sub_off, const std::vector<int32_t>& sub_nodes);
+
+// pairs of subdomains (I >= J, ascending) that A couples: an entry of a row of
+// Omega_I lies in a column of Omega_J
+void subdomain_pairs(const ddg_matrix* A, const int32_t* partition, const std::vector<int64_t>& sub_off,
+                     const std::vector<int32_t>& sub_nodes, int nsub, std::vector<int>& pI,
+                     std::vector<int>& pJ) {
+    pI.clear();
+    pJ.clear();
+    std::vector<int> mark(nsub, -1), js;
+    for (int I = 0; I < nsub; ++I) {
+        js.clear();
+        for (int64_t a = sub_off[I]; a < sub_off[I + 1]; ++a) {
+            const int g = sub_nodes[a];
+            for (int64_t e = A->rowptr[g]; e < A->rowptr[g + 1]; ++e) {
+                const int J = partition[A->col[e]];
+                if (J <= I && mark[J] != I) {
+                    mark[J] = I;
+                    js.push_back(J);
+                }
+            }
+        }
+        std::sort(js.begin(), js.end());
+        for (int J : js) {
+            pI.push_back(I);
+            pJ.push_back(J);
+        }
+    }
+}
+
+// Sec. 4: R0 from the generators (per-subdomain QR and rank drop), then A0 and
+// its block-bidiagonal factor, or the coarse level of the V-cycle when groups
+// is set.  Leaves use_coarse = 0 when every subdomain drops every generator.
+// The device memory it keeps is listed in h->coarse_allocs.
+void build_coarse(ddg_handle h, const double* F, int k, int overlap, const ddg_options& o,
+                  const int32_t* groups) {
+    const size_t mark_allocs = h->arena.ptrs.size();
+    const int64_t n = h->n;
+    const int nsub = h->nsub;
+    h->kmax = k;
+    double* dF = h->arena.alloc<double>((size_t)n * k);
+    h2d(dF, F, (size_t)n * k, h->stream);
+    h->Q64 = h->arena.alloc<double>((size_t)n * k);
+    int32_t* d_rank = h->arena.alloc<int32_t>(nsub);
+    ddg::coarse_qr(h, d_rank, dF, k);
+    std::vector<int32_t> rank(nsub);
+    d2h(rank.data(), d_rank, nsub, h->stream);
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    h->arena.release(dF);
+    h->arena.release(d_rank);
+    h->h_coff.assign(nsub + 1, 0);
+    for (int s = 0; s < nsub; ++s) h->h_coff[s + 1] = h->h_coff[s] + rank[s];
+    h->n0 = h->h_coff[nsub];
+    if (h->n0 == 0) h->use_coarse = 0;
+    if (h->use_coarse) {
+        h->coff = h->arena.alloc<int32_t>(nsub + 1);
+        h2d(h->coff, h->h_coff.data(), nsub + 1, h->stream);
+        // coupled pairs with coarse dofs on both sides, and the half-bandwidth of A0
+        std::vector<int> bI, bJ;
+        int64_t band = 0;
+        for (size_t p = 0; p < h->h_adjI.size(); ++p) {
+            const int I = h->h_adjI[p], J = h->h_adjJ[p];
+            if (h->h_coff[I + 1] == h->h_coff[I] || h->h_coff[J + 1] == h->h_coff[J]) continue;
+            bI.push_back(I);
+            bJ.push_back(J);
+            band = std::max<int64_t>(band, (int64_t)h->h_coff[I + 1] - 1 - h->h_coff[J]);
+        }
+        h->band = (int)band;
+        if (groups) {
+            setup_vcycle(h, F, k, overlap, o, groups, bI, bJ, h->h_sub_off, h->h_sub_nodes);
+        } else {
+            h->Wt = std::max(1, (int)((band + DDG_CT - 1) / DDG_CT));
+            const int NT0 = (h->n0 + DDG_CT - 1) / DDG_CT;
+            h->nK = (NT0 + h->Wt - 1) / h->Wt;
+            h->NT = h->nK * h->Wt;
+            h->n0p = h->NT * DDG_CT;
+            h->B = h->Wt * DDG_CT;
+            h->bandL = h->arena.alloc<double>((size_t)h->NT * (h->Wt + 1) * DDG_CT * DDG_CT);
+            ddg::coarse_assemble_band(h, bI, bJ);
+            ddg::coarse_band_cholesky(h);
+            ddg::coarse_build_apply(h);
+            const int n0p = h->n0p;
+            h->c64 = h->arena.alloc<double>(n0p);
+            h->y64 = h->arena.alloc<double>(n0p);
+            h->x64 = h->arena.alloc<double>(n0p);
+            h->c32 = h->arena.alloc<float>(n0p);
+            h->y32 = h->arena.alloc<float>(n0p);
+            h->x32 = h->arena.alloc<float>(n0p);
+            for (void* p : {(void*)h->c64, (void*)h->y64, (void*)h->x64})
+                DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(double), h->stream));
+            for (void* p : {(void*)h->c32, (void*)h->y32, (void*)h->x32})
+                DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(float), h->stream));
+        }
+        h->Q32 = h->arena.alloc<float>((size_t)n * k);
+        ddg::cast_q32(h);
+    }
+    h->coarse_allocs.clear();
+    for (size_t i = mark_allocs; i < h->arena.ptrs.size(); ++i)
+        if (h->arena.ptrs[i]) h->coarse_allocs.push_back(h->arena.ptrs[i]);
+}
 }  // namespace
 
 static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, const int32_t* groups,
@@ -1020,79 +1119,11 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         if (keep & (1 << DDG_PREC_FP64)) h->partial64 = h->arena.alloc<double>(pslots);
         if (keep & ((1 << DDG_PREC_FP32) | (1 << DDG_PREC_BF16))) h->partial32 = h->arena.alloc<float>(pslots);
 
-        // ---- coarse space (Sec. 4)
-        if (h->use_coarse) {
-            h->kmax = k;
-            double* dF = h->arena.alloc<double>((size_t)n * k);
-            h2d(dF, F, (size_t)n * k, h->stream);
-            h->Q64 = h->arena.alloc<double>((size_t)n * k);
-            int32_t* d_rank = h->arena.alloc<int32_t>(nsub);
-            ddg::coarse_qr(h, d_rank, dF, k);
-            std::vector<int32_t> rank(nsub);
-            d2h(rank.data(), d_rank, nsub, h->stream);
-            DDG_CUDA(cudaStreamSynchronize(h->stream));
-            h->arena.release(dF);
-            h->arena.release(d_rank);
-            h->h_coff.assign(nsub + 1, 0);
-            for (int s = 0; s < nsub; ++s) h->h_coff[s + 1] = h->h_coff[s] + rank[s];
-            h->n0 = h->h_coff[nsub];
-            if (h->n0 == 0) h->use_coarse = 0;
-        }
-        if (h->use_coarse) {
-            h->coff = h->arena.alloc<int32_t>(nsub + 1);
-            h2d(h->coff, h->h_coff.data(), nsub + 1, h->stream);
-            // adjacent subdomain pairs (I >= J) and the half-bandwidth of A0
-            std::vector<int> bI, bJ, mark(nsub, -1);
-            int64_t band = 0;
-            for (int I = 0; I < nsub; ++I) {
-                if (h->h_coff[I + 1] == h->h_coff[I]) continue;
-                std::vector<int> js;
-                for (int64_t a = sub_off[I]; a < sub_off[I + 1]; ++a) {
-                    const int g = sub_nodes[a];
-                    for (int64_t e = A->rowptr[g]; e < A->rowptr[g + 1]; ++e) {
-                        const int J = partition[A->col[e]];
-                        if (J <= I && mark[J] != I && h->h_coff[J + 1] > h->h_coff[J]) {
-                            mark[J] = I;
-                            js.push_back(J);
-                        }
-                    }
-                }
-                std::sort(js.begin(), js.end());
-                for (int J : js) {
-                    bI.push_back(I);
-                    bJ.push_back(J);
-                    band = std::max<int64_t>(band, (int64_t)h->h_coff[I + 1] - 1 - h->h_coff[J]);
-                }
-            }
-            h->band = (int)band;
-            if (groups) {
-                setup_vcycle(h, F, k, overlap, o, groups, bI, bJ, sub_off, sub_nodes);
-            } else {
-                h->Wt = std::max(1, (int)((band + DDG_CT - 1) / DDG_CT));
-                const int NT0 = (h->n0 + DDG_CT - 1) / DDG_CT;
-                h->nK = (NT0 + h->Wt - 1) / h->Wt;
-                h->NT = h->nK * h->Wt;
-                h->n0p = h->NT * DDG_CT;
-                h->B = h->Wt * DDG_CT;
-                h->bandL = h->arena.alloc<double>((size_t)h->NT * (h->Wt + 1) * DDG_CT * DDG_CT);
-                ddg::coarse_assemble_band(h, bI, bJ);
-                ddg::coarse_band_cholesky(h);
-                ddg::coarse_build_apply(h);
-                const int n0p = h->n0p;
-                h->c64 = h->arena.alloc<double>(n0p);
-                h->y64 = h->arena.alloc<double>(n0p);
-                h->x64 = h->arena.alloc<double>(n0p);
-                h->c32 = h->arena.alloc<float>(n0p);
-                h->y32 = h->arena.alloc<float>(n0p);
-                h->x32 = h->arena.alloc<float>(n0p);
-                for (void* p : {(void*)h->c64, (void*)h->y64, (void*)h->x64})
-                    DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(double), h->stream));
-                for (void* p : {(void*)h->c32, (void*)h->y32, (void*)h->x32})
-                    DDG_CUDA(cudaMemsetAsync(p, 0, n0p * sizeof(float), h->stream));
-            }
-            h->Q32 = h->arena.alloc<float>((size_t)n * k);
-            ddg::cast_q32(h);
-        }
+        // ---- coarse space (Sec. 4): pairs of subdomains that A couples, then
+        // R0, A0 and its factor (or the coarse level of the V-cycle)
+        subdomain_pairs(A, partition, sub_off, sub_nodes, nsub, h->h_adjI, h->h_adjJ);
+        h->h_sub_nodes = sub_nodes;
+        if (h->use_coarse) build_coarse(h, F, k, overlap, o, groups);
 
         // ---- CG workspace
         h->r = h->arena.alloc<double>(n);
@@ -1256,6 +1287,41 @@ ddg_status ddg_setup_vcycle(const ddg_matrix* A, const int32_t* partition, const
         return DDG_EINVAL;
     }
     return setup_impl(A, partition, coarse_partition, F, k, overlap, &o, stream, out);
+}
+
+ddg_status ddg_set_generators(ddg_handle h, const double* F, int k) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE(!h->inner, DDG_EINVAL, "a V-cycle handle keeps the generators it was built with");
+        DDG_REQUIRE(F && k >= 1 && k <= DDG_KMAX, DDG_EINVAL, "F must be non-null and k in [1, 96]");
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        // the captured preconditioner graphs hold launches of the old coarse space
+        for (cudaGraphExec_t& g : h->apply_exec)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        for (void* p : h->coarse_allocs) h->arena.release(p);
+        h->coarse_allocs.clear();
+        h->Q64 = nullptr;
+        h->Q32 = nullptr;
+        h->coff = nullptr;
+        h->c64 = h->y64 = h->x64 = nullptr;
+        h->c32 = h->y32 = h->x32 = nullptr;
+        h->Dm = h->Dt = h->Fm = h->Gm = ProfileMat{};
+        h->band = 0;
+        h->Wt = 1;
+        h->NT = h->nK = h->B = h->n0p = 0;
+        h->mw.m_alloc = 0;   // the batched workspace is sized by the coarse dimension
+        h->use_coarse = 1;
+        h->opt.use_coarse = 1;
+        DDG_CUDA(cudaMemsetAsync(h->errflags + E_COARSE_SPD, 0, sizeof(int32_t), h->stream));
+        build_coarse(h, F, k, 0, h->opt, nullptr);
+        int32_t bad = 0;
+        d2h(&bad, h->errflags + E_COARSE_SPD, 1, h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        DDG_REQUIRE(!bad, DDG_ENOTSPD, "the coarse matrix A0 is not positive definite");
+        return DDG_OK;
+    });
 }
 
 ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters, double* relres) {

@@ -261,6 +261,11 @@ struct ddg_handle_s {
     // replaces A0^{-1}.  Its input r32 and outputs z32, z64 are this handle's
     // c32, x32 and x64 (owned by the inner handle); it reads c64 in place.
     ddg_handle_s* inner = nullptr;
+    // subdomain pairs that A couples (I >= J), the partition's node lists and
+    // the device memory of the coarse space (released when it is rebuilt)
+    std::vector<int> h_adjI, h_adjJ;
+    std::vector<int32_t> h_sub_nodes;
+    std::vector<void*> coarse_allocs;
 
     // ---- CG workspace (FP64) and preconditioner vectors
     const double* rin64 = nullptr;  // input of the FP64 preconditioner apply

@@ -73,6 +73,7 @@ _SIGS = {
     "ddg_setup": (_I, [ctypes.POINTER(Matrix), _P, _P, _I, _I, ctypes.POINTER(Options), _P, ctypes.POINTER(_P)]),
     "ddg_setup_vcycle": (_I, [ctypes.POINTER(Matrix), _P, _P, _P, _I, _I, ctypes.POINTER(Options), _P,
                               ctypes.POINTER(_P)]),
+    "ddg_set_generators": (_I, [_P, _P, _I]),
     "ddg_solve": (_I, [_P, _P, _P, _D, _PI, _PD]),
     "ddg_solve_host": (_I, [_P, _P, _P, _D, _PI, _PD]),
     "ddg_solve_batch": (_I, [_P, _P, _P, _I, _D, _P, _P]),
@@ -243,6 +244,15 @@ class Solver:
         if prob.kappa is not None:
             kw.setdefault("coef", prob.kappa)
         return cls(prob.A, prob.part, prob.F, prob.overlap, **kw)
+
+    def set_generators(self, F):
+        """Rebuild the coarse space from new generators F (n x k host array),
+        keeping the local inverses (``ddg_set_generators``)."""
+        F = np.asarray(F, dtype=np.float64)
+        if F.ndim == 1:
+            F = F[:, None]
+        Fc, p_F = _host(F.T.ravel(), np.float64)
+        _check(load().ddg_set_generators(self.h, p_F, F.shape[1]), self.h)
 
     # ---- solves
     def solve(self, f, tol=1e-8, u=None):

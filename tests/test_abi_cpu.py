@@ -123,6 +123,12 @@ def test_vcycle_setup_rejects_bad_arguments_before_touching_the_gpu(lib, case):
     assert len(lib.ddg_last_error(None)) > 0
 
 
+def test_set_generators_rejects_a_null_handle(lib):
+    from paper_1504_00907_gb300 import ddg
+    F = np.ones(4)
+    assert lib.ddg_set_generators(None, F.ctypes.data_as(ctypes.c_void_p), 1) == ddg.DDG_EINVAL
+
+
 def test_product_path_has_no_cpu_fallback():
     # the binding never imports the oracle and refuses to run without a GPU
     src = open(os.path.join(ROOT, "paper_1504_00907_gb300", "ddg.py")).read()
