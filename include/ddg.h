@@ -169,15 +169,6 @@ ddg_status ddg_setup_vcycle(const ddg_matrix* A, const int32_t* partition,
                             const ddg_options* opt, void* stream, ddg_handle* out);
 
 /*
- * Solve A u = f by PCG from u0 = 0 (Sec. 7): stop when the recurrence
- * residual satisfies ||r||_2 <= tol ||f||_2 and the true residual does too
- * (a recurrence that drifts is replaced by the true residual and CG
- * restarts).  f, u: device FP64 [n].  *iters: iterations taken; *relres:
- * true relative residual ||f - A u|| / ||f||.  Either output may be NULL.
- * Errors: DDG_ENOCONV (maxit reached, u is the last iterate),
- * DDG_EBREAKDOWN, DDG_EINVAL, DDG_ECUDA.
- */
-/*
  * Replace the generators of a built handle (Sec. 4): R0, A0 and its factor
  * are rebuilt from F (host FP64 [n * k], column-major, 1 <= k <= 96); the
  * overlapping subdomains, colouring and local inverses are kept, so a sweep
@@ -189,6 +180,15 @@ ddg_status ddg_setup_vcycle(const ddg_matrix* A, const int32_t* partition,
  */
 ddg_status ddg_set_generators(ddg_handle h, const double* F, int k);
 
+/*
+ * Solve A u = f by PCG from u0 = 0 (Sec. 7): stop when the recurrence
+ * residual satisfies ||r||_2 <= tol ||f||_2 and the true residual does too
+ * (a recurrence that drifts is replaced by the true residual and CG
+ * restarts).  f, u: device FP64 [n].  *iters: iterations taken; *relres:
+ * true relative residual ||f - A u|| / ||f||.  Either output may be NULL.
+ * Errors: DDG_ENOCONV (maxit reached, u is the last iterate),
+ * DDG_EBREAKDOWN, DDG_EINVAL, DDG_ECUDA.
+ */
 ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters,
                      double* relres);
 
@@ -201,7 +201,10 @@ ddg_status ddg_solve_host(ddg_handle h, const double* f_host, double* u_host, do
  * Multi-RHS solve: F and U are device FP64 [n * m], dof-major.  Each column
  * runs its own CG (own alpha, beta, convergence); the preconditioner is
  * applied to all unconverged columns at once.  iters: host int[m] or NULL;
- * relres: host double[m] or NULL.
+ * relres: host double[m] or NULL.  With the FP64 preconditioner, a V-cycle
+ * handle or more than 32 generators per subdomain the columns are solved
+ * one at a time.  Errors: as ddg_solve (the worst column's status), and
+ * DDG_ETIMEOUT when a bounded wait of the tensor-core local solve ran out.
  */
 ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, double tol,
                            int* iters, double* relres);
