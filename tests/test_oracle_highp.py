@@ -71,3 +71,25 @@ def test_iterations_fall_with_p_and_beat_smaller_aggregates():
     F = di.aggregate_generators(prob.shape, prob.box, 6, p=1)
     res = orc.pcg(prob.A, prob.f, _oracle(prob, F).apply, tol=1e-8)
     assert res.converged and res.iters > its[3], (res.iters, its)
+
+
+def test_aggregates_must_tile_the_boxes():
+    import pytest
+    with pytest.raises(ValueError):
+        di.aggregate_generators((24, 24), (12, 12), 5, p=1)
+
+
+def test_bench_fractional_iterations_agree_with_the_oracle():
+    # bench.py reports the Sec. 7 fractional count from the library's
+    # residual history with its own helper; the oracle's definition decides
+    import bench
+    rng = np.random.default_rng(61)
+    for _ in range(20):
+        h = np.concatenate([[1.0], np.cumprod(10.0 ** -rng.uniform(0.2, 1.5, 12))])
+        tol = 10.0 ** -rng.uniform(2, 8)
+        ours = bench.fractional_iters(list(h), tol)
+        ref = orc.fractional_iterations(h, tol)
+        if np.isnan(ref):
+            assert ours is None
+        else:
+            assert abs(ours - ref) < 1e-12
