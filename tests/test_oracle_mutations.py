@@ -125,3 +125,25 @@ def test_unorthogonalised_basis_fails_orthonormality_pin():
             rows.append(v)
     R = np.array(rows)
     assert np.max(np.abs(R @ R.T - np.eye(R.shape[0]))) > 1e-3
+
+
+def test_transposed_band_storage_fails_sparse_direct_solve():
+    # The band branch of CoarseSolver with the upper band layout
+    # ab[b + j - i, i] (what LAPACK expects for lower=False) handed to the
+    # lower-band factorisation: the comparison with scipy's sparse LU
+    # (test_coarse_solver_banded_branch_matches_sparse_direct_solve) rejects it.
+    from scipy.sparse.linalg import spsolve
+    prob = di.make_biharmonic2d(N=48, box=16, overlap=2, p=3, seed=5)
+    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape)
+    C = M.A0.tocoo()
+    b = int(np.max(C.row - C.col))
+    ab = np.zeros((b + 1, M.A0.shape[0]))
+    up = C.row <= C.col
+    ab[b + C.row[up] - C.col[up], C.col[up]] = C.data[up]   # mistake: upper layout
+    c = np.random.default_rng(4).standard_normal(M.A0.shape[0])
+    ref = spsolve(M.A0.tocsc(), c)
+    try:
+        x = sla.cho_solve_banded((sla.cholesky_banded(ab, lower=True), True), c)
+    except np.linalg.LinAlgError:
+        return   # not even positive definite in that layout
+    assert np.abs(x - ref).max() > 1e-6 * np.abs(ref).max()
