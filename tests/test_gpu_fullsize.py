@@ -23,6 +23,7 @@ import numpy as np
 import pytest
 
 import ddg_inputs as di
+from closeness import assert_close
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -64,7 +65,7 @@ def test_poisson128_coarse_correction_reproduces_generators(poisson128):
     for j in (0, 3, 9):
         Fj = prob.F[:, j]
         z = s.coarse_correction(dev(prob.A @ Fj)).cpu().numpy()
-        assert rel(z, Fj) <= 1e-9, j
+        assert_close(z, Fj, 1e-9, label=str(j))
     s.set_precision("fp32")
 
 

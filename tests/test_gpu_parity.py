@@ -13,6 +13,7 @@ import pytest
 
 import ddg_inputs as di
 from oracle import ddg_oracle as orc
+from closeness import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -38,6 +39,13 @@ CASES = {
     # 66 generators per subdomain (p = 10, centred and scaled per subdomain):
     # the wide (96-column) QR and restriction kernels
     "biharmonic_p10_local": lambda: di.make_biharmonic2d(N=64, box=16, overlap=2, p=10, local=True),
+    # the benchmarks' full local-block shapes: Q1 elasticity 16^3 elements with
+    # 8-node boxes has a 3000-dof block (94 tile rows, about 47 bands, the
+    # row-parallel gather, the 4-CTA-per-SM shared-memory layout of the
+    # 64^3-element workload); variable coefficients 24^3 with 8^3 boxes have
+    # an interior block of 10^3 = 1000 dofs, as in the 96^3 batched workload
+    "elasticity_q1_16": lambda: di.make_elasticity3d(ne=16, box=8, overlap=1, p=2),
+    "varcoef_24": lambda: di.make_varcoef3d(N=24, box=8, overlap=1, p=2, m=None),
 }
 
 # FP64 building blocks agree to 1e-11 unless a subdomain's generator block
@@ -67,16 +75,12 @@ def dev(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
-
-
 @pytest.mark.parametrize("name", list(CASES))
 def test_spmv_matches_scipy(name):
     prob, solver, _ = setup_case(name)
     x = np.random.default_rng(5).standard_normal(prob.n)
     y = solver.spmv(dev(x)).cpu().numpy()
-    assert rel(y, prob.A @ x) <= 1e-14
+    assert_close(y, prob.A @ x, 1e-14)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -92,7 +96,7 @@ def test_coarse_correction_matches_oracle(name):
     solver.set_precision("fp64")
     r = np.random.default_rng(6).standard_normal(prob.n)
     z = solver.coarse_correction(dev(r)).cpu().numpy()
-    assert rel(z, oracle.coarse_correction(r)) <= FP64_TOL.get(name, 1e-11)
+    assert_close(z, oracle.coarse_correction(r), FP64_TOL.get(name, 1e-11))
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -101,18 +105,26 @@ def test_preconditioner_matches_oracle_fp64(name):
     solver.set_precision("fp64")
     r = np.random.default_rng(7).standard_normal(prob.n)
     z = solver.apply(dev(r)).cpu().numpy()
-    assert rel(z, oracle.apply(r)) <= FP64_TOL.get(name, 1e-11)
+    assert_close(z, oracle.apply(r), FP64_TOL.get(name, 1e-11))
 
 
-@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_24", "biharmonic_64", "varcoef_16"])
+# An FP32 inverse carries about cond(A_i) 2^-24 of relative error.  The
+# 3000-dof elasticity blocks reach cond(A_i) = 1563 (1563 * 2^-24 = 9.3e-5);
+# the scalar second-order blocks stay below 1e-5.
+@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_24", "biharmonic_64", "varcoef_16",
+                                  "varcoef_24", "elasticity_q1_16"])
 @pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("bf16", 3e-2)])
 def test_preconditioner_reduced_precision(name, prec, tol):
+    if name == "elasticity_q1_16":
+        if prec == "bf16":
+            pytest.skip("BF16 inverses of cond-1500 blocks: 2^-8 * 1563 > 1")
+        tol = 1e-4
     prob, solver, oracle = setup_case(name)
     solver.set_precision(prec)
     r = np.random.default_rng(8).standard_normal(prob.n)
     z = solver.apply(dev(r)).cpu().numpy()
     solver.set_precision("fp64")
-    assert rel(z, oracle.apply(r)) <= tol
+    assert_close(z, oracle.apply(r), tol)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -123,7 +135,7 @@ def test_solve_fp64_matches_oracle(name):
     ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
     u, iters, relres, st = solver.solve(dev(f), tol=1e-8)
     assert st == 0
-    assert rel(u.cpu().numpy(), ref.u) <= 1e-10
+    assert_close(u.cpu().numpy(), ref.u, 1e-10)
     assert abs(iters - ref.iters) <= 1
     assert relres <= 1e-8
     hist = solver.history()
@@ -135,8 +147,9 @@ def test_solve_fp64_matches_oracle(name):
 
 MIXED = [(n, "fp32") for n in ("poisson2d_64", "poisson3d_24", "poisson3d_ragged", "biharmonic_64",
                                  "varcoef_16", "twomaterial2d_aware_64", "twomaterial3d_aware_16",
-                                 "biharmonic_p10_local")]
-MIXED += [(n, "bf16") for n in ("poisson2d_64", "poisson3d_24", "poisson3d_ragged", "varcoef_16")]
+                                 "biharmonic_p10_local", "elasticity_q1_16", "varcoef_24")]
+MIXED += [(n, "bf16") for n in ("poisson2d_64", "poisson3d_24", "poisson3d_ragged", "varcoef_16",
+                                 "varcoef_24")]
 
 
 @pytest.mark.parametrize("name,prec", MIXED)
@@ -151,7 +164,7 @@ def test_solve_mixed_precision(name, prec):
     un = u.cpu().numpy()
     true_rel = np.linalg.norm(f - prob.A @ un) / np.linalg.norm(f)
     assert true_rel <= 1e-8 and relres <= 1e-8
-    assert rel(un, ref.u) <= 1e-7
+    assert_close(un, ref.u, 1e-7)
     assert iters <= ref.iters + 3
 
 
@@ -186,14 +199,15 @@ def test_batched_solve_matches_oracle_per_column(name, m, prec):
         assert true_rel <= 1e-8, (j, true_rel)
         if j < 3 or j == m - 1:
             ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
-            assert rel(Un[:, j], ref.u) <= 1e-7, j
+            assert_close(Un[:, j], ref.u, 1e-7, label=str(j))
             assert its[j] <= ref.iters + 3, (j, its[j], ref.iters)
 
 
 _tc_cache = {}
 
 
-@pytest.mark.parametrize("name,m", [("varcoef_16", 64), ("varcoef_16", 5), ("poisson3d_ragged", 33),
+@pytest.mark.parametrize("name,m", [("varcoef_16", 64), ("varcoef_24", 64), ("varcoef_16", 5),
+                                    ("poisson3d_ragged", 33),
                                     ("poisson2d_64", 16), ("poisson3d_graph", 48)])
 def test_batched_tensor_core_solve_matches_oracle(name, m):
     # tcgen05 BF16 local solves (residual and A_i^{-1} rounded to BF16, FP32
@@ -212,7 +226,7 @@ def test_batched_tensor_core_solve_matches_oracle(name, m):
         f = F[:, j]
         assert np.linalg.norm(f - prob.A @ Un[:, j]) / np.linalg.norm(f) <= 1e-8
         ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
-        assert rel(Un[:, j], ref.u) <= 1e-7, j
+        assert_close(Un[:, j], ref.u, 1e-7, label=str(j))
         assert its[j] <= ref.iters + 3, (j, its[j], ref.iters)
 
 
@@ -226,7 +240,7 @@ def test_batched_zero_column_and_single_solve_agree():
     for j in (0, 2):
         u, it, rr, st1 = solver.solve(dev(F[:, j]), tol=1e-9)
         assert abs(it - its[j]) <= 1
-        assert rel(Ub[:, j].cpu().numpy(), u.cpu().numpy()) <= 1e-8
+        assert_close(Ub[:, j].cpu().numpy(), u.cpu().numpy(), 1e-8)
     uh, ith, rrh, sth = solver.solve_host(F[:, 0], tol=1e-9)
     u0, it0, _, _ = solver.solve(dev(F[:, 0]), tol=1e-9)
     np.testing.assert_array_equal(uh, u0.cpu().numpy())
@@ -263,7 +277,7 @@ def test_solve_many_uneven_problems_concurrently():
         M = orc.DDGOracle(p.A, p.part, p.F, p.overlap, p.overlap_mode, p.shape, dpn=p.dofs_per_node)
         for j in range(F.shape[1]):
             ref = orc.pcg(M.A, F[:, j], M.apply, tol=1e-8)
-            assert rel(Un[:, j], ref.u) <= 1e-7
+            assert_close(Un[:, j], ref.u, 1e-7)
             assert its[k] <= ref.iters + 3
             k += 1
     for s in solvers:
@@ -307,7 +321,7 @@ def test_coarse_reproduces_generators_any_size():
     for j in (0, 4, 9):
         Fj = prob.F[:, j]
         z = solver.coarse_correction(dev(prob.A @ Fj)).cpu().numpy()
-        assert rel(z, Fj) <= 1e-10
+        assert_close(z, Fj, 1e-10)
 
 
 @pytest.mark.parametrize("name", ["poisson3d_24", "elasticity_q1_6"])
@@ -318,16 +332,16 @@ def test_many_chunk_gather_matches_oracle(name):
     prob, _, oracle = setup_case(name)
     s = ddg.Solver.from_problem(prob, precision="fp64", keep=("fp64", "fp32"), chunk_tiles=4)
     r = np.random.default_rng(9).standard_normal(prob.n)
-    assert rel(s.apply(dev(r)).cpu().numpy(), oracle.apply(r)) <= 1e-11
+    assert_close(s.apply(dev(r)).cpu().numpy(), oracle.apply(r), 1e-11)
     s.set_precision("fp32")
-    assert rel(s.apply(dev(r)).cpu().numpy(), oracle.apply(r)) <= 1e-5
+    assert_close(s.apply(dev(r)).cpu().numpy(), oracle.apply(r), 1e-5)
     ref = orc.pcg(oracle.A, prob.f, oracle.apply, tol=1e-8)
     for prec, tol in (("fp64", 1e-10), ("fp32", 1e-7)):
         s.set_precision(prec)
         u, it, rr, st = s.solve(dev(prob.f), tol=1e-8)
         u2 = s.solve(dev(prob.f), tol=1e-8)[0]
         assert st == 0 and abs(it - ref.iters) <= 1
-        assert rel(u.cpu().numpy(), ref.u) <= tol
+        assert_close(u.cpu().numpy(), ref.u, tol)
         assert torch.equal(u, u2)
     s.close()
 

@@ -11,6 +11,7 @@ import pytest
 
 import ddg_inputs as di
 from oracle import ddg_oracle as orc
+from closeness import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -50,10 +51,6 @@ def dev(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
-
-
 def rhs(prob):
     return prob.f if prob.f.ndim == 1 else prob.f[:, 0]
 
@@ -72,7 +69,7 @@ def test_vcycle_coarse_correction_matches_oracle(name):
     solver.set_precision("fp64")
     r = np.random.default_rng(50).standard_normal(prob.n)
     z = solver.coarse_correction(dev(r)).cpu().numpy()
-    assert rel(z, oracle.coarse_correction(r)) <= 1e-11
+    assert_close(z, oracle.coarse_correction(r), 1e-11)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -81,7 +78,7 @@ def test_vcycle_preconditioner_matches_oracle_fp64(name):
     solver.set_precision("fp64")
     r = np.random.default_rng(51).standard_normal(prob.n)
     z = solver.apply(dev(r)).cpu().numpy()
-    assert rel(z, oracle.apply(r)) <= 1e-11
+    assert_close(z, oracle.apply(r), 1e-11)
 
 
 # FP32 tolerance: the normwise error of a solve with an FP32 inverse is about
@@ -97,7 +94,7 @@ def test_vcycle_preconditioner_reduced_precision(name, prec, tol):
     r = np.random.default_rng(52).standard_normal(prob.n)
     z = solver.apply(dev(r)).cpu().numpy()
     solver.set_precision("fp64")
-    assert rel(z, oracle.apply(r)) <= tol
+    assert_close(z, oracle.apply(r), tol)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -108,7 +105,7 @@ def test_vcycle_solve_fp64_matches_oracle(name):
     ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
     u, iters, relres, st = solver.solve(dev(f), tol=1e-8)
     assert st == 0 and relres <= 1e-8
-    assert rel(u.cpu().numpy(), ref.u) <= 1e-10
+    assert_close(u.cpu().numpy(), ref.u, 1e-10)
     assert abs(iters - ref.iters) <= 1
     hist = solver.history()
     m = min(hist.size, ref.history.size)
@@ -128,7 +125,7 @@ def test_vcycle_solve_mixed_precision(name, prec):
     assert st == 0
     un = u.cpu().numpy()
     assert np.linalg.norm(f - prob.A @ un) / np.linalg.norm(f) <= 1e-8
-    assert rel(un, ref.u) <= 1e-7
+    assert_close(un, ref.u, 1e-7)
     assert iters <= ref.iters + 3
 
 
@@ -153,7 +150,7 @@ def test_vcycle_one_group_equals_two_level_on_gpu():
     z2, z3 = s2.apply(r).cpu().numpy(), s3.apply(r).cpu().numpy()
     s2.close()
     s3.close()
-    assert rel(z3, z2) <= 1e-11
+    assert_close(z3, z2, 1e-11)
 
 
 def test_vcycle_batch_solves_columns_one_at_a_time():
@@ -165,7 +162,7 @@ def test_vcycle_batch_solves_columns_one_at_a_time():
     for j in range(3):
         u, it, rr, st1 = solver.solve(dev(F[:, j]), tol=1e-8)
         assert st1 == 0 and it == its[j]
-        assert rel(U[:, j].cpu().numpy(), u.cpu().numpy()) <= 1e-14
+        assert_close(U[:, j].cpu().numpy(), u.cpu().numpy(), 1e-14)
     solver.set_precision("fp64")
 
 
