@@ -501,7 +501,7 @@ def elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, w
     def step():
         u, it, rr, st = solver.solve(b, TOL)
         g = (u - ut).contiguous()
-        lam, ita, rra = solver.adjoint(g, TOL)
+        lam, ita, rra, _ = solver.adjoint(g, TOL)
         dmu = solver.grad_coeff(lam, u)
         return u, lam, dmu, (it, rr, st), (ita, rra)
 
@@ -528,7 +528,7 @@ def elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, w
     e0.record(stream)
     u, it_f, rr_f, st_f = solver.solve(b, TOL)
     e1.record(stream)
-    lam, it_a, rr_a = solver.adjoint((u - ut).contiguous(), TOL)
+    lam, it_a, rr_a, _ = solver.adjoint((u - ut).contiguous(), TOL)
     e2.record(stream)
     solver.grad_coeff(lam, u)
     e3.record(stream)

@@ -27,7 +27,10 @@
  *     calls that return scalars synchronise that stream before returning.
  *   - Vectors are FP64, natural (caller) dof order, length n.  Multi-RHS
  *     blocks are dof-major: entry (dof g, rhs j) at g * m + j.
- *   - One handle must not be used from two host threads at once.
+ *   - One handle must not be used from two host threads at once.  A handle
+ *     remembers the device that was current at its setup and makes it
+ *     current for the duration of every call on it, so it may be called
+ *     from any host thread.
  */
 #ifndef DDG_H
 #define DDG_H
@@ -46,8 +49,11 @@ typedef enum {
     DDG_ENOMEM = 2,       /* device allocation failed */
     DDG_ENOTSPD = 3,      /* a local or the coarse Cholesky met a non-positive pivot */
     DDG_EBREAKDOWN = 4,   /* CG breakdown: p^T A p <= 0 or a NaN */
-    DDG_ENOCONV = 5,      /* maxit reached; u holds the last iterate */
-    DDG_ETIMEOUT = 6,     /* a bounded device wait ran out (the result is not valid) */
+    DDG_ENOCONV = 5,      /* maxit reached, or the recurrence met tol but the true
+                             residual stayed above it after 3 restarts of CG from the
+                             true residual; u holds the last iterate */
+    DDG_ETIMEOUT = 6,     /* a bounded device wait ran out (spin_budget_ms); the
+                             result is not valid, the handle stays usable */
     DDG_ECUDA = 7         /* a CUDA runtime call failed */
 } ddg_status;
 
@@ -93,6 +99,10 @@ typedef struct {
                              entry (rows and columns in ascending dof order) share one
                              stored inverse (constant-coefficient problems: the
                              interior subdomains); the results do not change; default 0 */
+    double spin_budget_ms; /* time limit of every device-side wait (the mbarrier waits
+                             of the tensor-core local solve), measured on the GPU's
+                             global timer; a wait that runs out makes the call return
+                             DDG_ETIMEOUT; default 1000 (0 also means 1000) */
 } ddg_options;
 
 typedef struct {
@@ -184,10 +194,13 @@ ddg_status ddg_set_generators(ddg_handle h, const double* F, int k);
  * Solve A u = f by PCG from u0 = 0 (Sec. 7): stop when the recurrence
  * residual satisfies ||r||_2 <= tol ||f||_2 and the true residual does too
  * (a recurrence that drifts is replaced by the true residual and CG
- * restarts).  f, u: device FP64 [n].  *iters: iterations taken; *relres:
- * true relative residual ||f - A u|| / ||f||.  Either output may be NULL.
- * Errors: DDG_ENOCONV (maxit reached, u is the last iterate),
- * DDG_EBREAKDOWN, DDG_EINVAL, DDG_ECUDA.
+ * restarts, at most 3 times).  f, u: device FP64 [n], distinct buffers (u is
+ * cleared before f is read, so f == u is rejected with DDG_EINVAL).
+ * *iters: iterations taken; *relres: true relative residual
+ * ||f - A u|| / ||f||.  Either output may be NULL.
+ * Errors: DDG_ENOCONV (maxit reached, or the true residual still above tol
+ * after the third restart; u is the last iterate and ddg_last_error says
+ * which), DDG_EBREAKDOWN, DDG_EINVAL, DDG_ECUDA.
  */
 ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters,
                      double* relres);
@@ -222,7 +235,8 @@ ddg_status ddg_solve_many(ddg_handle* hs, int nprob, const double* const* F, dou
                           const int* m, double tol, int* iters, double* relres);
 
 /* Adjoint solve lambda = A^{-T} g for a loss gradient g = dL/du (device
- * [n]); A is symmetric, so this reuses the preconditioner and CG. */
+ * [n], distinct from lambda); A is symmetric, so this reuses the
+ * preconditioner and CG.  Statuses as ddg_solve. */
 ddg_status ddg_adjoint(ddg_handle h, const double* dLdu, double* lambda, double tol,
                        int* iters, double* relres);
 
@@ -242,6 +256,15 @@ ddg_status ddg_coarse_correction(ddg_handle h, const double* r, double* z);
 
 /* y = A x in FP64 (device [n]). */
 ddg_status ddg_spmv(ddg_handle h, const double* x, double* y);
+
+/* Test hooks of the bounded device waits (the paper has no counterpart).
+ * DDG_DEBUG_TC_NO_COPIES: the producer thread of the tensor-core local solve
+ * issues no copies, so no copy is in flight and the MMA thread's first wait
+ * runs out after spin_budget_ms; the kernel records the timeout, frees its
+ * tensor memory and returns, and ddg_solve_batch returns DDG_ETIMEOUT.
+ * flags = 0 restores normal operation. */
+enum { DDG_DEBUG_TC_NO_COPIES = 1 };
+ddg_status ddg_set_debug(ddg_handle h, int flags);
 
 /* Switch the preconditioner precision (must be among keep_precisions). */
 ddg_status ddg_set_precision(ddg_handle h, int precision);

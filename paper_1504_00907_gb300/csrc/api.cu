@@ -243,6 +243,8 @@ void validate(const ddg_matrix* A, const int32_t* part, const double* F, int k, 
         DDG_REQUIRE(k >= 1 && k <= DDG_KMAX, DDG_EINVAL, "k must be in [1, 96]");
     }
     DDG_REQUIRE(o.maxit >= 1, DDG_EINVAL, "maxit must be >= 1");
+    DDG_REQUIRE(o.spin_budget_ms >= 0.0 && o.spin_budget_ms <= 3.6e6, DDG_EINVAL,
+                "spin_budget_ms must be in [0, 3.6e6]");
 }
 
 // ---------------------------------------------------------------- preconditioner
@@ -441,6 +443,9 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
             true_rel = std::sqrt(h->h_scal[S_TMP]) / fn;
             if (true_rel <= tol || restarts >= 3) {
                 st = true_rel <= tol ? DDG_OK : DDG_ENOCONV;
+                if (st != DDG_OK)
+                    h->err = "the recurrence residual met tol but the true residual stayed above it "
+                             "after 3 restarts of CG from the true residual";
                 break;
             }
             DDG_CUDA(cudaMemcpyAsync(h->r, h->q, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -454,6 +459,7 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
         ddg::cg_dots_after_precond(h, prec, false, pr);
         ddg::cg_update_p(h, prec, false);
     }
+    if (st == DDG_ENOCONV && h->err.empty()) h->err = "maxit iterations reached";
     if (true_rel < 0.0) {
         ProfScope ps(h, DDG_K_CG, 2, 0.0);
         ddg::residual64(h, f, u, h->q);
@@ -493,9 +499,18 @@ ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol
     const int beta = h->opt.beta == DDG_BETA_AUTO ? DDG_BETA_PR : h->opt.beta;
     const int pr = beta == DDG_BETA_PR;
     std::vector<double> sc(S_COUNT * DDG_MCHUNK);
+    int32_t timed_out = 0;
+    // the scalars of every column, and the timeout flag of the bounded waits
+    // of the tensor-core local solve: a solve whose wait ran out stops here
     auto read_sc = [&]() {
         d2h(sc.data(), w.scal, sc.size(), h->stream);
+        d2h(&timed_out, h->errflags + E_TIMEOUT, 1, h->stream);
         DDG_CUDA(cudaStreamSynchronize(h->stream));
+        if (timed_out) {
+            DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
+            throw DdgError{DDG_ETIMEOUT, "a bounded wait of the tensor-core local solve ran out"};
+        }
     };
     auto at = [&](int slot, int c) { return sc[slot * DDG_MCHUNK + c]; };
     DDG_CUDA(cudaMemsetAsync(w.scal, 0, S_COUNT * DDG_MCHUNK * sizeof(double), h->stream));
@@ -624,9 +639,24 @@ ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol
     return worst;
 }
 
+// Makes `dev` the calling thread's current device for the lifetime of the
+// object and restores the previous one afterwards (a handle's streams,
+// kernels and memory belong to the device that was current at its setup).
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int dev) {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 template <typename Fn>
 ddg_status guarded(ddg_handle h, Fn&& fn) {
     if (!h) return DDG_EINVAL;
+    DeviceScope scope(h->device);
     try {
         h->err.clear();
         return fn();
@@ -683,6 +713,7 @@ void ddg_default_options(ddg_options* o) {
     o->use_coarse = 1;
     o->rank_tol = 1e-10;
     o->chunk_tiles = 0;
+    o->spin_budget_ms = 1000.0;
 }
 
 }  // extern "C"
@@ -816,6 +847,8 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         }
         h->opt = o;
         h->precision = o.precision;
+        DDG_CUDA(cudaGetDevice(&h->device));
+        h->wait_ns = (unsigned long long)((o.spin_budget_ms > 0.0 ? o.spin_budget_ms : 1000.0) * 1e6);
         if (const char* ev = std::getenv("DDG_NO_GRAPHS")) h->use_graphs = ev[0] == '0';
         if (const char* ev = std::getenv("DDG_PDL")) h->use_pdl = ev[0] != '0';
         h->use_coarse = o.use_coarse;
@@ -1212,23 +1245,18 @@ void setup_vcycle(ddg_handle h, const double* F, int k, int overlap, const ddg_o
     blk.shrink_to_fit();
 
     // F0 = R0 F: row (I, s) is q_{I,s}^T F on the non-overlapping subdomain I
-    std::vector<double> Q((size_t)n * kmax);
-    d2h(Q.data(), h->Q64, Q.size(), h->stream);
-    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    // (computed on the device; the coarse level's setup reads it on the host)
     std::vector<double> F0((size_t)n0 * k, 0.0);
-    for (int I = 0; I < nsub; ++I) {
-        const int kI = coff[I + 1] - coff[I];
-        for (int64_t a = sub_off[I]; a < sub_off[I + 1]; ++a) {
-            const int64_t g = sub_nodes[a];
-            for (int s = 0; s < kI; ++s) {
-                const double q = Q[(size_t)a * kmax + s];
-                double* row = F0.data() + coff[I] + s;
-                for (int j = 0; j < k; ++j) row[(size_t)j * n0] += q * F[(size_t)j * n + g];
-            }
-        }
+    {
+        double* dF = h->arena.alloc<double>((size_t)n * k);
+        double* dF0 = h->arena.alloc<double>((size_t)n0 * k);
+        h2d(dF, F, (size_t)n * k, h->stream);
+        ddg::coarse_generators(h, dF, k, dF0);
+        d2h(F0.data(), dF0, F0.size(), h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        h->arena.release(dF);
+        h->arena.release(dF0);
     }
-    Q.clear();
-    Q.shrink_to_fit();
 
     // coarse dof -> coarse-level subdomain, ids compacted in ascending order
     std::vector<int32_t> ids;
@@ -1327,6 +1355,8 @@ ddg_status ddg_set_generators(ddg_handle h, const double* F, int k) {
 ddg_status ddg_solve(ddg_handle h, const double* f, double* u, double tol, int* iters, double* relres) {
     return guarded(h, [&]() {
         DDG_REQUIRE(f && u, DDG_EINVAL, "f and u must be non-null device pointers");
+        DDG_REQUIRE((const void*)f != (const void*)u, DDG_EINVAL,
+                    "f and u must not alias (u is cleared before f is read)");
         DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
         return pcg(h, f, u, tol, iters, relres);
     });
@@ -1469,6 +1499,14 @@ ddg_status ddg_spmv(ddg_handle h, const double* x, double* y) {
         DDG_REQUIRE(x && y, DDG_EINVAL, "null pointer");
         ddg::spmv64(h, x, y, false, 0);
         DDG_CUDA(cudaStreamSynchronize(h->stream));
+        return DDG_OK;
+    });
+}
+
+ddg_status ddg_set_debug(ddg_handle h, int flags) {
+    return guarded(h, [&]() {
+        DDG_REQUIRE((flags & ~DDG_DEBUG_TC_NO_COPIES) == 0, DDG_EINVAL, "unknown debug flag");
+        h->debug = flags;
         return DDG_OK;
     });
 }
@@ -1637,6 +1675,7 @@ ddg_status ddg_get_kernel_stats(ddg_handle h, ddg_kernel_stat* st) {
 
 ddg_status ddg_destroy(ddg_handle h) {
     if (!h) return DDG_OK;
+    DeviceScope scope(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->inner) ddg_destroy(h->inner);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -59,6 +60,26 @@ struct DdgError {
     do {                                               \
         if (!(cond)) throw DdgError{status, (text)};   \
     } while (0)
+
+// A kernel attribute (cudaFuncSetAttribute) is set per device: the largest
+// value set so far on each device, so that every device is configured once
+// and a value is never lowered.
+struct PerDeviceMax {
+    std::mutex mu;
+    int value[64] = {};
+    // true when `want` exceeds the value recorded for the current device (the
+    // caller then sets the attribute and calls commit)
+    bool needs(int want, int& dev) {
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = -1;
+        std::lock_guard<std::mutex> lock(mu);
+        return dev < 0 || want > value[dev];
+    }
+    void commit(int dev, int want) {
+        if (dev < 0) return;
+        std::lock_guard<std::mutex> lock(mu);
+        if (want > value[dev]) value[dev] = want;
+    }
+};
 
 // device allocation helper: every allocation is recorded for ddg_destroy
 struct DevArena {
@@ -182,6 +203,9 @@ struct ddg_handle_s {
     std::string err;
     int precision = DDG_PREC_FP64;
     double setup_ms = 0.0;
+    int device = 0;                 // CUDA device current at setup; made current by every call
+    int debug = 0;                  // DDG_DEBUG_* test hooks (ddg_set_debug)
+    unsigned long long wait_ns = 1000000000ull;   // limit of every device-side wait
 
     // ---- fine problem
     int64_t n = 0, nnz = 0;
@@ -336,6 +360,8 @@ void coarse_assemble_band(ddg_handle h, const std::vector<int>& blk_I, const std
 void coarse_assemble_blocks(ddg_handle h, const std::vector<int>& blk_I, const std::vector<int>& blk_J,
                             std::vector<double>& blocks);
 void coarse_band_cholesky(ddg_handle h);
+// F0 = R0 F (device, column-major [n0][k]) from F (device, column-major [n][k])
+void coarse_generators(ddg_handle h, const double* dF, int k, double* dF0);
 void coarse_build_apply(ddg_handle h);
 void coarse_restrict(ddg_handle h, int prec, bool residual);
 void coarse_solve(ddg_handle h, int prec);

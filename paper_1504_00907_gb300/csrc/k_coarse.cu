@@ -602,9 +602,34 @@ __global__ void coarse_prolong_kernel(int64_t n, const int32_t* __restrict__ par
     z[g] += acc;
 }
 
+// Sec. 6, three-level V-cycle: the coarsened generators F0 = R0 F.  Row
+// (I, s) of F0 is q_{I,s}^T F restricted to the subdomain I: one CTA per
+// subdomain, one thread per (s, j), summing over the subdomain's nodes in
+// position order.  F column-major [n][k], F0 column-major [n0][k].
+__global__ void __launch_bounds__(256) coarse_generators_kernel(
+    const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
+    const int32_t* __restrict__ coff, const double* __restrict__ Q, int kmax,
+    const double* __restrict__ F, int64_t n, int k, int n0, double* __restrict__ F0) {
+    const int I = blockIdx.x;
+    const int c0 = coff[I], kI = coff[I + 1] - c0;
+    const int64_t a0 = sub_off[I], a1 = sub_off[I + 1];
+    for (int e = threadIdx.x; e < kI * k; e += blockDim.x) {
+        const int s = e % kI, j = e / kI;
+        double acc = 0.0;
+        for (int64_t a = a0; a < a1; ++a) acc = fma(Q[a * kmax + s], F[(int64_t)j * n + sub_nodes[a]], acc);
+        F0[(int64_t)j * n0 + c0 + s] = acc;
+    }
+}
+
 }  // namespace
 
 namespace ddg {
+
+void coarse_generators(ddg_handle h, const double* dF, int k, double* dF0) {
+    coarse_generators_kernel<<<h->nsub, 256, 0, h->stream>>>(h->sub_off, h->sub_nodes, h->coff, h->Q64,
+                                                             h->kmax, dF, h->n, k, h->n0, dF0);
+    DDG_CHECK_LAUNCH();
+}
 
 void coarse_qr(ddg_handle h, int32_t* d_rank, const double* dF, int k) {
     auto qr = h->kmax <= 32 ? coarse_qr_kernel<32> : coarse_qr_kernel<DDG_KMAX>;

@@ -717,18 +717,20 @@ static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, 
     }
 }
 
-// The dynamic shared-memory limit is a property of the kernel, shared by all
-// handles: raise it to the largest size any handle needs, never lower it.
+// The dynamic shared-memory limit is a property of the kernel on each device,
+// shared by all handles there: raise it to the largest size any handle on
+// that device needs, never lower it.
 template <typename E, typename V>
 static void configure_local_solve(int Tmax) {
-    static int configured = 0;
+    static PerDeviceMax configured;
     const int smem = (int)local_solve_smem<V>(Tmax);
-    if (smem <= configured) return;
+    int dev = -1;
+    if (!configured.needs(smem, dev)) return;
     DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, false>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    configured = smem;
+    configured.commit(dev, smem);
 }
 
 void local_configure(ddg_handle h) {

@@ -943,11 +943,13 @@ static void multi_apply_t(ddg_handle h, int m) {
             attr[0].val.programmaticStreamSerializationAllowed = h->use_pdl ? 1 : 0;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            static bool configured = false;
-            if (!configured) {
+            static PerDeviceMax configured;   // the attribute is per device
+            const int smax = (int)(CG_KS * DDG_MCHUNK * sizeof(float));
+            int dev = -1;
+            if (configured.needs(smax, dev)) {
                 DDG_CUDA(cudaFuncSetAttribute(coarse_step_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(CG_KS * DDG_MCHUNK * sizeof(float))));
-                configured = true;
+                                              smax));
+                configured.commit(dev, smax);
             }
             const CoarseStep S{M.rowptr, M.lo, M.hi, M.v32, r0, cbase, x, a, sign, out};
             DDG_CUDA(cudaLaunchKernelEx(&cfg, coarse_step_multi_kernel, S, B, m, nsplit, w.gpart, w.gtick));

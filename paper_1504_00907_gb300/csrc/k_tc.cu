@@ -14,8 +14,11 @@
 //                 accumulator and commits each stage back to the producer;
 //   warps 0-3     read their 32 TMEM lanes (tcgen05.ld 32x32b) and add the
 //                 rows into z.
-// Every wait is bounded: a wait that runs out sets the error flag, the kernel
-// drains its own copies (bounded), frees its TMEM and returns.
+// Every wait is bounded by a time limit on the GPU's global timer (the
+// handle's spin_budget_ms): a wait that runs out sets the error flag, the
+// kernel drains the copies it has issued (each of them completes, since it
+// reads valid global memory; the drain still has a limit of its own, four
+// times the budget), frees its TMEM and returns.
 #include "ddg_internal.cuh"
 #include "dev_common.cuh"
 
@@ -25,7 +28,6 @@ constexpr int TC_M = 128;            // rows of Y per CTA (MMA M)
 constexpr int TC_K = 32;             // K per slab (two K = 16 MMAs)
 constexpr int TC_STAGES = 4;           // ring depth (measured against 3, 5, 6 and 8)
 constexpr int TC_THREADS = 128;
-constexpr uint32_t TC_POLLS = 1u << 22;   // bounded mbarrier polls
 constexpr int A_SLAB = TC_M * TC_K;       // elements per A slab
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -40,12 +42,27 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
     return d;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `bar` with the given parity to complete, for at most
+// `limit_ns` nanoseconds of the global timer (checked every 64 polls; a
+// poll count of 2^31 ends the wait as well, should the timer not advance).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     uint32_t ok = 0;
-    for (uint32_t i = 0; i < TC_POLLS; ++i) {
+    uint64_t t0 = 0;
+    for (uint32_t i = 0; i < (1u << 31); ++i) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(ok) : "r"(sa(bar)), "r"(parity) : "memory");
         if (ok) return true;
+        if ((i & 63) == 0) {
+            const uint64_t t = global_ns();
+            if (i == 0) t0 = t;
+            else if (t - t0 > limit_ns) return false;
+        }
     }
     return false;
 }
@@ -67,7 +84,7 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
     const int32_t* __restrict__ ov_nodes, const int32_t* __restrict__ Tq,
     const int64_t* __restrict__ slab_off, const int64_t* __restrict__ xoff,
     const __nv_bfloat16* __restrict__ Aslab, const __nv_bfloat16* __restrict__ Xslab,
-    float* __restrict__ z, int m, int* err) {
+    float* __restrict__ z, int m, int* err, uint64_t limit_ns, int no_copies) {
     constexpr int X_SLAB = N * TC_K;
     constexpr uint32_t A_BYTES = A_SLAB * 2, X_BYTES = X_SLAB * 2, STAGE = A_BYTES + X_BYTES;
     constexpr uint32_t TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
@@ -106,10 +123,10 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
     const uint32_t tmem = *tslot;
 
     int issued = 0;   // stages handed to the copy engine (producer only)
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !no_copies) {
         for (int J = 0; J < T; ++J) {
             const int s = J % TC_STAGES;
-            if (J >= TC_STAGES && !mbar_wait(&empty[s], ((J / TC_STAGES) - 1) & 1)) {
+            if (J >= TC_STAGES && !mbar_wait(&empty[s], ((J / TC_STAGES) - 1) & 1, limit_ns)) {
                 failed = 1;
                 break;
             }
@@ -129,7 +146,7 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
         bool ok = true;
         for (int J = 0; J < T; ++J) {
             const int s = J % TC_STAGES;
-            if (!mbar_wait(&full[s], (J / TC_STAGES) & 1)) {
+            if (!mbar_wait(&full[s], (J / TC_STAGES) & 1, limit_ns)) {
                 ok = false;
                 break;
             }
@@ -155,7 +172,7 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
     // polling `done` beside their role thread
     __syncwarp();
     // epilogue: TMEM lanes [32 w, 32 w + 32) hold rows blk * 128 + 32 w + lane
-    const bool have = mbar_wait(done, 0);
+    const bool have = mbar_wait(done, 0, limit_ns);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!have) failed = 1;
     __syncthreads();
@@ -198,10 +215,12 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
         }
     } else if (threadIdx.x == 0) {
         atomicExch(err, 1);
-        // drain the copies this CTA still has in flight before its shared
-        // memory goes away (bounded)
+        // drain every copy this CTA has issued and that may still be in
+        // flight (the last TC_STAGES stages: an earlier stage was consumed by
+        // an MMA before its slot was refilled) before the shared memory goes
+        // away; issued copies complete, the limit only guards the wait itself
         for (int J = (issued > TC_STAGES ? issued - TC_STAGES : 0); J < issued; ++J)
-            mbar_wait(&full[J % TC_STAGES], (J / TC_STAGES) & 1);
+            mbar_wait(&full[J % TC_STAGES], (J / TC_STAGES) & 1, 4 * limit_ns);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -386,11 +405,12 @@ __global__ void __launch_bounds__(256) tc_residual_kernel(
 
 template <int N>
 void configure_tc() {
-    static bool done = false;
-    if (done) return;
+    static PerDeviceMax configured;   // the attribute is per device
     const int smem = TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+    int dev = -1;
+    if (!configured.needs(smem, dev)) return;
     DDG_CUDA(cudaFuncSetAttribute(local_solve_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    done = true;
+    configured.commit(dev, smem);
 }
 
 template <int N>
@@ -399,7 +419,8 @@ void launch_tc(ddg_handle h, int i0, int i1, int m) {
     const int smem = TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
     local_solve_tc_kernel<N><<<i1 - i0, TC_THREADS, smem, h->stream>>>(
         h->tc.items, i0, h->ov_off, h->ov_nodes, h->Tq, h->tc.slab_off, h->tc.xoff, h->tc.A, h->tc.X,
-        h->mw.z32, m, h->errflags + E_TIMEOUT);
+        h->mw.z32, m, h->errflags + E_TIMEOUT, (uint64_t)h->wait_ns,
+        (h->debug & DDG_DEBUG_TC_NO_COPIES) ? 1 : 0);
     DDG_CHECK_LAUNCH();
 }
 

@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ddg.h")
 
 # status codes and enums (mirror include/ddg.h)
 DDG_OK, DDG_EINVAL, DDG_ENOMEM, DDG_ENOTSPD, DDG_EBREAKDOWN, DDG_ENOCONV, DDG_ETIMEOUT, DDG_ECUDA = range(8)
+DDG_DEBUG_TC_NO_COPIES = 1
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 OVERLAP = {"graph": 0, "box": 1}
 BETA = {"fr": 0, "pr": 1, "auto": 2}
@@ -35,7 +36,7 @@ class Options(ctypes.Structure):
                 ("overlap_mode", ctypes.c_int), ("beta", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("use_coarse", ctypes.c_int), ("rank_tol", ctypes.c_double),
                 ("chunk_tiles", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("dedup_local", ctypes.c_int)]
+                ("dedup_local", ctypes.c_int), ("spin_budget_ms", ctypes.c_double)]
 
 
 class Matrix(ctypes.Structure):
@@ -84,6 +85,7 @@ _SIGS = {
     "ddg_coarse_correction": (_I, [_P, _P, _P]),
     "ddg_spmv": (_I, [_P, _P, _P]),
     "ddg_set_precision": (_I, [_P, _I]),
+    "ddg_set_debug": (_I, [_P, _I]),
     "ddg_set_stream": (_I, [_P, _P]),
     "ddg_get_info": (_I, [_P, ctypes.POINTER(Info)]),
     "ddg_get_colouring": (_I, [_P, _P]),
@@ -177,7 +179,7 @@ class Solver:
     def __init__(self, A, part, F, overlap, *, mode="graph", shape=None, stencil_kind=0,
                  coef=None, dofs_per_node=1, precision="fp64", keep=None, beta="auto",
                  maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
-                 stream=None, coarse_groups=None, dedup_local=False):
+                 stream=None, coarse_groups=None, dedup_local=False, spin_budget_ms=1000.0):
         import torch
         lib = load()
         if not torch.cuda.is_available():
@@ -217,6 +219,7 @@ class Solver:
         o.chunk_tiles = chunk_tiles
         o.tensor_cores = 1 if tensor_cores else 0
         o.dedup_local = 1 if dedup_local else 0
+        o.spin_budget_ms = spin_budget_ms
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
@@ -304,6 +307,8 @@ class Solver:
         return U, its, rr, st
 
     def adjoint(self, g, tol=1e-8):
+        """lambda = A^{-1} g; returns (lambda, iterations, true relative
+        residual, status) like ``solve`` (DDG_ENOCONV is returned, not raised)."""
         import torch
         lam = torch.empty_like(g)
         it, rr = ctypes.c_int(0), ctypes.c_double(0.0)
@@ -311,7 +316,7 @@ class Solver:
                                 ctypes.byref(it), ctypes.byref(rr))
         if st not in (DDG_OK, DDG_ENOCONV):
             _check(st, self.h)
-        return lam, it.value, rr.value
+        return lam, it.value, rr.value, st
 
     def grad_coeff(self, lam, u):
         """dL/dc for the coefficient array c given at setup (kappa per cell
@@ -340,6 +345,10 @@ class Solver:
         y = torch.empty_like(x)
         _check(load().ddg_spmv(self.h, _dev(x, self.n, "x"), _dev(y, self.n)), self.h)
         return y
+
+    def set_debug(self, flags):
+        """Test hooks of the bounded device waits (DDG_DEBUG_*; 0 = off)."""
+        _check(load().ddg_set_debug(self.h, int(flags)), self.h)
 
     def set_precision(self, precision):
         _check(load().ddg_set_precision(self.h, PREC[precision]), self.h)
@@ -453,11 +462,22 @@ def solve_autograd(solver, kappa, f, tol=1e-10):
 
     ``solver`` must have been set up with coefficients ``c`` (the cell
     conductivities kappa of a variable-coefficient handle, or the element
-    shear moduli mu of a Q1-elasticity handle).  The forward solve and the
-    adjoint solve both run through the library; the backward returns
-    dL/df = lambda and dL/dc = -lambda^T (dA/dc) u (``ddg_grad_coeff``).
+    shear moduli mu of a Q1-elasticity handle), and ``kappa`` must hold those
+    same values: the handle's matrix and preconditioner are built from them,
+    so a different ``kappa`` (after an optimiser step, say) raises ValueError
+    instead of returning the solution and gradient of the old matrix; set up
+    a new Solver for new coefficients.  The forward solve and the adjoint
+    solve both run through the library; the backward returns dL/df = lambda
+    and dL/dc = -lambda^T (dA/dc) u (``ddg_grad_coeff``).  Both directions
+    raise DDGError unless their solve converged.
     """
     import torch
+
+    if solver._coef is None:
+        raise ValueError("the solver was set up without coefficients (coef=None)")
+    given = kappa.detach().to("cpu", torch.float64).reshape(-1)
+    if given.numel() != solver._coef.size or not torch.equal(given, torch.from_numpy(solver._coef)):
+        raise ValueError("kappa differs from the coefficients the solver was set up with")
 
     class _DDGSolve(torch.autograd.Function):
         @staticmethod
@@ -471,7 +491,9 @@ def solve_autograd(solver, kappa, f, tol=1e-10):
         @staticmethod
         def backward(ctx, gu):
             (u,) = ctx.saved_tensors
-            lam, _, _ = solver.adjoint(gu.contiguous(), tol)
+            lam, _, _, st = solver.adjoint(gu.contiguous(), tol)
+            if st != DDG_OK:
+                raise DDGError(st, "adjoint solve did not converge")
             dk = solver.grad_coeff(lam, u)
             return dk.view_as(kappa), lam
 

@@ -37,8 +37,9 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\\n", sizeof(ddg_options), offsetof(ddg_options, rank_tol),
          offsetof(ddg_options, chunk_tiles), offsetof(ddg_options, tensor_cores), sizeof(ddg_matrix));
-  printf("%zu %zu %zu %zu %zu\\n", offsetof(ddg_matrix, coef), sizeof(ddg_info), offsetof(ddg_info, setup_ms),
-         offsetof(ddg_info, local_inverses), offsetof(ddg_options, dedup_local));
+  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(ddg_matrix, coef), sizeof(ddg_info), offsetof(ddg_info, setup_ms),
+         offsetof(ddg_info, local_inverses), offsetof(ddg_options, dedup_local),
+         offsetof(ddg_options, spin_budget_ms));
   return 0;
 }
 """)
@@ -48,7 +49,8 @@ int main(void) {
     got = [int(x) for x in out]
     exp = [ctypes.sizeof(ddg.Options), ddg.Options.rank_tol.offset, ddg.Options.chunk_tiles.offset,
            ddg.Options.tensor_cores.offset, ctypes.sizeof(ddg.Matrix), ddg.Matrix.coef.offset, ctypes.sizeof(ddg.Info),
-           ddg.Info.setup_ms.offset, ddg.Info.local_inverses.offset, ddg.Options.dedup_local.offset]
+           ddg.Info.setup_ms.offset, ddg.Info.local_inverses.offset, ddg.Options.dedup_local.offset,
+           ddg.Options.spin_budget_ms.offset]
     assert got == exp
 
 
@@ -56,6 +58,7 @@ def test_defaults_and_status_strings(lib):
     from paper_1504_00907_gb300 import ddg
     o = ddg.default_options()
     assert (o.precision, o.maxit, o.use_coarse, o.rank_tol) == (0, 1000, 1, 1e-10)
+    assert o.spin_budget_ms == 1000.0
     assert lib.ddg_status_string(ddg.DDG_ENOTSPD) == b"DDG_ENOTSPD"
 
 

@@ -47,7 +47,7 @@ def test_gradient_matches_central_differences():
     u, it, rr, st = s.solve(fd_, tol=1e-13)
     assert st == 0
     g = u - torch.tensor(ut, dtype=torch.float64, device="cuda")
-    lam, _, _ = s.adjoint(g.contiguous(), tol=1e-13)
+    lam, _, _, _ = s.adjoint(g.contiguous(), tol=1e-13)
     dk = s.grad_coeff(lam, u).cpu().numpy()
     # central differences of the dense-solve loss, relative step 1e-6
     fd = np.zeros(kappa.size)
@@ -106,7 +106,7 @@ def test_q1_elasticity_mu_gradient_matches_central_differences():
     ut = torch.tensor(prob.target, dtype=torch.float64, device="cuda")
     u, it, rr, st = s.solve(b, tol=1e-13)
     assert st == 0
-    lam, _, _ = s.adjoint((u - ut).contiguous(), tol=1e-13)
+    lam, _, _, _ = s.adjoint((u - ut).contiguous(), tol=1e-13)
     dmu = s.grad_coeff(lam, u).cpu().numpy()
 
     def loss(m):
@@ -131,4 +131,43 @@ def test_q1_elasticity_mu_gradient_matches_central_differences():
     assert np.linalg.norm(g - fd) <= 1e-5 * np.linalg.norm(fd)
     dlogmu = mf * g
     assert np.linalg.norm(dlogmu - mf * fd) <= 1e-5 * np.linalg.norm(mf * fd)
+    s.close()
+
+
+def test_autograd_rejects_coefficients_that_differ_from_the_handle():
+    # the handle's matrix is built from the coefficients given at setup: a
+    # kappa with other values must not silently get the old matrix's answer
+    from paper_1504_00907_gb300 import ddg
+    kappa, A, f, _ = _problem()
+    s = _solver(kappa, A)
+    f_t = torch.tensor(f, dtype=torch.float64, device="cuda", requires_grad=True)
+    changed = torch.tensor(kappa * 1.01, dtype=torch.float64, device="cuda", requires_grad=True)
+    with pytest.raises(ValueError):
+        ddg.solve_autograd(s, changed, f_t)
+    same = torch.tensor(kappa, dtype=torch.float64, device="cuda", requires_grad=True)
+    u = ddg.solve_autograd(s, same, f_t, tol=1e-10)
+    assert u.shape == f_t.shape
+    s.close()
+
+
+def test_autograd_backward_raises_when_the_adjoint_does_not_converge():
+    # a failing adjoint solve is planted on the host (the binding's adjoint
+    # returns DDG_ENOCONV): the backward must raise, not return the
+    # unconverged lambda as dL/df
+    from paper_1504_00907_gb300 import ddg
+    kappa, A, f, _ = _problem()
+    s = _solver(kappa, A)
+    real = s.adjoint
+
+    def unconverged(g, tol=1e-8):
+        lam, it, rr, _ = real(g, tol)
+        return lam, it, rr, ddg.DDG_ENOCONV
+
+    s.adjoint = unconverged
+    k_t = torch.tensor(kappa, dtype=torch.float64, device="cuda", requires_grad=True)
+    f_t = torch.tensor(f, dtype=torch.float64, device="cuda", requires_grad=True)
+    u = ddg.solve_autograd(s, k_t, f_t, tol=1e-10)
+    with pytest.raises(ddg.DDGError) as e:
+        (u * u).sum().backward()
+    assert e.value.status == ddg.DDG_ENOCONV
     s.close()

@@ -121,7 +121,7 @@ def test_elasticity64_forward_adjoint_and_sampled_gradient():
     uc = u.cpu().numpy()
     assert true_rel(prob.A, uc, prob.f) <= 1e-8
     g = uc - prob.target
-    lam, ita, rra = s.adjoint(dev(g), 1e-8)
+    lam, ita, rra, _ = s.adjoint(dev(g), 1e-8)
     lc = lam.cpu().numpy()
     assert true_rel(prob.A, lc, g) <= 1e-8
     dmu = s.grad_coeff(lam, u).cpu().numpy()
