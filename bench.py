@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--size", type=int, default=WORKLOAD["N"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-configs", type=int, default=1,
+                    help="also time the oracle on the 64^2 Poisson and 64^3 variable-coefficient "
+                         "problems (0 skips them)")
     ap.add_argument("--batched-size", type=int, default=96,
                     help="grid of the multi-RHS arm (0 skips it)")
     ap.add_argument("--batched-m", type=int, default=64)
@@ -143,19 +146,30 @@ def code_hash(path):
 
 def traffic_from_profile(kernel_file, launch_bytes):
     """Per-launch DRAM traffic of the local-solve kernel from the committed ncu
-    summary, scaled to this launch's algorithmic bytes; None when the summary
-    was taken on a different version of the kernel source."""
-    path = os.path.join(ROOT, "profiles", "local_solve_fp32_poisson3d.md")
+    record (profiles/local_solve_fp32_poisson3d.json: DRAM bytes over
+    algorithmic bytes of the captured launches), scaled to this launch's
+    algorithmic bytes; None when the record was taken on a different version
+    of the kernel source."""
+    path = os.path.join(ROOT, "profiles", "local_solve_fp32_poisson3d.json")
     try:
-        text = open(path).read()
-    except OSError:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
         return None
-    sha = code_hash(kernel_file)
-    m = re.search(r"source sha1:\s*([0-9a-f]{12})", text)
-    r = re.search(r"traffic/algorithmic bytes:\s*([0-9.]+)", text)
-    if not m or not r or m.group(1) != sha:
+    if rec.get("source_sha1") != code_hash(kernel_file):
         return None
-    return float(r.group(1)) * launch_bytes
+    return float(rec["traffic_over_algorithmic"]) * launch_bytes
+
+
+def _oracle_solve(prob):
+    """Oracle setup and PCG solve of one problem; (iterations, setup s, solve s)."""
+    from oracle import ddg_oracle as orc
+    t0 = time.perf_counter()
+    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape,
+                      dpn=prob.dofs_per_node)
+    t1 = time.perf_counter()
+    f = prob.f if prob.f.ndim == 1 else prob.f[:, 0]
+    res = orc.pcg(M.A, f, M.apply, tol=TOL)
+    return res.iters, t1 - t0, time.perf_counter() - t1
 
 
 def cpu_baseline(sample_n=SAMPLE_N):
@@ -163,18 +177,33 @@ def cpu_baseline(sample_n=SAMPLE_N):
     the same H/h = 8, overlap 1 and p = 2 on a sample_n^3 grid; solve-only
     dof*iters/s (oracle setup excluded, like the GPU number)."""
     import ddg_inputs as di
-    from oracle import ddg_oracle as orc
     prob = di.make_poisson3d(N=sample_n, box=WORKLOAD["box"], overlap=WORKLOAD["overlap"],
                              p=WORKLOAD["p"], seed=WORKLOAD["seed"])
-    M = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape, dpn=prob.dofs_per_node)
-    t0 = time.perf_counter()
-    res = orc.pcg(M.A, prob.f, M.apply, tol=TOL)
-    dt = time.perf_counter() - t0
-    return {"value": prob.n * res.iters / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    iters, _, dt = _oracle_solve(prob)
+    return {"value": prob.n * iters / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"oracle PCG solve (setup excluded) of the same problem family on a {sample_n}^3 "
                       f"grid ({prob.n} dofs, {prob.nsub} subdomains of 8^3, overlap 1, p=2): "
-                      f"{res.iters} iterations in {dt:.2f} s; numpy/scipy with default BLAS threads",
-            "iters": res.iters, "seconds": dt}
+                      f"{iters} iterations in {dt:.2f} s; numpy/scipy with default BLAS threads",
+            "iters": iters, "seconds": dt}
+
+
+def cpu_configs():
+    """The oracle on the other configurations of the measurement plan: the
+    64^2 2D Poisson problem (16^2 boxes, overlap 2, p <= 2, f ~ U(-1,1) seed 0)
+    and a 64^3 copy of the variable-coefficient problem (kappa = exp(GRF 0.1),
+    8^3 boxes, overlap 1, p <= 2) with one right-hand side; setup and solve
+    wall times, iterations and solve-only dof*iters/s."""
+    import ddg_inputs as di
+    out = []
+    for name, make in (("poisson2d_64^2", lambda: di.make_poisson2d(N=64, box=16, overlap=2, p=2, seed=0)),
+                       ("varcoef3d_64^3 (one RHS)", lambda: di.make_varcoef3d(N=64, box=8, overlap=1, p=2,
+                                                                                m=1))):
+        prob = make()
+        iters, setup_s, solve_s = _oracle_solve(prob)
+        out.append({"workload": name, "dofs": prob.n, "iters": iters, "setup_s": setup_s,
+                    "solve_s": solve_s, "dof_iters_per_s": prob.n * iters / solve_s,
+                    "cores": os.cpu_count()})
+    return out
 
 
 def run_reference(args, rank, world):
@@ -854,6 +883,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline().items() if k not in ("iters", "seconds")}
+        if args.cpu_configs:
+            line["cpu_baseline"]["other_configs"] = cpu_configs()
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
