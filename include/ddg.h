@@ -133,6 +133,10 @@ typedef struct {
     double setup_ms;      /* wall time of ddg_setup */
     int precision;        /* current preconditioner precision */
     int local_inverses;   /* stored local inverses: nsub, fewer with dedup_local */
+    int graph_solve;      /* 1: the last single-vector solve ran as one CUDA graph launch
+                             (its CG loop decided on the device); 0: driven from the host
+                             (tracing on, or DDG_NO_GRAPHS set); -1: conditional graphs
+                             are unavailable, every solve is driven from the host */
 } ddg_info;
 
 /* Fill *opt with the defaults listed above. */

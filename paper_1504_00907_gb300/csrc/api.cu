@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <thread>
 #include <unordered_map>
@@ -361,8 +362,9 @@ void read_scalars(ddg_handle h) {
     DDG_CUDA(cudaStreamSynchronize(h->stream));
 }
 
-// PCG from u = 0 (Sec. 7).  Returns the status; u, history, iters, relres set.
-ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_out, double* relres_out) {
+// PCG from u = 0 (Sec. 7), driven from the host (two reads of the device
+// scalars per iteration).  Returns the status; u, history, iters, relres set.
+ddg_status pcg_host(ddg_handle h, const double* f, double* u, double tol, int* iters_out, double* relres_out) {
     const int prec = h->precision;
     const int beta = h->opt.beta == DDG_BETA_AUTO ? (prec == DDG_PREC_FP64 ? DDG_BETA_FR : DDG_BETA_PR)
                                                   : h->opt.beta;
@@ -473,6 +475,226 @@ ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_
     if (iters_out) *iters_out = it;
     if (relres_out) *relres_out = true_rel;
     return st;
+}
+
+// ---------------------------------------------------------------- graph-driven PCG
+// The whole solve of Sec. 7 as one CUDA graph: ||f|| and the start (u = 0,
+// r = f), a conditional WHILE node whose body is one CG iteration (the
+// preconditioner apply, the dots and p update, the SpMV and u/r update, and
+// the control kernels that record alpha_j, beta_j and ||r_k||, check the
+// true residual once the recurrence meets tol and restart CG from it), and
+// the true residual after a loop that ended without one.  The graph reads
+// f from h->fbuf and writes u to h->ubuf; the host reads the outcome once.
+
+void ensure_loop_buffers(ddg_handle h) {
+    if (h->ctl) return;
+    h->ctl = h->arena.alloc<CgCtl>(1);
+    DDG_CUDA(cudaMallocHost((void**)&h->h_ctl, sizeof(CgCtl)));
+    std::memset(h->h_ctl, 0, sizeof(CgCtl));
+    const size_t len = (size_t)h->opt.maxit + 1;
+    h->d_hist = h->arena.alloc<double>(len);
+    h->d_alpha = h->arena.alloc<double>(len);
+    h->d_beta = h->arena.alloc<double>(len);
+}
+
+// one CG iteration (from the preconditioner apply to the loop condition),
+// enqueued on h->stream
+void loop_body(ddg_handle h, int prec, int pr, cudaGraphConditionalHandle cond) {
+    const int* firstp = &h->ctl->first;
+    apply_prec(h, h->r);
+    {
+        ProfScope ps(h, DDG_K_CG, 2, 0.0);
+        ddg::cg_dots_after_precond(h, prec, false, pr, firstp);
+        ddg::cg_update_p(h, prec, false, firstp);
+    }
+    {
+        ProfScope ps(h, DDG_K_SPMV, 1, 0.0);
+        ddg::spmv64(h, h->p, h->q, true, S_PQ);
+    }
+    ProfScope ps(h, DDG_K_CG, 6, 0.0);
+    ddg::cg_update_ur(h);
+    ddg::loop_decide_recurrence(h);
+    ddg::residual64(h, h->fbuf, h->ubuf, h->q, &h->ctl->check);
+    ddg::dot64(h, h->q, h->q, S_TMP, &h->ctl->check);
+    ddg::loop_decide_true(h, cond);
+    ddg::copy_gated(h, h->q, h->r, &h->ctl->restart_now);
+}
+
+// Append the whole solve of h (current precision) to graph g as one branch
+// with no dependencies: captured on the handle's private streams.
+void capture_solve_branch(ddg_handle h, cudaGraph_t g) {
+    const int prec = h->precision;
+    const int beta = h->opt.beta == DDG_BETA_AUTO ? (prec == DDG_PREC_FP64 ? DDG_BETA_FR : DDG_BETA_PR)
+                                                  : h->opt.beta;
+    const int pr = beta == DDG_BETA_PR;
+    ensure_loop_buffers(h);
+    if (!h->cap_stream) DDG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (!h->cap_stream2) DDG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream, bs = h->cap_stream2;
+    cudaStream_t saved = h->stream;
+    int64_t c0[DDG_K_COUNT], c1[DDG_K_COUNT], c2[DDG_K_COUNT];
+    for (int c = 0; c < DDG_K_COUNT; ++c) c0[c] = h->prof_launches[c];
+    bool in_main = false, in_body = false;
+    try {
+        DDG_CUDA(cudaStreamSynchronize(saved));
+        h->stream = cs;
+        h->u = h->ubuf;
+        DDG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        in_main = true;
+        {
+            ProfScope ps(h, DDG_K_CG, 1, 0.0);
+            ddg::dot64(h, h->fbuf, h->fbuf, S_TMP);
+        }
+        DDG_CUDA(cudaMemsetAsync(h->ubuf, 0, h->n * sizeof(double), cs));
+        DDG_CUDA(cudaMemcpyAsync(h->r, h->fbuf, h->n * sizeof(double), cudaMemcpyDeviceToDevice, cs));
+        cudaGraphConditionalHandle cond;
+        DDG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+        {
+            ProfScope ps(h, DDG_K_CG, 1, 0.0);
+            ddg::loop_init(h, cond);
+        }
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t capg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        DDG_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &nd));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        DDG_CUDA(cudaGraphAddNode(&wnode, capg, deps, nullptr, nd, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        for (int c = 0; c < DDG_K_COUNT; ++c) c1[c] = h->prof_launches[c];
+        h->stream = bs;
+        DDG_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        in_body = true;
+        loop_body(h, prec, pr, cond);
+        cudaGraph_t bout = nullptr;
+        in_body = false;
+        DDG_CUDA(cudaStreamEndCapture(bs, &bout));
+        for (int c = 0; c < DDG_K_COUNT; ++c) c2[c] = h->prof_launches[c];
+        h->stream = cs;
+        DDG_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        {
+            ProfScope ps(h, DDG_K_CG, 3, 0.0);
+            ddg::residual64(h, h->fbuf, h->ubuf, h->q, &h->ctl->need_final);
+            ddg::dot64(h, h->q, h->q, S_TMP, &h->ctl->need_final);
+            ddg::loop_final(h);
+        }
+        cudaGraph_t gout = nullptr;
+        in_main = false;
+        DDG_CUDA(cudaStreamEndCapture(cs, &gout));
+    } catch (...) {
+        cudaGraph_t junk = nullptr;
+        if (in_body) cudaStreamEndCapture(bs, &junk);
+        if (in_main) cudaStreamEndCapture(cs, &junk);
+        cudaGetLastError();
+        h->stream = saved;
+        h->u = nullptr;
+        for (int c = 0; c < DDG_K_COUNT; ++c) h->prof_launches[c] = c0[c];
+        throw;
+    }
+    h->stream = saved;
+    h->u = nullptr;
+    for (int c = 0; c < DDG_K_COUNT; ++c) {
+        h->solve_body_launches[prec][c] = c2[c] - c1[c];
+        h->solve_pre_launches[prec][c] = (h->prof_launches[c] - c0[c]) - (c2[c] - c1[c]);
+        h->prof_launches[c] = c0[c];
+    }
+}
+
+// the instantiated whole-solve graph of the current precision, or nullptr
+// when conditional graphs are not available (the host loop runs instead)
+cudaGraphExec_t solve_graph(ddg_handle h) {
+    const int p = h->precision;
+    if (h->solve_exec[p] || h->solve_graph_failed) return h->solve_exec[p];
+    cudaGraph_t g = nullptr;
+    try {
+        DDG_CUDA(cudaGraphCreate(&g, 0));
+        capture_solve_branch(h, g);
+        DDG_CUDA(cudaGraphInstantiate(&h->solve_exec[p], g, 0));
+        cudaGraphDestroy(g);
+    } catch (DdgError& e) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->solve_exec[p] = nullptr;
+        h->solve_graph_failed = true;
+        h->solve_graph_error = e.msg;
+    }
+    return h->solve_exec[p];
+}
+
+// outcome of a graph-driven solve from the device control block: history,
+// CG coefficients (the longest restart segment), iterations, true residual
+ddg_status loop_outcome(ddg_handle h, int* iters_out, double* relres_out) {
+    const CgCtl& c = *h->h_ctl;
+    std::vector<double> hist(c.it + 1), al(std::max(1, c.it)), be(std::max(1, c.it));
+    d2h(hist.data(), h->d_hist, (size_t)c.it + 1, h->stream);
+    if (c.it > 0) {
+        d2h(al.data(), h->d_alpha, (size_t)c.it, h->stream);
+        d2h(be.data(), h->d_beta, (size_t)c.it, h->stream);
+    }
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    h->history.assign(hist.begin(), hist.end());
+    h->cg_alpha.clear();
+    h->cg_beta.clear();
+    for (int s = 0; s <= c.restarts; ++s) {
+        const int a = c.seg_start[s], b = s < c.restarts ? c.seg_start[s + 1] : c.it;
+        if (b - a > (int)h->cg_alpha.size()) {
+            h->cg_alpha.assign(al.begin() + a, al.begin() + b);
+            h->cg_beta.assign(be.begin() + a + 1, be.begin() + b);
+        }
+    }
+    for (int k = 0; k < DDG_K_COUNT; ++k)
+        h->prof_launches[k] += h->solve_pre_launches[h->precision][k] +
+                               (int64_t)c.it * h->solve_body_launches[h->precision][k];
+    if (iters_out) *iters_out = c.it;
+    if (relres_out) *relres_out = c.true_rel;
+    h->last_solve_graph = 1;
+    switch (c.state) {
+        case CG_CONV:
+        case CG_ZERO: return DDG_OK;
+        case CG_BREAKDOWN: return DDG_EBREAKDOWN;
+        case CG_MAXIT: h->err = "maxit iterations reached"; return DDG_ENOCONV;
+        case CG_STALLED:
+            h->err = "the recurrence residual met tol but the true residual stayed above it "
+                     "after 3 restarts of CG from the true residual";
+            return DDG_ENOCONV;
+        case CG_NANRHS: h->err = "f contains NaN"; return DDG_EINVAL;
+    }
+    h->err = "graph-driven solve ended in an unknown state";
+    return DDG_ECUDA;
+}
+
+// write tol and maxit into the control block (enqueued before the graph)
+void loop_params(ddg_handle h, double tol) {
+    h->h_ctl->tol = tol;
+    h->h_ctl->maxit = h->opt.maxit;
+    DDG_CUDA(cudaMemcpyAsync(h->ctl, h->h_ctl, sizeof(CgCtl), cudaMemcpyHostToDevice, h->stream));
+}
+
+// PCG from u = 0 (Sec. 7): one graph launch when available, else the host loop
+ddg_status pcg(ddg_handle h, const double* f, double* u, double tol, int* iters_out, double* relres_out) {
+    h->last_solve_graph = 0;
+    if (!h->use_graphs || h->prof_mask != 0) return pcg_host(h, f, u, tol, iters_out, relres_out);
+    cudaGraphExec_t ge = solve_graph(h);
+    if (!ge) {
+        // conditional graphs unavailable: the same solve, driven by the host
+        const ddg_status st = pcg_host(h, f, u, tol, iters_out, relres_out);
+        if (st == DDG_OK) h->err = "graph-driven solve unavailable: " + h->solve_graph_error;
+        return st;
+    }
+    if (f != h->fbuf)
+        DDG_CUDA(cudaMemcpyAsync(h->fbuf, f, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    loop_params(h, tol);
+    DDG_CUDA(cudaGraphLaunch(ge, h->stream));
+    if (u != h->ubuf)
+        DDG_CUDA(cudaMemcpyAsync(u, h->ubuf, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    DDG_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, h->stream));
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    return loop_outcome(h, iters_out, relres_out);
 }
 
 void prof_flush(ddg_handle h) {
@@ -652,6 +874,117 @@ struct DeviceScope {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+template <typename Fn>
+ddg_status guarded(ddg_handle h, Fn&& fn);
+
+// ---------------------------------------------------------------- many problems, one graph
+// Combined whole-solve graphs of handle lists (ddg_solve_many), kept until a
+// handle of the list changes (precision, generators) or is destroyed.
+struct ManyGraph {
+    std::vector<ddg_handle> hs;
+    std::vector<int> precs, versions;
+    cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_many_mu;
+std::vector<ManyGraph> g_many;
+
+void drop_many_graphs(ddg_handle h) {
+    std::lock_guard<std::mutex> lock(g_many_mu);
+    for (size_t i = 0; i < g_many.size();) {
+        if (std::find(g_many[i].hs.begin(), g_many[i].hs.end(), h) != g_many[i].hs.end()) {
+            if (g_many[i].exec) cudaGraphExecDestroy(g_many[i].exec);
+            g_many.erase(g_many.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+cudaGraphExec_t many_graph(ddg_handle* hs, int nprob) {
+    std::lock_guard<std::mutex> lock(g_many_mu);
+    for (ManyGraph& mg : g_many) {
+        if ((int)mg.hs.size() != nprob) continue;
+        bool same = true;
+        for (int p = 0; p < nprob && same; ++p)
+            same = mg.hs[p] == hs[p] && mg.precs[p] == hs[p]->precision && mg.versions[p] == hs[p]->version;
+        if (same) return mg.exec;
+    }
+    ManyGraph mg;
+    cudaGraph_t g = nullptr;
+    DDG_CUDA(cudaGraphCreate(&g, 0));
+    try {
+        for (int p = 0; p < nprob; ++p) capture_solve_branch(hs[p], g);
+        DDG_CUDA(cudaGraphInstantiate(&mg.exec, g, 0));
+    } catch (...) {
+        cudaGraphDestroy(g);
+        throw;
+    }
+    cudaGraphDestroy(g);
+    for (int p = 0; p < nprob; ++p) {
+        mg.hs.push_back(hs[p]);
+        mg.precs.push_back(hs[p]->precision);
+        mg.versions.push_back(hs[p]->version);
+    }
+    g_many.push_back(mg);
+    return mg.exec;
+}
+
+// ddg_solve_many as one graph launch when every problem has one right-hand
+// side, every handle can run graph-driven solves and all are on one device;
+// returns false (nothing done) otherwise.  The launch runs on hs[0]'s stream,
+// ordered after and before the work on every handle's stream by events.
+bool solve_many_graph(ddg_handle* hs, int nprob, const double* const* F, double* const* U, const int* m,
+                      double tol, int* iters, double* relres, ddg_status& worst) {
+    for (int p = 0; p < nprob; ++p) {
+        ddg_handle h = hs[p];
+        if (m[p] != 1 || !h->use_graphs || h->prof_mask != 0 || h->solve_graph_failed ||
+            h->device != hs[0]->device || (const void*)F[p] == (const void*)U[p])
+            return false;
+    }
+    DeviceScope scope(hs[0]->device);
+    cudaGraphExec_t ge = nullptr;
+    std::vector<cudaEvent_t> ev(nprob + 1, nullptr);
+    try {
+        for (int p = 0; p < nprob; ++p) {
+            hs[p]->err.clear();
+            ensure_loop_buffers(hs[p]);
+        }
+        ge = many_graph(hs, nprob);
+        for (auto& e : ev) DDG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaStream_t L = hs[0]->stream;
+        for (int p = 0; p < nprob; ++p) {
+            ddg_handle h = hs[p];
+            DDG_CUDA(cudaMemcpyAsync(h->fbuf, F[p], h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            loop_params(h, tol);
+            DDG_CUDA(cudaEventRecord(ev[p], h->stream));
+            DDG_CUDA(cudaStreamWaitEvent(L, ev[p], 0));
+        }
+        DDG_CUDA(cudaGraphLaunch(ge, L));
+        DDG_CUDA(cudaEventRecord(ev[nprob], L));
+        for (int p = 0; p < nprob; ++p) {
+            ddg_handle h = hs[p];
+            DDG_CUDA(cudaStreamWaitEvent(h->stream, ev[nprob], 0));
+            DDG_CUDA(cudaMemcpyAsync(U[p], h->ubuf, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            DDG_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, h->stream));
+        }
+        for (int p = 0; p < nprob; ++p) DDG_CUDA(cudaStreamSynchronize(hs[p]->stream));
+        worst = DDG_OK;
+        for (int p = 0; p < nprob; ++p) {
+            const ddg_status st = loop_outcome(hs[p], iters ? iters + p : nullptr, relres ? relres + p : nullptr);
+            if (st != DDG_OK && worst == DDG_OK) worst = st;
+        }
+    } catch (DdgError& e) {
+        for (auto& x : ev)
+            if (x) cudaEventDestroy(x);
+        hs[0]->err = e.msg;
+        if (!ge) return false;   // the graph could not be built: solve the problems one by one
+        worst = e.st;
+        return true;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    return true;
+}
 
 template <typename Fn>
 ddg_status guarded(ddg_handle h, Fn&& fn) {
@@ -1322,12 +1655,19 @@ ddg_status ddg_set_generators(ddg_handle h, const double* F, int k) {
         DDG_REQUIRE(!h->inner, DDG_EINVAL, "a V-cycle handle keeps the generators it was built with");
         DDG_REQUIRE(F && k >= 1 && k <= DDG_KMAX, DDG_EINVAL, "F must be non-null and k in [1, 96]");
         DDG_CUDA(cudaStreamSynchronize(h->stream));
-        // the captured preconditioner graphs hold launches of the old coarse space
+        // the captured graphs hold launches of the old coarse space
         for (cudaGraphExec_t& g : h->apply_exec)
             if (g) {
                 cudaGraphExecDestroy(g);
                 g = nullptr;
             }
+        for (cudaGraphExec_t& g : h->solve_exec)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        ++h->version;
+        drop_many_graphs(h);
         for (void* p : h->coarse_allocs) h->arena.release(p);
         h->coarse_allocs.clear();
         h->Q64 = nullptr;
@@ -1421,8 +1761,15 @@ ddg_status ddg_solve_many(ddg_handle* hs, int nprob, const double* const* F, dou
         for (int q = 0; q < p; ++q)
             if (hs[q] == hs[p]) return DDG_EINVAL;   // a handle serves one thread
     }
+    if (!(tol > 0.0)) return DDG_EINVAL;
     std::vector<int64_t> off(nprob + 1, 0);
     for (int p = 0; p < nprob; ++p) off[p + 1] = off[p] + m[p];
+    {
+        // single right-hand sides on one device: every problem's whole solve
+        // is a branch of one CUDA graph, launched once
+        ddg_status st = DDG_OK;
+        if (solve_many_graph(hs, nprob, F, U, m, tol, iters, relres, st)) return st;
+    }
     std::vector<ddg_status> st(nprob, DDG_OK);
     std::vector<std::thread> th;
     th.reserve(nprob);
@@ -1545,6 +1892,7 @@ ddg_status ddg_get_info(ddg_handle h, ddg_info* info) {
         info->setup_ms = h->setup_ms;
         info->precision = h->precision;
         info->local_inverses = h->nrep_local;
+        info->graph_solve = h->solve_graph_failed ? -1 : h->last_solve_graph;
         return DDG_OK;
     });
 }
@@ -1676,12 +2024,17 @@ ddg_status ddg_get_kernel_stats(ddg_handle h, ddg_kernel_stat* st) {
 ddg_status ddg_destroy(ddg_handle h) {
     if (!h) return DDG_OK;
     DeviceScope scope(h->device);
+    drop_many_graphs(h);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->inner) ddg_destroy(h->inner);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (cudaGraphExec_t g : h->apply_exec)
         if (g) cudaGraphExecDestroy(g);
+    for (cudaGraphExec_t g : h->solve_exec)
+        if (g) cudaGraphExecDestroy(g);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+    if (h->h_ctl) cudaFreeHost(h->h_ctl);
     h->arena.free_all();
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete h;

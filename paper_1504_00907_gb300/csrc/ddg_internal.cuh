@@ -151,6 +151,24 @@ enum {
     S_COUNT = 16
 };
 
+// Device-side state of a graph-driven PCG solve (one CUDA graph whose
+// conditional WHILE node repeats the CG iteration; the control kernels
+// decide convergence, breakdown, the true-residual check and restarts).
+enum { CG_RUN = 0, CG_CONV = 1, CG_BREAKDOWN = 2, CG_MAXIT = 3, CG_STALLED = 4, CG_ZERO = 5, CG_NANRHS = 6 };
+#define DDG_MAX_RESTARTS 3
+struct CgCtl {
+    int it;            // iterations done
+    int restarts;      // true-residual restarts done
+    int state;         // CG_*
+    int check;         // the recurrence met tol this iteration: check the true residual
+    int first;         // the next p update starts a segment (beta = 0)
+    int restart_now;   // copy the true residual into r before the next iteration
+    int need_final;    // the loop ended without a true residual: compute it after the loop
+    int maxit;
+    int seg_start[DDG_MAX_RESTARTS + 1];   // first iteration of each restart segment
+    double tol, fn, true_rel, pad;
+};
+
 // error flags written by kernels (int32)
 enum { E_LOCAL_SPD = 0, E_COARSE_SPD = 1, E_TIMEOUT = 2, E_COUNT = 4 };
 
@@ -311,8 +329,21 @@ struct ddg_handle_s {
     MultiWork mw;
     TcData tc;
 
+    // ---- graph-driven PCG (whole solve in one graph launch, one per precision)
+    CgCtl* ctl = nullptr;          // device
+    CgCtl* h_ctl = nullptr;        // pinned host copy
+    double *d_hist = nullptr, *d_alpha = nullptr, *d_beta = nullptr;   // [maxit + 1] each
+    cudaGraphExec_t solve_exec[3] = {nullptr, nullptr, nullptr};
+    int64_t solve_pre_launches[3][DDG_K_COUNT] = {};    // launched once per solve
+    int64_t solve_body_launches[3][DDG_K_COUNT] = {};   // launched once per iteration
+    bool solve_graph_failed = false;   // conditional graphs unavailable: host-driven loop
+    std::string solve_graph_error;
+    int last_solve_graph = 0;          // 1 when the last solve ran as one graph launch
+    int version = 0;                   // bumped when a change invalidates captured graphs
+
     // ---- CUDA graphs of the preconditioner apply inside PCG (one per precision)
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;   // body of a conditional node, captured beside cap_stream
     cudaGraphExec_t apply_exec[3] = {nullptr, nullptr, nullptr};
     int64_t apply_launches[3][DDG_K_COUNT] = {};
     bool use_graphs = true;
@@ -368,14 +399,17 @@ void coarse_solve(ddg_handle h, int prec);
 void coarse_prolong(ddg_handle h, int prec);
 
 // k_cg.cu
+// gate / firstp: device flags read by the kernels themselves (graph-driven
+// solves decide them on the device); nullptr = always run / use `first`
 void spmv64(ddg_handle h, const double* x, double* y, bool dot_with_x, int slot);
-void dot64(ddg_handle h, const double* a, const double* b, int slot);
+void dot64(ddg_handle h, const double* a, const double* b, int slot, const int* gate = nullptr);
+void copy_gated(ddg_handle h, const double* src, double* dst, const int* gate);
 void cg_update_ur(ddg_handle h);
-void cg_dots_after_precond(ddg_handle h, int prec, bool first, int pr);
-void cg_update_p(ddg_handle h, int prec, bool first);
+void cg_dots_after_precond(ddg_handle h, int prec, bool first, int pr, const int* firstp = nullptr);
+void cg_update_p(ddg_handle h, int prec, bool first, const int* firstp = nullptr);
 void convert_to_float(ddg_handle h, const double* src, float* dst);
 void convert_to_double(ddg_handle h, const float* src, double* dst);
-void residual64(ddg_handle h, const double* f, const double* u, double* r);
+void residual64(ddg_handle h, const double* f, const double* u, double* r, const int* gate = nullptr);
 void grad_coeff_var7(ddg_handle h, const double* lambda, const double* u, double* dk);
 void grad_coeff_q1(ddg_handle h, const double* lambda, const double* u, double* dk);
 void set_scalar(ddg_handle h, int slot, double v);
@@ -393,6 +427,12 @@ void multi_update_p(ddg_handle h, int m);
 void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double* out, int slot);
 void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace);
 void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int md, int k0, int cnt);
+
+// k_cg.cu: control kernels of the graph-driven PCG
+void loop_init(ddg_handle h, cudaGraphConditionalHandle cond);
+void loop_decide_recurrence(ddg_handle h);
+void loop_decide_true(ddg_handle h, cudaGraphConditionalHandle cond);
+void loop_final(ddg_handle h);
 
 // k_tc.cu (tcgen05 local solves of the batched path)
 int tc_n_for(int m);

@@ -138,12 +138,15 @@ __global__ void __launch_bounds__(RT) cg_update_ur_kernel(int64_t n, double* __r
 }
 
 // rho' = r^T z, qz = q^T z; beta = rho'/rho (FR) or -alpha qz / rho (PR); rho <- rho'
+// (first: a restart, beta = 0; read from *firstp when that is set, so that a
+// graph-driven solve decides it on the device)
 template <typename ZV>
 __global__ void __launch_bounds__(RT) cg_dots_kernel(int64_t n, const double* __restrict__ r,
                                                      const double* __restrict__ q,
                                                      const ZV* __restrict__ z, int first, int pr,
                                                      double* partials, unsigned* counter,
-                                                     double* scal) {
+                                                     double* scal, const int* firstp) {
+    if (firstp) first = *firstp;
     double acc[2] = {0.0, 0.0};
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x) {
@@ -168,16 +171,20 @@ __global__ void __launch_bounds__(RT) cg_dots_kernel(int64_t n, const double* __
 
 template <typename ZV>
 __global__ void cg_update_p_kernel(int64_t n, double* __restrict__ p, const ZV* __restrict__ z,
-                                   const double* __restrict__ scal, int first) {
+                                   const double* __restrict__ scal, int first, const int* firstp) {
+    if (firstp) first = *firstp;
     const double beta = first ? 0.0 : scal[S_BETA];
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x)
         p[g] = first ? (double)z[g] : fma(beta, p[g], (double)z[g]);
 }
 
+// (gate: when set, every block returns at once unless *gate != 0)
 __global__ void __launch_bounds__(RT) dot64_kernel(int64_t n, const double* __restrict__ a,
                                                    const double* __restrict__ b, double* partials,
-                                                   unsigned* counter, double* scal, int slot) {
+                                                   unsigned* counter, double* scal, int slot,
+                                                   const int* gate) {
+    if (gate && !*gate) return;
     double acc[1] = {0.0};
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n;
          g += (int64_t)gridDim.x * blockDim.x)
@@ -190,12 +197,20 @@ __global__ void __launch_bounds__(RT) dot64_kernel(int64_t n, const double* __re
 __global__ void residual64_kernel(int64_t n, const int64_t* __restrict__ rowptr,
                                   const int32_t* __restrict__ col, const double* __restrict__ val,
                                   const double* __restrict__ f, const double* __restrict__ u,
-                                  double* __restrict__ r) {
+                                  double* __restrict__ r, const int* gate) {
+    if (gate && !*gate) return;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
     double s = f[g];
     for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) s = fma(-val[e], u[col[e]], s);
     r[g] = s;
+}
+
+__global__ void copy_gated_kernel(int64_t n, const double* __restrict__ a, double* __restrict__ b,
+                                  const int* gate) {
+    if (!*gate) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) b[g] = a[g];
 }
 
 __global__ void to_float_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
@@ -285,6 +300,73 @@ __global__ void grad_q1_kernel(int ne, const double* __restrict__ kmu, const dou
     dmu[e] = -s;
 }
 
+// ---- control of the graph-driven PCG (single thread each) ----
+// Before the loop: ||f|| from scal[S_TMP]; the loop runs only for f != 0.
+__global__ void loop_init_kernel(CgCtl* ctl, double* scal, double* hist, cudaGraphConditionalHandle cond) {
+    const double fn = sqrt(scal[S_TMP]);
+    ctl->fn = fn;
+    ctl->it = 0;
+    ctl->restarts = 0;
+    ctl->check = 0;
+    ctl->first = 1;
+    ctl->restart_now = 0;
+    ctl->need_final = 0;
+    ctl->true_rel = 0.0;
+    ctl->seg_start[0] = 0;
+    scal[S_FLAG] = 0.0;
+    ctl->state = fn > 0.0 ? CG_RUN : (fn == fn ? CG_ZERO : CG_NANRHS);
+    hist[0] = fn > 0.0 ? 1.0 : 0.0;
+    cudaGraphSetConditional(cond, ctl->state == CG_RUN ? 1u : 0u);
+}
+
+// After the u/r update: record alpha_j, beta_j and ||r|| / ||f||; breakdown
+// ends the loop; a recurrence residual at or below tol asks for the true one.
+__global__ void loop_decide_recurrence_kernel(CgCtl* ctl, const double* scal, double* hist, double* alpha,
+                                              double* beta) {
+    const int it = ++ctl->it;
+    alpha[it - 1] = scal[S_ALPHA];
+    beta[it - 1] = scal[S_BETA];     // 0 at the start of a segment
+    ctl->first = 0;
+    ctl->restart_now = 0;
+    ctl->check = 0;
+    if (scal[S_FLAG] != 0.0) {
+        ctl->state = CG_BREAKDOWN;
+        ctl->need_final = 1;
+        return;
+    }
+    const double rel = sqrt(scal[S_RR]) / ctl->fn;
+    hist[it] = rel;
+    if (rel <= ctl->tol) ctl->check = 1;
+    else if (it >= ctl->maxit) {
+        ctl->state = CG_MAXIT;
+        ctl->need_final = 1;
+    }
+}
+
+// After the true residual (when asked for): accept, give up after the last
+// restart, or restart CG from the true residual; then the loop condition.
+__global__ void loop_decide_true_kernel(CgCtl* ctl, const double* scal, cudaGraphConditionalHandle cond) {
+    if (ctl->check) {
+        const double tr = sqrt(scal[S_TMP]) / ctl->fn;
+        ctl->true_rel = tr;
+        if (tr <= ctl->tol) {
+            ctl->state = CG_CONV;
+        } else if (ctl->restarts >= DDG_MAX_RESTARTS) {
+            ctl->state = CG_STALLED;
+        } else {
+            ctl->seg_start[++ctl->restarts] = ctl->it;
+            ctl->first = 1;
+            ctl->restart_now = 1;
+            if (ctl->it >= ctl->maxit) ctl->state = CG_MAXIT;
+        }
+    }
+    cudaGraphSetConditional(cond, ctl->state == CG_RUN ? 1u : 0u);
+}
+
+__global__ void loop_final_kernel(CgCtl* ctl, const double* scal) {
+    if (ctl->need_final) ctl->true_rel = sqrt(scal[S_TMP]) / ctl->fn;
+}
+
 inline unsigned red_grid(int64_t n) {
     int64_t b = (n + RT - 1) / RT;
     if (b > DDG_RED_BLOCKS) b = DDG_RED_BLOCKS;
@@ -313,9 +395,34 @@ void spmv64(ddg_handle h, const double* x, double* y, bool dot, int /*slot*/) {
     DDG_CHECK_LAUNCH();
 }
 
-void dot64(ddg_handle h, const double* a, const double* b, int slot) {
+void dot64(ddg_handle h, const double* a, const double* b, int slot, const int* gate) {
     dot64_kernel<<<red_grid(h->n), RT, 0, h->stream>>>(h->n, a, b, h->red_partials, h->red_counter,
-                                                       h->scal, slot);
+                                                       h->scal, slot, gate);
+    DDG_CHECK_LAUNCH();
+}
+
+void loop_init(ddg_handle h, cudaGraphConditionalHandle cond) {
+    loop_init_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->scal, h->d_hist, cond);
+    DDG_CHECK_LAUNCH();
+}
+
+void loop_decide_recurrence(ddg_handle h) {
+    loop_decide_recurrence_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->scal, h->d_hist, h->d_alpha, h->d_beta);
+    DDG_CHECK_LAUNCH();
+}
+
+void loop_decide_true(ddg_handle h, cudaGraphConditionalHandle cond) {
+    loop_decide_true_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->scal, cond);
+    DDG_CHECK_LAUNCH();
+}
+
+void loop_final(ddg_handle h) {
+    loop_final_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->scal);
+    DDG_CHECK_LAUNCH();
+}
+
+void copy_gated(ddg_handle h, const double* src, double* dst, const int* gate) {
+    copy_gated_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, src, dst, gate);
     DDG_CHECK_LAUNCH();
 }
 
@@ -325,28 +432,30 @@ void cg_update_ur(ddg_handle h) {
     DDG_CHECK_LAUNCH();
 }
 
-void cg_dots_after_precond(ddg_handle h, int prec, bool first, int pr) {
+void cg_dots_after_precond(ddg_handle h, int prec, bool first, int pr, const int* firstp) {
     if (prec == DDG_PREC_FP64)
         cg_dots_kernel<double><<<red_grid(h->n), RT, 0, h->stream>>>(h->n, h->r, h->q, h->z64, first, pr,
-                                                                     h->red_partials, h->red_counter, h->scal);
+                                                                     h->red_partials, h->red_counter, h->scal,
+                                                                     firstp);
     else
         cg_dots_kernel<float><<<red_grid(h->n), RT, 0, h->stream>>>(h->n, h->r, h->q, h->z32, first, pr,
-                                                                    h->red_partials, h->red_counter, h->scal);
+                                                                    h->red_partials, h->red_counter, h->scal,
+                                                                    firstp);
     DDG_CHECK_LAUNCH();
 }
 
-void cg_update_p(ddg_handle h, int prec, bool first) {
+void cg_update_p(ddg_handle h, int prec, bool first, const int* firstp) {
     const unsigned G = red_grid(h->n);
     if (prec == DDG_PREC_FP64)
-        cg_update_p_kernel<double><<<G, RT, 0, h->stream>>>(h->n, h->p, h->z64, h->scal, first);
+        cg_update_p_kernel<double><<<G, RT, 0, h->stream>>>(h->n, h->p, h->z64, h->scal, first, firstp);
     else
-        cg_update_p_kernel<float><<<G, RT, 0, h->stream>>>(h->n, h->p, h->z32, h->scal, first);
+        cg_update_p_kernel<float><<<G, RT, 0, h->stream>>>(h->n, h->p, h->z32, h->scal, first, firstp);
     DDG_CHECK_LAUNCH();
 }
 
-void residual64(ddg_handle h, const double* f, const double* u, double* r) {
+void residual64(ddg_handle h, const double* f, const double* u, double* r, const int* gate) {
     residual64_kernel<<<(unsigned)((h->n + 255) / 256), 256, 0, h->stream>>>(h->n, h->rowptr, h->col,
-                                                                             h->val64, f, u, r);
+                                                                             h->val64, f, u, r, gate);
     DDG_CHECK_LAUNCH();
 }
 

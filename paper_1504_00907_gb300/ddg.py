@@ -52,7 +52,7 @@ class Info(ctypes.Structure):
                 ("sum_local", ctypes.c_int64), ("local_tiles", ctypes.c_int64),
                 ("coarse_band", ctypes.c_int), ("coarse_blocks", ctypes.c_int),
                 ("setup_ms", ctypes.c_double), ("precision", ctypes.c_int),
-                ("local_inverses", ctypes.c_int)]
+                ("local_inverses", ctypes.c_int), ("graph_solve", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):

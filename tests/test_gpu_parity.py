@@ -364,3 +364,55 @@ def test_cg_coefficients_and_condition_estimate_match_oracle(name):
     lo_o, hi_o = orc.lanczos_extremes(ref.alphas[:m], ref.betas[:m - 1])
     assert abs(lo - lo_o) <= 1e-5 * hi_o and abs(hi - hi_o) <= 1e-5 * hi_o
     assert 0 < lo <= hi <= 1.0 + 1e-10 and bound > 0
+
+
+@pytest.mark.parametrize("name,prec", [("poisson3d_24", "fp64"), ("poisson3d_24", "fp32"),
+                                       ("biharmonic_64", "fp32"), ("elasticity_q1_6", "fp64")])
+def test_graph_driven_solve_equals_host_driven_solve(name, prec):
+    # The whole solve runs as one CUDA graph whose WHILE node repeats the CG
+    # iteration and whose control kernels decide convergence on the device;
+    # with graphs off the same kernels run from the host loop.  Same
+    # arithmetic in the same order: bitwise equal results and histories.
+    import os
+    from paper_1504_00907_gb300 import ddg
+    prob, solver, _ = setup_case(name)
+    os.environ["DDG_NO_GRAPHS"] = "1"
+    try:
+        host = ddg.Solver.from_problem(prob, precision=prec, keep=(prec,))
+    finally:
+        del os.environ["DDG_NO_GRAPHS"]
+    solver.set_precision(prec)
+    f = dev(prob.f if prob.f.ndim == 1 else prob.f[:, 0])
+    ug, itg, rrg, stg = solver.solve(f, tol=1e-8)
+    assert solver.info()["graph_solve"] == 1
+    uh, ith, rrh, sth = host.solve(f, tol=1e-8)
+    assert host.info()["graph_solve"] == 0
+    assert stg == sth == ddg.DDG_OK and itg == ith and rrg == rrh
+    assert torch.equal(ug, uh)
+    np.testing.assert_array_equal(solver.history(), host.history())
+    ag, bg = solver.cg_coefficients()
+    ah, bh = host.cg_coefficients()
+    np.testing.assert_array_equal(ag, ah)
+    np.testing.assert_array_equal(bg, bh)
+    # a graph-driven solve still counts its kernel launches (per iteration)
+    solver.profile(())
+    solver.solve(f, tol=1e-8)
+    assert sum(v["launches"] for v in solver.kernel_stats().values()) > 10 * itg
+    solver.set_precision("fp64")
+    host.close()
+
+
+def test_graph_driven_solve_maxit_and_zero_rhs():
+    from paper_1504_00907_gb300 import ddg
+    prob, _, _ = setup_case("poisson2d_64")
+    capped = ddg.Solver.from_problem(prob, maxit=3)
+    u, it, rr, st = capped.solve(dev(prob.f), tol=1e-14)
+    assert capped.info()["graph_solve"] == 1
+    assert st == ddg.DDG_ENOCONV and it == 3 and rr > 1e-14
+    ref = orc.pcg(setup_case("poisson2d_64")[2].A, prob.f, setup_case("poisson2d_64")[2].apply,
+                  tol=1e-14, maxit=3)
+    assert_close(u.cpu().numpy(), ref.u, 1e-10)
+    assert abs(rr - ref.true_relres) <= 1e-10 * ref.true_relres
+    u0, it0, rr0, st0 = capped.solve(dev(np.zeros(prob.n)), tol=1e-8)
+    assert st0 == ddg.DDG_OK and it0 == 0 and rr0 == 0.0 and not u0.abs().max().item()
+    capped.close()
