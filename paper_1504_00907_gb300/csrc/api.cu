@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <list>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -712,9 +713,9 @@ void prof_flush(ddg_handle h) {
 
 // Batched PCG on an n x m block (m <= DDG_MCHUNK), FP32/BF16 preconditioner:
 // every column runs its own CG (alpha, beta, convergence, restarts); the
-// preconditioner is applied to all columns at once.
-ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol, int* iters,
-                     double* relres) {
+// preconditioner is applied to all columns at once.  Driven from the host.
+ddg_status pcg_batch_host(ddg_handle h, const double* F, double* U, int m, double tol, int* iters,
+                          double* relres) {
     ddg::multi_ensure(h, m);
     MultiWork& w = h->mw;
     const int64_t n = h->n;
@@ -875,46 +876,232 @@ struct DeviceScope {
     }
 };
 
+// ---------------------------------------------------------------- graph-driven batched PCG
+// The batched solve as one CUDA graph, as for a single vector: every column
+// keeps its own CG, and the per-column decisions of the host loop above
+// (breakdown, true-residual check, restart, maxit) are taken by control
+// kernels with one thread per column.  The graph reads F from mw.Fb and
+// writes U to mw.Ub.
+void capture_batch(ddg_handle h, int m, cudaGraph_t g, int64_t* pre, int64_t* body_launches) {
+    MultiWork& w = h->mw;
+    const int beta = h->opt.beta == DDG_BETA_AUTO ? DDG_BETA_PR : h->opt.beta;
+    const int pr = beta == DDG_BETA_PR;
+    const int64_t n = h->n;
+    if (!h->cap_stream) DDG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (!h->cap_stream2) DDG_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+    cudaStream_t cs = h->cap_stream, bs = h->cap_stream2;
+    cudaStream_t saved = h->stream;
+    int64_t c0[DDG_K_COUNT];
+    for (int c = 0; c < DDG_K_COUNT; ++c) c0[c] = h->prof_launches[c];
+    bool in_main = false, in_body = false;
+    try {
+        DDG_CUDA(cudaStreamSynchronize(saved));
+        if (h->precision == DDG_PREC_BF16 && h->tc.A && h->tc.last_m != m) {
+            // padding rows/columns of the BF16 residual slabs must read as zero
+            DDG_CUDA(cudaMemsetAsync(h->tc.X, 0, h->tc.x_elems * sizeof(__nv_bfloat16), saved));
+            DDG_CUDA(cudaStreamSynchronize(saved));
+            h->tc.last_m = m;
+        }
+        h->stream = cs;
+        DDG_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        in_main = true;
+        DDG_CUDA(cudaMemsetAsync(w.scal, 0, S_COUNT * DDG_MCHUNK * sizeof(double), cs));
+        ddg::multi_resnorm(h, m, w.Fb, nullptr, nullptr, S_TMP);
+        DDG_CUDA(cudaMemsetAsync(w.Ub, 0, n * m * sizeof(double), cs));
+        DDG_CUDA(cudaMemsetAsync(w.P, 0, n * m * sizeof(double), cs));
+        DDG_CUDA(cudaMemcpyAsync(w.R, w.Fb, n * m * sizeof(double), cudaMemcpyDeviceToDevice, cs));
+        ddg::multi_to_float(h, m, nullptr);
+        cudaGraphConditionalHandle cond;
+        DDG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+        ddg::mloop_init(h, m, cond);
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t capg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        DDG_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &capg, &deps, nullptr, &nd));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wnode;
+        DDG_CUDA(cudaGraphAddNode(&wnode, capg, deps, nullptr, nd, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        int64_t c1[DDG_K_COUNT];
+        for (int c = 0; c < DDG_K_COUNT; ++c) c1[c] = h->prof_launches[c];
+        h->stream = bs;
+        DDG_CUDA(cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        in_body = true;
+        // one iteration: r32 is current (converted after the u/r update, or
+        // after a restart replaced columns of R)
+        w.r32_current = true;
+        ddg::multi_apply(h, m);
+        ddg::multi_dots(h, m, pr);
+        ddg::multi_update_p(h, m);
+        ddg::multi_spmv_pq(h, m);
+        ddg::multi_update_ur(h, m, w.Ub);
+        ddg::mloop_decide_recurrence(h, m);
+        ddg::multi_resnorm_gated(h, m, w.Fb, w.Ub, w.T, S_TMP, &w.ctl->any_cand);
+        ddg::mloop_decide_true(h, m, cond);
+        ddg::multi_replace_cols_gated(h, m, w.T, w.R, w.restart, &w.ctl->any_restart);
+        ddg::multi_to_float(h, m, &w.ctl->any_restart);
+        h->prof_launches[DDG_K_CG] += 9;   // the control, dot, update and gated kernels above
+        cudaGraph_t bout = nullptr;
+        in_body = false;
+        DDG_CUDA(cudaStreamEndCapture(bs, &bout));
+        for (int c = 0; c < DDG_K_COUNT; ++c) {
+            body_launches[c] = h->prof_launches[c] - c1[c];
+            pre[c] = c1[c] - c0[c];
+        }
+        pre[DDG_K_CG] += 9;   // norms, conversion, control kernels and the final residual
+        h->stream = cs;
+        DDG_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+        ddg::mloop_final_prep(h, m);
+        ddg::multi_resnorm_gated(h, m, w.Fb, w.Ub, nullptr, S_TMP, &w.ctl->any_unfinished);
+        ddg::mloop_final(h, m);
+        cudaGraph_t gout = nullptr;
+        in_main = false;
+        DDG_CUDA(cudaStreamEndCapture(cs, &gout));
+    } catch (...) {
+        cudaGraph_t junk = nullptr;
+        if (in_body) cudaStreamEndCapture(bs, &junk);
+        if (in_main) cudaStreamEndCapture(cs, &junk);
+        cudaGetLastError();
+        h->stream = saved;
+        w.r32_current = false;
+        for (int c = 0; c < DDG_K_COUNT; ++c) h->prof_launches[c] = c0[c];
+        throw;
+    }
+    h->stream = saved;
+    w.r32_current = false;
+    for (int c = 0; c < DDG_K_COUNT; ++c) h->prof_launches[c] = c0[c];
+}
+
+const ddg_handle_s::BatchGraph* batch_graph(ddg_handle h, int m) {
+    const int p = h->precision;
+    if (h->batch_gen != h->mw.gen) {
+        // the workspace was reallocated: the captured graphs point at the old one
+        for (auto& pe : h->batch_exec)
+            for (auto& e : pe) cudaGraphExecDestroy(e.exec);
+        for (auto& pe : h->batch_exec) pe.clear();
+        h->batch_gen = h->mw.gen;
+    }
+    for (auto& e : h->batch_exec[p])
+        if (e.m == m) return &e;
+    if (h->solve_graph_failed) return nullptr;
+    cudaGraph_t g = nullptr;
+    ddg_handle_s::BatchGraph bg{};
+    bg.m = m;
+    try {
+        DDG_CUDA(cudaGraphCreate(&g, 0));
+        capture_batch(h, m, g, bg.pre, bg.body);
+        DDG_CUDA(cudaGraphInstantiate(&bg.exec, g, 0));
+        cudaGraphDestroy(g);
+    } catch (DdgError& e) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->solve_graph_failed = true;
+        h->solve_graph_error = e.msg;
+        return nullptr;
+    }
+    h->batch_exec[p].push_back(bg);
+    return &h->batch_exec[p].back();
+}
+
+ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol, int* iters, double* relres) {
+    if (!h->use_graphs || h->prof_mask != 0) return pcg_batch_host(h, F, U, m, tol, iters, relres);
+    ddg::multi_ensure(h, m);
+    const ddg_handle_s::BatchGraph* bg = batch_graph(h, m);
+    if (!bg) return pcg_batch_host(h, F, U, m, tol, iters, relres);
+    cudaGraphExec_t ge = bg->exec;
+    MultiWork& w = h->mw;
+    const int64_t n = h->n;
+    if (F != w.Fb)
+        DDG_CUDA(cudaMemcpyAsync(w.Fb, F, n * m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    w.h_ctl->tol = tol;
+    w.h_ctl->maxit = h->opt.maxit;
+    DDG_CUDA(cudaMemcpyAsync(w.ctl, w.h_ctl, sizeof(MultiCtl), cudaMemcpyHostToDevice, h->stream));
+    DDG_CUDA(cudaGraphLaunch(ge, h->stream));
+    if (U != w.Ub)
+        DDG_CUDA(cudaMemcpyAsync(U, w.Ub, n * m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    DDG_CUDA(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(MultiCtl), cudaMemcpyDeviceToHost, h->stream));
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    const MultiCtl& c = *w.h_ctl;
+    for (int k = 0; k < DDG_K_COUNT; ++k) h->prof_launches[k] += bg->pre[k] + (int64_t)c.it * bg->body[k];
+    if (c.timed_out) {
+        DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        throw DdgError{DDG_ETIMEOUT, "a bounded wait of the tensor-core local solve ran out"};
+    }
+    ddg_status worst = DDG_OK;
+    for (int j = 0; j < m; ++j) {
+        if (iters) iters[j] = c.done_it[j];
+        if (relres) relres[j] = c.done_rel[j];
+        if (c.cstat[j] != DDG_OK && worst == DDG_OK) worst = (ddg_status)c.cstat[j];
+    }
+    return worst;
+}
+
 template <typename Fn>
 ddg_status guarded(ddg_handle h, Fn&& fn);
 
 // ---------------------------------------------------------------- many problems, one graph
 // Combined whole-solve graphs of handle lists (ddg_solve_many), kept until a
-// handle of the list changes (precision, generators) or is destroyed.
+// handle of the list changes (precision, generators, batched workspace) or
+// is destroyed.  Problem p is a single-vector solve (m = 1) or a batched
+// solve of m columns; each is one branch of the graph.
 struct ManyGraph {
     std::vector<ddg_handle> hs;
-    std::vector<int> precs, versions;
+    std::vector<int> precs, versions, ms, gens;
+    std::vector<std::vector<int64_t>> pre, body;   // launches per problem: once / per iteration
     cudaGraphExec_t exec = nullptr;
 };
 std::mutex g_many_mu;
-std::vector<ManyGraph> g_many;
+std::list<ManyGraph> g_many;   // a list: references stay valid
 
 void drop_many_graphs(ddg_handle h) {
     std::lock_guard<std::mutex> lock(g_many_mu);
-    for (size_t i = 0; i < g_many.size();) {
-        if (std::find(g_many[i].hs.begin(), g_many[i].hs.end(), h) != g_many[i].hs.end()) {
-            if (g_many[i].exec) cudaGraphExecDestroy(g_many[i].exec);
-            g_many.erase(g_many.begin() + (long)i);
+    for (auto it = g_many.begin(); it != g_many.end();) {
+        if (std::find(it->hs.begin(), it->hs.end(), h) != it->hs.end()) {
+            if (it->exec) cudaGraphExecDestroy(it->exec);
+            it = g_many.erase(it);
         } else {
-            ++i;
+            ++it;
         }
     }
 }
 
-cudaGraphExec_t many_graph(ddg_handle* hs, int nprob) {
+// the combined graph of these problems (built on first use)
+const ManyGraph& many_graph(ddg_handle* hs, int nprob, const int* m) {
     std::lock_guard<std::mutex> lock(g_many_mu);
     for (ManyGraph& mg : g_many) {
         if ((int)mg.hs.size() != nprob) continue;
         bool same = true;
         for (int p = 0; p < nprob && same; ++p)
-            same = mg.hs[p] == hs[p] && mg.precs[p] == hs[p]->precision && mg.versions[p] == hs[p]->version;
-        if (same) return mg.exec;
+            same = mg.hs[p] == hs[p] && mg.precs[p] == hs[p]->precision && mg.versions[p] == hs[p]->version &&
+                   mg.ms[p] == m[p] && mg.gens[p] == hs[p]->mw.gen;
+        if (same) return mg;
     }
     ManyGraph mg;
     cudaGraph_t g = nullptr;
     DDG_CUDA(cudaGraphCreate(&g, 0));
     try {
-        for (int p = 0; p < nprob; ++p) capture_solve_branch(hs[p], g);
+        for (int p = 0; p < nprob; ++p) {
+            ddg_handle h = hs[p];
+            std::vector<int64_t> pre(DDG_K_COUNT, 0), body(DDG_K_COUNT, 0);
+            if (m[p] == 1) {
+                capture_solve_branch(h, g);
+                for (int c = 0; c < DDG_K_COUNT; ++c) {
+                    pre[c] = h->solve_pre_launches[h->precision][c];
+                    body[c] = h->solve_body_launches[h->precision][c];
+                }
+            } else {
+                ddg::multi_ensure(h, m[p]);
+                capture_batch(h, m[p], g, pre.data(), body.data());
+            }
+            mg.pre.push_back(pre);
+            mg.body.push_back(body);
+        }
         DDG_CUDA(cudaGraphInstantiate(&mg.exec, g, 0));
     } catch (...) {
         cudaGraphDestroy(g);
@@ -925,60 +1112,107 @@ cudaGraphExec_t many_graph(ddg_handle* hs, int nprob) {
         mg.hs.push_back(hs[p]);
         mg.precs.push_back(hs[p]->precision);
         mg.versions.push_back(hs[p]->version);
+        mg.ms.push_back(m[p]);
+        mg.gens.push_back(hs[p]->mw.gen);
     }
     g_many.push_back(mg);
-    return mg.exec;
+    return g_many.back();
 }
 
-// ddg_solve_many as one graph launch when every problem has one right-hand
-// side, every handle can run graph-driven solves and all are on one device;
-// returns false (nothing done) otherwise.  The launch runs on hs[0]'s stream,
-// ordered after and before the work on every handle's stream by events.
+// ddg_solve_many as one graph launch when every handle can run graph-driven
+// solves, the batched ones (m > 1) take the batched path (FP32/BF16
+// preconditioner, two-level handle, at most 32 generators, m <= 64) and all
+// handles are on one device; returns false (nothing done) otherwise.  The
+// launch runs on hs[0]'s stream, ordered after and before the work on every
+// handle's stream by events.
 bool solve_many_graph(ddg_handle* hs, int nprob, const double* const* F, double* const* U, const int* m,
                       double tol, int* iters, double* relres, ddg_status& worst) {
     for (int p = 0; p < nprob; ++p) {
         ddg_handle h = hs[p];
-        if (m[p] != 1 || !h->use_graphs || h->prof_mask != 0 || h->solve_graph_failed ||
-            h->device != hs[0]->device || (const void*)F[p] == (const void*)U[p])
+        if (!h->use_graphs || h->prof_mask != 0 || h->solve_graph_failed || h->device != hs[0]->device ||
+            (const void*)F[p] == (const void*)U[p])
+            return false;
+        if (m[p] > 1 && (m[p] > DDG_MCHUNK || h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32))
             return false;
     }
     DeviceScope scope(hs[0]->device);
-    cudaGraphExec_t ge = nullptr;
+    bool built = false;
     std::vector<cudaEvent_t> ev(nprob + 1, nullptr);
     try {
         for (int p = 0; p < nprob; ++p) {
             hs[p]->err.clear();
-            ensure_loop_buffers(hs[p]);
+            if (m[p] == 1) ensure_loop_buffers(hs[p]);
+            else ddg::multi_ensure(hs[p], m[p]);
         }
-        ge = many_graph(hs, nprob);
+        const ManyGraph& mg = many_graph(hs, nprob, m);
+        built = true;
         for (auto& e : ev) DDG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         cudaStream_t L = hs[0]->stream;
         for (int p = 0; p < nprob; ++p) {
             ddg_handle h = hs[p];
-            DDG_CUDA(cudaMemcpyAsync(h->fbuf, F[p], h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-            loop_params(h, tol);
+            if (m[p] == 1) {
+                DDG_CUDA(cudaMemcpyAsync(h->fbuf, F[p], h->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+                loop_params(h, tol);
+            } else {
+                MultiWork& w = h->mw;
+                DDG_CUDA(cudaMemcpyAsync(w.Fb, F[p], h->n * m[p] * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+                w.h_ctl->tol = tol;
+                w.h_ctl->maxit = h->opt.maxit;
+                DDG_CUDA(cudaMemcpyAsync(w.ctl, w.h_ctl, sizeof(MultiCtl), cudaMemcpyHostToDevice, h->stream));
+            }
             DDG_CUDA(cudaEventRecord(ev[p], h->stream));
             DDG_CUDA(cudaStreamWaitEvent(L, ev[p], 0));
         }
-        DDG_CUDA(cudaGraphLaunch(ge, L));
+        DDG_CUDA(cudaGraphLaunch(mg.exec, L));
         DDG_CUDA(cudaEventRecord(ev[nprob], L));
         for (int p = 0; p < nprob; ++p) {
             ddg_handle h = hs[p];
             DDG_CUDA(cudaStreamWaitEvent(h->stream, ev[nprob], 0));
-            DDG_CUDA(cudaMemcpyAsync(U[p], h->ubuf, h->n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-            DDG_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, h->stream));
+            if (m[p] == 1) {
+                DDG_CUDA(cudaMemcpyAsync(U[p], h->ubuf, h->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+                DDG_CUDA(cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, h->stream));
+            } else {
+                MultiWork& w = h->mw;
+                DDG_CUDA(cudaMemcpyAsync(U[p], w.Ub, h->n * m[p] * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+                DDG_CUDA(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(MultiCtl), cudaMemcpyDeviceToHost, h->stream));
+            }
         }
         for (int p = 0; p < nprob; ++p) DDG_CUDA(cudaStreamSynchronize(hs[p]->stream));
         worst = DDG_OK;
+        int64_t off = 0;
         for (int p = 0; p < nprob; ++p) {
-            const ddg_status st = loop_outcome(hs[p], iters ? iters + p : nullptr, relres ? relres + p : nullptr);
+            ddg_handle h = hs[p];
+            ddg_status st = DDG_OK;
+            if (m[p] == 1) {
+                st = loop_outcome(h, iters ? iters + off : nullptr, relres ? relres + off : nullptr);
+            } else {
+                const MultiCtl& c = *h->mw.h_ctl;
+                for (int k = 0; k < DDG_K_COUNT; ++k)
+                    h->prof_launches[k] += mg.pre[p][k] + (int64_t)c.it * mg.body[p][k];
+                if (c.timed_out) {
+                    DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
+                    DDG_CUDA(cudaStreamSynchronize(h->stream));
+                    h->err = "a bounded wait of the tensor-core local solve ran out";
+                    st = DDG_ETIMEOUT;
+                }
+                for (int j = 0; j < m[p]; ++j) {
+                    if (iters) iters[off + j] = c.done_it[j];
+                    if (relres) relres[off + j] = c.done_rel[j];
+                    if (st == DDG_OK && c.cstat[j] != DDG_OK) st = (ddg_status)c.cstat[j];
+                }
+            }
             if (st != DDG_OK && worst == DDG_OK) worst = st;
+            off += m[p];
         }
     } catch (DdgError& e) {
         for (auto& x : ev)
             if (x) cudaEventDestroy(x);
         hs[0]->err = e.msg;
-        if (!ge) return false;   // the graph could not be built: solve the problems one by one
+        if (!built) return false;   // the graph could not be built: solve the problems one by one
         worst = e.st;
         return true;
     }
@@ -1666,6 +1900,10 @@ ddg_status ddg_set_generators(ddg_handle h, const double* F, int k) {
                 cudaGraphExecDestroy(g);
                 g = nullptr;
             }
+        for (auto& pe : h->batch_exec) {
+            for (auto& e : pe) cudaGraphExecDestroy(e.exec);
+            pe.clear();
+        }
         ++h->version;
         drop_many_graphs(h);
         for (void* p : h->coarse_allocs) h->arena.release(p);
@@ -2032,6 +2270,9 @@ ddg_status ddg_destroy(ddg_handle h) {
         if (g) cudaGraphExecDestroy(g);
     for (cudaGraphExec_t g : h->solve_exec)
         if (g) cudaGraphExecDestroy(g);
+    for (auto& pe : h->batch_exec)
+        for (auto& e : pe) cudaGraphExecDestroy(e.exec);
+    if (h->mw.h_ctl) cudaFreeHost(h->mw.h_ctl);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
     if (h->h_ctl) cudaFreeHost(h->h_ctl);

@@ -182,6 +182,14 @@ struct ProfileMat {         // rows with one contiguous column range each
     int64_t nnz = 0;
 };
 
+// Device-side state of a graph-driven batched PCG (per column: its own CG)
+struct MultiCtl {
+    int it, maxit, any_cand, any_restart, any_unfinished, timed_out, pad0, pad1;
+    double tol;
+    int done_it[DDG_MCHUNK], cstat[DDG_MCHUNK], nrest[DDG_MCHUNK], cand[DDG_MCHUNK];
+    double fn[DDG_MCHUNK], done_rel[DDG_MCHUNK];
+};
+
 // workspace of the batched (multi-RHS) PCG, grown on first use
 struct MultiWork {
     bool r32_current = false;   // r32 holds (float)R (written by update_ur)
@@ -198,6 +206,9 @@ struct MultiWork {
     std::vector<int> h_citem_off;
     float* gpart = nullptr;       // split partials of the coarse GEMMs
     unsigned* gtick = nullptr;    // one ticket per 32-row tile
+    int gen = 0;                  // bumped when the workspace is reallocated
+    MultiCtl* ctl = nullptr;      // graph-driven batched solves
+    MultiCtl* h_ctl = nullptr;    // pinned
 };
 
 // tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}
@@ -334,6 +345,14 @@ struct ddg_handle_s {
     CgCtl* h_ctl = nullptr;        // pinned host copy
     double *d_hist = nullptr, *d_alpha = nullptr, *d_beta = nullptr;   // [maxit + 1] each
     cudaGraphExec_t solve_exec[3] = {nullptr, nullptr, nullptr};
+    // whole batched solves per precision and column count (m <= DDG_MCHUNK)
+    struct BatchGraph {
+        int m;
+        cudaGraphExec_t exec;
+        int64_t pre[DDG_K_COUNT], body[DDG_K_COUNT];   // launches once / per iteration
+    };
+    std::vector<BatchGraph> batch_exec[3];
+    int batch_gen = 0;                 // MultiWork::gen the batched graphs were captured with
     int64_t solve_pre_launches[3][DDG_K_COUNT] = {};    // launched once per solve
     int64_t solve_body_launches[3][DDG_K_COUNT] = {};   // launched once per iteration
     bool solve_graph_failed = false;   // conditional graphs unavailable: host-driven loop
@@ -427,6 +446,17 @@ void multi_update_p(ddg_handle h, int m);
 void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double* out, int slot);
 void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace);
 void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int md, int k0, int cnt);
+// graph-driven batched PCG: gated variants and control kernels
+void multi_resnorm_gated(ddg_handle h, int m, const double* a, const double* b, double* out, int slot,
+                         const int* gate);
+void multi_replace_cols_gated(ddg_handle h, int m, const double* src, double* dst, const int* replace,
+                              const int* gate);
+void multi_to_float(ddg_handle h, int m, const int* gate);
+void mloop_init(ddg_handle h, int m, cudaGraphConditionalHandle cond);
+void mloop_decide_recurrence(ddg_handle h, int m);
+void mloop_decide_true(ddg_handle h, int m, cudaGraphConditionalHandle cond);
+void mloop_final_prep(ddg_handle h, int m);
+void mloop_final(ddg_handle h, int m);
 
 // k_cg.cu: control kernels of the graph-driven PCG
 void loop_init(ddg_handle h, cudaGraphConditionalHandle cond);

@@ -4,6 +4,8 @@
 // and restarts.  Every stage is a multi-column version of the single-RHS
 // kernel: the preconditioner reads each local inverse once per colour phase
 // for all m columns, which is what makes batching pay.
+#include <cstring>
+
 #include "ddg_internal.cuh"
 #include <algorithm>
 
@@ -301,7 +303,8 @@ __global__ void __launch_bounds__(MT) resnorm_multi_kernel(int64_t n, int m, con
                                                            const double* __restrict__ A_, const double* __restrict__ B_,
                                                            double* __restrict__ out, int nx, int ny, int nz,
                                                            double* partials, unsigned* counter, double* sc,
-                                                           int slot) {
+                                                           int slot, const int* gate) {
+    if (gate && !*gate) return;
     const int rpb = blockDim.x / m;
     const int c = threadIdx.x % m, rl = threadIdx.x / m;
     double acc[1] = {0.0};
@@ -318,7 +321,8 @@ __global__ void __launch_bounds__(MT) resnorm_multi_kernel(int64_t n, int m, con
 
 // copy the columns with replace[c] != 0 from src into dst (restart with the true residual)
 __global__ void replace_cols_kernel(int64_t n, int m, const double* __restrict__ src, double* __restrict__ dst,
-                                    const int* __restrict__ replace) {
+                                    const int* __restrict__ replace, const int* gate) {
+    if (gate && !*gate) return;
     const int rpb = blockDim.x / m;
     const int c = threadIdx.x % m;
     const int64_t g = (int64_t)blockIdx.x * rpb + threadIdx.x / m;
@@ -336,9 +340,114 @@ __global__ void copy_cols_kernel(int64_t n, const double* __restrict__ src, int 
     dst[g * md + k0 + t] = src[g * ms + j0 + t];
 }
 
-__global__ void to_float_n_kernel(int64_t cnt, const double* __restrict__ a, float* __restrict__ b) {
+__global__ void to_float_n_kernel(int64_t cnt, const double* __restrict__ a, float* __restrict__ b,
+                                  const int* gate = nullptr) {
+    if (gate && !*gate) return;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g < cnt) b[g] = (float)a[g];
+}
+
+// ---- control of the graph-driven batched PCG: one block of DDG_MCHUNK
+// threads, thread c for column c (the host loop's per-column decisions)
+__global__ void mloop_init_kernel(int m, MultiCtl* ctl, const double* sc, int* active, int* restart,
+                                  cudaGraphConditionalHandle cond) {
+    const int c = threadIdx.x;
+    bool act = false;
+    if (c < m) {
+        const double fn = sqrt(S(const_cast<double*>(sc), S_TMP, c));
+        act = fn > 0.0;
+        ctl->fn[c] = fn;
+        ctl->done_it[c] = act ? -1 : 0;
+        ctl->done_rel[c] = act ? -1.0 : 0.0;
+        ctl->cstat[c] = DDG_OK;
+        ctl->nrest[c] = 0;
+        ctl->cand[c] = 0;
+    }
+    active[c] = act ? 1 : 0;
+    restart[c] = 1;
+    const int any = __syncthreads_or(act);
+    if (c == 0) {
+        ctl->it = 0;
+        ctl->any_cand = 0;
+        ctl->any_restart = 0;
+        ctl->any_unfinished = 0;
+        ctl->timed_out = 0;
+        cudaGraphSetConditional(cond, any ? 1u : 0u);
+    }
+}
+
+// after the u/r update: breakdown, or the recurrence residual at or below tol
+// makes the column a candidate for the true-residual check
+__global__ void mloop_decide_recurrence_kernel(int m, MultiCtl* ctl, double* sc, int* active, int* restart) {
+    const int c = threadIdx.x;
+    const int it = ctl->it + 1;
+    restart[c] = 0;   // the dots of this iteration have used it
+    bool cand = false;
+    if (c < m && active[c]) {
+        if (S(sc, S_FLAG, c) != 0.0) {
+            ctl->cstat[c] = DDG_EBREAKDOWN;
+            active[c] = 0;
+            ctl->done_it[c] = it;
+        } else if (sqrt(S(sc, S_RR, c)) / ctl->fn[c] <= ctl->tol) {
+            cand = true;
+        }
+    }
+    if (c < m) ctl->cand[c] = cand ? 1 : 0;
+    const int any = __syncthreads_or(cand);
+    if (c == 0) {
+        ctl->it = it;
+        ctl->any_cand = any;
+        ctl->any_restart = 0;
+    }
+}
+
+// after the true residuals of the candidates: accept, give up after the last
+// restart, or restart the column from its true residual; loop condition
+__global__ void mloop_decide_true_kernel(int m, MultiCtl* ctl, const double* sc, int* active, int* restart,
+                                         const int* errflag, cudaGraphConditionalHandle cond) {
+    const int c = threadIdx.x;
+    const int it = ctl->it;
+    bool rs = false;
+    if (c < m && ctl->cand[c]) {
+        const double trel = sqrt(S(const_cast<double*>(sc), S_TMP, c)) / ctl->fn[c];
+        if (trel <= ctl->tol || ctl->nrest[c] >= DDG_MAX_RESTARTS) {
+            active[c] = 0;
+            ctl->done_it[c] = it;
+            ctl->done_rel[c] = trel;
+            ctl->cstat[c] = trel <= ctl->tol ? DDG_OK : DDG_ENOCONV;
+        } else {
+            restart[c] = 1;
+            ctl->nrest[c] += 1;
+            rs = true;
+        }
+        ctl->cand[c] = 0;
+    }
+    const int anyr = __syncthreads_or(rs);
+    const int anya = __syncthreads_or(c < m && active[c]);
+    if (c == 0) {
+        const int to = *errflag != 0;
+        ctl->any_restart = anyr;
+        ctl->timed_out = to;
+        cudaGraphSetConditional(cond, (anya && it < ctl->maxit && !to) ? 1u : 0u);
+    }
+}
+
+__global__ void mloop_final_prep_kernel(int m, MultiCtl* ctl) {
+    const int c = threadIdx.x;
+    const int any = __syncthreads_or(c < m && ctl->done_rel[c] < 0.0);
+    if (c == 0) ctl->any_unfinished = any;
+}
+
+// columns still running at the end (maxit, or a timeout) or broken down:
+// their true residual, and ENOCONV for the ones that never finished
+__global__ void mloop_final_kernel(int m, MultiCtl* ctl, const double* sc) {
+    const int c = threadIdx.x;
+    if (c >= m || !(ctl->done_rel[c] < 0.0)) return;
+    ctl->done_rel[c] = sqrt(S(const_cast<double*>(sc), S_TMP, c)) / ctl->fn[c];
+    if (ctl->done_it[c] < 0) {
+        ctl->done_it[c] = ctl->it;
+        ctl->cstat[c] = DDG_ENOCONV;
+    }
 }
 
 // ---------------------------------------------------------------- preconditioner
@@ -849,8 +958,14 @@ void multi_ensure(ddg_handle h, int m) {
     }
     w.items = h->arena.alloc<int2>(it.size());
     h2d(w.items, it.data(), it.size(), h->stream);
+    if (!w.ctl) {
+        w.ctl = h->arena.alloc<MultiCtl>(1);
+        DDG_CUDA(cudaMallocHost((void**)&w.h_ctl, sizeof(MultiCtl)));
+        std::memset(w.h_ctl, 0, sizeof(MultiCtl));
+    }
     DDG_CUDA(cudaStreamSynchronize(h->stream));
     w.m_alloc = m;
+    ++w.gen;
 }
 
 // algorithmic bytes of one tensor-core local-solve launch: the BF16 inverse
@@ -1010,15 +1125,54 @@ void multi_update_p(ddg_handle h, int m) {
 }
 
 // slot <- per-column ||a - A b||^2 (b may be null); out (may be null) <- a - A b
-void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double* out, int slot) {
+void multi_resnorm_gated(ddg_handle h, int m, const double* a, const double* b, double* out, int slot,
+                         const int* gate) {
     MultiWork& w = h->mw;
     const unsigned G = grid_for(h->n, m);
     const int bd = col_block(m);
 #define MR_CALL(SK)                                                                                        \
     resnorm_multi_kernel<SK><<<G, bd, 0, h->stream>>>(h->n, m, h->rowptr, h->col, h->val64, a, b, out, h->nx, \
-                                                      h->ny, h->nz, w.partials, h->red_counter, w.scal, slot)
+                                                      h->ny, h->nz, w.partials, h->red_counter, w.scal, slot, \
+                                                      gate)
     DDG_DISPATCH_SK(h, MR_CALL);
 #undef MR_CALL
+    DDG_CHECK_LAUNCH();
+}
+
+void multi_resnorm(ddg_handle h, int m, const double* a, const double* b, double* out, int slot) {
+    multi_resnorm_gated(h, m, a, b, out, slot, nullptr);
+}
+
+void multi_to_float(ddg_handle h, int m, const int* gate) {
+    MultiWork& w = h->mw;
+    to_float_n_kernel<<<(unsigned)((h->n * m + 255) / 256), 256, 0, h->stream>>>(h->n * m, w.R, w.r32, gate);
+    DDG_CHECK_LAUNCH();
+}
+
+void mloop_init(ddg_handle h, int m, cudaGraphConditionalHandle cond) {
+    mloop_init_kernel<<<1, DDG_MCHUNK, 0, h->stream>>>(m, h->mw.ctl, h->mw.scal, h->mw.active, h->mw.restart, cond);
+    DDG_CHECK_LAUNCH();
+}
+
+void mloop_decide_recurrence(ddg_handle h, int m) {
+    mloop_decide_recurrence_kernel<<<1, DDG_MCHUNK, 0, h->stream>>>(m, h->mw.ctl, h->mw.scal, h->mw.active,
+                                                                    h->mw.restart);
+    DDG_CHECK_LAUNCH();
+}
+
+void mloop_decide_true(ddg_handle h, int m, cudaGraphConditionalHandle cond) {
+    mloop_decide_true_kernel<<<1, DDG_MCHUNK, 0, h->stream>>>(m, h->mw.ctl, h->mw.scal, h->mw.active,
+                                                              h->mw.restart, h->errflags + E_TIMEOUT, cond);
+    DDG_CHECK_LAUNCH();
+}
+
+void mloop_final_prep(ddg_handle h, int m) {
+    mloop_final_prep_kernel<<<1, DDG_MCHUNK, 0, h->stream>>>(m, h->mw.ctl);
+    DDG_CHECK_LAUNCH();
+}
+
+void mloop_final(ddg_handle h, int m) {
+    mloop_final_kernel<<<1, DDG_MCHUNK, 0, h->stream>>>(m, h->mw.ctl, h->mw.scal);
     DDG_CHECK_LAUNCH();
 }
 
@@ -1027,11 +1181,17 @@ void copy_cols(ddg_handle h, const double* src, int ms, int j0, double* dst, int
     DDG_CHECK_LAUNCH();
 }
 
+void multi_replace_cols_gated(ddg_handle h, int m, const double* src, double* dst, const int* replace,
+                              const int* gate) {
+    const int bd = col_block(m), rpb = bd / m;
+    replace_cols_kernel<<<(unsigned)((h->n + rpb - 1) / rpb), bd, 0, h->stream>>>(h->n, m, src, dst, replace,
+                                                                                  gate);
+    DDG_CHECK_LAUNCH();
+}
+
 void multi_replace_cols(ddg_handle h, int m, const double* src, double* dst, const int* replace) {
     h->mw.r32_current = false;
-    const int bd = col_block(m), rpb = bd / m;
-    replace_cols_kernel<<<(unsigned)((h->n + rpb - 1) / rpb), bd, 0, h->stream>>>(h->n, m, src, dst, replace);
-    DDG_CHECK_LAUNCH();
+    multi_replace_cols_gated(h, m, src, dst, replace, nullptr);
 }
 
 }  // namespace ddg

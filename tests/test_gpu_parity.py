@@ -416,3 +416,52 @@ def test_graph_driven_solve_maxit_and_zero_rhs():
     u0, it0, rr0, st0 = capped.solve(dev(np.zeros(prob.n)), tol=1e-8)
     assert st0 == ddg.DDG_OK and it0 == 0 and rr0 == 0.0 and not u0.abs().max().item()
     capped.close()
+
+
+@pytest.mark.parametrize("name,m,prec,tc", [("poisson3d_ragged", 5, "fp32", False),
+                                            ("varcoef_24", 64, "bf16", True),
+                                            ("biharmonic_64", 4, "fp32", False)])
+def test_graph_driven_batch_equals_host_driven_batch(name, m, prec, tc):
+    # ddg_solve_batch as one graph launch (per-column control kernels decide
+    # convergence, true-residual checks and restarts on the device) against
+    # the host-driven loop: bitwise equal solutions, iterations and residuals
+    import os
+    from paper_1504_00907_gb300 import ddg
+    prob, _, _ = setup_case(name)
+    kw = dict(precision=prec, keep=(prec,), tensor_cores=tc)
+    g = ddg.Solver.from_problem(prob, **kw)
+    os.environ["DDG_NO_GRAPHS"] = "1"
+    try:
+        hst = ddg.Solver.from_problem(prob, **kw)
+    finally:
+        del os.environ["DDG_NO_GRAPHS"]
+    F = dev(di.normal_rhs(prob.n, 200 + m, m))
+    F[:, m // 2] = 0.0   # a zero column finishes before the loop
+    Ug, itg, rrg, stg = g.solve_batch(F, tol=1e-8)
+    Uh, ith, rrh, sth = hst.solve_batch(F, tol=1e-8)
+    assert stg == sth == ddg.DDG_OK
+    np.testing.assert_array_equal(itg, ith)
+    np.testing.assert_array_equal(rrg, rrh)
+    assert torch.equal(Ug, Uh)
+    assert itg[m // 2] == 0 and not Ug[:, m // 2].abs().max().item()
+    # the same graph again (cached), and a second column count
+    Ug2, itg2, _, _ = g.solve_batch(F, tol=1e-8)
+    assert torch.equal(Ug2, Ug) and np.array_equal(itg2, itg)
+    U3, it3, rr3, st3 = g.solve_batch(F[:, :3].contiguous(), tol=1e-8)
+    assert st3 == ddg.DDG_OK and np.all(rr3 <= 1e-8)
+    g.close()
+    hst.close()
+
+
+def test_graph_driven_batch_maxit_reports_every_column():
+    from paper_1504_00907_gb300 import ddg
+    prob, _, _ = setup_case("poisson3d_24")
+    s = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32",), maxit=2)
+    F = dev(di.normal_rhs(prob.n, 77, 6))
+    U, its, rrs, st = s.solve_batch(F, tol=1e-12)
+    assert st == ddg.DDG_ENOCONV and np.all(its == 2)
+    Un = U.cpu().numpy()
+    Fn = F.cpu().numpy()
+    true = np.linalg.norm(Fn - prob.A @ Un, axis=0) / np.linalg.norm(Fn, axis=0)
+    np.testing.assert_allclose(rrs, true, rtol=1e-8)
+    s.close()
