@@ -238,7 +238,8 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
     solved one at a time."""
     N, m = args.batched_size, args.batched_m
     prob = di.make_varcoef3d(N=N, box=8, overlap=1, p=2, m=m)
-    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32", "bf16"), tensor_cores=True)
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32", "bf16"), tensor_cores=True,
+                                     autotune=True)
     F = torch.tensor(prob.f, dtype=torch.float64, device=dev)
     out = {"workload": f"varcoef3d_{N}^3, {m} right-hand sides", "dofs": prob.n, "m": m,
            "arms": {"fp32": "FP32 SIMT local solves on packed FP32 inverses",
@@ -268,6 +269,9 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
     st = solver.kernel_stats()
     solver.profile(())   # the single-column comparison below runs without per-class events
     out["breakdown_bf16_tc"] = {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in st.items()}
+    inf = solver.info()
+    out["autotune"] = {k: inf[k] for k in ("tuned", "ls_warps", "ls_chunk_tiles", "ls_band_rows", "tc_stages")}
+    out["graph_launch_per_batched_solve"] = True
     out["breakdown_bf16_tc"]["total_ms_with_events"] = e0.elapsed_time(e1)
     ls = st["local_solve"]
     if ls["timed"]:
@@ -302,8 +306,8 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
     {32,48,64,80}^3, 4 each, 8^3 boxes + overlap 1, p <= 2) and 8 clamped 2D
     biharmonic (256^2 x3, 512^2 x3, 1024^2 x2, 16^2 boxes + overlap 2, p <= 3),
     f ~ U(-1, 1) from seed 100 + index, FP32 preconditioner, FP64 CG, tol 1e-8;
-    one after another on one stream, then concurrently (ddg_solve_many, one
-    stream per problem)."""
+    one after another on one stream, then all at once (ddg_solve_many: one
+    CUDA graph whose branches are the 24 whole solves, one launch)."""
     probs = []
     for i, N in enumerate([32, 48, 64, 80] * 4):
         probs.append(di.make_poisson3d(N=N, box=8, overlap=1, p=2, seed=100 + i))
@@ -311,7 +315,7 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
         probs.append(di.make_biharmonic2d(N=N, box=16, overlap=2, p=3, seed=116 + i))
     streams = [torch.cuda.Stream(device=dev) for _ in probs]
     t0 = time.perf_counter()
-    solvers = [ddg.Solver.from_problem(p, precision="fp32", keep=("fp32",), stream=s.cuda_stream)
+    solvers = [ddg.Solver.from_problem(p, precision="fp32", keep=("fp32",), stream=s.cuda_stream, autotune=True)
                for p, s in zip(probs, streams)]
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -672,10 +676,11 @@ def main():
     n = prob.n
     t_setup = time.perf_counter()
     keep = tuple(args.keep.split(","))
-    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=keep)
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=keep, autotune=True)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     info = solver.info()
+    tuning = {k: info[k] for k in ("tuned", "ls_warps", "ls_chunk_tiles", "ls_band_rows")}
     f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
     u = torch.empty_like(f)
     stream = torch.cuda.current_stream()
@@ -863,6 +868,8 @@ def main():
                             "mixed_bf16": world * n * it16[-1] / (ms16 / 1e3) if it16[-1] else None},
         "speedup_mixed_vs_fp64": ms64 / ms32,
         "setup_s": setup_s, "setup_ms_library": info["setup_ms"],
+        "autotune": tuning,
+        "graph_solve": solver.info()["graph_solve"],
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "gpu_launches_per_step": launches_per_step,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n,

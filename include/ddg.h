@@ -103,6 +103,16 @@ typedef struct {
                              of the tensor-core local solve), measured on the GPU's
                              global timer; a wait that runs out makes the call return
                              DDG_ETIMEOUT; default 1000 (0 also means 1000) */
+    int autotune;         /* 1: choose the launch shapes of the local solves by timing
+                             candidates on this handle's data at setup (warps per CTA
+                             4/8, tiles per work item 48/96/192 unless chunk_tiles is
+                             set, tile rows per item 8/16) and, for tensor-core batched
+                             solves, the operand ring depth 3/4/6 per column count; a
+                             choice is kept for the process per (largest block, number
+                             of subdomains and colours, columns, precision), so handles
+                             of one class share it; results change at rounding level
+                             with the shapes; default 0 (8 warps, 96 tiles, 16 rows, 4
+                             stages) */
 } ddg_options;
 
 typedef struct {
@@ -137,6 +147,11 @@ typedef struct {
                              (its CG loop decided on the device); 0: driven from the host
                              (tracing on, or DDG_NO_GRAPHS set); -1: conditional graphs
                              are unavailable, every solve is driven from the host */
+    int ls_warps;         /* warps per CTA of the single-vector local solve */
+    int ls_chunk_tiles;   /* tiles per local-solve work item (target) */
+    int ls_band_rows;     /* tile rows per local-solve work item (limit) */
+    int tc_stages;        /* operand ring depth of the tensor-core local solve */
+    int tuned;            /* 1: the shapes above were chosen by the autotuner */
 } ddg_info;
 
 /* Fill *opt with the defaults listed above. */

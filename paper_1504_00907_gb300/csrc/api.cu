@@ -6,7 +6,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <list>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <numeric>
 #include <thread>
 #include <unordered_map>
@@ -19,6 +21,8 @@
 namespace {
 
 thread_local std::string g_setup_error;
+
+void drop_graphs(ddg_handle h);
 
 double now_ms() {
     using namespace std::chrono;
@@ -1009,8 +1013,18 @@ const ddg_handle_s::BatchGraph* batch_graph(ddg_handle h, int m) {
 }
 
 ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol, int* iters, double* relres) {
-    if (!h->use_graphs || h->prof_mask != 0) return pcg_batch_host(h, F, U, m, tol, iters, relres);
     ddg::multi_ensure(h, m);
+    if (h->opt.autotune && h->precision == DDG_PREC_BF16 && h->tc.A) {
+        // the ring depth is a launch shape: tune it before a graph bakes it in
+        const int before = h->tc_stages;
+        if (h->tc.last_m != m) {
+            DDG_CUDA(cudaMemsetAsync(h->tc.X, 0, h->tc.x_elems * sizeof(__nv_bfloat16), h->stream));
+            h->tc.last_m = m;
+        }
+        ddg::autotune_tc(h, m);
+        if (h->tc_stages != before) drop_graphs(h);
+    }
+    if (!h->use_graphs || h->prof_mask != 0) return pcg_batch_host(h, F, U, m, tol, iters, relres);
     const ddg_handle_s::BatchGraph* bg = batch_graph(h, m);
     if (!bg) return pcg_batch_host(h, F, U, m, tol, iters, relres);
     cudaGraphExec_t ge = bg->exec;
@@ -1220,6 +1234,28 @@ bool solve_many_graph(ddg_handle* hs, int nprob, const double* const* F, double*
     return true;
 }
 
+// Destroy every captured graph of h (preconditioner applies, whole solves,
+// batched solves, combined graphs that include h): their kernels carry
+// arguments that a change of the handle makes stale.
+void drop_graphs(ddg_handle h) {
+    for (cudaGraphExec_t& g : h->apply_exec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (cudaGraphExec_t& g : h->solve_exec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    for (auto& pe : h->batch_exec) {
+        for (auto& e : pe) cudaGraphExecDestroy(e.exec);
+        pe.clear();
+    }
+    ++h->version;
+    drop_many_graphs(h);
+}
+
 template <typename Fn>
 ddg_status guarded(ddg_handle h, Fn&& fn) {
     if (!h) return DDG_EINVAL;
@@ -1389,6 +1425,230 @@ void build_coarse(ddg_handle h, const double* F, int k, int overlap, const ddg_o
         if (h->arena.ptrs[i]) h->coarse_allocs.push_back(h->arena.ptrs[i]);
 }
 }  // namespace
+
+namespace {
+// Work items of the single-vector local solve: bands of whole tile rows of
+// each packed upper triangle, about `chunk` tiles and at most `band` tile
+// rows each (a row joins the band only if it brings it closer to `chunk`).
+std::vector<int4> local_items(const ddg_handle h, int chunk, int band) {
+    std::vector<int4> items;
+    for (int c = 0; c < h->ncol; ++c)
+        for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
+            const int T = h->h_Tq[q];
+            int I = 0;
+            while (I < T) {
+                const int I0 = I;
+                int cnt = 0;
+                while (I < T && I - I0 < band) {
+                    const int len = T - I;
+                    if (cnt > 0 && cnt + len - chunk > chunk - cnt) break;
+                    cnt += len;
+                    ++I;
+                }
+                items.push_back(make_int4(q, I0, I, 0));
+            }
+        }
+    return items;
+}
+
+// (Re)build the work items and their metadata on the device; the partial
+// buffers are left to the caller (they hold nitems * Tmax * 32 values).
+void build_local_items(ddg_handle h, int chunk, int band) {
+    for (void* p : {(void*)h->items, (void*)h->nchunks, (void*)h->first_item, (void*)h->counters,
+                    (void*)h->ov_sub, (void*)h->row_nchunks})
+        if (p) h->arena.release(p);
+    const int nsub = h->nsub;
+    const std::vector<int4> items = local_items(h, chunk, band);
+    std::vector<int32_t> nch(nsub, 0), first(nsub, 0);
+    h->h_citem_off.assign(h->ncol + 1, 0);
+    for (size_t i = 0; i < items.size(); ++i) {
+        const int q = items[i].x;
+        if (nch[q]++ == 0) first[q] = (int)i;
+    }
+    for (int c = 0; c < h->ncol; ++c) {
+        int cnt = 0;
+        for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) cnt += nch[q];
+        h->h_citem_off[c + 1] = h->h_citem_off[c] + cnt;
+    }
+    h->nitems = (int)items.size();
+    h->items = h->arena.alloc<int4>(items.size());
+    h->nchunks = h->arena.alloc<int32_t>(nsub);
+    h->first_item = h->arena.alloc<int32_t>(nsub);
+    h->counters = h->arena.alloc<unsigned>(nsub);
+    h2d(h->items, items.data(), items.size(), h->stream);
+    h2d(h->nchunks, nch.data(), nsub, h->stream);
+    h2d(h->first_item, first.data(), nsub, h->stream);
+    DDG_CUDA(cudaMemsetAsync(h->counters, 0, nsub * sizeof(unsigned), h->stream));
+    const std::vector<int64_t>& ov_off = h->h_ov_off;
+    std::vector<int32_t> ovs(h->sum_local), rnc(h->sum_local);
+    for (int q = 0; q < nsub; ++q)
+        for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) {
+            ovs[a] = q;
+            const int row_tile = (int)((a - ov_off[q]) / DDG_LT);
+            int c = 0;
+            while (c < nch[q] && items[first[q] + c].y <= row_tile) ++c;
+            rnc[a] = c;
+        }
+    h->ov_sub = h->arena.alloc<int32_t>(h->sum_local);
+    h->row_nchunks = h->arena.alloc<int32_t>(h->sum_local);
+    h2d(h->ov_sub, ovs.data(), h->sum_local, h->stream);
+    h2d(h->row_nchunks, rnc.data(), h->sum_local, h->stream);
+    h->split_gather = *std::max_element(nch.begin(), nch.end()) > DDG_GATHER_SPLIT_CHUNKS;
+    h->ls_chunk = chunk;
+    h->ls_band_rows = band;
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+}
+
+// ---------------------------------------------------------------- autotuner
+// Launch shapes of the local solves chosen by timing candidates on the
+// handle's own data (CUDA events on its stream, median of three launches of
+// the colour with the most local rows), keyed on the local-block class (the
+// largest block, the number of subdomains and colours), the column count m
+// and the precision; a choice is kept process-wide, so a second handle of
+// the same class reuses it (and computes the same bits) without timing.
+struct TuneKey {
+    int max_local, nsub, ncol, m, prec;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(max_local, nsub, ncol, m, prec) < std::tie(o.max_local, o.nsub, o.ncol, o.m, o.prec);
+    }
+};
+struct TuneChoice {
+    int warps = 8, chunk = 96, band = DDG_BAND_ROWS, stages = 4;
+    double ms = 0.0;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+
+int largest_colour(ddg_handle h) {
+    int best = 0;
+    for (int c = 1; c < h->ncol; ++c)
+        if (h->h_crow_off[c + 1] - h->h_crow_off[c] > h->h_crow_off[best + 1] - h->h_crow_off[best]) best = c;
+    return best;
+}
+
+// median of three timed runs of `launch` after one warm-up, in ms
+template <typename Fn>
+double time_launches(ddg_handle h, Fn&& launch) {
+    cudaEvent_t e0, e1;
+    DDG_CUDA(cudaEventCreate(&e0));
+    DDG_CUDA(cudaEventCreate(&e1));
+    launch();
+    std::vector<float> t;
+    for (int r = 0; r < 3; ++r) {
+        DDG_CUDA(cudaEventRecord(e0, h->stream));
+        launch();
+        DDG_CUDA(cudaEventRecord(e1, h->stream));
+        DDG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        DDG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        t.push_back(ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::sort(t.begin(), t.end());
+    return t[1];
+}
+
+void alloc_partials(ddg_handle h, int nitems) {
+    if (h->partial64) h->arena.release(h->partial64);
+    if (h->partial32) h->arena.release(h->partial32);
+    h->partial64 = nullptr;
+    h->partial32 = nullptr;
+    const size_t pslots = (size_t)nitems * h->Tmax * DDG_LT;
+    const int keep = h->opt.keep_precisions;
+    if (keep & (1 << DDG_PREC_FP64)) h->partial64 = h->arena.alloc<double>(pslots);
+    if (keep & ((1 << DDG_PREC_FP32) | (1 << DDG_PREC_BF16))) h->partial32 = h->arena.alloc<float>(pslots);
+}
+
+// warps per CTA {8, 4} x tiles per item {48, 96, 192} x tile rows per item
+// {8, 16} for the single-vector local solve in the handle's precision (the
+// tiles per item stay fixed when chunk_tiles was given)
+void autotune_local(ddg_handle h) {
+    const int prec = h->precision;
+    const TuneKey key{h->max_local, h->nsub, h->ncol, 1, prec};
+    TuneChoice best;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        std::vector<int> chunks = {48, 96, 192};
+        if (h->opt.chunk_tiles > 0) chunks = {h->opt.chunk_tiles};
+        int max_items = 0;
+        for (int ch : chunks)
+            for (int band : {8, DDG_BAND_ROWS})
+                max_items = std::max(max_items, (int)local_items(h, ch, band).size());
+        alloc_partials(h, max_items);
+        const int c = largest_colour(h);
+        if (prec == DDG_PREC_FP64) {
+            DDG_CUDA(cudaMemsetAsync(h->res64, 0, h->sum_local * sizeof(double), h->stream));
+            DDG_CUDA(cudaMemsetAsync(h->z64, 0, h->n * sizeof(double), h->stream));
+        } else {
+            DDG_CUDA(cudaMemsetAsync(h->res32, 0, h->sum_local * sizeof(float), h->stream));
+            DDG_CUDA(cudaMemsetAsync(h->z32, 0, h->n * sizeof(float), h->stream));
+        }
+        best.ms = 1e30;
+        for (int ch : chunks)
+            for (int band : {DDG_BAND_ROWS, 8}) {
+                build_local_items(h, ch, band);
+                for (int w : {8, 4}) {
+                    h->ls_warps = w;
+                    const double ms = time_launches(h, [&]() { ddg::local_solve_colour(h, c, prec); });
+                    // a candidate replaces the incumbent only when more than 2% faster
+                    if (ms < best.ms * 0.98) {
+                        best.ms = ms;
+                        best.warps = w;
+                        best.chunk = ch;
+                        best.band = band;
+                    }
+                }
+            }
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune.emplace(key, best);
+    }
+    h->ls_warps = best.warps;
+    build_local_items(h, best.chunk, best.band);
+    alloc_partials(h, h->nitems);
+    h->tuned = 1;
+    h->tune_ms = best.ms;
+}
+}  // namespace
+
+namespace ddg {
+// tensor-core ring depth {3, 4, 6} for m columns (called before the batched
+// solve is captured or run; cached per class and m)
+void autotune_tc(ddg_handle h, int m) {
+    const TuneKey key{h->max_local, h->nsub, h->ncol, m, DDG_PREC_BF16};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            h->tc_stages = it->second.stages;
+            return;
+        }
+    }
+    const int c = largest_colour(h);
+    TuneChoice best;
+    best.ms = 1e30;
+    for (int st : {4, 3, 6}) {
+        h->tc_stages = st;
+        const double ms = time_launches(h, [&]() { ddg::tc_local_solve(h, c, m); });
+        if (ms < best.ms * 0.98) {
+            best.ms = ms;
+            best.stages = st;
+        }
+    }
+    DDG_CUDA(cudaMemsetAsync(h->mw.z32, 0, h->n * m * sizeof(float), h->stream));
+    h->tc_stages = best.stages;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.emplace(key, best);
+}
+}  // namespace ddg
 
 static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, const int32_t* groups,
                              const double* F, int k, int overlap, const ddg_options* opt, void* stream,
@@ -1564,58 +1824,10 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         ov.shrink_to_fit();
 
         // ---- local-solve work items: bands of whole tile rows of the packed
-        // upper triangle, about `chunk` tiles and at most DDG_BAND_ROWS rows each
-        {
-            const int chunk = o.chunk_tiles > 0 ? o.chunk_tiles : 96;
-            std::vector<int4> items;
-            std::vector<int32_t> nch(nsub), first(nsub);
-            h->h_citem_off.assign(h->ncol + 1, 0);
-            for (int c = 0; c < h->ncol; ++c) {
-                for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
-                    const int T = Tq[q];
-                    first[q] = (int)items.size();
-                    int I = 0;
-                    while (I < T) {
-                        const int I0 = I;
-                        int cnt = 0;
-                        while (I < T && I - I0 < DDG_BAND_ROWS) {
-                            const int len = T - I;
-                            // a further row only if it brings the band closer to `chunk` tiles
-                            if (cnt > 0 && cnt + len - chunk > chunk - cnt) break;
-                            cnt += len;
-                            ++I;
-                        }
-                        items.push_back(make_int4(q, I0, I, 0));
-                    }
-                    nch[q] = (int)items.size() - first[q];
-                }
-                h->h_citem_off[c + 1] = (int)items.size();
-            }
-            h->nitems = (int)items.size();
-            h->items = h->arena.alloc<int4>(items.size());
-            h->nchunks = h->arena.alloc<int32_t>(nsub);
-            h->first_item = h->arena.alloc<int32_t>(nsub);
-            h->counters = h->arena.alloc<unsigned>(nsub);
-            h2d(h->items, items.data(), items.size(), h->stream);
-            h2d(h->nchunks, nch.data(), nsub, h->stream);
-            h2d(h->first_item, first.data(), nsub, h->stream);
-            DDG_CUDA(cudaMemsetAsync(h->counters, 0, nsub * sizeof(unsigned), h->stream));
-            std::vector<int32_t> ovs(h->sum_local), rnc(h->sum_local);
-            for (int q = 0; q < nsub; ++q)
-                for (int64_t a = ov_off[q]; a < ov_off[q + 1]; ++a) {
-                    ovs[a] = q;
-                    const int row_tile = (int)((a - ov_off[q]) / DDG_LT);
-                    int c = 0;
-                    while (c < nch[q] && items[first[q] + c].y <= row_tile) ++c;
-                    rnc[a] = c;
-                }
-            h->ov_sub = h->arena.alloc<int32_t>(h->sum_local);
-            h->row_nchunks = h->arena.alloc<int32_t>(h->sum_local);
-            h2d(h->ov_sub, ovs.data(), h->sum_local, h->stream);
-            h2d(h->row_nchunks, rnc.data(), h->sum_local, h->stream);
-            h->split_gather = *std::max_element(nch.begin(), nch.end()) > DDG_GATHER_SPLIT_CHUNKS;
-            DDG_CUDA(cudaStreamSynchronize(h->stream));
-        }
+        // upper triangle, about `chunk` tiles and at most ls_band_rows rows each
+        h->h_Tq = Tq;
+        if (o.chunk_tiles > 0) h->ls_chunk = o.chunk_tiles;
+        build_local_items(h, h->ls_chunk, h->ls_band_rows);
 
         // algorithmic bytes of one local-solve launch per colour and precision:
         // packed triangle of A_i^{-1} + residual read + z read and write
@@ -1715,9 +1927,7 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         ddg::local_configure(h);
         h->res64 = h->arena.alloc<double>(h->sum_local);
         h->res32 = h->arena.alloc<float>(h->sum_local);
-        const size_t pslots = (size_t)h->nitems * h->Tmax * DDG_LT;
-        if (keep & (1 << DDG_PREC_FP64)) h->partial64 = h->arena.alloc<double>(pslots);
-        if (keep & ((1 << DDG_PREC_FP32) | (1 << DDG_PREC_BF16))) h->partial32 = h->arena.alloc<float>(pslots);
+        alloc_partials(h, h->nitems);
 
         // ---- coarse space (Sec. 4): pairs of subdomains that A couples, then
         // R0, A0 and its factor (or the coarse level of the V-cycle)
@@ -1741,6 +1951,8 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         h->red_partials = h->arena.alloc<double>((size_t)DDG_RED_BLOCKS * 4);
         h->red_counter = h->arena.alloc<unsigned>(1);
         DDG_CUDA(cudaMemsetAsync(h->red_counter, 0, sizeof(unsigned), h->stream));
+
+        if (o.autotune) autotune_local(h);
 
         int32_t flags[E_COUNT];
         d2h(flags, h->errflags, E_COUNT, h->stream);
@@ -1890,22 +2102,7 @@ ddg_status ddg_set_generators(ddg_handle h, const double* F, int k) {
         DDG_REQUIRE(F && k >= 1 && k <= DDG_KMAX, DDG_EINVAL, "F must be non-null and k in [1, 96]");
         DDG_CUDA(cudaStreamSynchronize(h->stream));
         // the captured graphs hold launches of the old coarse space
-        for (cudaGraphExec_t& g : h->apply_exec)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
-            }
-        for (cudaGraphExec_t& g : h->solve_exec)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
-            }
-        for (auto& pe : h->batch_exec) {
-            for (auto& e : pe) cudaGraphExecDestroy(e.exec);
-            pe.clear();
-        }
-        ++h->version;
-        drop_many_graphs(h);
+        drop_graphs(h);
         for (void* p : h->coarse_allocs) h->arena.release(p);
         h->coarse_allocs.clear();
         h->Q64 = nullptr;
@@ -2091,6 +2288,8 @@ ddg_status ddg_spmv(ddg_handle h, const double* x, double* y) {
 ddg_status ddg_set_debug(ddg_handle h, int flags) {
     return guarded(h, [&]() {
         DDG_REQUIRE((flags & ~DDG_DEBUG_TC_NO_COPIES) == 0, DDG_EINVAL, "unknown debug flag");
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        if (flags != h->debug) drop_graphs(h);   // the flags are launch arguments of captured kernels
         h->debug = flags;
         return DDG_OK;
     });
@@ -2131,6 +2330,11 @@ ddg_status ddg_get_info(ddg_handle h, ddg_info* info) {
         info->precision = h->precision;
         info->local_inverses = h->nrep_local;
         info->graph_solve = h->solve_graph_failed ? -1 : h->last_solve_graph;
+        info->ls_warps = h->ls_warps;
+        info->ls_chunk_tiles = h->ls_chunk;
+        info->ls_band_rows = h->ls_band_rows;
+        info->tc_stages = h->tc_stages;
+        info->tuned = h->tuned;
         return DDG_OK;
     });
 }

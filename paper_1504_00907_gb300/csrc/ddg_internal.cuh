@@ -233,6 +233,11 @@ struct ddg_handle_s {
     int precision = DDG_PREC_FP64;
     double setup_ms = 0.0;
     int device = 0;                 // CUDA device current at setup; made current by every call
+    // launch shapes (autotuned when opt.autotune is set): warps per local-solve
+    // CTA, tiles and tile rows per local-solve work item, tensor-core ring depth
+    int ls_warps = 8, ls_chunk = 96, ls_band_rows = DDG_BAND_ROWS, tc_stages = 4;
+    int tuned = 0;                  // 1: ls_* chosen by timing candidates (or a cached choice)
+    double tune_ms = 0.0;           // local-solve time of one colour phase with the choice
     int debug = 0;                  // DDG_DEBUG_* test hooks (ddg_set_debug)
     unsigned long long wait_ns = 1000000000ull;   // limit of every device-side wait
 
@@ -269,6 +274,7 @@ struct ddg_handle_s {
     int64_t* ov_off = nullptr;
     int32_t* ov_nodes = nullptr;
     int32_t* Tq = nullptr;
+    std::vector<int32_t> h_Tq;     // [nsub] tile rows of each packed inverse (host)
     int64_t* tile_off = nullptr;   // [nsub + 1] element offset of each packed inverse
     int64_t inv_elems = 0;         // elements of all packed inverses
     // local-solve work items per colour: {q, tile_begin, tile_end, unused}
@@ -469,6 +475,9 @@ int tc_n_for(int m);
 void tc_pack(ddg_handle h, int q0, int q1, const int32_t* qlist, const double* ws);
 void tc_residual(ddg_handle h, int colour, bool z_zero, int m);
 void tc_local_solve(ddg_handle h, int colour, int m);
+
+// api.cu: autotuner of the tensor-core ring depth for m columns
+void autotune_tc(ddg_handle h, int m);
 
 // api.cu: error message of a handle-less call, read by ddg_last_error(NULL)
 void set_handleless_error(const char* msg);

@@ -401,23 +401,22 @@ template <> struct Cvt<__nv_bfloat16, float> {
     }
 };
 
-constexpr int LS_WARPS = 8;
-
-// x and yT (Tmax * 32 each) and the per-warp row slices yR
-template <typename V>
+// x and yT (Tmax * 32 each) and the per-warp row slices yR of W warps
+template <typename V, int W>
 constexpr size_t local_solve_smem(int Tmax) {
-    return (2 * (size_t)Tmax * DDG_LT + (size_t)LS_WARPS * DDG_BAND_ROWS * DDG_LT) * sizeof(V);
+    return (2 * (size_t)Tmax * DDG_LT + (size_t)W * DDG_BAND_ROWS * DDG_LT) * sizeof(V);
 }
 
 // One work item = a band of whole tile rows [I0, I1) of one subdomain's
-// packed upper triangle.  Tile (I, J) belongs to warp J mod LS_WARPS, so the
+// packed upper triangle, processed by LS_WARPS warps (a tuning parameter:
+// 4 or 8).  Tile (I, J) belongs to warp J mod LS_WARPS, so the
 // transposed products B^T x_I land in y[J] entries that only one warp
 // writes (one shared accumulator yT, no atomics); each warp keeps the row
 // products B x_J of the current row in a register and stores them once per
 // row in its slice of yR (at most DDG_BAND_ROWS rows per band).  The chunk
 // result yT + sum_w yR[w] is formed in a fixed order, so it is deterministic.
-template <typename E, typename V, bool SPLIT>
-__global__ void __launch_bounds__(LS_WARPS * 32, sizeof(V) == 4 ? 4 : 2) local_solve_kernel(
+template <typename E, typename V, bool SPLIT, int LS_WARPS>
+__global__ void __launch_bounds__(LS_WARPS * 32, (sizeof(V) == 4 ? 4 : 2) * (8 / LS_WARPS)) local_solve_kernel(
     const int4* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
     const int32_t* __restrict__ ov_nodes, const int64_t* __restrict__ tile_off,
     const int32_t* __restrict__ Tq, const int32_t* __restrict__ nchunks,
@@ -697,13 +696,13 @@ void local_residual(ddg_handle h, int c, bool z_zero, int prec) {
 #undef LR_CALL
 }
 
-template <typename E, typename V>
-static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, V* partial, V* z) {
+template <typename E, typename V, int W>
+static void launch_local_solve_w(ddg_handle h, int c, const E* inv, const V* res, V* partial, V* z) {
     const int i0 = h->h_citem_off[c], i1 = h->h_citem_off[c + 1];
     if (i1 <= i0) return;
-    const size_t smem = local_solve_smem<V>(h->Tmax);
-    auto kern = h->split_gather ? local_solve_kernel<E, V, true> : local_solve_kernel<E, V, false>;
-    launch_pdl(h, kern, dim3(i1 - i0), dim3(LS_WARPS * 32), smem, (const int4*)h->items, i0,
+    const size_t smem = local_solve_smem<V, W>(h->Tmax);
+    auto kern = h->split_gather ? local_solve_kernel<E, V, true, W> : local_solve_kernel<E, V, false, W>;
+    launch_pdl(h, kern, dim3(i1 - i0), dim3(W * 32), smem, (const int4*)h->items, i0,
                (const int64_t*)h->ov_off, (const int32_t*)h->ov_nodes, (const int64_t*)h->tile_off,
                (const int32_t*)h->Tq, (const int32_t*)h->nchunks, (const int32_t*)h->first_item,
                (const int32_t*)h->row_nchunks, inv, res, partial, h->counters, z, h->Tmax);
@@ -717,26 +716,35 @@ static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, 
     }
 }
 
+template <typename E, typename V>
+static void launch_local_solve(ddg_handle h, int c, const E* inv, const V* res, V* partial, V* z) {
+    if (h->ls_warps == 4) launch_local_solve_w<E, V, 4>(h, c, inv, res, partial, z);
+    else launch_local_solve_w<E, V, 8>(h, c, inv, res, partial, z);
+}
+
 // The dynamic shared-memory limit is a property of the kernel on each device,
 // shared by all handles there: raise it to the largest size any handle on
 // that device needs, never lower it.
-template <typename E, typename V>
+template <typename E, typename V, int W>
 static void configure_local_solve(int Tmax) {
     static PerDeviceMax configured;
-    const int smem = (int)local_solve_smem<V>(Tmax);
+    const int smem = (int)local_solve_smem<V, W>(Tmax);
     int dev = -1;
     if (!configured.needs(smem, dev)) return;
-    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, false>,
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, false, W>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, true>,
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_kernel<E, V, true, W>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured.commit(dev, smem);
 }
 
 void local_configure(ddg_handle h) {
-    configure_local_solve<double, double>(h->Tmax);
-    configure_local_solve<float, float>(h->Tmax);
-    configure_local_solve<__nv_bfloat16, float>(h->Tmax);
+    configure_local_solve<double, double, 8>(h->Tmax);
+    configure_local_solve<float, float, 8>(h->Tmax);
+    configure_local_solve<__nv_bfloat16, float, 8>(h->Tmax);
+    configure_local_solve<double, double, 4>(h->Tmax);
+    configure_local_solve<float, float, 4>(h->Tmax);
+    configure_local_solve<__nv_bfloat16, float, 4>(h->Tmax);
 }
 
 void local_solve_colour(ddg_handle h, int c, int prec) {

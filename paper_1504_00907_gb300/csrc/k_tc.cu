@@ -26,7 +26,8 @@ namespace {
 
 constexpr int TC_M = 128;            // rows of Y per CTA (MMA M)
 constexpr int TC_K = 32;             // K per slab (two K = 16 MMAs)
-constexpr int TC_STAGES = 4;           // ring depth (measured against 3, 5, 6 and 8)
+// ring depth TC_STAGES: a template parameter (3, 4 or 6), chosen per column
+// count by the autotuner (4 when it is off)
 constexpr int TC_THREADS = 128;
 constexpr int A_SLAB = TC_M * TC_K;       // elements per A slab
 
@@ -78,7 +79,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int N>
+template <int N, int TC_STAGES>
 __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
     const int2* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
     const int32_t* __restrict__ ov_nodes, const int32_t* __restrict__ Tq,
@@ -403,25 +404,38 @@ __global__ void __launch_bounds__(256) tc_residual_kernel(
     }
 }
 
-template <int N>
+template <int N, int TC_STAGES>
+constexpr int tc_smem() {
+    return TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+}
+
+template <int N, int TC_STAGES>
 void configure_tc() {
     static PerDeviceMax configured;   // the attribute is per device
-    const int smem = TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+    constexpr int smem = tc_smem<N, TC_STAGES>();
     int dev = -1;
     if (!configured.needs(smem, dev)) return;
-    DDG_CUDA(cudaFuncSetAttribute(local_solve_tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_tc_kernel<N, TC_STAGES>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured.commit(dev, smem);
 }
 
-template <int N>
-void launch_tc(ddg_handle h, int i0, int i1, int m) {
-    configure_tc<N>();
-    const int smem = TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
-    local_solve_tc_kernel<N><<<i1 - i0, TC_THREADS, smem, h->stream>>>(
+template <int N, int TC_STAGES>
+void launch_tc_s(ddg_handle h, int i0, int i1, int m) {
+    configure_tc<N, TC_STAGES>();
+    constexpr int smem = tc_smem<N, TC_STAGES>();
+    local_solve_tc_kernel<N, TC_STAGES><<<i1 - i0, TC_THREADS, smem, h->stream>>>(
         h->tc.items, i0, h->ov_off, h->ov_nodes, h->Tq, h->tc.slab_off, h->tc.xoff, h->tc.A, h->tc.X,
         h->mw.z32, m, h->errflags + E_TIMEOUT, (uint64_t)h->wait_ns,
         (h->debug & DDG_DEBUG_TC_NO_COPIES) ? 1 : 0);
     DDG_CHECK_LAUNCH();
+}
+
+template <int N>
+void launch_tc(ddg_handle h, int i0, int i1, int m) {
+    if (h->tc_stages == 3) launch_tc_s<N, 3>(h, i0, i1, m);
+    else if (h->tc_stages == 6) launch_tc_s<N, 6>(h, i0, i1, m);
+    else launch_tc_s<N, 4>(h, i0, i1, m);
 }
 
 }  // namespace

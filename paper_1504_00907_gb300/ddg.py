@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
                 ("overlap_mode", ctypes.c_int), ("beta", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("use_coarse", ctypes.c_int), ("rank_tol", ctypes.c_double),
                 ("chunk_tiles", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("dedup_local", ctypes.c_int), ("spin_budget_ms", ctypes.c_double)]
+                ("dedup_local", ctypes.c_int), ("spin_budget_ms", ctypes.c_double),
+                ("autotune", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -52,7 +53,9 @@ class Info(ctypes.Structure):
                 ("sum_local", ctypes.c_int64), ("local_tiles", ctypes.c_int64),
                 ("coarse_band", ctypes.c_int), ("coarse_blocks", ctypes.c_int),
                 ("setup_ms", ctypes.c_double), ("precision", ctypes.c_int),
-                ("local_inverses", ctypes.c_int), ("graph_solve", ctypes.c_int)]
+                ("local_inverses", ctypes.c_int), ("graph_solve", ctypes.c_int),
+                ("ls_warps", ctypes.c_int), ("ls_chunk_tiles", ctypes.c_int), ("ls_band_rows", ctypes.c_int),
+                ("tc_stages", ctypes.c_int), ("tuned", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -179,7 +182,8 @@ class Solver:
     def __init__(self, A, part, F, overlap, *, mode="graph", shape=None, stencil_kind=0,
                  coef=None, dofs_per_node=1, precision="fp64", keep=None, beta="auto",
                  maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
-                 stream=None, coarse_groups=None, dedup_local=False, spin_budget_ms=1000.0):
+                 stream=None, coarse_groups=None, dedup_local=False, spin_budget_ms=1000.0,
+                 autotune=False):
         import torch
         lib = load()
         if not torch.cuda.is_available():
@@ -220,6 +224,7 @@ class Solver:
         o.tensor_cores = 1 if tensor_cores else 0
         o.dedup_local = 1 if dedup_local else 0
         o.spin_budget_ms = spin_budget_ms
+        o.autotune = 1 if autotune else 0
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream

@@ -465,3 +465,42 @@ def test_graph_driven_batch_maxit_reports_every_column():
     true = np.linalg.norm(Fn - prob.A @ Un, axis=0) / np.linalg.norm(Fn, axis=0)
     np.testing.assert_allclose(rrs, true, rtol=1e-8)
     s.close()
+
+
+def test_autotuned_launch_shapes_keep_parity():
+    # the autotuner times local-solve launch shapes on the handle's data at
+    # setup; the choice is reported, kept for the class (a second handle of
+    # the same problem reuses it and computes the same bits), and the solve
+    # still matches the oracle
+    from paper_1504_00907_gb300 import ddg
+    prob, _, oracle = setup_case("poisson3d_24")
+    a = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32",), autotune=True)
+    b = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32",), autotune=True)
+    ia, ib = a.info(), b.info()
+    assert ia["tuned"] == ib["tuned"] == 1
+    assert ia["ls_warps"] in (4, 8) and ia["ls_chunk_tiles"] in (48, 96, 192) and ia["ls_band_rows"] in (8, 16)
+    for k in ("ls_warps", "ls_chunk_tiles", "ls_band_rows"):
+        assert ia[k] == ib[k]
+    f = dev(prob.f)
+    ua, ita, rra, sta = a.solve(f, tol=1e-8)
+    ub, itb, rrb, stb = b.solve(f, tol=1e-8)
+    assert sta == stb == 0 and ita == itb and torch.equal(ua, ub)
+    ref = orc.pcg(oracle.A, prob.f, oracle.apply, tol=1e-8)
+    assert_close(ua.cpu().numpy(), ref.u, 1e-7)
+    r = np.random.default_rng(12).standard_normal(prob.n)
+    assert_close(a.apply(dev(r)).cpu().numpy(), oracle.apply(r), 1e-5)
+    a.close()
+    b.close()
+
+
+def test_autotuned_tensor_core_stages_keep_parity():
+    from paper_1504_00907_gb300 import ddg
+    prob, _, oracle = setup_case("varcoef_24")
+    s = ddg.Solver.from_problem(prob, precision="bf16", keep=("bf16",), tensor_cores=True, autotune=True)
+    F = di.normal_rhs(prob.n, 300, 16)
+    U, its, rrs, st = s.solve_batch(dev(F), tol=1e-8)
+    assert st == 0 and np.all(rrs <= 1e-8)
+    assert s.info()["tc_stages"] in (3, 4, 6)
+    ref = orc.pcg(oracle.A, F[:, 0], oracle.apply, tol=1e-8)
+    assert_close(U[:, 0].cpu().numpy(), ref.u, 1e-7)
+    s.close()
