@@ -64,6 +64,12 @@ enum { DDG_PREC_FP64 = 0, DDG_PREC_FP32 = 1, DDG_PREC_BF16 = 2 };
  * paper's definition); BOX = L-infinity grid distance Delta (needs the grid
  * shape in ddg_matrix; dofs must be in natural x-fastest grid order) */
 enum { DDG_OVERLAP_GRAPH = 0, DDG_OVERLAP_BOX = 1 };
+/* representation of the exact local solves A_i^{-1} (Sec. 6): dense inverses
+ * (packed symmetric tiles; overlapping subdomains of at most 3072 dofs) or
+ * banded Cholesky factors of A_i in its ascending dof order (any size; the
+ * work grows with the half-bandwidth).  AUTO takes the inverses when every
+ * block fits them, else the band. */
+enum { DDG_LOCAL_AUTO = 0, DDG_LOCAL_INV = 1, DDG_LOCAL_BAND = 2 };
 /* CG beta: Fletcher-Reeves (textbook) or Polak-Ribiere (flexible) */
 enum { DDG_BETA_FR = 0, DDG_BETA_PR = 1, DDG_BETA_AUTO = 2 };
 /* optional structure of A that enables a matrix-free SpMV for the FP64
@@ -113,6 +119,10 @@ typedef struct {
                              of one class share it; results change at rounding level
                              with the shapes; default 0 (8 warps, 96 tiles, 16 rows, 4
                              stages) */
+    int local_repr;       /* DDG_LOCAL_*, default AUTO.  With BAND: the BF16 precision
+                             uses the FP32 factors, tensor_cores and dedup_local are not
+                             available, ddg_solve_batch solves its columns one at a time,
+                             and the half-bandwidth must be at most 1024 */
 } ddg_options;
 
 typedef struct {
@@ -152,6 +162,9 @@ typedef struct {
     int ls_band_rows;     /* tile rows per local-solve work item (limit) */
     int tc_stages;        /* operand ring depth of the tensor-core local solve */
     int tuned;            /* 1: the shapes above were chosen by the autotuner */
+    int local_repr;       /* DDG_LOCAL_INV or DDG_LOCAL_BAND (what setup chose) */
+    int local_band;       /* half-bandwidth of the local matrices (BAND), else 0 */
+    int64_t local_elems;  /* stored elements of all local operators (one precision) */
 } ddg_info;
 
 /* Fill *opt with the defaults listed above. */

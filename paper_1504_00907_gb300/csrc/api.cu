@@ -251,6 +251,7 @@ void validate(const ddg_matrix* A, const int32_t* part, const double* F, int k, 
     DDG_REQUIRE(o.maxit >= 1, DDG_EINVAL, "maxit must be >= 1");
     DDG_REQUIRE(o.spin_budget_ms >= 0.0 && o.spin_budget_ms <= 3.6e6, DDG_EINVAL,
                 "spin_budget_ms must be in [0, 3.6e6]");
+    DDG_REQUIRE(o.local_repr >= DDG_LOCAL_AUTO && o.local_repr <= DDG_LOCAL_BAND, DDG_EINVAL, "bad local_repr");
 }
 
 // ---------------------------------------------------------------- preconditioner
@@ -362,9 +363,18 @@ void apply_in_pcg(ddg_handle h) {
     for (int c = 0; c < DDG_K_COUNT; ++c) h->prof_launches[c] += h->apply_launches[p][c];
 }
 
+// the CG scalars, and the timeout flag of the bounded waits of the local
+// solves (a solve whose wait ran out stops with DDG_ETIMEOUT)
 void read_scalars(ddg_handle h) {
+    int32_t timed_out = 0;
     d2h(h->h_scal, h->scal, S_COUNT, h->stream);
+    d2h(&timed_out, h->errflags + E_TIMEOUT, 1, h->stream);
     DDG_CUDA(cudaStreamSynchronize(h->stream));
+    if (timed_out) {
+        DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        throw DdgError{DDG_ETIMEOUT, "a bounded wait of a local solve ran out"};
+    }
 }
 
 // PCG from u = 0 (Sec. 7), driven from the host (two reads of the device
@@ -668,6 +678,11 @@ ddg_status loop_outcome(ddg_handle h, int* iters_out, double* relres_out) {
                      "after 3 restarts of CG from the true residual";
             return DDG_ENOCONV;
         case CG_NANRHS: h->err = "f contains NaN"; return DDG_EINVAL;
+        case CG_TIMEOUT:
+            DDG_CUDA(cudaMemsetAsync(h->errflags + E_TIMEOUT, 0, sizeof(int32_t), h->stream));
+            DDG_CUDA(cudaStreamSynchronize(h->stream));
+            h->err = "a bounded wait of a local solve ran out";
+            return DDG_ETIMEOUT;
     }
     h->err = "graph-driven solve ended in an unknown state";
     return DDG_ECUDA;
@@ -1146,7 +1161,8 @@ bool solve_many_graph(ddg_handle* hs, int nprob, const double* const* F, double*
         if (!h->use_graphs || h->prof_mask != 0 || h->solve_graph_failed || h->device != hs[0]->device ||
             (const void*)F[p] == (const void*)U[p])
             return false;
-        if (m[p] > 1 && (m[p] > DDG_MCHUNK || h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32))
+        if (m[p] > 1 && (m[p] > DDG_MCHUNK || h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 ||
+                         h->bl.on))
             return false;
     }
     DeviceScope scope(hs[0]->device);
@@ -1650,6 +1666,163 @@ void autotune_tc(ddg_handle h, int m) {
 }
 }  // namespace ddg
 
+namespace {
+// half-bandwidth max |i - j| of each A_i = A[ov, ov] in ascending dof order
+std::vector<int> local_bandwidths(const ddg_matrix* A, const std::vector<std::vector<int32_t>>& ov,
+                                  const std::vector<int>& sid) {
+    std::vector<int> bq(sid.size(), 0);
+    std::vector<int32_t> loc(A->n, -1);
+    for (size_t q = 0; q < sid.size(); ++q) {
+        const std::vector<int32_t>& idx = ov[sid[q]];
+        for (size_t r = 0; r < idx.size(); ++r) loc[idx[r]] = (int32_t)r;
+        int b = 0;
+        for (size_t r = 0; r < idx.size(); ++r)
+            for (int64_t e = A->rowptr[idx[r]]; e < A->rowptr[idx[r] + 1]; ++e) {
+                const int32_t c = loc[A->col[e]];
+                if (c >= 0) b = std::max(b, std::abs((int)r - c));
+            }
+        bq[q] = b;
+        for (int32_t g : idx) loc[g] = -1;
+    }
+    return bq;
+}
+
+// row chunks of a block for one element size: consecutive whole rows of at
+// most DDG_BAND_STAGE_BYTES
+std::vector<int2> band_chunks(const std::vector<int32_t>& row, size_t elem) {
+    std::vector<int2> ch;
+    const int rows = (int)row.size() - 1;
+    int r = 0;
+    while (r < rows) {
+        int e = r + 1;
+        while (e < rows && (size_t)(row[e + 1] - row[r]) * elem <= DDG_BAND_STAGE_BYTES) ++e;
+        ch.push_back(make_int2(r, e));
+        r = e;
+    }
+    return ch;
+}
+
+// Banded local factors (Sec. 6, exact local solves): Cholesky of every A_i
+// in FP64 with the tile band kernels, batched over subdomains, rewritten in
+// block form (C_K, D_K per super-block of B rows) in FP64 and/or FP32.
+void setup_band_local(ddg_handle h, const std::vector<int>& bq) {
+    BandLocal& L = h->bl;
+    const int nsub = h->nsub;
+    const int keep = h->opt.keep_precisions;
+    L.b = std::max(1, *std::max_element(bq.begin(), bq.end()));
+    L.Wt = (L.b + DDG_CT - 1) / DDG_CT;
+    L.B = L.Wt * DDG_CT;
+    DDG_REQUIRE(L.B <= 1024, DDG_EINVAL, "banded local factors take half-bandwidths of at most 1024");
+    const int B = L.B, b = L.b, Wt = L.Wt;
+    std::vector<int32_t> rowC(b + 1, 0), rowD(B + 1, 0);
+    for (int i = 0; i < b; ++i) rowC[i + 1] = rowC[i] + (B - ((B - b + i) & ~3));
+    for (int i = 0; i < B; ++i) rowD[i + 1] = rowD[i] + ((i + 4) & ~3);
+    L.sizeC = rowC[b];
+    L.sizeD = rowD[B];
+    std::vector<int32_t> nts(nsub);
+    L.h_nk.assign(nsub, 0);
+    L.h_qoff.assign(nsub + 1, 0);
+    int nKmax = 0;
+    for (int q = 0; q < nsub; ++q) {
+        const int nq = (int)(h->h_ov_off[q + 1] - h->h_ov_off[q]);
+        const int nk = std::max(1, (nq + B - 1) / B);
+        L.h_nk[q] = nk;
+        nts[q] = nk * Wt;
+        nKmax = std::max(nKmax, nk);
+        L.h_qoff[q + 1] = L.h_qoff[q] + (int64_t)nk * (L.sizeC + L.sizeD);
+    }
+    L.vec_elems = nKmax * B;
+    L.elems = L.h_qoff[nsub];
+    // shared-memory ring depth: what is left of 220 KB after the vectors
+    auto stages_for = [&](size_t sv) {
+        const size_t fixed = (size_t)L.vec_elems * sv + (size_t)((B + 15) & ~15) * sv + 256;
+        const size_t budget = (size_t)220 << 10;
+        return fixed >= budget ? 0 : (int)std::min<size_t>(4, (budget - fixed) / DDG_BAND_STAGE_BYTES);
+    };
+    L.stages64 = stages_for(8);
+    L.stages32 = stages_for(4);
+    if (keep & (1 << DDG_PREC_FP64))
+        DDG_REQUIRE(L.stages64 >= 2, DDG_EINVAL, "local block too large for the FP64 banded solve");
+    DDG_REQUIRE(L.stages32 >= 2, DDG_EINVAL, "local block too large for the banded solve");
+    L.nk = h->arena.alloc<int32_t>(nsub);
+    L.qoff = h->arena.alloc<int64_t>(nsub + 1);
+    L.rowC = h->arena.alloc<int32_t>(b + 1);
+    L.rowD = h->arena.alloc<int32_t>(B + 1);
+    h2d(L.nk, L.h_nk.data(), nsub, h->stream);
+    h2d(L.qoff, L.h_qoff.data(), nsub + 1, h->stream);
+    h2d(L.rowC, rowC.data(), b + 1, h->stream);
+    h2d(L.rowD, rowD.data(), B + 1, h->stream);
+    auto upload_chunks = [&](const std::vector<int32_t>& row, size_t elem, int2*& d, int& cnt) {
+        const std::vector<int2> ch = band_chunks(row, elem);
+        cnt = (int)ch.size();
+        d = h->arena.alloc<int2>(ch.size());
+        h2d(d, ch.data(), ch.size(), h->stream);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+    };
+    upload_chunks(rowC, 8, L.ch64C, L.nch64C);
+    upload_chunks(rowD, 8, L.ch64D, L.nch64D);
+    upload_chunks(rowC, 4, L.ch32C, L.nch32C);
+    upload_chunks(rowD, 4, L.ch32D, L.nch32D);
+    if (keep & (1 << DDG_PREC_FP64)) L.d64 = h->arena.alloc<double>(L.elems);
+    if (keep & ((1 << DDG_PREC_FP32) | (1 << DDG_PREC_BF16))) L.d32 = h->arena.alloc<float>(L.elems);
+    // FP64 workspaces per batch of subdomains (about 2 GB): band tiles, tile
+    // inverses and super-block inverses
+    const size_t tile = (size_t)DDG_CT * DDG_CT;
+    const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
+    auto per_sub = [&](int q) {
+        return (size_t)nts[q] * (Wt + 1) * tile + (size_t)nts[q] * tile + (size_t)L.h_nk[q] * Ptiles * tile;
+    };
+    const size_t budget = (size_t)1 << 28;   // doubles
+    int q0 = 0;
+    while (q0 < nsub) {
+        int q1 = q0;
+        size_t used = 0;
+        while (q1 < nsub && (q1 == q0 || used + per_sub(q1) <= budget)) used += per_sub(q1++);
+        const int nb = q1 - q0;
+        std::vector<int32_t> ql(nb), nt(nb);
+        std::vector<int64_t> bo(nb), dof(nb), wo(nb);
+        size_t ob = 0, od = 0, ow = 0;
+        int NTmax = 0;
+        for (int t = 0; t < nb; ++t) {
+            const int q = q0 + t;
+            ql[t] = q;
+            nt[t] = nts[q];
+            NTmax = std::max(NTmax, nts[q]);
+            bo[t] = (int64_t)ob;
+            dof[t] = (int64_t)od;
+            wo[t] = (int64_t)ow;
+            ob += (size_t)nts[q] * (Wt + 1) * tile;
+            od += (size_t)nts[q] * tile;
+            ow += (size_t)L.h_nk[q] * Ptiles * tile;
+        }
+        double* band = h->arena.alloc<double>(ob);
+        double* dinv = h->arena.alloc<double>(od);
+        double* W = h->arena.alloc<double>(ow);
+        int32_t* dql = h->arena.alloc<int32_t>(nb);
+        int32_t* dnt = h->arena.alloc<int32_t>(nb);
+        int64_t* dbo = h->arena.alloc<int64_t>(nb);
+        int64_t* ddo = h->arena.alloc<int64_t>(nb);
+        int64_t* dwo = h->arena.alloc<int64_t>(nb);
+        h2d(dql, ql.data(), nb, h->stream);
+        h2d(dnt, nt.data(), nb, h->stream);
+        h2d(dbo, bo.data(), nb, h->stream);
+        h2d(ddo, dof.data(), nb, h->stream);
+        h2d(dwo, wo.data(), nb, h->stream);
+        DDG_CUDA(cudaMemsetAsync(band, 0, ob * sizeof(double), h->stream));
+        DDG_CUDA(cudaMemsetAsync(W, 0, ow * sizeof(double), h->stream));
+        ddg::band_local_assemble(h, dql, nb, dbo, dnt, band);
+        ddg::band_factor_batched(h, band, Wt, nb, NTmax, dbo, dnt, dinv, ddo, W, dwo, h->errflags + E_LOCAL_SPD);
+        ddg::band_local_pack(h, dql, nb, NTmax / Wt, dbo, dwo, band, W);
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        for (void* p : {(void*)band, (void*)dinv, (void*)W, (void*)dql, (void*)dnt, (void*)dbo, (void*)ddo,
+                        (void*)dwo})
+            h->arena.release(p);
+        q0 = q1;
+    }
+    ddg::band_local_configure(h);
+}
+}  // namespace
+
 static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, const int32_t* groups,
                              const double* F, int k, int overlap, const ddg_options* opt, void* stream,
                              ddg_handle* out) {
@@ -1776,6 +1949,17 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         std::vector<int64_t> ov_off(nsub + 1, 0);
         std::vector<int32_t> Tq(nsub);
         std::vector<int64_t> tile_off(nsub + 1, 0);
+        // representation of the local solves: dense inverses while every block
+        // fits them, else (or on request) banded Cholesky factors
+        int largest = 0;
+        for (const auto& om : ov) largest = std::max(largest, (int)om.size());
+        const bool band_local = o.local_repr == DDG_LOCAL_BAND ||
+                                (o.local_repr == DDG_LOCAL_AUTO && largest > 96 * DDG_LT);
+        DDG_REQUIRE(!(band_local && (o.tensor_cores || o.dedup_local)), DDG_EINVAL,
+                    "tensor_cores and dedup_local need dense local inverses (local_repr INV)");
+        h->bl.on = band_local;
+        std::vector<int> bq;   // half-bandwidth of each A_i (band), sweep order
+        if (band_local) bq = local_bandwidths(A, ov, h->h_sid);
         // subdomains with equal local matrices share the stored inverse of the
         // first of them (opt.dedup_local); rep[q] == q keeps its own
         std::vector<int32_t> rep(nsub);
@@ -1788,7 +1972,9 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
             const int nq = (int)ov[h->h_sid[q]].size();
             ov_off[q + 1] = ov_off[q] + nq;
             Tq[q] = (nq + DDG_LT - 1) / DDG_LT;
-            if (rep[q] == q) {
+            if (band_local) {
+                tile_off[q] = 0;
+            } else if (rep[q] == q) {
                 reps.push_back(q);
                 tile_off[q] = tile_cursor;
                 tile_cursor += (int64_t)ddgdev::packed_elems(Tq[q], ddgdev::packed_narrow_width(nq, Tq[q]));
@@ -1802,7 +1988,13 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         h->sum_local = ov_off[nsub];
         h->inv_elems = tile_cursor;
         h->Tmax = (h->max_local + DDG_LT - 1) / DDG_LT;
-        DDG_REQUIRE(h->Tmax <= 96, DDG_EINVAL, "overlapping subdomains larger than 3072 dofs are not supported");
+        DDG_REQUIRE(band_local || h->Tmax <= 96, DDG_EINVAL,
+                    "dense local inverses take overlapping subdomains of at most 3072 dofs (local_repr BAND "
+                    "takes larger ones)");
+        if (band_local) {
+            h->Tmax = 1;   // no packed inverses and no dense work items
+            h->nrep_local = nsub;
+        }
         h->h_ov_off = ov_off;
         h->h_crow_off.assign(h->ncol + 1, 0);
         for (int c = 0; c < h->ncol; ++c) h->h_crow_off[c + 1] = ov_off[h->h_csub_off[c + 1]];
@@ -1827,7 +2019,7 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         // upper triangle, about `chunk` tiles and at most ls_band_rows rows each
         h->h_Tq = Tq;
         if (o.chunk_tiles > 0) h->ls_chunk = o.chunk_tiles;
-        build_local_items(h, h->ls_chunk, h->ls_band_rows);
+        if (!band_local) build_local_items(h, h->ls_chunk, h->ls_band_rows);
 
         // algorithmic bytes of one local-solve launch per colour and precision:
         // packed triangle of A_i^{-1} + residual read + z read and write
@@ -1892,10 +2084,25 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         h->errflags = h->arena.alloc<int32_t>(E_COUNT);
         DDG_CUDA(cudaMemsetAsync(h->errflags, 0, E_COUNT * sizeof(int32_t), h->stream));
         const size_t tile_elems = (size_t)h->inv_elems;
-        if (keep & (1 << DDG_PREC_FP64)) h->inv64 = h->arena.alloc<double>(tile_elems);
-        if (keep & (1 << DDG_PREC_FP32)) h->inv32 = h->arena.alloc<float>(tile_elems);
-        if (keep & (1 << DDG_PREC_BF16)) h->inv16 = h->arena.alloc<__nv_bfloat16>(tile_elems);
-        {
+        if (!band_local) {
+            if (keep & (1 << DDG_PREC_FP64)) h->inv64 = h->arena.alloc<double>(tile_elems);
+            if (keep & (1 << DDG_PREC_FP32)) h->inv32 = h->arena.alloc<float>(tile_elems);
+            if (keep & (1 << DDG_PREC_BF16)) h->inv16 = h->arena.alloc<__nv_bfloat16>(tile_elems);
+        }
+        if (band_local) {
+            setup_band_local(h, bq);
+            for (int p = 0; p < 3; ++p) {
+                // the block-form factor is read twice (forward, backward) plus
+                // the residual read and z read + write
+                const double se = p == DDG_PREC_FP64 ? 8.0 : 4.0;
+                for (int c = 0; c < h->ncol; ++c) {
+                    h->colour_bytes[p][c] = 0.0;
+                    for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q)
+                        h->colour_bytes[p][c] += 2.0 * (double)(h->bl.h_qoff[q + 1] - h->bl.h_qoff[q]) * se +
+                                                 3.0 * (double)(ov_off[q + 1] - ov_off[q]) * se;
+                }
+            }
+        } else {
             const size_t Np = (size_t)h->Tmax * DDG_LT;
             const size_t per = Np * Np * sizeof(double);
             // chunks of whole waves (a multiple of the SM count), about 3 GB of workspace
@@ -1924,7 +2131,7 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
             h->arena.release(invdiag);
             if (qlist) h->arena.release(qlist);
         }
-        ddg::local_configure(h);
+        if (!band_local) ddg::local_configure(h);
         h->res64 = h->arena.alloc<double>(h->sum_local);
         h->res32 = h->arena.alloc<float>(h->sum_local);
         alloc_partials(h, h->nitems);
@@ -1952,7 +2159,7 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
         h->red_counter = h->arena.alloc<unsigned>(1);
         DDG_CUDA(cudaMemsetAsync(h->red_counter, 0, sizeof(unsigned), h->stream));
 
-        if (o.autotune) autotune_local(h);
+        if (o.autotune && !band_local) autotune_local(h);
 
         int32_t flags[E_COUNT];
         d2h(flags, h->errflags, E_COUNT, h->stream);
@@ -2156,7 +2363,7 @@ ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, doub
         DDG_REQUIRE(F && U && m >= 1, DDG_EINVAL, "F, U must be non-null and m >= 1");
         DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
         ddg_status worst = DDG_OK;
-        if (h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32) {
+        if (h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 || h->bl.on) {
             // the FP64 and the V-cycle preconditioners, and coarse spaces of
             // more than 32 generators per subdomain, run one column at a time
             for (int j = 0; j < m; ++j) {
@@ -2335,6 +2542,9 @@ ddg_status ddg_get_info(ddg_handle h, ddg_info* info) {
         info->ls_band_rows = h->ls_band_rows;
         info->tc_stages = h->tc_stages;
         info->tuned = h->tuned;
+        info->local_repr = h->bl.on ? DDG_LOCAL_BAND : DDG_LOCAL_INV;
+        info->local_band = h->bl.on ? h->bl.b : 0;
+        info->local_elems = h->bl.on ? h->bl.elems : h->inv_elems;
         return DDG_OK;
     });
 }

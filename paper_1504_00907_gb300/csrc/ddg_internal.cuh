@@ -154,7 +154,8 @@ enum {
 // Device-side state of a graph-driven PCG solve (one CUDA graph whose
 // conditional WHILE node repeats the CG iteration; the control kernels
 // decide convergence, breakdown, the true-residual check and restarts).
-enum { CG_RUN = 0, CG_CONV = 1, CG_BREAKDOWN = 2, CG_MAXIT = 3, CG_STALLED = 4, CG_ZERO = 5, CG_NANRHS = 6 };
+enum { CG_RUN = 0, CG_CONV = 1, CG_BREAKDOWN = 2, CG_MAXIT = 3, CG_STALLED = 4, CG_ZERO = 5, CG_NANRHS = 6,
+       CG_TIMEOUT = 7 };
 #define DDG_MAX_RESTARTS 3
 struct CgCtl {
     int it;            // iterations done
@@ -209,6 +210,29 @@ struct MultiWork {
     int gen = 0;                  // bumped when the workspace is reallocated
     MultiCtl* ctl = nullptr;      // graph-driven batched solves
     MultiCtl* h_ctl = nullptr;    // pinned
+};
+
+// banded local factors (local_repr BAND): the Cholesky factor of every A_i in
+// block form, super-blocks of B = 64 Wt rows; per super-block K the stored
+// rows of C_K = L_{K,K-1} (rows i < b, columns [(B - b + i) & ~3, B)) and of
+// D_K = L_KK^{-1} (row i: columns [0, i] padded to a multiple of 4)
+#define DDG_BAND_STAGE_BYTES 32768
+struct BandLocal {
+    bool on = false;
+    int Wt = 0, B = 0, b = 0;          // tiles per super-block, its rows, half-bandwidth
+    int sizeC = 0, sizeD = 0;          // stored elements of one C_K / D_K
+    int vec_elems = 0;                 // largest nK_q * B
+    int stages64 = 0, stages32 = 0;    // shared-memory ring depth per precision
+    std::vector<int> h_nk;             // [nsub] super-blocks per subdomain (sweep position)
+    std::vector<int64_t> h_qoff;       // [nsub + 1] element offsets of each subdomain's blocks
+    int32_t* nk = nullptr;
+    int64_t* qoff = nullptr;
+    int32_t *rowC = nullptr, *rowD = nullptr;   // [b + 1], [B + 1] row offsets inside a block
+    int2 *ch64C = nullptr, *ch64D = nullptr, *ch32C = nullptr, *ch32D = nullptr;   // row chunks
+    int nch64C = 0, nch64D = 0, nch32C = 0, nch32D = 0;
+    double* d64 = nullptr;
+    float* d32 = nullptr;
+    int64_t elems = 0;
 };
 
 // tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}
@@ -345,6 +369,7 @@ struct ddg_handle_s {
 
     MultiWork mw;
     TcData tc;
+    BandLocal bl;
 
     // ---- graph-driven PCG (whole solve in one graph launch, one per precision)
     CgCtl* ctl = nullptr;          // device
@@ -409,7 +434,19 @@ void local_configure(ddg_handle h);
 void local_residual(ddg_handle h, int colour, bool z_zero, int prec);
 void local_solve_colour(ddg_handle h, int colour, int prec);
 
+// k_band.cu (banded local factors)
+void band_local_assemble(ddg_handle h, const int32_t* qlist, int nb, const int64_t* boff, const int32_t* nts,
+                         double* band);
+void band_local_pack(ddg_handle h, const int32_t* qlist, int nb, int nKmax, const int64_t* boff,
+                     const int64_t* woff, const double* band, const double* W);
+size_t band_solve_smem(const BandLocal& L, int prec, int stages);
+void band_local_configure(ddg_handle h);
+void band_local_solve_colour(ddg_handle h, int c, int prec);
+
 // k_coarse.cu
+void band_factor_batched(ddg_handle h, double* band, int Wt, int nb, int NTmax, const int64_t* boff,
+                         const int32_t* nts, double* dinv, const int64_t* doff, double* W,
+                         const int64_t* woff, int* err);
 void coarse_qr(ddg_handle h, int32_t* d_rank, const double* dF, int k);
 void coarse_assemble_band(ddg_handle h, const std::vector<int>& blk_I, const std::vector<int>& blk_J);
 // the kmax x kmax blocks A0[(I,.),(J,.)] of the listed pairs, copied to the host

@@ -345,7 +345,14 @@ __global__ void loop_decide_recurrence_kernel(CgCtl* ctl, const double* scal, do
 
 // After the true residual (when asked for): accept, give up after the last
 // restart, or restart CG from the true residual; then the loop condition.
-__global__ void loop_decide_true_kernel(CgCtl* ctl, const double* scal, cudaGraphConditionalHandle cond) {
+__global__ void loop_decide_true_kernel(CgCtl* ctl, const double* scal, const int* errflag,
+                                        cudaGraphConditionalHandle cond) {
+    if (*errflag) {
+        // a bounded wait of a local solve ran out: the iterate is not valid
+        ctl->state = CG_TIMEOUT;
+        cudaGraphSetConditional(cond, 0u);
+        return;
+    }
     if (ctl->check) {
         const double tr = sqrt(scal[S_TMP]) / ctl->fn;
         ctl->true_rel = tr;
@@ -412,7 +419,7 @@ void loop_decide_recurrence(ddg_handle h) {
 }
 
 void loop_decide_true(ddg_handle h, cudaGraphConditionalHandle cond) {
-    loop_decide_true_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->scal, cond);
+    loop_decide_true_kernel<<<1, 1, 0, h->stream>>>(h->ctl, h->scal, h->errflags + E_TIMEOUT, cond);
     DDG_CHECK_LAUNCH();
 }
 

@@ -215,12 +215,21 @@ __device__ __forceinline__ void acc_zero4(double (&acc)[4][4]) {
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 }
 
+// Batched use (local band factors of many subdomains): blockIdx.y selects
+// band b of a batch, stored at band + boff[b] with its tile inverses at
+// dinv + doff[b] and nts[b] tile rows; boff == nullptr is the single band.
 __global__ void __launch_bounds__(256) band_potrf_kernel(double* band, int Wt, int k, double* dinv,
-                                                         int* err) {
+                                                         int* err, const int64_t* boff, const int64_t* doff,
+                                                         const int32_t* nts) {
     extern __shared__ double sm[];
     double* S = sm;
     double* X = sm + CT * CLD;
     __shared__ int bad;
+    if (boff) {
+        if (k >= nts[blockIdx.y]) return;
+        band += boff[blockIdx.y];
+        dinv += doff[blockIdx.y];
+    }
     double* tile = band + (size_t)k * (Wt + 1) * CT * CT;   // (k, k): offset R - C = 0
     if (threadIdx.x == 0) bad = 0;
     ct_load(S, tile);
@@ -266,11 +275,17 @@ __global__ void __launch_bounds__(256) band_potrf_kernel(double* band, int Wt, i
 
 // L_ik = A_ik L_kk^{-T} for i = k+1 .. k+m
 __global__ void __launch_bounds__(256) band_trsm_kernel(double* band, int Wt, int k,
-                                                        const double* dinv) {
+                                                        const double* dinv, const int64_t* boff,
+                                                        const int64_t* doff, const int32_t* nts) {
     extern __shared__ double sm[];
     double* A = sm;
     double* X = sm + CT * CLD;
     const int i = k + 1 + blockIdx.x;
+    if (boff) {
+        if (i >= nts[blockIdx.y]) return;
+        band += boff[blockIdx.y];
+        dinv += doff[blockIdx.y];
+    }
     double* tile = band + ((size_t)i * (Wt + 1) + (i - k)) * CT * CT;
     ct_load(A, tile);
     ct_load(X, dinv + (size_t)k * CT * CT);
@@ -286,7 +301,8 @@ __global__ void __launch_bounds__(256) band_trsm_kernel(double* band, int Wt, in
 }
 
 // A_ij -= L_ik L_jk^T for k < j <= i <= k+m
-__global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, int k) {
+__global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, int k, const int64_t* boff,
+                                                          const int32_t* nts) {
     extern __shared__ double sm[];
     double* A = sm;
     double* Bt = sm + CT * CLD;
@@ -297,6 +313,10 @@ __global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, 
         ++w;
     }
     const int j = k + 1 + p;
+    if (boff) {
+        if (i >= nts[blockIdx.y]) return;
+        band += boff[blockIdx.y];
+    }
     ct_load(A, band + ((size_t)i * (Wt + 1) + (i - k)) * CT * CT);
     ct_load(Bt, band + ((size_t)j * (Wt + 1) + (j - k)) * CT * CT);
     __syncthreads();
@@ -315,11 +335,20 @@ __global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, 
 // ii > jj: W_ij = -dinv_i sum_{m=jj}^{ii-1} L_im W_mj (tile forward substitution)
 __global__ void __launch_bounds__(256) superblock_inverse_kernel(const double* band, int Wt,
                                                                  const double* dinv, double* W,
-                                                                 int NT) {
+                                                                 int NT, const int64_t* boff,
+                                                                 const int64_t* doff, const int64_t* woff,
+                                                                 const int32_t* nts) {
     extern __shared__ double sm[];
     double* A = sm;
     double* Bm = sm + CT * CLD;
     const int K = blockIdx.y, jj = blockIdx.x;
+    if (boff) {
+        NT = nts[blockIdx.z];
+        if (K * Wt >= NT) return;
+        band += boff[blockIdx.z];
+        dinv += doff[blockIdx.z];
+        W += woff[blockIdx.z];
+    }
     const int base = K * Wt;
     const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
     auto wtile = [&](int ii, int j2) { return W + ((size_t)K * Ptiles + (size_t)ii * (ii + 1) / 2 + j2) * CT * CT; };
@@ -693,13 +722,14 @@ void coarse_band_cholesky(ddg_handle h) {
     double* dinv = h->arena.alloc<double>((size_t)h->NT * CT * CT);
     const int Wt = h->Wt, NT = h->NT;
     for (int k = 0; k < NT; ++k) {
-        band_potrf_kernel<<<1, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, h->errflags + E_COARSE_SPD);
+        band_potrf_kernel<<<1, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, h->errflags + E_COARSE_SPD,
+                                                      nullptr, nullptr, nullptr);
         DDG_CHECK_LAUNCH();
         const int m = std::min(Wt, NT - 1 - k);
         if (m > 0) {
-            band_trsm_kernel<<<m, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv);
+            band_trsm_kernel<<<m, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, nullptr, nullptr, nullptr);
             DDG_CHECK_LAUNCH();
-            band_update_kernel<<<m * (m + 1) / 2, 256, sm2, h->stream>>>(h->bandL, Wt, k);
+            band_update_kernel<<<m * (m + 1) / 2, 256, sm2, h->stream>>>(h->bandL, Wt, k, nullptr, nullptr);
             DDG_CHECK_LAUNCH();
         }
     }
@@ -707,11 +737,40 @@ void coarse_band_cholesky(ddg_handle h) {
     const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
     double* W = h->arena.alloc<double>((size_t)h->nK * Ptiles * CT * CT);
     DDG_CUDA(cudaMemsetAsync(W, 0, (size_t)h->nK * Ptiles * CT * CT * sizeof(double), h->stream));
-    superblock_inverse_kernel<<<dim3(Wt, h->nK), 256, sm2, h->stream>>>(h->bandL, Wt, dinv, W, NT);
+    superblock_inverse_kernel<<<dim3(Wt, h->nK), 256, sm2, h->stream>>>(h->bandL, Wt, dinv, W, NT, nullptr,
+                                                                         nullptr, nullptr, nullptr);
     DDG_CHECK_LAUNCH();
     h->coarseW = W;
     DDG_CUDA(cudaStreamSynchronize(h->stream));
     h->arena.release(dinv);
+}
+
+// Band Cholesky of nb bands at once (the local band factors): band b holds
+// nts[b] tile rows of Wt + 1 tiles at band + boff[b] (device offsets); the
+// tile inverses L_kk^{-1} go to dinv + doff[b] and the super-block inverses
+// D_K = L_KK^{-1} (lower tiles) to W + woff[b].  A non-positive pivot sets err.
+void band_factor_batched(ddg_handle h, double* band, int Wt, int nb, int NTmax, const int64_t* boff,
+                         const int32_t* nts, double* dinv, const int64_t* doff, double* W,
+                         const int64_t* woff, int* err) {
+    const size_t sm2 = 2 * CT * CLD * sizeof(double);
+    DDG_CUDA(cudaFuncSetAttribute(band_potrf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    DDG_CUDA(cudaFuncSetAttribute(superblock_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    for (int k = 0; k < NTmax; ++k) {
+        band_potrf_kernel<<<dim3(1, nb), 256, sm2, h->stream>>>(band, Wt, k, dinv, err, boff, doff, nts);
+        DDG_CHECK_LAUNCH();
+        const int m = std::min(Wt, NTmax - 1 - k);
+        if (m > 0) {
+            band_trsm_kernel<<<dim3(m, nb), 256, sm2, h->stream>>>(band, Wt, k, dinv, boff, doff, nts);
+            DDG_CHECK_LAUNCH();
+            band_update_kernel<<<dim3(m * (m + 1) / 2, nb), 256, sm2, h->stream>>>(band, Wt, k, boff, nts);
+            DDG_CHECK_LAUNCH();
+        }
+    }
+    superblock_inverse_kernel<<<dim3(Wt, NTmax / Wt, nb), 256, sm2, h->stream>>>(band, Wt, dinv, W, NTmax, boff,
+                                                                               doff, woff, nts);
+    DDG_CHECK_LAUNCH();
 }
 
 // Rows are stored on [lo & ~3, (hi + 3) & ~3) so that every row starts on a

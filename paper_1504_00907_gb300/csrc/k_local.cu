@@ -748,6 +748,10 @@ void local_configure(ddg_handle h) {
 }
 
 void local_solve_colour(ddg_handle h, int c, int prec) {
+    if (h->bl.on) {
+        band_local_solve_colour(h, c, prec);
+        return;
+    }
     if (prec == DDG_PREC_FP64)
         launch_local_solve<double, double>(h, c, h->inv64, h->res64, h->partial64, h->z64);
     else if (prec == DDG_PREC_FP32)

@@ -40,7 +40,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(ddg_matrix, coef), sizeof(ddg_info), offsetof(ddg_info, setup_ms),
          offsetof(ddg_info, local_inverses), offsetof(ddg_options, dedup_local),
          offsetof(ddg_options, spin_budget_ms), offsetof(ddg_info, graph_solve));
-  printf("%zu %zu\\n", offsetof(ddg_options, autotune), offsetof(ddg_info, tuned));
+  printf("%zu %zu %zu %zu\\n", offsetof(ddg_options, autotune), offsetof(ddg_info, tuned),
+         offsetof(ddg_options, local_repr), offsetof(ddg_info, local_elems));
   return 0;
 }
 """)
@@ -52,7 +53,8 @@ int main(void) {
            ddg.Options.tensor_cores.offset, ctypes.sizeof(ddg.Matrix), ddg.Matrix.coef.offset, ctypes.sizeof(ddg.Info),
            ddg.Info.setup_ms.offset, ddg.Info.local_inverses.offset, ddg.Options.dedup_local.offset,
            ddg.Options.spin_budget_ms.offset, ddg.Info.graph_solve.offset,
-           ddg.Options.autotune.offset, ddg.Info.tuned.offset]
+           ddg.Options.autotune.offset, ddg.Info.tuned.offset, ddg.Options.local_repr.offset,
+           ddg.Info.local_elems.offset]
     assert got == exp
 
 
