@@ -63,8 +63,11 @@ def parse():
     ap.add_argument("--elasticity-steps", type=int, default=3)
     ap.add_argument("--materials-size", type=int, default=1024,
                     help="material-aware generator arm: N of the N^2 two-material grid (0 skips it)")
-    ap.add_argument("--psweep-size", type=int, default=500,
+    ap.add_argument("--psweep-size", type=int, default=1000,
                     help="Fig. 3 arm: N of the N^2 biharmonic for the p sweep (0 skips it)")
+    ap.add_argument("--psweep-box", type=int, default=125,
+                    help="Fig. 3 arm: subdomain width H/h (125 in the paper: 129^2-dof local blocks, "
+                         "solved through banded factors)")
     ap.add_argument("--dedup", type=int, default=1,
                     help="arm with shared inverses of identical local matrices (0 skips it)")
     ap.add_argument("--vcycle-group", type=int, default=4,
@@ -458,12 +461,15 @@ def fractional_iters(hist, tol):
 
 def psweep_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
     """Fig. 3: iterations against the degree p of the coarse basis on the
-    clamped biharmonic, N^2 nodes, H/h = 50 (subdomains of 50^2 nodes),
-    Delta = 2, monomials centred and scaled per subdomain, p = 1..10; then
-    p = 1 aggregated on 25^2 and 10^2 sub-boxes.  FP64 preconditioner (exact
-    local solves, as in the paper), FP64 CG to 1e-8, f ~ U(-1, 1)."""
-    N, box = args.psweep_size, 50
-    runs = [("p", p) for p in range(1, 11)] + [("agg", 25), ("agg", 10)]
+    clamped biharmonic, N^2 nodes, H/h = box (the paper: 1000^2 nodes, 8^2
+    subdomains of 125^2, local blocks of 129^2 = 16641 dofs, which the
+    library solves through banded Cholesky factors), Delta = 2, monomials
+    centred and scaled per subdomain, p = 1..10; then p = 1 on aggregates of
+    a fifth of the subdomain width (as many coarse dofs as p ~ 10).  FP64
+    preconditioner (exact local solves, as in the paper), FP64 CG to 1e-8,
+    f ~ U(-1, 1)."""
+    N, box = args.psweep_size, args.psweep_box
+    runs = [("p", p) for p in range(1, 11)] + [("agg", box // 5)]
     out = []
     # one handle: the local blocks are factorised once, and every basis only
     # rebuilds R0, A0 and its factor (ddg_set_generators)
@@ -472,6 +478,7 @@ def psweep_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world
     t0 = time.perf_counter()
     s = ddg.Solver(prob.A, prob.part, prob.F, prob.overlap, mode=prob.overlap_mode, shape=prob.shape,
                    precision="fp64", keep=("fp64",))
+    sinfo = s.info()
     torch.cuda.synchronize()
     local_setup_s = time.perf_counter() - t0
     f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
@@ -501,9 +508,14 @@ def psweep_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world
                     "status": int(st), "ms": ms, "coarse_rebuild_s": setup_s,
                     "kappa_estimate": lmax / lmin, "n_over_n0": prob.n / info["n0"]})
     s.close()
+    p10 = [r for r in out if r["basis"] == "p=10"]
     return {"workload": f"biharmonic2d_{N}^2: 13-pt clamped, {box}^2 boxes (H/h = {box}), overlap 2, "
                         "local monomials p = 1..10 and p = 1 on smaller aggregates, FP64, tol 1e-8",
-            "local_setup_s": local_setup_s, "runs": out}
+            "local_setup_s": local_setup_s, "local_repr": "band" if sinfo["local_repr"] == 2 else "inverse",
+            "max_local_dofs": sinfo["max_local"], "local_half_bandwidth": sinfo["local_band"],
+            "local_factor_gb_fp64": sinfo["local_elems"] * 8 / 1e9,
+            "n_over_n0_p10": p10[0]["n_over_n0"] if p10 else None, "paper_n_over_n0_p10": 284,
+            "runs": out}
 
 
 def elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):

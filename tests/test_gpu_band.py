@@ -7,13 +7,15 @@ block by a dense Cholesky factorisation, so the comparison checks the band
 assembly, the batched band factorisation, the block-form rewrite and the
 streamed recurrences together.
 
-Tolerances: FP64 preconditioner 1e-11 (the blocks here have cond(A_i) below
-2e3, so rounding stays near cond u = 4e-13); FP64 PCG solution 1e-10 with
-iterations within 1; FP32 factors: the error of a triangular solve is about
-cond(L) 2^-24 = sqrt(cond(A_i)) 2^-24 <= 45 * 6e-8 = 3e-6 for cond(A_i) up to
-2e3, so the preconditioner bound is 1e-5 as for FP32 inverses, and mixed
-solves reach the true residual 1e-8 with solutions within 1e-7 of the
-oracle's.
+Tolerances: FP64 preconditioner 1e-11 (the blocks here have cond(A_i) up to
+1.1e4, so rounding stays near cond u = 2.5e-12); FP64 PCG solution 1e-10
+with iterations within 1.  FP32 factors: solving A_i x = r through FP32 L
+and L^T carries a relative error of order cond(A_i) 2^-24, so the FP32
+preconditioner bound is max(1e-5, cond_max 2^-24) with cond_max the largest
+condition number of the case's local blocks (numpy eigvalsh of the blocks;
+for the two large cases computed once: 1818.7 for the 66^2 Poisson blocks,
+130.6 for the 17^3 ones).  Mixed solves reach the true residual 1e-8 with
+solutions within 1e-7 of the oracle's.
 """
 import numpy as np
 import pytest
@@ -78,6 +80,19 @@ def test_large_blocks_choose_the_band(name):
     np.testing.assert_array_equal(solver.colouring(), oracle.colour)
 
 
+LARGE_COND = {"poisson2d_band_4356": 1818.7, "poisson3d_band_4913": 130.6}
+
+
+def cond_max(name, prob, oracle):
+    if name in LARGE_COND:
+        return LARGE_COND[name]
+    worst = 0.0
+    for idx in oracle.omega:
+        w = np.linalg.eigvalsh(prob.A[idx][:, idx].toarray())
+        worst = max(worst, w[-1] / w[0])
+    return worst
+
+
 @pytest.mark.parametrize("name", list(LARGE) + list(SMALL))
 def test_band_preconditioner_matches_oracle(name):
     prob, solver, oracle = setup(name)
@@ -86,7 +101,8 @@ def test_band_preconditioner_matches_oracle(name):
     solver.set_precision("fp64")
     assert_close(solver.apply(dev(r)).cpu().numpy(), ref, 1e-11, "fp64")
     solver.set_precision("fp32")
-    assert_close(solver.apply(dev(r)).cpu().numpy(), ref, 1e-5, "fp32")
+    tol32 = max(1e-5, cond_max(name, prob, oracle) * 2.0 ** -24)
+    assert_close(solver.apply(dev(r)).cpu().numpy(), ref, tol32, "fp32")
     solver.set_precision("fp64")
 
 
