@@ -70,6 +70,12 @@ enum { DDG_OVERLAP_GRAPH = 0, DDG_OVERLAP_BOX = 1 };
  * work grows with the half-bandwidth).  AUTO takes the inverses when every
  * block fits them, else the band. */
 enum { DDG_LOCAL_AUTO = 0, DDG_LOCAL_INV = 1, DDG_LOCAL_BAND = 2 };
+/* ordering of the exact coarse Cholesky factor of A0 (Sec. 4): the natural
+ * subdomain order (a band; its solve is a block-bidiagonal recurrence) or
+ * nested dissection of the subdomain graph (a multifrontal factor, far
+ * fewer entries on 3D problems, a solve of a few dependent steps per level
+ * of the dissection tree) */
+enum { DDG_COARSE_BAND = 0, DDG_COARSE_ND = 1 };
 /* CG beta: Fletcher-Reeves (textbook) or Polak-Ribiere (flexible) */
 enum { DDG_BETA_FR = 0, DDG_BETA_PR = 1, DDG_BETA_AUTO = 2 };
 /* optional structure of A that enables a matrix-free SpMV for the FP64
@@ -123,6 +129,8 @@ typedef struct {
                              uses the FP32 factors, tensor_cores and dedup_local are not
                              available, ddg_solve_batch solves its columns one at a time,
                              and the half-bandwidth must be at most 1024 */
+    int coarse_order;     /* DDG_COARSE_*, default BAND.  With ND, ddg_solve_batch solves
+                             its columns one at a time */
 } ddg_options;
 
 typedef struct {
@@ -165,6 +173,10 @@ typedef struct {
     int local_repr;       /* DDG_LOCAL_INV or DDG_LOCAL_BAND (what setup chose) */
     int local_band;       /* half-bandwidth of the local matrices (BAND), else 0 */
     int64_t local_elems;  /* stored elements of all local operators (one precision) */
+    int coarse_order;     /* DDG_COARSE_* */
+    int coarse_fronts;    /* ND: fronts of the dissection tree */
+    int coarse_levels;    /* ND: levels of the dissection tree */
+    int64_t coarse_elems; /* stored elements of the coarse solve (one precision) */
 } ddg_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -252,6 +252,8 @@ void validate(const ddg_matrix* A, const int32_t* part, const double* F, int k, 
     DDG_REQUIRE(o.spin_budget_ms >= 0.0 && o.spin_budget_ms <= 3.6e6, DDG_EINVAL,
                 "spin_budget_ms must be in [0, 3.6e6]");
     DDG_REQUIRE(o.local_repr >= DDG_LOCAL_AUTO && o.local_repr <= DDG_LOCAL_BAND, DDG_EINVAL, "bad local_repr");
+    DDG_REQUIRE(o.coarse_order == DDG_COARSE_BAND || o.coarse_order == DDG_COARSE_ND, DDG_EINVAL,
+                "bad coarse_order");
 }
 
 // ---------------------------------------------------------------- preconditioner
@@ -267,7 +269,7 @@ void local_step(ddg_handle h, int c, bool z_zero, int prec) {
 int64_t coarse_vcycle(ddg_handle h, int prec);
 
 void coarse_step(ddg_handle h, int prec, bool residual) {
-    ProfScope ps(h, DDG_K_COARSE, h->inner ? 2 : 2 + 2 * h->nK, 0.0);
+    ProfScope ps(h, DDG_K_COARSE, h->inner ? 2 : 2 + (h->nd.on ? ddg::nd_solve_launches(h) : 2 * h->nK), 0.0);
     ddg::coarse_restrict(h, prec, residual);
     if (h->inner) h->prof_launches[DDG_K_COARSE] += coarse_vcycle(h, prec);
     else ddg::coarse_solve(h, prec);
@@ -1162,7 +1164,7 @@ bool solve_many_graph(ddg_handle* hs, int nprob, const double* const* F, double*
             (const void*)F[p] == (const void*)U[p])
             return false;
         if (m[p] > 1 && (m[p] > DDG_MCHUNK || h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 ||
-                         h->bl.on))
+                         h->bl.on || h->nd.on))
             return false;
     }
     DeviceScope scope(hs[0]->device);
@@ -1410,6 +1412,20 @@ void build_coarse(ddg_handle h, const double* F, int k, int overlap, const ddg_o
         h->band = (int)band;
         if (groups) {
             setup_vcycle(h, F, k, overlap, o, groups, bI, bJ, h->h_sub_off, h->h_sub_nodes);
+        } else if (o.coarse_order == DDG_COARSE_ND) {
+            // nested-dissection factor of A0 (multifrontal, dense fronts)
+            const int n0 = h->n0;
+            h->n0p = n0;
+            h->nK = 0;
+            double* blocks = ddg::coarse_assemble_blocks_device(h, bI, bJ);
+            ddg::nd_coarse_setup(h, bI, bJ, blocks);
+            h->arena.release(blocks);
+            h->c64 = h->arena.alloc<double>(n0);
+            h->y64 = h->arena.alloc<double>(n0);
+            h->x64 = h->arena.alloc<double>(n0);
+            h->c32 = h->arena.alloc<float>(n0);
+            h->y32 = h->arena.alloc<float>(n0);
+            h->x32 = h->arena.alloc<float>(n0);
         } else {
             h->Wt = std::max(1, (int)((band + DDG_CT - 1) / DDG_CT));
             const int NT0 = (h->n0 + DDG_CT - 1) / DDG_CT;
@@ -2318,6 +2334,7 @@ ddg_status ddg_set_generators(ddg_handle h, const double* F, int k) {
         h->c64 = h->y64 = h->x64 = nullptr;
         h->c32 = h->y32 = h->x32 = nullptr;
         h->Dm = h->Dt = h->Fm = h->Gm = ProfileMat{};
+        h->nd = NdCoarse{};
         h->band = 0;
         h->Wt = 1;
         h->NT = h->nK = h->B = h->n0p = 0;
@@ -2363,7 +2380,7 @@ ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, doub
         DDG_REQUIRE(F && U && m >= 1, DDG_EINVAL, "F, U must be non-null and m >= 1");
         DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
         ddg_status worst = DDG_OK;
-        if (h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 || h->bl.on) {
+        if (h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 || h->bl.on || h->nd.on) {
             // the FP64 and the V-cycle preconditioners, and coarse spaces of
             // more than 32 generators per subdomain, run one column at a time
             for (int j = 0; j < m; ++j) {
@@ -2545,6 +2562,10 @@ ddg_status ddg_get_info(ddg_handle h, ddg_info* info) {
         info->local_repr = h->bl.on ? DDG_LOCAL_BAND : DDG_LOCAL_INV;
         info->local_band = h->bl.on ? h->bl.b : 0;
         info->local_elems = h->bl.on ? h->bl.elems : h->inv_elems;
+        info->coarse_order = h->nd.on ? DDG_COARSE_ND : DDG_COARSE_BAND;
+        info->coarse_fronts = h->nd.on ? h->nd.nfront : 0;
+        info->coarse_levels = h->nd.on ? h->nd.nlevel : 0;
+        info->coarse_elems = h->nd.on ? h->nd.elems : (h->use_coarse ? h->Dm.nnz + h->Dt.nnz + h->Fm.nnz + h->Gm.nnz : 0);
         return DDG_OK;
     });
 }

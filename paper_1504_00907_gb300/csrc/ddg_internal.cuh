@@ -235,6 +235,23 @@ struct BandLocal {
     int64_t elems = 0;
 };
 
+// nested-dissection coarse factor (coarse_order ND): per front the rows of
+// D = L_SS^{-1} (row i: columns [0, i] padded to 4) and of L_US (row u: nS
+// columns padded to 4), work lists per level (deepest first)
+struct NdCoarse {
+    bool on = false;
+    int nfront = 0, nlevel = 0;
+    int64_t elems = 0;                 // stored elements (one precision)
+    int32_t *nS = nullptr, *nU = nullptr, *sdof = nullptr, *udof = nullptr;
+    int64_t *soff = nullptr, *uoff = nullptr, *doff = nullptr, *loff = nullptr, *cboff = nullptr;
+    int2 *drows = nullptr, *lrows = nullptr, *bcols = nullptr;   // (front, row) / (front, 32-column block)
+    int32_t* rtgt = nullptr;           // targets of the per-level sums of the forward updates
+    int64_t *rptr = nullptr, *rsrc = nullptr;
+    std::vector<int> h_drow_off, h_lrow_off, h_bcol_off, h_red_off;   // [nlevel + 1]
+    double *d64 = nullptr, *contrib64 = nullptr, *w64 = nullptr, *t64 = nullptr;
+    float *d32 = nullptr, *contrib32 = nullptr, *w32 = nullptr, *t32 = nullptr;
+};
+
 // tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}
 struct TcData {
     __nv_bfloat16* A = nullptr;    // 128 x 32 slabs, core-matrix order
@@ -370,6 +387,7 @@ struct ddg_handle_s {
     MultiWork mw;
     TcData tc;
     BandLocal bl;
+    NdCoarse nd;
 
     // ---- graph-driven PCG (whole solve in one graph launch, one per precision)
     CgCtl* ctl = nullptr;          // device
@@ -447,6 +465,9 @@ void band_local_solve_colour(ddg_handle h, int c, int prec);
 void band_factor_batched(ddg_handle h, double* band, int Wt, int nb, int NTmax, const int64_t* boff,
                          const int32_t* nts, double* dinv, const int64_t* doff, double* W,
                          const int64_t* woff, int* err);
+void front_factor_batched(ddg_handle h, double* fronts, int nb, int NTmax, int NSmax, const int64_t* foff,
+                          const int32_t* nts, const int32_t* nss, double* dinv, const int64_t* doff, double* W,
+                          const int64_t* woff, int* err);
 void coarse_qr(ddg_handle h, int32_t* d_rank, const double* dF, int k);
 void coarse_assemble_band(ddg_handle h, const std::vector<int>& blk_I, const std::vector<int>& blk_J);
 // the kmax x kmax blocks A0[(I,.),(J,.)] of the listed pairs, copied to the host
@@ -456,6 +477,12 @@ void coarse_band_cholesky(ddg_handle h);
 // F0 = R0 F (device, column-major [n0][k]) from F (device, column-major [n][k])
 void coarse_generators(ddg_handle h, const double* dF, int k, double* dF0);
 void coarse_build_apply(ddg_handle h);
+// the blocks of the listed pairs on the device (caller releases)
+double* coarse_assemble_blocks_device(ddg_handle h, const std::vector<int>& blk_I, const std::vector<int>& blk_J);
+// k_nd.cu: nested-dissection coarse factor and its solve
+void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector<int>& bJ, const double* blocks);
+void nd_coarse_solve(ddg_handle h, int prec);
+int nd_solve_launches(ddg_handle h);
 void coarse_restrict(ddg_handle h, int prec, bool residual);
 void coarse_solve(ddg_handle h, int prec);
 void coarse_prolong(ddg_handle h, int prec);

@@ -215,22 +215,34 @@ __device__ __forceinline__ void acc_zero4(double (&acc)[4][4]) {
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 }
 
-// Batched use (local band factors of many subdomains): blockIdx.y selects
-// band b of a batch, stored at band + boff[b] with its tile inverses at
-// dinv + doff[b] and nts[b] tile rows; boff == nullptr is the single band.
+// Tile (R, C), R >= C, of a factor stored as a band (tile row R holds the
+// tiles R - Wt .. R, offset R - C) or, DENSE, as a full lower triangle of
+// tiles in row order (the frontal matrices of the nested-dissection factor).
+template <bool DENSE>
+__device__ __forceinline__ size_t tile_at(int R, int C, int Wt) {
+    return (DENSE ? (size_t)R * (R + 1) / 2 + C : (size_t)R * (Wt + 1) + (R - C)) * CT * CT;
+}
+
+// Batched use (local band factors of many subdomains, the fronts of one
+// level of the nested-dissection tree): blockIdx.y selects matrix b of a
+// batch, stored at band + boff[b] with its tile inverses at dinv + doff[b]
+// and nts[b] tile rows, of which the first nss[b] are eliminated (a partial
+// factorisation leaves the Schur complement in the trailing tiles; nss ==
+// nullptr eliminates all); boff == nullptr is the single band.
+template <bool DENSE>
 __global__ void __launch_bounds__(256) band_potrf_kernel(double* band, int Wt, int k, double* dinv,
                                                          int* err, const int64_t* boff, const int64_t* doff,
-                                                         const int32_t* nts) {
+                                                         const int32_t* nts, const int32_t* nss) {
     extern __shared__ double sm[];
     double* S = sm;
     double* X = sm + CT * CLD;
     __shared__ int bad;
     if (boff) {
-        if (k >= nts[blockIdx.y]) return;
+        if (k >= (nss ? nss[blockIdx.y] : nts[blockIdx.y])) return;
         band += boff[blockIdx.y];
         dinv += doff[blockIdx.y];
     }
-    double* tile = band + (size_t)k * (Wt + 1) * CT * CT;   // (k, k): offset R - C = 0
+    double* tile = band + tile_at<DENSE>(k, k, Wt);
     if (threadIdx.x == 0) bad = 0;
     ct_load(S, tile);
     __syncthreads();
@@ -274,19 +286,21 @@ __global__ void __launch_bounds__(256) band_potrf_kernel(double* band, int Wt, i
 }
 
 // L_ik = A_ik L_kk^{-T} for i = k+1 .. k+m
+template <bool DENSE>
 __global__ void __launch_bounds__(256) band_trsm_kernel(double* band, int Wt, int k,
                                                         const double* dinv, const int64_t* boff,
-                                                        const int64_t* doff, const int32_t* nts) {
+                                                        const int64_t* doff, const int32_t* nts,
+                                                        const int32_t* nss) {
     extern __shared__ double sm[];
     double* A = sm;
     double* X = sm + CT * CLD;
     const int i = k + 1 + blockIdx.x;
     if (boff) {
-        if (i >= nts[blockIdx.y]) return;
+        if (i >= nts[blockIdx.y] || (nss && k >= nss[blockIdx.y])) return;
         band += boff[blockIdx.y];
         dinv += doff[blockIdx.y];
     }
-    double* tile = band + ((size_t)i * (Wt + 1) + (i - k)) * CT * CT;
+    double* tile = band + tile_at<DENSE>(i, k, Wt);
     ct_load(A, tile);
     ct_load(X, dinv + (size_t)k * CT * CT);
     __syncthreads();
@@ -301,8 +315,9 @@ __global__ void __launch_bounds__(256) band_trsm_kernel(double* band, int Wt, in
 }
 
 // A_ij -= L_ik L_jk^T for k < j <= i <= k+m
+template <bool DENSE>
 __global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, int k, const int64_t* boff,
-                                                          const int32_t* nts) {
+                                                          const int32_t* nts, const int32_t* nss) {
     extern __shared__ double sm[];
     double* A = sm;
     double* Bt = sm + CT * CLD;
@@ -314,16 +329,16 @@ __global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, 
     }
     const int j = k + 1 + p;
     if (boff) {
-        if (i >= nts[blockIdx.y]) return;
+        if (i >= nts[blockIdx.y] || (nss && k >= nss[blockIdx.y])) return;
         band += boff[blockIdx.y];
     }
-    ct_load(A, band + ((size_t)i * (Wt + 1) + (i - k)) * CT * CT);
-    ct_load(Bt, band + ((size_t)j * (Wt + 1) + (j - k)) * CT * CT);
+    ct_load(A, band + tile_at<DENSE>(i, k, Wt));
+    ct_load(Bt, band + tile_at<DENSE>(j, k, Wt));
     __syncthreads();
     double acc[4][4];
     acc_zero4(acc);
     ct_mac<true>(acc, A, Bt);
-    double* C = band + ((size_t)i * (Wt + 1) + (i - j)) * CT * CT;
+    double* C = band + tile_at<DENSE>(i, j, Wt);
     const int r0 = (threadIdx.x >> 4) * 4, c0 = (threadIdx.x & 15) * 4;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -332,18 +347,26 @@ __global__ void __launch_bounds__(256) band_update_kernel(double* band, int Wt, 
 }
 
 // W = L_KK^{-1} of super-block K, tile column jj: W_jj = dinv, and for
-// ii > jj: W_ij = -dinv_i sum_{m=jj}^{ii-1} L_im W_mj (tile forward substitution)
+// ii > jj: W_ij = -dinv_i sum_{m=jj}^{ii-1} L_im W_mj (tile forward substitution).
+// DENSE: one super-block per batch entry, its nss[b] eliminated tiles.
+template <bool DENSE>
 __global__ void __launch_bounds__(256) superblock_inverse_kernel(const double* band, int Wt,
                                                                  const double* dinv, double* W,
                                                                  int NT, const int64_t* boff,
                                                                  const int64_t* doff, const int64_t* woff,
-                                                                 const int32_t* nts) {
+                                                                 const int32_t* nts, const int32_t* nss) {
     extern __shared__ double sm[];
     double* A = sm;
     double* Bm = sm + CT * CLD;
     const int K = blockIdx.y, jj = blockIdx.x;
+    const int Wl = Wt;   // tiles per super-block; the band layout's Wt
     if (boff) {
         NT = nts[blockIdx.z];
+        if (DENSE) {
+            Wt = nss[blockIdx.z];
+            NT = Wt;
+            if (jj >= Wt) return;
+        }
         if (K * Wt >= NT) return;
         band += boff[blockIdx.z];
         dinv += doff[blockIdx.z];
@@ -363,7 +386,7 @@ __global__ void __launch_bounds__(256) superblock_inverse_kernel(const double* b
         acc_zero4(acc);
         for (int mm = jj; mm < ii; ++mm) {
             const int Rm = base + mm;
-            ct_load(A, band + ((size_t)Ri * (Wt + 1) + (Ri - Rm)) * CT * CT);
+            ct_load(A, band + tile_at<DENSE>(Ri, Rm, Wl));
             ct_load(Bm, wtile(mm, jj));
             __syncthreads();
             ct_mac<false>(acc, A, Bm);
@@ -713,23 +736,58 @@ void coarse_assemble_blocks(ddg_handle h, const std::vector<int>& bI, const std:
     h->arena.release(dB);
 }
 
+double* coarse_assemble_blocks_device(ddg_handle h, const std::vector<int>& bI, const std::vector<int>& bJ) {
+    const size_t per = (size_t)h->kmax * h->kmax;
+    double* dB = h->arena.alloc<double>(std::max<size_t>(1, bI.size() * per));
+    if (bI.empty()) return dB;
+    int32_t* dI = h->arena.alloc<int32_t>(bI.size());
+    int32_t* dJ = h->arena.alloc<int32_t>(bJ.size());
+    DDG_CUDA(cudaMemsetAsync(dB, 0, bI.size() * per * sizeof(double), h->stream));
+    h2d(dI, bI.data(), bI.size(), h->stream);
+    h2d(dJ, bJ.data(), bJ.size(), h->stream);
+    coarse_assemble_kernel<<<(unsigned)bI.size(), 128, 0, h->stream>>>(
+        dI, dJ, h->sub_off, h->sub_nodes, h->pos, h->part, h->rowptr, h->col, h->val64, h->Q64, h->kmax,
+        h->coff, nullptr, 0, dB);
+    DDG_CHECK_LAUNCH();
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    h->arena.release(dI);
+    h->arena.release(dJ);
+    return dB;
+}
+
+// the tile kernels take two 64 x 65 FP64 tiles of dynamic shared memory
+static void configure_band_kernels() {
+    static PerDeviceMax configured;
+    const int sm2 = (int)(2 * CT * CLD * sizeof(double));
+    int dev = -1;
+    if (!configured.needs(sm2, dev)) return;
+    DDG_CUDA(cudaFuncSetAttribute(band_potrf_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_trsm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    DDG_CUDA(cudaFuncSetAttribute(superblock_inverse_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_potrf_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_trsm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    DDG_CUDA(cudaFuncSetAttribute(band_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    DDG_CUDA(cudaFuncSetAttribute(superblock_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2));
+    configured.commit(dev, sm2);
+}
+
 void coarse_band_cholesky(ddg_handle h) {
     const size_t sm2 = 2 * CT * CLD * sizeof(double);
-    DDG_CUDA(cudaFuncSetAttribute(band_potrf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    DDG_CUDA(cudaFuncSetAttribute(band_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    DDG_CUDA(cudaFuncSetAttribute(band_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    DDG_CUDA(cudaFuncSetAttribute(superblock_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    configure_band_kernels();
     double* dinv = h->arena.alloc<double>((size_t)h->NT * CT * CT);
     const int Wt = h->Wt, NT = h->NT;
     for (int k = 0; k < NT; ++k) {
-        band_potrf_kernel<<<1, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, h->errflags + E_COARSE_SPD,
-                                                      nullptr, nullptr, nullptr);
+        band_potrf_kernel<false><<<1, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, h->errflags + E_COARSE_SPD,
+                                                             nullptr, nullptr, nullptr, nullptr);
         DDG_CHECK_LAUNCH();
         const int m = std::min(Wt, NT - 1 - k);
         if (m > 0) {
-            band_trsm_kernel<<<m, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, nullptr, nullptr, nullptr);
+            band_trsm_kernel<false><<<m, 256, sm2, h->stream>>>(h->bandL, Wt, k, dinv, nullptr, nullptr, nullptr,
+                                                                nullptr);
             DDG_CHECK_LAUNCH();
-            band_update_kernel<<<m * (m + 1) / 2, 256, sm2, h->stream>>>(h->bandL, Wt, k, nullptr, nullptr);
+            band_update_kernel<false><<<m * (m + 1) / 2, 256, sm2, h->stream>>>(h->bandL, Wt, k, nullptr, nullptr,
+                                                                                nullptr);
             DDG_CHECK_LAUNCH();
         }
     }
@@ -737,8 +795,8 @@ void coarse_band_cholesky(ddg_handle h) {
     const size_t Ptiles = (size_t)Wt * (Wt + 1) / 2;
     double* W = h->arena.alloc<double>((size_t)h->nK * Ptiles * CT * CT);
     DDG_CUDA(cudaMemsetAsync(W, 0, (size_t)h->nK * Ptiles * CT * CT * sizeof(double), h->stream));
-    superblock_inverse_kernel<<<dim3(Wt, h->nK), 256, sm2, h->stream>>>(h->bandL, Wt, dinv, W, NT, nullptr,
-                                                                         nullptr, nullptr, nullptr);
+    superblock_inverse_kernel<false><<<dim3(Wt, h->nK), 256, sm2, h->stream>>>(h->bandL, Wt, dinv, W, NT, nullptr,
+                                                                                nullptr, nullptr, nullptr, nullptr);
     DDG_CHECK_LAUNCH();
     h->coarseW = W;
     DDG_CUDA(cudaStreamSynchronize(h->stream));
@@ -753,23 +811,51 @@ void band_factor_batched(ddg_handle h, double* band, int Wt, int nb, int NTmax, 
                          const int32_t* nts, double* dinv, const int64_t* doff, double* W,
                          const int64_t* woff, int* err) {
     const size_t sm2 = 2 * CT * CLD * sizeof(double);
-    DDG_CUDA(cudaFuncSetAttribute(band_potrf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    DDG_CUDA(cudaFuncSetAttribute(band_trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    DDG_CUDA(cudaFuncSetAttribute(band_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    DDG_CUDA(cudaFuncSetAttribute(superblock_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    configure_band_kernels();
     for (int k = 0; k < NTmax; ++k) {
-        band_potrf_kernel<<<dim3(1, nb), 256, sm2, h->stream>>>(band, Wt, k, dinv, err, boff, doff, nts);
+        band_potrf_kernel<false><<<dim3(1, nb), 256, sm2, h->stream>>>(band, Wt, k, dinv, err, boff, doff, nts,
+                                                                       nullptr);
         DDG_CHECK_LAUNCH();
         const int m = std::min(Wt, NTmax - 1 - k);
         if (m > 0) {
-            band_trsm_kernel<<<dim3(m, nb), 256, sm2, h->stream>>>(band, Wt, k, dinv, boff, doff, nts);
+            band_trsm_kernel<false><<<dim3(m, nb), 256, sm2, h->stream>>>(band, Wt, k, dinv, boff, doff, nts,
+                                                                          nullptr);
             DDG_CHECK_LAUNCH();
-            band_update_kernel<<<dim3(m * (m + 1) / 2, nb), 256, sm2, h->stream>>>(band, Wt, k, boff, nts);
+            band_update_kernel<false><<<dim3(m * (m + 1) / 2, nb), 256, sm2, h->stream>>>(band, Wt, k, boff, nts,
+                                                                                          nullptr);
             DDG_CHECK_LAUNCH();
         }
     }
-    superblock_inverse_kernel<<<dim3(Wt, NTmax / Wt, nb), 256, sm2, h->stream>>>(band, Wt, dinv, W, NTmax, boff,
-                                                                               doff, woff, nts);
+    superblock_inverse_kernel<false><<<dim3(Wt, NTmax / Wt, nb), 256, sm2, h->stream>>>(
+        band, Wt, dinv, W, NTmax, boff, doff, woff, nts, nullptr);
+    DDG_CHECK_LAUNCH();
+}
+
+// Partial Cholesky of the dense fronts of one level of the nested-dissection
+// tree: front b (lower tiles at fronts + foff[b], nts[b] tile rows) has its
+// first nss[b] tile columns eliminated, leaving L11, L21 and the Schur
+// complement (the update matrix) in place; the inverse of L11 (packed lower
+// tiles) goes to W + woff[b].
+void front_factor_batched(ddg_handle h, double* fronts, int nb, int NTmax, int NSmax, const int64_t* foff,
+                          const int32_t* nts, const int32_t* nss, double* dinv, const int64_t* doff, double* W,
+                          const int64_t* woff, int* err) {
+    const size_t sm2 = 2 * CT * CLD * sizeof(double);
+    configure_band_kernels();
+    for (int k = 0; k < NSmax; ++k) {
+        band_potrf_kernel<true><<<dim3(1, nb), 256, sm2, h->stream>>>(fronts, 0, k, dinv, err, foff, doff, nts,
+                                                                      nss);
+        DDG_CHECK_LAUNCH();
+        const int m = NTmax - 1 - k;
+        if (m > 0) {
+            band_trsm_kernel<true><<<dim3(m, nb), 256, sm2, h->stream>>>(fronts, 0, k, dinv, foff, doff, nts, nss);
+            DDG_CHECK_LAUNCH();
+            band_update_kernel<true><<<dim3(m * (m + 1) / 2, nb), 256, sm2, h->stream>>>(fronts, 0, k, foff, nts,
+                                                                                         nss);
+            DDG_CHECK_LAUNCH();
+        }
+    }
+    superblock_inverse_kernel<true><<<dim3(NSmax, 1, nb), 256, sm2, h->stream>>>(fronts, 0, dinv, W, 0, foff, doff,
+                                                                                woff, nts, nss);
     DDG_CHECK_LAUNCH();
 }
 
@@ -927,6 +1013,10 @@ static void coarse_solve_t(ddg_handle h, V* c, V* y, V* x) {
 }
 
 void coarse_solve(ddg_handle h, int prec) {
+    if (h->nd.on) {
+        nd_coarse_solve(h, prec);
+        return;
+    }
     if (prec == DDG_PREC_FP64) coarse_solve_t<double>(h, h->c64, h->y64, h->x64);
     else coarse_solve_t<float>(h, h->c32, h->y32, h->x32);
 }

@@ -1,0 +1,684 @@
+// Exact coarse solve A0^{-1} (Sec. 4) through a nested-dissection Cholesky
+// factor of A0 (coarse_order ND).
+//
+// The coarse dofs of one subdomain stay together: the graph is that of the
+// subdomains that A0 couples, each weighted by its number of coarse dofs.
+// Nested dissection (recursive bisection by BFS level sets from a
+// pseudo-peripheral subdomain, the middle level the separator) orders the
+// subdomains; each separator is a front of the multifrontal factorisation:
+// its dense frontal matrix holds the front's own rows S and the rows U of
+// the ancestors' subdomains that its subtree couples to.  Fronts are
+// factorised level by level from the leaves (children's Schur complements
+// added into the parent, original A0 blocks placed in the front of the
+// earlier-eliminated subdomain), with the batched tile kernels in dense
+// mode.  Per front the solve keeps D = L_SS^{-1} and L_US (FP64 and FP32):
+//   forward  (leaves first)  y_S = D w_S,  w_U -= L_US y_S
+//   backward (root first)    x_S = D^T (y_S - L_US^T x_U)
+// The updates of w from the fronts of one level are summed per target dof in
+// a fixed order, so the solve is deterministic.
+#include <algorithm>
+#include <deque>
+#include <numeric>
+#include <unordered_map>
+#include <vector>
+
+#include "ddg_internal.cuh"
+#include "dev_common.cuh"
+
+namespace {
+
+constexpr int CT = DDG_CT;
+constexpr int ND_LEAF_DOFS = 256;   // a part of at most this many coarse dofs is a leaf front
+
+__host__ __device__ __forceinline__ int r4(int v) { return (v + 3) & ~3; }
+
+// element offset of row i of a packed lower triangle whose row r holds the
+// columns [0, r] padded to a multiple of 4: sum_{r < i} r4(r + 1)
+__host__ __device__ __forceinline__ int64_t drow(int i) {
+    const int64_t q = i / 4, rem = i % 4;
+    return 4 * (2 * q * (q + 1) + rem * (q + 1));
+}
+
+// element (r, c), r >= c, of a front stored as lower 64 x 64 tiles in row order
+__device__ __forceinline__ size_t dtile(int r, int c) {
+    const int R = r / CT, C = c / CT;
+    return ((size_t)R * (R + 1) / 2 + C) * CT * CT + (size_t)(r % CT) * CT + (c % CT);
+}
+
+struct NdPlace {
+    int64_t foff, blk;
+    int rpos, cpos, kr, kc, trans, diag;
+};
+
+// the blocks A0[(I,.),(J,.)] (I >= J, row stride kmax) into their fronts
+__global__ void nd_scatter_kernel(const NdPlace* __restrict__ pl, const double* __restrict__ blocks, int kmax,
+                                  double* fronts) {
+    const NdPlace P = pl[blockIdx.x];
+    for (int e = threadIdx.x; e < P.kr * P.kc; e += blockDim.x) {
+        const int s = e / P.kc, t = e % P.kc;
+        if (P.diag && t > s) continue;
+        const double v = P.trans ? blocks[P.blk + (size_t)t * kmax + s] : blocks[P.blk + (size_t)s * kmax + t];
+        fronts[P.foff + dtile(P.rpos + s, P.cpos + t)] = v;
+    }
+}
+
+// unit diagonal on the padding rows of a front: [a0, a1) and [b0, b1)
+__global__ void nd_pad_kernel(const int64_t* __restrict__ foff, const int4* __restrict__ pads, double* fronts) {
+    const int4 p = pads[blockIdx.x];
+    double* F = fronts + foff[blockIdx.x];
+    for (int i = p.x + threadIdx.x; i < p.y; i += blockDim.x) F[dtile(i, i)] = 1.0;
+    for (int i = p.z + threadIdx.x; i < p.w; i += blockDim.x) F[dtile(i, i)] = 1.0;
+}
+
+struct NdChild {
+    int64_t cfoff, pfoff, map_off;
+    int cbase;   // first row of the child's update matrix in its front
+};
+
+// parent[map a][map b] += child update[a][b], b <= a (one row a per CTA)
+__global__ void nd_extend_kernel(const NdChild* __restrict__ ch, const int2* __restrict__ items,
+                                 const int32_t* __restrict__ map, double* fronts) {
+    const int2 it = items[blockIdx.x];
+    const NdChild C = ch[it.x];
+    const int a = it.y;
+    const int pa = map[C.map_off + a];
+    for (int b = threadIdx.x; b <= a; b += blockDim.x)
+        fronts[C.pfoff + dtile(pa, map[C.map_off + b])] += fronts[C.cfoff + dtile(C.cbase + a, C.cbase + b)];
+}
+
+struct NdPack {
+    int64_t foff, woff, doff, loff;
+    int nS, nU, ubase;   // ubase: first row of U in the front (64 * tiles of S)
+};
+
+// D = L_SS^{-1} rows (kind 0) and L_US rows (kind 1) of one front per item
+__global__ void nd_pack_kernel(const NdPack* __restrict__ fp, const int4* __restrict__ items,
+                               const double* __restrict__ fronts, const double* __restrict__ W, double* out64,
+                               float* out32) {
+    const int4 it = items[blockIdx.x];   // (front, kind, row, unused)
+    const NdPack P = fp[it.x];
+    const int i = it.z;
+    if (it.y == 0) {
+        const int len = r4(i + 1);
+        for (int j = threadIdx.x; j < len; j += blockDim.x) {
+            double v = 0.0;
+            if (j <= i) {
+                const int ti = i / CT, tj = j / CT;
+                v = W[P.woff + ((size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (size_t)(i % CT) * CT + (j % CT)];
+            }
+            const int64_t o = P.doff + drow(i) + j;
+            if (out64) out64[o] = v;
+            if (out32) out32[o] = (float)v;
+        }
+    } else {
+        const int len = r4(P.nS);
+        for (int s = threadIdx.x; s < len; s += blockDim.x) {
+            const double v = s < P.nS ? fronts[P.foff + dtile(P.ubase + i, s)] : 0.0;
+            const int64_t o = P.loff + (int64_t)i * len + s;
+            if (out64) out64[o] = v;
+            if (out32) out32[o] = (float)v;
+        }
+    }
+}
+
+// ---- solve kernels (one level each); front arrays: S/U dof lists (coarse
+// ids), D and L_US offsets, contribution offsets
+struct NdSolve {
+    const int32_t *nS, *nU;
+    const int64_t *soff, *uoff, *doff, *loff, *coff;
+    const int32_t *sdof, *udof;
+};
+
+// y[S_f[i]] = sum_{j <= i} D_f[i][j] w[S_f[j]], a warp per row
+template <typename V>
+__global__ void __launch_bounds__(256) nd_fwd_d_kernel(NdSolve F, const int2* __restrict__ items, int n,
+                                                       const V* __restrict__ data, const V* w, V* y) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (wi >= n) return;
+    const int2 it = items[wi];
+    const int f = it.x, i = it.y;
+    const int32_t* S = F.sdof + F.soff[f];
+    const V* row = data + F.doff[f] + drow(i);
+    V s = 0;
+    for (int j = lane; j <= i; j += 32) s = fma(row[j], w[S[j]], s);
+    s = ddgdev::warp_sum(s);
+    if (lane == 0) y[S[i]] = s;
+}
+
+// contrib[coff_f + u] = sum_s L_f[u][s] y[S_f[s]], a warp per row
+template <typename V>
+__global__ void __launch_bounds__(256) nd_fwd_l_kernel(NdSolve F, const int2* __restrict__ items, int n,
+                                                       const V* __restrict__ data, const V* y, V* contrib) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (wi >= n) return;
+    const int2 it = items[wi];
+    const int f = it.x, u = it.y;
+    const int nS = F.nS[f];
+    const int32_t* S = F.sdof + F.soff[f];
+    const V* row = data + F.loff[f] + (int64_t)u * r4(nS);
+    V s = 0;
+    for (int j = lane; j < nS; j += 32) s = fma(row[j], y[S[j]], s);
+    s = ddgdev::warp_sum(s);
+    if (lane == 0) contrib[F.coff[f] + u] = s;
+}
+
+// w[t] -= the level's contributions to target t, in front order
+template <typename V>
+__global__ void nd_fwd_reduce_kernel(const int32_t* __restrict__ tgt, const int64_t* __restrict__ ptr,
+                                     const int64_t* __restrict__ src, int n, const V* contrib, V* w) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    V s = 0;
+    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) s += contrib[src[e]];
+    w[tgt[t]] -= s;
+}
+
+// tmp[S_f[s]] = y[S_f[s]] - sum_u L_f[u][s] x[U_f[u]] for the 32 columns of
+// block cb (lane = column, warps over rows, a fixed-order sum over warps)
+template <typename V>
+__global__ void __launch_bounds__(256) nd_bwd_l_kernel(NdSolve F, const int2* __restrict__ items,
+                                                       const V* __restrict__ data, const V* y, const V* x,
+                                                       V* tmp) {
+    __shared__ V part[8][32];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int2 it = items[blockIdx.x];
+    const int f = it.x, s = it.y * 32 + (threadIdx.x & 31), warp = threadIdx.x >> 5;
+    const int nS = F.nS[f], nU = F.nU[f];
+    const int32_t* U = F.udof + F.uoff[f];
+    const V* L = data + F.loff[f];
+    const int ld = r4(nS);
+    V acc = 0;
+    if (s < ld)
+        for (int u = warp; u < nU; u += 8) acc = fma(L[(int64_t)u * ld + s], x[U[u]], acc);
+    part[warp][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (warp == 0 && s < nS) {
+        V t = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < 8; ++w2) t += part[w2][threadIdx.x];
+        const int g = F.sdof[F.soff[f] + s];
+        tmp[g] = y[g] - t;
+    }
+}
+
+// x[S_f[j]] = sum_{i >= j} D_f[i][j] tmp[S_f[i]] for the 32 columns j of block cb
+template <typename V>
+__global__ void __launch_bounds__(256) nd_bwd_d_kernel(NdSolve F, const int2* __restrict__ items,
+                                                       const V* __restrict__ data, const V* tmp, V* x) {
+    __shared__ V part[8][32];
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int2 it = items[blockIdx.x];
+    const int f = it.x, j0 = it.y * 32, j = j0 + (threadIdx.x & 31), warp = threadIdx.x >> 5;
+    const int nS = F.nS[f];
+    const int32_t* S = F.sdof + F.soff[f];
+    const V* D = data + F.doff[f];
+    V acc = 0;
+    if (j < nS)
+        for (int i = j0 + warp; i < nS; i += 8)
+            if (i >= j) acc = fma(D[drow(i) + j], tmp[S[i]], acc);
+    part[warp][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (warp == 0 && j < nS) {
+        V t = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < 8; ++w2) t += part[w2][threadIdx.x];
+        x[S[j]] = t;
+    }
+}
+
+// ---- host symbolic analysis
+struct FrontH {
+    std::vector<int> S, U;
+    int child[2] = {-1, -1};
+    int nchild = 0, parent = -1, depth = 0;
+};
+
+struct NdBuilder {
+    const std::vector<std::vector<int>>& adj;
+    const std::vector<int>& rank;
+    std::vector<FrontH> fronts;
+    std::vector<int> stamp, level;
+    int cur = 0;
+    NdBuilder(const std::vector<std::vector<int>>& a, const std::vector<int>& r)
+        : adj(a), rank(r), stamp(a.size(), -1), level(a.size(), -1) {}
+
+    // BFS levels inside the set marked with `cur`; returns the visit order
+    std::vector<int> bfs(int start) {
+        std::vector<int> order{start};
+        level[start] = 0;
+        std::vector<int> seen{start};
+        for (size_t h = 0; h < order.size(); ++h) {
+            const int u = order[h];
+            for (int w : adj[u])
+                if (stamp[w] == cur && level[w] < 0) {
+                    level[w] = level[u] + 1;
+                    order.push_back(w);
+                }
+        }
+        return order;
+    }
+    void clear_levels(const std::vector<int>& order) {
+        for (int v : order) level[v] = -1;
+    }
+
+    int leaf(const std::vector<int>& nodes) {
+        FrontH f;
+        f.S = nodes;
+        std::sort(f.S.begin(), f.S.end());
+        fronts.push_back(f);
+        return (int)fronts.size() - 1;
+    }
+
+    int build(std::vector<int> nodes) {
+        int64_t weight = 0;
+        for (int v : nodes) weight += rank[v];
+        if (weight <= ND_LEAF_DOFS || nodes.size() <= 2) return leaf(nodes);
+        const int mark = ++cur;
+        for (int v : nodes) stamp[v] = mark;
+        // pseudo-peripheral start: two sweeps to the farthest node
+        int start = *std::min_element(nodes.begin(), nodes.end());
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            std::vector<int> order = bfs(start);
+            int far = start;
+            for (int v : order)
+                if (level[v] > level[far] || (level[v] == level[far] && v < far)) far = v;
+            clear_levels(order);
+            start = far;
+        }
+        std::vector<int> order = bfs(start);
+        int maxl = 0;
+        int64_t reached = 0;
+        for (int v : order) {
+            maxl = std::max(maxl, level[v]);
+            reached += rank[v];
+        }
+        std::vector<int64_t> wl(maxl + 1, 0);
+        for (int v : order) wl[level[v]] += rank[v];
+        int k = 0;
+        int64_t cum = 0;
+        for (int l = 0; l <= maxl; ++l) {
+            cum += wl[l];
+            if (2 * cum >= reached) {
+                k = l;
+                break;
+            }
+        }
+        if (k == 0 && maxl >= 1) k = 1;
+        std::vector<int> S, V1, V2;
+        for (int v : nodes) {
+            const int l = level[v];
+            if (l == k) S.push_back(v);
+            else if (l >= 0 && l < k) V1.push_back(v);
+            else V2.push_back(v);
+        }
+        clear_levels(order);
+        for (int v : nodes) stamp[v] = -1;
+        if (V1.empty() || V2.empty() || S.empty()) return leaf(nodes);
+        const int c1 = build(V1);
+        const int c2 = build(V2);
+        FrontH f;
+        f.S = S;
+        std::sort(f.S.begin(), f.S.end());
+        f.child[0] = c1;
+        f.child[1] = c2;
+        f.nchild = 2;
+        fronts.push_back(f);
+        const int id = (int)fronts.size() - 1;
+        fronts[c1].parent = id;
+        fronts[c2].parent = id;
+        return id;
+    }
+};
+
+template <typename T>
+T* upload(ddg_handle h, const std::vector<T>& v) {
+    T* d = h->arena.alloc<T>(v.size());
+    h2d(d, v.data(), v.size(), h->stream);
+    return d;
+}
+
+}  // namespace
+
+namespace ddg {
+
+// Symbolic analysis and numeric factorisation of the nested-dissection
+// coarse factor; pairs bI >= bJ are the subdomain pairs that A0 couples
+// (both with coarse dofs), blocks (device) their kmax x kmax blocks of A0.
+void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector<int>& bJ, const double* blocks) {
+    NdCoarse& N = h->nd;
+    const int nsub = h->nsub, kmax = h->kmax;
+    const std::vector<int>& coff = h->h_coff;
+    std::vector<int> rank(nsub);
+    for (int v = 0; v < nsub; ++v) rank[v] = coff[v + 1] - coff[v];
+    std::vector<std::vector<int>> adj(nsub);
+    for (size_t p = 0; p < bI.size(); ++p)
+        if (bI[p] != bJ[p]) {
+            adj[bI[p]].push_back(bJ[p]);
+            adj[bJ[p]].push_back(bI[p]);
+        }
+    std::vector<int> nodes;
+    for (int v = 0; v < nsub; ++v)
+        if (rank[v] > 0) nodes.push_back(v);
+    NdBuilder nb(adj, rank);
+    nb.build(nodes);
+    std::vector<FrontH>& fr = nb.fronts;
+    const int nf = (int)fr.size();
+    // postorder = creation order; the root is the last front
+    std::vector<int> fof(nsub, -1), eidx(nsub, -1);
+    {
+        int e = 0;
+        for (int f = 0; f < nf; ++f)
+            for (int v : fr[f].S) {
+                fof[v] = f;
+                eidx[v] = e++;
+            }
+    }
+    int nlevel = 1;
+    for (int f = nf - 1; f >= 0; --f) {
+        if (fr[f].parent >= 0) fr[f].depth = fr[fr[f].parent].depth + 1;
+        nlevel = std::max(nlevel, fr[f].depth + 1);
+    }
+    // U_f: subdomains of ancestors coupled to the subtree of f, in elimination order
+    {
+        std::vector<int> mark(nsub, -1);
+        for (int f = 0; f < nf; ++f) {
+            std::vector<int>& U = fr[f].U;
+            auto take = [&](int w) {
+                if (fof[w] > f && mark[w] != f) {
+                    mark[w] = f;
+                    U.push_back(w);
+                }
+            };
+            for (int v : fr[f].S)
+                for (int w : adj[v]) take(w);
+            for (int c = 0; c < fr[f].nchild; ++c)
+                for (int w : fr[fr[f].child[c]].U) take(w);
+            std::sort(U.begin(), U.end(), [&](int a, int b) { return eidx[a] < eidx[b]; });
+        }
+    }
+    // per front: dof counts, tiles, positions of its subdomains
+    std::vector<int> nS(nf), nU(nf), nSt(nf), NT(nf);
+    std::vector<std::unordered_map<int, int>> pos(nf);
+    std::vector<int64_t> foff(nf + 1, 0), doff(nf + 1, 0), woff(nf + 1, 0);
+    for (int f = 0; f < nf; ++f) {
+        int a = 0;
+        for (int v : fr[f].S) {
+            pos[f][v] = a;
+            a += rank[v];
+        }
+        nS[f] = a;
+        nSt[f] = std::max(1, (a + CT - 1) / CT);
+        int b = 0;
+        for (int v : fr[f].U) {
+            pos[f][v] = nSt[f] * CT + b;
+            b += rank[v];
+        }
+        nU[f] = b;
+        NT[f] = nSt[f] + (b + CT - 1) / CT;
+        foff[f + 1] = foff[f] + (int64_t)NT[f] * (NT[f] + 1) / 2 * CT * CT;
+        doff[f + 1] = doff[f] + (int64_t)nSt[f] * CT * CT;
+        woff[f + 1] = woff[f] + (int64_t)nSt[f] * (nSt[f] + 1) / 2 * CT * CT;
+    }
+    N.nfront = nf;
+    N.nlevel = nlevel;
+    // placement of the original blocks: the front of the earlier-eliminated subdomain
+    std::vector<NdPlace> place(bI.size());
+    for (size_t p = 0; p < bI.size(); ++p) {
+        const int I = bI[p], J = bJ[p];
+        const bool i_later = eidx[I] >= eidx[J];
+        const int L = i_later ? I : J, E = i_later ? J : I;
+        const int f = fof[E];
+        NdPlace P;
+        P.foff = foff[f];
+        P.blk = (int64_t)p * kmax * kmax;
+        P.rpos = pos[f].at(L);
+        P.cpos = pos[f].at(E);
+        P.kr = rank[L];
+        P.kc = rank[E];
+        P.trans = (I != J && L == J) ? 1 : 0;
+        P.diag = I == J ? 1 : 0;
+        place[p] = P;
+    }
+    std::vector<int4> pads(nf);
+    for (int f = 0; f < nf; ++f)
+        pads[f] = make_int4(nS[f], nSt[f] * CT, nSt[f] * CT + nU[f], NT[f] * CT);
+    // extend-add maps: child update row a -> parent front position
+    std::vector<int32_t> maps;
+    std::vector<NdChild> childs(nf);
+    for (int c = 0; c < nf; ++c) {
+        const int f = fr[c].parent;
+        NdChild C{};
+        C.cfoff = foff[c];
+        C.cbase = nSt[c] * CT;
+        C.map_off = (int64_t)maps.size();
+        C.pfoff = f >= 0 ? foff[f] : 0;
+        if (f >= 0)
+            for (int w : fr[c].U)
+                for (int t = 0; t < rank[w]; ++t) maps.push_back(pos[f].at(w) + t);
+        childs[c] = C;
+    }
+    // solve layout: D rows and L_US rows per front, contributions per front
+    std::vector<int64_t> sdoff(nf + 1, 0), sloff(nf + 1, 0), soff(nf + 1, 0), uoff(nf + 1, 0), cboff(nf + 1, 0);
+    std::vector<int32_t> sdof, udof;
+    int64_t cur = 0;
+    for (int f = 0; f < nf; ++f) {
+        sdoff[f] = cur;
+        cur += drow(nS[f]);
+        sloff[f] = cur;
+        cur += (int64_t)nU[f] * r4(nS[f]);
+        for (int v : fr[f].S)
+            for (int t = 0; t < rank[v]; ++t) sdof.push_back(coff[v] + t);
+        for (int v : fr[f].U)
+            for (int t = 0; t < rank[v]; ++t) udof.push_back(coff[v] + t);
+        soff[f + 1] = (int64_t)sdof.size();
+        uoff[f + 1] = (int64_t)udof.size();
+        cboff[f + 1] = cboff[f] + nU[f];
+    }
+    N.elems = cur;
+    // fronts by level, deepest first (the forward order)
+    std::vector<std::vector<int>> bylevel(nlevel);
+    for (int f = 0; f < nf; ++f) bylevel[nlevel - 1 - fr[f].depth].push_back(f);
+    std::vector<int2> drows, lrows, bcols;
+    std::vector<int32_t> rtgt;
+    std::vector<int64_t> rptr{0}, rsrc;
+    N.h_drow_off.assign(nlevel + 1, 0);
+    N.h_lrow_off.assign(nlevel + 1, 0);
+    N.h_bcol_off.assign(nlevel + 1, 0);
+    N.h_red_off.assign(nlevel + 1, 0);
+    for (int l = 0; l < nlevel; ++l) {
+        std::unordered_map<int, std::vector<int64_t>> contrib;
+        std::vector<int> order;
+        for (int f : bylevel[l]) {
+            for (int i = 0; i < nS[f]; ++i) drows.push_back(make_int2(f, i));
+            for (int u = 0; u < nU[f]; ++u) {
+                lrows.push_back(make_int2(f, u));
+                const int t = udof[uoff[f] + u];
+                auto it = contrib.find(t);
+                if (it == contrib.end()) {
+                    order.push_back(t);
+                    contrib[t] = {cboff[f] + u};
+                } else {
+                    it->second.push_back(cboff[f] + u);
+                }
+            }
+            for (int cb = 0; cb < (nS[f] + 31) / 32; ++cb) bcols.push_back(make_int2(f, cb));
+        }
+        std::sort(order.begin(), order.end());
+        for (int t : order) {
+            rtgt.push_back(t);
+            for (int64_t e : contrib[t]) rsrc.push_back(e);
+            rptr.push_back((int64_t)rsrc.size());
+        }
+        N.h_drow_off[l + 1] = (int)drows.size();
+        N.h_lrow_off[l + 1] = (int)lrows.size();
+        N.h_bcol_off[l + 1] = (int)bcols.size();
+        N.h_red_off[l + 1] = (int)rtgt.size();
+    }
+    // device copies of the solve layout
+    N.nS = upload(h, nS);
+    N.nU = upload(h, nU);
+    N.soff = upload(h, soff);
+    N.uoff = upload(h, uoff);
+    N.doff = upload(h, sdoff);
+    N.loff = upload(h, sloff);
+    N.cboff = upload(h, cboff);
+    N.sdof = upload(h, sdof.empty() ? std::vector<int32_t>{0} : sdof);
+    N.udof = upload(h, udof.empty() ? std::vector<int32_t>{0} : udof);
+    N.drows = upload(h, drows.empty() ? std::vector<int2>{make_int2(0, 0)} : drows);
+    N.lrows = upload(h, lrows.empty() ? std::vector<int2>{make_int2(0, 0)} : lrows);
+    N.bcols = upload(h, bcols.empty() ? std::vector<int2>{make_int2(0, 0)} : bcols);
+    N.rtgt = upload(h, rtgt.empty() ? std::vector<int32_t>{0} : rtgt);
+    N.rptr = upload(h, rptr);
+    N.rsrc = upload(h, rsrc.empty() ? std::vector<int64_t>{0} : rsrc);
+    N.d64 = h->arena.alloc<double>(N.elems);
+    N.d32 = h->arena.alloc<float>(N.elems);
+    N.contrib64 = h->arena.alloc<double>(std::max<int64_t>(1, cboff[nf]));
+    N.contrib32 = h->arena.alloc<float>(std::max<int64_t>(1, cboff[nf]));
+    N.w64 = h->arena.alloc<double>(std::max(1, h->n0));
+    N.w32 = h->arena.alloc<float>(std::max(1, h->n0));
+    N.t64 = h->arena.alloc<double>(std::max(1, h->n0));
+    N.t32 = h->arena.alloc<float>(std::max(1, h->n0));
+
+    // ---- numeric factorisation (FP64 workspaces, released at the end)
+    double* fronts = h->arena.alloc<double>(foff[nf]);
+    double* dinv = h->arena.alloc<double>(doff[nf]);
+    double* W = h->arena.alloc<double>(woff[nf]);
+    DDG_CUDA(cudaMemsetAsync(fronts, 0, foff[nf] * sizeof(double), h->stream));
+    DDG_CUDA(cudaMemsetAsync(W, 0, woff[nf] * sizeof(double), h->stream));
+    std::vector<void*> tmp;
+    auto up = [&](auto v) {
+        auto* d = upload(h, v);
+        tmp.push_back((void*)d);
+        return d;
+    };
+    if (!place.empty()) {
+        NdPlace* dpl = up(place);
+        nd_scatter_kernel<<<(unsigned)place.size(), 128, 0, h->stream>>>(dpl, blocks, kmax, fronts);
+        DDG_CHECK_LAUNCH();
+    }
+    {
+        int64_t* dfo = up(std::vector<int64_t>(foff.begin(), foff.end() - 1));
+        int4* dpads = up(pads);
+        nd_pad_kernel<<<nf, 128, 0, h->stream>>>(dfo, dpads, fronts);
+        DDG_CHECK_LAUNCH();
+    }
+    std::vector<NdPack> packs(nf);
+    for (int f = 0; f < nf; ++f) packs[f] = NdPack{foff[f], woff[f], sdoff[f], sloff[f], nS[f], nU[f], nSt[f] * CT};
+    NdChild* dch = upload(h, childs);
+    int32_t* dmaps = upload(h, maps.empty() ? std::vector<int32_t>{0} : maps);
+    NdPack* dpk = upload(h, packs);
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    for (void* p : tmp) h->arena.release(p);
+    tmp.clear();
+    for (int l = 0; l < nlevel; ++l) {
+        const std::vector<int>& fl = bylevel[l];
+        // children's update matrices into the fronts of this level, first
+        // children then second children (one writer per parent entry)
+        for (int slot = 0; slot < 2; ++slot) {
+            std::vector<int2> items;
+            for (int f : fl)
+                if (fr[f].nchild > slot) {
+                    const int c = fr[f].child[slot];
+                    for (int a = 0; a < nU[c]; ++a) items.push_back(make_int2(c, a));
+                }
+            if (items.empty()) continue;
+            int2* di = up(items);
+            nd_extend_kernel<<<(unsigned)items.size(), 256, 0, h->stream>>>(dch, di, dmaps, fronts);
+            DDG_CHECK_LAUNCH();
+        }
+        // partial factorisation of the level's fronts
+        std::vector<int64_t> bo, dof2, wo;
+        std::vector<int32_t> nts, nss;
+        int NTmax = 0, NSmax = 0;
+        for (int f : fl) {
+            bo.push_back(foff[f]);
+            dof2.push_back(doff[f]);
+            wo.push_back(woff[f]);
+            nts.push_back(NT[f]);
+            nss.push_back(nSt[f]);
+            NTmax = std::max(NTmax, NT[f]);
+            NSmax = std::max(NSmax, nSt[f]);
+        }
+        front_factor_batched(h, fronts, (int)fl.size(), NTmax, NSmax, up(bo), up(nts), up(nss), dinv, up(dof2), W,
+                             up(wo), h->errflags + E_COARSE_SPD);
+        // D and L_US rows of the level into the solve arrays
+        std::vector<int4> items;
+        for (int f : fl) {
+            for (int i = 0; i < nS[f]; ++i) items.push_back(make_int4(f, 0, i, 0));
+            for (int u = 0; u < nU[f]; ++u) items.push_back(make_int4(f, 1, u, 0));
+        }
+        if (!items.empty()) {
+            int4* di = up(items);
+            nd_pack_kernel<<<(unsigned)items.size(), 128, 0, h->stream>>>(dpk, di, fronts, W, N.d64, N.d32);
+            DDG_CHECK_LAUNCH();
+        }
+        // the level's workspaces are needed until its launches have run
+        DDG_CUDA(cudaStreamSynchronize(h->stream));
+        for (void* p : tmp) h->arena.release(p);
+        tmp.clear();
+    }
+    DDG_CUDA(cudaStreamSynchronize(h->stream));
+    for (void* p : {(void*)dch, (void*)dmaps, (void*)dpk}) h->arena.release(p);
+    h->arena.release(fronts);
+    h->arena.release(dinv);
+    h->arena.release(W);
+    N.on = true;
+}
+
+template <typename V>
+static void nd_solve_t(ddg_handle h, const V* data, V* c, V* y, V* x, V* contrib, V* tmp) {
+    const NdCoarse& N = h->nd;
+    const NdSolve F{N.nS, N.nU, N.soff, N.uoff, N.doff, N.loff, N.cboff, N.sdof, N.udof};
+    // forward, deepest level first: w = c is updated in place
+    for (int l = 0; l < N.nlevel; ++l) {
+        const int d0 = N.h_drow_off[l], d1 = N.h_drow_off[l + 1];
+        if (d1 > d0)
+            launch_pdl(h, nd_fwd_d_kernel<V>, dim3((unsigned)((d1 - d0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.drows + d0), d1 - d0, data, (const V*)c, y);
+        const int l0 = N.h_lrow_off[l], l1 = N.h_lrow_off[l + 1];
+        if (l1 > l0) {
+            launch_pdl(h, nd_fwd_l_kernel<V>, dim3((unsigned)((l1 - l0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.lrows + l0), l1 - l0, data, (const V*)y, contrib);
+            const int r0 = N.h_red_off[l], r1 = N.h_red_off[l + 1];
+            launch_pdl(h, nd_fwd_reduce_kernel<V>, dim3((unsigned)((r1 - r0 + 255) / 256)), dim3(256), 0,
+                       (const int32_t*)(N.rtgt + r0), (const int64_t*)(N.rptr + r0), (const int64_t*)N.rsrc,
+                       r1 - r0, (const V*)contrib, c);
+        }
+    }
+    // backward, root first
+    for (int l = N.nlevel - 1; l >= 0; --l) {
+        const int b0 = N.h_bcol_off[l], b1 = N.h_bcol_off[l + 1];
+        if (b1 <= b0) continue;
+        launch_pdl(h, nd_bwd_l_kernel<V>, dim3((unsigned)(b1 - b0)), dim3(256), 0, F, (const int2*)(N.bcols + b0),
+                   data, (const V*)y, (const V*)x, tmp);
+        launch_pdl(h, nd_bwd_d_kernel<V>, dim3((unsigned)(b1 - b0)), dim3(256), 0, F, (const int2*)(N.bcols + b0),
+                   data, (const V*)tmp, x);
+    }
+}
+
+int nd_solve_launches(ddg_handle h) {
+    const NdCoarse& N = h->nd;
+    int cnt = 0;
+    for (int l = 0; l < N.nlevel; ++l) {
+        if (N.h_drow_off[l + 1] > N.h_drow_off[l]) ++cnt;
+        if (N.h_lrow_off[l + 1] > N.h_lrow_off[l]) cnt += 2;
+        if (N.h_bcol_off[l + 1] > N.h_bcol_off[l]) cnt += 2;
+    }
+    return cnt;
+}
+
+void nd_coarse_solve(ddg_handle h, int prec) {
+    NdCoarse& N = h->nd;
+    if (prec == DDG_PREC_FP64) nd_solve_t<double>(h, N.d64, h->c64, h->y64, h->x64, N.contrib64, N.t64);
+    else nd_solve_t<float>(h, N.d32, h->c32, h->y32, h->x32, N.contrib32, N.t32);
+}
+
+}  // namespace ddg

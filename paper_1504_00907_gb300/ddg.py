@@ -22,6 +22,7 @@ DDG_OK, DDG_EINVAL, DDG_ENOMEM, DDG_ENOTSPD, DDG_EBREAKDOWN, DDG_ENOCONV, DDG_ET
 DDG_DEBUG_TC_NO_COPIES = 1
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 LOCAL = {"auto": 0, "inv": 1, "band": 2}
+COARSE = {"band": 0, "nd": 1}
 OVERLAP = {"graph": 0, "box": 1}
 BETA = {"fr": 0, "pr": 1, "auto": 2}
 
@@ -38,7 +39,7 @@ class Options(ctypes.Structure):
                 ("use_coarse", ctypes.c_int), ("rank_tol", ctypes.c_double),
                 ("chunk_tiles", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("dedup_local", ctypes.c_int), ("spin_budget_ms", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("local_repr", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("local_repr", ctypes.c_int), ("coarse_order", ctypes.c_int)]
 
 
 class Matrix(ctypes.Structure):
@@ -57,7 +58,8 @@ class Info(ctypes.Structure):
                 ("local_inverses", ctypes.c_int), ("graph_solve", ctypes.c_int),
                 ("ls_warps", ctypes.c_int), ("ls_chunk_tiles", ctypes.c_int), ("ls_band_rows", ctypes.c_int),
                 ("tc_stages", ctypes.c_int), ("tuned", ctypes.c_int), ("local_repr", ctypes.c_int),
-                ("local_band", ctypes.c_int), ("local_elems", ctypes.c_int64)]
+                ("local_band", ctypes.c_int), ("local_elems", ctypes.c_int64), ("coarse_order", ctypes.c_int),
+                ("coarse_fronts", ctypes.c_int), ("coarse_levels", ctypes.c_int), ("coarse_elems", ctypes.c_int64)]
 
 
 class KernelStat(ctypes.Structure):
@@ -185,7 +187,7 @@ class Solver:
                  coef=None, dofs_per_node=1, precision="fp64", keep=None, beta="auto",
                  maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
                  stream=None, coarse_groups=None, dedup_local=False, spin_budget_ms=1000.0,
-                 autotune=False, local_repr="auto"):
+                 autotune=False, local_repr="auto", coarse_order="band"):
         import torch
         lib = load()
         if not torch.cuda.is_available():
@@ -228,6 +230,7 @@ class Solver:
         o.spin_budget_ms = spin_budget_ms
         o.autotune = 1 if autotune else 0
         o.local_repr = LOCAL[local_repr]
+        o.coarse_order = COARSE[coarse_order]
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream

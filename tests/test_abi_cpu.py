@@ -42,6 +42,7 @@ int main(void) {
          offsetof(ddg_options, spin_budget_ms), offsetof(ddg_info, graph_solve));
   printf("%zu %zu %zu %zu\\n", offsetof(ddg_options, autotune), offsetof(ddg_info, tuned),
          offsetof(ddg_options, local_repr), offsetof(ddg_info, local_elems));
+  printf("%zu %zu\\n", offsetof(ddg_options, coarse_order), offsetof(ddg_info, coarse_elems));
   return 0;
 }
 """)
@@ -54,7 +55,7 @@ int main(void) {
            ddg.Info.setup_ms.offset, ddg.Info.local_inverses.offset, ddg.Options.dedup_local.offset,
            ddg.Options.spin_budget_ms.offset, ddg.Info.graph_solve.offset,
            ddg.Options.autotune.offset, ddg.Info.tuned.offset, ddg.Options.local_repr.offset,
-           ddg.Info.local_elems.offset]
+           ddg.Info.local_elems.offset, ddg.Options.coarse_order.offset, ddg.Info.coarse_elems.offset]
     assert got == exp
 
 

@@ -1,0 +1,122 @@
+"""Nested-dissection coarse factor (coarse_order ND) against the oracle.
+
+The exact coarse solve A0^{-1} of Sec. 4 runs through a multifrontal
+Cholesky factor of A0 ordered by nested dissection of the subdomain graph
+(the oracle factorises A0 densely, or banded above 6000 coarse dofs).  The
+coarse correction does not depend on the ordering, so FP64 results agree to
+rounding: 1e-11 for the coarse correction and the preconditioner, 1e-10 for
+PCG solutions (iterations within 1).  FP32 factors: mixed solves reach the
+true residual 1e-8 and stay within 1e-7 of the oracle's solution.
+
+Cases: 3D Poisson with 8^3 subdomains of 4^3 (a dissection tree of several
+levels), the 13-point biharmonic (A0 couples diagonal neighbours), Q1
+elasticity (30 generators per subdomain), graph overlap with rank-deficient
+subdomains, and a single-front case.
+"""
+import numpy as np
+import pytest
+
+import ddg_inputs as di
+from closeness import assert_close
+from oracle import ddg_oracle as orc
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+CASES = {
+    "poisson3d_32_box4": lambda: di.make_poisson3d(N=32, box=4, overlap=1, p=2, seed=41),
+    "biharmonic_128_box16": lambda: di.make_biharmonic2d(N=128, box=16, overlap=2, p=3, seed=42),
+    "elasticity_q1_12": lambda: di.make_elasticity3d(ne=12, box=3, overlap=1, p=2),
+    "poisson3d_graph_rankdrop": lambda: di.make_poisson3d(N=10, box=2, overlap=1, p=2, seed=43, mode="graph"),
+    "poisson2d_single_front": lambda: di.make_poisson2d(N=40, box=10, overlap=1, p=2, seed=44),
+}
+
+_cache = {}
+
+
+def setup(name):
+    if name not in _cache:
+        from paper_1504_00907_gb300 import ddg
+        prob = CASES[name]()
+        nd = ddg.Solver.from_problem(prob, precision="fp64", keep=("fp64", "fp32"), coarse_order="nd")
+        oracle = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape,
+                               dpn=prob.dofs_per_node)
+        _cache[name] = (prob, nd, oracle)
+    return _cache[name]
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def rhs(prob):
+    return prob.f if prob.f.ndim == 1 else prob.f[:, 0]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_nd_structure(name):
+    prob, nd, oracle = setup(name)
+    info = nd.info()
+    assert info["coarse_order"] == 1 and info["n0"] == oracle.A0.shape[0]
+    assert info["coarse_fronts"] >= 1 and info["coarse_levels"] >= 1
+    if name == "poisson3d_32_box4":
+        assert info["coarse_levels"] >= 3
+    np.testing.assert_array_equal(nd.coarse_offsets(), oracle.coarse_offsets)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_nd_coarse_correction_matches_oracle(name):
+    prob, nd, oracle = setup(name)
+    nd.set_precision("fp64")
+    r = np.random.default_rng(45).standard_normal(prob.n)
+    z = nd.coarse_correction(dev(r)).cpu().numpy()
+    assert_close(z, oracle.coarse_correction(r), 1e-11)
+    # and it is deterministic
+    z2 = nd.coarse_correction(dev(r)).cpu().numpy()
+    assert np.array_equal(z, z2)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_nd_preconditioner_and_solve_match_oracle(name):
+    prob, nd, oracle = setup(name)
+    nd.set_precision("fp64")
+    r = np.random.default_rng(46).standard_normal(prob.n)
+    assert_close(nd.apply(dev(r)).cpu().numpy(), oracle.apply(r), 1e-11)
+    f = rhs(prob)
+    ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
+    u, iters, relres, st = nd.solve(dev(f), tol=1e-8)
+    assert st == 0 and relres <= 1e-8 and abs(iters - ref.iters) <= 1
+    assert_close(u.cpu().numpy(), ref.u, 1e-10)
+
+
+@pytest.mark.parametrize("name", ["poisson3d_32_box4", "biharmonic_128_box16", "elasticity_q1_12"])
+def test_nd_mixed_solve_matches_oracle(name):
+    prob, nd, oracle = setup(name)
+    f = rhs(prob)
+    ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
+    nd.set_precision("fp32")
+    u, iters, relres, st = nd.solve(dev(f), tol=1e-8)
+    nd.set_precision("fp64")
+    un = u.cpu().numpy()
+    assert st == 0 and relres <= 1e-8
+    assert np.linalg.norm(f - prob.A @ un) / np.linalg.norm(f) <= 1e-8
+    assert_close(un, ref.u, 1e-7)
+    assert iters <= ref.iters + 3
+
+
+def test_nd_reproduces_generators_and_rebuilds_with_new_generators():
+    # F restricted to each subdomain spans part of the coarse space, so the
+    # coarse correction reproduces every generator column; ddg_set_generators
+    # rebuilds the dissection for the new coarse space
+    prob, nd, _ = setup("poisson3d_32_box4")
+    nd.set_precision("fp64")
+    for j in (0, 5, 9):
+        Fj = prob.F[:, j]
+        assert_close(nd.coarse_correction(dev(prob.A @ Fj)).cpu().numpy(), Fj, 1e-10)
+    F1 = di.monomials(di.fd_node_coords(prob.shape), 1)
+    nd.set_generators(F1)
+    M1 = orc.DDGOracle(prob.A, prob.part, F1, prob.overlap, prob.overlap_mode, prob.shape)
+    r = np.random.default_rng(47).standard_normal(prob.n)
+    assert_close(nd.coarse_correction(dev(r)).cpu().numpy(), M1.coarse_correction(r), 1e-11)
+    nd.set_generators(prob.F)
+    _cache.pop("poisson3d_32_box4")
