@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(BL_THREADS) band_solve_kernel(
     const int npad = nK * B;
     for (int i = tid; i < npad; i += BL_CONSUMERS) vec[i] = i < n ? res[o + i] : (V)0;
     consumers_sync();
-    const int warp = tid >> 5, lane = tid & 31;
+    const int warp = tid >> 5, lane = tid & 31;   // consumer warps 0..15
     int seq = 0;
     bool stop = false;   // the same in every consumer thread (a barrier vote)
     int bad = 0;         // this thread's wait for a chunk ran out
@@ -269,13 +269,21 @@ __global__ void __launch_bounds__(BL_THREADS) band_solve_kernel(
                 const int2 ch = chC[c];
                 const V* chunk;
                 acquire(chunk);
-                for (int i = ch.x + warp; i < ch.y; i += BL_NW) {
-                    const int a = (B - b + i) & ~3;
-                    const V* row = chunk + (rowC[i] - rowC[ch.x]);
+                // four rows per warp, eight lanes per row: three shuffle steps
+                // per row (the FP64 adds of a full-warp sum would cost half as
+                // much again as the row's multiply-adds)
+                for (int i0 = ch.x + warp * 4; i0 < ch.y; i0 += BL_NW * 4) {
+                    const int i = i0 + (lane >> 3), l8 = lane & 7;
                     V s = 0;
-                    for (int j = lane; j < B - a; j += 32) s = fma(row[j], yprev[a + j], s);
-                    s = ddgdev::warp_sum(s);
-                    if (lane == 0) tbuf[i] -= s;
+                    if (i < ch.y) {
+                        const int a = (B - b + i) & ~3;
+                        const V* row = chunk + (rowC[i] - rowC[ch.x]);
+                        for (int j = l8; j < B - a; j += 8) s = fma(row[j], yprev[a + j], s);
+                    }
+                    s += __shfl_xor_sync(0xffffffffu, s, 4);
+                    s += __shfl_xor_sync(0xffffffffu, s, 2);
+                    s += __shfl_xor_sync(0xffffffffu, s, 1);
+                    if (l8 == 0 && i < ch.y) tbuf[i] -= s;
                 }
                 release();
             }
@@ -284,12 +292,17 @@ __global__ void __launch_bounds__(BL_THREADS) band_solve_kernel(
             const int2 ch = chD[c];
             const V* chunk;
             acquire(chunk);
-            for (int i = ch.x + warp; i < ch.y; i += BL_NW) {
-                const V* row = chunk + (rowD[i] - rowD[ch.x]);
+            for (int i0 = ch.x + warp * 4; i0 < ch.y; i0 += BL_NW * 4) {
+                const int i = i0 + (lane >> 3), l8 = lane & 7;
                 V s = 0;
-                for (int j = lane; j <= i; j += 32) s = fma(row[j], tbuf[j], s);
-                s = ddgdev::warp_sum(s);
-                if (lane == 0) vK[i] = s;
+                if (i < ch.y) {
+                    const V* row = chunk + (rowD[i] - rowD[ch.x]);
+                    for (int j = l8; j <= i; j += 8) s = fma(row[j], tbuf[j], s);
+                }
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                if (l8 == 0 && i < ch.y) vK[i] = s;
             }
             release();
         }
