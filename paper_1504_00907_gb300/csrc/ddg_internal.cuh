@@ -241,15 +241,17 @@ struct BandLocal {
 struct NdCoarse {
     bool on = false;
     int nfront = 0, nlevel = 0;
-    int64_t elems = 0;                 // stored elements (one precision)
-    int32_t *nS = nullptr, *nU = nullptr, *sdof = nullptr, *udof = nullptr;
-    int64_t *soff = nullptr, *uoff = nullptr, *doff = nullptr, *loff = nullptr, *cboff = nullptr;
-    int2 *drows = nullptr, *lrows = nullptr, *bcols = nullptr;   // (front, row) / (front, 32-column block)
+    int64_t elems = 0;                 // stored elements (one precision): D, L_US, D^T, L_US^T
+    int32_t *nS = nullptr, *nU = nullptr, *s0 = nullptr;   // front sizes, first S position
+    int32_t *up = nullptr;             // positions of the fronts' U dofs (elimination order)
+    int32_t* elim = nullptr;           // [n0] coarse dof at each elimination position
+    int64_t *uoff = nullptr, *doff = nullptr, *loff = nullptr, *dtoff = nullptr, *ltoff = nullptr, *cboff = nullptr;
+    int2 *srows = nullptr, *urows = nullptr;   // (front, S row) / (front, U row) per level
     int32_t* rtgt = nullptr;           // targets of the per-level sums of the forward updates
     int64_t *rptr = nullptr, *rsrc = nullptr;
-    std::vector<int> h_drow_off, h_lrow_off, h_bcol_off, h_red_off;   // [nlevel + 1]
-    double *d64 = nullptr, *contrib64 = nullptr, *w64 = nullptr, *t64 = nullptr;
-    float *d32 = nullptr, *contrib32 = nullptr, *w32 = nullptr, *t32 = nullptr;
+    std::vector<int> h_srow_off, h_urow_off, h_red_off;   // [nlevel + 1], levels deepest first
+    double *d64 = nullptr, *contrib64 = nullptr, *w64 = nullptr, *t64 = nullptr, *x64 = nullptr;
+    float *d32 = nullptr, *contrib32 = nullptr, *w32 = nullptr, *t32 = nullptr, *x32 = nullptr;
 };
 
 // tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}

@@ -14,8 +14,12 @@
 // mode.  Per front the solve keeps D = L_SS^{-1} and L_US (FP64 and FP32):
 //   forward  (leaves first)  y_S = D w_S,  w_U -= L_US y_S
 //   backward (root first)    x_S = D^T (y_S - L_US^T x_U)
-// The updates of w from the fronts of one level are summed per target dof in
-// a fixed order, so the solve is deterministic.
+// The solve runs on vectors permuted to the elimination order, where every
+// front's S rows are one contiguous range; D, D^T, L_US and L_US^T are all
+// stored by rows, so each of the four products is a row-per-warp GEMV over
+// contiguous data (only x_U is gathered).  The updates of w from the fronts
+// of one level are summed per target in a fixed order, so the solve is
+// deterministic.
 #include <algorithm>
 #include <deque>
 #include <numeric>
@@ -37,6 +41,13 @@ __host__ __device__ __forceinline__ int r4(int v) { return (v + 3) & ~3; }
 __host__ __device__ __forceinline__ int64_t drow(int i) {
     const int64_t q = i / 4, rem = i % 4;
     return 4 * (2 * q * (q + 1) + rem * (q + 1));
+}
+
+// element offset of row j of a packed upper triangle of n columns whose row
+// r holds the columns [r & ~3, n) padded to a multiple of 4
+__host__ __device__ __forceinline__ int64_t dtrow(int j, int n) {
+    const int64_t q = j / 4, rem = j % 4;
+    return (int64_t)j * r4(n) - 8 * q * (q - 1) - 4 * q * rem;
 }
 
 // element (r, c), r >= c, of a front stored as lower 64 x 64 tiles in row order
@@ -87,83 +98,91 @@ __global__ void nd_extend_kernel(const NdChild* __restrict__ ch, const int2* __r
 }
 
 struct NdPack {
-    int64_t foff, woff, doff, loff;
+    int64_t foff, woff, doff, loff, dtoff, ltoff;
     int nS, nU, ubase;   // ubase: first row of U in the front (64 * tiles of S)
 };
 
-// D = L_SS^{-1} rows (kind 0) and L_US rows (kind 1) of one front per item
+__device__ __forceinline__ double nd_dinv(const NdPack& P, const double* W, int i, int j) {
+    const int ti = i / CT, tj = j / CT;
+    return W[P.woff + ((size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (size_t)(i % CT) * CT + (j % CT)];
+}
+
+// rows of D = L_SS^{-1} (kind 0), L_US (kind 1), D^T (kind 2) and L_US^T
+// (kind 3) of one front per item
 __global__ void nd_pack_kernel(const NdPack* __restrict__ fp, const int4* __restrict__ items,
                                const double* __restrict__ fronts, const double* __restrict__ W, double* out64,
                                float* out32) {
     const int4 it = items[blockIdx.x];   // (front, kind, row, unused)
     const NdPack P = fp[it.x];
     const int i = it.z;
+    int64_t o0;
+    int c0, len;
     if (it.y == 0) {
-        const int len = r4(i + 1);
-        for (int j = threadIdx.x; j < len; j += blockDim.x) {
-            double v = 0.0;
-            if (j <= i) {
-                const int ti = i / CT, tj = j / CT;
-                v = W[P.woff + ((size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (size_t)(i % CT) * CT + (j % CT)];
-            }
-            const int64_t o = P.doff + drow(i) + j;
-            if (out64) out64[o] = v;
-            if (out32) out32[o] = (float)v;
-        }
+        o0 = P.doff + drow(i), c0 = 0, len = r4(i + 1);
+    } else if (it.y == 1) {
+        o0 = P.loff + (int64_t)i * r4(P.nS), c0 = 0, len = r4(P.nS);
+    } else if (it.y == 2) {
+        o0 = P.dtoff + dtrow(i, P.nS), c0 = i & ~3, len = r4(P.nS) - c0;
     } else {
-        const int len = r4(P.nS);
-        for (int s = threadIdx.x; s < len; s += blockDim.x) {
-            const double v = s < P.nS ? fronts[P.foff + dtile(P.ubase + i, s)] : 0.0;
-            const int64_t o = P.loff + (int64_t)i * len + s;
-            if (out64) out64[o] = v;
-            if (out32) out32[o] = (float)v;
-        }
+        o0 = P.ltoff + (int64_t)i * r4(P.nU), c0 = 0, len = r4(P.nU);
+    }
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        const int c = c0 + e;
+        double v = 0.0;
+        if (it.y == 0) v = c <= i ? nd_dinv(P, W, i, c) : 0.0;
+        else if (it.y == 1) v = c < P.nS ? fronts[P.foff + dtile(P.ubase + i, c)] : 0.0;
+        else if (it.y == 2) v = (c >= i && c < P.nS) ? nd_dinv(P, W, c, i) : 0.0;
+        else v = c < P.nU ? fronts[P.foff + dtile(P.ubase + c, i)] : 0.0;
+        if (out64) out64[o0 + e] = v;
+        if (out32) out32[o0 + e] = (float)v;
     }
 }
 
-// ---- solve kernels (one level each); front arrays: S/U dof lists (coarse
-// ids), D and L_US offsets, contribution offsets
+// ---- solve kernels (one level each) on vectors in elimination order
 struct NdSolve {
-    const int32_t *nS, *nU;
-    const int64_t *soff, *uoff, *doff, *loff, *coff;
-    const int32_t *sdof, *udof;
+    const int32_t *nS, *nU, *s0, *up;
+    const int64_t *uoff, *doff, *loff, *dtoff, *ltoff, *cb;
 };
 
-// y[S_f[i]] = sum_{j <= i} D_f[i][j] w[S_f[j]], a warp per row
-template <typename V>
-__global__ void __launch_bounds__(256) nd_fwd_d_kernel(NdSolve F, const int2* __restrict__ items, int n,
-                                                       const V* __restrict__ data, const V* w, V* y) {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (wi >= n) return;
-    const int2 it = items[wi];
-    const int f = it.x, i = it.y;
-    const int32_t* S = F.sdof + F.soff[f];
-    const V* row = data + F.doff[f] + drow(i);
-    V s = 0;
-    for (int j = lane; j <= i; j += 32) s = fma(row[j], w[S[j]], s);
-    s = ddgdev::warp_sum(s);
-    if (lane == 0) y[S[i]] = s;
-}
+enum { ND_FD = 0, ND_FL = 1, ND_BL = 2, ND_BD = 3 };
 
-// contrib[coff_f + u] = sum_s L_f[u][s] y[S_f[s]], a warp per row
-template <typename V>
-__global__ void __launch_bounds__(256) nd_fwd_l_kernel(NdSolve F, const int2* __restrict__ items, int n,
-                                                       const V* __restrict__ data, const V* y, V* contrib) {
+// one row per warp:
+//   FD  y[s0 + r]   = sum_{j <= r} D[r][j] w[s0 + j]
+//   FL  contrib[cb + r] = sum_s L[r][s] y[s0 + s]
+//   BL  tmp[s0 + r] = y[s0 + r] - sum_u L^T[r][u] x[up_u]
+//   BD  x[s0 + r]   = sum_{c >= r} D^T[r][c] tmp[s0 + c]
+template <typename V, int MODE>
+__global__ void __launch_bounds__(256) nd_rows_kernel(NdSolve F, const int2* __restrict__ items, int n,
+                                                      const V* __restrict__ data, const V* in, const V* aux,
+                                                      V* out) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (wi >= n) return;
     const int2 it = items[wi];
-    const int f = it.x, u = it.y;
-    const int nS = F.nS[f];
-    const int32_t* S = F.sdof + F.soff[f];
-    const V* row = data + F.loff[f] + (int64_t)u * r4(nS);
+    const int f = it.x, r = it.y;
+    const int nS = F.nS[f], s0 = F.s0[f];
+    const V* row;
+    int c0, len;
+    if (MODE == ND_FD) row = data + F.doff[f] + drow(r), c0 = 0, len = r + 1;
+    else if (MODE == ND_FL) row = data + F.loff[f] + (int64_t)r * r4(nS), c0 = 0, len = nS;
+    else if (MODE == ND_BL) row = data + F.ltoff[f] + (int64_t)r * r4(F.nU[f]), c0 = 0, len = F.nU[f];
+    else row = data + F.dtoff[f] + dtrow(r, nS), c0 = r & ~3, len = nS - c0;
     V s = 0;
-    for (int j = lane; j < nS; j += 32) s = fma(row[j], y[S[j]], s);
+    if (MODE == ND_BL) {
+        const int32_t* up = F.up + F.uoff[f];
+#pragma unroll 4
+        for (int j = lane; j < len; j += 32) s = fma(row[j], in[up[j]], s);
+    } else {
+        const V* v = in + s0 + c0;
+#pragma unroll 4
+        for (int j = lane; j < len; j += 32) s = fma(row[j], v[j], s);
+    }
     s = ddgdev::warp_sum(s);
-    if (lane == 0) contrib[F.coff[f] + u] = s;
+    if (lane != 0) return;
+    if (MODE == ND_FL) out[F.cb[f] + r] = s;
+    else if (MODE == ND_BL) out[s0 + r] = aux[s0 + r] - s;
+    else out[s0 + r] = s;
 }
 
 // w[t] -= the level's contributions to target t, in front order
@@ -179,59 +198,15 @@ __global__ void nd_fwd_reduce_kernel(const int32_t* __restrict__ tgt, const int6
     w[tgt[t]] -= s;
 }
 
-// tmp[S_f[s]] = y[S_f[s]] - sum_u L_f[u][s] x[U_f[u]] for the 32 columns of
-// block cb (lane = column, warps over rows, a fixed-order sum over warps)
-template <typename V>
-__global__ void __launch_bounds__(256) nd_bwd_l_kernel(NdSolve F, const int2* __restrict__ items,
-                                                       const V* __restrict__ data, const V* y, const V* x,
-                                                       V* tmp) {
-    __shared__ V part[8][32];
+// dst[p] = src[idx[p]] (into elimination order), or dst[idx[p]] = src[p] (back)
+template <typename V, bool GATHER>
+__global__ void nd_permute_kernel(int n, const int32_t* __restrict__ idx, const V* src, V* dst) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int2 it = items[blockIdx.x];
-    const int f = it.x, s = it.y * 32 + (threadIdx.x & 31), warp = threadIdx.x >> 5;
-    const int nS = F.nS[f], nU = F.nU[f];
-    const int32_t* U = F.udof + F.uoff[f];
-    const V* L = data + F.loff[f];
-    const int ld = r4(nS);
-    V acc = 0;
-    if (s < ld)
-        for (int u = warp; u < nU; u += 8) acc = fma(L[(int64_t)u * ld + s], x[U[u]], acc);
-    part[warp][threadIdx.x & 31] = acc;
-    __syncthreads();
-    if (warp == 0 && s < nS) {
-        V t = 0;
-#pragma unroll
-        for (int w2 = 0; w2 < 8; ++w2) t += part[w2][threadIdx.x];
-        const int g = F.sdof[F.soff[f] + s];
-        tmp[g] = y[g] - t;
-    }
-}
-
-// x[S_f[j]] = sum_{i >= j} D_f[i][j] tmp[S_f[i]] for the 32 columns j of block cb
-template <typename V>
-__global__ void __launch_bounds__(256) nd_bwd_d_kernel(NdSolve F, const int2* __restrict__ items,
-                                                       const V* __restrict__ data, const V* tmp, V* x) {
-    __shared__ V part[8][32];
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int2 it = items[blockIdx.x];
-    const int f = it.x, j0 = it.y * 32, j = j0 + (threadIdx.x & 31), warp = threadIdx.x >> 5;
-    const int nS = F.nS[f];
-    const int32_t* S = F.sdof + F.soff[f];
-    const V* D = data + F.doff[f];
-    V acc = 0;
-    if (j < nS)
-        for (int i = j0 + warp; i < nS; i += 8)
-            if (i >= j) acc = fma(D[drow(i) + j], tmp[S[i]], acc);
-    part[warp][threadIdx.x & 31] = acc;
-    __syncthreads();
-    if (warp == 0 && j < nS) {
-        V t = 0;
-#pragma unroll
-        for (int w2 = 0; w2 < 8; ++w2) t += part[w2][threadIdx.x];
-        x[S[j]] = t;
-    }
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    if (GATHER) dst[p] = src[idx[p]];
+    else dst[idx[p]] = src[p];
 }
 
 // ---- host symbolic analysis
@@ -465,42 +440,56 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
                 for (int t = 0; t < rank[w]; ++t) maps.push_back(pos[f].at(w) + t);
         childs[c] = C;
     }
-    // solve layout: D rows and L_US rows per front, contributions per front
-    std::vector<int64_t> sdoff(nf + 1, 0), sloff(nf + 1, 0), soff(nf + 1, 0), uoff(nf + 1, 0), cboff(nf + 1, 0);
-    std::vector<int32_t> sdof, udof;
+    // solve layout, in elimination order: front f's S dofs are the positions
+    // s0[f] .. s0[f] + nS[f]; per front the rows of D, L_US, D^T and L_US^T
+    std::vector<int32_t> s0(nf, 0), upos, elim(h->n0, 0), pos_of(h->n0, 0);
+    std::vector<int64_t> sdoff(nf + 1, 0), sloff(nf + 1, 0), stoff(nf + 1, 0), sltoff(nf + 1, 0), uoff(nf + 1, 0),
+        cboff(nf + 1, 0);
+    {
+        int p = 0;
+        for (int f = 0; f < nf; ++f) {
+            s0[f] = p;
+            for (int v : fr[f].S)
+                for (int t = 0; t < rank[v]; ++t) {
+                    elim[p] = coff[v] + t;
+                    pos_of[coff[v] + t] = p;
+                    ++p;
+                }
+        }
+    }
     int64_t cur = 0;
     for (int f = 0; f < nf; ++f) {
         sdoff[f] = cur;
         cur += drow(nS[f]);
         sloff[f] = cur;
         cur += (int64_t)nU[f] * r4(nS[f]);
-        for (int v : fr[f].S)
-            for (int t = 0; t < rank[v]; ++t) sdof.push_back(coff[v] + t);
+        stoff[f] = cur;
+        cur += dtrow(nS[f], nS[f]);
+        sltoff[f] = cur;
+        cur += (int64_t)nS[f] * r4(nU[f]);
         for (int v : fr[f].U)
-            for (int t = 0; t < rank[v]; ++t) udof.push_back(coff[v] + t);
-        soff[f + 1] = (int64_t)sdof.size();
-        uoff[f + 1] = (int64_t)udof.size();
+            for (int t = 0; t < rank[v]; ++t) upos.push_back(pos_of[coff[v] + t]);
+        uoff[f + 1] = (int64_t)upos.size();
         cboff[f + 1] = cboff[f] + nU[f];
     }
     N.elems = cur;
     // fronts by level, deepest first (the forward order)
     std::vector<std::vector<int>> bylevel(nlevel);
     for (int f = 0; f < nf; ++f) bylevel[nlevel - 1 - fr[f].depth].push_back(f);
-    std::vector<int2> drows, lrows, bcols;
+    std::vector<int2> srows, urows;
     std::vector<int32_t> rtgt;
     std::vector<int64_t> rptr{0}, rsrc;
-    N.h_drow_off.assign(nlevel + 1, 0);
-    N.h_lrow_off.assign(nlevel + 1, 0);
-    N.h_bcol_off.assign(nlevel + 1, 0);
+    N.h_srow_off.assign(nlevel + 1, 0);
+    N.h_urow_off.assign(nlevel + 1, 0);
     N.h_red_off.assign(nlevel + 1, 0);
     for (int l = 0; l < nlevel; ++l) {
         std::unordered_map<int, std::vector<int64_t>> contrib;
         std::vector<int> order;
         for (int f : bylevel[l]) {
-            for (int i = 0; i < nS[f]; ++i) drows.push_back(make_int2(f, i));
+            for (int i = 0; i < nS[f]; ++i) srows.push_back(make_int2(f, i));
             for (int u = 0; u < nU[f]; ++u) {
-                lrows.push_back(make_int2(f, u));
-                const int t = udof[uoff[f] + u];
+                urows.push_back(make_int2(f, u));
+                const int t = upos[uoff[f] + u];
                 auto it = contrib.find(t);
                 if (it == contrib.end()) {
                     order.push_back(t);
@@ -509,7 +498,6 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
                     it->second.push_back(cboff[f] + u);
                 }
             }
-            for (int cb = 0; cb < (nS[f] + 31) / 32; ++cb) bcols.push_back(make_int2(f, cb));
         }
         std::sort(order.begin(), order.end());
         for (int t : order) {
@@ -517,24 +505,24 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
             for (int64_t e : contrib[t]) rsrc.push_back(e);
             rptr.push_back((int64_t)rsrc.size());
         }
-        N.h_drow_off[l + 1] = (int)drows.size();
-        N.h_lrow_off[l + 1] = (int)lrows.size();
-        N.h_bcol_off[l + 1] = (int)bcols.size();
+        N.h_srow_off[l + 1] = (int)srows.size();
+        N.h_urow_off[l + 1] = (int)urows.size();
         N.h_red_off[l + 1] = (int)rtgt.size();
     }
     // device copies of the solve layout
     N.nS = upload(h, nS);
     N.nU = upload(h, nU);
-    N.soff = upload(h, soff);
+    N.s0 = upload(h, s0);
+    N.up = upload(h, upos.empty() ? std::vector<int32_t>{0} : upos);
     N.uoff = upload(h, uoff);
     N.doff = upload(h, sdoff);
     N.loff = upload(h, sloff);
+    N.dtoff = upload(h, stoff);
+    N.ltoff = upload(h, sltoff);
     N.cboff = upload(h, cboff);
-    N.sdof = upload(h, sdof.empty() ? std::vector<int32_t>{0} : sdof);
-    N.udof = upload(h, udof.empty() ? std::vector<int32_t>{0} : udof);
-    N.drows = upload(h, drows.empty() ? std::vector<int2>{make_int2(0, 0)} : drows);
-    N.lrows = upload(h, lrows.empty() ? std::vector<int2>{make_int2(0, 0)} : lrows);
-    N.bcols = upload(h, bcols.empty() ? std::vector<int2>{make_int2(0, 0)} : bcols);
+    N.elim = upload(h, elim.empty() ? std::vector<int32_t>{0} : elim);
+    N.srows = upload(h, srows.empty() ? std::vector<int2>{make_int2(0, 0)} : srows);
+    N.urows = upload(h, urows.empty() ? std::vector<int2>{make_int2(0, 0)} : urows);
     N.rtgt = upload(h, rtgt.empty() ? std::vector<int32_t>{0} : rtgt);
     N.rptr = upload(h, rptr);
     N.rsrc = upload(h, rsrc.empty() ? std::vector<int64_t>{0} : rsrc);
@@ -546,6 +534,8 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     N.w32 = h->arena.alloc<float>(std::max(1, h->n0));
     N.t64 = h->arena.alloc<double>(std::max(1, h->n0));
     N.t32 = h->arena.alloc<float>(std::max(1, h->n0));
+    N.x64 = h->arena.alloc<double>(std::max(1, h->n0));
+    N.x32 = h->arena.alloc<float>(std::max(1, h->n0));
 
     // ---- numeric factorisation (FP64 workspaces, released at the end)
     double* fronts = h->arena.alloc<double>(foff[nf]);
@@ -571,7 +561,8 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         DDG_CHECK_LAUNCH();
     }
     std::vector<NdPack> packs(nf);
-    for (int f = 0; f < nf; ++f) packs[f] = NdPack{foff[f], woff[f], sdoff[f], sloff[f], nS[f], nU[f], nSt[f] * CT};
+    for (int f = 0; f < nf; ++f)
+        packs[f] = NdPack{foff[f], woff[f], sdoff[f], sloff[f], stoff[f], sltoff[f], nS[f], nU[f], nSt[f] * CT};
     NdChild* dch = upload(h, childs);
     int32_t* dmaps = upload(h, maps.empty() ? std::vector<int32_t>{0} : maps);
     NdPack* dpk = upload(h, packs);
@@ -612,7 +603,11 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         // D and L_US rows of the level into the solve arrays
         std::vector<int4> items;
         for (int f : fl) {
-            for (int i = 0; i < nS[f]; ++i) items.push_back(make_int4(f, 0, i, 0));
+            for (int i = 0; i < nS[f]; ++i) {
+                items.push_back(make_int4(f, 0, i, 0));
+                items.push_back(make_int4(f, 2, i, 0));
+                if (nU[f] > 0) items.push_back(make_int4(f, 3, i, 0));
+            }
             for (int u = 0; u < nU[f]; ++u) items.push_back(make_int4(f, 1, u, 0));
         }
         if (!items.empty()) {
@@ -634,51 +629,58 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
 }
 
 template <typename V>
-static void nd_solve_t(ddg_handle h, const V* data, V* c, V* y, V* x, V* contrib, V* tmp) {
+static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V* w, V* tmp, V* xp, V* contrib) {
     const NdCoarse& N = h->nd;
-    const NdSolve F{N.nS, N.nU, N.soff, N.uoff, N.doff, N.loff, N.cboff, N.sdof, N.udof};
-    // forward, deepest level first: w = c is updated in place
+    const NdSolve F{N.nS, N.nU, N.s0, N.up, N.uoff, N.doff, N.loff, N.dtoff, N.ltoff, N.cboff};
+    const int n0 = h->n0;
+    const unsigned pb = (unsigned)((n0 + 255) / 256);
+    launch_pdl(h, nd_permute_kernel<V, true>, dim3(pb), dim3(256), 0, n0, (const int32_t*)N.elim, c, w);
+    // forward, deepest level first; w is updated in place
     for (int l = 0; l < N.nlevel; ++l) {
-        const int d0 = N.h_drow_off[l], d1 = N.h_drow_off[l + 1];
-        if (d1 > d0)
-            launch_pdl(h, nd_fwd_d_kernel<V>, dim3((unsigned)((d1 - d0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.drows + d0), d1 - d0, data, (const V*)c, y);
-        const int l0 = N.h_lrow_off[l], l1 = N.h_lrow_off[l + 1];
-        if (l1 > l0) {
-            launch_pdl(h, nd_fwd_l_kernel<V>, dim3((unsigned)((l1 - l0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.lrows + l0), l1 - l0, data, (const V*)y, contrib);
+        const int a0 = N.h_srow_off[l], a1 = N.h_srow_off[l + 1];
+        if (a1 > a0)
+            launch_pdl(h, nd_rows_kernel<V, ND_FD>, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.srows + a0), a1 - a0, data, (const V*)w, (const V*)nullptr, y);
+        const int b0 = N.h_urow_off[l], b1 = N.h_urow_off[l + 1];
+        if (b1 > b0) {
+            launch_pdl(h, nd_rows_kernel<V, ND_FL>, dim3((unsigned)((b1 - b0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.urows + b0), b1 - b0, data, (const V*)y, (const V*)nullptr, contrib);
             const int r0 = N.h_red_off[l], r1 = N.h_red_off[l + 1];
             launch_pdl(h, nd_fwd_reduce_kernel<V>, dim3((unsigned)((r1 - r0 + 255) / 256)), dim3(256), 0,
                        (const int32_t*)(N.rtgt + r0), (const int64_t*)(N.rptr + r0), (const int64_t*)N.rsrc,
-                       r1 - r0, (const V*)contrib, c);
+                       r1 - r0, (const V*)contrib, w);
         }
     }
     // backward, root first
     for (int l = N.nlevel - 1; l >= 0; --l) {
-        const int b0 = N.h_bcol_off[l], b1 = N.h_bcol_off[l + 1];
-        if (b1 <= b0) continue;
-        launch_pdl(h, nd_bwd_l_kernel<V>, dim3((unsigned)(b1 - b0)), dim3(256), 0, F, (const int2*)(N.bcols + b0),
-                   data, (const V*)y, (const V*)x, tmp);
-        launch_pdl(h, nd_bwd_d_kernel<V>, dim3((unsigned)(b1 - b0)), dim3(256), 0, F, (const int2*)(N.bcols + b0),
-                   data, (const V*)tmp, x);
+        const int a0 = N.h_srow_off[l], a1 = N.h_srow_off[l + 1];
+        if (a1 <= a0) continue;
+        const dim3 g((unsigned)((a1 - a0 + 7) / 8));
+        launch_pdl(h, nd_rows_kernel<V, ND_BL>, g, dim3(256), 0, F, (const int2*)(N.srows + a0), a1 - a0, data,
+                   (const V*)xp, (const V*)y, tmp);
+        launch_pdl(h, nd_rows_kernel<V, ND_BD>, g, dim3(256), 0, F, (const int2*)(N.srows + a0), a1 - a0, data,
+                   (const V*)tmp, (const V*)nullptr, xp);
     }
+    launch_pdl(h, nd_permute_kernel<V, false>, dim3(pb), dim3(256), 0, n0, (const int32_t*)N.elim, (const V*)xp,
+               xout);
 }
 
 int nd_solve_launches(ddg_handle h) {
     const NdCoarse& N = h->nd;
-    int cnt = 0;
+    int cnt = 2;
     for (int l = 0; l < N.nlevel; ++l) {
-        if (N.h_drow_off[l + 1] > N.h_drow_off[l]) ++cnt;
-        if (N.h_lrow_off[l + 1] > N.h_lrow_off[l]) cnt += 2;
-        if (N.h_bcol_off[l + 1] > N.h_bcol_off[l]) cnt += 2;
+        if (N.h_srow_off[l + 1] > N.h_srow_off[l]) cnt += 3;
+        if (N.h_urow_off[l + 1] > N.h_urow_off[l]) cnt += 2;
     }
     return cnt;
 }
 
 void nd_coarse_solve(ddg_handle h, int prec) {
     NdCoarse& N = h->nd;
-    if (prec == DDG_PREC_FP64) nd_solve_t<double>(h, N.d64, h->c64, h->y64, h->x64, N.contrib64, N.t64);
-    else nd_solve_t<float>(h, N.d32, h->c32, h->y32, h->x32, N.contrib32, N.t32);
+    if (prec == DDG_PREC_FP64)
+        nd_solve_t<double>(h, N.d64, h->c64, h->y64, h->x64, N.w64, N.t64, N.x64, N.contrib64);
+    else
+        nd_solve_t<float>(h, N.d32, h->c32, h->y32, h->x32, N.w32, N.t32, N.x32, N.contrib32);
 }
 
 }  // namespace ddg
