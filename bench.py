@@ -816,7 +816,7 @@ def main():
               "setup_s": nsetup, "ms": nms, "iters": nres[-1][1], "true_relres": nres[-1][2],
               "status": int(nres[-1][3]), "dof_iters_per_s": world * n * nres[-1][1] / (nms / 1e3),
               "breakdown_one_solve": nbreak,
-              "coarse_bytes_per_apply_fp32": 2 * 4 * ninfo["coarse_elems"],
+              "coarse_bytes_per_apply_fp32": 4 * ninfo["coarse_elems"],
               "band_coarse_bytes_per_apply_fp32": 4 * info["coarse_elems"]}
 
     # Sec. 7: condition estimate of M^{-1}A from the Lanczos tridiagonal of

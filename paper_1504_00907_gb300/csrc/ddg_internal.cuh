@@ -241,17 +241,18 @@ struct BandLocal {
 struct NdCoarse {
     bool on = false;
     int nfront = 0, nlevel = 0;
-    int64_t elems = 0;                 // stored elements (one precision): D, L_US, D^T, L_US^T
+    int64_t elems = 0;                 // stored elements (one precision): D, G, D^T, G^T
     int32_t *nS = nullptr, *nU = nullptr, *s0 = nullptr;   // front sizes, first S position
     int32_t *up = nullptr;             // positions of the fronts' U dofs (elimination order)
     int32_t* elim = nullptr;           // [n0] coarse dof at each elimination position
-    int64_t *uoff = nullptr, *doff = nullptr, *loff = nullptr, *dtoff = nullptr, *ltoff = nullptr, *cboff = nullptr;
-    int2 *srows = nullptr, *urows = nullptr;   // (front, S row) / (front, U row) per level
-    int32_t* rtgt = nullptr;           // targets of the per-level sums of the forward updates
-    int64_t *rptr = nullptr, *rsrc = nullptr;
-    std::vector<int> h_srow_off, h_urow_off, h_red_off;   // [nlevel + 1], levels deepest first
-    double *d64 = nullptr, *contrib64 = nullptr, *w64 = nullptr, *t64 = nullptr, *x64 = nullptr;
-    float *d32 = nullptr, *contrib32 = nullptr, *w32 = nullptr, *t32 = nullptr, *x32 = nullptr;
+    int64_t *uoff = nullptr, *doff = nullptr, *goff = nullptr, *dtoff = nullptr, *gtoff = nullptr;
+    int2 *fitems = nullptr, *bitems = nullptr;   // forward / backward items per level
+    int32_t* rtgt = nullptr;           // targets of the forward updates, per level
+    int64_t* rptr = nullptr;
+    int2* rsrc = nullptr;              // (front, G row) pairs per target, in a fixed order
+    std::vector<int> h_fwd_off, h_bwd_off;   // [nlevel + 1], levels deepest first
+    double *d64 = nullptr, *w64 = nullptr, *x64 = nullptr;
+    float *d32 = nullptr, *w32 = nullptr, *x32 = nullptr;
 };
 
 // tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}

@@ -11,15 +11,16 @@
 // factorised level by level from the leaves (children's Schur complements
 // added into the parent, original A0 blocks placed in the front of the
 // earlier-eliminated subdomain), with the batched tile kernels in dense
-// mode.  Per front the solve keeps D = L_SS^{-1} and L_US (FP64 and FP32):
-//   forward  (leaves first)  y_S = D w_S,  w_U -= L_US y_S
-//   backward (root first)    x_S = D^T (y_S - L_US^T x_U)
-// The solve runs on vectors permuted to the elimination order, where every
-// front's S rows are one contiguous range; D, D^T, L_US and L_US^T are all
-// stored by rows, so each of the four products is a row-per-warp GEMV over
-// contiguous data (only x_U is gathered).  The updates of w from the fronts
-// of one level are summed per target in a fixed order, so the solve is
-// deterministic.
+// mode.  Per front the solve keeps D = L_SS^{-1} and G = L_US D (FP64 and
+// FP32), since L_US y_S = L_US D w_S = G w_S and D^T L_US^T = G^T:
+//   forward  (leaves first)  y_S = D w_S,  w_U -= G w_S
+//   backward (root first)    x_S = D^T y_S - G^T x_U
+// so each level is one launch per direction (its products read only data
+// that earlier levels finished).  The solve runs on vectors permuted to the
+// elimination order, where every front's S rows are one contiguous range;
+// D, D^T, G and G^T are stored by rows, so every product is a row-per-warp
+// dot product over contiguous data (only x_U is gathered).  The updates of
+// w are summed per target in a fixed order, so the solve is deterministic.
 #include <algorithm>
 #include <deque>
 #include <numeric>
@@ -28,10 +29,11 @@
 
 #include "ddg_internal.cuh"
 #include "dev_common.cuh"
+#include "tile64.cuh"
 
 namespace {
 
-constexpr int CT = DDG_CT;
+using namespace tile64;
 constexpr int ND_LEAF_DOFS = 256;   // a part of at most this many coarse dofs is a leaf front
 
 __host__ __device__ __forceinline__ int r4(int v) { return (v + 3) & ~3; }
@@ -98,8 +100,8 @@ __global__ void nd_extend_kernel(const NdChild* __restrict__ ch, const int2* __r
 }
 
 struct NdPack {
-    int64_t foff, woff, doff, loff, dtoff, ltoff;
-    int nS, nU, ubase;   // ubase: first row of U in the front (64 * tiles of S)
+    int64_t foff, woff, goff, doff, loff, dtoff, ltoff;   // loff / ltoff: rows of G / G^T
+    int nS, nU, nSt;
 };
 
 __device__ __forceinline__ double nd_dinv(const NdPack& P, const double* W, int i, int j) {
@@ -107,10 +109,46 @@ __device__ __forceinline__ double nd_dinv(const NdPack& P, const double* W, int 
     return W[P.woff + ((size_t)ti * (ti + 1) / 2 + tj) * CT * CT + (size_t)(i % CT) * CT + (j % CT)];
 }
 
-// rows of D = L_SS^{-1} (kind 0), L_US (kind 1), D^T (kind 2) and L_US^T
-// (kind 3) of one front per item
+// G = L_US D of one front, 64 x 64 tile (I, J) per CTA: the sum over the
+// tiles m >= J of L_US(I, m) D(m, J) (D lower triangular); G stored as row
+// tiles nUt x nSt at Gw + goff.  grid (nUt * nSt max, fronts of the level)
+__global__ void __launch_bounds__(256) nd_gprod_kernel(const NdPack* __restrict__ fp,
+                                                       const int32_t* __restrict__ flist,
+                                                       const double* __restrict__ fronts,
+                                                       const double* __restrict__ W, double* Gw) {
+    extern __shared__ double sm[];
+    double* A = sm;
+    double* Bm = sm + CT * CLD;
+    const NdPack P = fp[flist[blockIdx.y]];
+    const int nUt = (P.nU + CT - 1) / CT;
+    if ((int)blockIdx.x >= nUt * P.nSt) return;
+    const int I = blockIdx.x / P.nSt, J = blockIdx.x % P.nSt;
+    double acc[4][4];
+    acc_zero4(acc);
+    for (int m = J; m < P.nSt; ++m) {
+        const int R = P.nSt + I;
+        ct_load(A, fronts + P.foff + ((size_t)R * (R + 1) / 2 + m) * CT * CT);
+        ct_load(Bm, W + P.woff + ((size_t)m * (m + 1) / 2 + J) * CT * CT);
+        __syncthreads();
+        ct_mac<false>(acc, A, Bm);
+        __syncthreads();
+    }
+    const int r0 = (threadIdx.x >> 4) * 4, c0 = (threadIdx.x & 15) * 4;
+    double* out = Gw + P.goff + ((size_t)I * P.nSt + J) * CT * CT;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) out[(r0 + a) * CT + c0 + b] = acc[a][b];
+}
+
+__device__ __forceinline__ double nd_g(const NdPack& P, const double* Gw, int u, int s) {
+    return Gw[P.goff + ((size_t)(u / CT) * P.nSt + s / CT) * CT * CT + (size_t)(u % CT) * CT + (s % CT)];
+}
+
+// rows of D = L_SS^{-1} (kind 0), G (kind 1), D^T (kind 2) and G^T (kind 3)
+// of one front per item
 __global__ void nd_pack_kernel(const NdPack* __restrict__ fp, const int4* __restrict__ items,
-                               const double* __restrict__ fronts, const double* __restrict__ W, double* out64,
+                               const double* __restrict__ Gw, const double* __restrict__ W, double* out64,
                                float* out32) {
     const int4 it = items[blockIdx.x];   // (front, kind, row, unused)
     const NdPack P = fp[it.x];
@@ -130,72 +168,83 @@ __global__ void nd_pack_kernel(const NdPack* __restrict__ fp, const int4* __rest
         const int c = c0 + e;
         double v = 0.0;
         if (it.y == 0) v = c <= i ? nd_dinv(P, W, i, c) : 0.0;
-        else if (it.y == 1) v = c < P.nS ? fronts[P.foff + dtile(P.ubase + i, c)] : 0.0;
+        else if (it.y == 1) v = c < P.nS ? nd_g(P, Gw, i, c) : 0.0;
         else if (it.y == 2) v = (c >= i && c < P.nS) ? nd_dinv(P, W, c, i) : 0.0;
-        else v = c < P.nU ? fronts[P.foff + dtile(P.ubase + c, i)] : 0.0;
+        else v = c < P.nU ? nd_g(P, Gw, c, i) : 0.0;
         if (out64) out64[o0 + e] = v;
         if (out32) out32[o0 + e] = (float)v;
     }
 }
 
-// ---- solve kernels (one level each) on vectors in elimination order
+// ---- solve kernels (one launch per level and direction) on vectors in
+// elimination order
 struct NdSolve {
     const int32_t *nS, *nU, *s0, *up;
-    const int64_t *uoff, *doff, *loff, *dtoff, *ltoff, *cb;
+    const int64_t *uoff, *doff, *goff, *dtoff, *gtoff;
 };
 
-enum { ND_FD = 0, ND_FL = 1, ND_BL = 2, ND_BD = 3 };
+// forward, one warp per item: (front f, row i) gives y[s0 + i] = D[i] . w_S;
+// (-1 - k, 0) gives target k of the level: w[tgt_k] -= the sum, in a fixed
+// order, of G_f[u] . w_{S_f} over the (front, row) pairs listed for it
+template <typename V>
+__global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
+                                                     const int32_t* __restrict__ tgt, const int64_t* __restrict__ ptr,
+                                                     const int2* __restrict__ src, const V* __restrict__ data, V* w,
+                                                     V* y) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (wi >= n) return;
+    const int2 it = items[wi];
+    if (it.x >= 0) {
+        const int f = it.x, i = it.y;
+        const V* row = data + F.doff[f] + drow(i);
+        const V* v = w + F.s0[f];
+        V s = 0;
+#pragma unroll 4
+        for (int j = lane; j <= i; j += 32) s = fma(row[j], v[j], s);
+        s = ddgdev::warp_sum(s);
+        if (lane == 0) y[F.s0[f] + i] = s;
+        return;
+    }
+    const int k = -1 - it.x;
+    V s = 0;
+    for (int64_t e = ptr[k]; e < ptr[k + 1]; ++e) {
+        const int2 fu = src[e];
+        const int f = fu.x, nS = F.nS[f];
+        const V* row = data + F.goff[f] + (int64_t)fu.y * r4(nS);
+        const V* v = w + F.s0[f];
+        V t = 0;
+#pragma unroll 4
+        for (int j = lane; j < nS; j += 32) t = fma(row[j], v[j], t);
+        s += ddgdev::warp_sum(t);
+    }
+    if (lane == 0) w[tgt[k]] -= s;
+}
 
-// one row per warp:
-//   FD  y[s0 + r]   = sum_{j <= r} D[r][j] w[s0 + j]
-//   FL  contrib[cb + r] = sum_s L[r][s] y[s0 + s]
-//   BL  tmp[s0 + r] = y[s0 + r] - sum_u L^T[r][u] x[up_u]
-//   BD  x[s0 + r]   = sum_{c >= r} D^T[r][c] tmp[s0 + c]
-template <typename V, int MODE>
-__global__ void __launch_bounds__(256) nd_rows_kernel(NdSolve F, const int2* __restrict__ items, int n,
-                                                      const V* __restrict__ data, const V* in, const V* aux,
-                                                      V* out) {
+// backward, one warp per (front f, row s): x[s0 + s] = D^T[s] . y_S - G^T[s] . x_U
+template <typename V>
+__global__ void __launch_bounds__(256) nd_bwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
+                                                     const V* __restrict__ data, const V* y, V* x) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (wi >= n) return;
     const int2 it = items[wi];
     const int f = it.x, r = it.y;
-    const int nS = F.nS[f], s0 = F.s0[f];
-    const V* row;
-    int c0, len;
-    if (MODE == ND_FD) row = data + F.doff[f] + drow(r), c0 = 0, len = r + 1;
-    else if (MODE == ND_FL) row = data + F.loff[f] + (int64_t)r * r4(nS), c0 = 0, len = nS;
-    else if (MODE == ND_BL) row = data + F.ltoff[f] + (int64_t)r * r4(F.nU[f]), c0 = 0, len = F.nU[f];
-    else row = data + F.dtoff[f] + dtrow(r, nS), c0 = r & ~3, len = nS - c0;
+    const int nS = F.nS[f], nU = F.nU[f], s0 = F.s0[f];
+    const int c0 = r & ~3;
+    const V* drow_ = data + F.dtoff[f] + dtrow(r, nS);
+    const V* vy = y + s0 + c0;
     V s = 0;
-    if (MODE == ND_BL) {
-        const int32_t* up = F.up + F.uoff[f];
 #pragma unroll 4
-        for (int j = lane; j < len; j += 32) s = fma(row[j], in[up[j]], s);
-    } else {
-        const V* v = in + s0 + c0;
+    for (int j = lane; j < nS - c0; j += 32) s = fma(drow_[j], vy[j], s);
+    const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
+    const int32_t* up = F.up + F.uoff[f];
 #pragma unroll 4
-        for (int j = lane; j < len; j += 32) s = fma(row[j], v[j], s);
-    }
+    for (int j = lane; j < nU; j += 32) s = fma(-grow[j], x[up[j]], s);
     s = ddgdev::warp_sum(s);
-    if (lane != 0) return;
-    if (MODE == ND_FL) out[F.cb[f] + r] = s;
-    else if (MODE == ND_BL) out[s0 + r] = aux[s0 + r] - s;
-    else out[s0 + r] = s;
-}
-
-// w[t] -= the level's contributions to target t, in front order
-template <typename V>
-__global__ void nd_fwd_reduce_kernel(const int32_t* __restrict__ tgt, const int64_t* __restrict__ ptr,
-                                     const int64_t* __restrict__ src, int n, const V* contrib, V* w) {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    V s = 0;
-    for (int64_t e = ptr[t]; e < ptr[t + 1]; ++e) s += contrib[src[e]];
-    w[tgt[t]] -= s;
+    if (lane == 0) x[s0 + r] = s;
 }
 
 // dst[p] = src[idx[p]] (into elimination order), or dst[idx[p]] = src[p] (back)
@@ -441,10 +490,9 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         childs[c] = C;
     }
     // solve layout, in elimination order: front f's S dofs are the positions
-    // s0[f] .. s0[f] + nS[f]; per front the rows of D, L_US, D^T and L_US^T
+    // s0[f] .. s0[f] + nS[f]; per front the rows of D, G, D^T and G^T
     std::vector<int32_t> s0(nf, 0), upos, elim(h->n0, 0), pos_of(h->n0, 0);
-    std::vector<int64_t> sdoff(nf + 1, 0), sloff(nf + 1, 0), stoff(nf + 1, 0), sltoff(nf + 1, 0), uoff(nf + 1, 0),
-        cboff(nf + 1, 0);
+    std::vector<int64_t> sdoff(nf + 1, 0), sgoff(nf + 1, 0), stoff(nf + 1, 0), sgtoff(nf + 1, 0), uoff(nf + 1, 0);
     {
         int p = 0;
         for (int f = 0; f < nf; ++f) {
@@ -461,53 +509,55 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     for (int f = 0; f < nf; ++f) {
         sdoff[f] = cur;
         cur += drow(nS[f]);
-        sloff[f] = cur;
+        sgoff[f] = cur;
         cur += (int64_t)nU[f] * r4(nS[f]);
         stoff[f] = cur;
         cur += dtrow(nS[f], nS[f]);
-        sltoff[f] = cur;
+        sgtoff[f] = cur;
         cur += (int64_t)nS[f] * r4(nU[f]);
         for (int v : fr[f].U)
             for (int t = 0; t < rank[v]; ++t) upos.push_back(pos_of[coff[v] + t]);
         uoff[f + 1] = (int64_t)upos.size();
-        cboff[f + 1] = cboff[f] + nU[f];
     }
     N.elems = cur;
-    // fronts by level, deepest first (the forward order)
+    // fronts by level, deepest first (the forward order); per level the
+    // forward items (the fronts' D rows, then one item per target of G w_S)
+    // and the backward items (the fronts' rows)
     std::vector<std::vector<int>> bylevel(nlevel);
     for (int f = 0; f < nf; ++f) bylevel[nlevel - 1 - fr[f].depth].push_back(f);
-    std::vector<int2> srows, urows;
+    std::vector<int2> fitems, bitems, rsrc;
     std::vector<int32_t> rtgt;
-    std::vector<int64_t> rptr{0}, rsrc;
-    N.h_srow_off.assign(nlevel + 1, 0);
-    N.h_urow_off.assign(nlevel + 1, 0);
-    N.h_red_off.assign(nlevel + 1, 0);
+    std::vector<int64_t> rptr{0};
+    N.h_fwd_off.assign(nlevel + 1, 0);
+    N.h_bwd_off.assign(nlevel + 1, 0);
     for (int l = 0; l < nlevel; ++l) {
-        std::unordered_map<int, std::vector<int64_t>> contrib;
+        std::unordered_map<int, std::vector<int2>> contrib;
         std::vector<int> order;
         for (int f : bylevel[l]) {
-            for (int i = 0; i < nS[f]; ++i) srows.push_back(make_int2(f, i));
+            for (int i = 0; i < nS[f]; ++i) {
+                fitems.push_back(make_int2(f, i));
+                bitems.push_back(make_int2(f, i));
+            }
             for (int u = 0; u < nU[f]; ++u) {
-                urows.push_back(make_int2(f, u));
                 const int t = upos[uoff[f] + u];
                 auto it = contrib.find(t);
                 if (it == contrib.end()) {
                     order.push_back(t);
-                    contrib[t] = {cboff[f] + u};
+                    contrib[t] = {make_int2(f, u)};
                 } else {
-                    it->second.push_back(cboff[f] + u);
+                    it->second.push_back(make_int2(f, u));
                 }
             }
         }
         std::sort(order.begin(), order.end());
         for (int t : order) {
+            fitems.push_back(make_int2(-1 - (int)rtgt.size(), 0));
             rtgt.push_back(t);
-            for (int64_t e : contrib[t]) rsrc.push_back(e);
+            for (const int2& e : contrib[t]) rsrc.push_back(e);
             rptr.push_back((int64_t)rsrc.size());
         }
-        N.h_srow_off[l + 1] = (int)srows.size();
-        N.h_urow_off[l + 1] = (int)urows.size();
-        N.h_red_off[l + 1] = (int)rtgt.size();
+        N.h_fwd_off[l + 1] = (int)fitems.size();
+        N.h_bwd_off[l + 1] = (int)bitems.size();
     }
     // device copies of the solve layout
     N.nS = upload(h, nS);
@@ -516,31 +566,30 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     N.up = upload(h, upos.empty() ? std::vector<int32_t>{0} : upos);
     N.uoff = upload(h, uoff);
     N.doff = upload(h, sdoff);
-    N.loff = upload(h, sloff);
+    N.goff = upload(h, sgoff);
     N.dtoff = upload(h, stoff);
-    N.ltoff = upload(h, sltoff);
-    N.cboff = upload(h, cboff);
+    N.gtoff = upload(h, sgtoff);
     N.elim = upload(h, elim.empty() ? std::vector<int32_t>{0} : elim);
-    N.srows = upload(h, srows.empty() ? std::vector<int2>{make_int2(0, 0)} : srows);
-    N.urows = upload(h, urows.empty() ? std::vector<int2>{make_int2(0, 0)} : urows);
+    N.fitems = upload(h, fitems.empty() ? std::vector<int2>{make_int2(0, 0)} : fitems);
+    N.bitems = upload(h, bitems.empty() ? std::vector<int2>{make_int2(0, 0)} : bitems);
     N.rtgt = upload(h, rtgt.empty() ? std::vector<int32_t>{0} : rtgt);
     N.rptr = upload(h, rptr);
-    N.rsrc = upload(h, rsrc.empty() ? std::vector<int64_t>{0} : rsrc);
+    N.rsrc = upload(h, rsrc.empty() ? std::vector<int2>{make_int2(0, 0)} : rsrc);
     N.d64 = h->arena.alloc<double>(N.elems);
     N.d32 = h->arena.alloc<float>(N.elems);
-    N.contrib64 = h->arena.alloc<double>(std::max<int64_t>(1, cboff[nf]));
-    N.contrib32 = h->arena.alloc<float>(std::max<int64_t>(1, cboff[nf]));
     N.w64 = h->arena.alloc<double>(std::max(1, h->n0));
     N.w32 = h->arena.alloc<float>(std::max(1, h->n0));
-    N.t64 = h->arena.alloc<double>(std::max(1, h->n0));
-    N.t32 = h->arena.alloc<float>(std::max(1, h->n0));
     N.x64 = h->arena.alloc<double>(std::max(1, h->n0));
     N.x32 = h->arena.alloc<float>(std::max(1, h->n0));
 
     // ---- numeric factorisation (FP64 workspaces, released at the end)
+    std::vector<int64_t> gwoff(nf + 1, 0);
+    for (int f = 0; f < nf; ++f)
+        gwoff[f + 1] = gwoff[f] + (int64_t)((nU[f] + CT - 1) / CT) * nSt[f] * CT * CT;
     double* fronts = h->arena.alloc<double>(foff[nf]);
     double* dinv = h->arena.alloc<double>(doff[nf]);
     double* W = h->arena.alloc<double>(woff[nf]);
+    double* Gw = h->arena.alloc<double>(std::max<int64_t>(1, gwoff[nf]));
     DDG_CUDA(cudaMemsetAsync(fronts, 0, foff[nf] * sizeof(double), h->stream));
     DDG_CUDA(cudaMemsetAsync(W, 0, woff[nf] * sizeof(double), h->stream));
     std::vector<void*> tmp;
@@ -562,7 +611,7 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     }
     std::vector<NdPack> packs(nf);
     for (int f = 0; f < nf; ++f)
-        packs[f] = NdPack{foff[f], woff[f], sdoff[f], sloff[f], stoff[f], sltoff[f], nS[f], nU[f], nSt[f] * CT};
+        packs[f] = NdPack{foff[f], woff[f], gwoff[f], sdoff[f], sgoff[f], stoff[f], sgtoff[f], nS[f], nU[f], nSt[f]};
     NdChild* dch = upload(h, childs);
     int32_t* dmaps = upload(h, maps.empty() ? std::vector<int32_t>{0} : maps);
     NdPack* dpk = upload(h, packs);
@@ -600,7 +649,19 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         }
         front_factor_batched(h, fronts, (int)fl.size(), NTmax, NSmax, up(bo), up(nts), up(nss), dinv, up(dof2), W,
                              up(wo), h->errflags + E_COARSE_SPD);
-        // D and L_US rows of the level into the solve arrays
+        // G = L_US D of the level's fronts
+        {
+            int gmax = 0;
+            std::vector<int32_t> fls(fl.begin(), fl.end());
+            for (int f : fl) gmax = std::max(gmax, ((nU[f] + CT - 1) / CT) * nSt[f]);
+            if (gmax > 0) {
+                const size_t sm2 = 2 * CT * CLD * sizeof(double);
+                DDG_CUDA(cudaFuncSetAttribute(nd_gprod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+                nd_gprod_kernel<<<dim3(gmax, (unsigned)fl.size()), 256, sm2, h->stream>>>(dpk, up(fls), fronts, W, Gw);
+                DDG_CHECK_LAUNCH();
+            }
+        }
+        // D, G, D^T and G^T rows of the level into the solve arrays
         std::vector<int4> items;
         for (int f : fl) {
             for (int i = 0; i < nS[f]; ++i) {
@@ -612,7 +673,7 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         }
         if (!items.empty()) {
             int4* di = up(items);
-            nd_pack_kernel<<<(unsigned)items.size(), 128, 0, h->stream>>>(dpk, di, fronts, W, N.d64, N.d32);
+            nd_pack_kernel<<<(unsigned)items.size(), 128, 0, h->stream>>>(dpk, di, Gw, W, N.d64, N.d32);
             DDG_CHECK_LAUNCH();
         }
         // the level's workspaces are needed until its launches have run
@@ -625,41 +686,31 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     h->arena.release(fronts);
     h->arena.release(dinv);
     h->arena.release(W);
+    h->arena.release(Gw);
     N.on = true;
 }
 
 template <typename V>
-static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V* w, V* tmp, V* xp, V* contrib) {
+static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V* w, V* xp) {
     const NdCoarse& N = h->nd;
-    const NdSolve F{N.nS, N.nU, N.s0, N.up, N.uoff, N.doff, N.loff, N.dtoff, N.ltoff, N.cboff};
+    const NdSolve F{N.nS, N.nU, N.s0, N.up, N.uoff, N.doff, N.goff, N.dtoff, N.gtoff};
     const int n0 = h->n0;
     const unsigned pb = (unsigned)((n0 + 255) / 256);
     launch_pdl(h, nd_permute_kernel<V, true>, dim3(pb), dim3(256), 0, n0, (const int32_t*)N.elim, c, w);
     // forward, deepest level first; w is updated in place
     for (int l = 0; l < N.nlevel; ++l) {
-        const int a0 = N.h_srow_off[l], a1 = N.h_srow_off[l + 1];
+        const int a0 = N.h_fwd_off[l], a1 = N.h_fwd_off[l + 1];
         if (a1 > a0)
-            launch_pdl(h, nd_rows_kernel<V, ND_FD>, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.srows + a0), a1 - a0, data, (const V*)w, (const V*)nullptr, y);
-        const int b0 = N.h_urow_off[l], b1 = N.h_urow_off[l + 1];
-        if (b1 > b0) {
-            launch_pdl(h, nd_rows_kernel<V, ND_FL>, dim3((unsigned)((b1 - b0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.urows + b0), b1 - b0, data, (const V*)y, (const V*)nullptr, contrib);
-            const int r0 = N.h_red_off[l], r1 = N.h_red_off[l + 1];
-            launch_pdl(h, nd_fwd_reduce_kernel<V>, dim3((unsigned)((r1 - r0 + 255) / 256)), dim3(256), 0,
-                       (const int32_t*)(N.rtgt + r0), (const int64_t*)(N.rptr + r0), (const int64_t*)N.rsrc,
-                       r1 - r0, (const V*)contrib, w);
-        }
+            launch_pdl(h, nd_fwd_kernel<V>, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.fitems + a0), a1 - a0, (const int32_t*)N.rtgt, (const int64_t*)N.rptr,
+                       (const int2*)N.rsrc, data, w, y);
     }
     // backward, root first
     for (int l = N.nlevel - 1; l >= 0; --l) {
-        const int a0 = N.h_srow_off[l], a1 = N.h_srow_off[l + 1];
-        if (a1 <= a0) continue;
-        const dim3 g((unsigned)((a1 - a0 + 7) / 8));
-        launch_pdl(h, nd_rows_kernel<V, ND_BL>, g, dim3(256), 0, F, (const int2*)(N.srows + a0), a1 - a0, data,
-                   (const V*)xp, (const V*)y, tmp);
-        launch_pdl(h, nd_rows_kernel<V, ND_BD>, g, dim3(256), 0, F, (const int2*)(N.srows + a0), a1 - a0, data,
-                   (const V*)tmp, (const V*)nullptr, xp);
+        const int a0 = N.h_bwd_off[l], a1 = N.h_bwd_off[l + 1];
+        if (a1 > a0)
+            launch_pdl(h, nd_bwd_kernel<V>, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.bitems + a0), a1 - a0, data, (const V*)y, xp);
     }
     launch_pdl(h, nd_permute_kernel<V, false>, dim3(pb), dim3(256), 0, n0, (const int32_t*)N.elim, (const V*)xp,
                xout);
@@ -669,18 +720,16 @@ int nd_solve_launches(ddg_handle h) {
     const NdCoarse& N = h->nd;
     int cnt = 2;
     for (int l = 0; l < N.nlevel; ++l) {
-        if (N.h_srow_off[l + 1] > N.h_srow_off[l]) cnt += 3;
-        if (N.h_urow_off[l + 1] > N.h_urow_off[l]) cnt += 2;
+        if (N.h_fwd_off[l + 1] > N.h_fwd_off[l]) ++cnt;
+        if (N.h_bwd_off[l + 1] > N.h_bwd_off[l]) ++cnt;
     }
     return cnt;
 }
 
 void nd_coarse_solve(ddg_handle h, int prec) {
     NdCoarse& N = h->nd;
-    if (prec == DDG_PREC_FP64)
-        nd_solve_t<double>(h, N.d64, h->c64, h->y64, h->x64, N.w64, N.t64, N.x64, N.contrib64);
-    else
-        nd_solve_t<float>(h, N.d32, h->c32, h->y32, h->x32, N.w32, N.t32, N.x32, N.contrib32);
+    if (prec == DDG_PREC_FP64) nd_solve_t<double>(h, N.d64, h->c64, h->y64, h->x64, N.w64, N.x64);
+    else nd_solve_t<float>(h, N.d32, h->c32, h->y32, h->x32, N.w32, N.x32);
 }
 
 }  // namespace ddg
