@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
         const V* row = data + F.doff[f] + drow(i);
         const V* v = w + F.s0[f];
         V s = 0;
-#pragma unroll 4
+#pragma unroll 8
         for (int j = lane; j <= i; j += 32) s = fma(row[j], v[j], s);
         s = ddgdev::warp_sum(s);
         if (lane == 0) y[F.s0[f] + i] = s;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
         const V* row = data + F.goff[f] + (int64_t)fu.y * r4(nS);
         const V* v = w + F.s0[f];
         V t = 0;
-#pragma unroll 4
+#pragma unroll 8
         for (int j = lane; j < nS; j += 32) t = fma(row[j], v[j], t);
         s += ddgdev::warp_sum(t);
     }
@@ -237,11 +237,11 @@ __global__ void __launch_bounds__(256) nd_bwd_kernel(NdSolve F, const int2* __re
     const V* drow_ = data + F.dtoff[f] + dtrow(r, nS);
     const V* vy = y + s0 + c0;
     V s = 0;
-#pragma unroll 4
+#pragma unroll 8
     for (int j = lane; j < nS - c0; j += 32) s = fma(drow_[j], vy[j], s);
     const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
     const int32_t* up = F.up + F.uoff[f];
-#pragma unroll 4
+#pragma unroll 8
     for (int j = lane; j < nU; j += 32) s = fma(-grow[j], x[up[j]], s);
     s = ddgdev::warp_sum(s);
     if (lane == 0) x[s0 + r] = s;
