@@ -22,6 +22,7 @@
 // dot product over contiguous data (only x_U is gathered).  The updates of
 // w are summed per target in a fixed order, so the solve is deterministic.
 #include <algorithm>
+#include <cstdlib>
 #include <deque>
 #include <numeric>
 #include <unordered_map>
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
         const V* row = data + F.doff[f] + drow(i);
         const V* v = w + F.s0[f];
         V s = 0;
-#pragma unroll 8
+#pragma unroll 4
         for (int j = lane; j <= i; j += 32) s = fma(row[j], v[j], s);
         s = ddgdev::warp_sum(s);
         if (lane == 0) y[F.s0[f] + i] = s;
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
         const V* row = data + F.goff[f] + (int64_t)fu.y * r4(nS);
         const V* v = w + F.s0[f];
         V t = 0;
-#pragma unroll 8
+#pragma unroll 4
         for (int j = lane; j < nS; j += 32) t = fma(row[j], v[j], t);
         s += ddgdev::warp_sum(t);
     }
@@ -237,14 +238,129 @@ __global__ void __launch_bounds__(256) nd_bwd_kernel(NdSolve F, const int2* __re
     const V* drow_ = data + F.dtoff[f] + dtrow(r, nS);
     const V* vy = y + s0 + c0;
     V s = 0;
-#pragma unroll 8
+#pragma unroll 4
     for (int j = lane; j < nS - c0; j += 32) s = fma(drow_[j], vy[j], s);
     const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
     const int32_t* up = F.up + F.uoff[f];
-#pragma unroll 8
+#pragma unroll 4
     for (int j = lane; j < nU; j += 32) s = fma(-grow[j], x[up[j]], s);
     s = ddgdev::warp_sum(s);
     if (lane == 0) x[s0 + r] = s;
+}
+
+__device__ __forceinline__ uint64_t nd_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned nd_load_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+struct NdPersist {
+    NdSolve F;
+    const int2 *fitems, *bitems, *rsrc;
+    const int32_t *rtgt, *elim, *fwd_off, *bwd_off;   // level offsets (device, [nlevel + 1])
+    const int64_t* rptr;
+    int n0, nlevel;
+    unsigned* bar;      // grid barrier counter, zero at launch
+    int* err;           // set when a barrier wait runs out
+    uint64_t limit_ns;
+};
+
+// The whole ND solve in one cooperative launch: the permutation, the forward
+// levels, the backward levels and the inverse permutation are phases of a
+// grid-stride loop over the same items as the per-level kernels, separated
+// by grid barriers (a monotone counter; every wait bounded by limit_ns).
+// Vectors written in one phase and read in a later one are read through L2
+// (__ldcg), never from a possibly stale L1 line.
+template <typename V>
+__global__ void __launch_bounds__(256, 4) nd_persistent_kernel(NdPersist P, const V* __restrict__ data, const V* c,
+                                                            V* w, V* y, V* xp, V* xout) {
+    const NdSolve& F = P.F;
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * 8 + (threadIdx.x >> 5), nw = gridDim.x * 8;
+    unsigned phase = 0;
+    auto barrier = [&]() {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(P.bar, 1u);
+            const unsigned target = (phase + 1) * gridDim.x;
+            const uint64_t t0 = nd_ns();
+            for (uint32_t i = 0;; ++i) {
+                if (nd_load_acquire(P.bar) >= target) break;
+                if ((i & 63) == 63 && nd_ns() - t0 > P.limit_ns) {
+                    atomicExch(P.err, 1);
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        ++phase;
+    };
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n0; p += gridDim.x * blockDim.x)
+        w[p] = c[P.elim[p]];
+    barrier();
+    for (int l = 0; l < P.nlevel; ++l) {
+        const int a0 = P.fwd_off[l], a1 = P.fwd_off[l + 1];
+        for (int wi = a0 + gw; wi < a1; wi += nw) {
+            const int2 it = P.fitems[wi];
+            if (it.x >= 0) {
+                const int f = it.x, i = it.y;
+                const V* row = data + F.doff[f] + drow(i);
+                const V* v = w + F.s0[f];
+                V s = 0;
+#pragma unroll 4
+                for (int j = lane; j <= i; j += 32) s = fma(row[j], __ldcg(v + j), s);
+                s = ddgdev::warp_sum(s);
+                if (lane == 0) y[F.s0[f] + i] = s;
+            } else {
+                const int k = -1 - it.x;
+                V s = 0;
+                for (int64_t e = P.rptr[k]; e < P.rptr[k + 1]; ++e) {
+                    const int2 fu = P.rsrc[e];
+                    const int f = fu.x, nS = F.nS[f];
+                    const V* row = data + F.goff[f] + (int64_t)fu.y * r4(nS);
+                    const V* v = w + F.s0[f];
+                    V t = 0;
+#pragma unroll 4
+                    for (int j = lane; j < nS; j += 32) t = fma(row[j], __ldcg(v + j), t);
+                    s += ddgdev::warp_sum(t);
+                }
+                if (lane == 0) w[P.rtgt[k]] = __ldcg(w + P.rtgt[k]) - s;
+            }
+        }
+        barrier();
+    }
+    for (int l = P.nlevel - 1; l >= 0; --l) {
+        const int a0 = P.bwd_off[l], a1 = P.bwd_off[l + 1];
+        for (int wi = a0 + gw; wi < a1; wi += nw) {
+            const int2 it = P.bitems[wi];
+            const int f = it.x, r = it.y;
+            const int nS = F.nS[f], nU = F.nU[f], s0 = F.s0[f];
+            const int c0 = r & ~3;
+            const V* drow_ = data + F.dtoff[f] + dtrow(r, nS);
+            const V* vy = y + s0 + c0;
+            V s = 0;
+#pragma unroll 4
+            for (int j = lane; j < nS - c0; j += 32) s = fma(drow_[j], __ldcg(vy + j), s);
+            const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
+            const int32_t* up = F.up + F.uoff[f];
+#pragma unroll 4
+            for (int j = lane; j < nU; j += 32) s = fma(-grow[j], __ldcg(xp + up[j]), s);
+            s = ddgdev::warp_sum(s);
+            if (lane == 0) xp[s0 + r] = s;
+        }
+        barrier();
+    }
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P.n0; p += gridDim.x * blockDim.x)
+        xout[P.elim[p]] = __ldcg(xp + p);
 }
 
 // dst[p] = src[idx[p]] (into elimination order), or dst[idx[p]] = src[p] (back)
@@ -575,6 +691,9 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     N.rtgt = upload(h, rtgt.empty() ? std::vector<int32_t>{0} : rtgt);
     N.rptr = upload(h, rptr);
     N.rsrc = upload(h, rsrc.empty() ? std::vector<int2>{make_int2(0, 0)} : rsrc);
+    N.fwd_off = upload(h, N.h_fwd_off);
+    N.bwd_off = upload(h, N.h_bwd_off);
+    N.bar = h->arena.alloc<unsigned>(1);
     N.d64 = h->arena.alloc<double>(N.elems);
     N.d32 = h->arena.alloc<float>(N.elems);
     N.w64 = h->arena.alloc<double>(std::max(1, h->n0));
@@ -688,6 +807,24 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     h->arena.release(W);
     h->arena.release(Gw);
     N.on = true;
+    if (const char* ev = std::getenv("DDG_ND_PERSISTENT")) N.persistent = ev[0] != '0';
+}
+
+// grid of the persistent solve: every CTA co-resident (a cooperative launch
+// checks it), at most one CTA per eight items of the widest phase
+template <typename V>
+static int nd_persistent_grid(ddg_handle h) {
+    int dev = 0, sms = 1, per = 0;
+    DDG_CUDA(cudaGetDevice(&dev));
+    DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DDG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, nd_persistent_kernel<V>, 256, 0));
+    const NdCoarse& N = h->nd;
+    int widest = (h->n0 + 255) / 256;
+    for (int l = 0; l < N.nlevel; ++l) {
+        widest = std::max(widest, (N.h_fwd_off[l + 1] - N.h_fwd_off[l] + 7) / 8);
+        widest = std::max(widest, (N.h_bwd_off[l + 1] - N.h_bwd_off[l] + 7) / 8);
+    }
+    return std::max(1, std::min(std::max(1, per) * sms, widest));
 }
 
 template <typename V>
@@ -695,6 +832,22 @@ static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V
     const NdCoarse& N = h->nd;
     const NdSolve F{N.nS, N.nU, N.s0, N.up, N.uoff, N.doff, N.goff, N.dtoff, N.gtoff};
     const int n0 = h->n0;
+    if (N.persistent) {
+        const NdPersist P{F, N.fitems, N.bitems, N.rsrc, N.rtgt, N.elim, N.fwd_off, N.bwd_off, N.rptr, n0,
+                          N.nlevel, N.bar, h->errflags + E_TIMEOUT, (uint64_t)h->wait_ns};
+        DDG_CUDA(cudaMemsetAsync(N.bar, 0, sizeof(unsigned), h->stream));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)nd_persistent_grid<V>(h));
+        cfg.blockDim = dim3(256);
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        DDG_CUDA(cudaLaunchKernelEx(&cfg, nd_persistent_kernel<V>, P, data, c, w, y, xp, xout));
+        return;
+    }
     const unsigned pb = (unsigned)((n0 + 255) / 256);
     launch_pdl(h, nd_permute_kernel<V, true>, dim3(pb), dim3(256), 0, n0, (const int32_t*)N.elim, c, w);
     // forward, deepest level first; w is updated in place
@@ -718,6 +871,7 @@ static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V
 
 int nd_solve_launches(ddg_handle h) {
     const NdCoarse& N = h->nd;
+    if (N.persistent) return 1;
     int cnt = 2;
     for (int l = 0; l < N.nlevel; ++l) {
         if (N.h_fwd_off[l + 1] > N.h_fwd_off[l]) ++cnt;

@@ -132,3 +132,28 @@ def test_nd_reproduces_generators_and_rebuilds_with_new_generators():
     assert_close(nd.coarse_correction(dev(r)).cpu().numpy(), M1.coarse_correction(r), 1e-11)
     nd.set_generators(prob.F)
     _cache.pop("poisson3d_32_box4")
+
+
+def test_persistent_and_per_level_nd_solves_agree():
+    # the ND solve as one cooperative launch (grid barriers between levels)
+    # and as one launch per level and direction: the same products in the
+    # same order, so the same bits
+    import os
+    from paper_1504_00907_gb300 import ddg
+    prob = CASES["poisson3d_32_box4"]()
+    a = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"), coarse_order="nd")
+    os.environ["DDG_ND_PERSISTENT"] = "0"
+    try:
+        b = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"), coarse_order="nd")
+    finally:
+        del os.environ["DDG_ND_PERSISTENT"]
+    r = dev(np.random.default_rng(48).standard_normal(prob.n))
+    for prec in ("fp64", "fp32"):
+        a.set_precision(prec)
+        b.set_precision(prec)
+        assert torch.equal(a.coarse_correction(r), b.coarse_correction(r)), prec
+    ua, ita, _, sta = a.solve(dev(prob.f), tol=1e-8)
+    ub, itb, _, stb = b.solve(dev(prob.f), tol=1e-8)
+    assert sta == stb == 0 and ita == itb and torch.equal(ua, ub)
+    a.close()
+    b.close()
