@@ -253,7 +253,7 @@ struct NdCoarse {
     std::vector<int> h_fwd_off, h_bwd_off;   // [nlevel + 1], levels deepest first
     int32_t *fwd_off = nullptr, *bwd_off = nullptr;   // device copies
     unsigned* bar = nullptr;           // grid barrier of the persistent solve
-    bool persistent = true;            // one cooperative launch (DDG_ND_PERSISTENT=0: one per level)
+    bool persistent = false;           // one cooperative launch (DDG_ND_PERSISTENT=1) or one per level
     double *d64 = nullptr, *w64 = nullptr, *x64 = nullptr;
     float *d32 = nullptr, *w32 = nullptr, *x32 = nullptr;
 };

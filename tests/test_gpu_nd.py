@@ -141,12 +141,12 @@ def test_persistent_and_per_level_nd_solves_agree():
     import os
     from paper_1504_00907_gb300 import ddg
     prob = CASES["poisson3d_32_box4"]()
-    a = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"), coarse_order="nd")
-    os.environ["DDG_ND_PERSISTENT"] = "0"
+    os.environ["DDG_ND_PERSISTENT"] = "1"
     try:
-        b = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"), coarse_order="nd")
+        a = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"), coarse_order="nd")
     finally:
         del os.environ["DDG_ND_PERSISTENT"]
+    b = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"), coarse_order="nd")
     r = dev(np.random.default_rng(48).standard_normal(prob.n))
     for prec in ("fp64", "fp32"):
         a.set_precision(prec)
