@@ -333,8 +333,11 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
     t0 = time.perf_counter()
     tot_seq = 0
     seq_status = []
+    per_problem_ms = []
     for s, f in zip(solvers, rhs):
+        t1 = time.perf_counter()
         _, it, rr, st1 = s.solve(f, TOL)
+        per_problem_ms.append(1e3 * (time.perf_counter() - t1))
         tot_seq += it
         seq_status.append(int(st1))
     torch.cuda.synchronize()
@@ -351,7 +354,9 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
            "sequential_s": seq_s, "concurrent_s": conc_s,
            "dof_iters_per_s_concurrent": world * work / conc_s,
            "dof_iters_per_s_sequential": world * work / seq_s,
-           "speedup_concurrent": seq_s / conc_s, "sequential_status": seq_status}
+           "speedup_concurrent": seq_s / conc_s, "sequential_status": seq_status,
+           "per_problem_sequential_ms": per_problem_ms,
+           "largest_problem_ms": max(per_problem_ms)}
     for s in solvers:
         s.close()
     return res

@@ -181,6 +181,7 @@ struct ProfileMat {         // rows with one contiguous column range each
     double* v64 = nullptr;
     float* v32 = nullptr;
     int64_t nnz = 0;
+    std::vector<int64_t> h_rowptr;   // host copy of rowptr
 };
 
 // Device-side state of a graph-driven batched PCG (per column: its own CG)

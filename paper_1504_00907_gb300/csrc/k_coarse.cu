@@ -500,11 +500,24 @@ constexpr int GEMV_PF = 8;      // 16-byte chunks per thread loaded before the d
 // does not depend on that step, so it is read first; griddepcontrol.wait
 // then orders the reads of x and a after the previous kernel's writes.
 // Without the launch attribute both griddepcontrol instructions are no-ops.
+// pf / pf_bytes: the next step's matrix rows, which every CTA's thread 0
+// hands in equal 16-byte-multiple slices to the L2 prefetcher
+// (cp.async.bulk.prefetch) before it reads its own row, so that the next
+// step of the dependent chain finds its data in L2
 template <typename V, typename MV>
 __global__ void __launch_bounds__(GEMV_TPR) profile_gemv_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-    const MV* __restrict__ vals, int r0, const V* x, const V* a, V sign, V* out) {
+    const MV* __restrict__ vals, int r0, const V* x, const V* a, V sign, V* out, const char* pf,
+    unsigned long long pf_bytes) {
     __shared__ V sh[GEMV_TPR / 32];
+    if (pf && threadIdx.x == 0) {
+        const unsigned long long chunk = ((pf_bytes + gridDim.x - 1) / gridDim.x + 15) & ~15ull;
+        const unsigned long long off = (unsigned long long)blockIdx.x * chunk;
+        if (off < pf_bytes) {
+            const unsigned sz = (unsigned)(chunk < pf_bytes - off ? chunk : pf_bytes - off);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(pf + off), "r"(sz) : "memory");
+        }
+    }
     const int i = r0 + blockIdx.x;
     const int l = lo[i];
     const int nch = (hi[i] - l) >> 2;
@@ -845,6 +858,7 @@ static void alloc_profile(ddg_handle h, ProfileMat& M, const std::vector<int>& l
         rp[i + 1] = rp[i] + (hi4[i] - lo4[i]);
     }
     M.nnz = rp[rows];
+    M.h_rowptr = rp;
     M.rowptr = h->arena.alloc<int64_t>(rows + 1);
     M.lo = h->arena.alloc<int32_t>(rows);
     M.hi = h->arena.alloc<int32_t>(rows);
@@ -947,7 +961,18 @@ void coarse_restrict(ddg_handle h, int prec, bool residual) {
 
 template <typename V>
 static void gemv(ddg_handle h, const ProfileMat& M, int r0, int r1, const V* x, const V* a, V sign,
-                 V* out) {
+                 V* out, const ProfileMat* pfM = nullptr, int pf0 = 0, int pf1 = 0) {
+    // the rows [pf0, pf1) of pfM go to L2 while this step runs (16-byte
+    // multiples: every profile row is a multiple of four values)
+    const char* pf = nullptr;
+    unsigned long long pf_bytes = 0;
+    if (pfM && pf1 > pf0 && !pfM->h_rowptr.empty()) {
+        const size_t es = sizeof(V) == 8 ? 8 : 4;
+        const char* base = sizeof(V) == 8 ? (const char*)pfM->v64 : (const char*)pfM->v32;
+        pf = base + (size_t)pfM->h_rowptr[pf0] * es;
+        pf_bytes = (unsigned long long)(pfM->h_rowptr[pf1] - pfM->h_rowptr[pf0]) * es;
+        if (pf_bytes == 0) pf = nullptr;
+    }
     if (r1 <= r0) return;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(r1 - r0));
@@ -961,24 +986,31 @@ static void gemv(ddg_handle h, const ProfileMat& M, int r0, int r1, const V* x, 
     if (sizeof(V) == 8)
         DDG_CUDA(cudaLaunchKernelEx(&cfg, profile_gemv_kernel<double, double>, (const int64_t*)M.rowptr,
                                     (const int32_t*)M.lo, (const int32_t*)M.hi, (const double*)M.v64, r0,
-                                    (const double*)x, (const double*)a, (double)sign, (double*)out));
+                                    (const double*)x, (const double*)a, (double)sign, (double*)out, pf,
+                                    pf_bytes));
     else
         DDG_CUDA(cudaLaunchKernelEx(&cfg, profile_gemv_kernel<float, float>, (const int64_t*)M.rowptr,
                                     (const int32_t*)M.lo, (const int32_t*)M.hi, (const float*)M.v32, r0,
-                                    (const float*)x, (const float*)a, (float)sign, (float*)out));
+                                    (const float*)x, (const float*)a, (float)sign, (float*)out, pf,
+                                    pf_bytes));
 }
 
 // y = L^{-1} c and x = L^{-T} y on the block-bidiagonal factor:
 //   y = D c (all super-blocks at once), then y_K -= F_K y_{K-1} for K = 1, 2, ...
 //   x = D^T y, then x_K -= G_K x_{K+1} for K = nK-2, ..., 0
 // 2 nK launches, of which 2 (nK - 1) form the dependent chain
+// Each step of the two chains prefetches the next step's block of F or G
+// into L2 (and the block-diagonal steps the chain's first block), so the
+// chain reads from L2 while HBM streams the block after it.
 template <typename V>
 static void coarse_solve_t(ddg_handle h, V* c, V* y, V* x) {
     const int B = h->B, nK = h->nK, n0p = h->n0p;
-    gemv<V>(h, h->Dm, 0, n0p, c, nullptr, (V)1, y);
-    for (int K = 1; K < nK; ++K) gemv<V>(h, h->Fm, K * B, (K + 1) * B, y, y, (V)-1, y);
-    gemv<V>(h, h->Dt, 0, n0p, y, nullptr, (V)1, x);
-    for (int K = nK - 2; K >= 0; --K) gemv<V>(h, h->Gm, K * B, (K + 1) * B, x, x, (V)-1, x);
+    gemv<V>(h, h->Dm, 0, n0p, c, nullptr, (V)1, y, &h->Fm, B, std::min(2, nK) * B);
+    for (int K = 1; K < nK; ++K)
+        gemv<V>(h, h->Fm, K * B, (K + 1) * B, y, y, (V)-1, y, &h->Fm, (K + 1) * B, std::min(K + 2, nK) * B);
+    gemv<V>(h, h->Dt, 0, n0p, y, nullptr, (V)1, x, &h->Gm, std::max(0, nK - 2) * B, std::max(0, nK - 1) * B);
+    for (int K = nK - 2; K >= 0; --K)
+        gemv<V>(h, h->Gm, K * B, (K + 1) * B, x, x, (V)-1, x, &h->Gm, std::max(0, K - 1) * B, K * B);
 }
 
 void coarse_solve(ddg_handle h, int prec) {
