@@ -58,6 +58,8 @@ def parse():
                     help="grid of the multi-RHS arm (0 skips it)")
     ap.add_argument("--batched-m", type=int, default=64)
     ap.add_argument("--uneven", type=int, default=1, help="run the uneven 24-problem arm (0 skips it)")
+    ap.add_argument("--uneven-order", default="nd", choices=["band", "nd"],
+                    help="coarse factor ordering of the uneven arm's problems")
     ap.add_argument("--elasticity-size", type=int, default=64,
                     help="elements per side of the Q1 elasticity arm (0 skips it)")
     ap.add_argument("--elasticity-steps", type=int, default=3)
@@ -72,6 +74,9 @@ def parse():
                     help="arm with shared inverses of identical local matrices (0 skips it)")
     ap.add_argument("--nd", type=int, default=1,
                     help="arm with the nested-dissection coarse factor on the headline problem (0 skips it)")
+    ap.add_argument("--scale-size", type=int, default=0,
+                    help="optional arm: the headline problem family at N^3 (e.g. 256: 16.8 M dofs, coarse "
+                         "dimension 327680) with the band and the nested-dissection coarse factors (0 skips it)")
     ap.add_argument("--vcycle-group", type=int, default=4,
                     help="three-level arm: subdomains per axis of a coarse-level subdomain (0 skips it)")
     ap.add_argument("--keep", default="fp64,fp32,bf16",
@@ -312,7 +317,8 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
     biharmonic (256^2 x3, 512^2 x3, 1024^2 x2, 16^2 boxes + overlap 2, p <= 3),
     f ~ U(-1, 1) from seed 100 + index, FP32 preconditioner, FP64 CG, tol 1e-8;
     one after another on one stream, then all at once (ddg_solve_many: one
-    CUDA graph whose branches are the 24 whole solves, one launch)."""
+    CUDA graph whose branches are the 24 whole solves, one launch).  The
+    coarse factor of every problem is ordered by args.uneven_order."""
     probs = []
     for i, N in enumerate([32, 48, 64, 80] * 4):
         probs.append(di.make_poisson3d(N=N, box=8, overlap=1, p=2, seed=100 + i))
@@ -320,7 +326,8 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
         probs.append(di.make_biharmonic2d(N=N, box=16, overlap=2, p=3, seed=116 + i))
     streams = [torch.cuda.Stream(device=dev) for _ in probs]
     t0 = time.perf_counter()
-    solvers = [ddg.Solver.from_problem(p, precision="fp32", keep=("fp32",), stream=s.cuda_stream, autotune=True)
+    solvers = [ddg.Solver.from_problem(p, precision="fp32", keep=("fp32",), stream=s.cuda_stream, autotune=True,
+                                       coarse_order=args.uneven_order)
                for p, s in zip(probs, streams)]
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -349,7 +356,7 @@ def uneven_arm(args, ddg, di, torch, dev, barrier, max_over_ranks, world):
     conc_s = max_over_ranks(time.perf_counter() - t0)
     work = sum(p.n * int(i) for p, i in zip(probs, its))
     res = {"workload": "16 x 3D Poisson (32..80)^3 + 8 x 2D biharmonic 256^2..1024^2",
-           "problems": len(probs), "dofs_total": dofs, "setup_s": setup_s,
+           "problems": len(probs), "dofs_total": dofs, "setup_s": setup_s, "coarse_order": args.uneven_order,
            "status": int(st), "iters": [int(i) for i in its], "max_true_relres": float(rrs.max()),
            "sequential_s": seq_s, "concurrent_s": conc_s,
            "dof_iters_per_s_concurrent": world * work / conc_s,
@@ -466,6 +473,49 @@ def safe_condition_estimate(solver):
         return solver.condition_estimate(TOL)
     except ddg.DDGError:
         return None, None, None
+
+
+def scale_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world):
+    """The headline problem family at N^3 (8^3 boxes + overlap 1, p <= 2, FP32
+    preconditioner, tol 1e-8) with the natural-order band and with the
+    nested-dissection coarse factor, one handle after the other: setup,
+    solve time, iterations and the coarse share of one event-timed solve."""
+    N = args.scale_size
+    prob = di.make_poisson3d(N=N, box=WORKLOAD["box"], overlap=WORKLOAD["overlap"], p=WORKLOAD["p"],
+                             seed=WORKLOAD["seed"])
+    f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    u = torch.empty_like(f)
+    out = {"workload": f"poisson3d_{N}^3: 8^3 boxes + overlap 1, p<=2, FP32 preconditioner, tol 1e-8",
+           "dofs": prob.n}
+    for order in ("nd", "band"):
+        t0 = time.perf_counter()
+        s = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32",), coarse_order=order)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        s.solve(f, TOL, u)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [s.solve(f, TOL, u) for _ in range(3)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / 3)
+        s.profile(ddg.KERNEL_CLASSES)
+        s.solve(f, TOL, u)
+        torch.cuda.synchronize()
+        ks = s.kernel_stats()
+        s.profile(())
+        inf = s.info()
+        s.close()
+        out[order] = {"setup_s": setup_s, "ms": ms, "iters": res[-1][1], "true_relres": res[-1][2],
+                      "status": int(res[-1][3]), "coarse_dim": inf["n0"], "coarse_elems": inf["coarse_elems"],
+                      "coarse_levels": inf["coarse_levels"],
+                      "coarse_ms_one_solve": ks["coarse"]["ms"], "local_solve_ms_one_solve": ks["local_solve"]["ms"],
+                      "dof_iters_per_s": world * prob.n * res[-1][1] / (ms / 1e3)}
+        del s
+        torch.cuda.empty_cache()
+    return out
 
 
 def fractional_iters(hist, tol):
@@ -910,6 +960,10 @@ def main():
     if args.materials_size > 0:
         materials = materials_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
 
+    scale = None
+    if args.scale_size > 0:
+        scale = scale_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
+
     elasticity = None
     if args.elasticity_size > 0:
         elasticity = elasticity_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, world)
@@ -945,6 +999,7 @@ def main():
         "stopping_variants": stopping,
         "dedup_local_constant_coefficient": dedup,
         "nested_dissection_coarse": nd,
+        "coarse_orders_at_scale": scale,
         "batched": batched,
         "uneven_batch": uneven,
         "elasticity_differentiation": elasticity,

@@ -1164,7 +1164,7 @@ bool solve_many_graph(ddg_handle* hs, int nprob, const double* const* F, double*
             (const void*)F[p] == (const void*)U[p])
             return false;
         if (m[p] > 1 && (m[p] > DDG_MCHUNK || h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 ||
-                         h->bl.on || h->nd.on))
+                         h->bl.on))
             return false;
     }
     DeviceScope scope(hs[0]->device);
@@ -2380,7 +2380,7 @@ ddg_status ddg_solve_batch(ddg_handle h, const double* F, double* U, int m, doub
         DDG_REQUIRE(F && U && m >= 1, DDG_EINVAL, "F, U must be non-null and m >= 1");
         DDG_REQUIRE(tol > 0.0, DDG_EINVAL, "tol must be > 0");
         ddg_status worst = DDG_OK;
-        if (h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 || h->bl.on || h->nd.on) {
+        if (h->precision == DDG_PREC_FP64 || h->inner || h->kmax > 32 || h->bl.on) {
             // the FP64 and the V-cycle preconditioners, and coarse spaces of
             // more than 32 generators per subdomain, run one column at a time
             for (int j = 0; j < m; ++j) {

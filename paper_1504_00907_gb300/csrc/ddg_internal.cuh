@@ -208,6 +208,7 @@ struct MultiWork {
     std::vector<int> h_citem_off;
     float* gpart = nullptr;       // split partials of the coarse GEMMs
     unsigned* gtick = nullptr;    // one ticket per 32-row tile
+    float *ndw = nullptr, *ndx = nullptr;   // nested-dissection coarse solve: vectors in elimination order
     int gen = 0;                  // bumped when the workspace is reallocated
     MultiCtl* ctl = nullptr;      // graph-driven batched solves
     MultiCtl* h_ctl = nullptr;    // pinned
@@ -489,6 +490,7 @@ double* coarse_assemble_blocks_device(ddg_handle h, const std::vector<int>& blk_
 // k_nd.cu: nested-dissection coarse factor and its solve
 void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector<int>& bJ, const double* blocks);
 void nd_coarse_solve(ddg_handle h, int prec);
+void nd_coarse_solve_multi(ddg_handle h, int m, const float* c, float* y, float* x, float* w, float* xp);
 int nd_solve_launches(ddg_handle h);
 void coarse_restrict(ddg_handle h, int prec, bool residual);
 void coarse_solve(ddg_handle h, int prec);

@@ -913,8 +913,9 @@ void multi_ensure(ddg_handle h, int m) {
                     (void*)w.r32, (void*)w.z32,
                     (void*)w.res32, (void*)w.c32, (void*)w.y32, (void*)w.x32,
                     (void*)w.scal, (void*)w.partials, (void*)w.active, (void*)w.restart,
-                    (void*)w.items, (void*)w.gpart, (void*)w.gtick})
+                    (void*)w.items, (void*)w.gpart, (void*)w.gtick, (void*)w.ndw, (void*)w.ndx})
         if (p) h->arena.release(p);
+    w.ndw = w.ndx = nullptr;
     const int64_t n = h->n;
     w.R = h->arena.alloc<double>(n * m);
     w.P = h->arena.alloc<double>(n * m);
@@ -931,7 +932,10 @@ void multi_ensure(ddg_handle h, int m) {
     w.x32 = h->arena.alloc<float>(n0p * m);
     for (float* p : {w.c32, w.y32, w.x32})
         DDG_CUDA(cudaMemsetAsync(p, 0, n0p * m * sizeof(float), h->stream));
-    if (h->use_coarse) {
+    if (h->use_coarse && h->nd.on) {
+        w.ndw = h->arena.alloc<float>((size_t)h->n0 * m);
+        w.ndx = h->arena.alloc<float>((size_t)h->n0 * m);
+    } else if (h->use_coarse) {
         const int nsplit = (h->B + CG_KS - 1) / CG_KS;
         // a step covers at most all n0p rows (the block-diagonal D launches)
         w.gpart = h->arena.alloc<float>((size_t)nsplit * h->n0p * m);
@@ -1024,7 +1028,7 @@ static void multi_apply_t(ddg_handle h, int m) {
     };
     for (int c = 0; c < h->ncol; ++c) local(c, c == 0);
     if (h->use_coarse) {
-        ProfScope ps(h, DDG_K_COARSE, 2 + 2 * h->nK, 0.0);
+        ProfScope ps(h, DDG_K_COARSE, 2 + (h->nd.on ? nd_solve_launches(h) : 2 * h->nK), 0.0);
         const int bd = col_block(m);
         const size_t smem = (size_t)(bd / m) * h->kmax * m * sizeof(float);
 #define RESTRICT_MULTI(KM)                                                                              \
@@ -1045,6 +1049,9 @@ static void multi_apply_t(ddg_handle h, int m) {
 #undef RESTRICT_MULTI4
         const int B = h->B, nK = h->nK;
         const int nsplit = (B + CG_KS - 1) / CG_KS;
+        if (h->nd.on) {
+            nd_coarse_solve_multi(h, m, w.c32, w.y32, w.x32, w.ndw, w.ndx);
+        } else {
         // rows [r0, r0 + rows); cbase < 0: each row's own super-block
         auto step = [&](const ProfileMat& M, int r0, int rows, int cbase, const float* x, const float* a,
                         float sign, float* out) {
@@ -1075,6 +1082,7 @@ static void multi_apply_t(ddg_handle h, int m) {
         for (int K = 1; K < nK; ++K) step(h->Fm, K * B, B, (K - 1) * B, w.y32, w.y32, -1.f, w.y32);
         step(h->Dt, 0, n0p, -1, w.y32, nullptr, 1.f, w.x32);
         for (int K = nK - 2; K >= 0; --K) step(h->Gm, K * B, B, (K + 1) * B, w.x32, w.x32, -1.f, w.x32);
+        }
         if (vec4)
             coarse_prolong_multi4_kernel<<<(unsigned)((n * (m / 4) + 255) / 256), 256, 0, h->stream>>>(
                 n, m, h->part, h->pos, h->Q32, h->kmax, h->coff, w.x32, w.z32);

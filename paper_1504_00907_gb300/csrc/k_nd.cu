@@ -363,6 +363,99 @@ __global__ void __launch_bounds__(256, 4) nd_persistent_kernel(NdPersist P, cons
         xout[P.elim[p]] = __ldcg(xp + p);
 }
 
+// ---- the same solve for m right-hand sides (FP32, dof-major n0 x m,
+// m <= 64): one warp per row, lane c for the columns c and c + 32 (the row's
+// entries are read once per warp and broadcast)
+static_assert(DDG_MCHUNK <= 64, "the multi-column ND kernels give each lane two columns");
+
+__device__ __forceinline__ void nd_row_multi(const float* row, int len, const float* v, int m, int lane,
+                                             float (&acc)[2]) {
+    for (int j = 0; j < len; ++j) {
+        const float a = row[j];
+        const float* vj = v + (int64_t)j * m;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = lane + 32 * u;
+            if (c < m) acc[u] = fmaf(a, vj[c], acc[u]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) nd_fwd_multi_kernel(NdSolve F, const int2* __restrict__ items, int n,
+                                                           const int32_t* __restrict__ tgt,
+                                                           const int64_t* __restrict__ ptr,
+                                                           const int2* __restrict__ src,
+                                                           const float* __restrict__ data, float* w, float* y,
+                                                           int m) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (wi >= n) return;
+    const int2 it = items[wi];
+    float acc[2] = {0.f, 0.f};
+    if (it.x >= 0) {
+        const int f = it.x, i = it.y;
+        nd_row_multi(data + F.doff[f] + drow(i), i + 1, w + (int64_t)F.s0[f] * m, m, lane, acc);
+        float* out = y + (int64_t)(F.s0[f] + i) * m;
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (lane + 32 * u < m) out[lane + 32 * u] = acc[u];
+        return;
+    }
+    const int k = -1 - it.x;
+    for (int64_t e = ptr[k]; e < ptr[k + 1]; ++e) {
+        const int2 fu = src[e];
+        const int f = fu.x, nS = F.nS[f];
+        nd_row_multi(data + F.goff[f] + (int64_t)fu.y * r4(nS), nS, w + (int64_t)F.s0[f] * m, m, lane, acc);
+    }
+    float* out = w + (int64_t)tgt[k] * m;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (lane + 32 * u < m) out[lane + 32 * u] -= acc[u];
+}
+
+__global__ void __launch_bounds__(256) nd_bwd_multi_kernel(NdSolve F, const int2* __restrict__ items, int n,
+                                                           const float* __restrict__ data, const float* y, float* x,
+                                                           int m) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (wi >= n) return;
+    const int2 it = items[wi];
+    const int f = it.x, r = it.y;
+    const int nS = F.nS[f], nU = F.nU[f], s0 = F.s0[f];
+    const int c0 = r & ~3;
+    float acc[2] = {0.f, 0.f};
+    nd_row_multi(data + F.dtoff[f] + dtrow(r, nS), nS - c0, y + (int64_t)(s0 + c0) * m, m, lane, acc);
+    const float* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
+    const int32_t* up = F.up + F.uoff[f];
+    for (int j = 0; j < nU; ++j) {
+        const float a = grow[j];
+        const float* xj = x + (int64_t)up[j] * m;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = lane + 32 * u;
+            if (c < m) acc[u] = fmaf(-a, xj[c], acc[u]);
+        }
+    }
+    float* out = x + (int64_t)(s0 + r) * m;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (lane + 32 * u < m) out[lane + 32 * u] = acc[u];
+}
+
+template <bool GATHER>
+__global__ void nd_permute_multi_kernel(int64_t total, int m, const int32_t* __restrict__ idx, const float* src,
+                                        float* dst) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int64_t p = e / m, c = e - p * m;
+    if (GATHER) dst[e] = src[(int64_t)idx[p] * m + c];
+    else dst[(int64_t)idx[p] * m + c] = src[e];
+}
+
 // dst[p] = src[idx[p]] (into elimination order), or dst[idx[p]] = src[p] (back)
 template <typename V, bool GATHER>
 __global__ void nd_permute_kernel(int n, const int32_t* __restrict__ idx, const V* src, V* dst) {
@@ -882,6 +975,31 @@ int nd_solve_launches(ddg_handle h) {
         if (N.h_bwd_off[l + 1] > N.h_bwd_off[l]) ++cnt;
     }
     return cnt;
+}
+
+// m right-hand sides: c, y, x as the batched path's coarse vectors (n0 x m,
+// dof-major), w and xp work vectors of the same size in elimination order
+void nd_coarse_solve_multi(ddg_handle h, int m, const float* c, float* y, float* x, float* w, float* xp) {
+    const NdCoarse& N = h->nd;
+    const NdSolve F{N.nS, N.nU, N.s0, N.up, N.uoff, N.doff, N.goff, N.dtoff, N.gtoff};
+    const int64_t total = (int64_t)h->n0 * m;
+    const unsigned pb = (unsigned)((total + 255) / 256);
+    launch_pdl(h, nd_permute_multi_kernel<true>, dim3(pb), dim3(256), 0, total, m, (const int32_t*)N.elim, c, w);
+    for (int l = 0; l < N.nlevel; ++l) {
+        const int a0 = N.h_fwd_off[l], a1 = N.h_fwd_off[l + 1];
+        if (a1 > a0)
+            launch_pdl(h, nd_fwd_multi_kernel, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.fitems + a0), a1 - a0, (const int32_t*)N.rtgt, (const int64_t*)N.rptr,
+                       (const int2*)N.rsrc, (const float*)N.d32, w, y, m);
+    }
+    for (int l = N.nlevel - 1; l >= 0; --l) {
+        const int a0 = N.h_bwd_off[l], a1 = N.h_bwd_off[l + 1];
+        if (a1 > a0)
+            launch_pdl(h, nd_bwd_multi_kernel, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
+                       (const int2*)(N.bitems + a0), a1 - a0, (const float*)N.d32, (const float*)y, xp, m);
+    }
+    launch_pdl(h, nd_permute_multi_kernel<false>, dim3(pb), dim3(256), 0, total, m, (const int32_t*)N.elim,
+               (const float*)xp, x);
 }
 
 void nd_coarse_solve(ddg_handle h, int prec) {
