@@ -129,8 +129,9 @@ typedef struct {
                              uses the FP32 factors, tensor_cores and dedup_local are not
                              available, ddg_solve_batch solves its columns one at a time,
                              and the half-bandwidth must be at most 1024 */
-    int coarse_order;     /* DDG_COARSE_*, default BAND.  With ND, ddg_solve_batch solves
-                             its columns one at a time */
+    int coarse_order;     /* DDG_COARSE_*, default ND (the nested-dissection factor is
+                             smaller and its solve shorter than the natural-order band
+                             on the grids measured; BAND keeps the natural order) */
 } ddg_options;
 
 typedef struct {

@@ -1335,6 +1335,7 @@ void ddg_default_options(ddg_options* o) {
     o->rank_tol = 1e-10;
     o->chunk_tiles = 0;
     o->spin_budget_ms = 1000.0;
+    o->coarse_order = DDG_COARSE_ND;
 }
 
 }  // extern "C"

@@ -209,6 +209,7 @@ struct MultiWork {
     float* gpart = nullptr;       // split partials of the coarse GEMMs
     unsigned* gtick = nullptr;    // one ticket per 32-row tile
     float *ndw = nullptr, *ndx = nullptr;   // nested-dissection coarse solve: vectors in elimination order
+    float* ndp = nullptr;                   // and its partial G rows
     int gen = 0;                  // bumped when the workspace is reallocated
     MultiCtl* ctl = nullptr;      // graph-driven batched solves
     MultiCtl* h_ctl = nullptr;    // pinned
@@ -253,6 +254,15 @@ struct NdCoarse {
     int64_t* rptr = nullptr;
     int2* rsrc = nullptr;              // (front, G row) pairs per target, in a fixed order
     std::vector<int> h_fwd_off, h_bwd_off;   // [nlevel + 1], levels deepest first
+    // multi-column solve: 32-row tiles (front, first row, D or G) forward and
+    // (front, first row) backward, targets per level, partial-row index of
+    // every listed (front, G row) pair, total G rows
+    int4* mfitems = nullptr;
+    int2* mbitems = nullptr;
+    int64_t* rsrcp = nullptr;
+    std::vector<int> h_mf_off, h_mb_off, h_tgt_off;
+    std::vector<int> h_mf_ks, h_mb_ks;   // CTAs per tile (one cluster) per level
+    int64_t urows = 0;
     int32_t *fwd_off = nullptr, *bwd_off = nullptr;   // device copies
     unsigned* bar = nullptr;           // grid barrier of the persistent solve
     bool persistent = false;           // one cooperative launch (DDG_ND_PERSISTENT=1) or one per level
@@ -490,7 +500,8 @@ double* coarse_assemble_blocks_device(ddg_handle h, const std::vector<int>& blk_
 // k_nd.cu: nested-dissection coarse factor and its solve
 void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector<int>& bJ, const double* blocks);
 void nd_coarse_solve(ddg_handle h, int prec);
-void nd_coarse_solve_multi(ddg_handle h, int m, const float* c, float* y, float* x, float* w, float* xp);
+int nd_solve_multi_launches(ddg_handle h);
+void nd_coarse_solve_multi(ddg_handle h, int m, const float* c, float* y, float* x, float* w, float* xp, float* P);
 int nd_solve_launches(ddg_handle h);
 void coarse_restrict(ddg_handle h, int prec, bool residual);
 void coarse_solve(ddg_handle h, int prec);

@@ -913,9 +913,9 @@ void multi_ensure(ddg_handle h, int m) {
                     (void*)w.r32, (void*)w.z32,
                     (void*)w.res32, (void*)w.c32, (void*)w.y32, (void*)w.x32,
                     (void*)w.scal, (void*)w.partials, (void*)w.active, (void*)w.restart,
-                    (void*)w.items, (void*)w.gpart, (void*)w.gtick, (void*)w.ndw, (void*)w.ndx})
+                    (void*)w.items, (void*)w.gpart, (void*)w.gtick, (void*)w.ndw, (void*)w.ndx, (void*)w.ndp})
         if (p) h->arena.release(p);
-    w.ndw = w.ndx = nullptr;
+    w.ndw = w.ndx = w.ndp = nullptr;
     const int64_t n = h->n;
     w.R = h->arena.alloc<double>(n * m);
     w.P = h->arena.alloc<double>(n * m);
@@ -935,6 +935,7 @@ void multi_ensure(ddg_handle h, int m) {
     if (h->use_coarse && h->nd.on) {
         w.ndw = h->arena.alloc<float>((size_t)h->n0 * m);
         w.ndx = h->arena.alloc<float>((size_t)h->n0 * m);
+        w.ndp = h->arena.alloc<float>((size_t)std::max<int64_t>(1, h->nd.urows) * m);
     } else if (h->use_coarse) {
         const int nsplit = (h->B + CG_KS - 1) / CG_KS;
         // a step covers at most all n0p rows (the block-diagonal D launches)
@@ -1028,7 +1029,7 @@ static void multi_apply_t(ddg_handle h, int m) {
     };
     for (int c = 0; c < h->ncol; ++c) local(c, c == 0);
     if (h->use_coarse) {
-        ProfScope ps(h, DDG_K_COARSE, 2 + (h->nd.on ? nd_solve_launches(h) : 2 * h->nK), 0.0);
+        ProfScope ps(h, DDG_K_COARSE, 2 + (h->nd.on ? nd_solve_multi_launches(h) : 2 * h->nK), 0.0);
         const int bd = col_block(m);
         const size_t smem = (size_t)(bd / m) * h->kmax * m * sizeof(float);
 #define RESTRICT_MULTI(KM)                                                                              \
@@ -1050,7 +1051,7 @@ static void multi_apply_t(ddg_handle h, int m) {
         const int B = h->B, nK = h->nK;
         const int nsplit = (B + CG_KS - 1) / CG_KS;
         if (h->nd.on) {
-            nd_coarse_solve_multi(h, m, w.c32, w.y32, w.x32, w.ndw, w.ndx);
+            nd_coarse_solve_multi(h, m, w.c32, w.y32, w.x32, w.ndw, w.ndx, w.ndp);
         } else {
         // rows [r0, r0 + rows); cbase < 0: each row's own super-block
         auto step = [&](const ProfileMat& M, int r0, int rows, int cbase, const float* x, const float* a,

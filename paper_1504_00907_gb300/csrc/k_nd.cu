@@ -364,49 +364,222 @@ __global__ void __launch_bounds__(256, 4) nd_persistent_kernel(NdPersist P, cons
 }
 
 // ---- the same solve for m right-hand sides (FP32, dof-major n0 x m,
-// m <= 64): one warp per row, lane c for the columns c and c + 32 (the row's
-// entries are read once per warp and broadcast)
-static_assert(DDG_MCHUNK <= 64, "the multi-column ND kernels give each lane two columns");
+// m <= 64).  Every front product is a small dense matrix product with m
+// columns, so a CTA takes a 32-row tile of one front's D, G, D^T or G^T and
+// runs over K in 128-wide stages (A stage 32 x 128, vector stage 128 x m)
+// copied into shared memory with cp.async, two stages in flight; each
+// thread keeps 2 rows x 4 adjacent columns.  Where a level has few tiles, a
+// cluster of KS CTAs splits each tile's stages and CTA 0 of the cluster sums
+// the partial tiles from the others' shared memory in rank order.  The
+// forward G products of a level go to per-front partial rows P (nU x m per
+// front), which a second launch sums in the same fixed order as the
+// one-column solve and subtracts from their targets.
+static_assert(DDG_MCHUNK <= 64, "the multi-column ND tiles hold at most 64 columns");
+constexpr int NDT = 32;                                 // rows per tile
+constexpr int NDK = 128;                                // K per stage
+constexpr int ND_LDA = NDK + 4;                         // A stage row stride (16-byte rows)
+constexpr int ND_AS = NDT * ND_LDA;
+constexpr int ND_STAGE = ND_AS + NDK * 64;              // floats per stage
+constexpr size_t ND_TILE_SMEM = 2 * ND_STAGE * sizeof(float);
+constexpr int ND_MAX_KS = 8;                            // CTAs per cluster (portable limit)
 
-__device__ __forceinline__ void nd_row_multi(const float* row, int len, const float* v, int m, int lane,
-                                             float (&acc)[2]) {
-    for (int j = 0; j < len; ++j) {
-        const float a = row[j];
-        const float* vj = v + (int64_t)j * m;
+struct NdTileAcc {
+    float a[2][4];
+};
+
+// asynchronous copies global -> shared; a null source fills zeros
+__device__ __forceinline__ void nd_cp16(float* dst, const float* src, const float* dummy) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src ? src : dummy),
+                 "r"(src ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void nd_cp4(float* dst, const float* src, const float* dummy) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src ? src : dummy), "r"(src ? 4 : 0)
+                 : "memory");
+}
+
+// acc += A[., k] B[k, :] over the stages [st0, st1) of the K range starting
+// at kbeg (stage t covers kbeg + t NDK .. + NDK, cut at kend).
+// aptr(rr, c): address of the 4 entries A(r0 + rr, c .. c + 3) (c a
+// multiple of 4; rows are stored zero-padded to multiples of 4) or null for
+// zeros; brow(k): row k of B (m floats, 16-byte aligned when m % 4 == 0).
+template <class AP, class BR>
+__device__ __forceinline__ void nd_tile_run(int kbeg, int kend, int st0, int st1, int m, AP aptr, BR brow,
+                                            float* smem, const float* dummy, NdTileAcc& acc) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const bool vec = (m & 3) == 0;
+    auto issue = [&](int buf, int k0) {
+        float* As = smem + buf * ND_STAGE;
+        float* Bs = As + ND_AS;
+        for (int e = tid; e < NDT * NDK / 4; e += 256) {
+            const int rr = e / (NDK / 4), c = k0 + 4 * (e - rr * (NDK / 4));
+            nd_cp16(As + rr * ND_LDA + (c - k0), c < kend ? aptr(rr, c) : nullptr, dummy);
+        }
+        if (vec) {
+            const int m4 = m >> 2;
+            for (int e = tid; e < NDK * m4; e += 256) {
+                const int kk = e / m4, col = 4 * (e - kk * m4), k = k0 + kk;
+                nd_cp16(Bs + kk * 64 + col, k < kend ? brow(k) + col : nullptr, dummy);
+            }
+        } else {
+            for (int e = tid; e < NDK * m; e += 256) {
+                const int kk = e / m, col = e - kk * m, k = k0 + kk;
+                nd_cp4(Bs + kk * 64 + col, k < kend ? brow(k) + col : nullptr, dummy);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (st1 > st0) issue(st0 & 1, kbeg + st0 * NDK);
+    for (int st = st0; st < st1; ++st) {
+        if (st + 1 < st1) {
+            issue((st + 1) & 1, kbeg + (st + 1) * NDK);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float* As = smem + (st & 1) * ND_STAGE;
+        const float* Bs = As + ND_AS;
+#pragma unroll 4
+        for (int kk = 0; kk < NDK; kk += 4) {
+            const float4 a0 = *reinterpret_cast<const float4*>(As + ty * ND_LDA + kk);
+            const float4 a1 = *reinterpret_cast<const float4*>(As + (ty + 16) * ND_LDA + kk);
+            const float av0[4] = {a0.x, a0.y, a0.z, a0.w}, av1[4] = {a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int c = lane + 32 * u;
-            if (c < m) acc[u] = fmaf(a, vj[c], acc[u]);
+            for (int q = 0; q < 4; ++q) {
+                const float4 b = *reinterpret_cast<const float4*>(Bs + (kk + q) * 64 + 4 * tx);
+                const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc.a[0][j] = fmaf(av0[q], bv[j], acc.a[0][j]);
+                    acc.a[1][j] = fmaf(av1[q], bv[j], acc.a[1][j]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ unsigned nd_cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned nd_cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void nd_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float nd_ld_remote(const float* local, unsigned rank) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(local), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(r) : "memory");
+    return v;
+}
+
+// the stages [st0, st1) of n that cluster CTA q of ks takes
+__device__ __forceinline__ void nd_split(int n, int q, int ks, int& st0, int& st1) {
+    const int per = (n + ks - 1) / ks;
+    st0 = min(n, q * per);
+    st1 = min(n, st0 + per);
+}
+
+// sums the cluster's partial tiles into CTA 0 (rank order); returns false
+// on the other CTAs, which then have nothing to store
+__device__ __forceinline__ bool nd_cluster_reduce(NdTileAcc* t, int nt, float* smem) {
+    const unsigned ks = nd_cluster_size();
+    if (ks == 1) return true;
+    const unsigned q = nd_cluster_rank();
+    const int tid = threadIdx.x;
+    for (int u = 0; u < nt; ++u)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) smem[(u * 8 + i * 4 + j) * 256 + tid] = t[u].a[i][j];
+    nd_cluster_sync();
+    if (q == 0) {
+        for (unsigned p = 1; p < ks; ++p)
+            for (int u = 0; u < nt; ++u)
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) t[u].a[i][j] += nd_ld_remote(smem + (u * 8 + i * 4 + j) * 256 + tid, p);
+    }
+    nd_cluster_sync();   // the other CTAs keep their shared memory until CTA 0 has read it
+    return q == 0;
+}
+
+__device__ __forceinline__ void nd_store_tile(const NdTileAcc& acc, const NdTileAcc* sub, float* out, int r0,
+                                              int nrow, int m) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int r = r0 + ty + 16 * i;
+        if (r >= nrow) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * tx + j;
+            if (c < m) out[(int64_t)r * m + c] = sub ? acc.a[i][j] - sub->a[i][j] : acc.a[i][j];
         }
     }
 }
 
-__global__ void __launch_bounds__(256) nd_fwd_multi_kernel(NdSolve F, const int2* __restrict__ items, int n,
-                                                           const int32_t* __restrict__ tgt,
-                                                           const int64_t* __restrict__ ptr,
-                                                           const int2* __restrict__ src,
-                                                           const float* __restrict__ data, float* w, float* y,
-                                                           int m) {
+// forward tile (f, r0, kind): kind 0 gives rows r0.. of y_S = D w_S, kind 1
+// rows r0.. of the partial product P_f = G_f w_S; a cluster of KS CTAs per
+// tile (grid = tiles x KS)
+__global__ void __launch_bounds__(256) nd_fwd_tile_kernel(NdSolve F, const int4* __restrict__ items,
+                                                          const float* __restrict__ data, const float* w, float* y,
+                                                          float* P, int m) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    extern __shared__ __align__(16) float nd_smem[];
+    const int ks = (int)nd_cluster_size();
+    const int4 it = items[blockIdx.x / ks];
+    const int f = it.x, r0 = it.y, kind = it.z;
+    const int nS = F.nS[f], s0 = F.s0[f];
+    const int nrow = kind == 0 ? nS : F.nU[f];
+    const int kend = kind == 0 ? min(r0 + NDT, nS) : nS;
+    const float* base = data + (kind == 0 ? F.doff[f] : F.goff[f]);
+    const float* W = w + (int64_t)s0 * m;
+    const int ld = r4(nS);
+    auto aptr = [&](int rr, int c) -> const float* {
+        const int r = r0 + rr;
+        if (kind == 0) return (r < nS && c <= r) ? base + drow(r) + c : nullptr;
+        return r < nrow ? base + (int64_t)r * ld + c : nullptr;
+    };
+    auto brow = [&](int k) { return W + (int64_t)k * m; };
+    NdTileAcc acc = {};
+    int st0, st1;
+    nd_split((kend + NDK - 1) / NDK, (int)nd_cluster_rank(), ks, st0, st1);
+    nd_tile_run(0, kend, st0, st1, m, aptr, brow, nd_smem, data, acc);
+    if (!nd_cluster_reduce(&acc, 1, nd_smem)) return;
+    float* out = kind == 0 ? y + (int64_t)s0 * m : P + F.uoff[f] * m;
+    nd_store_tile(acc, nullptr, out, r0, nrow, m);
+}
+
+// one warp per target k of the level: w[tgt_k] -= the sum over its partial
+// rows, in the listed order
+__global__ void __launch_bounds__(256) nd_fwd_reduce_kernel(const int32_t* __restrict__ tgt,
+                                                            const int64_t* __restrict__ ptr,
+                                                            const int64_t* __restrict__ srcp, int t0, int nt,
+                                                            const float* __restrict__ P, float* w, int m) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (wi >= n) return;
-    const int2 it = items[wi];
+    if (wi >= nt) return;
+    const int k = t0 + wi;
     float acc[2] = {0.f, 0.f};
-    if (it.x >= 0) {
-        const int f = it.x, i = it.y;
-        nd_row_multi(data + F.doff[f] + drow(i), i + 1, w + (int64_t)F.s0[f] * m, m, lane, acc);
-        float* out = y + (int64_t)(F.s0[f] + i) * m;
+    for (int64_t e = ptr[k]; e < ptr[k + 1]; ++e) {
+        const float* p = P + srcp[e] * m;
 #pragma unroll
         for (int u = 0; u < 2; ++u)
-            if (lane + 32 * u < m) out[lane + 32 * u] = acc[u];
-        return;
-    }
-    const int k = -1 - it.x;
-    for (int64_t e = ptr[k]; e < ptr[k + 1]; ++e) {
-        const int2 fu = src[e];
-        const int f = fu.x, nS = F.nS[f];
-        nd_row_multi(data + F.goff[f] + (int64_t)fu.y * r4(nS), nS, w + (int64_t)F.s0[f] * m, m, lane, acc);
+            if (lane + 32 * u < m) acc[u] += p[lane + 32 * u];
     }
     float* out = w + (int64_t)tgt[k] * m;
 #pragma unroll
@@ -414,34 +587,41 @@ __global__ void __launch_bounds__(256) nd_fwd_multi_kernel(NdSolve F, const int2
         if (lane + 32 * u < m) out[lane + 32 * u] -= acc[u];
 }
 
-__global__ void __launch_bounds__(256) nd_bwd_multi_kernel(NdSolve F, const int2* __restrict__ items, int n,
-                                                           const float* __restrict__ data, const float* y, float* x,
-                                                           int m) {
+// backward tile (f, r0): rows r0.. of x_S = D^T y_S - G^T x_U (x_U gathered
+// from the ancestors' rows, already solved); the D^T and G^T stages form
+// one sequence that a cluster of KS CTAs splits
+__global__ void __launch_bounds__(256) nd_bwd_tile_kernel(NdSolve F, const int2* __restrict__ items,
+                                                          const float* __restrict__ data, const float* y, float* x,
+                                                          int m) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (wi >= n) return;
-    const int2 it = items[wi];
-    const int f = it.x, r = it.y;
+    extern __shared__ __align__(16) float nd_smem[];
+    const int ks = (int)nd_cluster_size();
+    const int2 it = items[blockIdx.x / ks];
+    const int f = it.x, r0 = it.y;
     const int nS = F.nS[f], nU = F.nU[f], s0 = F.s0[f];
-    const int c0 = r & ~3;
-    float acc[2] = {0.f, 0.f};
-    nd_row_multi(data + F.dtoff[f] + dtrow(r, nS), nS - c0, y + (int64_t)(s0 + c0) * m, m, lane, acc);
-    const float* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
+    const float* dt = data + F.dtoff[f];
+    const float* gt = data + F.gtoff[f];
     const int32_t* up = F.up + F.uoff[f];
-    for (int j = 0; j < nU; ++j) {
-        const float a = grow[j];
-        const float* xj = x + (int64_t)up[j] * m;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int c = lane + 32 * u;
-            if (c < m) acc[u] = fmaf(-a, xj[c], acc[u]);
-        }
-    }
-    float* out = x + (int64_t)(s0 + r) * m;
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-        if (lane + 32 * u < m) out[lane + 32 * u] = acc[u];
+    const int ldu = r4(nU);
+    NdTileAcc t[2] = {};   // D^T y_S and G^T x_U
+    const int n1 = (nS - r0 + NDK - 1) / NDK, n2 = (nU + NDK - 1) / NDK;
+    int a, b;
+    nd_split(n1 + n2, (int)nd_cluster_rank(), ks, a, b);
+    auto dptr = [&](int rr, int c) -> const float* {
+        const int r = r0 + rr;
+        return (r < nS && c >= (r & ~3)) ? dt + dtrow(r, nS) + (c - (r & ~3)) : nullptr;
+    };
+    auto yrow = [&](int k) { return y + (int64_t)(s0 + k) * m; };
+    nd_tile_run(r0, nS, min(a, n1), min(b, n1), m, dptr, yrow, nd_smem, data, t[0]);
+    auto gptr = [&](int rr, int c) -> const float* {
+        const int r = r0 + rr;
+        return r < nS ? gt + (int64_t)r * ldu + c : nullptr;
+    };
+    auto xrow = [&](int k) { return x + (int64_t)up[k] * m; };
+    nd_tile_run(0, nU, max(a, n1) - n1, max(b, n1) - n1, m, gptr, xrow, nd_smem, data, t[1]);
+    if (!nd_cluster_reduce(t, 2, nd_smem)) return;
+    nd_store_tile(t[0], &t[1], x + (int64_t)s0 * m, r0, nS, m);
 }
 
 template <bool GATHER>
@@ -734,11 +914,15 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     // and the backward items (the fronts' rows)
     std::vector<std::vector<int>> bylevel(nlevel);
     for (int f = 0; f < nf; ++f) bylevel[nlevel - 1 - fr[f].depth].push_back(f);
-    std::vector<int2> fitems, bitems, rsrc;
+    std::vector<int2> fitems, bitems, rsrc, mbitems;
+    std::vector<int4> mfitems;
     std::vector<int32_t> rtgt;
-    std::vector<int64_t> rptr{0};
+    std::vector<int64_t> rptr{0}, rsrcp;
     N.h_fwd_off.assign(nlevel + 1, 0);
     N.h_bwd_off.assign(nlevel + 1, 0);
+    N.h_mf_off.assign(nlevel + 1, 0);
+    N.h_mb_off.assign(nlevel + 1, 0);
+    N.h_tgt_off.assign(nlevel + 1, 0);
     for (int l = 0; l < nlevel; ++l) {
         std::unordered_map<int, std::vector<int2>> contrib;
         std::vector<int> order;
@@ -747,6 +931,12 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
                 fitems.push_back(make_int2(f, i));
                 bitems.push_back(make_int2(f, i));
             }
+            // multi-column tiles of 32 rows: D and G forward, D^T / G^T backward
+            for (int i = 0; i < nS[f]; i += NDT) {
+                mfitems.push_back(make_int4(f, i, 0, 0));
+                mbitems.push_back(make_int2(f, i));
+            }
+            for (int u = 0; u < nU[f]; u += NDT) mfitems.push_back(make_int4(f, u, 1, 0));
             for (int u = 0; u < nU[f]; ++u) {
                 const int t = upos[uoff[f] + u];
                 auto it = contrib.find(t);
@@ -762,11 +952,47 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         for (int t : order) {
             fitems.push_back(make_int2(-1 - (int)rtgt.size(), 0));
             rtgt.push_back(t);
-            for (const int2& e : contrib[t]) rsrc.push_back(e);
+            for (const int2& e : contrib[t]) {
+                rsrc.push_back(e);
+                rsrcp.push_back(uoff[e.x] + e.y);
+            }
             rptr.push_back((int64_t)rsrc.size());
         }
         N.h_fwd_off[l + 1] = (int)fitems.size();
         N.h_bwd_off[l + 1] = (int)bitems.size();
+        N.h_mf_off[l + 1] = (int)mfitems.size();
+        N.h_mb_off[l + 1] = (int)mbitems.size();
+        N.h_tgt_off[l + 1] = (int)rtgt.size();
+    }
+    N.urows = uoff[nf];
+    // cluster size per level of the multi-column solve: split the stages of
+    // each tile over up to 8 CTAs while the level has fewer tiles than two
+    // per SM (the CTAs of a cluster take at most the tile's stage count)
+    {
+        int dev = 0, sms = 0;
+        DDG_CUDA(cudaGetDevice(&dev));
+        DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        auto pick = [&](int ntiles, int maxst) {
+            int ks = 1;
+            while (ks * 2 <= ND_MAX_KS && ks * 2 <= maxst && ntiles * ks * 2 <= 2 * sms) ks *= 2;
+            return ks;
+        };
+        N.h_mf_ks.assign(nlevel, 1);
+        N.h_mb_ks.assign(nlevel, 1);
+        for (int l = 0; l < nlevel; ++l) {
+            int mf = 0, mb = 0;
+            for (int e = N.h_mf_off[l]; e < N.h_mf_off[l + 1]; ++e) {
+                const int4 t = mfitems[e];
+                const int kend = t.z == 0 ? std::min(t.y + NDT, nS[t.x]) : nS[t.x];
+                mf = std::max(mf, (kend + NDK - 1) / NDK);
+            }
+            for (int e = N.h_mb_off[l]; e < N.h_mb_off[l + 1]; ++e) {
+                const int2 t = mbitems[e];
+                mb = std::max(mb, (nS[t.x] - t.y + NDK - 1) / NDK + (nU[t.x] + NDK - 1) / NDK);
+            }
+            N.h_mf_ks[l] = pick(N.h_mf_off[l + 1] - N.h_mf_off[l], mf);
+            N.h_mb_ks[l] = pick(N.h_mb_off[l + 1] - N.h_mb_off[l], mb);
+        }
     }
     // device copies of the solve layout
     N.nS = upload(h, nS);
@@ -784,6 +1010,9 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     N.rtgt = upload(h, rtgt.empty() ? std::vector<int32_t>{0} : rtgt);
     N.rptr = upload(h, rptr);
     N.rsrc = upload(h, rsrc.empty() ? std::vector<int2>{make_int2(0, 0)} : rsrc);
+    N.rsrcp = upload(h, rsrcp.empty() ? std::vector<int64_t>{0} : rsrcp);
+    N.mfitems = upload(h, mfitems.empty() ? std::vector<int4>{make_int4(0, 0, 0, 0)} : mfitems);
+    N.mbitems = upload(h, mbitems.empty() ? std::vector<int2>{make_int2(0, 0)} : mbitems);
     N.fwd_off = upload(h, N.h_fwd_off);
     N.bwd_off = upload(h, N.h_bwd_off);
     N.bar = h->arena.alloc<unsigned>(1);
@@ -977,26 +1206,71 @@ int nd_solve_launches(ddg_handle h) {
     return cnt;
 }
 
-// m right-hand sides: c, y, x as the batched path's coarse vectors (n0 x m,
-// dof-major), w and xp work vectors of the same size in elimination order
-void nd_coarse_solve_multi(ddg_handle h, int m, const float* c, float* y, float* x, float* w, float* xp) {
+// a tile kernel over ntiles tiles, ks CTAs (one cluster) per tile
+template <typename... KArgs, typename... Args>
+static void launch_cluster(ddg_handle h, void (*kern)(KArgs...), int ks, int ntiles, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ntiles * ks));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = ND_TILE_SMEM;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = h->use_pdl ? 1 : 0;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = (unsigned)ks;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    DDG_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
+
+int nd_solve_multi_launches(ddg_handle h) {
     const NdCoarse& N = h->nd;
+    int cnt = 2;
+    for (int l = 0; l < N.nlevel; ++l) {
+        if (N.h_mf_off[l + 1] > N.h_mf_off[l]) ++cnt;
+        if (N.h_tgt_off[l + 1] > N.h_tgt_off[l]) ++cnt;
+        if (N.h_mb_off[l + 1] > N.h_mb_off[l]) ++cnt;
+    }
+    return cnt;
+}
+
+// m right-hand sides: c, y, x as the batched path's coarse vectors (n0 x m,
+// dof-major), w and xp work vectors of the same size in elimination order,
+// P the partial rows (sum of the fronts' nU) x m
+void nd_coarse_solve_multi(ddg_handle h, int m, const float* c, float* y, float* x, float* w, float* xp, float* P) {
+    const NdCoarse& N = h->nd;
+    static PerDeviceMax configured;   // the shared-memory attribute is per device
+    int dev = -1;
+    if (configured.needs((int)ND_TILE_SMEM, dev)) {
+        DDG_CUDA(cudaFuncSetAttribute(nd_fwd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)ND_TILE_SMEM));
+        DDG_CUDA(cudaFuncSetAttribute(nd_bwd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)ND_TILE_SMEM));
+        configured.commit(dev, (int)ND_TILE_SMEM);
+    }
     const NdSolve F{N.nS, N.nU, N.s0, N.up, N.uoff, N.doff, N.goff, N.dtoff, N.gtoff};
     const int64_t total = (int64_t)h->n0 * m;
     const unsigned pb = (unsigned)((total + 255) / 256);
     launch_pdl(h, nd_permute_multi_kernel<true>, dim3(pb), dim3(256), 0, total, m, (const int32_t*)N.elim, c, w);
     for (int l = 0; l < N.nlevel; ++l) {
-        const int a0 = N.h_fwd_off[l], a1 = N.h_fwd_off[l + 1];
+        const int a0 = N.h_mf_off[l], a1 = N.h_mf_off[l + 1];
         if (a1 > a0)
-            launch_pdl(h, nd_fwd_multi_kernel, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.fitems + a0), a1 - a0, (const int32_t*)N.rtgt, (const int64_t*)N.rptr,
-                       (const int2*)N.rsrc, (const float*)N.d32, w, y, m);
+            launch_cluster(h, nd_fwd_tile_kernel, N.h_mf_ks[l], a1 - a0, F, (const int4*)(N.mfitems + a0),
+                           (const float*)N.d32, (const float*)w, y, P, m);
+        const int t0 = N.h_tgt_off[l], t1 = N.h_tgt_off[l + 1];
+        if (t1 > t0)
+            launch_pdl(h, nd_fwd_reduce_kernel, dim3((unsigned)((t1 - t0 + 7) / 8)), dim3(256), 0,
+                       (const int32_t*)N.rtgt, (const int64_t*)N.rptr, (const int64_t*)N.rsrcp, t0, t1 - t0,
+                       (const float*)P, w, m);
     }
     for (int l = N.nlevel - 1; l >= 0; --l) {
-        const int a0 = N.h_bwd_off[l], a1 = N.h_bwd_off[l + 1];
+        const int a0 = N.h_mb_off[l], a1 = N.h_mb_off[l + 1];
         if (a1 > a0)
-            launch_pdl(h, nd_bwd_multi_kernel, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.bitems + a0), a1 - a0, (const float*)N.d32, (const float*)y, xp, m);
+            launch_cluster(h, nd_bwd_tile_kernel, N.h_mb_ks[l], a1 - a0, F, (const int2*)(N.mbitems + a0),
+                           (const float*)N.d32, (const float*)y, xp, m);
     }
     launch_pdl(h, nd_permute_multi_kernel<false>, dim3(pb), dim3(256), 0, total, m, (const int32_t*)N.elim,
                (const float*)xp, x);

@@ -187,7 +187,7 @@ class Solver:
                  coef=None, dofs_per_node=1, precision="fp64", keep=None, beta="auto",
                  maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
                  stream=None, coarse_groups=None, dedup_local=False, spin_budget_ms=1000.0,
-                 autotune=False, local_repr="auto", coarse_order="band"):
+                 autotune=False, local_repr="auto", coarse_order="nd"):
         import torch
         lib = load()
         if not torch.cuda.is_available():

@@ -64,6 +64,7 @@ def test_defaults_and_status_strings(lib):
     o = ddg.default_options()
     assert (o.precision, o.maxit, o.use_coarse, o.rank_tol) == (0, 1000, 1, 1e-10)
     assert o.spin_budget_ms == 1000.0
+    assert o.coarse_order == ddg.COARSE["nd"]
     assert lib.ddg_status_string(ddg.DDG_ENOTSPD) == b"DDG_ENOTSPD"
 
 

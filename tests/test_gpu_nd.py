@@ -1,4 +1,5 @@
-"""Nested-dissection coarse factor (coarse_order ND) against the oracle.
+"""The two orderings of the exact coarse factor against the oracle: nested
+dissection (coarse_order ND, the default) and the natural-order band.
 
 The exact coarse solve A0^{-1} of Sec. 4 runs through a multifrontal
 Cholesky factor of A0 ordered by nested dissection of the subdomain graph
@@ -44,17 +45,18 @@ def tol64(name, floor):
 
 
 _cache = {}
+ORDERS = ("nd", "band")
 
 
-def setup(name):
-    if name not in _cache:
+def setup(name, order="nd"):
+    if (name, order) not in _cache:
         from paper_1504_00907_gb300 import ddg
         prob = CASES[name]()
-        nd = ddg.Solver.from_problem(prob, precision="fp64", keep=("fp64", "fp32"), coarse_order="nd")
+        s = ddg.Solver.from_problem(prob, precision="fp64", keep=("fp64", "fp32"), coarse_order=order)
         oracle = orc.DDGOracle(prob.A, prob.part, prob.F, prob.overlap, prob.overlap_mode, prob.shape,
                                dpn=prob.dofs_per_node)
-        _cache[name] = (prob, nd, oracle)
-    return _cache[name]
+        _cache[(name, order)] = (prob, s, oracle)
+    return _cache[(name, order)]
 
 
 def dev(x):
@@ -65,20 +67,29 @@ def rhs(prob):
     return prob.f if prob.f.ndim == 1 else prob.f[:, 0]
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_nd_structure(name):
-    prob, nd, oracle = setup(name)
+def test_coarse_structure(name, order):
+    prob, nd, oracle = setup(name, order)
     info = nd.info()
-    assert info["coarse_order"] == 1 and info["n0"] == oracle.A0.shape[0]
-    assert info["coarse_fronts"] >= 1 and info["coarse_levels"] >= 1
-    if name == "poisson3d_32_box4":
-        assert info["coarse_levels"] >= 3
+    assert info["n0"] == oracle.A0.shape[0]
+    if order == "nd":
+        assert info["coarse_order"] == 1
+        assert info["coarse_fronts"] >= 1 and info["coarse_levels"] >= 1
+        if name == "poisson3d_32_box4":
+            assert info["coarse_levels"] >= 3
+        # the default options take the ND ordering
+        from paper_1504_00907_gb300 import ddg
+        assert ddg.default_options().coarse_order == 1
+    else:
+        assert info["coarse_order"] == 0 and info["coarse_fronts"] == 0
     np.testing.assert_array_equal(nd.coarse_offsets(), oracle.coarse_offsets)
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_nd_coarse_correction_matches_oracle(name):
-    prob, nd, oracle = setup(name)
+def test_coarse_correction_matches_oracle(name, order):
+    prob, nd, oracle = setup(name, order)
     nd.set_precision("fp64")
     r = np.random.default_rng(45).standard_normal(prob.n)
     z = nd.coarse_correction(dev(r)).cpu().numpy()
@@ -88,9 +99,10 @@ def test_nd_coarse_correction_matches_oracle(name):
     assert np.array_equal(z, z2)
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name", list(CASES))
-def test_nd_preconditioner_and_solve_match_oracle(name):
-    prob, nd, oracle = setup(name)
+def test_preconditioner_and_solve_match_oracle(name, order):
+    prob, nd, oracle = setup(name, order)
     nd.set_precision("fp64")
     r = np.random.default_rng(46).standard_normal(prob.n)
     assert_close(nd.apply(dev(r)).cpu().numpy(), oracle.apply(r), tol64(name, 1e-11))
@@ -101,9 +113,10 @@ def test_nd_preconditioner_and_solve_match_oracle(name):
     assert_close(u.cpu().numpy(), ref.u, tol64(name, 1e-10))
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name", ["poisson3d_32_box4", "biharmonic_128_box16", "elasticity_q1_12"])
-def test_nd_mixed_solve_matches_oracle(name):
-    prob, nd, oracle = setup(name)
+def test_mixed_solve_matches_oracle(name, order):
+    prob, nd, oracle = setup(name, order)
     f = rhs(prob)
     ref = orc.pcg(oracle.A, f, oracle.apply, tol=1e-8)
     nd.set_precision("fp32")
@@ -131,7 +144,7 @@ def test_nd_reproduces_generators_and_rebuilds_with_new_generators():
     r = np.random.default_rng(47).standard_normal(prob.n)
     assert_close(nd.coarse_correction(dev(r)).cpu().numpy(), M1.coarse_correction(r), 1e-11)
     nd.set_generators(prob.F)
-    _cache.pop("poisson3d_32_box4")
+    _cache.pop(("poisson3d_32_box4", "nd"))
 
 
 def test_persistent_and_per_level_nd_solves_agree():
@@ -159,13 +172,14 @@ def test_persistent_and_per_level_nd_solves_agree():
     b.close()
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("name,m", [("poisson3d_32_box4", 8), ("biharmonic_128_box16", 5),
                                     ("elasticity_q1_12", 64), ("poisson3d_graph_rankdrop", 33)])
-def test_nd_batched_solve_matches_oracle_per_column(name, m):
-    # the batched FP32 preconditioner runs the ND coarse solve on all m
-    # columns at once (dof-major n0 x m vectors); m = 5 and 33 take the
-    # scalar restriction, m = 64 fills both column halves of every lane
-    prob, nd, oracle = setup(name)
+def test_batched_solve_matches_oracle_per_column(name, m, order):
+    # the batched FP32 preconditioner runs the coarse solve on all m columns
+    # at once (dof-major n0 x m vectors); m = 5 and 33 take the scalar
+    # restriction, m = 64 fills both column halves of every ND lane
+    prob, nd, oracle = setup(name, order)
     F = di.normal_rhs(prob.n, 60 + m, m)
     nd.set_precision("fp32")
     U, its, rrs, st = nd.solve_batch(dev(F), tol=1e-8)
