@@ -79,6 +79,9 @@ def parse():
                          "dimension 327680) with the band and the nested-dissection coarse factors (0 skips it)")
     ap.add_argument("--vcycle-group", type=int, default=4,
                     help="three-level arm: subdomains per axis of a coarse-level subdomain (0 skips it)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="headline handle with the default local-solve configuration (for profiler captures, "
+                         "whose timings would steer the tuner)")
     ap.add_argument("--keep", default="fp64,fp32,bf16",
                     help="local-inverse precisions kept at setup (profiling runs keep fewer)")
     return ap.parse_args()
@@ -757,7 +760,7 @@ def main():
     n = prob.n
     t_setup = time.perf_counter()
     keep = tuple(args.keep.split(","))
-    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=keep, autotune=True)
+    solver = ddg.Solver.from_problem(prob, precision="fp32", keep=keep, autotune=not args.no_autotune)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     info = solver.info()

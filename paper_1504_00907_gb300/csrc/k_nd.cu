@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256, 4) nd_persistent_kernel(NdPersist P, cons
 // ---- the same solve for m right-hand sides (FP32, dof-major n0 x m,
 // m <= 64).  Every front product is a small dense matrix product with m
 // columns, so a CTA takes a 32-row tile of one front's D, G, D^T or G^T and
-// runs over K in 128-wide stages (A stage 32 x 128, vector stage 128 x m)
+// runs over K in 64-wide stages (A stage 32 x 64, vector stage 64 x m)
 // copied into shared memory with cp.async, two stages in flight; each
 // thread keeps 2 rows x 4 adjacent columns.  Where a level has few tiles, a
 // cluster of KS CTAs splits each tile's stages and CTA 0 of the cluster sums
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(256, 4) nd_persistent_kernel(NdPersist P, cons
 // one-column solve and subtracts from their targets.
 static_assert(DDG_MCHUNK <= 64, "the multi-column ND tiles hold at most 64 columns");
 constexpr int NDT = 32;                                 // rows per tile
-constexpr int NDK = 128;                                // K per stage
+constexpr int NDK = 64;                                 // K per stage
 constexpr int ND_LDA = NDK + 4;                         // A stage row stride (16-byte rows)
 constexpr int ND_AS = NDT * ND_LDA;
 constexpr int ND_STAGE = ND_AS + NDK * 64;              // floats per stage
@@ -966,7 +966,7 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
     }
     N.urows = uoff[nf];
     // cluster size per level of the multi-column solve: split the stages of
-    // each tile over up to 8 CTAs while the level has fewer tiles than two
+    // each tile over up to 8 CTAs while the level has fewer tiles than four
     // per SM (the CTAs of a cluster take at most the tile's stage count)
     {
         int dev = 0, sms = 0;
@@ -974,7 +974,7 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         auto pick = [&](int ntiles, int maxst) {
             int ks = 1;
-            while (ks * 2 <= ND_MAX_KS && ks * 2 <= maxst && ntiles * ks * 2 <= 2 * sms) ks *= 2;
+            while (ks * 2 <= ND_MAX_KS && ks * 2 <= maxst && ntiles * ks * 2 <= 4 * sms) ks *= 2;
             return ks;
         };
         N.h_mf_ks.assign(nlevel, 1);
