@@ -588,64 +588,78 @@ __global__ void __launch_bounds__(MT) coarse_restrict_multi_kernel(
 // Coarse GEMMs of the batched path: (32-row tile, CG_KS-column split) items
 constexpr int CG_ROWS = 32, CG_KS = 128;
 
-// c = R0 (r - A z) for m % 4 == 0 and kmax <= KM <= 16: a CTA of RT4 threads
-// per subdomain, m/4 threads per row each owning 4 columns; the row slots'
-// float4 accumulators are added into shared memory one slot after another
-// (fixed order)
-constexpr int RT4 = 128;
-template <int SK, int KM>
-__global__ void __launch_bounds__(RT4) coarse_restrict_multi4_kernel(
+// c = R0 (r - A z) for m % 4 == 0 and kmax <= 32: a CTA of RS_T threads per
+// subdomain walks its rows in chunks of RS_ROWS.  The chunk's rows of
+// w = r - A z (m/4 threads per row, four columns each, up to four rows in
+// flight per thread) and its rows of Q go to shared memory; then every
+// thread adds, over the chunk's rows in order, the products for its
+// (generator, 4-column) outputs (at most 2 per thread).
+constexpr int RS_T = 256, RS_ROWS = 64;
+template <int SK>
+__global__ void __launch_bounds__(RS_T) coarse_restrict_stage4_kernel(
     const int64_t* __restrict__ sub_off, const int32_t* __restrict__ sub_nodes,
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
     const float* __restrict__ r, const float* __restrict__ z, const float* __restrict__ Q, int kmax,
     const int32_t* __restrict__ coff, float* __restrict__ cvec, int m, int nx, int ny, int nz) {
-    extern __shared__ __align__(16) float shr[];   // [kmax][m]
-    const int s = blockIdx.x;
-    const int q4 = m >> 2, rp = RT4 / q4;
-    const int cq = threadIdx.x % q4, gq = threadIdx.x / q4;
-    const bool lane_on = gq < rp;
-    float4 acc[KM];
-#pragma unroll
-    for (int jj = 0; jj < KM; ++jj) acc[jj] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __shared__ __align__(16) float sw[RS_ROWS * DDG_MCHUNK];
+    __shared__ float sq[RS_ROWS * 32];
+    const int s = blockIdx.x, tid = threadIdx.x;
+    const int q4 = m >> 2, slots = RS_T / q4;
+    const int cq = tid % q4, rs = tid / q4;
+    const int nout = kmax * q4;
+    float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
     const int64_t b0 = sub_off[s], b1 = sub_off[s + 1];
-    if (lane_on) {
-        for (int64_t a = b0 + gq; a < b1; a += rp) {
-            const int g = sub_nodes[a];
-            const float4 rv = *reinterpret_cast<const float4*>(r + (int64_t)g * m + 4 * cq);
-            const float4 az = apply_row4<SK>(g, 4 * cq, m, rowptr, col, val, z, nx, ny, nz);
-            const float4 w = make_float4(rv.x - az.x, rv.y - az.y, rv.z - az.z, rv.w - az.w);
-            const float* qa = Q + a * kmax;
+    for (int64_t a0 = b0; a0 < b1; a0 += RS_ROWS) {
+        const int rows = (int)min((int64_t)RS_ROWS, b1 - a0);
+        if (rs < slots)
+            for (int i0 = rs; i0 < RS_ROWS; i0 += 4 * slots) {
+                float4 wv[4];
 #pragma unroll
-            for (int jj = 0; jj < KM; ++jj)
-                if (jj < kmax) {
-                    const float qv = qa[jj];
-                    acc[jj].x = fma(qv, w.x, acc[jj].x);
-                    acc[jj].y = fma(qv, w.y, acc[jj].y);
-                    acc[jj].z = fma(qv, w.z, acc[jj].z);
-                    acc[jj].w = fma(qv, w.w, acc[jj].w);
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * slots;
+                    if (i < rows) {
+                        const int g = sub_nodes[a0 + i];
+                        const float4 rv = *reinterpret_cast<const float4*>(r + (int64_t)g * m + 4 * cq);
+                        const float4 az = apply_row4<SK>(g, 4 * cq, m, rowptr, col, val, z, nx, ny, nz);
+                        wv[u] = make_float4(rv.x - az.x, rv.y - az.y, rv.z - az.z, rv.w - az.w);
+                    }
                 }
-        }
-    }
-    for (int e = threadIdx.x; e < kmax * m; e += RT4) shr[e] = 0.f;
-    for (int slot = 0; slot < rp; ++slot) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * slots;
+                    if (i < rows) *reinterpret_cast<float4*>(sw + i * m + 4 * cq) = wv[u];
+                }
+            }
+        for (int e = tid; e < rows * kmax; e += RS_T) sq[e] = Q[a0 * kmax + e];
         __syncthreads();
-        if (gq == slot) {
 #pragma unroll
-            for (int jj = 0; jj < KM; ++jj)
-                if (jj < kmax) {
-                    float4* d = reinterpret_cast<float4*>(shr + jj * m + 4 * cq);
-                    float4 v = *d;
-                    v.x += acc[jj].x;
-                    v.y += acc[jj].y;
-                    v.z += acc[jj].z;
-                    v.w += acc[jj].w;
-                    *d = v;
+        for (int u = 0; u < 2; ++u) {
+            const int o = tid + u * RS_T;
+            if (o < nout) {
+                const int j = o / q4, c4 = o - j * q4;
+                float4 t = acc[u];
+                for (int i = 0; i < rows; ++i) {
+                    const float qv = sq[i * kmax + j];
+                    const float4 wv = *reinterpret_cast<const float4*>(sw + i * m + 4 * c4);
+                    t.x = fma(qv, wv.x, t.x);
+                    t.y = fma(qv, wv.y, t.y);
+                    t.z = fma(qv, wv.z, t.z);
+                    t.w = fma(qv, wv.w, t.w);
                 }
+                acc[u] = t;
+            }
+        }
+        __syncthreads();
+    }
+    const int ks = coff[s + 1] - coff[s];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int o = tid + u * RS_T;
+        if (o < nout) {
+            const int j = o / q4, c4 = o - j * q4;
+            if (j < ks) *reinterpret_cast<float4*>(cvec + (int64_t)(coff[s] + j) * m + 4 * c4) = acc[u];
         }
     }
-    __syncthreads();
-    const int ks = coff[s + 1] - coff[s];
-    for (int e = threadIdx.x; e < ks * m; e += RT4) cvec[(int64_t)coff[s] * m + e] = shr[e];
 }
 
 // z[g, c4..c4+3] += sum_j Q[pos g, j] y[coff_{part g} + j, c4..c4+3]  (m % 4 == 0)
@@ -1036,18 +1050,15 @@ static void multi_apply_t(ddg_handle h, int m) {
     coarse_restrict_multi_kernel<SK, KM><<<h->nsub, bd, smem, h->stream>>>(                             \
         h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff, \
         w.c32, m, h->nx, h->ny, h->nz)
-#define RESTRICT_MULTI4(KM)                                                                              \
-    coarse_restrict_multi4_kernel<SK, KM><<<h->nsub, RT4, (size_t)h->kmax * m * sizeof(float), h->stream>>>( \
-        h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff,  \
-        w.c32, m, h->nx, h->ny, h->nz)
         const bool vec4 = m % 4 == 0;
-        if (vec4 && h->kmax <= 8) RESTRICT_MULTI4(8);
-        else if (vec4 && h->kmax <= 16) RESTRICT_MULTI4(16);
+        if (vec4)
+            coarse_restrict_stage4_kernel<SK><<<h->nsub, RS_T, 0, h->stream>>>(
+                h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, w.r32, w.z32, h->Q32, h->kmax, h->coff,
+                w.c32, m, h->nx, h->ny, h->nz);
         else if (h->kmax <= 8) RESTRICT_MULTI(8);
         else if (h->kmax <= 16) RESTRICT_MULTI(16);
         else RESTRICT_MULTI(32);
 #undef RESTRICT_MULTI
-#undef RESTRICT_MULTI4
         const int B = h->B, nK = h->nK;
         const int nsplit = (B + CG_KS - 1) / CG_KS;
         if (h->nd.on) {
