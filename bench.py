@@ -247,8 +247,9 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
     """Many right-hand sides in one batched solve: 3D variable-coefficient
     diffusion (cell-centred, kappa = exp(GRF, length 0.1, sigma 1)), 12^3 boxes
     of 8^3 + overlap 1, p <= 2, m right-hand sides ~ N(0, 1), FP32
-    preconditioner with per-column FP64 CG; compared with the same columns
-    solved one at a time."""
+    preconditioner with per-column FP64 CG; the local solves on SIMT FP32
+    cores, on tcgen05 with BF16 operands and with TF32 operands; compared
+    with the same columns solved one at a time."""
     N, m = args.batched_size, args.batched_m
     prob = di.make_varcoef3d(N=N, box=8, overlap=1, p=2, m=m)
     solver = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32", "bf16"), tensor_cores=True,
@@ -311,6 +312,40 @@ def batched_arm(args, ddg, di, torch, dev, stream, barrier, max_over_ranks, worl
     ms1 = e0.elapsed_time(e1)
     out["single_rhs_fp32"] = {"ms_per_rhs": ms1 / k1, "dof_iters_per_s": prob.n * tot_it / (ms1 / 1e3)}
     solver.close()
+    del solver
+    torch.cuda.empty_cache()
+    # the TF32 operands: a handle whose FP32 batched solves run tcgen05 TF32
+    # local solves (A_i^{-1} and the residual rounded to TF32, twice the BF16
+    # bytes)
+    t32 = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp32",), tensor_cores="tf32", autotune=True)
+    t32.solve_batch(F, TOL)
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    U, its, rrs, st = t32.solve_batch(F, TOL)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    out["tf32_tc"] = {"ms": ms, "status": int(st), "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                      "max_true_relres": float(rrs.max()),
+                      "dof_iters_per_s": world * prob.n * float(its.sum()) / (ms / 1e3)}
+    out["arms"]["tf32_tc"] = "tcgen05 TF32 local solves (FP32 accumulate) on TF32 inverse slabs"
+    t32.profile(ddg.KERNEL_CLASSES)
+    t32.solve_batch(F, TOL)
+    torch.cuda.synchronize()
+    ls = t32.kernel_stats()["local_solve"]
+    t32.profile(())
+    if ls["timed"]:
+        pk = peaks()
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        ach = ls["bytes"] / (ls["ms"] / 1e3) / 1e9
+        out["roofline_tf32_local_solve"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                            "frac": ach / peak, "launches": ls["timed"],
+                                            "avg_launch_ms": ls["ms"] / ls["timed"],
+                                            "algorithmic_bytes_per_launch": ls["bytes"] / ls["timed"],
+                                            "tc_stages": t32.info()["tc_stages"]}
+    t32.close()
     return out
 
 

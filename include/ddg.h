@@ -70,6 +70,9 @@ enum { DDG_OVERLAP_GRAPH = 0, DDG_OVERLAP_BOX = 1 };
  * work grows with the half-bandwidth).  AUTO takes the inverses when every
  * block fits them, else the band. */
 enum { DDG_LOCAL_AUTO = 0, DDG_LOCAL_INV = 1, DDG_LOCAL_BAND = 2 };
+/* tensor-core operands of the batched local solve (Sec. 6's exact local
+ * solves as GEMMs over the right-hand sides): none, BF16 or TF32 */
+enum { DDG_TC_OFF = 0, DDG_TC_BF16 = 1, DDG_TC_TF32 = 2 };
 /* ordering of the exact coarse Cholesky factor of A0 (Sec. 4): the natural
  * subdomain order (a band; its solve is a block-bidiagonal recurrence) or
  * nested dissection of the subdomain graph (a multifrontal factor, far
@@ -103,10 +106,14 @@ typedef struct {
     double rank_tol;      /* Sec. 4 rank drop: keep column j while |R_jj| >
                              rank_tol * |R_00|; default 1e-10 */
     int chunk_tiles;      /* local-solve work item size in 32x32 tiles; 0 = auto */
-    int tensor_cores;     /* 1: also keep BF16 128x32 slabs of every A_i^{-1}; then
-                             ddg_solve_batch in DDG_PREC_BF16 runs its local solves on
-                             the tcgen05 tensor cores (BF16 x BF16, FP32 accumulate);
-                             default 0 */
+    int tensor_cores;     /* DDG_TC_*, default OFF.  BF16: also keep BF16 128x32 slabs
+                             of every A_i^{-1}; ddg_solve_batch in DDG_PREC_BF16 then
+                             runs its local solves on the tcgen05 tensor cores (BF16 x
+                             BF16, FP32 accumulate).  TF32: keep the slabs in FP32
+                             rounded to TF32 (twice the bytes); ddg_solve_batch in
+                             DDG_PREC_FP32 then runs its local solves as tcgen05 TF32 x
+                             TF32 products with FP32 accumulation (the residual is
+                             rounded to TF32 too) */
     int dedup_local;      /* 1: subdomains whose local matrices A_i are equal entry for
                              entry (rows and columns in ascending dof order) share one
                              stored inverse (constant-coefficient problems: the

@@ -252,6 +252,7 @@ void validate(const ddg_matrix* A, const int32_t* part, const double* F, int k, 
     DDG_REQUIRE(o.spin_budget_ms >= 0.0 && o.spin_budget_ms <= 3.6e6, DDG_EINVAL,
                 "spin_budget_ms must be in [0, 3.6e6]");
     DDG_REQUIRE(o.local_repr >= DDG_LOCAL_AUTO && o.local_repr <= DDG_LOCAL_BAND, DDG_EINVAL, "bad local_repr");
+    DDG_REQUIRE(o.tensor_cores >= DDG_TC_OFF && o.tensor_cores <= DDG_TC_TF32, DDG_EINVAL, "bad tensor_cores");
     DDG_REQUIRE(o.coarse_order == DDG_COARSE_BAND || o.coarse_order == DDG_COARSE_ND, DDG_EINVAL,
                 "bad coarse_order");
 }
@@ -917,9 +918,9 @@ void capture_batch(ddg_handle h, int m, cudaGraph_t g, int64_t* pre, int64_t* bo
     bool in_main = false, in_body = false;
     try {
         DDG_CUDA(cudaStreamSynchronize(saved));
-        if (h->precision == DDG_PREC_BF16 && h->tc.A && h->tc.last_m != m) {
-            // padding rows/columns of the BF16 residual slabs must read as zero
-            DDG_CUDA(cudaMemsetAsync(h->tc.X, 0, h->tc.x_elems * sizeof(__nv_bfloat16), saved));
+        if (h->precision == h->tc.prec() && h->tc.last_m != m) {
+            // padding rows/columns of the residual slabs must read as zero
+            DDG_CUDA(cudaMemsetAsync(h->tc.x_ptr(), 0, h->tc.x_bytes(), saved));
             DDG_CUDA(cudaStreamSynchronize(saved));
             h->tc.last_m = m;
         }
@@ -1031,11 +1032,11 @@ const ddg_handle_s::BatchGraph* batch_graph(ddg_handle h, int m) {
 
 ddg_status pcg_batch(ddg_handle h, const double* F, double* U, int m, double tol, int* iters, double* relres) {
     ddg::multi_ensure(h, m);
-    if (h->opt.autotune && h->precision == DDG_PREC_BF16 && h->tc.A) {
+    if (h->opt.autotune && h->precision == h->tc.prec()) {
         // the ring depth is a launch shape: tune it before a graph bakes it in
         const int before = h->tc_stages;
         if (h->tc.last_m != m) {
-            DDG_CUDA(cudaMemsetAsync(h->tc.X, 0, h->tc.x_elems * sizeof(__nv_bfloat16), h->stream));
+            DDG_CUDA(cudaMemsetAsync(h->tc.x_ptr(), 0, h->tc.x_bytes(), h->stream));
             h->tc.last_m = m;
         }
         ddg::autotune_tc(h, m);
@@ -1656,7 +1657,8 @@ namespace ddg {
 // tensor-core ring depth {3, 4, 6} for m columns (called before the batched
 // solve is captured or run; cached per class and m)
 void autotune_tc(ddg_handle h, int m) {
-    const TuneKey key{h->max_local, h->nsub, h->ncol, m, DDG_PREC_BF16};
+    // keyed on the operand type: BF16 and TF32 slabs differ in bytes per stage
+    const TuneKey key{h->max_local, h->nsub, h->ncol, m, h->tc.kind == DDG_TC_TF32 ? 100 + DDG_PREC_FP32 : DDG_PREC_BF16};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune.find(key);
@@ -2091,9 +2093,15 @@ static ddg_status setup_impl(const ddg_matrix* A, const int32_t* partition, cons
             h2d(h->tc.slab_off, soff.data(), nsub + 1, h->stream);
             h2d(h->tc.xoff, xo.data(), nsub + 1, h->stream);
             h2d(h->tc.items, tit.data(), tit.size(), h->stream);
-            h->tc.A = h->arena.alloc<__nv_bfloat16>((size_t)soff[nsub] * 128 * 32);
+            h->tc.kind = o.tensor_cores;
             h->tc.x_elems = xo[nsub] * (int64_t)DDG_MCHUNK * 32;
-            h->tc.X = h->arena.alloc<__nv_bfloat16>(h->tc.x_elems);
+            if (o.tensor_cores == DDG_TC_TF32) {
+                h->tc.A32 = h->arena.alloc<float>((size_t)soff[nsub] * 128 * 32);
+                h->tc.X32 = h->arena.alloc<float>(h->tc.x_elems);
+            } else {
+                h->tc.A = h->arena.alloc<__nv_bfloat16>((size_t)soff[nsub] * 128 * 32);
+                h->tc.X = h->arena.alloc<__nv_bfloat16>(h->tc.x_elems);
+            }
             DDG_CUDA(cudaStreamSynchronize(h->stream));
         }
 

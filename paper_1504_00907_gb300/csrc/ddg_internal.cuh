@@ -272,8 +272,11 @@ struct NdCoarse {
 
 // tensor-core (tcgen05) multi-RHS local solves: BF16 slabs of every A_i^{-1}
 struct TcData {
-    __nv_bfloat16* A = nullptr;    // 128 x 32 slabs, core-matrix order
-    __nv_bfloat16* X = nullptr;    // residual slabs N x 32 per subdomain
+    int kind = 0;                  // DDG_TC_*: the operand type of the slabs below
+    __nv_bfloat16* A = nullptr;    // 128 x 32 slabs, core-matrix order (BF16)
+    __nv_bfloat16* X = nullptr;    // residual slabs N x 32 per subdomain (BF16)
+    float* A32 = nullptr;          // the same slabs in TF32 (FP32 storage)
+    float* X32 = nullptr;
     int64_t* slab_off = nullptr;   // [nsub + 1] in A slabs
     int64_t* xoff = nullptr;       // [nsub + 1] in X slabs
     int2* items = nullptr;         // (sweep position, 128-row block) per colour
@@ -282,6 +285,10 @@ struct TcData {
     std::vector<int> h_cslab_off;
     int64_t x_elems = 0;
     int last_m = -1;
+    // the precision whose batched local solves run on the tensor cores
+    int prec() const { return kind == DDG_TC_BF16 ? DDG_PREC_BF16 : (kind == DDG_TC_TF32 ? DDG_PREC_FP32 : -1); }
+    size_t x_bytes() const { return (size_t)x_elems * (kind == DDG_TC_TF32 ? 4 : 2); }
+    void* x_ptr() const { return kind == DDG_TC_TF32 ? (void*)X32 : (void*)X; }
 };
 
 struct ddg_handle_s {

@@ -993,7 +993,9 @@ static double tc_bytes(ddg_handle h, int c, int m) {
     double b = 0.0;
     for (int q = h->h_csub_off[c]; q < h->h_csub_off[c + 1]; ++q) {
         const double nq = (double)(h->h_ov_off[q + 1] - h->h_ov_off[q]);
-        b += nq * nq * 2.0 + nq * m * (2.0 + 8.0);
+        // inverse elements and residual slab entries at the operand width, z read and written in FP32
+        const double ew = h->tc.kind == DDG_TC_TF32 ? 4.0 : 2.0;
+        b += nq * nq * ew + nq * m * (ew + 8.0);
     }
     return b;
 }
@@ -1006,10 +1008,10 @@ static void multi_apply_t(ddg_handle h, int m) {
     if (!w.r32_current)
         to_float_n_kernel<<<(unsigned)((n * m + 255) / 256), 256, 0, h->stream>>>(n * m, w.R, w.r32);
     DDG_CUDA(cudaMemsetAsync(w.z32, 0, n * m * sizeof(float), h->stream));
-    const bool tc = prec == DDG_PREC_BF16 && h->tc.A != nullptr;
+    const bool tc = prec == h->tc.prec();
     if (tc && h->tc.last_m != m) {
-        // padding rows/columns of the BF16 residual slabs must read as zero
-        DDG_CUDA(cudaMemsetAsync(h->tc.X, 0, h->tc.x_elems * sizeof(__nv_bfloat16), h->stream));
+        // padding rows/columns of the residual slabs must read as zero
+        DDG_CUDA(cudaMemsetAsync(h->tc.x_ptr(), 0, h->tc.x_bytes(), h->stream));
         h->tc.last_m = m;
     }
     auto local = [&](int c, bool zz) {

@@ -2,15 +2,17 @@
 //
 // For the batched solve the local step z[Omega~_i] += A_i^{-1} R~_i (r - A z)
 // (Sec. 6) is a dense GEMM Y_i = A_i^{-1} X_i with X_i = n_i x m.  A_i^{-1} is
-// kept in BF16 as 128 x 32 slabs (K-major, SWIZZLE_NONE core-matrix order:
-// core matrix (8 rows x 16 bytes) (mc, kc) at byte (mc * 4 + kc) * 128); the
-// local residual is written straight into BF16 X^T slabs (N x 32, same core
-// order).  One CTA computes one 128-row block of Y_i:
+// kept as 128 x 32 slabs in BF16 or in TF32 (FP32 storage), K-major,
+// SWIZZLE_NONE core-matrix order: core matrix (8 rows x 16 bytes) (mc, kc) at
+// byte (mc * KC + kc) * 128 with KC = 4 core matrices along K for BF16 and 8
+// for TF32; the local residual is written straight into X^T slabs of the same
+// type (N x 32, same core order).  One CTA computes one 128-row block of Y_i:
 //   thread 0      producer: cp.async.bulk of the A slab and the X slab of each
 //                 K step into a STAGES-deep shared-memory ring (mbarrier
 //                 transaction counts);
 //   thread 32     issues tcgen05.mma kind::f16 (BF16 x BF16 -> FP32, M = 128,
-//                 N = m rounded up to 16, K = 16, two per slab) into a TMEM
+//                 N = m rounded up to 16, K = 16, two per slab) or kind::tf32
+//                 (TF32 x TF32 -> FP32, K = 8, four per slab) into a TMEM
 //                 accumulator and commits each stage back to the producer;
 //   warps 0-3     read their 32 TMEM lanes (tcgen05.ld 32x32b) and add the
 //                 rows into z.
@@ -19,6 +21,8 @@
 // kernel drains the copies it has issued (each of them completes, since it
 // reads valid global memory; the drain still has a limit of its own, four
 // times the budget), frees its TMEM and returns.
+#include <type_traits>
+
 #include "ddg_internal.cuh"
 #include "dev_common.cuh"
 
@@ -30,6 +34,16 @@ constexpr int TC_K = 32;             // K per slab (two K = 16 MMAs)
 // count by the autotuner (4 when it is off)
 constexpr int TC_THREADS = 128;
 constexpr int A_SLAB = TC_M * TC_K;       // elements per A slab
+
+template <bool TF32>
+using TcElem = typename std::conditional<TF32, float, __nv_bfloat16>::type;
+
+// round to TF32 (nearest, ties away from zero), kept in FP32 storage
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -79,15 +93,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int N, int TC_STAGES>
+template <int N, int TC_STAGES, bool TF32>
 __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
     const int2* __restrict__ items, int item_base, const int64_t* __restrict__ ov_off,
     const int32_t* __restrict__ ov_nodes, const int32_t* __restrict__ Tq,
     const int64_t* __restrict__ slab_off, const int64_t* __restrict__ xoff,
-    const __nv_bfloat16* __restrict__ Aslab, const __nv_bfloat16* __restrict__ Xslab,
+    const TcElem<TF32>* __restrict__ Aslab, const TcElem<TF32>* __restrict__ Xslab,
     float* __restrict__ z, int m, int* err, uint64_t limit_ns, int no_copies) {
+    using E = TcElem<TF32>;
     constexpr int X_SLAB = N * TC_K;
-    constexpr uint32_t A_BYTES = A_SLAB * 2, X_BYTES = X_SLAB * 2, STAGE = A_BYTES + X_BYTES;
+    constexpr uint32_t A_BYTES = A_SLAB * sizeof(E), X_BYTES = X_SLAB * sizeof(E), STAGE = A_BYTES + X_BYTES;
+    // MMAs per slab (each covers 32 bytes of K: two core matrices) and the
+    // byte stride between 8-row core-matrix groups
+    constexpr int KSTEPS = TF32 ? 4 : 2;
+    constexpr uint32_t SBO = TF32 ? 1024 : 512;
     constexpr uint32_t TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + TC_STAGES * STAGE);
@@ -101,8 +120,8 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
     const int T = Tq[q];
     const int64_t o = ov_off[q];
     const int n = (int)(ov_off[q + 1] - o);
-    const __nv_bfloat16* Ab = Aslab + (slab_off[q] + (int64_t)blk * T) * A_SLAB;
-    const __nv_bfloat16* Xb = Xslab + xoff[q] * X_SLAB;
+    const E* Ab = Aslab + (slab_off[q] + (int64_t)blk * T) * A_SLAB;
+    const E* Xb = Xslab + xoff[q] * X_SLAB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -140,9 +159,11 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
             issued = J + 1;
         }
     } else if (threadIdx.x == 32) {
-        // kind::f16: D F32 (bit 4), A BF16 (bit 7), B BF16 (bit 10), K-major A and B,
-        // N >> 3 at bit 17, M >> 4 at bit 24
-        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+        // D F32 (bits 4-5 = 1), A and B type at bits 7-9 and 10-12 (kind::f16:
+        // BF16 = 1; kind::tf32: TF32 = 2), K-major A and B, N >> 3 at bit 17,
+        // M >> 4 at bit 24
+        constexpr uint32_t ab = TF32 ? 2u : 1u;
+        const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) |
                                ((uint32_t)(TC_M >> 4) << 24);
         bool ok = true;
         for (int J = 0; J < T; ++J) {
@@ -154,12 +175,16 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = sa(smem + s * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-                const uint64_t ad = sdesc(a0 + kk * 256, 128, 512);
-                const uint64_t bd = sdesc(b0 + kk * 256, 128, 512);
+            for (int kk = 0; kk < KSTEPS; ++kk) {
+                const uint64_t ad = sdesc(a0 + kk * 256, 128, SBO);
+                const uint64_t bd = sdesc(b0 + kk * 256, 128, SBO);
                 const uint32_t acc = (J > 0 || kk > 0) ? 1u : 0u;
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                if constexpr (TF32)
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+                                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                else
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(sa(&empty[s])) : "memory");
@@ -232,45 +257,50 @@ __global__ void __launch_bounds__(TC_THREADS) local_solve_tc_kernel(
 }
 
 // A_i^{-1} (FP64 workspace after local_factor_invert: inverse in the upper
-// 32x32 tiles) -> BF16 128 x 32 slabs in core-matrix order
+// 32x32 tiles) -> BF16 or TF32 128 x 32 slabs in core-matrix order
+template <bool TF32>
 __global__ void tc_pack_kernel(int q0, const int32_t* __restrict__ qlist, const double* __restrict__ ws, int Np,
                                const int64_t* __restrict__ ov_off, const int32_t* __restrict__ Tq,
-                               const int64_t* __restrict__ slab_off, __nv_bfloat16* __restrict__ out) {
+                               const int64_t* __restrict__ slab_off, TcElem<TF32>* __restrict__ out) {
+    // elements per 16-byte core-matrix row, core matrices along K per slab
+    constexpr int EPR = TF32 ? 4 : 8, KC = TC_K / EPR;
     const int b = blockIdx.x, q = qlist ? qlist[q0 + b] : q0 + b;
     const int n = (int)(ov_off[q + 1] - ov_off[q]);
     const int T = Tq[q];
     const int Mb = (n + TC_M - 1) / TC_M;
     const double* A = ws + (size_t)b * Np * Np;
-    __nv_bfloat16* dst = out + slab_off[q] * A_SLAB;
+    TcElem<TF32>* dst = out + slab_off[q] * A_SLAB;
     const int64_t total = (int64_t)Mb * T * A_SLAB;
     for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
         const int64_t slab = e / A_SLAB;
         const int w = (int)(e % A_SLAB);
         const int blk = (int)(slab / T), J = (int)(slab % T);
-        // invert core_off: w = ((mc * 4 + kc) * 64) + (r % 8) * 8 + (k % 8)
-        const int core = w >> 6, within = w & 63;
-        const int mc = core >> 2, kc = core & 3;
-        const int row = blk * TC_M + mc * 8 + (within >> 3);
-        const int col = J * TC_K + kc * 8 + (within & 7);
+        // invert the layout: w = ((mc * KC + kc) * 8 * EPR) + (r % 8) * EPR + (k % EPR)
+        const int core = w / (8 * EPR), within = w % (8 * EPR);
+        const int mc = core / KC, kc = core % KC;
+        const int row = blk * TC_M + mc * 8 + within / EPR;
+        const int col = J * TC_K + kc * EPR + within % EPR;
         double v = 0.0;
         if (row < n && col < n)
             v = (row / DDG_LT <= col / DDG_LT) ? A[(size_t)row * Np + col] : A[(size_t)col * Np + row];
-        dst[e] = __float2bfloat16_rn((float)v);
+        if constexpr (TF32) dst[e] = to_tf32((float)v);
+        else dst[e] = __float2bfloat16_rn((float)v);
     }
 }
 
-// (r - A z) at the colour's rows, all m columns, written as BF16 X^T slabs:
-// one CTA per (subdomain, 32-row slab); the residual is computed with
+// (r - A z) at the colour's rows, all m columns, written as BF16 or TF32 X^T
+// slabs: one CTA per (subdomain, 32-row slab); the residual is computed with
 // coalesced reads (consecutive threads = consecutive columns), staged in
 // shared memory and written out in core-matrix order with 16-byte stores.
-template <int SK>
+template <int SK, bool TF32>
 __global__ void __launch_bounds__(256) tc_residual_kernel(
     const int2* __restrict__ slabs, int slab_base, int m, int N, const int32_t* __restrict__ ov_nodes,
     const int64_t* __restrict__ ov_off, const int64_t* __restrict__ xoff,
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const float* __restrict__ val,
-    const float* __restrict__ r, const float* __restrict__ z, __nv_bfloat16* __restrict__ X, int z_zero,
+    const float* __restrict__ r, const float* __restrict__ z, TcElem<TF32>* __restrict__ X, int z_zero,
     int nx, int ny, int nz) {
-    __shared__ __nv_bfloat16 sx[TC_K][DDG_MCHUNK + 8];
+    using E = TcElem<TF32>;
+    __shared__ __align__(16) E sx[TC_K][DDG_MCHUNK + 8];
     // row metadata of the slab, shared by all m columns: node, and for the
     // CSR path up to 16 (column, value) pairs per row
     __shared__ int sg[TC_K], scnt[TC_K];
@@ -347,9 +377,14 @@ __global__ void __launch_bounds__(256) tc_residual_kernel(
                     s = make_float4(s.x - az.x, s.y - az.y, s.z - az.z, s.w - az.w);
                 }
             }
-            __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(&sx[kr][c4]);
-            d[0] = __floats2bfloat162_rn(s.x, s.y);
-            d[1] = __floats2bfloat162_rn(s.z, s.w);
+            if constexpr (TF32) {
+                *reinterpret_cast<float4*>(&sx[kr][c4]) =
+                    make_float4(to_tf32(s.x), to_tf32(s.y), to_tf32(s.z), to_tf32(s.w));
+            } else {
+                __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(&sx[kr][c4]);
+                d[0] = __floats2bfloat162_rn(s.x, s.y);
+                d[1] = __floats2bfloat162_rn(s.z, s.w);
+            }
         }
     } else {
     #pragma unroll 4
@@ -386,56 +421,74 @@ __global__ void __launch_bounds__(256) tc_residual_kernel(
                     }
                 }
             }
-            sx[kr][c] = __float2bfloat16_rn(s);
+            if constexpr (TF32) sx[kr][c] = to_tf32(s);
+            else sx[kr][c] = __float2bfloat16_rn(s);
         }
     }
     __syncthreads();
-    // core-matrix rows: (n, kc) holds k = kc*8 .. kc*8+7 of column n, 16 bytes
+    // core-matrix rows: (n, kc) holds k = kc*EPR .. kc*EPR+EPR-1 of column n,
+    // 16 bytes (EPR = 8 BF16 or 4 TF32 elements, KC = 32 / EPR)
+    constexpr int EPR = TF32 ? 4 : 8, KC = TC_K / EPR;
     uint4* dst = reinterpret_cast<uint4*>(X + (xoff[q] + J) * (int64_t)(N * TC_K));
-    for (int e = threadIdx.x; e < N * 4; e += blockDim.x) {
-        const int core_row = e;                   // ((nc * 4 + kc) * 8 + n % 8)
+    for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
+        const int core_row = e;                   // ((nc * KC + kc) * 8 + n % 8)
         const int cm = core_row >> 3, nr = core_row & 7;
-        const int nc = cm >> 2, kc = cm & 3;
+        const int nc = cm / KC, kc = cm % KC;
         const int nn = nc * 8 + nr;
-        __align__(16) __nv_bfloat16 v[8];
+        __align__(16) E v[EPR];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) v[t] = sx[kc * 8 + t][nn];
+        for (int t = 0; t < EPR; ++t) v[t] = sx[kc * EPR + t][nn];
         dst[e] = *reinterpret_cast<const uint4*>(v);
     }
 }
 
-template <int N, int TC_STAGES>
+template <int N, int TC_STAGES, bool TF32>
 constexpr int tc_smem() {
-    return TC_STAGES * (A_SLAB * 2 + N * TC_K * 2) + (2 * TC_STAGES + 1) * 8 + 16;
+    return TC_STAGES * (A_SLAB + N * TC_K) * (int)sizeof(TcElem<TF32>) + (2 * TC_STAGES + 1) * 8 + 16;
 }
 
-template <int N, int TC_STAGES>
+template <int N, int TC_STAGES, bool TF32>
 void configure_tc() {
     static PerDeviceMax configured;   // the attribute is per device
-    constexpr int smem = tc_smem<N, TC_STAGES>();
+    constexpr int smem = tc_smem<N, TC_STAGES, TF32>();
     int dev = -1;
     if (!configured.needs(smem, dev)) return;
-    DDG_CUDA(cudaFuncSetAttribute(local_solve_tc_kernel<N, TC_STAGES>,
+    DDG_CUDA(cudaFuncSetAttribute(local_solve_tc_kernel<N, TC_STAGES, TF32>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured.commit(dev, smem);
 }
 
-template <int N, int TC_STAGES>
+template <int N, int TC_STAGES, bool TF32>
 void launch_tc_s(ddg_handle h, int i0, int i1, int m) {
-    configure_tc<N, TC_STAGES>();
-    constexpr int smem = tc_smem<N, TC_STAGES>();
-    local_solve_tc_kernel<N, TC_STAGES><<<i1 - i0, TC_THREADS, smem, h->stream>>>(
-        h->tc.items, i0, h->ov_off, h->ov_nodes, h->Tq, h->tc.slab_off, h->tc.xoff, h->tc.A, h->tc.X,
+    configure_tc<N, TC_STAGES, TF32>();
+    constexpr int smem = tc_smem<N, TC_STAGES, TF32>();
+    const TcElem<TF32>* A;
+    const TcElem<TF32>* X;
+    if constexpr (TF32) {
+        A = h->tc.A32;
+        X = h->tc.X32;
+    } else {
+        A = h->tc.A;
+        X = h->tc.X;
+    }
+    local_solve_tc_kernel<N, TC_STAGES, TF32><<<i1 - i0, TC_THREADS, smem, h->stream>>>(
+        h->tc.items, i0, h->ov_off, h->ov_nodes, h->Tq, h->tc.slab_off, h->tc.xoff, A, X,
         h->mw.z32, m, h->errflags + E_TIMEOUT, (uint64_t)h->wait_ns,
         (h->debug & DDG_DEBUG_TC_NO_COPIES) ? 1 : 0);
     DDG_CHECK_LAUNCH();
 }
 
+template <int N, bool TF32>
+void launch_tc_k(ddg_handle h, int i0, int i1, int m) {
+    if (h->tc_stages == 3) launch_tc_s<N, 3, TF32>(h, i0, i1, m);
+    else if (h->tc_stages == 6) launch_tc_s<N, 6, TF32>(h, i0, i1, m);
+    else launch_tc_s<N, 4, TF32>(h, i0, i1, m);
+}
+
 template <int N>
 void launch_tc(ddg_handle h, int i0, int i1, int m) {
-    if (h->tc_stages == 3) launch_tc_s<N, 3>(h, i0, i1, m);
-    else if (h->tc_stages == 6) launch_tc_s<N, 6>(h, i0, i1, m);
-    else launch_tc_s<N, 4>(h, i0, i1, m);
+    if (h->tc.kind == DDG_TC_TF32) launch_tc_k<N, true>(h, i0, i1, m);
+    else launch_tc_k<N, false>(h, i0, i1, m);
 }
 
 }  // namespace
@@ -446,9 +499,13 @@ int tc_n_for(int m) { return ((m + 15) / 16) * 16; }
 
 void tc_pack(ddg_handle h, int q0, int q1, const int32_t* qlist, const double* ws) {
     const int nb = q1 - q0;
-    if (nb <= 0 || !h->tc.A) return;
-    tc_pack_kernel<<<nb, 256, 0, h->stream>>>(q0, qlist, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq, h->tc.slab_off,
-                                              h->tc.A);
+    if (nb <= 0 || h->tc.kind == DDG_TC_OFF) return;
+    if (h->tc.kind == DDG_TC_TF32)
+        tc_pack_kernel<true><<<nb, 256, 0, h->stream>>>(q0, qlist, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq,
+                                                        h->tc.slab_off, h->tc.A32);
+    else
+        tc_pack_kernel<false><<<nb, 256, 0, h->stream>>>(q0, qlist, ws, h->Tmax * DDG_LT, h->ov_off, h->Tq,
+                                                         h->tc.slab_off, h->tc.A);
     DDG_CHECK_LAUNCH();
 }
 
@@ -457,10 +514,17 @@ void tc_residual(ddg_handle h, int c, bool z_zero, int m) {
     if (s1 <= s0) return;
     const int N = tc_n_for(m);
     MultiWork& w = h->mw;
-#define TC_RES(SK)                                                                                       \
-    tc_residual_kernel<SK><<<s1 - s0, 256, 0, h->stream>>>(h->tc.slabs, s0, m, N, h->ov_nodes, h->ov_off, \
-                                                           h->tc.xoff, h->rowptr, h->col, h->val32, w.r32, \
-                                                           w.z32, h->tc.X, z_zero, h->nx, h->ny, h->nz)
+#define TC_RES(SK)                                                                                          \
+    do {                                                                                                     \
+        if (h->tc.kind == DDG_TC_TF32)                                                                       \
+            tc_residual_kernel<SK, true><<<s1 - s0, 256, 0, h->stream>>>(                                    \
+                h->tc.slabs, s0, m, N, h->ov_nodes, h->ov_off, h->tc.xoff, h->rowptr, h->col, h->val32, w.r32, \
+                w.z32, h->tc.X32, z_zero, h->nx, h->ny, h->nz);                                              \
+        else                                                                                                 \
+            tc_residual_kernel<SK, false><<<s1 - s0, 256, 0, h->stream>>>(                                   \
+                h->tc.slabs, s0, m, N, h->ov_nodes, h->ov_off, h->tc.xoff, h->rowptr, h->col, h->val32, w.r32, \
+                w.z32, h->tc.X, z_zero, h->nx, h->ny, h->nz);                                                \
+    } while (0)
     DDG_DISPATCH_SK(h, TC_RES);
 #undef TC_RES
     DDG_CHECK_LAUNCH();

@@ -23,6 +23,7 @@ DDG_DEBUG_TC_NO_COPIES = 1
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
 LOCAL = {"auto": 0, "inv": 1, "band": 2}
 COARSE = {"band": 0, "nd": 1}
+TC = {"off": 0, "bf16": 1, "tf32": 2}
 OVERLAP = {"graph": 0, "box": 1}
 BETA = {"fr": 0, "pr": 1, "auto": 2}
 
@@ -225,7 +226,7 @@ class Solver:
         o.use_coarse = 1 if use_coarse else 0
         o.rank_tol = rank_tol
         o.chunk_tiles = chunk_tiles
-        o.tensor_cores = 1 if tensor_cores else 0
+        o.tensor_cores = TC[tensor_cores] if isinstance(tensor_cores, str) else (1 if tensor_cores else 0)
         o.dedup_local = 1 if dedup_local else 0
         o.spin_budget_ms = spin_budget_ms
         o.autotune = 1 if autotune else 0

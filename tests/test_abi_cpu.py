@@ -78,7 +78,7 @@ def _matrix(rowptr, col, val):
     return m
 
 
-@pytest.mark.parametrize("case", ["neg_part", "col_range", "k_zero", "box_shape"])
+@pytest.mark.parametrize("case", ["neg_part", "col_range", "k_zero", "box_shape", "tc_kind"])
 def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib, case):
     from paper_1504_00907_gb300 import ddg
     import ddg_inputs as di
@@ -99,6 +99,8 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib, case):
     if case == "box_shape":
         o.overlap_mode = 1
         m.dim, m.nx, m.ny, m.nz = 2, 5, 4, 1
+    if case == "tc_kind":
+        o.tensor_cores = 3
     h = ctypes.c_void_p()
     st = lib.ddg_setup(ctypes.byref(m), part.ctypes.data_as(ctypes.c_void_p),
                        F.ctypes.data_as(ctypes.c_void_p), k, 1, ctypes.byref(o), None, ctypes.byref(h))

@@ -217,18 +217,22 @@ def test_batched_solve_matches_oracle_per_column(name, m, prec):
 _tc_cache = {}
 
 
-@pytest.mark.parametrize("name,m", [("varcoef_16", 64), ("varcoef_24", 64), ("varcoef_16", 5),
-                                    ("poisson3d_ragged", 33),
-                                    ("poisson2d_64", 16), ("poisson3d_graph", 48)])
-def test_batched_tensor_core_solve_matches_oracle(name, m):
-    # tcgen05 BF16 local solves (residual and A_i^{-1} rounded to BF16, FP32
-    # accumulation) inside the FP32 preconditioner, FP64 CG per column
+@pytest.mark.parametrize("name,m,kind", [("varcoef_16", 64, "bf16"), ("varcoef_24", 64, "bf16"),
+                                         ("varcoef_16", 5, "bf16"), ("poisson3d_ragged", 33, "bf16"),
+                                         ("poisson2d_64", 16, "bf16"), ("poisson3d_graph", 48, "bf16"),
+                                         ("varcoef_16", 64, "tf32"), ("varcoef_16", 5, "tf32"),
+                                         ("poisson3d_ragged", 33, "tf32"), ("poisson2d_64", 16, "tf32"),
+                                         ("poisson3d_graph", 48, "tf32")])
+def test_batched_tensor_core_solve_matches_oracle(name, m, kind):
+    # tcgen05 local solves inside the FP32 preconditioner, FP64 CG per
+    # column: BF16 (residual and A_i^{-1} rounded to BF16) or TF32 (rounded
+    # to TF32), FP32 accumulation either way
     from paper_1504_00907_gb300 import ddg
     prob, _, oracle = setup_case(name)
-    if name not in _tc_cache:
-        _tc_cache[name] = ddg.Solver.from_problem(prob, precision="bf16", keep=("bf16",),
-                                                  tensor_cores=True)
-    solver = _tc_cache[name]
+    if (name, kind) not in _tc_cache:
+        prec = "bf16" if kind == "bf16" else "fp32"
+        _tc_cache[(name, kind)] = ddg.Solver.from_problem(prob, precision=prec, keep=(prec,), tensor_cores=kind)
+    solver = _tc_cache[(name, kind)]
     F = di.normal_rhs(prob.n, 90 + m, m)
     U, its, rrs, st = solver.solve_batch(dev(F), tol=1e-8)
     assert st == 0 and np.all(rrs <= 1e-8)
