@@ -508,10 +508,14 @@ def test_autotuned_launch_shapes_keep_parity():
     b.close()
 
 
-def test_autotuned_tensor_core_stages_keep_parity():
+@pytest.mark.parametrize("kind", ["bf16", "tf32"])
+def test_autotuned_tensor_core_stages_keep_parity(kind):
+    # the ring depth is tuned per operand type (BF16 and TF32 stages differ
+    # in bytes) and either choice keeps parity
     from paper_1504_00907_gb300 import ddg
     prob, _, oracle = setup_case("varcoef_24")
-    s = ddg.Solver.from_problem(prob, precision="bf16", keep=("bf16",), tensor_cores=True, autotune=True)
+    prec = "bf16" if kind == "bf16" else "fp32"
+    s = ddg.Solver.from_problem(prob, precision=prec, keep=(prec,), tensor_cores=kind, autotune=True)
     F = di.normal_rhs(prob.n, 300, 16)
     U, its, rrs, st = s.solve_batch(dev(F), tol=1e-8)
     assert st == 0 and np.all(rrs <= 1e-8)
