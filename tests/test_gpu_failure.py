@@ -25,11 +25,13 @@ def dev(x):
     return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
 
 
-def test_tensor_core_wait_runs_out_and_the_handle_recovers():
+@pytest.mark.parametrize("kind", ["bf16", "tf32"])
+def test_tensor_core_wait_runs_out_and_the_handle_recovers(kind):
     import time
     from paper_1504_00907_gb300 import ddg
     prob = di.make_varcoef3d(N=16, box=8, overlap=1, p=2, m=None)
-    s = ddg.Solver.from_problem(prob, precision="bf16", keep=("bf16",), tensor_cores=True,
+    prec = "bf16" if kind == "bf16" else "fp32"
+    s = ddg.Solver.from_problem(prob, precision=prec, keep=(prec,), tensor_cores=kind,
                                 spin_budget_ms=20.0)
     F = dev(di.normal_rhs(prob.n, 70, 16))
     U_ref, its, rrs, st = s.solve_batch(F, tol=1e-8)
