@@ -95,9 +95,9 @@ __global__ void __launch_bounds__(RT) spmv_lap64_kernel(int nx, int ny, int nz,
         const int i = g - t * nx, j = t % ny, k = t / ny;
         const double xc = x[g];
         // the neighbours' sum, then one FMA: one FP64 operation fewer per
-        // row than subtracting the neighbours one by one (FP64 issue bound)
-        double nb = 0.0;
-        if (i > 0) nb += x[g - 1];
+        // row than subtracting the neighbours one by one (FP64 issue bound);
+        // the sum starts from the first neighbour, not from an added zero
+        double nb = i > 0 ? x[g - 1] : 0.0;
         if (i < nx - 1) nb += x[g + 1];
         if (j > 0) nb += x[g - nx];
         if (j < ny - 1) nb += x[g + nx];
