@@ -184,22 +184,36 @@ struct NdSolve {
     const int64_t *uoff, *doff, *goff, *dtoff, *gtoff;
 };
 
+// the warp's factor row into L2, one 128-byte line per lane and step
+// (every line it names holds part of the row, so the address is valid)
+template <typename T>
+__device__ __forceinline__ void nd_prefetch_row(const T* row, int len, int lane) {
+    if (len <= 0) return;
+    const uintptr_t b = reinterpret_cast<uintptr_t>(row), e = b + (uintptr_t)len * sizeof(T);
+    for (uintptr_t a = (b & ~(uintptr_t)127) + (uintptr_t)lane * 128; a < e; a += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 // forward, one warp per item: (front f, row i) gives y[s0 + i] = D[i] . w_S;
 // (-1 - k, 0) gives target k of the level: w[tgt_k] -= the sum, in a fixed
-// order, of G_f[u] . w_{S_f} over the (front, row) pairs listed for it
+// order, of G_f[u] . w_{S_f} over the (front, row) pairs listed for it.
+// The factor rows do not depend on the previous level, so a warp prefetches
+// them before it waits for that level (programmatic dependent launch); the
+// vectors are read after the wait.
 template <typename V>
 __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
                                                      const int32_t* __restrict__ tgt, const int64_t* __restrict__ ptr,
                                                      const int2* __restrict__ src, const V* __restrict__ data, V* w,
                                                      V* y) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (wi >= n) return;
+    if (wi >= n) return;   // reads nothing the previous level writes
     const int2 it = items[wi];
     if (it.x >= 0) {
         const int f = it.x, i = it.y;
         const V* row = data + F.doff[f] + drow(i);
+        nd_prefetch_row(row, i + 1, lane);
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         const V* v = w + F.s0[f];
         V s = 0;
 #pragma unroll 4
@@ -209,8 +223,15 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
         return;
     }
     const int k = -1 - it.x;
+    const int64_t e0 = ptr[k], e1 = ptr[k + 1];
+    for (int64_t e = e0; e < e1; ++e) {
+        const int2 fu = src[e];
+        const int nS = F.nS[fu.x];
+        nd_prefetch_row(data + F.goff[fu.x] + (int64_t)fu.y * r4(nS), nS, lane);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     V s = 0;
-    for (int64_t e = ptr[k]; e < ptr[k + 1]; ++e) {
+    for (int64_t e = e0; e < e1; ++e) {
         const int2 fu = src[e];
         const int f = fu.x, nS = F.nS[f];
         const V* row = data + F.goff[f] + (int64_t)fu.y * r4(nS);
@@ -224,24 +245,28 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
 }
 
 // backward, one warp per (front f, row s): x[s0 + s] = D^T[s] . y_S - G^T[s] . x_U
+// (the factor rows and the U positions prefetched before the wait, as forward)
 template <typename V>
 __global__ void __launch_bounds__(256) nd_bwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
                                                      const V* __restrict__ data, const V* y, V* x) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (wi >= n) return;
+    if (wi >= n) return;   // reads nothing the previous level writes
     const int2 it = items[wi];
     const int f = it.x, r = it.y;
     const int nS = F.nS[f], nU = F.nU[f], s0 = F.s0[f];
     const int c0 = r & ~3;
     const V* drow_ = data + F.dtoff[f] + dtrow(r, nS);
+    const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
+    const int32_t* up = F.up + F.uoff[f];
+    nd_prefetch_row(drow_, nS - c0, lane);
+    nd_prefetch_row(grow, nU, lane);
+    nd_prefetch_row(up, nU, lane);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const V* vy = y + s0 + c0;
     V s = 0;
 #pragma unroll 4
     for (int j = lane; j < nS - c0; j += 32) s = fma(drow_[j], vy[j], s);
-    const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
-    const int32_t* up = F.up + F.uoff[f];
 #pragma unroll 4
     for (int j = lane; j < nU; j += 32) s = fma(-grow[j], x[up[j]], s);
     s = ddgdev::warp_sum(s);
