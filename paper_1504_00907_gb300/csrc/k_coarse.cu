@@ -561,6 +561,17 @@ __global__ void __launch_bounds__(256) coarse_restrict_kernel(
     __shared__ V red[32 * 8];
     __shared__ V out[KC];
     const int s = blockIdx.x;
+    // launched as a programmatic dependent of the last local solve: the
+    // subdomain's rows of Q (fixed at setup) go to L2 before the wait, r and
+    // z are read after it
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    {
+        const uintptr_t b = reinterpret_cast<uintptr_t>(Q + sub_off[s] * kmax);
+        const uintptr_t e = reinterpret_cast<uintptr_t>(Q + sub_off[s + 1] * kmax);
+        for (uintptr_t p = (b & ~(uintptr_t)127) + (uintptr_t)threadIdx.x * 128; p < e; p += (uintptr_t)blockDim.x * 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     V acc[KC];
 #pragma unroll
     for (int j = 0; j < KC; ++j) acc[j] = 0;
@@ -626,11 +637,19 @@ __global__ void coarse_prolong_kernel(int64_t n, const int32_t* __restrict__ par
                                       const int32_t* __restrict__ pos, const V* __restrict__ Q,
                                       int kmax, const int32_t* __restrict__ coff,
                                       const V* __restrict__ y, V* __restrict__ z) {
+    // a programmatic dependent of the coarse solve: the row of Q and the
+    // indices (fixed at setup) are read before the wait, y and z after it
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    if (g >= n) return;   // reads nothing the coarse solve writes
     const int s = part[g];
     const int c0 = coff[s], ks = coff[s + 1] - c0;
     const V* qa = Q + (int64_t)pos[g] * kmax;
+    if (ks > 0) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(qa));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(qa + ks - 1));
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     V acc = 0;
     for (int j = 0; j < ks; ++j) acc = fma(qa[j], y[c0 + j], acc);
     z[g] += acc;
@@ -937,13 +956,17 @@ void coarse_build_apply(ddg_handle h) {
 template <int SK, int KC>
 static void launch_restrict_k(ddg_handle h, int prec, bool residual) {
     if (prec == DDG_PREC_FP64)
-        coarse_restrict_kernel<SK, KC, double, double><<<h->nsub, 256, 0, h->stream>>>(
-            h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val64, h->rin64, h->z64, h->Q64,
-            h->kmax, h->coff, h->c64, residual, h->nx, h->ny, h->nz);
+        launch_pdl(h, coarse_restrict_kernel<SK, KC, double, double>, dim3(h->nsub), dim3(256), 0,
+                   (const int64_t*)h->sub_off, (const int32_t*)h->sub_nodes, (const int64_t*)h->rowptr,
+                   (const int32_t*)h->col, (const double*)h->val64, (const double*)h->rin64,
+                   (const double*)h->z64, (const double*)h->Q64, h->kmax, (const int32_t*)h->coff, h->c64,
+                   residual ? 1 : 0, h->nx, h->ny, h->nz);
     else
-        coarse_restrict_kernel<SK, KC, float, float><<<h->nsub, 256, 0, h->stream>>>(
-            h->sub_off, h->sub_nodes, h->rowptr, h->col, h->val32, h->r32, h->z32, h->Q32, h->kmax,
-            h->coff, h->c32, residual, h->nx, h->ny, h->nz);
+        launch_pdl(h, coarse_restrict_kernel<SK, KC, float, float>, dim3(h->nsub), dim3(256), 0,
+                   (const int64_t*)h->sub_off, (const int32_t*)h->sub_nodes, (const int64_t*)h->rowptr,
+                   (const int32_t*)h->col, (const float*)h->val32, (const float*)h->r32, (const float*)h->z32,
+                   (const float*)h->Q32, h->kmax, (const int32_t*)h->coff, h->c32, residual ? 1 : 0, h->nx,
+                   h->ny, h->nz);
     DDG_CHECK_LAUNCH();
 }
 
@@ -1025,11 +1048,13 @@ void coarse_solve(ddg_handle h, int prec) {
 void coarse_prolong(ddg_handle h, int prec) {
     const unsigned blocks = (unsigned)((h->n + 255) / 256);
     if (prec == DDG_PREC_FP64)
-        coarse_prolong_kernel<double><<<blocks, 256, 0, h->stream>>>(h->n, h->part, h->pos, h->Q64,
-                                                                     h->kmax, h->coff, h->x64, h->z64);
+        launch_pdl(h, coarse_prolong_kernel<double>, dim3(blocks), dim3(256), 0, h->n, (const int32_t*)h->part,
+                   (const int32_t*)h->pos, (const double*)h->Q64, h->kmax, (const int32_t*)h->coff,
+                   (const double*)h->x64, h->z64);
     else
-        coarse_prolong_kernel<float><<<blocks, 256, 0, h->stream>>>(h->n, h->part, h->pos, h->Q32,
-                                                                    h->kmax, h->coff, h->x32, h->z32);
+        launch_pdl(h, coarse_prolong_kernel<float>, dim3(blocks), dim3(256), 0, h->n, (const int32_t*)h->part,
+                   (const int32_t*)h->pos, (const float*)h->Q32, h->kmax, (const int32_t*)h->coff,
+                   (const float*)h->x32, h->z32);
     DDG_CHECK_LAUNCH();
 }
 
