@@ -189,6 +189,18 @@ class Solver:
                  maxit=1000, use_coarse=True, rank_tol=1e-10, chunk_tiles=0, tensor_cores=False,
                  stream=None, coarse_groups=None, dedup_local=False, spin_budget_ms=1000.0,
                  autotune=False, local_repr="auto", coarse_order="nd"):
+        """Set up the preconditioner for the CSR matrix ``A`` (scipy), the
+        partition ``part`` (subdomain id per dof) and the generators ``F``
+        (n x k) with ``overlap`` layers (``ddg_setup``).
+
+        precision: "fp64" | "fp32" | "bf16" (preconditioner; CG is FP64);
+        keep: the precisions whose local inverses are stored (set_precision
+        switches among them); tensor_cores: False | "bf16" | "tf32" (True
+        means "bf16"): operands of the tcgen05 local solves of solve_batch
+        at precision "bf16" or "fp32" respectively; coarse_order: "nd" |
+        "band"; local_repr: "auto" | "inv" | "band"; coarse_groups: group id
+        per subdomain for the three-level V-cycle (``ddg_setup_vcycle``).
+        The remaining keywords mirror the fields of ``ddg_options``."""
         import torch
         lib = load()
         if not torch.cuda.is_available():
