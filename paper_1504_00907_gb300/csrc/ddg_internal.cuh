@@ -262,6 +262,7 @@ struct NdCoarse {
     int64_t* rsrcp = nullptr;
     std::vector<int> h_mf_off, h_mb_off, h_tgt_off;
     std::vector<int> h_mf_ks, h_mb_ks;   // CTAs per tile (one cluster) per level
+    std::vector<int> h_fwd_wpr, h_bwd_wpr;   // warps per item of the single-vector solve, per level
     int64_t urows = 0;
     int32_t *fwd_off = nullptr, *bwd_off = nullptr;   // device copies
     unsigned* bar = nullptr;           // grid barrier of the persistent solve

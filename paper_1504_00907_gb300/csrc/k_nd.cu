@@ -184,93 +184,123 @@ struct NdSolve {
     const int64_t *uoff, *doff, *goff, *dtoff, *gtoff;
 };
 
-// the warp's factor row into L2, one 128-byte line per lane and step
-// (every line it names holds part of the row, so the address is valid)
+// a factor row into L2, one 128-byte line per thread and step (every line
+// it names holds part of the row, so the address is valid); t is the
+// thread's index among the nt threads that share the row
 template <typename T>
-__device__ __forceinline__ void nd_prefetch_row(const T* row, int len, int lane) {
+__device__ __forceinline__ void nd_prefetch_row(const T* row, int len, int t, int nt) {
     if (len <= 0) return;
     const uintptr_t b = reinterpret_cast<uintptr_t>(row), e = b + (uintptr_t)len * sizeof(T);
-    for (uintptr_t a = (b & ~(uintptr_t)127) + (uintptr_t)lane * 128; a < e; a += 32 * 128)
+    for (uintptr_t a = (b & ~(uintptr_t)127) + (uintptr_t)t * 128; a < e; a += (uintptr_t)nt * 128)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
 }
 
-// forward, one warp per item: (front f, row i) gives y[s0 + i] = D[i] . w_S;
-// (-1 - k, 0) gives target k of the level: w[tgt_k] -= the sum, in a fixed
-// order, of G_f[u] . w_{S_f} over the (front, row) pairs listed for it.
-// The factor rows do not depend on the previous level, so a warp prefetches
-// them before it waits for that level (programmatic dependent launch); the
-// vectors are read after the wait.
-template <typename V>
+// WPR warps share one item (levels near the root have long rows and few of
+// them); the WPR warp sums are added in warp order through shared memory,
+// so the result depends on WPR (fixed per level at setup) and nothing else
+template <typename V, int WPR>
+__device__ __forceinline__ bool nd_combine(V& s, V* part) {
+    if (WPR == 1) return (threadIdx.x & 31) == 0;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) part[warp] = s;
+    __syncthreads();
+    if (warp % WPR != 0 || (threadIdx.x & 31) != 0) return false;
+    V t = part[warp];
+#pragma unroll
+    for (int u = 1; u < WPR; ++u) t += part[warp + u];
+    s = t;
+    return true;
+}
+
+// forward, one item per WPR warps: (front f, row i) gives y[s0 + i] =
+// D[i] . w_S; (-1 - k, 0) gives target k of the level: w[tgt_k] -= the sum,
+// in a fixed order, of G_f[u] . w_{S_f} over the (front, row) pairs listed
+// for it.  The factor rows do not depend on the previous level, so the
+// warps prefetch them before they wait for that level (programmatic
+// dependent launch); the vectors are read after the wait.
+template <typename V, int WPR>
 __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
                                                      const int32_t* __restrict__ tgt, const int64_t* __restrict__ ptr,
                                                      const int2* __restrict__ src, const V* __restrict__ data, V* w,
                                                      V* y) {
+    __shared__ V part[8];
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (wi >= n) return;   // reads nothing the previous level writes
-    const int2 it = items[wi];
+    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) / WPR, lane = threadIdx.x & 31;
+    const int t = ((threadIdx.x >> 5) % WPR) * 32 + lane;   // thread's index within its item
+    if (WPR == 1 && wi >= n) return;   // reads nothing the previous level writes
+    const bool live = wi < n;
+    const int2 it = live ? items[wi] : make_int2(0, 0);
+    V s = 0;
+    int out = -1;
     if (it.x >= 0) {
         const int f = it.x, i = it.y;
         const V* row = data + F.doff[f] + drow(i);
-        nd_prefetch_row(row, i + 1, lane);
+        if (live) nd_prefetch_row(row, i + 1, t, 32 * WPR);
         asm volatile("griddepcontrol.wait;" ::: "memory");
         const V* v = w + F.s0[f];
-        V s = 0;
+        if (live) {
 #pragma unroll 4
-        for (int j = lane; j <= i; j += 32) s = fma(row[j], v[j], s);
+            for (int j = t; j <= i; j += 32 * WPR) s = fma(row[j], v[j], s);
+        }
         s = ddgdev::warp_sum(s);
-        if (lane == 0) y[F.s0[f] + i] = s;
-        return;
-    }
-    const int k = -1 - it.x;
-    const int64_t e0 = ptr[k], e1 = ptr[k + 1];
-    for (int64_t e = e0; e < e1; ++e) {
-        const int2 fu = src[e];
-        const int nS = F.nS[fu.x];
-        nd_prefetch_row(data + F.goff[fu.x] + (int64_t)fu.y * r4(nS), nS, lane);
-    }
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    V s = 0;
-    for (int64_t e = e0; e < e1; ++e) {
-        const int2 fu = src[e];
-        const int f = fu.x, nS = F.nS[f];
-        const V* row = data + F.goff[f] + (int64_t)fu.y * r4(nS);
-        const V* v = w + F.s0[f];
-        V t = 0;
+        out = F.s0[f] + i;
+    } else {
+        const int k = -1 - it.x;
+        const int64_t e0 = ptr[k], e1 = ptr[k + 1];
+        for (int64_t e = e0; e < e1; ++e) {
+            const int2 fu = src[e];
+            const int nS = F.nS[fu.x];
+            nd_prefetch_row(data + F.goff[fu.x] + (int64_t)fu.y * r4(nS), nS, t, 32 * WPR);
+        }
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        for (int64_t e = e0; e < e1; ++e) {
+            const int2 fu = src[e];
+            const int f = fu.x, nS = F.nS[f];
+            const V* row = data + F.goff[f] + (int64_t)fu.y * r4(nS);
+            const V* v = w + F.s0[f];
+            V tt = 0;
 #pragma unroll 4
-        for (int j = lane; j < nS; j += 32) t = fma(row[j], v[j], t);
-        s += ddgdev::warp_sum(t);
+            for (int j = t; j < nS; j += 32 * WPR) tt = fma(row[j], v[j], tt);
+            s += ddgdev::warp_sum(tt);
+        }
     }
-    if (lane == 0) w[tgt[k]] -= s;
+    if (!nd_combine<V, WPR>(s, part) || !live) return;
+    if (out >= 0) y[out] = s;
+    else w[tgt[-1 - it.x]] -= s;
 }
 
-// backward, one warp per (front f, row s): x[s0 + s] = D^T[s] . y_S - G^T[s] . x_U
-// (the factor rows and the U positions prefetched before the wait, as forward)
-template <typename V>
+// backward, one item per WPR warps (front f, row s): x[s0 + s] = D^T[s] . y_S
+// - G^T[s] . x_U (the factor rows and the U positions prefetched before the
+// wait, as forward)
+template <typename V, int WPR>
 __global__ void __launch_bounds__(256) nd_bwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
                                                      const V* __restrict__ data, const V* y, V* x) {
+    __shared__ V part[8];
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (wi >= n) return;   // reads nothing the previous level writes
-    const int2 it = items[wi];
+    const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) / WPR, lane = threadIdx.x & 31;
+    const int t = ((threadIdx.x >> 5) % WPR) * 32 + lane;
+    if (WPR == 1 && wi >= n) return;   // reads nothing the previous level writes
+    const bool live = wi < n;
+    const int2 it = live ? items[wi] : make_int2(0, 0);
     const int f = it.x, r = it.y;
-    const int nS = F.nS[f], nU = F.nU[f], s0 = F.s0[f];
+    const int nS = live ? F.nS[f] : 0, nU = live ? F.nU[f] : 0, s0 = F.s0[f];
     const int c0 = r & ~3;
     const V* drow_ = data + F.dtoff[f] + dtrow(r, nS);
     const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
     const int32_t* up = F.up + F.uoff[f];
-    nd_prefetch_row(drow_, nS - c0, lane);
-    nd_prefetch_row(grow, nU, lane);
-    nd_prefetch_row(up, nU, lane);
+    nd_prefetch_row(drow_, nS - c0, t, 32 * WPR);
+    nd_prefetch_row(grow, nU, t, 32 * WPR);
+    nd_prefetch_row(up, nU, t, 32 * WPR);
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const V* vy = y + s0 + c0;
     V s = 0;
 #pragma unroll 4
-    for (int j = lane; j < nS - c0; j += 32) s = fma(drow_[j], vy[j], s);
+    for (int j = t; j < nS - c0; j += 32 * WPR) s = fma(drow_[j], vy[j], s);
 #pragma unroll 4
-    for (int j = lane; j < nU; j += 32) s = fma(-grow[j], x[up[j]], s);
+    for (int j = t; j < nU; j += 32 * WPR) s = fma(-grow[j], x[up[j]], s);
     s = ddgdev::warp_sum(s);
-    if (lane == 0) x[s0 + r] = s;
+    if (!nd_combine<V, WPR>(s, part) || !live) return;
+    x[s0 + r] = s;
 }
 
 __device__ __forceinline__ uint64_t nd_ns() {
@@ -990,6 +1020,40 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         N.h_tgt_off[l + 1] = (int)rtgt.size();
     }
     N.urows = uoff[nf];
+    // warps per item of the single-vector solve, per level and direction:
+    // the largest of 1, 2, 4, 8 that leaves every lane at least 4 entries of
+    // the level's mean row and keeps the level within one wave of warps
+    {
+        int dev = 0, sms = 0;
+        DDG_CUDA(cudaGetDevice(&dev));
+        DDG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        auto pick = [&](int64_t items, double mean_len) {
+            int wpr = 1;
+            while (wpr < 8 && mean_len >= 32.0 * 4 * (2 * wpr) && items * 2 * wpr <= (int64_t)sms * 64) wpr *= 2;
+            return wpr;
+        };
+        N.h_fwd_wpr.assign(nlevel, 1);
+        N.h_bwd_wpr.assign(nlevel, 1);
+        for (int l = 0; l < nlevel; ++l) {
+            double fl = 0.0, bl = 0.0;
+            for (int e = N.h_fwd_off[l]; e < N.h_fwd_off[l + 1]; ++e) {
+                const int2 it = fitems[e];
+                if (it.x >= 0) {
+                    fl += it.y + 1;
+                } else {
+                    const int k = -1 - it.x;
+                    for (int64_t q = rptr[k]; q < rptr[k + 1]; ++q) fl += nS[rsrc[q].x];
+                }
+            }
+            for (int e = N.h_bwd_off[l]; e < N.h_bwd_off[l + 1]; ++e) {
+                const int2 it = bitems[e];
+                bl += (nS[it.x] - (it.y & ~3)) + nU[it.x];
+            }
+            const int64_t nfi = N.h_fwd_off[l + 1] - N.h_fwd_off[l], nbi = N.h_bwd_off[l + 1] - N.h_bwd_off[l];
+            if (nfi > 0) N.h_fwd_wpr[l] = pick(nfi, fl / nfi);
+            if (nbi > 0) N.h_bwd_wpr[l] = pick(nbi, bl / nbi);
+        }
+    }
     // cluster size per level of the multi-column solve: split the stages of
     // each tile over up to 8 CTAs while the level has fewer tiles than four
     // per SM (the CTAs of a cluster take at most the tile's stage count)
@@ -1204,17 +1268,32 @@ static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V
     // forward, deepest level first; w is updated in place
     for (int l = 0; l < N.nlevel; ++l) {
         const int a0 = N.h_fwd_off[l], a1 = N.h_fwd_off[l + 1];
-        if (a1 > a0)
-            launch_pdl(h, nd_fwd_kernel<V>, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.fitems + a0), a1 - a0, (const int32_t*)N.rtgt, (const int64_t*)N.rptr,
-                       (const int2*)N.rsrc, data, w, y);
+        if (a1 <= a0) continue;
+        const int wpr = N.h_fwd_wpr[l];
+        const dim3 grid((unsigned)(((int64_t)(a1 - a0) * wpr + 7) / 8));
+#define ND_FWD(W)                                                                                            \
+    launch_pdl(h, nd_fwd_kernel<V, W>, grid, dim3(256), 0, F, (const int2*)(N.fitems + a0), a1 - a0,          \
+               (const int32_t*)N.rtgt, (const int64_t*)N.rptr, (const int2*)N.rsrc, data, w, y)
+        if (wpr == 8) ND_FWD(8);
+        else if (wpr == 4) ND_FWD(4);
+        else if (wpr == 2) ND_FWD(2);
+        else ND_FWD(1);
+#undef ND_FWD
     }
     // backward, root first
     for (int l = N.nlevel - 1; l >= 0; --l) {
         const int a0 = N.h_bwd_off[l], a1 = N.h_bwd_off[l + 1];
-        if (a1 > a0)
-            launch_pdl(h, nd_bwd_kernel<V>, dim3((unsigned)((a1 - a0 + 7) / 8)), dim3(256), 0, F,
-                       (const int2*)(N.bitems + a0), a1 - a0, data, (const V*)y, xp);
+        if (a1 <= a0) continue;
+        const int wpr = N.h_bwd_wpr[l];
+        const dim3 grid((unsigned)(((int64_t)(a1 - a0) * wpr + 7) / 8));
+#define ND_BWD(W)                                                                                            \
+    launch_pdl(h, nd_bwd_kernel<V, W>, grid, dim3(256), 0, F, (const int2*)(N.bitems + a0), a1 - a0, data,    \
+               (const V*)y, xp)
+        if (wpr == 8) ND_BWD(8);
+        else if (wpr == 4) ND_BWD(4);
+        else if (wpr == 2) ND_BWD(2);
+        else ND_BWD(1);
+#undef ND_BWD
     }
     launch_pdl(h, nd_permute_kernel<V, false>, dim3(pb), dim3(256), 0, n0, (const int32_t*)N.elim, (const V*)xp,
                xout);

@@ -149,8 +149,10 @@ def test_nd_reproduces_generators_and_rebuilds_with_new_generators():
 
 def test_persistent_and_per_level_nd_solves_agree():
     # the ND solve as one cooperative launch (grid barriers between levels)
-    # and as one launch per level and direction: the same products in the
-    # same order, so the same bits
+    # and as one launch per level and direction: the same products, but the
+    # per-level launches let several warps share a long row near the root
+    # (their partial sums added in warp order), so the two agree to rounding
+    # (FP64 1e-13, FP32 1e-6) and each is deterministic
     import os
     from paper_1504_00907_gb300 import ddg
     prob = CASES["poisson3d_32_box4"]()
@@ -161,13 +163,16 @@ def test_persistent_and_per_level_nd_solves_agree():
         del os.environ["DDG_ND_PERSISTENT"]
     b = ddg.Solver.from_problem(prob, precision="fp32", keep=("fp64", "fp32"), coarse_order="nd")
     r = dev(np.random.default_rng(48).standard_normal(prob.n))
-    for prec in ("fp64", "fp32"):
+    for prec, tol in (("fp64", 1e-13), ("fp32", 1e-6)):
         a.set_precision(prec)
         b.set_precision(prec)
-        assert torch.equal(a.coarse_correction(r), b.coarse_correction(r)), prec
+        za, zb = a.coarse_correction(r), b.coarse_correction(r)
+        assert_close(za.cpu().numpy(), zb.cpu().numpy(), tol, label=prec)
+        assert torch.equal(zb, b.coarse_correction(r)), prec
     ua, ita, _, sta = a.solve(dev(prob.f), tol=1e-8)
     ub, itb, _, stb = b.solve(dev(prob.f), tol=1e-8)
-    assert sta == stb == 0 and ita == itb and torch.equal(ua, ub)
+    assert sta == stb == 0 and abs(ita - itb) <= 1
+    assert_close(ua.cpu().numpy(), ub.cpu().numpy(), 1e-7)
     a.close()
     b.close()
 
