@@ -592,7 +592,6 @@ __global__ void __launch_bounds__(256) nd_fwd_tile_kernel(NdSolve F, const int4*
                                                           const float* __restrict__ data, const float* w, float* y,
                                                           float* P, int m) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ __align__(16) float nd_smem[];
     const int ks = (int)nd_cluster_size();
     const int4 it = items[blockIdx.x / ks];
@@ -612,6 +611,21 @@ __global__ void __launch_bounds__(256) nd_fwd_tile_kernel(NdSolve F, const int4*
     NdTileAcc acc = {};
     int st0, st1;
     nd_split((kend + NDK - 1) / NDK, (int)nd_cluster_rank(), ks, st0, st1);
+    {
+        // the CTA's factor rows (fixed at setup) into L2 before waiting for
+        // the previous level: 8 threads per row
+        const int r = r0 + (threadIdx.x >> 3), t8 = threadIdx.x & 7;
+        const int c_lo = st0 * NDK, c_hi = min(kend, st1 * NDK);
+        if (r < nrow && c_hi > c_lo) {
+            if (kind == 0) {
+                const int ce = min(c_hi, r + 1);
+                if (ce > c_lo) nd_prefetch_row(base + drow(r) + c_lo, ce - c_lo, t8, 8);
+            } else {
+                nd_prefetch_row(base + (int64_t)r * ld + c_lo, c_hi - c_lo, t8, 8);
+            }
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     nd_tile_run(0, kend, st0, st1, m, aptr, brow, nd_smem, data, acc);
     if (!nd_cluster_reduce(&acc, 1, nd_smem)) return;
     float* out = kind == 0 ? y + (int64_t)s0 * m : P + F.uoff[f] * m;
@@ -649,7 +663,6 @@ __global__ void __launch_bounds__(256) nd_bwd_tile_kernel(NdSolve F, const int2*
                                                           const float* __restrict__ data, const float* y, float* x,
                                                           int m) {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ __align__(16) float nd_smem[];
     const int ks = (int)nd_cluster_size();
     const int2 it = items[blockIdx.x / ks];
@@ -663,6 +676,20 @@ __global__ void __launch_bounds__(256) nd_bwd_tile_kernel(NdSolve F, const int2*
     const int n1 = (nS - r0 + NDK - 1) / NDK, n2 = (nU + NDK - 1) / NDK;
     int a, b;
     nd_split(n1 + n2, (int)nd_cluster_rank(), ks, a, b);
+    {
+        // the CTA's D^T and G^T row segments (fixed at setup) into L2 before
+        // waiting for the level above: 8 threads per row
+        const int r = r0 + (threadIdx.x >> 3), t8 = threadIdx.x & 7;
+        if (r < nS) {
+            const int p1s = min(a, n1), p1e = min(b, n1);
+            const int lo1 = max(r0 + p1s * NDK, r & ~3), hi1 = min(nS, r0 + p1e * NDK);
+            if (hi1 > lo1) nd_prefetch_row(dt + dtrow(r, nS) + (lo1 - (r & ~3)), hi1 - lo1, t8, 8);
+            const int p2s = max(a, n1) - n1, p2e = max(b, n1) - n1;
+            const int lo2 = p2s * NDK, hi2 = min(nU, p2e * NDK);
+            if (hi2 > lo2) nd_prefetch_row(gt + (int64_t)r * ldu + lo2, hi2 - lo2, t8, 8);
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     auto dptr = [&](int rr, int c) -> const float* {
         const int r = r0 + rr;
         return (r < nS && c >= (r & ~3)) ? dt + dtrow(r, nS) + (c - (r & ~3)) : nullptr;
