@@ -263,6 +263,7 @@ struct NdCoarse {
     std::vector<int> h_mf_off, h_mb_off, h_tgt_off;
     std::vector<int> h_mf_ks, h_mb_ks;   // CTAs per tile (one cluster) per level
     std::vector<int> h_fwd_wpr, h_bwd_wpr;   // warps per item of the single-vector solve, per level
+    std::vector<int> h_fwd_pf, h_bwd_pf;     // whether a level prefetches its factor rows into L2
     int64_t urows = 0;
     int32_t *fwd_off = nullptr, *bwd_off = nullptr;   // device copies
     unsigned* bar = nullptr;           // grid barrier of the persistent solve

@@ -222,7 +222,7 @@ template <typename V, int WPR>
 __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
                                                      const int32_t* __restrict__ tgt, const int64_t* __restrict__ ptr,
                                                      const int2* __restrict__ src, const V* __restrict__ data, V* w,
-                                                     V* y) {
+                                                     V* y, int pf) {
     __shared__ V part[8];
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) / WPR, lane = threadIdx.x & 31;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
     if (it.x >= 0) {
         const int f = it.x, i = it.y;
         const V* row = data + F.doff[f] + drow(i);
-        if (live) nd_prefetch_row(row, i + 1, t, 32 * WPR);
+        if (live && pf) nd_prefetch_row(row, i + 1, t, 32 * WPR);
         asm volatile("griddepcontrol.wait;" ::: "memory");
         const V* v = w + F.s0[f];
         if (live) {
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
     } else {
         const int k = -1 - it.x;
         const int64_t e0 = ptr[k], e1 = ptr[k + 1];
-        for (int64_t e = e0; e < e1; ++e) {
+        for (int64_t e = e0; pf && e < e1; ++e) {
             const int2 fu = src[e];
             const int nS = F.nS[fu.x];
             nd_prefetch_row(data + F.goff[fu.x] + (int64_t)fu.y * r4(nS), nS, t, 32 * WPR);
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256) nd_fwd_kernel(NdSolve F, const int2* __re
 // wait, as forward)
 template <typename V, int WPR>
 __global__ void __launch_bounds__(256) nd_bwd_kernel(NdSolve F, const int2* __restrict__ items, int n,
-                                                     const V* __restrict__ data, const V* y, V* x) {
+                                                     const V* __restrict__ data, const V* y, V* x, int pf) {
     __shared__ V part[8];
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int wi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) / WPR, lane = threadIdx.x & 31;
@@ -288,9 +288,11 @@ __global__ void __launch_bounds__(256) nd_bwd_kernel(NdSolve F, const int2* __re
     const V* drow_ = data + F.dtoff[f] + dtrow(r, nS);
     const V* grow = data + F.gtoff[f] + (int64_t)r * r4(nU);
     const int32_t* up = F.up + F.uoff[f];
-    nd_prefetch_row(drow_, nS - c0, t, 32 * WPR);
-    nd_prefetch_row(grow, nU, t, 32 * WPR);
-    nd_prefetch_row(up, nU, t, 32 * WPR);
+    if (pf) {
+        nd_prefetch_row(drow_, nS - c0, t, 32 * WPR);
+        nd_prefetch_row(grow, nU, t, 32 * WPR);
+        nd_prefetch_row(up, nU, t, 32 * WPR);
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const V* vy = y + s0 + c0;
     V s = 0;
@@ -1061,6 +1063,8 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
         };
         N.h_fwd_wpr.assign(nlevel, 1);
         N.h_bwd_wpr.assign(nlevel, 1);
+        N.h_fwd_pf.assign(nlevel, 1);
+        N.h_bwd_pf.assign(nlevel, 1);
         for (int l = 0; l < nlevel; ++l) {
             double fl = 0.0, bl = 0.0;
             for (int e = N.h_fwd_off[l]; e < N.h_fwd_off[l + 1]; ++e) {
@@ -1079,6 +1083,11 @@ void nd_coarse_setup(ddg_handle h, const std::vector<int>& bI, const std::vector
             const int64_t nfi = N.h_fwd_off[l + 1] - N.h_fwd_off[l], nbi = N.h_bwd_off[l + 1] - N.h_bwd_off[l];
             if (nfi > 0) N.h_fwd_wpr[l] = pick(nfi, fl / nfi);
             if (nbi > 0) N.h_bwd_wpr[l] = pick(nbi, bl / nbi);
+            // prefetch a level's factor rows only while they fit well inside
+            // L2 (12 M elements: 48 MB in FP32, 96 MB in FP64); larger levels
+            // would evict their own prefetched lines before use
+            N.h_fwd_pf[l] = fl <= 12e6 ? 1 : 0;
+            N.h_bwd_pf[l] = bl <= 12e6 ? 1 : 0;
         }
     }
     // cluster size per level of the multi-column solve: split the stages of
@@ -1300,7 +1309,7 @@ static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V
         const dim3 grid((unsigned)(((int64_t)(a1 - a0) * wpr + 7) / 8));
 #define ND_FWD(W)                                                                                            \
     launch_pdl(h, nd_fwd_kernel<V, W>, grid, dim3(256), 0, F, (const int2*)(N.fitems + a0), a1 - a0,          \
-               (const int32_t*)N.rtgt, (const int64_t*)N.rptr, (const int2*)N.rsrc, data, w, y)
+               (const int32_t*)N.rtgt, (const int64_t*)N.rptr, (const int2*)N.rsrc, data, w, y, N.h_fwd_pf[l])
         if (wpr == 8) ND_FWD(8);
         else if (wpr == 4) ND_FWD(4);
         else if (wpr == 2) ND_FWD(2);
@@ -1315,7 +1324,7 @@ static void nd_solve_t(ddg_handle h, const V* data, const V* c, V* y, V* xout, V
         const dim3 grid((unsigned)(((int64_t)(a1 - a0) * wpr + 7) / 8));
 #define ND_BWD(W)                                                                                            \
     launch_pdl(h, nd_bwd_kernel<V, W>, grid, dim3(256), 0, F, (const int2*)(N.bitems + a0), a1 - a0, data,    \
-               (const V*)y, xp)
+               (const V*)y, xp, N.h_bwd_pf[l])
         if (wpr == 8) ND_BWD(8);
         else if (wpr == 4) ND_BWD(4);
         else if (wpr == 2) ND_BWD(2);
